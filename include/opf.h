@@ -1,0 +1,201 @@
+/*
+ * opf.h -- C ABI of the B300 reduced-space OPF library (libopf.so).
+ *
+ * Method: feasible reduced-space optimal power flow (Pacaud, Maldonado,
+ * Shin, Schanen, Anitescu, arXiv 2110.02590).  The library evaluates, on one
+ * GPU and in FP64, the hot path of the method:
+ *   - the Newton-Raphson power flow that keeps every iterate on g(x,u) = 0
+ *     (eq. projection:newtonraphson, Sec. III-A), with a numeric LU
+ *     refactorisation of G_x = dg/dx on a sparsity pattern fixed at load;
+ *   - the reduced gradient of the scaled augmented Lagrangian by the adjoint
+ *     method (Prop. 1, Sec. III-B; eq. gradient_auglag, Sec. IV-A);
+ *   - the dense reduced Hessian from batched adjoint-adjoint Hessian-vector
+ *     products (Prop. 2, Sec. III-B; Sec. III-C "Reduced Hessian").
+ *
+ * Notation and layouts (all FP64, per unit):
+ *   buses 0..n_bus-1; ref_bus carries exactly one generator; the PV buses are
+ *   the other generator buses and the PQ buses the rest, both in ascending id;
+ *   u = (v_ref, v_pv, p_pv), n_u = 1 + 2 n_pv          (eq. statecontrol)
+ *   x = (theta_pv, theta_pq, v_pq), n_x = n_pv + 2 n_pq
+ *   g = (P_pv - p_pv + pd_pv, P_pq + pd_pq, Q_pq + qd_pq), P,Q = injections
+ *   c = (|S_f|^2 per branch, |S_t|^2 per branch, v_pq, p_ref, q_ref, q_pv),
+ *       m = 2 n_branch + n_pq + n_pv + 2                  (Sec. II-B, IV-A)
+ *   F = sigma_f f + sum_i [ y_i sigma_i (c_i - s_i) + rho/2 sigma_i^2 (c_i - s_i)^2 ]
+ *       (scaled augmented Lagrangian, Sec. IV-A "Scaling"), f = generation cost.
+ *   Branches use the pi model: series y = 1/(r + jx), tap on the from side,
+ *   charging b/2 at each end.
+ *
+ * Conventions: every call is ordered on the context's CUDA stream; pointers
+ * are device pointers owned by the caller unless marked (host); outputs that
+ * are host structs are valid when the call returns (the call synchronises
+ * the stream).  No call throws or aborts: failures return an opf_status.
+ * The library never falls back to the CPU.
+ */
+#ifndef OPF_H
+#define OPF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OPF_OK = 0,
+  OPF_EINVAL = 1,     /* bad argument or network (message: opf_last_error) */
+  OPF_ENOMEM = 2,     /* device or host allocation failed */
+  OPF_ECUDA = 3,      /* a CUDA runtime call failed */
+  OPF_ENOCONV = 4,    /* Newton-Raphson hit max_it or produced a non-finite residual */
+  OPF_ESINGULAR = 5,  /* a zero or non-finite pivot in the LU refactorisation */
+  OPF_ENOTPD = 6,     /* dense Cholesky failed after the inertia corrections */
+  OPF_ESTATE = 7,     /* gradient/Hessian requested without a converged power flow */
+  OPF_ETIMEOUT = 8    /* a bounded device-side wait gave up */
+} opf_status;
+
+typedef struct opf_ctx opf_ctx;
+
+/* Network description (all arrays host, copied at load). */
+typedef struct {
+  int n_bus, n_branch, n_gen, ref_bus;
+  const double *pd, *qd;               /* nominal loads [n_bus] */
+  const double *vmin, *vmax;           /* voltage bounds [n_bus] */
+  const int *br_from, *br_to;          /* branch ends [n_branch] */
+  const double *br_r, *br_x, *br_b;    /* series r, x, total charging b [n_branch] */
+  const double *br_tap, *br_rate;      /* off-nominal tap (1 = line), MVA rating [n_branch] */
+  const int *gen_bus;                  /* one generator per bus at most [n_gen] */
+  const double *gen_c2, *gen_c1, *gen_c0;  /* cost c2 p^2 + c1 p + c0, p in p.u. [n_gen] */
+  const double *gen_pmin, *gen_pmax, *gen_qmin, *gen_qmax;  /* [n_gen] */
+  double base_mva;
+} opf_network_desc;
+
+/*
+ * opf_load_network: validate the network, build the index maps (eq.
+ * statecontrol), run the symbolic analysis of G_x once (exact minimum degree
+ * on the bus graph, filled pattern, level sets; Sec. V-A "Sparse linear
+ * system": the pattern is fixed by the topology), upload everything and
+ * allocate all workspaces.  `stream` is a cudaStream_t (NULL = legacy
+ * default stream).  Errors: OPF_EINVAL (branch end out of range or a
+ * self-loop, r = x = 0, two generators on a bus, no generator on ref_bus,
+ * a state bus not connected to the slack), OPF_ENOMEM, OPF_ECUDA.
+ * On success *out owns all device memory until opf_free.
+ */
+opf_status opf_load_network(const opf_network_desc* desc, void* stream, opf_ctx** out);
+void opf_free(opf_ctx* ctx);
+opf_status opf_set_stream(opf_ctx* ctx, void* stream);
+
+/* Sizes (host outputs; any pointer may be NULL). */
+opf_status opf_dims(const opf_ctx* ctx, int* nx, int* nu, int* m, int* npv, int* npq);
+
+/*
+ * Symbolic analysis export, for bit-exact comparison (host outputs).
+ * opf_symbolic_sizes: nnz of the filled pattern (L + U + diagonal), number of
+ * state buses (n_bus - 1), number of forward and backward levels.
+ * opf_symbolic_export: bus_order[n_state_bus] (elimination order of the
+ * buses), perm[n_x] (perm[k] = x index of the k-th pivot; the variables of a
+ * bus are consecutive, theta before v), rowptr[n_x+1] and colidx[nnz] (row-wise
+ * filled pattern in pivot order, sorted), lev_f[n_x] (level of row k of L:
+ * 1 + the largest level among its off-diagonal columns, 0 if none), lev_b[n_x]
+ * (the same for the rows of U, counted from the last row).
+ */
+opf_status opf_symbolic_sizes(const opf_ctx* ctx, int* nnz, int* n_state_bus, int* n_lev_f,
+                              int* n_lev_b);
+opf_status opf_symbolic_export(const opf_ctx* ctx, int* bus_order, int* perm, int* rowptr,
+                               int* colidx, int* lev_f, int* lev_b);
+
+/*
+ * Host-only symbolic analysis (no GPU needed): the same ordering, filled
+ * pattern and level sets that opf_load_network computes, for callers that
+ * want to inspect or compare the integer structures.  Export layout as for
+ * opf_symbolic_export.  Errors: OPF_EINVAL (invalid network).
+ */
+typedef struct opf_symbolic opf_symbolic;
+opf_status opf_symbolic_analyze(const opf_network_desc* desc, opf_symbolic** out);
+opf_status opf_symbolic_info(const opf_symbolic* sym, int* nx, int* nnz, int* n_state_bus,
+                             int* n_lev_f, int* n_lev_b);
+opf_status opf_symbolic_get(const opf_symbolic* sym, int* bus_order, int* perm, int* rowptr,
+                            int* colidx, int* lev_f, int* lev_b);
+void opf_symbolic_free(opf_symbolic* sym);
+
+typedef struct {
+  double tol;  /* stop when ||g||_2 < tol (the paper uses 1e-10, Sec. V-A) */
+  int max_it;  /* Newton updates allowed (default 20) */
+} opf_pf_opts;
+
+typedef struct {
+  int iterations;   /* Newton updates performed */
+  double res2;      /* ||g||_2 at the returned x */
+  double resinf;    /* ||g||_inf at the returned x */
+} opf_pf_info;
+
+/*
+ * opf_powerflow: Newton-Raphson x <- x - G_x^{-1} g (eq.
+ * projection:newtonraphson) at controls u[n_u] and loads pd, qd [n_bus]
+ * (NULL = the nominal loads of the description), starting from
+ * x_inout[n_x] and overwriting it.  Each iteration evaluates g and the
+ * Jacobian values into the fixed pattern, refactorises, and solves; the
+ * factors of the Jacobian at the returned x stay in the context for the
+ * gradient and Hessian.  opts NULL = {1e-10, 20}.  info (host) may be NULL.
+ * Errors: OPF_ENOCONV, OPF_ESINGULAR (the context then has no valid state).
+ */
+opf_status opf_powerflow(opf_ctx* ctx, const double* u, const double* pd, const double* qd,
+                         double* x_inout, const opf_pf_opts* opts, opf_pf_info* info);
+
+/* Augmented-Lagrangian inputs: sigma_c, y, s [m] device arrays; omega [m]
+ * optional second-order weights (NULL = rho sigma_c^2, i.e. the exact Hessian
+ * of F; the Schur complement of Prop. 3 uses rho sigma^2 Sigma_s / (rho sigma^2
+ * + Sigma_s)). */
+typedef struct {
+  double sigma_f;
+  double rho;
+  const double* sigma_c;
+  const double* y;
+  const double* s;
+  const double* omega;
+} opf_al_params;
+
+/*
+ * opf_reduced_gradient (Prop. 1 with the AL functional of eq.
+ * gradient_auglag, scaled as in Sec. IV-A): at the state of the last
+ * converged opf_powerflow, solve G_x^T lambda = -(d_x F)^T with the stored
+ * factors (U^T then L^T) and form grad_u = d_u F + lambda^T G_u.  Outputs
+ * (device, each may be NULL): F[1], grad_u[n_u], grad_s[m] = -phi' with
+ * phi'_i = y_i sigma_i + rho sigma_i^2 (c_i - s_i), c[m], lambda[n_x],
+ * grad_pd[n_bus], grad_qd[n_bus] (total derivatives of F w.r.t. the loads).
+ * Errors: OPF_ESTATE without a converged power flow.
+ */
+opf_status opf_reduced_gradient(opf_ctx* ctx, const opf_al_params* p, double* F,
+                                double* grad_u, double* grad_s, double* c, double* lambda,
+                                double* grad_pd, double* grad_qd);
+
+typedef struct {
+  int block_k;  /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32 (0 = 8) */
+  int grid;     /* resident CTA tiles (0 = two per SM) */
+  int plain;    /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
+} opf_hess_opts;
+
+typedef struct {
+  int block_k, grid, tiles, launches;
+  float ms_total;  /* device time of the call (CUDA events on the context stream) */
+  float ms_hvp;    /* device time of the HVP phase alone */
+} opf_hess_info;
+
+/*
+ * opf_reduced_hessian: the dense reduced Hessian H[n_u * n_u] (column-major)
+ * of F (or of the omega-weighted functional) at the state of the last
+ * converged power flow, from n_u adjoint-adjoint HVPs (Prop. 2): for each
+ * block of directions W, G_x Z = -G_u W (L then U sweeps), the second-order
+ * terms of the injections, line flows and costs along every branch, then
+ * G_x^T Psi = -(l_xu W + l_xx Z) (U^T then L^T sweeps) and
+ * H[:, block] = l_uu W + l_ux Z + G_u^T Psi.  The factors of G_x are the ones
+ * left by opf_powerflow (factorised once, Sec. III-C).  H is not
+ * symmetrised.  opts/info may be NULL.  Errors: OPF_ESTATE, OPF_EINVAL.
+ */
+opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts,
+                               double* H, opf_hess_info* info);
+
+/* Human-readable status and the last error message of this thread. */
+const char* opf_status_str(int status);
+const char* opf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPF_H */

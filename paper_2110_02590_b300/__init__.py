@@ -1,0 +1,268 @@
+"""B300-native reduced-space OPF hot path (arXiv 2110.02590): Python binding.
+
+Argument marshalling over the C ABI of ``libopf.so`` (``include/opf.h``).
+PyTorch supplies device memory and the CUDA stream; every step of the path
+runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing, building a context raises.
+
+    from paper_2110_02590_b300 import synth, OPFContext
+    net = synth.workload("large9200")
+    ctx = OPFContext(net)
+    x, info = ctx.powerflow(u)                 # u: cuda float64 tensor
+    g = ctx.reduced_gradient(al)               # al: dict of cuda tensors
+    H, hinfo = ctx.reduced_hessian(al, block_k=8)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libopf.so")
+_lib = None
+
+OPF_STATUS = {0: "OPF_OK", 1: "OPF_EINVAL", 2: "OPF_ENOMEM", 3: "OPF_ECUDA", 4: "OPF_ENOCONV",
+              5: "OPF_ESINGULAR", 6: "OPF_ENOTPD", 7: "OPF_ESTATE", 8: "OPF_ETIMEOUT"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class NetworkDesc(C.Structure):
+    _fields_ = [("n_bus", C.c_int), ("n_branch", C.c_int), ("n_gen", C.c_int), ("ref_bus", C.c_int),
+                ("pd", _dp), ("qd", _dp), ("vmin", _dp), ("vmax", _dp),
+                ("br_from", _ip), ("br_to", _ip),
+                ("br_r", _dp), ("br_x", _dp), ("br_b", _dp), ("br_tap", _dp), ("br_rate", _dp),
+                ("gen_bus", _ip),
+                ("gen_c2", _dp), ("gen_c1", _dp), ("gen_c0", _dp),
+                ("gen_pmin", _dp), ("gen_pmax", _dp), ("gen_qmin", _dp), ("gen_qmax", _dp),
+                ("base_mva", C.c_double)]
+
+
+class PfOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_it", C.c_int)]
+
+
+class PfInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("res2", C.c_double), ("resinf", C.c_double)]
+
+
+class AlParams(C.Structure):
+    _fields_ = [("sigma_f", C.c_double), ("rho", C.c_double), ("sigma_c", C.c_void_p),
+                ("y", C.c_void_p), ("s", C.c_void_p), ("omega", C.c_void_p)]
+
+
+class HessOpts(C.Structure):
+    _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int)]
+
+
+class HessInfo(C.Structure):
+    _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("tiles", C.c_int), ("launches", C.c_int),
+                ("ms_total", C.c_float), ("ms_hvp", C.c_float)]
+
+
+class OPFError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {OPF_STATUS.get(status, status)} ({lib().opf_last_error().decode()})")
+
+
+def lib():
+    """Load libopf.so (built in-tree by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libopf.so not built ({LIB_PATH}); run python -m paper_2110_02590_b300.build")
+        L = C.CDLL(LIB_PATH)
+        L.opf_load_network.argtypes = [C.POINTER(NetworkDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.opf_free.argtypes = [C.c_void_p]
+        L.opf_free.restype = None
+        L.opf_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.opf_dims.argtypes = [C.c_void_p] + [_ip] * 5
+        L.opf_symbolic_sizes.argtypes = [C.c_void_p] + [_ip] * 4
+        L.opf_symbolic_export.argtypes = [C.c_void_p] + [_ip] * 6
+        L.opf_powerflow.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.POINTER(PfOpts), C.POINTER(PfInfo)]
+        L.opf_reduced_gradient.argtypes = [C.c_void_p, C.POINTER(AlParams)] + [C.c_void_p] * 7
+        L.opf_reduced_hessian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
+                                          C.POINTER(HessInfo)]
+        L.opf_symbolic_analyze.argtypes = [C.POINTER(NetworkDesc), C.POINTER(C.c_void_p)]
+        L.opf_symbolic_info.argtypes = [C.c_void_p] + [_ip] * 5
+        L.opf_symbolic_get.argtypes = [C.c_void_p] + [_ip] * 6
+        L.opf_symbolic_free.argtypes = [C.c_void_p]
+        L.opf_symbolic_free.restype = None
+        L.opf_status_str.restype = C.c_char_p
+        L.opf_status_str.argtypes = [C.c_int]
+        L.opf_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names declared in include/opf.h (checked against the library by the tests)."""
+    import re
+    hdr = os.path.join(_HERE, "..", "include", "opf.h")
+    with open(hdr) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:opf_status|void|const char\*)\s+(opf_\w+)\s*\(", text, re.M)))
+
+
+def _make_desc(net):
+    """NetworkDesc over contiguous host copies of the network tables (kept alive by the caller)."""
+    a = lambda v: np.ascontiguousarray(v, dtype=np.float64)  # noqa: E731
+    ai = lambda v: np.ascontiguousarray(v, dtype=np.int32)  # noqa: E731
+    k = dict(pd=a(net.pd), qd=a(net.qd), vmin=a(net.vmin), vmax=a(net.vmax),
+             f=ai(net.br_from), t=ai(net.br_to), r=a(net.br_r), x=a(net.br_x), b=a(net.br_b),
+             tap=a(net.br_tap), rate=a(net.br_rate), gbus=ai(net.gen_bus), c2=a(net.gen_c2),
+             c1=a(net.gen_c1), c0=a(net.gen_c0), pmin=a(net.gen_pmin), pmax=a(net.gen_pmax),
+             qmin=a(net.gen_qmin), qmax=a(net.gen_qmax))
+    d = lambda v: v.ctypes.data_as(_dp)  # noqa: E731
+    i = lambda v: v.ctypes.data_as(_ip)  # noqa: E731
+    desc = NetworkDesc(int(net.n_bus), int(net.n_branch), int(net.n_gen), int(net.ref_bus),
+                       d(k["pd"]), d(k["qd"]), d(k["vmin"]), d(k["vmax"]), i(k["f"]), i(k["t"]),
+                       d(k["r"]), d(k["x"]), d(k["b"]), d(k["tap"]), d(k["rate"]), i(k["gbus"]),
+                       d(k["c2"]), d(k["c1"]), d(k["c0"]), d(k["pmin"]), d(k["pmax"]), d(k["qmin"]),
+                       d(k["qmax"]), float(getattr(net, "base_mva", 100.0)))
+    return desc, k
+
+
+def symbolic_analyze(net) -> dict:
+    """Host-only symbolic analysis of G_x (ordering, filled pattern, level sets); needs no GPU."""
+    L = lib()
+    desc, keep = _make_desc(net)
+    h = C.c_void_p()
+    st = L.opf_symbolic_analyze(C.byref(desc), C.byref(h))
+    if st != 0:
+        raise OPFError(st, "opf_symbolic_analyze")
+    try:
+        nx, nnz, nsb, nlf, nlb = (C.c_int() for _ in range(5))
+        L.opf_symbolic_info(h, *[C.byref(v) for v in (nx, nnz, nsb, nlf, nlb)])
+        out = dict(bus_order=np.zeros(nsb.value, np.int32), perm=np.zeros(nx.value, np.int32),
+                   rowptr=np.zeros(nx.value + 1, np.int32), colidx=np.zeros(nnz.value, np.int32),
+                   lev_f=np.zeros(nx.value, np.int32), lev_b=np.zeros(nx.value, np.int32))
+        L.opf_symbolic_get(h, *[out[k].ctypes.data_as(_ip) for k in
+                                ("bus_order", "perm", "rowptr", "colidx", "lev_f", "lev_b")])
+        out["nlev_f"], out["nlev_b"] = nlf.value, nlb.value
+        return out
+    finally:
+        L.opf_symbolic_free(h)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class OPFContext:
+    """One network on one GPU: symbolic analysis, factors and workspaces."""
+
+    def __init__(self, net, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        L = lib()
+        self.net = net
+        desc, self._keep = _make_desc(net)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.opf_load_network(C.byref(desc), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(h))
+        if st != 0:
+            raise OPFError(st, "opf_load_network")
+        self.h = h
+        dims = [C.c_int() for _ in range(5)]
+        L.opf_dims(h, *[C.byref(v) for v in dims])
+        self.nx, self.nu, self.m, self.npv, self.npq = (v.value for v in dims)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.opf_free(self.h)
+            self.h = None
+
+    def _sync_stream(self):
+        lib().opf_set_stream(self.h, C.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream))
+
+    def _dev(self, v):
+        t = self.torch
+        if isinstance(v, t.Tensor):
+            if v.device != self.device or v.dtype != t.float64 or not v.is_contiguous():
+                raise ValueError("expected a contiguous float64 tensor on the context's device")
+            return v
+        return t.as_tensor(np.ascontiguousarray(v, dtype=np.float64), device=self.device)
+
+    # ---------------------------------------------------------------- symbolic
+    def symbolic(self) -> dict:
+        L = lib()
+        nnz, nsb, nlf, nlb = (C.c_int() for _ in range(4))
+        L.opf_symbolic_sizes(self.h, C.byref(nnz), C.byref(nsb), C.byref(nlf), C.byref(nlb))
+        out = dict(bus_order=np.zeros(nsb.value, np.int32), perm=np.zeros(self.nx, np.int32),
+                   rowptr=np.zeros(self.nx + 1, np.int32), colidx=np.zeros(nnz.value, np.int32),
+                   lev_f=np.zeros(self.nx, np.int32), lev_b=np.zeros(self.nx, np.int32))
+        st = L.opf_symbolic_export(self.h, *[out[k].ctypes.data_as(_ip) for k in
+                                             ("bus_order", "perm", "rowptr", "colidx", "lev_f", "lev_b")])
+        if st != 0:
+            raise OPFError(st, "opf_symbolic_export")
+        out["nlev_f"], out["nlev_b"] = nlf.value, nlb.value
+        return out
+
+    # ---------------------------------------------------------------- power flow
+    def powerflow(self, u, pd=None, qd=None, x0=None, tol=1e-10, max_it=20, check=True):
+        """Newton-Raphson from x0 (default flat start).  Returns (x, info)."""
+        t = self.torch
+        self._sync_stream()
+        u = self._dev(u)
+        pd = None if pd is None else self._dev(pd)
+        qd = None if qd is None else self._dev(qd)
+        if x0 is None:
+            x = t.cat([t.zeros(self.npv + self.npq, dtype=t.float64, device=self.device),
+                       t.ones(self.npq, dtype=t.float64, device=self.device)])
+        else:
+            x = self._dev(x0).clone()
+        info = PfInfo()
+        st = lib().opf_powerflow(self.h, _ptr(u), _ptr(pd), _ptr(qd), _ptr(x), C.byref(PfOpts(tol, max_it)),
+                                 C.byref(info))
+        res = dict(status=st, iterations=info.iterations, res2=info.res2, resinf=info.resinf)
+        if check and st != 0:
+            raise OPFError(st, "opf_powerflow")
+        return x, res
+
+    def _al(self, al):
+        keep = [self._dev(al["sigma_c"]), self._dev(al["y"]), self._dev(al["s"])]
+        om = al.get("omega")
+        if om is not None:
+            keep.append(self._dev(om))
+        p = AlParams(float(al["sigma_f"]), float(al["rho"]), keep[0].data_ptr(), keep[1].data_ptr(),
+                     keep[2].data_ptr(), keep[3].data_ptr() if om is not None else None)
+        return p, keep
+
+    def reduced_gradient(self, al) -> dict:
+        """Prop. 1 gradient of the scaled AL at the last converged power flow."""
+        t = self.torch
+        self._sync_stream()
+        p, keep = self._al(al)
+        z = lambda n: t.empty(n, dtype=t.float64, device=self.device)  # noqa: E731
+        out = dict(F=z(1), grad_u=z(self.nu), grad_s=z(self.m), c=z(self.m), lam=z(self.nx),
+                   grad_pd=z(self.net.n_bus), grad_qd=z(self.net.n_bus))
+        st = lib().opf_reduced_gradient(self.h, C.byref(p), *[_ptr(out[k]) for k in
+                                                             ("F", "grad_u", "grad_s", "c", "lam", "grad_pd",
+                                                              "grad_qd")])
+        if st != 0:
+            raise OPFError(st, "opf_reduced_gradient")
+        return out
+
+    def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None):
+        """Dense reduced Hessian (n_u x n_u) by adjoint-adjoint HVPs (Prop. 2).
+
+        Returns (H, info); H is column-major in memory, i.e. H_t[j] is column j.
+        """
+        t = self.torch
+        self._sync_stream()
+        p, keep = self._al(al)
+        H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
+        info = HessInfo()
+        st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(HessOpts(int(block_k), int(grid), int(plain))),
+                                       _ptr(H), C.byref(info))
+        if st != 0:
+            raise OPFError(st, "opf_reduced_hessian")
+        return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
+                         ms_total=info.ms_total, ms_hvp=info.ms_hvp)

@@ -1,0 +1,529 @@
+// C ABI of libopf (declared in include/opf.h): set-up, power flow, reduced
+// gradient and reduced Hessian.  Host orchestration only; all arithmetic of
+// the path runs in the kernels of opf_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "opf_internal.h"
+
+using namespace opf;
+
+static thread_local std::string g_err;
+
+#define FAIL(st, msg)  \
+  do {                 \
+    g_err = (msg);     \
+    return (st);       \
+  } while (0)
+
+#define CK(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      g_err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return OPF_ECUDA;                                                     \
+    }                                                                       \
+  } while (0)
+
+template <class T>
+static opf_status dalloc(opf_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    FAIL(OPF_ENOMEM, "device allocation failed");
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return OPF_OK;
+}
+
+template <class T>
+static opf_status dupload(opf_ctx* c, T** p, const std::vector<T>& v) {
+  opf_status st = dalloc(c, p, v.size());
+  if (st) return st;
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return OPF_OK;
+}
+
+#define TRY(x)                     \
+  do {                             \
+    opf_status s_ = (x);           \
+    if (s_ != OPF_OK) return s_;   \
+  } while (0)
+
+static int find_pos(const Symbolic& s, int row, int col) {
+  int lo = s.rp[row], hi = s.rp[row + 1] - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (s.ci[mid] < col) lo = mid + 1; else hi = mid;
+  }
+  return (s.ci[lo] == col) ? lo : -1;
+}
+
+static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
+  std::string why = build_hostnet(d, c->h);
+  if (!why.empty()) FAIL(OPF_EINVAL, why);
+  HostNet& h = c->h;
+  Symbolic& s = c->s;
+  build_symbolic(h, s);
+  const int nb = h.nb, nl = h.nl, nx = h.nx, nnz = (int)s.ci.size();
+  CK(cudaGetDevice(&c->device));
+  CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+
+  // pivot-order positions of the bus variables
+  std::vector<int> pth(nb, -1), pvv(nb, -1);
+  for (int i = 0; i < nb; i++) {
+    if (h.xth[i] >= 0) pth[i] = s.iperm[h.xth[i]];
+    if (h.xv[i] >= 0) pvv[i] = s.iperm[h.xv[i]];
+  }
+  // Jacobian slots (positions of the entries of G_x in the filled pattern)
+  std::vector<int> slot_self(4 * (size_t)nb, -1), slot_adj(8 * (size_t)nl, -1);
+  for (int i = 0; i < nb; i++) {
+    if (h.type[i] == REF) continue;
+    const bool pq = h.type[i] == PQ;
+    slot_self[4 * i + 0] = find_pos(s, pth[i], pth[i]);
+    if (pq) {
+      slot_self[4 * i + 1] = find_pos(s, pth[i], pvv[i]);
+      slot_self[4 * i + 2] = find_pos(s, pvv[i], pth[i]);
+      slot_self[4 * i + 3] = find_pos(s, pvv[i], pvv[i]);
+    }
+    for (int k = h.adj_ptr[i]; k < h.adj_ptr[i + 1]; k++) {
+      const int e = h.adj[k], l = e >> 1;
+      const int o = (e & 1) ? h.f[l] : h.t[l];
+      int* sl = &slot_adj[4 * (size_t)e];
+      if (h.type[o] != REF) sl[0] = find_pos(s, pth[i], pth[o]);
+      if (h.type[o] == PQ) sl[1] = find_pos(s, pth[i], pvv[o]);
+      if (pq && h.type[o] != REF) sl[2] = find_pos(s, pvv[i], pth[o]);
+      if (pq && h.type[o] == PQ) sl[3] = find_pos(s, pvv[i], pvv[o]);
+      for (int q = 0; q < 4; q++)
+        if (sl[q] == -1 && ((q == 0 && h.type[o] != REF) || (q == 1 && h.type[o] == PQ) ||
+                            (q == 2 && pq && h.type[o] != REF) || (q == 3 && pq && h.type[o] == PQ)))
+          FAIL(OPF_EINVAL, "internal: Jacobian entry outside the filled pattern");
+    }
+  }
+  // transposition map
+  std::vector<int> tmap(nnz);
+  for (int i = 0; i < nx; i++)
+    for (int p = s.rp[i]; p < s.rp[i + 1]; p++) tmap[p] = find_pos(s, s.ci[p], i);
+  // columns of L: (row, position in row) sorted by row
+  std::vector<int> lcnt(nx + 1, 0);
+  for (int r = 0; r < nx; r++)
+    for (int p = s.rp[r]; p < s.dp[r]; p++) lcnt[s.ci[p] + 1]++;
+  for (int j = 0; j < nx; j++) lcnt[j + 1] += lcnt[j];
+  std::vector<int> lcol_row(lcnt[nx]), lcol_pos(lcnt[nx]);
+  {
+    std::vector<int> fill(lcnt.begin(), lcnt.end() - 1);
+    for (int r = 0; r < nx; r++)
+      for (int p = s.rp[r]; p < s.dp[r]; p++) {
+        const int j = s.ci[p];
+        lcol_row[fill[j]] = r;
+        lcol_pos[fill[j]++] = p;
+      }
+  }
+  // level row lists and LU tasks
+  auto level_lists = [&](const std::vector<int>& lev, int nlev, std::vector<int>& ptr, std::vector<int>& rows) {
+    ptr.assign(nlev + 1, 0);
+    for (int i = 0; i < nx; i++) ptr[lev[i] + 1]++;
+    for (int k = 0; k < nlev; k++) ptr[k + 1] += ptr[k];
+    rows.assign(nx, 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < nx; i++) rows[fill[lev[i]]++] = i;
+  };
+  std::vector<int> lrows_f, lrows_b;
+  level_lists(s.lev_f, s.nlev_f, c->h_lev_ptr_f, lrows_f);
+  level_lists(s.lev_b, s.nlev_b, c->h_lev_ptr_b, lrows_b);
+  std::vector<int> task_col, task_k;
+  c->h_task_ptr.assign(s.nlev_f + 1, 0);
+  for (int lv = 0; lv < s.nlev_f; lv++) {
+    for (int q = c->h_lev_ptr_f[lv]; q < c->h_lev_ptr_f[lv + 1]; q++) {
+      const int j = lrows_f[q];
+      for (int k = lcnt[j]; k < lcnt[j + 1]; k++) {
+        task_col.push_back(j);
+        task_k.push_back(k);
+      }
+    }
+    c->h_task_ptr[lv + 1] = (int)task_col.size();
+  }
+  // control buses: slack first, then PV
+  std::vector<int> gn_bus, gn_of(nb, -1), ubus(h.nu, -1);
+  gn_bus.push_back(h.ref);
+  for (int i = 0; i < nb; i++)
+    if (h.type[i] == PV) gn_bus.push_back(i);
+  for (size_t k = 0; k < gn_bus.size(); k++) gn_of[gn_bus[k]] = (int)k;
+  ubus[0] = h.ref;
+  for (int i = 0; i < nb; i++)
+    if (h.type[i] == PV) {
+      ubus[h.uv[i]] = i;
+      ubus[h.up[i]] = i;
+    }
+
+  // upload
+  DevNet& n = c->dn;
+  n.nb = nb;
+  n.nl = nl;
+  n.ng = h.ng;
+  n.ref = h.ref;
+  n.npv = h.npv;
+  n.npq = h.npq;
+  n.nx = nx;
+  n.nu = h.nu;
+  n.m = h.m;
+  n.ngn = (int)gn_bus.size();
+  n.nnz = nnz;
+  n.nlev_f = s.nlev_f;
+  n.nlev_b = s.nlev_b;
+  int* ip;
+  double* dptr;
+  TRY(dupload(c, &ip, h.f)); n.f = ip;
+  TRY(dupload(c, &ip, h.t)); n.t = ip;
+  TRY(dupload(c, &ip, h.gbus)); n.gbus = ip;
+  TRY(dupload(c, &dptr, h.Y)); n.Y = dptr;
+  TRY(dupload(c, &ip, h.type)); n.type = ip;
+  TRY(dupload(c, &ip, h.gen_at)); n.gen_at = ip;
+  TRY(dupload(c, &ip, h.pvpos)); n.pvpos = ip;
+  TRY(dupload(c, &ip, h.pqpos)); n.pqpos = ip;
+  TRY(dupload(c, &ip, h.xth)); n.xth = ip;
+  TRY(dupload(c, &ip, h.xv)); n.xv = ip;
+  TRY(dupload(c, &ip, h.uv)); n.uv = ip;
+  TRY(dupload(c, &ip, h.up)); n.up = ip;
+  TRY(dupload(c, &ip, pth)); n.pth = ip;
+  TRY(dupload(c, &ip, pvv)); n.pvv = ip;
+  TRY(dupload(c, &ip, h.adj_ptr)); n.adj_ptr = ip;
+  TRY(dupload(c, &ip, h.adj)); n.adj = ip;
+  TRY(dupload(c, &ip, gn_of)); n.gn_of = ip;
+  TRY(dupload(c, &ip, gn_bus)); n.gn_bus = ip;
+  TRY(dupload(c, &dptr, h.c2)); n.c2 = dptr;
+  TRY(dupload(c, &dptr, h.c1)); n.c1 = dptr;
+  TRY(dupload(c, &c->c0, h.c0));
+  TRY(dupload(c, &ip, s.rp)); n.rp = ip;
+  TRY(dupload(c, &ip, s.ci)); n.ci = ip;
+  TRY(dupload(c, &ip, s.dp)); n.dp = ip;
+  TRY(dupload(c, &ip, s.perm)); n.perm = ip;
+  TRY(dupload(c, &ip, c->h_lev_ptr_f)); n.lev_ptr_f = ip;
+  TRY(dupload(c, &ip, lrows_f)); n.lev_rows_f = ip;
+  TRY(dupload(c, &ip, c->h_lev_ptr_b)); n.lev_ptr_b = ip;
+  TRY(dupload(c, &ip, lrows_b)); n.lev_rows_b = ip;
+  TRY(dupload(c, &ip, slot_self)); n.slot_self = ip;
+  TRY(dupload(c, &ip, slot_adj)); n.slot_adj = ip;
+  TRY(dupload(c, &c->tmap, tmap));
+  TRY(dupload(c, &c->lcol_row, lcol_row));
+  TRY(dupload(c, &c->lcol_pos, lcol_pos));
+  TRY(dupload(c, &c->task_col, task_col));
+  TRY(dupload(c, &c->task_k, task_k));
+  TRY(dupload(c, &c->ubus, ubus));
+  TRY(dupload(c, &c->pd_nom, h.pd));
+  TRY(dupload(c, &c->qd_nom, h.qd));
+  // workspaces
+  TRY(dalloc(c, &c->LU, nnz));
+  TRY(dalloc(c, &c->T, nnz));
+  TRY(dalloc(c, &c->invdiag, nx));
+  TRY(dalloc(c, &c->x, nx));
+  TRY(dalloc(c, &c->u, h.nu));
+  TRY(dalloc(c, &c->pd, nb));
+  TRY(dalloc(c, &c->qd, nb));
+  TRY(dalloc(c, &c->vbus, nb));
+  TRY(dalloc(c, &c->thbus, nb));
+  TRY(dalloc(c, &c->g, nx));
+  TRY(dalloc(c, &c->dvec, nx));
+  TRY(dalloc(c, &c->yvec, nx));
+  TRY(dalloc(c, &c->scal, 8));
+  TRY(dalloc(c, &c->flags, 4));
+  TRY(dalloc(c, &c->flows, 4 * (size_t)nl));
+  TRY(dalloc(c, &c->Pbus, nb));
+  TRY(dalloc(c, &c->Qbus, nb));
+  TRY(dalloc(c, &c->cvec, h.m));
+  TRY(dalloc(c, &c->phid, h.m));
+  TRY(dalloc(c, &c->omega, h.m));
+  TRY(dalloc(c, &c->dFx, nx));
+  TRY(dalloc(c, &c->dFu, h.nu));
+  TRY(dalloc(c, &c->lam, nx));
+  TRY(dalloc(c, &c->btab, 26 * (size_t)nl));
+  TRY(dalloc(c, &c->busw, 4 * (size_t)nb));
+  CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
+  CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
+  for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
+  return OPF_OK;
+}
+
+static void free_impl(opf_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  for (int k = 0; k < 4; k++)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  delete c;
+}
+
+static void export_sym(const Symbolic& s, int* bus_order, int* perm, int* rowptr, int* colidx,
+                       int* lev_f, int* lev_b) {
+  if (bus_order) std::memcpy(bus_order, s.bus_order.data(), s.bus_order.size() * sizeof(int));
+  if (perm) std::memcpy(perm, s.perm.data(), s.perm.size() * sizeof(int));
+  if (rowptr) std::memcpy(rowptr, s.rp.data(), s.rp.size() * sizeof(int));
+  if (colidx) std::memcpy(colidx, s.ci.data(), s.ci.size() * sizeof(int));
+  if (lev_f) std::memcpy(lev_f, s.lev_f.data(), s.lev_f.size() * sizeof(int));
+  if (lev_b) std::memcpy(lev_b, s.lev_b.data(), s.lev_b.size() * sizeof(int));
+}
+
+extern "C" {
+
+opf_status opf_load_network(const opf_network_desc* desc, void* stream, opf_ctx** out) {
+  if (!out) FAIL(OPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  opf_ctx* c = new (std::nothrow) opf_ctx();
+  if (!c) FAIL(OPF_ENOMEM, "host allocation failed");
+  for (int k = 0; k < 4; k++) c->ev[k] = nullptr;
+  c->stream = static_cast<cudaStream_t>(stream);
+  opf_status st = load_impl(c, desc);
+  if (st != OPF_OK) {
+    std::string keep = g_err;
+    free_impl(c);
+    g_err = keep;
+    return st;
+  }
+  *out = c;
+  return OPF_OK;
+}
+
+void opf_free(opf_ctx* ctx) { free_impl(ctx); }
+
+opf_status opf_set_stream(opf_ctx* c, void* stream) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
+  c->stream = static_cast<cudaStream_t>(stream);
+  return OPF_OK;
+}
+
+opf_status opf_dims(const opf_ctx* c, int* nx, int* nu, int* m, int* npv, int* npq) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
+  if (nx) *nx = c->h.nx;
+  if (nu) *nu = c->h.nu;
+  if (m) *m = c->h.m;
+  if (npv) *npv = c->h.npv;
+  if (npq) *npq = c->h.npq;
+  return OPF_OK;
+}
+
+opf_status opf_symbolic_sizes(const opf_ctx* c, int* nnz, int* nsb, int* nlf, int* nlb) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
+  if (nnz) *nnz = (int)c->s.ci.size();
+  if (nsb) *nsb = (int)c->s.bus_order.size();
+  if (nlf) *nlf = c->s.nlev_f;
+  if (nlb) *nlb = c->s.nlev_b;
+  return OPF_OK;
+}
+
+opf_status opf_symbolic_export(const opf_ctx* c, int* bus_order, int* perm, int* rowptr,
+                               int* colidx, int* lev_f, int* lev_b) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
+  export_sym(c->s, bus_order, perm, rowptr, colidx, lev_f, lev_b);
+  return OPF_OK;
+}
+
+}  // extern "C"
+
+struct opf_symbolic {
+  HostNet h;
+  Symbolic s;
+};
+
+extern "C" {
+
+opf_status opf_symbolic_analyze(const opf_network_desc* desc, opf_symbolic** out) {
+  if (!out) FAIL(OPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  opf_symbolic* sy = new (std::nothrow) opf_symbolic();
+  if (!sy) FAIL(OPF_ENOMEM, "host allocation failed");
+  std::string why = build_hostnet(desc, sy->h);
+  if (!why.empty()) {
+    delete sy;
+    FAIL(OPF_EINVAL, why);
+  }
+  build_symbolic(sy->h, sy->s);
+  *out = sy;
+  return OPF_OK;
+}
+
+opf_status opf_symbolic_info(const opf_symbolic* sy, int* nx, int* nnz, int* nsb, int* nlf, int* nlb) {
+  if (!sy) FAIL(OPF_EINVAL, "symbolic handle is NULL");
+  if (nx) *nx = sy->h.nx;
+  if (nnz) *nnz = (int)sy->s.ci.size();
+  if (nsb) *nsb = (int)sy->s.bus_order.size();
+  if (nlf) *nlf = sy->s.nlev_f;
+  if (nlb) *nlb = sy->s.nlev_b;
+  return OPF_OK;
+}
+
+opf_status opf_symbolic_get(const opf_symbolic* sy, int* bus_order, int* perm, int* rowptr,
+                            int* colidx, int* lev_f, int* lev_b) {
+  if (!sy) FAIL(OPF_EINVAL, "symbolic handle is NULL");
+  export_sym(sy->s, bus_order, perm, rowptr, colidx, lev_f, lev_b);
+  return OPF_OK;
+}
+
+void opf_symbolic_free(opf_symbolic* sy) { delete sy; }
+
+opf_status opf_powerflow(opf_ctx* c, const double* u, const double* pd, const double* qd,
+                         double* x_inout, const opf_pf_opts* opts, opf_pf_info* info) {
+  if (!c || !u || !x_inout) FAIL(OPF_EINVAL, "ctx, u and x_inout are required");
+  const double tol = opts ? opts->tol : 1e-10;
+  const int max_it = opts ? opts->max_it : 20;
+  if (!(tol > 0.0) || max_it < 0) FAIL(OPF_EINVAL, "tol must be > 0 and max_it >= 0");
+  const int nx = c->h.nx, nb = c->h.nb;
+  cudaStream_t st = c->stream;
+  c->have_state = false;
+  CK(cudaMemcpyAsync(c->u, u, c->h.nu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(c->pd, pd ? pd : c->pd_nom, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(c->qd, qd ? qd : c->qd_nom, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(c->x, x_inout, nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  opf_status result = OPF_ENOCONV;
+  int it = 0;
+  double res2 = NAN, resinf = NAN;
+  for (it = 0;; it++) {
+    launch_unpack(c, c->x, c->u);
+    CK(cudaMemsetAsync(c->LU, 0, c->dn.nnz * sizeof(double), st));
+    CK(cudaMemsetAsync(c->scal, 0, 2 * sizeof(double), st));
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
+    launch_pf_eval(c);
+    launch_lu(c);
+    CK(cudaMemcpyAsync(c->h_scal, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    res2 = std::sqrt(c->h_scal[0]);
+    resinf = c->h_scal[1];
+    if (!std::isfinite(res2)) {
+      result = OPF_ENOCONV;
+      g_err = "non-finite power-flow residual";
+      break;
+    }
+    if (res2 < tol) {
+      result = c->h_flags[0] ? OPF_ESINGULAR : OPF_OK;
+      if (result) g_err = "singular Jacobian at the solution";
+      break;
+    }
+    if (c->h_flags[0]) {
+      result = OPF_ESINGULAR;
+      g_err = "zero or non-finite pivot in the LU refactorisation";
+      break;
+    }
+    if (it >= max_it) {
+      result = OPF_ENOCONV;
+      g_err = "Newton-Raphson reached max_it";
+      break;
+    }
+    launch_solve1(c, c->g, c->dvec, false, 1.0);
+    launch_axpy(c, c->x, c->dvec, -1.0, nx);
+  }
+  CK(cudaMemcpyAsync(x_inout, c->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  if (info) {
+    info->iterations = it;
+    info->res2 = res2;
+    info->resinf = resinf;
+  }
+  c->have_state = (result == OPF_OK);
+  return result;
+}
+
+static opf_status check_al(const opf_ctx* c, const opf_al_params* p) {
+  (void)c;
+  if (!p || !p->sigma_c || !p->y || !p->s) FAIL(OPF_EINVAL, "AL parameters need sigma_c, y and s");
+  if (!(p->rho >= 0.0) || !std::isfinite(p->sigma_f)) FAIL(OPF_EINVAL, "rho must be >= 0, sigma_f finite");
+  return OPF_OK;
+}
+
+opf_status opf_reduced_gradient(opf_ctx* c, const opf_al_params* p, double* F, double* grad_u,
+                                double* grad_s, double* cout, double* lambda, double* grad_pd,
+                                double* grad_qd) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
+  if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  TRY(check_al(c, p));
+  cudaStream_t st = c->stream;
+  launch_first_order(c, p, grad_s);
+  if (F) CK(cudaMemcpyAsync(F, c->scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (grad_u) launch_grad_u(c, grad_u);
+  if (cout) CK(cudaMemcpyAsync(cout, c->cvec, c->h.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (lambda) CK(cudaMemcpyAsync(lambda, c->lam, c->h.nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (grad_pd || grad_qd) launch_grad_load(c, p->sigma_f, grad_pd, grad_qd);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  return OPF_OK;
+}
+
+static opf_status ensure_scratch(opf_ctx* c, size_t doubles) {
+  if (c->scratch_bytes >= doubles * sizeof(double)) return OPF_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  if (cudaMalloc(&c->scratch, doubles * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->scratch = nullptr;
+    FAIL(OPF_ENOMEM, "cannot allocate the Hessian workspace");
+  }
+  c->scratch_bytes = doubles * sizeof(double);
+  return OPF_OK;
+}
+
+opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hess_opts* o,
+                               double* H, opf_hess_info* info) {
+  if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
+  if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  TRY(check_al(c, p));
+  int C = (o && o->block_k) ? o->block_k : 8;
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
+    FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
+  const bool plain = o && o->plain;
+  const int ntiles = (c->h.nu + C - 1) / C;
+  int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : 2 * c->sm_count);
+  grid = std::max(1, std::min(grid, ntiles));
+  TRY(ensure_scratch(c, hvp_stride(c, C) * (size_t)grid));
+  cudaStream_t st = c->stream;
+  CK(cudaEventRecord(c->ev[0], st));
+  launch_first_order(c, p, nullptr);
+  launch_hess_prep(c, p->sigma_f);
+  CK(cudaEventRecord(c->ev[1], st));
+  int launches = 0;
+  if (plain) {
+    for (int t = 0; t < ntiles; t++, launches++) launch_hvp(c, C, H, 1, t, 1, t + 1);
+  } else {
+    launch_hvp(c, C, H, grid, 0, 1, ntiles);
+    launches = 1;
+  }
+  CK(cudaEventRecord(c->ev[2], st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  if (info) {
+    info->block_k = C;
+    info->grid = grid;
+    info->tiles = ntiles;
+    info->launches = launches;
+    cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
+    cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
+  }
+  return OPF_OK;
+}
+
+const char* opf_status_str(int s) {
+  switch (s) {
+    case OPF_OK: return "ok";
+    case OPF_EINVAL: return "invalid argument";
+    case OPF_ENOMEM: return "out of memory";
+    case OPF_ECUDA: return "CUDA error";
+    case OPF_ENOCONV: return "Newton-Raphson did not converge";
+    case OPF_ESINGULAR: return "singular Jacobian";
+    case OPF_ENOTPD: return "matrix not positive definite";
+    case OPF_ESTATE: return "no converged power-flow state";
+    case OPF_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* opf_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations of libopf: the context, the host symbolic analysis and
+// the kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/opf.h"
+
+namespace opf {
+
+enum BusType { REF = 0, PV = 1, PQ = 2 };
+
+// Host-side network with index maps (eq. statecontrol).
+struct HostNet {
+  int nb = 0, nl = 0, ng = 0, ref = 0, npv = 0, npq = 0, nx = 0, nu = 0, m = 0;
+  std::vector<int> f, t, gbus;
+  std::vector<double> Y;  // 8 * nl: Gff, Bff, Gft, Bft, Gtf, Btf, Gtt, Btt (blocks of nl)
+  std::vector<double> pd, qd, c2, c1, c0;
+  std::vector<int> type, gen_at, pvpos, pqpos, xth, xv, uv, up;
+  std::vector<int> adj_ptr, adj;  // bus -> incident entries, entry = 2 * branch + side
+};
+
+// Symbolic analysis of G_x (pivot order, filled pattern, level sets).
+struct Symbolic {
+  std::vector<int> bus_order, perm, iperm;
+  std::vector<int> rp, ci, dp;     // row-wise filled pattern, pivot order
+  std::vector<int> lev_f, lev_b;   // level of each row (forward / backward)
+  int nlev_f = 0, nlev_b = 0;
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_hostnet(const opf_network_desc* d, HostNet& h);
+void build_symbolic(const HostNet& h, Symbolic& s);
+
+// Device views passed to kernels (plain pointers).
+struct DevNet {
+  int nb, nl, ng, ref, npv, npq, nx, nu, m, ngn, nnz;
+  const int *f, *t, *gbus;
+  const double* Y;
+  const int *type, *gen_at, *pvpos, *pqpos, *xth, *xv, *uv, *up;
+  const int *pth, *pvv;            // pivot-order index of theta / v of each bus (-1)
+  const int *adj_ptr, *adj;
+  const int* gn_of;                // per bus: index among ref + PV buses (-1)
+  const int* gn_bus;               // [ngn]
+  const double *c2, *c1;
+  // LU pattern
+  const int *rp, *ci, *dp, *perm;
+  const int *lev_ptr_f, *lev_rows_f, *lev_ptr_b, *lev_rows_b;
+  int nlev_f, nlev_b;
+  const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
+  const int* slot_adj;             // [4 * 2 nl]
+};
+
+// kernel launchers (opf_kernels.cu)
+void launch_unpack(opf_ctx* c, const double* x, const double* u);
+void launch_pf_eval(opf_ctx* c);
+void launch_lu(opf_ctx* c);
+void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale);
+void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n);
+void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
+void launch_grad_u(opf_ctx* c, double* gu);
+void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
+void launch_hess_prep(opf_ctx* c, double sigma_f);
+size_t hvp_stride(const opf_ctx* c, int C);
+bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles);
+
+}  // namespace opf
+
+struct opf_ctx {
+  opf::HostNet h;
+  opf::Symbolic s;
+  opf::DevNet dn;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 0;
+  std::vector<void*> allocs;
+
+  // device: LU values and schedules
+  double *LU = nullptr, *T = nullptr, *invdiag = nullptr;
+  int* tmap = nullptr;
+  int *lcol_pos = nullptr;        // per lower entry (CSC order): position of L_rj in row r
+  int *lcol_row = nullptr;
+  int *task_col = nullptr, *task_k = nullptr;
+  std::vector<int> h_task_ptr;    // per forward level
+  std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
+
+  // device: state of the last converged power flow
+  double *x = nullptr, *u = nullptr, *pd = nullptr, *qd = nullptr;
+  double *pd_nom = nullptr, *qd_nom = nullptr, *c0 = nullptr;
+  int* ubus = nullptr;            // bus of each control (v_ref, v_pv, p_pv)
+  double *vbus = nullptr, *thbus = nullptr;
+  double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
+  double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...
+  int* flags = nullptr;           // [4] error flags set by kernels
+  double* h_scal = nullptr;       // pinned host mirror of scal
+  int* h_flags = nullptr;         // pinned host mirror of flags
+  bool have_state = false;
+
+  // gradient / Hessian workspaces
+  double *flows = nullptr;        // [4 nl]: Pf, Qf, Pt, Qt
+  double *Pbus = nullptr, *Qbus = nullptr;
+  double *cvec = nullptr, *phid = nullptr, *omega = nullptr;
+  double *dFx = nullptr, *dFu = nullptr, *lam = nullptr;
+  double *btab = nullptr;         // [26 nl] per-branch Hessian table
+  double *busw = nullptr;         // [4 nb]: kQ, kP, diag v, diag p
+  double* scratch = nullptr;      // HVP per-CTA slabs
+  size_t scratch_bytes = 0;
+  cudaEvent_t ev[4];
+};

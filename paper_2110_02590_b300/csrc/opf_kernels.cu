@@ -1,0 +1,763 @@
+// Device kernels of libopf (sm_103a, FP64).
+//
+// Layout: the factors of G_x live in one row-wise array on the filled pattern
+// (pivot order): LU holds L (strictly lower, unit diagonal implied) and U
+// (diagonal and upper); T holds the transposed values (T at (i,j) = LU at
+// (j,i)) so that the forward and backward sweeps of both G_x and G_x^T read
+// rows contiguously.  invdiag holds 1/U_ii so no sweep divides.
+//
+// The Hessian kernel gives each CTA a tile of Hessian columns and runs the
+// whole adjoint-adjoint pipeline of Prop. 2 on it with no inter-CTA
+// synchronisation: the columns of the Hessian are independent given the
+// factors, so CTAs never wait on one another.  Within a CTA a warp holds
+// 32/C rows x C columns; the C lanes of a row read the same factor entry
+// (broadcast) and C consecutive right-hand-side values (one coalesced load).
+#include <algorithm>
+#include <cstdint>
+
+#include "opf_internal.h"
+
+namespace opf {
+
+// ------------------------------------------------------------ branch flows
+
+struct Flow {
+  double P, Q, A, Bq, vs, vo;
+  double dP[4], dQ[4];  // side-local order (v_s, v_o, theta_s, theta_o)
+};
+
+__device__ __forceinline__ void side_coeffs(const DevNet& n, int l, int s, double& Gss, double& Bss,
+                                            double& Gso, double& Bso) {
+  const int nl = n.nl;
+  if (s == 0) {
+    Gss = n.Y[l];
+    Bss = n.Y[nl + l];
+    Gso = n.Y[2 * nl + l];
+    Bso = n.Y[3 * nl + l];
+  } else {
+    Gss = n.Y[6 * nl + l];
+    Bss = n.Y[7 * nl + l];
+    Gso = n.Y[4 * nl + l];
+    Bso = n.Y[5 * nl + l];
+  }
+}
+
+// Flow out of one end of a branch (pi model, polar form) and its gradient.
+__device__ __forceinline__ void side_flow(const DevNet& n, int l, int s, double vs, double vo,
+                                          double ang, Flow& o) {
+  double Gss, Bss, Gso, Bso;
+  side_coeffs(n, l, s, Gss, Bss, Gso, Bso);
+  double sn, cs;
+  sincos(ang, &sn, &cs);
+  const double A = Gso * cs + Bso * sn;   // d A / d ang = -Bq
+  const double Bq = Gso * sn - Bso * cs;  // d Bq / d ang = A
+  const double vv = vs * vo;
+  o.A = A;
+  o.Bq = Bq;
+  o.vs = vs;
+  o.vo = vo;
+  o.P = vs * vs * Gss + vv * A;
+  o.Q = -vs * vs * Bss + vv * Bq;
+  o.dP[0] = 2.0 * vs * Gss + vo * A;
+  o.dP[1] = vs * A;
+  o.dP[2] = -vv * Bq;
+  o.dP[3] = vv * Bq;
+  o.dQ[0] = -2.0 * vs * Bss + vo * Bq;
+  o.dQ[1] = vs * Bq;
+  o.dQ[2] = vv * A;
+  o.dQ[3] = -vv * A;
+}
+
+__device__ __forceinline__ int other_end(const DevNet& n, int e) {
+  const int l = e >> 1;
+  return (e & 1) ? n.f[l] : n.t[l];
+}
+
+__global__ void unpack_kernel(DevNet n, const double* x, const double* u, double* vb, double* tb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  vb[i] = (n.type[i] == PQ) ? x[n.xv[i]] : u[n.uv[i]];
+  tb[i] = (n.type[i] == REF) ? 0.0 : x[n.xth[i]];
+}
+
+// g and the values of G_x in the fixed pattern; one thread owns the rows of its bus.
+__global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, const double* u,
+                               const double* pd, const double* qd, double* g, double* LU,
+                               double* scal) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double g2 = 0.0, gi = 0.0;
+  if (i < n.nb && n.type[i] != REF) {
+    const bool pq = n.type[i] == PQ;
+    double P = 0, Q = 0, dPv = 0, dPt = 0, dQv = 0, dQt = 0;
+    const double vi = vb[i], ti = tb[i];
+    for (int k = n.adj_ptr[i]; k < n.adj_ptr[i + 1]; k++) {
+      const int e = n.adj[k], l = e >> 1, s = e & 1, o = other_end(n, e);
+      Flow fl;
+      side_flow(n, l, s, vi, vb[o], ti - tb[o], fl);
+      P += fl.P;
+      Q += fl.Q;
+      dPv += fl.dP[0];
+      dPt += fl.dP[2];
+      dQv += fl.dQ[0];
+      dQt += fl.dQ[2];
+      const int* sl = n.slot_adj + 4 * (size_t)e;
+      if (sl[0] >= 0) LU[sl[0]] += fl.dP[3];
+      if (sl[1] >= 0) LU[sl[1]] += fl.dP[1];
+      if (sl[2] >= 0) LU[sl[2]] += fl.dQ[3];
+      if (sl[3] >= 0) LU[sl[3]] += fl.dQ[1];
+    }
+    const int* ss = n.slot_self + 4 * (size_t)i;
+    LU[ss[0]] += dPt;
+    if (ss[1] >= 0) LU[ss[1]] += dPv;
+    if (ss[2] >= 0) LU[ss[2]] += dQt;
+    if (ss[3] >= 0) LU[ss[3]] += dQv;
+    const double pg = (n.type[i] == PV) ? u[n.up[i]] : 0.0;
+    const double gp = P - pg + pd[i];
+    g[n.xth[i]] = gp;
+    g2 = gp * gp;
+    gi = fabs(gp);
+    if (pq) {
+      const double gq = Q + qd[i];
+      g[n.xv[i]] = gq;
+      g2 += gq * gq;
+      gi = fmax(gi, fabs(gq));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    g2 += __shfl_down_sync(0xffffffffu, g2, off);
+    gi = fmax(gi, __shfl_down_sync(0xffffffffu, gi, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&scal[0], g2);
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(&scal[1]), (unsigned long long)__double_as_longlong(gi));
+  }
+}
+
+// ------------------------------------------------------------ numeric LU
+
+// Right-looking elimination of the columns of one level: each warp takes one
+// (column j, row r) pair, forms L_rj = A_rj / U_jj and subtracts L_rj U_j,c
+// from A_rc for every c in row j of U (lanes over c).  Columns of one level
+// never update each other's rows or columns, so only the targets race, and
+// they are combined by atomic adds.
+__global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const int* __restrict__ dp, const int* __restrict__ task_col,
+                                const int* __restrict__ task_k, const int* __restrict__ lcol_row,
+                                const int* __restrict__ lcol_pos, int t0, int t1, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int t = t0 + warp; t < t1; t += nw) {
+    const int j = task_col[t], k = task_k[t];
+    const int r = lcol_row[k], prj = lcol_pos[k];
+    const double ujj = LU[dp[j]];
+    const double l = LU[prj] / ujj;
+    __syncwarp();
+    if (lane == 0) {
+      LU[prj] = l;
+      if (!(fabs(ujj) > 0.0) || !isfinite(l)) flags[0] = 1;
+    }
+    const int rb = rp[r], re = rp[r + 1];
+    for (int q = dp[j] + 1 + lane; q < rp[j + 1]; q += 32) {
+      const int c = ci[q];
+      const double v = -l * LU[q];
+      int lo = rb, hi = re - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ci[mid] < c) lo = mid + 1; else hi = mid;
+      }
+      atomicAdd(&LU[lo], v);
+    }
+  }
+}
+
+__global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, const int* tmap,
+                                 const int* dp, int nx, int nnz, int* flags) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int i = tid; i < nx; i += nt) {
+    const double d = LU[dp[i]];
+    if (!(fabs(d) > 0.0) || !isfinite(d)) flags[0] = 1;
+    invdiag[i] = 1.0 / d;
+  }
+  for (int p = tid; p < nnz; p += nt) T[p] = LU[tmap[p]];
+}
+
+// ------------------------------------------------------------ sweeps
+
+// One level-scheduled triangular sweep over a CTA-private right-hand-side slab
+// X[n_x][C].  FWD: rows ascending by level over the lower part of V; else the
+// upper part.  DIAG: multiply by 1/U_ii after the row.
+template <int C, bool FWD, bool DIAG>
+__device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
+                                      const double* __restrict__ invdiag, double* X) {
+  constexpr int RPW = 32 / C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = lane % C;
+  const int nslots = (blockDim.x >> 5) * RPW, myslot = warp * RPW + lane / C;
+  const int nlev = FWD ? n.nlev_f : n.nlev_b;
+  const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
+  const int* lrows = FWD ? n.lev_rows_f : n.lev_rows_b;
+  for (int lv = 0; lv < nlev; lv++) {
+    const int b = lptr[lv], e = lptr[lv + 1];
+    for (int k = b + myslot; k < e; k += nslots) {
+      const int i = lrows[k];
+      const int p0 = FWD ? n.rp[i] : n.dp[i] + 1;
+      const int p1 = FWD ? n.dp[i] : n.rp[i + 1];
+      double s0 = X[(size_t)i * C + col], s1 = 0.0;
+      int p = p0;
+      for (; p + 1 < p1; p += 2) {
+        s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
+        s1 -= V[p + 1] * X[(size_t)n.ci[p + 1] * C + col];
+      }
+      if (p < p1) s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
+      double s = s0 + s1;
+      if (DIAG) s *= invdiag[i];
+      X[(size_t)i * C + col] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Single right-hand side: out = G_x^{-1} (scale b) or G_x^{-T} (scale b).  One CTA.
+__global__ void __launch_bounds__(1024) solve1_kernel(DevNet n, const double* LU, const double* T,
+                                                       const double* invdiag, const double* b,
+                                                       double* out, double* y, int transposed,
+                                                       double scale) {
+  for (int i = threadIdx.x; i < n.nx; i += blockDim.x) y[i] = scale * b[n.perm[i]];
+  __syncthreads();
+  if (!transposed) {
+    sweep<1, true, false>(n, LU, invdiag, y);
+    sweep<1, false, true>(n, LU, invdiag, y);
+  } else {
+    sweep<1, true, true>(n, T, invdiag, y);
+    sweep<1, false, false>(n, T, invdiag, y);
+  }
+  for (int i = threadIdx.x; i < n.nx; i += blockDim.x) out[n.perm[i]] = y[i];
+}
+
+__global__ void axpy_kernel(double* x, const double* d, double a, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += a * d[i];
+}
+
+// ------------------------------------------------------------ gradient
+
+__global__ void branch_flow_kernel(DevNet n, const double* vb, const double* tb, double* flows,
+                                   double* c) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n.nl) return;
+  const int a = n.f[l], b = n.t[l];
+  Flow ff, ft;
+  side_flow(n, l, 0, vb[a], vb[b], tb[a] - tb[b], ff);
+  side_flow(n, l, 1, vb[b], vb[a], tb[b] - tb[a], ft);
+  flows[l] = ff.P;
+  flows[n.nl + l] = ff.Q;
+  flows[2 * n.nl + l] = ft.P;
+  flows[3 * n.nl + l] = ft.Q;
+  c[l] = ff.P * ff.P + ff.Q * ff.Q;
+  c[n.nl + l] = ft.P * ft.P + ft.Q * ft.Q;
+}
+
+__global__ void bus_inj_kernel(DevNet n, const double* vb, const double* flows, const double* pd,
+                               const double* qd, double* Pb, double* Qb, double* c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  double P = 0, Q = 0;
+  for (int k = n.adj_ptr[i]; k < n.adj_ptr[i + 1]; k++) {
+    const int e = n.adj[k], l = e >> 1, s = e & 1;
+    P += flows[(2 * s) * n.nl + l];
+    Q += flows[(2 * s + 1) * n.nl + l];
+  }
+  Pb[i] = P;
+  Qb[i] = Q;
+  const int o = 2 * n.nl;
+  if (n.type[i] == PQ) c[o + n.pqpos[i]] = vb[i];
+  else if (n.type[i] == REF) {
+    c[o + n.npq] = P + pd[i];
+    c[o + n.npq + 1] = Q + qd[i];
+  } else c[o + n.npq + 2 + n.pvpos[i]] = Q + qd[i];
+}
+
+// phi'_i, grad_s, omega and the value of F (reduced into scal[2]).
+__global__ void al_weights_kernel(DevNet n, const double* c, const double* sig, const double* y,
+                                  const double* s, const double* om_in, double rho, double sigma_f,
+                                  const double* Pb, const double* u, const double* pd,
+                                  const double* c0, double* phid, double* gs, double* om,
+                                  double* scal) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < n.m) {
+    const double r = c[i] - s[i], sg = sig[i];
+    phid[i] = y[i] * sg + rho * sg * sg * r;
+    if (gs) gs[i] = -phid[i];
+    om[i] = om_in ? om_in[i] : rho * sg * sg;
+    part = y[i] * sg * r + 0.5 * rho * sg * sg * r * r;
+  }
+  if (i < n.ng) {
+    // cost of generator i (the slack takes p_ref = P_ref + pd_ref)
+    const int b = n.gbus[i];
+    const double p = (n.type[b] == REF) ? Pb[b] + pd[b] : u[n.up[b]];
+    part += sigma_f * (n.c2[i] * p * p + n.c1[i] * p + c0[i]);
+  }
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&scal[2], part);
+}
+
+// First-order weights of F on the injections of bus b.
+__device__ __forceinline__ void f_weights(const DevNet& n, int b, const double* phid,
+                                          double sigma_f, double pref, double& wP, double& wQ) {
+  const int orr = 2 * n.nl + n.npq;
+  if (n.type[b] == REF) {
+    const int g = n.gen_at[b];
+    wP = phid[orr] + sigma_f * (2.0 * n.c2[g] * pref + n.c1[g]);
+    wQ = phid[orr + 1];
+  } else if (n.type[b] == PV) {
+    wP = 0.0;
+    wQ = phid[orr + 2 + n.pvpos[b]];
+  } else {
+    wP = 0.0;
+    wQ = 0.0;
+  }
+}
+
+// Partial derivatives of F w.r.t. (v_i, theta_i), gathered over the incident branches.
+__global__ void dF_bus_kernel(DevNet n, const double* vb, const double* tb, const double* u,
+                              const double* phid, const double* Pb, const double* pd,
+                              double sigma_f, double* dFx, double* dFu) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  const double pref = Pb[n.ref] + pd[n.ref];
+  double wPi, wQi;
+  f_weights(n, i, phid, sigma_f, pref, wPi, wQi);
+  double dv = 0.0, dt = 0.0;
+  for (int k = n.adj_ptr[i]; k < n.adj_ptr[i + 1]; k++) {
+    const int e = n.adj[k], l = e >> 1, s = e & 1, o = other_end(n, e);
+    Flow fi, fo;
+    side_flow(n, l, s, vb[i], vb[o], tb[i] - tb[o], fi);
+    side_flow(n, l, 1 - s, vb[o], vb[i], tb[o] - tb[i], fo);
+    const double phi_i = phid[s * n.nl + l], phi_o = phid[(1 - s) * n.nl + l];
+    double wPo, wQo;
+    f_weights(n, o, phid, sigma_f, pref, wPo, wQo);
+    const double ai = 2.0 * phi_i * fi.P + wPi, bi = 2.0 * phi_i * fi.Q + wQi;
+    const double ao = 2.0 * phi_o * fo.P + wPo, bo = 2.0 * phi_o * fo.Q + wQo;
+    dv += ai * fi.dP[0] + bi * fi.dQ[0] + ao * fo.dP[1] + bo * fo.dQ[1];
+    dt += ai * fi.dP[2] + bi * fi.dQ[2] + ao * fo.dP[3] + bo * fo.dQ[3];
+  }
+  if (n.type[i] == PQ) dv += phid[2 * n.nl + n.pqpos[i]];
+  if (n.type[i] != REF) dFx[n.xth[i]] = dt;
+  if (n.type[i] == PQ) dFx[n.xv[i]] = dv;
+  else dFu[n.uv[i]] = dv;
+  if (n.type[i] == PV) {
+    const int g = n.gen_at[i];
+    const double p = u[n.up[i]];
+    dFu[n.up[i]] = sigma_f * (2.0 * n.c2[g] * p + n.c1[g]);
+  }
+}
+
+// grad_u = d_u F + G_u^T lambda, one thread per control bus (slack and PV).
+__global__ void grad_u_kernel(DevNet n, const double* vb, const double* tb, const double* lam,
+                              const double* dFu, double* gu) {
+  int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= n.ngn) return;
+  const int k = n.gn_bus[gidx];
+  double gv = dFu[n.uv[k]], selfP = 0.0;
+  for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+    const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
+    Flow fo;
+    side_flow(n, l, 1 - s, vb[o], vb[k], tb[o] - tb[k], fo);
+    if (n.type[o] != REF) gv += lam[n.xth[o]] * fo.dP[1];
+    if (n.type[o] == PQ) gv += lam[n.xv[o]] * fo.dQ[1];
+    if (n.type[k] == PV) {
+      Flow fk;
+      side_flow(n, l, s, vb[k], vb[o], tb[k] - tb[o], fk);
+      selfP += fk.dP[0];
+    }
+  }
+  if (n.type[k] == PV) {
+    gv += lam[n.xth[k]] * selfP;
+    gu[n.up[k]] = dFu[n.up[k]] - lam[n.xth[k]];
+  }
+  gu[n.uv[k]] = gv;
+}
+
+__global__ void grad_load_kernel(DevNet n, const double* lam, const double* phid, const double* Pb,
+                                 const double* pd, double sigma_f, double* gpd, double* gqd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  const int orr = 2 * n.nl + n.npq;
+  if (n.type[i] == REF) {
+    const int g = n.gen_at[i];
+    const double pref = Pb[i] + pd[i];
+    if (gpd) gpd[i] = sigma_f * (2.0 * n.c2[g] * pref + n.c1[g]) + phid[orr];
+    if (gqd) gqd[i] = phid[orr + 1];
+  } else {
+    if (gpd) gpd[i] = lam[n.xth[i]];
+    if (gqd) gqd[i] = (n.type[i] == PV) ? phid[orr + 2 + n.pvpos[i]] : lam[n.xv[i]];
+  }
+}
+
+// ------------------------------------------------------------ Hessian tables
+
+// Packed index of the symmetric 4x4 branch matrix, branch-local order (v_f, v_t, theta_f, theta_t).
+__host__ __device__ __forceinline__ int pk(int a, int b) {
+  if (a > b) {
+    int t = a;
+    a = b;
+    b = t;
+  }
+  return a * 4 - (a * (a - 1)) / 2 + (b - a);
+}
+// Table rows: 0..9 packed M; 10+4s+k = dP of side s; 18+4s+k = dQ of side s (k branch-local).
+#define TAB_DP(s, k) (10 + 4 * (s) + (k))
+#define TAB_DQ(s, k) (18 + 4 * (s) + (k))
+
+// Per branch: the 4x4 second derivative of l = F + lambda^T g restricted to the
+// branch (injection weights, line-flow penalty curvature and omega-weighted
+// Gauss-Newton term of the flows), and both ends' flow gradients.
+__global__ void hess_prep_kernel(DevNet n, const double* vb, const double* tb, const double* lam,
+                                 const double* phid, const double* om, const double* Pb,
+                                 const double* pd, double sigma_f, double* tab) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n.nl) return;
+  const int nl = n.nl, orr = 2 * nl + n.npq;
+  const double pref = Pb[n.ref] + pd[n.ref];
+  double M[10];
+#pragma unroll
+  for (int k = 0; k < 10; k++) M[k] = 0.0;
+  for (int s = 0; s < 2; s++) {
+    const int b = s ? n.t[l] : n.f[l], o = s ? n.f[l] : n.t[l];
+    Flow F;
+    side_flow(n, l, s, vb[b], vb[o], tb[b] - tb[o], F);
+    double wP, wQ;
+    if (n.type[b] == REF) {
+      const int g = n.gen_at[b];
+      wP = phid[orr] + sigma_f * (2.0 * n.c2[g] * pref + n.c1[g]);
+      wQ = phid[orr + 1];
+    } else if (n.type[b] == PV) {
+      wP = lam[n.xth[b]];
+      wQ = phid[orr + 2 + n.pvpos[b]];
+    } else {
+      wP = lam[n.xth[b]];
+      wQ = lam[n.xv[b]];
+    }
+    const double ph = phid[s * nl + l], w2 = om[s * nl + l];
+    const double aP = wP + 2.0 * ph * F.P, aQ = wQ + 2.0 * ph * F.Q;
+    const double A = F.A, Bq = F.Bq, vs = F.vs, vo = F.vo, vv = vs * vo;
+    double Gss, Bss, Gso, Bso;
+    side_coeffs(n, l, s, Gss, Bss, Gso, Bso);
+    const double hP[4][4] = {{2.0 * Gss, A, -vo * Bq, vo * Bq},
+                             {A, 0.0, -vs * Bq, vs * Bq},
+                             {-vo * Bq, -vs * Bq, -vv * A, vv * A},
+                             {vo * Bq, vs * Bq, vv * A, -vv * A}};
+    const double hQ[4][4] = {{-2.0 * Bss, Bq, vo * A, -vo * A},
+                             {Bq, 0.0, vs * A, -vs * A},
+                             {vo * A, vs * A, -vv * Bq, vv * Bq},
+                             {-vo * A, -vs * A, vv * Bq, -vv * Bq}};
+    double gh[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) gh[k] = 2.0 * (F.P * F.dP[k] + F.Q * F.dQ[k]);
+    // side-local (v_s, v_o, th_s, th_o) -> branch-local (v_f, v_t, th_f, th_t)
+    const int map[4] = {s, 1 - s, 2 + s, 3 - s};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = a; c < 4; c++) {
+        const double val = aP * hP[a][c] + aQ * hQ[a][c] +
+                           2.0 * ph * (F.dP[a] * F.dP[c] + F.dQ[a] * F.dQ[c]) + w2 * gh[a] * gh[c];
+        M[pk(map[a], map[c])] += val;
+      }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      tab[(size_t)TAB_DP(s, map[k]) * nl + l] = F.dP[k];
+      tab[(size_t)TAB_DQ(s, map[k]) * nl + l] = F.dQ[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 10; k++) tab[(size_t)k * nl + l] = M[k];
+}
+
+// Bus weights: [0] kQ (omega of q_ref / q_pv), [1] kP (omega of p_ref plus the
+// slack cost curvature 2 sigma_f c2), [2] omega of v_pq, [3] 2 sigma_f c2 of a PV unit.
+__global__ void bus_weight_kernel(DevNet n, const double* om, double sigma_f, double* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  const int orr = 2 * n.nl + n.npq, nb = n.nb;
+  double kQ = 0, kP = 0, dv = 0, dpp = 0;
+  if (n.type[i] == REF) {
+    kQ = om[orr + 1];
+    kP = om[orr] + 2.0 * sigma_f * n.c2[n.gen_at[i]];
+  } else if (n.type[i] == PV) {
+    kQ = om[orr + 2 + n.pvpos[i]];
+    dpp = 2.0 * sigma_f * n.c2[n.gen_at[i]];
+  } else {
+    dv = om[2 * n.nl + n.pqpos[i]];
+  }
+  w[i] = kQ;
+  w[nb + i] = kP;
+  w[2 * nb + i] = dv;
+  w[3 * nb + i] = dpp;
+}
+
+// ------------------------------------------------------------ HVP tiles
+
+struct HvpArgs {
+  DevNet n;
+  const double *LU, *T, *invdiag, *tab, *busw;
+  const int* ubus;  // bus of each control
+  double* H;
+  double* scratch;
+  size_t stride;    // doubles of scratch per CTA
+  int ntiles, first_tile, tile_step;
+};
+
+template <int C>
+__device__ __forceinline__ void direction(const DevNet& n, const double* Z, int b, int c, int j,
+                                          double& vd, double& td) {
+  vd = (n.type[b] == PQ) ? Z[(size_t)n.pvv[b] * C + c] : ((n.uv[b] == j) ? 1.0 : 0.0);
+  td = (n.type[b] == REF) ? 0.0 : Z[(size_t)n.pth[b] * C + c];
+}
+
+// One CTA = one tile of C Hessian columns at a time: B = -G_u W, Z = G_x^{-1} B,
+// second-order terms, Psi = G_x^{-T} R, H[:, tile] = T + G_u^T Psi (Prop. 2).
+template <int C>
+__global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
+  const DevNet& n = a.n;
+  const int nl = n.nl, nb = n.nb, nu = n.nu;
+  double* Z = a.scratch + a.stride * blockIdx.x;
+  double* R = Z + (size_t)n.nx * C;
+  double* QD = R + (size_t)n.nx * C;
+  double* PD = QD + (size_t)n.ngn * C;
+  const double* tab = a.tab;
+  for (int tile = a.first_tile + blockIdx.x * a.tile_step; tile < a.ntiles;
+       tile += gridDim.x * a.tile_step) {
+    const int j0 = tile * C;
+    // (0) right-hand side B = -G_u W, W = unit directions j0 .. j0 + C - 1
+    for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      const int j = j0 + c;
+      if (j >= nu) continue;
+      const int k = a.ubus[j];
+      if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
+        Z[(size_t)n.pth[k] * C + c] = 1.0;
+        continue;
+      }
+      double selfP = 0.0;
+      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
+        if (n.type[o] != REF) Z[(size_t)n.pth[o] * C + c] -= tab[(size_t)TAB_DP(1 - s, s) * nl + l];
+        if (n.type[o] == PQ) Z[(size_t)n.pvv[o] * C + c] -= tab[(size_t)TAB_DQ(1 - s, s) * nl + l];
+        selfP += tab[(size_t)TAB_DP(s, s) * nl + l];
+      }
+      if (n.type[k] == PV) Z[(size_t)n.pth[k] * C + c] -= selfP;
+    }
+    __syncthreads();
+    // (1)-(2) first second-order adjoint: L then U sweeps
+    sweep<C, true, false>(n, a.LU, a.invdiag, Z);
+    sweep<C, false, true>(n, a.LU, a.invdiag, Z);
+    // (3) directional derivatives of Q (slack and PV) and P (slack) for the Gauss-Newton terms
+    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
+      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = j0 + c;
+      double qd = 0.0, pdr = 0.0;
+      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+        const int e = n.adj[q], l = e >> 1, s = e & 1;
+        double d[4];
+        direction<C>(n, Z, n.f[l], c, j, d[0], d[2]);
+        direction<C>(n, Z, n.t[l], c, j, d[1], d[3]);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          qd += tab[(size_t)TAB_DQ(s, t) * nl + l] * d[t];
+          pdr += tab[(size_t)TAB_DP(s, t) * nl + l] * d[t];
+        }
+      }
+      QD[(size_t)gi * C + c] = qd;
+      if (k == n.ref) PD[c] = pdr;
+    }
+    __syncthreads();
+    // (4) y = (grad^2 l) (z; w) per bus; R = -y_x, H[u rows] = y_u
+    for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
+      const int i = it / C, c = it % C, j = j0 + c;
+      double vi, ti;
+      direction<C>(n, Z, i, c, j, vi, ti);
+      double yv = 0.0, yt = 0.0, sq_v = 0.0, sq_t = 0.0, sp_v = 0.0, sp_t = 0.0;
+      for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
+        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
+        double vo, to;
+        direction<C>(n, Z, o, c, j, vo, to);
+        const double d[4] = {s ? vo : vi, s ? vi : vo, s ? to : ti, s ? ti : to};
+        const int rv = s, rt = 2 + s;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          yv += tab[(size_t)pk(rv, t) * nl + l] * d[t];
+          yt += tab[(size_t)pk(rt, t) * nl + l] * d[t];
+        }
+        const int go = n.gn_of[o];
+        if (go >= 0) {
+          const double w = a.busw[o] * QD[(size_t)go * C + c];
+          yv += w * tab[(size_t)TAB_DQ(1 - s, rv) * nl + l];
+          yt += w * tab[(size_t)TAB_DQ(1 - s, rt) * nl + l];
+          if (o == n.ref) {
+            const double w2 = a.busw[nb + o] * PD[c];
+            yv += w2 * tab[(size_t)TAB_DP(1 - s, rv) * nl + l];
+            yt += w2 * tab[(size_t)TAB_DP(1 - s, rt) * nl + l];
+          }
+        }
+        sq_v += tab[(size_t)TAB_DQ(s, rv) * nl + l];
+        sq_t += tab[(size_t)TAB_DQ(s, rt) * nl + l];
+        sp_v += tab[(size_t)TAB_DP(s, rv) * nl + l];
+        sp_t += tab[(size_t)TAB_DP(s, rt) * nl + l];
+      }
+      const int gi = n.gn_of[i];
+      if (gi >= 0) {
+        const double w = a.busw[i] * QD[(size_t)gi * C + c];
+        yv += w * sq_v;
+        yt += w * sq_t;
+        if (i == n.ref) {
+          const double w2 = a.busw[nb + i] * PD[c];
+          yv += w2 * sp_v;
+          yt += w2 * sp_t;
+        }
+      }
+      if (n.type[i] == PQ) yv += a.busw[2 * nb + i] * vi;
+      if (n.type[i] != REF) R[(size_t)n.pth[i] * C + c] = -yt;
+      if (n.type[i] == PQ) {
+        R[(size_t)n.pvv[i] * C + c] = -yv;
+      } else if (j < nu) {
+        double* Hc = a.H + (size_t)j * nu;
+        Hc[n.uv[i]] = yv;
+        if (n.type[i] == PV) Hc[n.up[i]] = (n.up[i] == j) ? a.busw[3 * nb + i] : 0.0;
+      }
+    }
+    __syncthreads();
+    // (5)-(6) second second-order adjoint: U^T then L^T sweeps
+    sweep<C, true, true>(n, a.T, a.invdiag, R);
+    sweep<C, false, false>(n, a.T, a.invdiag, R);
+    // (7) H[:, tile] += G_u^T Psi
+    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
+      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = j0 + c;
+      if (j >= nu) continue;
+      double gv = 0.0, selfP = 0.0;
+      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
+        if (n.type[o] != REF) gv += R[(size_t)n.pth[o] * C + c] * tab[(size_t)TAB_DP(1 - s, s) * nl + l];
+        if (n.type[o] == PQ) gv += R[(size_t)n.pvv[o] * C + c] * tab[(size_t)TAB_DQ(1 - s, s) * nl + l];
+        selfP += tab[(size_t)TAB_DP(s, s) * nl + l];
+      }
+      double* Hc = a.H + (size_t)j * nu;
+      if (n.type[k] == PV) {
+        const double psi = R[(size_t)n.pth[k] * C + c];
+        gv += psi * selfP;
+        Hc[n.up[k]] -= psi;
+      }
+      Hc[n.uv[k]] += gv;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_unpack(opf_ctx* c, const double* x, const double* u) {
+  unpack_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, x, u, c->vbus, c->thbus);
+}
+
+void launch_pf_eval(opf_ctx* c) {
+  pf_eval_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->u, c->pd,
+                                                               c->qd, c->g, c->LU, c->scal);
+}
+
+void launch_lu(opf_ctx* c) {
+  const int nlev = c->dn.nlev_f;
+  for (int lv = 0; lv < nlev; lv++) {
+    const int t0 = c->h_task_ptr[lv], t1 = c->h_task_ptr[lv + 1];
+    if (t1 == t0) continue;
+    const int warps = t1 - t0;
+    const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
+    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->dn.rp, c->dn.ci, c->dn.dp, c->task_col,
+                                                   c->task_k, c->lcol_row, c->lcol_pos, t0, t1, c->flags);
+  }
+  lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
+                                                           c->dn.nx, c->dn.nnz, c->flags);
+}
+
+void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
+  solve1_kernel<<<1, 1024, 0, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
+                                           transposed ? 1 : 0, scale);
+}
+
+void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n) {
+  axpy_kernel<<<nblk(n, 256), 256, 0, c->stream>>>(x, d, a, n);
+}
+
+void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
+  const DevNet& n = c->dn;
+  cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
+  launch_unpack(c, c->x, c->u);
+  branch_flow_kernel<<<nblk(n.nl, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->flows, c->cvec);
+  bus_inj_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->flows, c->pd, c->qd, c->Pbus,
+                                                         c->Qbus, c->cvec);
+  const int mm = std::max(n.m, n.ng);
+  al_weights_kernel<<<nblk(mm, 256), 256, 0, c->stream>>>(
+      n, c->cvec, p->sigma_c, p->y, p->s, p->omega, p->rho, p->sigma_f, c->Pbus, c->u, c->pd,
+      c->c0, c->phid, grad_s, c->omega, c->scal);
+  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, c->phid, c->Pbus,
+                                                        c->pd, p->sigma_f, c->dFx, c->dFu);
+  launch_solve1(c, c->dFx, c->lam, true, -1.0);
+}
+
+void launch_grad_u(opf_ctx* c, double* gu) {
+  grad_u_kernel<<<nblk(c->dn.ngn, 128), 128, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->lam, c->dFu, gu);
+}
+
+void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd) {
+  grad_load_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, c->lam, c->phid, c->Pbus, c->pd,
+                                                               sigma_f, gpd, gqd);
+}
+
+void launch_hess_prep(opf_ctx* c, double sigma_f) {
+  const DevNet& n = c->dn;
+  hess_prep_kernel<<<nblk(n.nl, 128), 128, 0, c->stream>>>(n, c->vbus, c->thbus, c->lam, c->phid,
+                                                           c->omega, c->Pbus, c->pd, sigma_f, c->btab);
+  bus_weight_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->omega, sigma_f, c->busw);
+}
+
+size_t hvp_stride(const opf_ctx* c, int C) {
+  size_t s = 2 * (size_t)c->dn.nx * C + (size_t)c->dn.ngn * C + C;
+  return (s + 31) & ~(size_t)31;
+}
+
+template <int C>
+static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int tile_step, int ntiles) {
+  HvpArgs a;
+  a.n = c->dn;
+  a.LU = c->LU;
+  a.T = c->T;
+  a.invdiag = c->invdiag;
+  a.tab = c->btab;
+  a.busw = c->busw;
+  a.ubus = c->ubus;
+  a.H = H;
+  a.scratch = c->scratch;
+  a.stride = hvp_stride(c, C);
+  a.ntiles = ntiles;
+  a.first_tile = first_tile;
+  a.tile_step = tile_step;
+  hvp_tile_kernel<C><<<grid, 256, 0, c->stream>>>(a);
+}
+
+bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles) {
+  switch (C) {
+    case 1: launch_hvp_t<1>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 2: launch_hvp_t<2>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 4: launch_hvp_t<4>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 8: launch_hvp_t<8>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 16: launch_hvp_t<16>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 32: launch_hvp_t<32>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    default: return false;
+  }
+}
+
+}  // namespace opf
