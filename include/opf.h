@@ -166,9 +166,11 @@ opf_status opf_reduced_gradient(opf_ctx* ctx, const opf_al_params* p, double* F,
                                 double* grad_pd, double* grad_qd);
 
 typedef struct {
-  int block_k;  /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32 (0 = 8) */
-  int grid;     /* resident CTA tiles (0 = two per SM) */
-  int plain;    /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
+  int block_k;   /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32 (0 = 8) */
+  int grid;      /* resident CTA tiles (0 = one per tile, capped at 4 per SM) */
+  int plain;     /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
+  int col_begin; /* first Hessian column to compute (0) */
+  int col_count; /* number of columns (0 = through n_u); the others of H are left untouched */
 } opf_hess_opts;
 
 typedef struct {
@@ -190,6 +192,9 @@ typedef struct {
  */
 opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts,
                                double* H, opf_hess_info* info);
+
+/* Number of kernels this context has launched since it was created (host output). */
+opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);
 
 /* Human-readable status and the last error message of this thread. */
 const char* opf_status_str(int status);

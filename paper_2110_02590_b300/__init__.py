@@ -55,7 +55,8 @@ class AlParams(C.Structure):
 
 
 class HessOpts(C.Structure):
-    _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int)]
+    _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int), ("col_begin", C.c_int),
+                ("col_count", C.c_int)]
 
 
 class HessInfo(C.Structure):
@@ -93,6 +94,7 @@ def lib():
         L.opf_symbolic_get.argtypes = [C.c_void_p] + [_ip] * 6
         L.opf_symbolic_free.argtypes = [C.c_void_p]
         L.opf_symbolic_free.restype = None
+        L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
         L.opf_last_error.restype = C.c_char_p
@@ -250,7 +252,12 @@ class OPFContext:
             raise OPFError(st, "opf_reduced_gradient")
         return out
 
-    def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None):
+    def launch_count(self) -> int:
+        v = C.c_longlong()
+        lib().opf_launch_count(self.h, C.byref(v))
+        return v.value
+
+    def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None, col_begin=0, col_count=0):
         """Dense reduced Hessian (n_u x n_u) by adjoint-adjoint HVPs (Prop. 2).
 
         Returns (H, info); H is column-major in memory, i.e. H_t[j] is column j.
@@ -260,7 +267,8 @@ class OPFContext:
         p, keep = self._al(al)
         H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
         info = HessInfo()
-        st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(HessOpts(int(block_k), int(grid), int(plain))),
+        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count))
+        st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(opts),
                                        _ptr(H), C.byref(info))
         if st != 0:
             raise OPFError(st, "opf_reduced_hessian")

@@ -479,8 +479,12 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
     FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
   const bool plain = o && o->plain;
-  const int ntiles = (c->h.nu + C - 1) / C;
-  int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : 2 * c->sm_count);
+  const int nu = c->h.nu;
+  const int col0 = o ? o->col_begin : 0;
+  const int ncol = (o && o->col_count > 0) ? o->col_count : nu - col0;
+  if (col0 < 0 || col0 >= nu || ncol < 1 || col0 + ncol > nu) FAIL(OPF_EINVAL, "column range outside [0, n_u)");
+  const int ntiles = (ncol + C - 1) / C;
+  int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : std::min(ntiles, 4 * c->sm_count));
   grid = std::max(1, std::min(grid, ntiles));
   TRY(ensure_scratch(c, hvp_stride(c, C) * (size_t)grid));
   cudaStream_t st = c->stream;
@@ -490,9 +494,9 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   CK(cudaEventRecord(c->ev[1], st));
   int launches = 0;
   if (plain) {
-    for (int t = 0; t < ntiles; t++, launches++) launch_hvp(c, C, H, 1, t, 1, t + 1);
+    for (int t = 0; t < ntiles; t++, launches++) launch_hvp(c, C, H, 1, t, 1, t + 1, col0, col0 + ncol);
   } else {
-    launch_hvp(c, C, H, grid, 0, 1, ntiles);
+    launch_hvp(c, C, H, grid, 0, 1, ntiles, col0, col0 + ncol);
     launches = 1;
   }
   CK(cudaEventRecord(c->ev[2], st));
@@ -506,6 +510,12 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
     cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
   }
+  return OPF_OK;
+}
+
+opf_status opf_launch_count(const opf_ctx* c, long long* launches) {
+  if (!c || !launches) FAIL(OPF_EINVAL, "ctx and launches are required");
+  *launches = c->launches;
   return OPF_OK;
 }
 

@@ -65,7 +65,8 @@ void launch_grad_u(opf_ctx* c, double* gu);
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
 void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);
-bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles);
+bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
+                int col0, int col_end);
 
 }  // namespace opf
 
@@ -108,4 +109,5 @@ struct opf_ctx {
   double* scratch = nullptr;      // HVP per-CTA slabs
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];
+  long long launches = 0;         // kernels launched by this context
 };

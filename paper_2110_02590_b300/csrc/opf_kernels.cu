@@ -509,6 +509,7 @@ struct HvpArgs {
   double* scratch;
   size_t stride;    // doubles of scratch per CTA
   int ntiles, first_tile, tile_step;
+  int col0, col_end;  // columns computed: col0 .. col_end - 1
 };
 
 template <int C>
@@ -523,7 +524,7 @@ __device__ __forceinline__ void direction(const DevNet& n, const double* Z, int 
 template <int C>
 __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
   const DevNet& n = a.n;
-  const int nl = n.nl, nb = n.nb, nu = n.nu;
+  const int nl = n.nl, nb = n.nb, nu = n.nu, jend = a.col_end;
   double* Z = a.scratch + a.stride * blockIdx.x;
   double* R = Z + (size_t)n.nx * C;
   double* QD = R + (size_t)n.nx * C;
@@ -531,13 +532,13 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
   const double* tab = a.tab;
   for (int tile = a.first_tile + blockIdx.x * a.tile_step; tile < a.ntiles;
        tile += gridDim.x * a.tile_step) {
-    const int j0 = tile * C;
+    const int j0 = a.col0 + tile * C;
     // (0) right-hand side B = -G_u W, W = unit directions j0 .. j0 + C - 1
     for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
       const int j = j0 + c;
-      if (j >= nu) continue;
+      if (j >= jend) continue;
       const int k = a.ubus[j];
       if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
         Z[(size_t)n.pth[k] * C + c] = 1.0;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
       if (n.type[i] != REF) R[(size_t)n.pth[i] * C + c] = -yt;
       if (n.type[i] == PQ) {
         R[(size_t)n.pvv[i] * C + c] = -yv;
-      } else if (j < nu) {
+      } else if (j < jend) {
         double* Hc = a.H + (size_t)j * nu;
         Hc[n.uv[i]] = yv;
         if (n.type[i] == PV) Hc[n.up[i]] = (n.up[i] == j) ? a.busw[3 * nb + i] : 0.0;
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
     // (7) H[:, tile] += G_u^T Psi
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
       const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = j0 + c;
-      if (j >= nu) continue;
+      if (j >= jend) continue;
       double gv = 0.0, selfP = 0.0;
       for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
         const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
@@ -661,10 +662,12 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_unpack(opf_ctx* c, const double* x, const double* u) {
+  c->launches++;
   unpack_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, x, u, c->vbus, c->thbus);
 }
 
 void launch_pf_eval(opf_ctx* c) {
+  c->launches++;
   pf_eval_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->u, c->pd,
                                                                c->qd, c->g, c->LU, c->scal);
 }
@@ -676,19 +679,23 @@ void launch_lu(opf_ctx* c) {
     if (t1 == t0) continue;
     const int warps = t1 - t0;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
+    c->launches++;
     lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->dn.rp, c->dn.ci, c->dn.dp, c->task_col,
                                                    c->task_k, c->lcol_row, c->lcol_pos, t0, t1, c->flags);
   }
+  c->launches++;
   lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
                                                            c->dn.nx, c->dn.nnz, c->flags);
 }
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
+  c->launches++;
   solve1_kernel<<<1, 1024, 0, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
                                            transposed ? 1 : 0, scale);
 }
 
 void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n) {
+  c->launches++;
   axpy_kernel<<<nblk(n, 256), 256, 0, c->stream>>>(x, d, a, n);
 }
 
@@ -696,31 +703,39 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
   const DevNet& n = c->dn;
   cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
   launch_unpack(c, c->x, c->u);
+  c->launches++;
   branch_flow_kernel<<<nblk(n.nl, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->flows, c->cvec);
+  c->launches++;
   bus_inj_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->flows, c->pd, c->qd, c->Pbus,
                                                          c->Qbus, c->cvec);
   const int mm = std::max(n.m, n.ng);
+  c->launches++;
   al_weights_kernel<<<nblk(mm, 256), 256, 0, c->stream>>>(
       n, c->cvec, p->sigma_c, p->y, p->s, p->omega, p->rho, p->sigma_f, c->Pbus, c->u, c->pd,
       c->c0, c->phid, grad_s, c->omega, c->scal);
+  c->launches++;
   dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, c->phid, c->Pbus,
                                                         c->pd, p->sigma_f, c->dFx, c->dFu);
   launch_solve1(c, c->dFx, c->lam, true, -1.0);
 }
 
 void launch_grad_u(opf_ctx* c, double* gu) {
+  c->launches++;
   grad_u_kernel<<<nblk(c->dn.ngn, 128), 128, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->lam, c->dFu, gu);
 }
 
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd) {
+  c->launches++;
   grad_load_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, c->lam, c->phid, c->Pbus, c->pd,
                                                                sigma_f, gpd, gqd);
 }
 
 void launch_hess_prep(opf_ctx* c, double sigma_f) {
   const DevNet& n = c->dn;
+  c->launches++;
   hess_prep_kernel<<<nblk(n.nl, 128), 128, 0, c->stream>>>(n, c->vbus, c->thbus, c->lam, c->phid,
                                                            c->omega, c->Pbus, c->pd, sigma_f, c->btab);
+  c->launches++;
   bus_weight_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->omega, sigma_f, c->busw);
 }
 
@@ -730,7 +745,8 @@ size_t hvp_stride(const opf_ctx* c, int C) {
 }
 
 template <int C>
-static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int tile_step, int ntiles) {
+static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int tile_step, int ntiles,
+                         int col0, int col_end) {
   HvpArgs a;
   a.n = c->dn;
   a.LU = c->LU;
@@ -745,17 +761,21 @@ static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int ti
   a.ntiles = ntiles;
   a.first_tile = first_tile;
   a.tile_step = tile_step;
+  a.col0 = col0;
+  a.col_end = col_end;
   hvp_tile_kernel<C><<<grid, 256, 0, c->stream>>>(a);
+  c->launches++;
 }
 
-bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles) {
+bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
+                int col0, int col_end) {
   switch (C) {
-    case 1: launch_hvp_t<1>(c, H, grid, first_tile, tile_step, ntiles); return true;
-    case 2: launch_hvp_t<2>(c, H, grid, first_tile, tile_step, ntiles); return true;
-    case 4: launch_hvp_t<4>(c, H, grid, first_tile, tile_step, ntiles); return true;
-    case 8: launch_hvp_t<8>(c, H, grid, first_tile, tile_step, ntiles); return true;
-    case 16: launch_hvp_t<16>(c, H, grid, first_tile, tile_step, ntiles); return true;
-    case 32: launch_hvp_t<32>(c, H, grid, first_tile, tile_step, ntiles); return true;
+    case 1: launch_hvp_t<1>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    case 2: launch_hvp_t<2>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    case 4: launch_hvp_t<4>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    case 8: launch_hvp_t<8>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    case 16: launch_hvp_t<16>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    case 32: launch_hvp_t<32>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
     default: return false;
   }
 }
