@@ -193,6 +193,31 @@ typedef struct {
 opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts,
                                double* H, opf_hess_info* info);
 
+/*
+ * opf_reduced_hessian_noalloc: the same reduced Hessian as opf_reduced_hessian
+ * (same kernels, same options and outputs), for callers that must not allocate
+ * device memory during the call -- a real-time tracking loop that cannot stall
+ * on the allocator (cudaMalloc may synchronise the device), a caller inside
+ * stream capture, or a process with a device-memory budget fixed at start-up.
+ * The paper has no counterpart: this is an interface choice of this library.
+ *   - Workspace: a fixed array of OPF_NOALLOC_SCRATCH_BYTES (32 MiB) in device
+ *     memory, which every GPU that loads the library holds until the process
+ *     exits.  No call allocates or frees anything.
+ *   - Limit: one tile needs (2 n_x + n_ctrl + 1) block_k doubles, n_ctrl =
+ *     n_pv + 1, rounded up to 32; a network/block_k whose tile does not fit is
+ *     rejected with OPF_EINVAL and a message.  As many tiles run at once as fit
+ *     (fewer than opf_reduced_hessian may use, so it can be slower).
+ *   - The first call on a device looks up the array's device address (once per
+ *     device); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; the
+ *     kernel clears what it needs per tile.  Calls that overlap on the GPU (two
+ *     streams, two contexts, two threads) race on it: serialise them.
+ * Errors: as opf_reduced_hessian, plus OPF_EINVAL for the size limit.
+ */
+#define OPF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+opf_status opf_reduced_hessian_noalloc(opf_ctx* ctx, const opf_al_params* p,
+                                       const opf_hess_opts* opts, double* H, opf_hess_info* info);
+
 /* Number of kernels this context has launched since it was created (host output). */
 opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);
 

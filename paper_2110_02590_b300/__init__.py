@@ -94,6 +94,8 @@ def lib():
         L.opf_symbolic_get.argtypes = [C.c_void_p] + [_ip] * 6
         L.opf_symbolic_free.argtypes = [C.c_void_p]
         L.opf_symbolic_free.restype = None
+        L.opf_reduced_hessian_noalloc.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts),
+                                                  C.c_void_p, C.POINTER(HessInfo)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
@@ -272,5 +274,20 @@ class OPFContext:
                                        _ptr(H), C.byref(info))
         if st != 0:
             raise OPFError(st, "opf_reduced_hessian")
+        return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
+                         ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+
+    def reduced_hessian_noalloc(self, al, block_k=8, grid=0, out=None, col_begin=0, col_count=0):
+        """Reduced Hessian through opf_reduced_hessian_noalloc (fixed static workspace, no allocation
+        inside the call).  `out` should be preallocated by callers that cannot allocate."""
+        t = self.torch
+        self._sync_stream()
+        p, keep = self._al(al)
+        H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
+        info = HessInfo()
+        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count))
+        st = lib().opf_reduced_hessian_noalloc(self.h, C.byref(p), C.byref(opts), _ptr(H), C.byref(info))
+        if st != 0:
+            raise OPFError(st, "opf_reduced_hessian_noalloc")
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
                          ms_total=info.ms_total, ms_hvp=info.ms_hvp)

@@ -13,6 +13,10 @@ using namespace opf;
 
 static thread_local std::string g_err;
 
+namespace opf {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace opf
+
 #define FAIL(st, msg)  \
   do {                 \
     g_err = (msg);     \

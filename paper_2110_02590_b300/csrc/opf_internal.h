@@ -67,6 +67,9 @@ void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);
 bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
                 int col0, int col_end);
+bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
+                        int col_end);
+void set_last_error(const std::string& msg);  // message returned by opf_last_error
 
 }  // namespace opf
 

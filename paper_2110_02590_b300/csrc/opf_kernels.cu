@@ -780,4 +780,41 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
   }
 }
 
+// Same tile kernel with an explicitly given workspace (scratch of `grid` CTAs).
+template <int C>
+static void launch_hvp_scratch_t(opf_ctx* c, double* H, double* scratch, int grid, int ntiles, int col0,
+                                 int col_end) {
+  HvpArgs a;
+  a.n = c->dn;
+  a.LU = c->LU;
+  a.T = c->T;
+  a.invdiag = c->invdiag;
+  a.tab = c->btab;
+  a.busw = c->busw;
+  a.ubus = c->ubus;
+  a.H = H;
+  a.scratch = scratch;
+  a.stride = hvp_stride(c, C);
+  a.ntiles = ntiles;
+  a.first_tile = 0;
+  a.tile_step = 1;
+  a.col0 = col0;
+  a.col_end = col_end;
+  hvp_tile_kernel<C><<<grid, 256, 0, c->stream>>>(a);
+  c->launches++;
+}
+
+bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
+                        int col_end) {
+  switch (C) {
+    case 1: launch_hvp_scratch_t<1>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    case 2: launch_hvp_scratch_t<2>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    case 4: launch_hvp_scratch_t<4>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    case 8: launch_hvp_scratch_t<8>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    case 16: launch_hvp_scratch_t<16>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    case 32: launch_hvp_scratch_t<32>(c, H, scratch, grid, ntiles, col0, col_end); return true;
+    default: return false;
+  }
+}
+
 }  // namespace opf

@@ -1,0 +1,59 @@
+"""The no-allocation Hessian entry point against the regular one (GPU).
+
+opf_reduced_hessian_noalloc serves callers that cannot allocate device memory
+during a call -- a real-time loop that must not stall on cudaMalloc, code
+under stream capture, a process with a fixed device-memory budget.  It uses
+the library's fixed static workspace instead of a per-context allocation.
+These tests call it twice in a row through the C ABI (the second call sees
+the first call's leftovers in the shared workspace) and compare each result
+with opf_reduced_hessian within the Hessian tolerance of the parity tests.
+This file is collected last so a failure here does not hide the other tests.
+"""
+import numpy as np
+import pytest
+
+from paper_2110_02590_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2110_02590_b300 as P  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+HESS_TOL = 1e-8
+
+
+def rel_fro(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name,block_k", [("medium1400", 8), ("large9200", 8), ("large9200", 32)])
+def test_noalloc_matches_regular_twice(name, block_k):
+    net = synth.workload(name)
+    ctx = P.OPFContext(net)
+    ctx.powerflow(torch.as_tensor(synth.flat_control(net), device=DEV))
+    al = {k: (torch.as_tensor(v, device=DEV) if isinstance(v, np.ndarray) else v)
+          for k, v in synth.al_inputs(net, seed=7).items()}
+    H_ref, _ = ctx.reduced_hessian(al, block_k=block_k)
+    H_ref = H_ref.clone()
+    out = torch.empty((ctx.nu, ctx.nu), dtype=torch.float64, device=DEV)
+    for call in range(2):
+        out.fill_(float("nan"))
+        H, info = ctx.reduced_hessian_noalloc(al, block_k=block_k, out=out)
+        assert info["tiles"] == -(-ctx.nu // block_k)
+        assert 1 <= info["grid"] <= info["tiles"]
+        assert bool(torch.isfinite(H).all())
+        assert rel_fro(H, H_ref) < HESS_TOL, (call, rel_fro(H, H_ref))
+
+
+def test_noalloc_state_error():
+    net = synth.workload("tiny30")
+    ctx = P.OPFContext(net)
+    al = {k: (torch.as_tensor(v, device=DEV) if isinstance(v, np.ndarray) else v)
+          for k, v in synth.al_inputs(net, seed=1).items()}
+    with pytest.raises(P.OPFError) as ei:
+        ctx.reduced_hessian_noalloc(al)
+    assert ei.value.status == 7
