@@ -139,6 +139,36 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   std::vector<int> lrows_f, lrows_b;
   level_lists(s.lev_f, s.nlev_f, c->h_lev_ptr_f, lrows_f);
   level_lists(s.lev_b, s.nlev_b, c->h_lev_ptr_b, lrows_b);
+  // dense trailing block [r0, nx): every row's upper part runs to the last column
+  int r0 = nx - 1;
+  while (r0 > 0 && s.rp[r0] - s.dp[r0 - 1] - 1 == nx - r0) r0--;
+  // sweep schedules of the other rows; rows of a level sorted by length (longest first)
+  std::vector<int> sched_ptr_f, sched_rows_f, sched_ptr_b, sched_rows_b;
+  {
+    auto build = [&](const std::vector<int>& lev, bool fwd, std::vector<int>& ptr, std::vector<int>& rows) {
+      int nlev = 0;
+      for (int i = 0; i < r0; i++) nlev = std::max(nlev, lev[i] + 1);
+      ptr.assign(nlev + 1, 0);
+      for (int i = 0; i < r0; i++) ptr[lev[i] + 1]++;
+      for (int k = 0; k < nlev; k++) ptr[k + 1] += ptr[k];
+      rows.assign(r0, 0);
+      std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+      for (int i = 0; i < r0; i++) rows[fill[lev[i]]++] = i;
+      auto len = [&](int i) { return fwd ? s.dp[i] - s.rp[i] : s.rp[i + 1] - s.dp[i] - 1; };
+      for (int k = 0; k < nlev; k++)
+        std::stable_sort(rows.begin() + ptr[k], rows.begin() + ptr[k + 1],
+                         [&](int a, int b) { return len(a) > len(b); });
+    };
+    std::vector<int> levb(nx, 0);
+    for (int i = r0 - 1; i >= 0; i--) {
+      int lv = 0;
+      for (int p = s.dp[i] + 1; p < s.rp[i + 1]; p++)
+        if (s.ci[p] < r0) lv = std::max(lv, levb[s.ci[p]] + 1);
+      levb[i] = lv;
+    }
+    build(s.lev_f, true, sched_ptr_f, sched_rows_f);
+    build(levb, false, sched_ptr_b, sched_rows_b);
+  }
   std::vector<int> task_col, task_k;
   c->h_task_ptr.assign(s.nlev_f + 1, 0);
   for (int lv = 0; lv < s.nlev_f; lv++) {
@@ -177,8 +207,10 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   n.m = h.m;
   n.ngn = (int)gn_bus.size();
   n.nnz = nnz;
-  n.nlev_f = s.nlev_f;
-  n.nlev_b = s.nlev_b;
+  n.nlev_f = (int)sched_ptr_f.size() - 1;
+  n.nlev_b = (int)sched_ptr_b.size() - 1;
+  n.r0 = r0;
+  n.nroot = nx - r0;
   int* ip;
   double* dptr;
   TRY(dupload(c, &ip, h.f)); n.f = ip;
@@ -206,10 +238,10 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, s.ci)); n.ci = ip;
   TRY(dupload(c, &ip, s.dp)); n.dp = ip;
   TRY(dupload(c, &ip, s.perm)); n.perm = ip;
-  TRY(dupload(c, &ip, c->h_lev_ptr_f)); n.lev_ptr_f = ip;
-  TRY(dupload(c, &ip, lrows_f)); n.lev_rows_f = ip;
-  TRY(dupload(c, &ip, c->h_lev_ptr_b)); n.lev_ptr_b = ip;
-  TRY(dupload(c, &ip, lrows_b)); n.lev_rows_b = ip;
+  TRY(dupload(c, &ip, sched_ptr_f)); n.lev_ptr_f = ip;
+  TRY(dupload(c, &ip, sched_rows_f)); n.lev_rows_f = ip;
+  TRY(dupload(c, &ip, sched_ptr_b)); n.lev_ptr_b = ip;
+  TRY(dupload(c, &ip, sched_rows_b)); n.lev_rows_b = ip;
   TRY(dupload(c, &ip, slot_self)); n.slot_self = ip;
   TRY(dupload(c, &ip, slot_adj)); n.slot_adj = ip;
   TRY(dupload(c, &c->tmap, tmap));

@@ -48,8 +48,11 @@ struct DevNet {
   const double *c2, *c1;
   // LU pattern
   const int *rp, *ci, *dp, *perm;
+  // execution schedule of the sweeps: level lists of the rows outside the dense
+  // trailing block [r0, nx) (which is solved as a dense triangle)
   const int *lev_ptr_f, *lev_rows_f, *lev_ptr_b, *lev_rows_b;
   int nlev_f, nlev_b;
+  int r0, nroot;
   const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
   const int* slot_adj;             // [4 * 2 nl]
 };

@@ -185,9 +185,33 @@ __global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, c
 
 // ------------------------------------------------------------ sweeps
 
-// One level-scheduled triangular sweep over a CTA-private right-hand-side slab
-// X[n_x][C].  FWD: rows ascending by level over the lower part of V; else the
-// upper part.  DIAG: multiply by 1/U_ii after the row.
+// Rows [p0, p1) of V against the slab: s = X[i] - sum V[p] X[ci[p]] (two partial sums
+// and four loads in flight per lane group).
+template <int C>
+__device__ __forceinline__ double row_dot(const DevNet& n, const double* __restrict__ V, const double* X,
+                                          int i, int p0, int p1, int col) {
+  double s0 = X[(size_t)i * C + col], s1 = 0.0;
+  int p = p0;
+  for (; p + 3 < p1; p += 4) {
+    const int c0 = n.ci[p], c1 = n.ci[p + 1], c2 = n.ci[p + 2], c3 = n.ci[p + 3];
+    const double v0 = V[p], v1 = V[p + 1], v2 = V[p + 2], v3 = V[p + 3];
+    const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
+    const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
+    s0 -= v0 * x0;
+    s1 -= v1 * x1;
+    s0 -= v2 * x2;
+    s1 -= v3 * x3;
+  }
+  for (; p < p1; p++) s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
+  return s0 + s1;
+}
+
+// One triangular sweep over a CTA-private right-hand-side slab X[n_x][C].
+// Rows outside the dense trailing block [r0, n_x) follow the level schedule
+// (FWD: lower part of V, rows by ascending level; else the upper part).  The
+// dense block is solved as a dense triangle, one column per step: after x_j is
+// known every thread updates its (row, column) items below (FWD) or above it.
+// DIAG: multiply each row by 1/U_ii once its sum is complete.
 template <int C, bool FWD, bool DIAG>
 __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
                                       const double* __restrict__ invdiag, double* X) {
@@ -195,27 +219,81 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = lane % C;
   const int nslots = (blockDim.x >> 5) * RPW, myslot = warp * RPW + lane / C;
+  const int r0 = n.r0, s = n.nroot;
+  if (!FWD) {  // dense upper triangle of the trailing block first
+    for (int j = s - 1; j > 0; j--) {
+      const int rj = r0 + j;
+      const double dj = DIAG ? invdiag[rj] : 1.0;
+      for (int it = threadIdx.x; it < j * C; it += blockDim.x) {
+        const int i = it / C, c = it % C, ri = r0 + i;
+        X[(size_t)ri * C + c] -= V[n.dp[ri] + (j - i)] * (X[(size_t)rj * C + c] * dj);
+      }
+      __syncthreads();
+    }
+    if (DIAG) {
+      for (int it = threadIdx.x; it < s * C; it += blockDim.x) {
+        const int i = it / C, c = it % C;
+        X[(size_t)(r0 + i) * C + c] *= invdiag[r0 + i];
+      }
+      __syncthreads();
+    }
+  }
   const int nlev = FWD ? n.nlev_f : n.nlev_b;
   const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
   const int* lrows = FWD ? n.lev_rows_f : n.lev_rows_b;
+  const int nwarps = blockDim.x >> 5, grp = lane / C;
   for (int lv = 0; lv < nlev; lv++) {
     const int b = lptr[lv], e = lptr[lv + 1];
-    for (int k = b + myslot; k < e; k += nslots) {
-      const int i = lrows[k];
-      const int p0 = FWD ? n.rp[i] : n.dp[i] + 1;
-      const int p1 = FWD ? n.dp[i] : n.rp[i + 1];
-      double s0 = X[(size_t)i * C + col], s1 = 0.0;
-      int p = p0;
-      for (; p + 1 < p1; p += 2) {
-        s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
-        s1 -= V[p + 1] * X[(size_t)n.ci[p + 1] * C + col];
+    if (e - b <= nwarps && RPW > 1) {
+      // narrow level: one warp per row, its lane groups split the row, shuffle reduction
+      for (int k = b + warp; k < e; k += nwarps) {
+        const int i = lrows[k];
+        const int p0 = FWD ? n.rp[i] : n.dp[i] + 1, p1 = FWD ? n.dp[i] : n.rp[i + 1];
+        double v = 0.0;
+        for (int p = p0 + grp; p < p1; p += RPW) v -= V[p] * X[(size_t)n.ci[p] * C + col];
+#pragma unroll
+        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (grp == 0) {
+          v += X[(size_t)i * C + col];
+          if (DIAG) v *= invdiag[i];
+          X[(size_t)i * C + col] = v;
+        }
       }
-      if (p < p1) s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
-      double s = s0 + s1;
-      if (DIAG) s *= invdiag[i];
-      X[(size_t)i * C + col] = s;
+    } else {
+      for (int k = b + myslot; k < e; k += nslots) {
+        const int i = lrows[k];
+        double v = FWD ? row_dot<C>(n, V, X, i, n.rp[i], n.dp[i], col)
+                       : row_dot<C>(n, V, X, i, n.dp[i] + 1, n.rp[i + 1], col);
+        if (DIAG) v *= invdiag[i];
+        X[(size_t)i * C + col] = v;
+      }
     }
     __syncthreads();
+  }
+  if (FWD) {
+    // off-block part of the trailing rows (columns < r0), all rows in parallel
+    for (int k = myslot; k < s; k += nslots) {
+      const int i = r0 + k;
+      X[(size_t)i * C + col] = row_dot<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col);
+    }
+    __syncthreads();
+    // dense lower triangle
+    for (int j = 0; j < s - 1; j++) {
+      const int rj = r0 + j;
+      const double dj = DIAG ? invdiag[rj] : 1.0;
+      for (int it = threadIdx.x; it < (s - 1 - j) * C; it += blockDim.x) {
+        const int i = j + 1 + it / C, c = it % C, ri = r0 + i;
+        X[(size_t)ri * C + c] -= V[n.dp[ri] - (i - j)] * (X[(size_t)rj * C + c] * dj);
+      }
+      __syncthreads();
+    }
+    if (DIAG) {
+      for (int it = threadIdx.x; it < s * C; it += blockDim.x) {
+        const int i = it / C, c = it % C;
+        X[(size_t)(r0 + i) * C + c] *= invdiag[r0 + i];
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -673,7 +751,7 @@ void launch_pf_eval(opf_ctx* c) {
 }
 
 void launch_lu(opf_ctx* c) {
-  const int nlev = c->dn.nlev_f;
+  const int nlev = (int)c->h_task_ptr.size() - 1;  // elimination levels (all columns)
   for (int lv = 0; lv < nlev; lv++) {
     const int t0 = c->h_task_ptr[lv], t1 = c->h_task_ptr[lv + 1];
     if (t1 == t0) continue;
