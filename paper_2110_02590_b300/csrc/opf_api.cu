@@ -169,17 +169,20 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     build(s.lev_f, true, sched_ptr_f, sched_rows_f);
     build(levb, false, sched_ptr_b, sched_rows_b);
   }
+  // LU tasks: (column, lower entry) pairs of the columns outside the dense trailing
+  // block, grouped by elimination level; the trailing block is factorised densely.
   std::vector<int> task_col, task_k;
-  c->h_task_ptr.assign(s.nlev_f + 1, 0);
+  c->h_task_ptr.assign(1, 0);
   for (int lv = 0; lv < s.nlev_f; lv++) {
     for (int q = c->h_lev_ptr_f[lv]; q < c->h_lev_ptr_f[lv + 1]; q++) {
       const int j = lrows_f[q];
+      if (j >= r0) continue;
       for (int k = lcnt[j]; k < lcnt[j + 1]; k++) {
         task_col.push_back(j);
         task_k.push_back(k);
       }
     }
-    c->h_task_ptr[lv + 1] = (int)task_col.size();
+    if ((int)task_col.size() > c->h_task_ptr.back()) c->h_task_ptr.push_back((int)task_col.size());
   }
   // control buses: slack first, then PV
   std::vector<int> gn_bus, gn_of(nb, -1), ubus(h.nu, -1);
@@ -281,6 +284,26 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
+  // the numeric refactorisation as one CUDA graph (captured once on a private stream)
+  CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_lu_kernels(c);
+      e = cudaStreamEndCapture(c->cap_stream, &graph);
+    }
+    c->stream = user;
+    c->lu_graph_kernels = c->launches - l0;
+    c->launches = l0;
+    CK(e);
+    e = cudaGraphInstantiate(&c->lu_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+  }
   return OPF_OK;
 }
 
@@ -293,6 +316,8 @@ static void free_impl(opf_ctx* c) {
   if (c->h_flags) cudaFreeHost(c->h_flags);
   for (int k = 0; k < 4; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->lu_exec) cudaGraphExecDestroy(c->lu_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 

@@ -60,7 +60,8 @@ struct DevNet {
 // kernel launchers (opf_kernels.cu)
 void launch_unpack(opf_ctx* c, const double* x, const double* u);
 void launch_pf_eval(opf_ctx* c);
-void launch_lu(opf_ctx* c);
+void launch_lu(opf_ctx* c);          // replays the captured refactorisation graph
+void launch_lu_kernels(opf_ctx* c);  // the kernel sequence itself (captured at load)
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale);
 void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n);
 void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
@@ -116,4 +117,7 @@ struct opf_ctx {
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];
   long long launches = 0;         // kernels launched by this context
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t lu_exec = nullptr;
+  long long lu_graph_kernels = 0;
 };

@@ -172,6 +172,27 @@ __global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const in
   }
 }
 
+// In-place LU without pivoting of the dense trailing block [r0, r0 + s) once every
+// other column has been eliminated (all its Schur updates applied).  Entry
+// (i, j) of the block sits at dp[r0+i] + (j - i) of row r0 + i.  One CTA.
+__global__ void __launch_bounds__(1024) lu_dense_block_kernel(double* LU, const int* __restrict__ dp,
+                                                              int r0, int s, int* flags) {
+  for (int k = 0; k < s - 1; k++) {
+    const int rk = r0 + k;
+    const double ukk = LU[dp[rk]];
+    if (threadIdx.x == 0 && (!(fabs(ukk) > 0.0) || !isfinite(ukk))) flags[0] = 1;
+    const double inv = 1.0 / ukk;
+    for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) LU[dp[r0 + i] - (i - k)] *= inv;
+    __syncthreads();
+    const int w = s - 1 - k;
+    for (int it = threadIdx.x; it < w * w; it += blockDim.x) {
+      const int i = k + 1 + it / w, j = k + 1 + it % w, ri = r0 + i;
+      LU[dp[ri] + (j - i)] -= LU[dp[ri] - (i - k)] * LU[dp[rk] + (j - k)];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, const int* tmap,
                                  const int* dp, int nx, int nnz, int* flags) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -750,11 +771,10 @@ void launch_pf_eval(opf_ctx* c) {
                                                                c->qd, c->g, c->LU, c->scal);
 }
 
-void launch_lu(opf_ctx* c) {
-  const int nlev = (int)c->h_task_ptr.size() - 1;  // elimination levels (all columns)
+void launch_lu_kernels(opf_ctx* c) {
+  const int nlev = (int)c->h_task_ptr.size() - 1;  // elimination levels of the non-trailing columns
   for (int lv = 0; lv < nlev; lv++) {
     const int t0 = c->h_task_ptr[lv], t1 = c->h_task_ptr[lv + 1];
-    if (t1 == t0) continue;
     const int warps = t1 - t0;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
     c->launches++;
@@ -762,8 +782,15 @@ void launch_lu(opf_ctx* c) {
                                                    c->task_k, c->lcol_row, c->lcol_pos, t0, t1, c->flags);
   }
   c->launches++;
+  lu_dense_block_kernel<<<1, 1024, 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags);
+  c->launches++;
   lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
                                                            c->dn.nx, c->dn.nnz, c->flags);
+}
+
+void launch_lu(opf_ctx* c) {
+  cudaGraphLaunch(c->lu_exec, c->stream);
+  c->launches += c->lu_graph_kernels;
 }
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
