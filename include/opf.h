@@ -171,6 +171,7 @@ typedef struct {
   int plain;     /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
   int col_begin; /* first Hessian column to compute (0) */
   int col_count; /* number of columns (0 = through n_u); the others of H are left untouched */
+  int threads;   /* threads per tile CTA: 256 or 512 (0 = 256) */
 } opf_hess_opts;
 
 typedef struct {

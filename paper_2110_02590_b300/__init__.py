@@ -56,7 +56,7 @@ class AlParams(C.Structure):
 
 class HessOpts(C.Structure):
     _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int), ("col_begin", C.c_int),
-                ("col_count", C.c_int)]
+                ("col_count", C.c_int), ("threads", C.c_int)]
 
 
 class HessInfo(C.Structure):
@@ -259,7 +259,8 @@ class OPFContext:
         lib().opf_launch_count(self.h, C.byref(v))
         return v.value
 
-    def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None, col_begin=0, col_count=0):
+    def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None, col_begin=0, col_count=0,
+                        threads=0):
         """Dense reduced Hessian (n_u x n_u) by adjoint-adjoint HVPs (Prop. 2).
 
         Returns (H, info); H is column-major in memory, i.e. H_t[j] is column j.
@@ -269,7 +270,7 @@ class OPFContext:
         p, keep = self._al(al)
         H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
         info = HessInfo()
-        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count))
+        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count), int(threads))
         st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(opts),
                                        _ptr(H), C.byref(info))
         if st != 0:
@@ -285,7 +286,7 @@ class OPFContext:
         p, keep = self._al(al)
         H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
         info = HessInfo()
-        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count))
+        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count), 0)
         st = lib().opf_reduced_hessian_noalloc(self.h, C.byref(p), C.byref(opts), _ptr(H), C.byref(info))
         if st != 0:
             raise OPFError(st, "opf_reduced_hessian_noalloc")

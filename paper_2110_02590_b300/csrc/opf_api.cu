@@ -280,7 +280,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->dFu, h.nu));
   TRY(dalloc(c, &c->lam, nx));
   TRY(dalloc(c, &c->btab, 26 * (size_t)nl));
-  TRY(dalloc(c, &c->busw, 4 * (size_t)nb));
+  TRY(dalloc(c, &c->busw, 8 * (size_t)nb));
   CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
@@ -539,6 +539,9 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   int C = (o && o->block_k) ? o->block_k : 8;
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
     FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
+  const int nt = (o && o->threads) ? o->threads : 256;
+  if (nt != 256 && nt != 512) FAIL(OPF_EINVAL, "threads must be 256 or 512");
+  c->hvp_threads = nt;
   const bool plain = o && o->plain;
   const int nu = c->h.nu;
   const int col0 = o ? o->col_begin : 0;

@@ -112,7 +112,8 @@ struct opf_ctx {
   double *cvec = nullptr, *phid = nullptr, *omega = nullptr;
   double *dFx = nullptr, *dFu = nullptr, *lam = nullptr;
   double *btab = nullptr;         // [26 nl] per-branch Hessian table
-  double *busw = nullptr;         // [4 nb]: kQ, kP, diag v, diag p
+  double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
+  int hvp_threads = 256;          // threads per HVP tile CTA
   double* scratch = nullptr;      // HVP per-CTA slabs
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];

@@ -598,6 +598,26 @@ __global__ void bus_weight_kernel(DevNet n, const double* om, double sigma_f, do
   w[3 * nb + i] = dpp;
 }
 
+// Rows 4..7 of the bus weights: dQ_i/dv_i, dQ_i/dtheta_i, dP_i/dv_i, dP_i/dtheta_i
+// (sums over the incident branch ends, from the branch table).
+__global__ void bus_self_grad_kernel(DevNet n, const double* tab, double* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  const int nl = n.nl, nb = n.nb;
+  double qv = 0, qt = 0, pv = 0, pt = 0;
+  for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
+    const int e = n.adj[q], l = e >> 1, s = e & 1;
+    qv += tab[(size_t)TAB_DQ(s, s) * nl + l];
+    qt += tab[(size_t)TAB_DQ(s, 2 + s) * nl + l];
+    pv += tab[(size_t)TAB_DP(s, s) * nl + l];
+    pt += tab[(size_t)TAB_DP(s, 2 + s) * nl + l];
+  }
+  w[4 * nb + i] = qv;
+  w[5 * nb + i] = qt;
+  w[6 * nb + i] = pv;
+  w[7 * nb + i] = pt;
+}
+
 // ------------------------------------------------------------ HVP tiles
 
 struct HvpArgs {
@@ -620,8 +640,8 @@ __device__ __forceinline__ void direction(const DevNet& n, const double* Z, int 
 
 // One CTA = one tile of C Hessian columns at a time: B = -G_u W, Z = G_x^{-1} B,
 // second-order terms, Psi = G_x^{-T} R, H[:, tile] = T + G_u^T Psi (Prop. 2).
-template <int C>
-__global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
+template <int C, int NT>
+__global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
   const DevNet& n = a.n;
   const int nl = n.nl, nb = n.nb, nu = n.nu, jend = a.col_end;
   double* Z = a.scratch + a.stride * blockIdx.x;
@@ -666,9 +686,10 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
         direction<C>(n, Z, n.f[l], c, j, d[0], d[2]);
         direction<C>(n, Z, n.t[l], c, j, d[1], d[3]);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-          qd += tab[(size_t)TAB_DQ(s, t) * nl + l] * d[t];
-          pdr += tab[(size_t)TAB_DP(s, t) * nl + l] * d[t];
+        for (int t = 0; t < 4; t++) qd += tab[(size_t)TAB_DQ(s, t) * nl + l] * d[t];
+        if (k == n.ref) {
+#pragma unroll
+          for (int t = 0; t < 4; t++) pdr += tab[(size_t)TAB_DP(s, t) * nl + l] * d[t];
         }
       }
       QD[(size_t)gi * C + c] = qd;
@@ -680,7 +701,7 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
       const int i = it / C, c = it % C, j = j0 + c;
       double vi, ti;
       direction<C>(n, Z, i, c, j, vi, ti);
-      double yv = 0.0, yt = 0.0, sq_v = 0.0, sq_t = 0.0, sp_v = 0.0, sp_t = 0.0;
+      double yv = 0.0, yt = 0.0;
       for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
         const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
         double vo, to;
@@ -703,20 +724,16 @@ __global__ void __launch_bounds__(256) hvp_tile_kernel(HvpArgs a) {
             yt += w2 * tab[(size_t)TAB_DP(1 - s, rt) * nl + l];
           }
         }
-        sq_v += tab[(size_t)TAB_DQ(s, rv) * nl + l];
-        sq_t += tab[(size_t)TAB_DQ(s, rt) * nl + l];
-        sp_v += tab[(size_t)TAB_DP(s, rv) * nl + l];
-        sp_t += tab[(size_t)TAB_DP(s, rt) * nl + l];
       }
       const int gi = n.gn_of[i];
-      if (gi >= 0) {
+      if (gi >= 0) {  // own injections: the gradients dQ_i, dP_i w.r.t. (v_i, theta_i) are per-bus sums
         const double w = a.busw[i] * QD[(size_t)gi * C + c];
-        yv += w * sq_v;
-        yt += w * sq_t;
+        yv += w * a.busw[4 * nb + i];
+        yt += w * a.busw[5 * nb + i];
         if (i == n.ref) {
           const double w2 = a.busw[nb + i] * PD[c];
-          yv += w2 * sp_v;
-          yt += w2 * sp_t;
+          yv += w2 * a.busw[6 * nb + i];
+          yt += w2 * a.busw[7 * nb + i];
         }
       }
       if (n.type[i] == PQ) yv += a.busw[2 * nb + i] * vi;
@@ -842,6 +859,8 @@ void launch_hess_prep(opf_ctx* c, double sigma_f) {
                                                            c->omega, c->Pbus, c->pd, sigma_f, c->btab);
   c->launches++;
   bus_weight_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->omega, sigma_f, c->busw);
+  c->launches++;
+  bus_self_grad_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->btab, c->busw);
 }
 
 size_t hvp_stride(const opf_ctx* c, int C) {
@@ -868,7 +887,10 @@ static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int ti
   a.tile_step = tile_step;
   a.col0 = col0;
   a.col_end = col_end;
-  hvp_tile_kernel<C><<<grid, 256, 0, c->stream>>>(a);
+  if (c->hvp_threads == 512)
+    hvp_tile_kernel<C, 512><<<grid, 512, 0, c->stream>>>(a);
+  else
+    hvp_tile_kernel<C, 256><<<grid, 256, 0, c->stream>>>(a);
   c->launches++;
 }
 
@@ -905,7 +927,7 @@ static void launch_hvp_scratch_t(opf_ctx* c, double* H, double* scratch, int gri
   a.tile_step = 1;
   a.col0 = col0;
   a.col_end = col_end;
-  hvp_tile_kernel<C><<<grid, 256, 0, c->stream>>>(a);
+  hvp_tile_kernel<C, 256><<<grid, 256, 0, c->stream>>>(a);
   c->launches++;
 }
 
