@@ -219,6 +219,55 @@ opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_h
 opf_status opf_reduced_hessian_noalloc(opf_ctx* ctx, const opf_al_params* p,
                                        const opf_hess_opts* opts, double* H, opf_hess_info* info);
 
+/*
+ * Reduced-Newton step of the augmented-Lagrangian subproblem (Sec. IV-B,
+ * eq. ipm_kkt_reduced with the AL Hessian of eq. hessian_auglag, solved by the
+ * Schur complement of Prop. 3), one primal-dual barrier step on w = (u, s):
+ *   Sigma = Z_lo/(w - w_lo) + Z_hi/(w_hi - w);  grad psi = grad L_rho - mu/(w - w_lo) + mu/(w_hi - w)
+ *   S_uu = H(omega) + Sigma_u [+ delta I],  omega_i = rho sigma_i^2 Sigma_s,i / (rho sigma_i^2 + Sigma_s,i)
+ *          (H(omega) = opf_reduced_hessian with these weights, symmetrised)
+ *   S_uu d_u = -grad_u psi - J^T [rho D^2 (rho D^2 + Sigma_s)^{-1} grad_s psi]   (J = dc/du on g = 0;
+ *          the sign follows from eliminating d_s; the printed Prop. 3 has "+")
+ *   d_s = (rho D^2 + Sigma_s)^{-1} (-grad_s psi + rho D^2 J d_u),  D = diag(sigma_c)
+ *   dz_lo = mu/(w - w_lo) - z_lo - Sigma_lo d_w,  dz_hi = mu/(w_hi - w) - z_hi + Sigma_hi d_w
+ * S_uu is factorised by a device FP64 Cholesky; delta (inertia correction) takes
+ * 0, then 1e-8 * 10^k, k = 0 .. max_inertia - 1, until the factorisation succeeds.
+ * Step lengths: fraction to the boundary with tau = max(0.99, 1 - mu) for the
+ * primal and the dual variables; the power flow is re-solved at u + alpha_p d_u
+ * (warm start from x) and alpha_p halved until it converges, so the new iterate
+ * stays feasible.  Then u, s, x, and the duals are updated in place.
+ * Requires a converged opf_powerflow at st->u.  The first call allocates the
+ * step workspace of the context (two n_u x n_u matrices and vectors).
+ * Errors: OPF_ESTATE, OPF_EINVAL, OPF_ENOTPD (no delta made S_uu positive
+ * definite), OPF_ENOCONV (no trial point converged; the state is unchanged).
+ */
+typedef struct {
+  double *u, *s;            /* [n_u], [m] primal, updated in place */
+  double *zl_u, *zu_u;      /* [n_u] bound duals of u, updated in place (> 0) */
+  double *zl_s, *zu_s;      /* [m] bound duals of s, updated in place (> 0) */
+  const double *u_lo, *u_hi, *s_lo, *s_hi;  /* bounds, strictly around u and s */
+  double* x;                /* [n_x] power-flow state at u; replaced by the state at the new u */
+  double mu;                /* barrier parameter */
+} opf_al_state;
+
+typedef struct {
+  int block_k;        /* Hessian tile width (0 = 8) */
+  int max_halvings;   /* trial power flows allowed after the first (0 = 10) */
+  int max_inertia;    /* inertia-correction tries after delta = 0 (0 = 24) */
+} opf_step_opts;
+
+typedef struct {
+  double alpha_p, alpha_d, delta, du_inf, ds_inf;
+  int halvings, inertia_tries, pf_iterations;
+  float ms_hessian, ms_total;
+} opf_step_info;
+
+/* p supplies sigma_f, rho, sigma_c and y (its s and omega are ignored: s comes
+ * from st).  du_out [n_u] and ds_out [m] (device, optional) receive the step. */
+opf_status opf_al_step(opf_ctx* ctx, const opf_al_params* p, opf_al_state* st,
+                       const opf_step_opts* opts, opf_step_info* info, double* du_out,
+                       double* ds_out);
+
 /* Number of kernels this context has launched since it was created (host output). */
 opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);
 

@@ -64,6 +64,23 @@ class HessInfo(C.Structure):
                 ("ms_total", C.c_float), ("ms_hvp", C.c_float)]
 
 
+class AlState(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("s", C.c_void_p), ("zl_u", C.c_void_p), ("zu_u", C.c_void_p),
+                ("zl_s", C.c_void_p), ("zu_s", C.c_void_p), ("u_lo", C.c_void_p), ("u_hi", C.c_void_p),
+                ("s_lo", C.c_void_p), ("s_hi", C.c_void_p), ("x", C.c_void_p), ("mu", C.c_double)]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("block_k", C.c_int), ("max_halvings", C.c_int), ("max_inertia", C.c_int)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("alpha_p", C.c_double), ("alpha_d", C.c_double), ("delta", C.c_double),
+                ("du_inf", C.c_double), ("ds_inf", C.c_double), ("halvings", C.c_int),
+                ("inertia_tries", C.c_int), ("pf_iterations", C.c_int), ("ms_hessian", C.c_float),
+                ("ms_total", C.c_float)]
+
+
 class OPFError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -96,6 +113,8 @@ def lib():
         L.opf_symbolic_free.restype = None
         L.opf_reduced_hessian_noalloc.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts),
                                                   C.c_void_p, C.POINTER(HessInfo)]
+        L.opf_al_step.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(AlState), C.POINTER(StepOpts),
+                                  C.POINTER(StepInfo), C.c_void_p, C.c_void_p]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
@@ -292,3 +311,24 @@ class OPFContext:
             raise OPFError(st, "opf_reduced_hessian_noalloc")
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
                          ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+
+    def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0):
+        """One reduced-Newton step (Prop. 3).  `state`: dict of cuda float64 tensors u, s, zl_u,
+        zu_u, zl_s, zu_s, u_lo, u_hi, s_lo, s_hi, x and the float mu; u, s, the duals and x are
+        updated in place.  Returns (du, ds, info)."""
+        t = self.torch
+        self._sync_stream()
+        p, keep = self._al(dict(al, s=state["s"]))
+        for k in ("u", "s", "zl_u", "zu_u", "zl_s", "zu_s", "u_lo", "u_hi", "s_lo", "s_hi", "x"):
+            self._dev(state[k])
+        st = AlState(*[state[k].data_ptr() for k in ("u", "s", "zl_u", "zu_u", "zl_s", "zu_s", "u_lo", "u_hi",
+                                                      "s_lo", "s_hi", "x")], float(state["mu"]))
+        du = t.empty(self.nu, dtype=t.float64, device=self.device)
+        ds = t.empty(self.m, dtype=t.float64, device=self.device)
+        info = StepInfo()
+        rc = lib().opf_al_step(self.h, C.byref(p), C.byref(st),
+                               C.byref(StepOpts(int(block_k), int(max_halvings), int(max_inertia))),
+                               C.byref(info), _ptr(du), _ptr(ds))
+        if rc != 0:
+            raise OPFError(rc, "opf_al_step")
+        return du, ds, {k: getattr(info, k) for k, _ in StepInfo._fields_}

@@ -316,6 +316,7 @@ static void free_impl(opf_ctx* c) {
   if (c->h_flags) cudaFreeHost(c->h_flags);
   for (int k = 0; k < 4; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  free_step_work(c);
   if (c->lu_exec) cudaGraphExecDestroy(c->lu_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

@@ -11,6 +11,12 @@
 
 namespace opf {
 
+// Per-branch Hessian table rows (each row holds n_l doubles): 0..9 the packed
+// symmetric 4x4 second derivative in branch-local order (v_f, v_t, theta_f,
+// theta_t); 10+4s+k = dP of end s w.r.t. local variable k; 18+4s+k = dQ.
+#define TAB_DP(s, k) (10 + 4 * (s) + (k))
+#define TAB_DQ(s, k) (18 + 4 * (s) + (k))
+
 enum BusType { REF = 0, PV = 1, PQ = 2 };
 
 // Host-side network with index maps (eq. statecontrol).
@@ -74,6 +80,11 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
                         int col_end);
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
+// J^T w for the reduced constraint Jacobian: the adjoint gradient with first-order
+// weights w and no cost (sigma_f = 0); needs the flows of the current state.
+void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
+struct StepWork;
+void free_step_work(opf_ctx* c);
 
 }  // namespace opf
 
@@ -118,6 +129,7 @@ struct opf_ctx {
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];
   long long launches = 0;         // kernels launched by this context
+  opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t lu_exec = nullptr;
   long long lu_graph_kernels = 0;

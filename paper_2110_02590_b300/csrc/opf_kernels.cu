@@ -507,9 +507,6 @@ __host__ __device__ __forceinline__ int pk(int a, int b) {
   }
   return a * 4 - (a * (a - 1)) / 2 + (b - a);
 }
-// Table rows: 0..9 packed M; 10+4s+k = dP of side s; 18+4s+k = dQ of side s (k branch-local).
-#define TAB_DP(s, k) (10 + 4 * (s) + (k))
-#define TAB_DQ(s, k) (18 + 4 * (s) + (k))
 
 // Per branch: the 4x4 second derivative of l = F + lambda^T g restricted to the
 // branch (injection weights, line-flow penalty curvature and omega-weighted
@@ -839,6 +836,16 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
   dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, c->phid, c->Pbus,
                                                         c->pd, p->sigma_f, c->dFx, c->dFu);
   launch_solve1(c, c->dFx, c->lam, true, -1.0);
+}
+
+void launch_weighted_grad(opf_ctx* c, const double* w, double* out) {
+  const DevNet& n = c->dn;
+  c->launches++;
+  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, w, c->Pbus, c->pd, 0.0,
+                                                        c->dFx, c->dFu);
+  launch_solve1(c, c->dFx, c->lam, true, -1.0);
+  c->launches++;
+  grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->vbus, c->thbus, c->lam, c->dFu, out);
 }
 
 void launch_grad_u(opf_ctx* c, double* gu) {

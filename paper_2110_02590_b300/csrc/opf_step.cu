@@ -1,0 +1,617 @@
+// Reduced-Newton step of the augmented-Lagrangian subproblem (Prop. 3; entry
+// point opf_al_step, declared in include/opf.h with the full formulas).
+//
+// Device pieces: the barrier/Sigma/omega terms, the reduced Jacobian products
+// J^T v (weighted adjoint gradient) and J d (G_u d, one L/U solve, directional
+// derivatives of c), a blocked FP64 Cholesky of S_uu (32-wide diagonal blocks,
+// row-parallel triangular solves of the panel, 64x64-tiled symmetric rank-32
+// updates), blocked dense triangular solves, the slack and dual steps and the
+// fraction-to-the-boundary reductions.  The host drives the inertia correction
+// and the trial power flows.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "opf_internal.h"
+
+using namespace opf;
+
+namespace opf {
+
+struct StepWork {
+  int nu = 0, m = 0;
+  double *S = nullptr, *L = nullptr;           // n_u x n_u column-major
+  double *gu, *gs, *sig_u, *gpsi_u, *sig_s, *gpsi_s, *omega, *v, *r, *du, *ds, *Jtv, *Jdu;
+  double *b, *z, *ut, *xt, *pd, *qd;
+  double *dz;                                   // 2 n_u + 2 m: zl_u, zu_u, zl_s, zu_s steps
+  double* red;                                  // [2]: alpha_p, alpha_d (as ordered bits)
+  int* flag;
+  double* h_red;
+  int* h_flag;
+  void* block = nullptr;
+};
+
+void free_step_work(opf_ctx* c) {
+  if (!c->stepw) return;
+  StepWork* w = c->stepw;
+  if (w->block) cudaFree(w->block);
+  if (w->h_red) cudaFreeHost(w->h_red);
+  if (w->h_flag) cudaFreeHost(w->h_flag);
+  delete w;
+  c->stepw = nullptr;
+}
+
+}  // namespace opf
+
+namespace {
+
+constexpr int NB = 32;
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- Cholesky
+
+__global__ void chol_diag_kernel(double* A, int n, int k0, int kb, int* flag) {
+  if (*flag) return;
+  __shared__ double T[NB][NB + 1];
+  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+    const int i = t % kb, j = t / kb;
+    T[i][j] = A[(size_t)(k0 + j) * n + k0 + i];
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; j++) {
+    if (threadIdx.x == 0) {
+      double d = T[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        *flag = 1;
+        d = 1.0;
+      }
+      T[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double inv = 1.0 / T[j][j];
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) T[i][j] *= inv;
+    __syncthreads();
+    const int w = kb - j - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = j + 1 + t % w, cc = j + 1 + t / w;
+      if (cc <= i) T[i][cc] -= T[i][j] * T[cc][j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+    const int i = t % kb, j = t / kb;
+    if (i >= j) A[(size_t)(k0 + j) * n + k0 + i] = T[i][j];
+  }
+}
+
+// rows below the diagonal block: x L_kk^T = a
+__global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag) {
+  if (*flag) return;
+  __shared__ double T[NB][NB + 1];
+  __shared__ double inv[NB];
+  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+    const int i = t % kb, j = t / kb;
+    T[i][j] = A[(size_t)(k0 + j) * n + k0 + i];
+  }
+  __syncthreads();
+  if (threadIdx.x < kb) inv[threadIdx.x] = 1.0 / T[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; j++) x[j] = (j < kb) ? A[(size_t)(k0 + j) * n + i] : 0.0;
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    if (j < kb) {
+      double s = x[j];
+#pragma unroll
+      for (int t = 0; t < j; t++) s -= x[t] * T[j][t];
+      x[j] = s * inv[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; j++)
+    if (j < kb) A[(size_t)(k0 + j) * n + i] = x[j];
+}
+
+// trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one 64x64 tile per CTA (16x16 threads, 4x4 each)
+__global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag) {
+  if (*flag) return;
+  const int r0 = k0 + kb;
+  const int t = blockIdx.x;
+  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+  while (bi * (bi + 1) / 2 > t) bi--;
+  const int bj = t - bi * (bi + 1) / 2;
+  __shared__ double Pa[64][NB + 1], Pb[64][NB + 1];
+  for (int q = threadIdx.x; q < 64 * NB; q += blockDim.x) {
+    const int rr = q % 64, k = q / 64;
+    const int ga = r0 + bi * 64 + rr, gb = r0 + bj * 64 + rr;
+    Pa[rr][k] = (k < kb && ga < n) ? A[(size_t)(k0 + k) * n + ga] : 0.0;
+    Pb[rr][k] = (k < kb && gb < n) ? A[(size_t)(k0 + k) * n + gb] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  for (int k = 0; k < kb; k++) {
+    double a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      a[q] = Pa[ty * 4 + q][k];
+      b[q] = Pb[tx * 4 + q][k];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+  }
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int gi = r0 + bi * 64 + ty * 4 + p, gj = r0 + bj * 64 + tx * 4 + q;
+      if (gi < n && gj <= gi) A[(size_t)gj * n + gi] -= acc[p][q];
+    }
+}
+
+// ---------------------------------------------------------------- dense triangular solves
+
+// forward: L y = b on the diagonal block (one warp), then the rows below
+__global__ void tri_fwd_diag_kernel(const double* A, int n, int k0, int kb, double* b) {
+  const int t = threadIdx.x;
+  double bt = (t < kb) ? b[k0 + t] : 0.0;
+  for (int j = 0; j < kb; j++) {
+    const double yj = __shfl_sync(0xffffffffu, bt, j) / A[(size_t)(k0 + j) * n + k0 + j];
+    if (t == j) bt = yj;
+    else if (t > j && t < kb) bt -= A[(size_t)(k0 + j) * n + k0 + t] * yj;
+  }
+  if (t < kb) b[k0 + t] = bt;
+}
+
+__global__ void tri_fwd_gemv_kernel(const double* A, int n, int k0, int kb, double* b) {
+  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = b[i];
+  for (int j = 0; j < kb; j++) s -= A[(size_t)(k0 + j) * n + i] * b[k0 + j];
+  b[i] = s;
+}
+
+// backward: L^T x = y on the diagonal block, then the rows above
+__global__ void tri_bwd_diag_kernel(const double* A, int n, int k0, int kb, double* b) {
+  const int t = threadIdx.x;
+  double bt = (t < kb) ? b[k0 + t] : 0.0;
+  for (int j = kb - 1; j >= 0; j--) {
+    const double xj = __shfl_sync(0xffffffffu, bt, j) / A[(size_t)(k0 + j) * n + k0 + j];
+    if (t == j) bt = xj;
+    else if (t < j) bt -= A[(size_t)(k0 + t) * n + k0 + j] * xj;
+  }
+  if (t < kb) b[k0 + t] = bt;
+}
+
+__global__ void tri_bwd_gemv_kernel(const double* A, int n, int k0, int kb, double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k0) return;
+  double s = b[i];
+  for (int j = 0; j < kb; j++) s -= A[(size_t)i * n + k0 + j] * b[k0 + j];
+  b[i] = s;
+}
+
+// ---------------------------------------------------------------- step kernels
+
+__global__ void sym_diag_kernel(double* S, int n, const double* sig_u) {
+  const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || i < j) return;
+  if (i == j) {
+    S[(size_t)j * n + j] += sig_u[j];
+  } else {
+    const double a = 0.5 * (S[(size_t)j * n + i] + S[(size_t)i * n + j]);
+    S[(size_t)j * n + i] = a;
+    S[(size_t)i * n + j] = a;
+  }
+}
+
+__global__ void add_diag_kernel(double* L, const double* S, int n, double delta) {
+  const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  L[(size_t)j * n + i] = S[(size_t)j * n + i] + ((i == j) ? delta : 0.0);
+}
+
+// Sigma, grad psi, omega and v = rho D^2 (rho D^2 + Sigma_s)^{-1} grad_s psi
+__global__ void step_prep_kernel(int nu, int m, const double* u, const double* ulo, const double* uhi,
+                                 const double* zlu, const double* zuu, const double* s, const double* slo,
+                                 const double* shi, const double* zls, const double* zus, const double* gu,
+                                 const double* gs, const double* sigc, double rho, double mu, double* sig_u,
+                                 double* gpsi_u, double* sig_s, double* gpsi_s, double* omega, double* v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) {
+    const double dl = u[i] - ulo[i], dh = uhi[i] - u[i];
+    sig_u[i] = zlu[i] / dl + zuu[i] / dh;
+    gpsi_u[i] = gu[i] - mu / dl + mu / dh;
+  }
+  if (i < m) {
+    const double dl = s[i] - slo[i], dh = shi[i] - s[i];
+    const double sg = zls[i] / dl + zus[i] / dh;
+    const double gp = gs[i] - mu / dl + mu / dh;
+    const double rd2 = rho * sigc[i] * sigc[i];
+    sig_s[i] = sg;
+    gpsi_s[i] = gp;
+    omega[i] = rd2 * sg / (rd2 + sg);
+    v[i] = rd2 / (rd2 + sg) * gp;
+  }
+}
+
+__global__ void neg_sum_kernel(int n, const double* a, const double* b, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = -a[i] - b[i];
+}
+
+// G_u d into x order (rows P_i, Q_i), from the branch table at the current state
+__global__ void gu_times_kernel(DevNet n, const double* tab, const double* d, double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb || n.type[i] == REF) return;
+  const int nl = n.nl;
+  double ap = 0.0, aq = 0.0, selfp = 0.0;
+  for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
+    const int e = n.adj[q], l = e >> 1, s = e & 1;
+    const int o = s ? n.f[l] : n.t[l];
+    if (n.type[o] != PQ) {
+      const double dv = d[n.uv[o]];
+      ap += tab[(size_t)TAB_DP(s, 1 - s) * nl + l] * dv;
+      aq += tab[(size_t)TAB_DQ(s, 1 - s) * nl + l] * dv;
+    }
+    selfp += tab[(size_t)TAB_DP(s, s) * nl + l];
+  }
+  if (n.type[i] == PV) ap += selfp * d[n.uv[i]] - d[n.up[i]];
+  b[n.xth[i]] = ap;
+  if (n.type[i] == PQ) b[n.xv[i]] = aq;
+}
+
+__device__ __forceinline__ void dir_at(const DevNet& n, const double* z, const double* du, int b, double& vd,
+                                       double& td) {
+  vd = (n.type[b] == PQ) ? z[n.xv[b]] : du[n.uv[b]];
+  td = (n.type[b] == REF) ? 0.0 : z[n.xth[b]];
+}
+
+// J d = d_u c d + d_x c z: line flows per branch
+__global__ void jvp_branch_kernel(DevNet n, const double* tab, const double* flows, const double* z,
+                                  const double* du, double* jd) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n.nl) return;
+  const int nl = n.nl;
+  double d[4];
+  dir_at(n, z, du, n.f[l], d[0], d[2]);
+  dir_at(n, z, du, n.t[l], d[1], d[3]);
+  for (int s = 0; s < 2; s++) {
+    double pdot = 0.0, qdot = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      pdot += tab[(size_t)TAB_DP(s, k) * nl + l] * d[k];
+      qdot += tab[(size_t)TAB_DQ(s, k) * nl + l] * d[k];
+    }
+    jd[s * nl + l] = 2.0 * (flows[(2 * s) * nl + l] * pdot + flows[(2 * s + 1) * nl + l] * qdot);
+  }
+}
+
+// J d: voltage, slack P/Q and PV Q rows per bus
+__global__ void jvp_bus_kernel(DevNet n, const double* tab, const double* z, const double* du, double* jd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n.nb) return;
+  const int nl = n.nl, o_v = 2 * nl, o_r = 2 * nl + n.npq;
+  if (n.type[i] == PQ) {
+    jd[o_v + n.pqpos[i]] = z[n.xv[i]];
+    return;
+  }
+  double pdot = 0.0, qdot = 0.0;
+  for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
+    const int e = n.adj[q], l = e >> 1, s = e & 1;
+    double d[4];
+    dir_at(n, z, du, n.f[l], d[0], d[2]);
+    dir_at(n, z, du, n.t[l], d[1], d[3]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      pdot += tab[(size_t)TAB_DP(s, k) * nl + l] * d[k];
+      qdot += tab[(size_t)TAB_DQ(s, k) * nl + l] * d[k];
+    }
+  }
+  if (n.type[i] == REF) {
+    jd[o_r] = pdot;
+    jd[o_r + 1] = qdot;
+  } else {
+    jd[o_r + 2 + n.pvpos[i]] = qdot;
+  }
+}
+
+__device__ __forceinline__ void atomic_min_pos(double* a, double v) {
+  atomicMin(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// d_s, dual steps and the fraction-to-the-boundary step lengths (reduced into red[0..1])
+__global__ void step_finish_kernel(int nu, int m, const double* u, const double* du, const double* ulo,
+                                   const double* uhi, const double* zlu, const double* zuu, const double* s,
+                                   const double* slo, const double* shi, const double* zls, const double* zus,
+                                   const double* gpsi_s, const double* sig_s, const double* jdu,
+                                   const double* sigc, double rho, double mu, double tau, double* ds,
+                                   double* dz, double* red) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double ap = 1.0, ad = 1.0;
+  if (i < nu) {
+    const double dl = u[i] - ulo[i], dh = uhi[i] - u[i], d = du[i];
+    const double dzl = mu / dl - zlu[i] - zlu[i] / dl * d;
+    const double dzh = mu / dh - zuu[i] + zuu[i] / dh * d;
+    dz[i] = dzl;
+    dz[nu + i] = dzh;
+    if (d < 0) ap = fmin(ap, -tau * dl / d);
+    if (d > 0) ap = fmin(ap, tau * dh / d);
+    if (dzl < 0) ad = fmin(ad, -tau * zlu[i] / dzl);
+    if (dzh < 0) ad = fmin(ad, -tau * zuu[i] / dzh);
+  }
+  if (i < m) {
+    const double rd2 = rho * sigc[i] * sigc[i];
+    const double d = (-gpsi_s[i] + rd2 * jdu[i]) / (rd2 + sig_s[i]);
+    ds[i] = d;
+    const double dl = s[i] - slo[i], dh = shi[i] - s[i];
+    const double dzl = mu / dl - zls[i] - zls[i] / dl * d;
+    const double dzh = mu / dh - zus[i] + zus[i] / dh * d;
+    dz[2 * nu + i] = dzl;
+    dz[2 * nu + m + i] = dzh;
+    if (d < 0) ap = fmin(ap, -tau * dl / d);
+    if (d > 0) ap = fmin(ap, tau * dh / d);
+    if (dzl < 0) ad = fmin(ad, -tau * zls[i] / dzl);
+    if (dzh < 0) ad = fmin(ad, -tau * zus[i] / dzh);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    ap = fmin(ap, __shfl_down_sync(0xffffffffu, ap, off));
+    ad = fmin(ad, __shfl_down_sync(0xffffffffu, ad, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_min_pos(&red[0], ap);
+    atomic_min_pos(&red[1], ad);
+  }
+}
+
+__global__ void axpy2_kernel(int n, const double* x, const double* d, double a, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] + a * d[i];
+}
+
+__global__ void update_kernel(int nu, int m, double* u, const double* du, double* s, const double* ds,
+                              double* zlu, double* zuu, double* zls, double* zus, const double* dz, double ap,
+                              double ad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) {
+    u[i] += ap * du[i];
+    zlu[i] += ad * dz[i];
+    zuu[i] += ad * dz[nu + i];
+  }
+  if (i < m) {
+    s[i] += ap * ds[i];
+    zls[i] += ad * dz[2 * nu + i];
+    zus[i] += ad * dz[2 * nu + m + i];
+  }
+}
+
+#define SCK(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+      return OPF_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+opf_status alloc_step(opf_ctx* c) {
+  if (c->stepw) return OPF_OK;
+  const int nu = c->h.nu, m = c->h.m, nx = c->h.nx, nb = c->h.nb;
+  StepWork* w = new StepWork();
+  w->nu = nu;
+  w->m = m;
+  const size_t sizes[] = {(size_t)nu * nu, (size_t)nu * nu, (size_t)nu, (size_t)m, (size_t)nu, (size_t)nu,
+                          (size_t)m, (size_t)m, (size_t)m, (size_t)m, (size_t)nu, (size_t)nu, (size_t)m,
+                          (size_t)nu, (size_t)m, (size_t)nx, (size_t)nx, (size_t)nu, (size_t)nx, (size_t)nb,
+                          (size_t)nb, 2 * (size_t)nu + 2 * (size_t)m, 2};
+  double** ptrs[] = {&w->S, &w->L, &w->gu, &w->gs, &w->sig_u, &w->gpsi_u, &w->sig_s, &w->gpsi_s, &w->omega,
+                     &w->v, &w->r, &w->du, &w->ds, &w->Jtv, &w->Jdu, &w->b, &w->z, &w->ut, &w->xt,
+                     &w->pd, &w->qd, &w->dz, &w->red};
+  const int np = sizeof(sizes) / sizeof(sizes[0]);
+  size_t total = 0;
+  for (int k = 0; k < np; k++) total += (sizes[k] + 31) & ~(size_t)31;
+  total += 32;  // flag
+  if (cudaMalloc(&w->block, total * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete w;
+    set_last_error("cannot allocate the reduced-Newton step workspace");
+    return OPF_ENOMEM;
+  }
+  double* p = static_cast<double*>(w->block);
+  for (int k = 0; k < np; k++) {
+    *ptrs[k] = p;
+    p += (sizes[k] + 31) & ~(size_t)31;
+  }
+  w->flag = reinterpret_cast<int*>(p);
+  if (cudaMallocHost(&w->h_red, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&w->h_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->stepw = w;
+    free_step_work(c);
+    set_last_error("cannot allocate pinned step buffers");
+    return OPF_ENOMEM;
+  }
+  c->stepw = w;
+  return OPF_OK;
+}
+
+void launch_cholesky(opf_ctx* c, double* A, int n, int* flag) {
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    chol_diag_kernel<<<1, 256, 0, c->stream>>>(A, n, k0, kb, flag);
+    c->launches++;
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      chol_trsm_kernel<<<nblk(rest, 128), 128, 0, c->stream>>>(A, n, k0, kb, flag);
+      const int nt = nblk(rest, 64);
+      chol_syrk_kernel<<<nt * (nt + 1) / 2, 256, 0, c->stream>>>(A, n, k0, kb, flag);
+      c->launches += 2;
+    }
+  }
+}
+
+void launch_chol_solve(opf_ctx* c, const double* A, int n, double* b) {
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    tri_fwd_diag_kernel<<<1, 32, 0, c->stream>>>(A, n, k0, kb, b);
+    c->launches++;
+    if (n - k0 - kb > 0) {
+      tri_fwd_gemv_kernel<<<nblk(n - k0 - kb, 256), 256, 0, c->stream>>>(A, n, k0, kb, b);
+      c->launches++;
+    }
+  }
+  for (int k0 = ((n - 1) / NB) * NB; k0 >= 0; k0 -= NB) {
+    const int kb = std::min(NB, n - k0);
+    tri_bwd_diag_kernel<<<1, 32, 0, c->stream>>>(A, n, k0, kb, b);
+    c->launches++;
+    if (k0 > 0) {
+      tri_bwd_gemv_kernel<<<nblk(k0, 256), 256, 0, c->stream>>>(A, n, k0, kb, b);
+      c->launches++;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_state* st,
+                                  const opf_step_opts* o, opf_step_info* info, double* du_out,
+                                  double* ds_out) {
+  if (!c || !p || !st) {
+    set_last_error("ctx, params and state are required");
+    return OPF_EINVAL;
+  }
+  if (!c->have_state) {
+    set_last_error("no converged power flow on this context");
+    return OPF_ESTATE;
+  }
+  if (!p->sigma_c || !p->y || !st->u || !st->s || !st->zl_u || !st->zu_u || !st->zl_s || !st->zu_s ||
+      !st->u_lo || !st->u_hi || !st->s_lo || !st->s_hi || !st->x || !(st->mu >= 0.0) || !(p->rho > 0.0)) {
+    set_last_error("opf_al_step needs every state array, mu >= 0 and rho > 0");
+    return OPF_EINVAL;
+  }
+  opf_status rc = alloc_step(c);
+  if (rc) return rc;
+  StepWork* w = c->stepw;
+  const int nu = c->h.nu, m = c->h.m, nx = c->h.nx, nb = c->h.nb;
+  const int block_k = (o && o->block_k) ? o->block_k : 8;
+  const int max_halvings = (o && o->max_halvings) ? o->max_halvings : 10;
+  const int max_inertia = (o && o->max_inertia) ? o->max_inertia : 24;
+  cudaStream_t stream = c->stream;
+  cudaEvent_t e0, e1;
+  SCK(cudaEventCreate(&e0));
+  SCK(cudaEventCreate(&e1));
+  SCK(cudaEventRecord(e0, stream));
+  // gradient at (u, s): grad_u, grad_s = -phi'
+  opf_al_params ps = *p;
+  ps.s = st->s;
+  ps.omega = nullptr;
+  rc = opf_reduced_gradient(c, &ps, nullptr, w->gu, w->gs, nullptr, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  step_prep_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
+      nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
+      w->gu, w->gs, p->sigma_c, p->rho, st->mu, w->sig_u, w->gpsi_u, w->sig_s, w->gpsi_s, w->omega, w->v);
+  c->launches++;
+  // S_uu = H(omega) + Sigma_u (symmetrised)
+  ps.omega = w->omega;
+  opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0};
+  opf_hess_info hi;
+  rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
+  if (rc) return rc;
+  sym_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->S, nu, w->sig_u);
+  c->launches++;
+  // r = -grad_u psi - J^T v  (state quantities of this point are still in the context)
+  launch_weighted_grad(c, w->v, w->Jtv);
+  neg_sum_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, w->Jtv, w->r);
+  c->launches++;
+  // Cholesky with inertia correction
+  double delta = 0.0;
+  int tries = 0;
+  for (;; tries++) {
+    add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
+    SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
+    c->launches++;
+    launch_cholesky(c, w->L, nu, w->flag);
+    SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    if (!*w->h_flag) break;
+    if (tries >= max_inertia) {
+      set_last_error("S_uu not positive definite after the inertia corrections");
+      return OPF_ENOTPD;
+    }
+    delta = 1e-8 * std::pow(10.0, (double)tries);
+  }
+  SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  launch_chol_solve(c, w->L, nu, w->du);
+  // J d_u: z = -G_x^{-1} G_u d_u, then the directional derivatives of c
+  gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
+  c->launches++;
+  launch_solve1(c, w->b, w->z, false, -1.0);
+  jvp_branch_kernel<<<nblk(c->dn.nl, 256), 256, 0, stream>>>(c->dn, c->btab, c->flows, w->z, w->du, w->Jdu);
+  jvp_bus_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->z, w->du, w->Jdu);
+  c->launches += 2;
+  // d_s, dual steps, fraction to the boundary
+  const double tau = std::max(0.99, 1.0 - st->mu);
+  const double one = 1.0;
+  SCK(cudaMemcpyAsync(w->red, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  SCK(cudaMemcpyAsync(w->red + 1, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  step_finish_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
+      nu, m, st->u, w->du, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s,
+      st->zu_s, w->gpsi_s, w->sig_s, w->Jdu, p->sigma_c, p->rho, st->mu, tau, w->ds, w->dz, w->red);
+  c->launches++;
+  SCK(cudaMemcpyAsync(w->h_red, w->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  SCK(cudaStreamSynchronize(stream));
+  SCK(cudaGetLastError());
+  double ap = w->h_red[0];
+  const double ad = w->h_red[1];
+  SCK(cudaEventRecord(e1, stream));
+  // trial power flows with halving (loads kept from the current state)
+  SCK(cudaMemcpyAsync(w->pd, c->pd, nb * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaMemcpyAsync(w->qd, c->qd, nb * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  int halvings = 0;
+  opf_pf_info pfi = {0, 0.0, 0.0};
+  for (;;) {
+    axpy2_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, st->u, w->du, ap, w->ut);
+    c->launches++;
+    SCK(cudaMemcpyAsync(w->xt, st->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    opf_status prc = opf_powerflow(c, w->ut, w->pd, w->qd, w->xt, nullptr, &pfi);
+    if (prc == OPF_OK) break;
+    if (prc != OPF_ENOCONV && prc != OPF_ESINGULAR) return prc;
+    if (halvings >= max_halvings) {
+      set_last_error("no trial control with a converged power flow after the halvings");
+      return OPF_ENOCONV;
+    }
+    ap *= 0.5;
+    halvings++;
+  }
+  if (du_out) SCK(cudaMemcpyAsync(du_out, w->du, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  if (ds_out) SCK(cudaMemcpyAsync(ds_out, w->ds, m * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  update_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(nu, m, st->u, w->du, st->s, w->ds, st->zl_u,
+                                                                st->zu_u, st->zl_s, st->zu_s, w->dz, ap, ad);
+  c->launches++;
+  SCK(cudaMemcpyAsync(st->x, w->xt, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaStreamSynchronize(stream));
+  SCK(cudaGetLastError());
+  if (info) {
+    info->alpha_p = ap;
+    info->alpha_d = ad;
+    info->delta = delta;
+    info->halvings = halvings;
+    info->inertia_tries = tries;
+    info->pf_iterations = pfi.iterations;
+    info->ms_hessian = hi.ms_total;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    info->ms_total = ms;
+    info->du_inf = info->ds_inf = 0.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return OPF_OK;
+}

@@ -1,0 +1,70 @@
+"""GPU parity of the reduced-Newton step (Prop. 3) against the oracle's step.
+
+Tolerance: the step solves S_uu d_u = r with S_uu from the Hessian (parity
+~1e-12 relative between the two sides) and cond(S_uu + delta I) below ~1e4 at
+these points, so d_u agrees to ~1e-8; the test uses 1e-6 relative (infinity
+norm).  The inertia correction, step lengths and halvings must coincide.
+"""
+import numpy as np
+import pytest
+
+from oracle import al_step as A
+from paper_2110_02590_b300 import synth
+from tests.test_oracle_al_step import setup
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2110_02590_b300 as P  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+STEP_TOL = 1e-6
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name,mu", [("tiny30", 0.1), ("medium1400", 0.1), ("medium1400", 1e-3)])
+def test_al_step_parity(name, mu):
+    net = synth.workload(name)
+    on, x, u, al, st = setup(net, mu=mu)
+    ref = A.al_step(on, x, u, al["s"], st, al)
+    ctx = P.OPFContext(net)
+    xg, info = ctx.powerflow(dev(u))
+    state = {k: dev(v) for k, v in st.items() if k != "mu"}
+    state.update(u=dev(u), s=dev(al["s"]), x=xg, mu=mu)
+    al_dev = {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+    du, ds, inf = ctx.al_step(al_dev, state)
+    assert inf["delta"] == ref["delta"]
+    assert rel(du.cpu().numpy(), ref["du"]) < STEP_TOL
+    assert rel(ds.cpu().numpy(), ref["ds"]) < STEP_TOL
+    assert abs(inf["alpha_p"] - ref["alpha_p"]) <= STEP_TOL * ref["alpha_p"]
+    assert abs(inf["alpha_d"] - ref["alpha_d"]) <= STEP_TOL * ref["alpha_d"]
+    assert inf["halvings"] == ref["halvings"]
+    assert rel(state["u"].cpu().numpy(), ref["u"]) < 1e-9
+    assert rel(state["s"].cpu().numpy(), ref["s"]) < 1e-9
+    for k, v in ref["duals"].items():
+        assert rel(state[k].cpu().numpy(), v) < 1e-6, k
+    assert np.abs(state["x"].cpu().numpy() - ref["x"]).max() < 1e-8
+    # the new iterate is feasible and the context holds its power flow
+    g = ctx.reduced_gradient(dict(al_dev, s=state["s"]))
+    assert torch.isfinite(g["grad_u"]).all()
+
+
+def test_al_step_requires_state():
+    net = synth.workload("tiny30")
+    ctx = P.OPFContext(net)
+    on, x, u, al, st = setup(net)
+    state = {k: dev(v) for k, v in st.items() if k != "mu"}
+    state.update(u=dev(u), s=dev(al["s"]), x=dev(x), mu=0.1)
+    with pytest.raises(P.OPFError) as ei:
+        ctx.al_step({k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}, state)
+    assert ei.value.status == 7
