@@ -195,6 +195,25 @@ opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_h
                                double* H, opf_hess_info* info);
 
 /*
+ * opf_reduced_hessian_batched: the dense reduced Hessians of n contexts
+ * (snapshots: the same or different networks, each at its own converged power
+ * flow) in one persistent launch.  Per context the first-order quantities and
+ * branch tables are evaluated as in opf_reduced_hessian; then one kernel walks
+ * a queue of (context, column tile) pairs, tiles of the largest networks first
+ * (longest processing time first), each CTA pulling the next pair when it
+ * finishes one (the batched multi-right-hand-side HVPs of Sec. V-A across
+ * snapshots).  params[k] and H[k] (n_u(k) x n_u(k) column-major) belong to
+ * ctxs[k].  Everything runs on ctxs[0]'s stream; all contexts must live on
+ * the same device.  opts: block_k and grid (0 = as many CTAs as fit); plain,
+ * columns and threads are ignored.  The workspace is held by ctxs[0] (grown on
+ * demand).  Errors: OPF_EINVAL, OPF_ESTATE (a context without a converged
+ * power flow).
+ */
+opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al_params* params,
+                                       double* const* H, const opf_hess_opts* opts,
+                                       opf_hess_info* info);
+
+/*
  * opf_reduced_hessian_noalloc: the same reduced Hessian as opf_reduced_hessian
  * (same kernels, same options and outputs), for callers that must not allocate
  * device memory during the call -- a real-time tracking loop that cannot stall

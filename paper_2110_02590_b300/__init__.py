@@ -115,6 +115,8 @@ def lib():
                                                   C.c_void_p, C.POINTER(HessInfo)]
         L.opf_al_step.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(AlState), C.POINTER(StepOpts),
                                   C.POINTER(StepInfo), C.c_void_p, C.c_void_p]
+        L.opf_reduced_hessian_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AlParams),
+                                                  C.POINTER(C.c_void_p), C.POINTER(HessOpts), C.POINTER(HessInfo)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
@@ -171,6 +173,35 @@ def symbolic_analyze(net) -> dict:
         return out
     finally:
         L.opf_symbolic_free(h)
+
+
+def reduced_hessian_batched(ctxs, als, block_k=8, grid=0, outs=None):
+    """Hessians of several contexts (each at its converged power flow) in one persistent launch.
+
+    Returns ([H_k], info); H_k is the n_u(k) x n_u(k) Hessian of ctxs[k] with the AL inputs als[k].
+    """
+    import torch
+    n = len(ctxs)
+    for c in ctxs:
+        c._sync_stream()
+    ctxs[0]._sync_stream()
+    params, keep = [], []
+    for c, al in zip(ctxs, als):
+        p, kp = c._al(al)
+        params.append(p)
+        keep.append(kp)
+    if outs is None:
+        outs = [torch.empty((c.nu, c.nu), dtype=torch.float64, device=c.device) for c in ctxs]
+    hs = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    ps = (AlParams * n)(*params)
+    Hp = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    info = HessInfo()
+    st = lib().opf_reduced_hessian_batched(hs, n, ps, Hp, C.byref(HessOpts(int(block_k), int(grid), 0, 0, 0, 0)),
+                                           C.byref(info))
+    if st != 0:
+        raise OPFError(st, "opf_reduced_hessian_batched")
+    return [o.T for o in outs], dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles,
+                                     launches=info.launches, ms_total=info.ms_total, ms_hvp=info.ms_hvp)
 
 
 def _ptr(t):

@@ -317,6 +317,7 @@ static void free_impl(opf_ctx* c) {
   for (int k = 0; k < 4; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   free_step_work(c);
+  if (c->batch_buf) cudaFree(c->batch_buf);
   if (c->lu_exec) cudaGraphExecDestroy(c->lu_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -574,6 +575,86 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
     info->launches = launches;
     cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
+  }
+  return OPF_OK;
+}
+
+opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al_params* params,
+                                       double* const* H, const opf_hess_opts* o, opf_hess_info* info) {
+  if (!ctxs || n < 1 || !params || !H) FAIL(OPF_EINVAL, "ctxs, params and H are required, n >= 1");
+  opf_ctx* c0 = ctxs[0];
+  if (!c0) FAIL(OPF_EINVAL, "null context");
+  const int C = (o && o->block_k) ? o->block_k : 8;
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
+    FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
+  std::vector<int> order(n);
+  size_t stride = 0;
+  for (int k = 0; k < n; k++) {
+    opf_ctx* c = ctxs[k];
+    if (!c || !H[k]) FAIL(OPF_EINVAL, "null context or Hessian pointer in the batch");
+    if (c->device != c0->device) FAIL(OPF_EINVAL, "all contexts of a batch must be on one device");
+    if (!c->have_state) FAIL(OPF_ESTATE, "a context of the batch has no converged power flow");
+    TRY(check_al(c, &params[k]));
+    stride = std::max(stride, hvp_stride(c, C));
+    order[k] = k;
+  }
+  cudaStream_t st = c0->stream;
+  CK(cudaEventRecord(c0->ev[0], st));
+  // first-order quantities and branch tables per context, on the batch stream
+  std::vector<HvpArgs> args(n);
+  for (int k = 0; k < n; k++) {
+    opf_ctx* c = ctxs[k];
+    cudaStream_t keep = c->stream;
+    c->stream = st;
+    launch_first_order(c, &params[k], nullptr);
+    launch_hess_prep(c, params[k].sigma_f);
+    c->stream = keep;
+    args[k] = make_hvp_args(c, C, H[k], 0, c->h.nu);
+  }
+  // tile queue: contexts by decreasing factor size (longest processing time first)
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)ctxs[a]->dn.nnz * ctxs[a]->h.nu > (long long)ctxs[b]->dn.nnz * ctxs[b]->h.nu;
+  });
+  std::vector<int2> tiles;
+  for (int k : order)
+    for (int t = 0; t < args[k].ntiles; t++) tiles.push_back(make_int2(k, t));
+  const int ntot = (int)tiles.size();
+  const size_t bytes = n * sizeof(HvpArgs) + ntot * sizeof(int2) + 256;
+  if (c0->batch_bytes < bytes) {
+    CK(cudaStreamSynchronize(st));
+    if (c0->batch_buf) cudaFree(c0->batch_buf);
+    c0->batch_buf = nullptr;
+    c0->batch_bytes = 0;
+    if (cudaMalloc(&c0->batch_buf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      FAIL(OPF_ENOMEM, "cannot allocate the batch tables");
+    }
+    c0->batch_bytes = bytes;
+  }
+  char* base = static_cast<char*>(c0->batch_buf);
+  HvpArgs* d_args = reinterpret_cast<HvpArgs*>(base);
+  int2* d_tiles = reinterpret_cast<int2*>(base + n * sizeof(HvpArgs));
+  int* d_counter = reinterpret_cast<int*>(base + n * sizeof(HvpArgs) + ntot * sizeof(int2));
+  CK(cudaMemcpyAsync(d_args, args.data(), n * sizeof(HvpArgs), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_tiles, tiles.data(), ntot * sizeof(int2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
+  const int occ = std::max(1, hvp_batch_occupancy(C));
+  int grid = (o && o->grid > 0) ? o->grid : occ * c0->sm_count;
+  grid = std::max(1, std::min(grid, ntot));
+  TRY(ensure_scratch(c0, stride * (size_t)grid));
+  CK(cudaEventRecord(c0->ev[1], st));
+  launch_hvp_batch(st, C, d_args, d_tiles, ntot, d_counter, c0->scratch, stride, grid);
+  c0->launches++;
+  CK(cudaEventRecord(c0->ev[2], st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  if (info) {
+    info->block_k = C;
+    info->grid = grid;
+    info->tiles = ntot;
+    info->launches = 1;
+    cudaEventElapsedTime(&info->ms_total, c0->ev[0], c0->ev[2]);
+    cudaEventElapsedTime(&info->ms_hvp, c0->ev[1], c0->ev[2]);
   }
   return OPF_OK;
 }

@@ -63,6 +63,18 @@ struct DevNet {
   const int* slot_adj;             // [4 * 2 nl]
 };
 
+// Arguments of the HVP tile kernels (one network, one Hessian).
+struct HvpArgs {
+  DevNet n;
+  const double *LU, *T, *invdiag, *tab, *busw;
+  const int* ubus;  // bus of each control
+  double* H;
+  double* scratch;
+  size_t stride;    // doubles of scratch per CTA
+  int ntiles, first_tile, tile_step;
+  int col0, col_end;  // columns computed: col0 .. col_end - 1
+};
+
 // kernel launchers (opf_kernels.cu)
 void launch_unpack(opf_ctx* c, const double* x, const double* u);
 void launch_pf_eval(opf_ctx* c);
@@ -80,6 +92,10 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
                         int col_end);
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
+HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end);
+int hvp_batch_occupancy(int C);  // resident CTAs per SM of the batched tile kernel
+bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
+                      double* scratch, size_t stride, int grid);
 // J^T w for the reduced constraint Jacobian: the adjoint gradient with first-order
 // weights w and no cost (sigma_f = 0); needs the flows of the current state.
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
@@ -130,6 +146,8 @@ struct opf_ctx {
   cudaEvent_t ev[4];
   long long launches = 0;         // kernels launched by this context
   opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
+  void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
+  size_t batch_bytes = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t lu_exec = nullptr;
   long long lu_graph_kernels = 0;

@@ -617,16 +617,7 @@ __global__ void bus_self_grad_kernel(DevNet n, const double* tab, double* w) {
 
 // ------------------------------------------------------------ HVP tiles
 
-struct HvpArgs {
-  DevNet n;
-  const double *LU, *T, *invdiag, *tab, *busw;
-  const int* ubus;  // bus of each control
-  double* H;
-  double* scratch;
-  size_t stride;    // doubles of scratch per CTA
-  int ntiles, first_tile, tile_step;
-  int col0, col_end;  // columns computed: col0 .. col_end - 1
-};
+
 
 template <int C>
 __device__ __forceinline__ void direction(const DevNet& n, const double* Z, int b, int c, int j,
@@ -635,19 +626,18 @@ __device__ __forceinline__ void direction(const DevNet& n, const double* Z, int 
   td = (n.type[b] == REF) ? 0.0 : Z[(size_t)n.pth[b] * C + c];
 }
 
-// One CTA = one tile of C Hessian columns at a time: B = -G_u W, Z = G_x^{-1} B,
+// One tile of C Hessian columns on one CTA: B = -G_u W, Z = G_x^{-1} B,
 // second-order terms, Psi = G_x^{-T} R, H[:, tile] = T + G_u^T Psi (Prop. 2).
-template <int C, int NT>
-__global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
+// Z is the CTA's workspace (2 n_x C + n_ctrl C + C doubles).
+template <int C>
+__device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) {
   const DevNet& n = a.n;
   const int nl = n.nl, nb = n.nb, nu = n.nu, jend = a.col_end;
-  double* Z = a.scratch + a.stride * blockIdx.x;
   double* R = Z + (size_t)n.nx * C;
   double* QD = R + (size_t)n.nx * C;
   double* PD = QD + (size_t)n.ngn * C;
   const double* tab = a.tab;
-  for (int tile = a.first_tile + blockIdx.x * a.tile_step; tile < a.ntiles;
-       tile += gridDim.x * a.tile_step) {
+  {
     const int j0 = a.col0 + tile * C;
     // (0) right-hand side B = -G_u W, W = unit directions j0 .. j0 + C - 1
     for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
@@ -767,6 +757,37 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
       Hc[n.uv[k]] += gv;
     }
     __syncthreads();
+  }
+}
+
+template <int C, int NT>
+__global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
+  double* Z = a.scratch + a.stride * blockIdx.x;
+  for (int tile = a.first_tile + blockIdx.x * a.tile_step; tile < a.ntiles; tile += gridDim.x * a.tile_step)
+    hvp_tile<C>(a, Z, tile);
+}
+
+// Persistent batched form: CTAs pull (context, tile) pairs from a queue (ordered
+// largest network first) and run the same tile body with that context's
+// arguments staged in shared memory.  No CTA waits on another.
+template <int C>
+__global__ void __launch_bounds__(256) hvp_batch_kernel(const HvpArgs* __restrict__ args,
+                                                        const int2* __restrict__ tiles, int ntot,
+                                                        int* counter, double* scratch, size_t stride) {
+  __shared__ HvpArgs sa;
+  __shared__ int s_tile;
+  double* Z = scratch + stride * blockIdx.x;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntot) break;
+    const int2 ct = tiles[t];
+    const int* src = reinterpret_cast<const int*>(args + ct.x);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int k = threadIdx.x; k < (int)(sizeof(HvpArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    hvp_tile<C>(sa, Z, ct.y);
   }
 }
 
@@ -910,6 +931,58 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
     case 8: launch_hvp_t<8>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
     case 16: launch_hvp_t<16>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
     case 32: launch_hvp_t<32>(c, H, grid, first_tile, tile_step, ntiles, col0, col_end); return true;
+    default: return false;
+  }
+}
+
+HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end) {
+  HvpArgs a;
+  a.n = c->dn;
+  a.LU = c->LU;
+  a.T = c->T;
+  a.invdiag = c->invdiag;
+  a.tab = c->btab;
+  a.busw = c->busw;
+  a.ubus = c->ubus;
+  a.H = H;
+  a.scratch = nullptr;
+  a.stride = hvp_stride(c, C);
+  a.ntiles = (col_end - col0 + C - 1) / C;
+  a.first_tile = 0;
+  a.tile_step = 1;
+  a.col0 = col0;
+  a.col_end = col_end;
+  return a;
+}
+
+template <int C>
+static int batch_occ() {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_batch_kernel<C>, 256, 0);
+  return occ;
+}
+
+int hvp_batch_occupancy(int C) {
+  switch (C) {
+    case 1: return batch_occ<1>();
+    case 2: return batch_occ<2>();
+    case 4: return batch_occ<4>();
+    case 8: return batch_occ<8>();
+    case 16: return batch_occ<16>();
+    case 32: return batch_occ<32>();
+    default: return 0;
+  }
+}
+
+bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
+                      double* scratch, size_t stride, int grid) {
+  switch (C) {
+    case 1: hvp_batch_kernel<1><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 2: hvp_batch_kernel<2><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 4: hvp_batch_kernel<4><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 8: hvp_batch_kernel<8><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 16: hvp_batch_kernel<16><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 32: hvp_batch_kernel<32><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
     default: return false;
   }
 }
