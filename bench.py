@@ -1,10 +1,13 @@
 """Benchmark: HVPs/s and ms per full reduced Hessian on the 9.2k-bus synthetic grid (FP64).
 
-One step = one pass of the hot path on a new load snapshot (AR(1) load
-trajectory): Newton-Raphson power flow warm-started from the previous state
-(g, G_x, LU refactorisation, sweeps), reduced gradient (adjoint), and the
-full dense reduced Hessian from batched adjoint-adjoint HVPs.  value =
-Hessian columns (HVPs) per second of step time, summed over ranks.
+One step = one real-time tracking update on a new load snapshot (AR(1) load
+trajectory), i.e. one pass of the whole hot path: Newton-Raphson power flow
+at the new loads warm-started from the previous state (g, G_x, LU
+refactorisation, sweeps), then one reduced-Newton step of the AL subproblem
+(reduced gradient, full reduced Hessian at the Schur weights from batched
+adjoint-adjoint HVPs, device Cholesky, reduced Jacobian products, power flow
+at the trial control).  value = Hessian columns (HVPs) per second of step
+time, summed over ranks.  The Hessian alone is timed and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -50,11 +53,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block-k", type=int, default=8)
     ap.add_argument("--plain-cols", type=int, default=64)
-    ap.add_argument("--cpu-cols", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -69,7 +71,7 @@ def workload_config(nu, extra=None):
     cfg = {"workload": "9.2k-bus synthetic grid (9,200 buses, 1,450 generators, 16,000 branches, "
                        "20% transformers), AR(1) load snapshots",
            "n_bus": 9200, "n_u": nu, "n_x": 16949, "m": 41201,
-           "step": "power flow + reduced gradient + full reduced Hessian",
+           "step": "tracking update: power flow at new loads + reduced-Newton step",
            "l2": "flushed between timed steps (256 MB write)"}
     if extra:
         cfg.update(extra)
@@ -78,70 +80,73 @@ def workload_config(nu, extra=None):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_step(on, u, al, x0, pd, qd, cols):
-    """One step of the oracle: power flow, gradient, `cols` Hessian columns.  Returns timings."""
-    t0 = time.perf_counter()
-    x, info = on.powerflow(u, pd=pd, qd=qd, x0=x0)
-    t1 = time.perf_counter()
-    on.reduced_gradient(x, u, al, pd=pd, qd=qd)
-    t2 = time.perf_counter()
-    on.reduced_hessian(x, u, al, cols=cols, pd=pd, qd=qd)
-    t3 = time.perf_counter()
-    return x, t2 - t0, t3 - t2
-
-
-def cpu_value(nu, ncols, fixed_s, cols_s):
-    return nu / (fixed_s + cols_s * nu / ncols)
-
-
-def run_cpu_baseline(net, ncols):
-    import oracle
-    on = oracle.OracleNet(net)
-    u = synth.flat_control(net)
+def interior_point(net, x_c_fn, u):
+    """Interior primal-dual start: u 2% inside its bounds, s = c(u) clipped 1% inside its
+    bounds, bound duals mu / distance (central path), mu = 0.1."""
+    u_lo, u_hi = synth.control_bounds(net)
+    u = np.clip(u, u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
     al = synth.al_inputs(net, seed=7)
-    pds, qds = synth.ar1_loads(net, 2, seed=100)
-    x, _ = on.powerflow(u)
-    nu = len(u)
-    ncols = max(1, min(ncols, nu))
-    cols = np.linspace(0, nu - 1, ncols).round().astype(np.int32)
-    x, fixed, colt = oracle_step(on, u, al, x, pds[1], qds[1], cols)
-    return {"value": cpu_value(nu, ncols, fixed, colt), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one step on the same workload with {ncols} of {nu} Hessian columns "
-                      f"(power flow + gradient {fixed:.2f} s, columns {colt:.2f} s), scaled to all columns; "
-                      "single-threaded FP64 C, gcc -O2"}
+    lo, hi = al["s_lo"], al["s_hi"]
+    s = np.clip(x_c_fn(u), lo + 0.01 * (hi - lo), hi - 0.01 * (hi - lo))
+    mu = 0.1
+    st = dict(u_lo=u_lo, u_hi=u_hi, s_lo=lo, s_hi=hi, mu=mu, zl_u=mu / (u - u_lo), zu_u=mu / (u_hi - u),
+              zl_s=mu / (s - lo), zu_s=mu / (hi - s))
+    return u, s, al, st
+
+
+def oracle_tracking(net, nsteps, seed=100):
+    """The oracle's tracking loop (FP64 C + numpy): per step, the power flow at the new loads and
+    one reduced-Newton step.  Returns the per-step wall times (s)."""
+    import oracle
+    from oracle import al_step as A
+    from threadpoolctl import threadpool_limits
+    on = oracle.OracleNet(net)
+    u0 = synth.flat_control(net)
+    x, _ = on.powerflow(u0)
+
+    def cfun(u):
+        xx, _ = on.powerflow(u, x0=x)
+        return on.eval(xx, u)["c"]
+    u, s, al, st = interior_point(net, cfun, u0)
+    x, _ = on.powerflow(u, x0=x)
+    pds, qds = synth.ar1_loads(net, nsteps + 1, seed=seed)
+    times, delta = [], 0.0
+    with threadpool_limits(limits=1):
+        for k in range(1, nsteps + 1):
+            t0 = time.perf_counter()
+            x, _ = on.powerflow(u, pd=pds[k], qd=qds[k], x0=x)
+            out = A.al_step(on, x, u, s, st, al, pd=pds[k], qd=qds[k], delta_start=delta)
+            times.append(time.perf_counter() - t0)
+            delta = out["delta"]
+            u, s, x = out["u"], out["s"], out["x"]
+            st.update(out["duals"])
+    return times
+
+
+def run_cpu_baseline(net):
+    t = oracle_tracking(net, 1)[0]
+    nu = 1 + 2 * (net.n_gen - 1)
+    return {"value": nu / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one tracking step of the same workload ({t:.1f} s): power flow at new loads and one "
+                      "reduced-Newton step with all Hessian columns; FP64 C oracle, BLAS limited to 1 thread"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
     net = synth.workload(WORKLOAD)
-    on = oracle.OracleNet(net)
-    u = synth.flat_control(net)
-    al = synth.al_inputs(net, seed=7)
-    nu = len(u)
-    pds, qds = synth.ar1_loads(net, args.warmup + args.steps + 1, seed=100)
-    x, _ = on.powerflow(u)
-    ncols = max(8, min(args.cpu_cols, nu))
-    cols = np.linspace(0, nu - 1, ncols).round().astype(np.int32)
-    for w in range(args.warmup):
-        x, _, _ = oracle_step(on, u, al, x, pds[w + 1], qds[w + 1], cols)
-    vals, times = [], []
-    for k in range(args.steps):
-        s = args.warmup + 1 + k
-        x, fixed, colt = oracle_step(on, u, al, x, pds[s], qds[s], cols)
-        vals.append(cpu_value(nu, ncols, fixed, colt))
-        times.append(fixed + colt * nu / ncols)
-    value = statistics.mean(vals)
+    nu = 1 + 2 * (net.n_gen - 1)
+    times = oracle_tracking(net, args.warmup + args.steps)[args.warmup:]
     ms = 1e3 * statistics.mean(times)
+    value = nu / (ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": workload_config(nu, {"cpu_columns_per_step": ncols}),
+            "config": workload_config(nu),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: power flow, gradient and {ncols} of {nu} Hessian columns "
-                                       "of the FP64 C oracle, scaled to all columns"},
+                             "sample": "every step of the tracking loop, full Hessian, FP64 C oracle, "
+                                       "BLAS limited to 1 thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -213,6 +218,41 @@ def hbm_bytes_per_hessian(sym, nx, nu, k):
     return blocks * (24 * nnz_lu + 64 * nx * k)
 
 
+def batched_snapshots(P, torch, dev, block_k):
+    """Config-3 batch: 128 x 500-bus, 64 x 2,000-bus and 16 x 9,200-bus snapshots, each at its own
+    AR(1) load and power flow; all Hessians in one persistent launch vs one call per snapshot."""
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
+    snaps = []
+    for name, cnt in (("batchA500", 128), ("batchB2000", 64), ("large9200", 16)):
+        net = synth.workload(name)
+        pds, qds = synth.ar1_loads(net, cnt + 1, seed=400)
+        al = synth.al_inputs(net, seed=7)
+        ald = {k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+        u = d(synth.flat_control(net))
+        for k in range(cnt):
+            c = P.OPFContext(net, device=dev.index)
+            c.powerflow(u, pd=d(pds[k + 1]), qd=d(qds[k + 1]))
+            snaps.append((c, ald))
+    outs = [torch.empty((c.nu, c.nu), dtype=torch.float64, device=dev) for c, _ in snaps]
+    nhvp = sum(c.nu for c, _ in snaps)
+    ms = []
+    for r in range(4):
+        _, info = P.reduced_hessian_batched([c for c, _ in snaps], [a for _, a in snaps], block_k=block_k,
+                                            outs=outs)
+        if r:
+            ms.append(info["ms_total"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (c, a), o in zip(snaps, outs):
+        c.reduced_hessian(a, block_k=block_k, out=o)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    bms = statistics.median(ms)
+    return {"snapshots": len(snaps), "hvps": nhvp, "launches": 1, "tiles": info["tiles"], "grid": info["grid"],
+            "ms_batched": bms, "hvps_per_s_batched": nhvp / (bms * 1e-3),
+            "ms_per_snapshot_calls": seq_s * 1e3, "hvps_per_s_per_snapshot_calls": nhvp / seq_s}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -222,52 +262,55 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2110_02590_b300 as P
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
 
     net = synth.workload(WORKLOAD)
     ctx = P.OPFContext(net, device=local)
     nu, nx = ctx.nu, ctx.nx
     sym = ctx.symbolic()
-    u = torch.as_tensor(synth.flat_control(net), device=dev)
-    al_h = synth.al_inputs(net, seed=7)
-    al = {k: (torch.as_tensor(v, device=dev) if isinstance(v, np.ndarray) else v) for k, v in al_h.items()}
+    x0, _ = ctx.powerflow(d(synth.flat_control(net)))
+
+    def cfun(u):
+        xx, _ = ctx.powerflow(d(u), x0=x0)
+        al0 = {k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in synth.al_inputs(net, seed=7).items()}
+        return ctx.reduced_gradient(al0)["c"].cpu().numpy()
+    u_h, s_h, al_h, st_h = interior_point(net, cfun, synth.flat_control(net))
+    al = {k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al_h.items() if k != "s"}
+    state = {k: d(v) for k, v in st_h.items() if k != "mu"}
+    state.update(u=d(u_h), s=d(s_h), mu=st_h["mu"])
+    state["x"], _ = ctx.powerflow(state["u"], x0=x0)
+    tune = ctx.autotune(dict(al, s=state["s"]))
     nsnap = args.warmup + args.steps + 1
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
-    pds = torch.as_tensor(pds_h, device=dev)
-    qds = torch.as_tensor(qds_h, device=dev)
-    x, _ = ctx.powerflow(u)
-    H = torch.empty((nu, nu), dtype=torch.float64, device=dev)
+    pds, qds = d(pds_h), d(qds_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    delta = [0.0]
 
-    def step(s):
-        nonlocal x
-        x, info = ctx.powerflow(u, pd=pds[s], qd=qds[s], x0=x)
-        g = ctx.reduced_gradient(al)
-        _, hinfo = ctx.reduced_hessian(al, block_k=args.block_k, out=H)
-        return g, hinfo, info
+    def step(k, pd, qd):
+        state["x"], pinfo = ctx.powerflow(state["u"], pd=pd, qd=qd, x0=state["x"])
+        _, _, sinfo = ctx.al_step(al, state, block_k=0, delta_start=delta[0])
+        delta[0] = sinfo["delta"]
+        return pinfo, sinfo
 
     for w in range(args.warmup):
-        step(1 + w)
+        step(w, pds[1 + w], qds[1 + w])
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    hess_ms, hvp_ms, pf_iters = [], [], []
+    infos = []
     launches0 = ctx.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            g, hinfo, info = step(args.warmup + 1 + k)
+            infos.append(step(k, pds[args.warmup + 1 + k], qds[args.warmup + 1 + k]))
             ev[k][1].record(stream)
-            hess_ms.append(hinfo["ms_total"])
-            hvp_ms.append(hinfo["ms_hvp"])
-            pf_iters.append(info["iterations"])
         torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -275,81 +318,87 @@ def run_gpu(args):
     ms_per_step = total_ms / args.steps
     value = world * nu / (ms_per_step * 1e-3)
 
+    # the Hessian alone (exact weights) at the current state, and the HVP kernel phase
+    alh = dict(al, s=state["s"])
+    hs = []
+    for r in range(4):
+        flush.zero_()
+        _, hinfo = ctx.reduced_hessian(alh)
+        if r:
+            hs.append((hinfo["ms_total"], hinfo["ms_hvp"]))
+    hess_ms = statistics.median(h[0] for h in hs)
+    hvp_ms = statistics.median(h[1] for h in hs)
     # plain form (k = 1, one direction per launch) on a column sample
     pc = max(1, min(args.plain_cols, nu))
-    _, pinfo = ctx.reduced_hessian(al, block_k=1, plain=True, out=H, col_begin=0, col_count=pc)
+    _, pinfo = ctx.reduced_hessian(alh, block_k=1, plain=True, col_begin=0, col_count=pc)
     plain_ms_per_col = pinfo["ms_hvp"] / pc
 
-    # dominant kernel roofline (the HVP tile kernel; its time is the HVP phase of the Hessian call)
     flops = hvp_flops_per_column(sym, nx, net.n_branch) * nu
-    hvp_s = statistics.median(hvp_ms) * 1e-3
-    achieved_tf = flops / hvp_s / 1e12
+    achieved_tf = flops / (hvp_ms * 1e-3) / 1e12
     hbm_peak, hbm_kind = peaks()
-    hbm_b = hbm_bytes_per_hessian(sym, nx, nu, args.block_k)
+    hbm_b = hbm_bytes_per_hessian(sym, nx, nu, tune["block_k"])
 
-    # end to end: host (pinned) inputs in, Hessian and gradient out, through the C ABI
-    pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
-    host_pd, host_qd = pin(pds_h), pin(qds_h)
-    host_u = pin(synth.flat_control(net))
-    host_al = {k: pin(v) for k, v in al_h.items() if isinstance(v, np.ndarray)}
-    host_H = torch.empty((nu, nu), dtype=torch.float64).pin_memory()
-    host_g = torch.empty(nu, dtype=torch.float64).pin_memory()
-    dev_u = torch.empty_like(u)
+    # end to end: loads in from pinned host memory, the new controls and slacks out, per step
+    host_pd = torch.as_tensor(pds_h).pin_memory()
+    host_qd = torch.as_tensor(qds_h).pin_memory()
+    host_u = torch.empty(nu, dtype=torch.float64).pin_memory()
+    host_s = torch.empty(ctx.m, dtype=torch.float64).pin_memory()
     dev_pd = torch.empty(net.n_bus, dtype=torch.float64, device=dev)
     dev_qd = torch.empty_like(dev_pd)
-    dev_al = {k: torch.empty(v.shape, dtype=torch.float64, device=dev) for k, v in host_al.items()}
-    dev_al.update({k: v for k, v in al_h.items() if not isinstance(v, np.ndarray)})
     ks = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(ks):
-        s = 1 + (k % (nsnap - 1))
-        dev_pd.copy_(host_pd[s], non_blocking=True)
-        dev_qd.copy_(host_qd[s], non_blocking=True)
-        dev_u.copy_(host_u, non_blocking=True)
-        for kk, v in host_al.items():
-            dev_al[kk].copy_(v, non_blocking=True)
-        x, _ = ctx.powerflow(dev_u, pd=dev_pd, qd=dev_qd, x0=x)
-        g = ctx.reduced_gradient(dev_al)
-        ctx.reduced_hessian(dev_al, block_k=args.block_k, out=H)
-        host_H.copy_(H, non_blocking=True)
-        host_g.copy_(g["grad_u"], non_blocking=True)
+        sidx = 1 + (k % (nsnap - 1))
+        dev_pd.copy_(host_pd[sidx], non_blocking=True)
+        dev_qd.copy_(host_qd[sidx], non_blocking=True)
+        step(k, dev_pd, dev_qd)
+        host_u.copy_(state["u"], non_blocking=True)
+        host_s.copy_(state["s"], non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ks
-    h2d = 8 * (2 * net.n_bus + nu + sum(v.numel() for v in host_al.values()))
-    d2h = 8 * (nu * nu + nu)
+
+    batch = None if args.no_batch else batched_snapshots(P, torch, dev, tune["block_k"])
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
+    sinfos = [i[1] for i in infos]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(nu, {"block_k": args.block_k, "grid": hinfo["grid"], "tiles": hinfo["tiles"],
+        "config": workload_config(nu, {"step": "tracking update: power flow at new loads + reduced-Newton step "
+                                               "(gradient, Schur Hessian, Cholesky, trial power flow)",
+                                       "block_k": tune["block_k"], "threads": tune["threads"],
+                                       "autotuned": True,
                                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
-        "ms_per_hessian": statistics.median(hess_ms),
-        "ms_hvp_phase": statistics.median(hvp_ms),
-        "hvps_per_s_hessian_only": nu / (statistics.median(hess_ms) * 1e-3),
+        "ms_per_hessian": hess_ms,
+        "ms_hvp_phase": hvp_ms,
+        "hvps_per_s_hessian_only": nu / (hess_ms * 1e-3),
+        "ms_hessian_in_step": statistics.median(i["ms_hessian"] for i in sinfos),
+        "step_detail": {"pf_iterations": statistics.median(i[0]["iterations"] for i in infos),
+                        "inertia_delta": statistics.median(i["delta"] for i in sinfos),
+                        "halvings": sum(i["halvings"] for i in sinfos)},
         "plain": {"ms_per_hvp": plain_ms_per_col, "hvps_per_s": 1e3 / plain_ms_per_col,
                   "ms_per_hessian_extrapolated": plain_ms_per_col * nu, "columns_timed": pc},
-        "batched_over_plain": (nu / hvp_s) / (1e3 / plain_ms_per_col),
-        "pf_iterations": statistics.median(pf_iters),
+        "batched_over_plain": (nu / (hvp_ms * 1e-3)) / (1e3 / plain_ms_per_col),
+        "batched_snapshots": batch,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "hvp_tile_kernel", "flops_per_launch": flops,
                      "peak_note": "FP64 FMA pipe, nominal 1.25 TFLOP/s (microbenchmark on this pool: 1.12)",
-                     "hbm": {"bytes_per_hessian": hbm_b, "achieved_gbs": hbm_b / hvp_s / 1e9,
+                     "hbm": {"bytes_per_hessian": hbm_b, "achieved_gbs": hbm_b / (hvp_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
-                             "frac": hbm_b / hvp_s / 1e9 / hbm_peak}},
-        "e2e": {"value": world * nu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "steps": ks},
+                             "frac": hbm_b / (hvp_ms * 1e-3) / 1e9 / hbm_peak}},
+        "e2e": {"value": world * nu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * net.n_bus,
+                "d2h_bytes_per_step": 8 * (nu + ctx.m), "ms_per_step": e2e_s * 1e3, "steps": ks},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     if not args.no_cpu:
-        line["cpu_baseline"] = run_cpu_baseline(net, args.cpu_cols)
+        line["cpu_baseline"] = run_cpu_baseline(net)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -166,7 +166,8 @@ opf_status opf_reduced_gradient(opf_ctx* ctx, const opf_al_params* p, double* F,
                                 double* grad_pd, double* grad_qd);
 
 typedef struct {
-  int block_k;   /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32 (0 = 8) */
+  int block_k;   /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32
+                    (0 = the context's autotuned choice, else 8) */
   int grid;      /* resident CTA tiles (0 = one per tile, capped at 4 per SM) */
   int plain;     /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
   int col_begin; /* first Hessian column to compute (0) */
@@ -193,6 +194,18 @@ typedef struct {
  */
 opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts,
                                double* H, opf_hess_info* info);
+
+/*
+ * opf_hessian_autotune: time opf_reduced_hessian on the context's current state
+ * for each (block_k, threads) in {(4,256), (8,256), (8,512), (16,256),
+ * (16,512), (32,256)} (one untimed and one timed call each, CUDA events on the
+ * context stream), keep the fastest as the context's choice for block_k = 0,
+ * and return it in best (host) with its time in best_ms (host, may be NULL).
+ * H (device, n_u x n_u) is scratch for the trial calls.  Errors as
+ * opf_reduced_hessian.
+ */
+opf_status opf_hessian_autotune(opf_ctx* ctx, const opf_al_params* p, double* H, opf_hess_opts* best,
+                                float* best_ms);
 
 /*
  * opf_reduced_hessian_batched: the dense reduced Hessians of n contexts
@@ -250,7 +263,9 @@ opf_status opf_reduced_hessian_noalloc(opf_ctx* ctx, const opf_al_params* p,
  *   d_s = (rho D^2 + Sigma_s)^{-1} (-grad_s psi + rho D^2 J d_u),  D = diag(sigma_c)
  *   dz_lo = mu/(w - w_lo) - z_lo - Sigma_lo d_w,  dz_hi = mu/(w_hi - w) - z_hi + Sigma_hi d_w
  * S_uu is factorised by a device FP64 Cholesky; delta (inertia correction) takes
- * 0, then 1e-8 * 10^k, k = 0 .. max_inertia - 1, until the factorisation succeeds.
+ * 0, then 1e-8 * 10^k, k = 0 .. max_inertia - 1, until the factorisation succeeds
+ * (with opts->delta_start > 0: delta_start, then 10x per try, as a loop that
+ * carries the previous step's delta over).
  * Step lengths: fraction to the boundary with tau = max(0.99, 1 - mu) for the
  * primal and the dual variables; the power flow is re-solved at u + alpha_p d_u
  * (warm start from x) and alpha_p halved until it converges, so the new iterate
@@ -272,7 +287,8 @@ typedef struct {
 typedef struct {
   int block_k;        /* Hessian tile width (0 = 8) */
   int max_halvings;   /* trial power flows allowed after the first (0 = 10) */
-  int max_inertia;    /* inertia-correction tries after delta = 0 (0 = 24) */
+  int max_inertia;    /* inertia-correction tries after the first (0 = 24) */
+  double delta_start; /* first delta tried (0 = start at 0) */
 } opf_step_opts;
 
 typedef struct {

@@ -24,7 +24,8 @@ dz_hi = mu/(w_hi - w) - z_hi + Sigma_hi d_w.  Fraction to the boundary with
 tau = max(0.99, 1 - mu); the trial control is accepted when the power flow
 converges, else alpha is halved (feasibility of every iterate, Sec. I).
 Inertia correction: delta in {0, 1e-8, 1e-7, ..., 1e16} added to the u-block
-(i.e. to S_uu) until the Cholesky factorisation succeeds.  The reduced Hessian
+(i.e. to S_uu) until the Cholesky factorisation succeeds; with delta_start > 0
+the tries are delta_start, 10 delta_start, ... (carrying a previous step's delta).  The reduced Hessian
 of the AL is indefinite away from a solution, so the correction is needed.
 """
 import numpy as np
@@ -48,18 +49,18 @@ def newton_pieces(on, x, u, s, st, al, pd=None, qd=None):
                 rd2=rd2, omega=rd2 * sig_s / (rd2 + sig_s))
 
 
-def cholesky_with_inertia(S, max_tries=24):
-    delta = 0.0
+def cholesky_with_inertia(S, max_tries=24, delta_start=0.0):
+    delta = delta_start
     for k in range(max_tries + 1):
         try:
             L = np.linalg.cholesky(S + delta * np.eye(S.shape[0]))
             return L, delta
         except np.linalg.LinAlgError:
-            delta = 1e-8 * 10.0 ** k
+            delta = delta_start * 10.0 ** (k + 1) if delta_start > 0 else 1e-8 * 10.0 ** k
     raise np.linalg.LinAlgError("not positive definite after inertia corrections")
 
 
-def schur_step(on, x, u, s, st, al, pd=None, qd=None):
+def schur_step(on, x, u, s, st, al, pd=None, qd=None, delta_start=0.0):
     """(d_u, d_s) by Prop. 3 with the oracle's reduced Hessian and reduced Jacobian products."""
     P = newton_pieces(on, x, u, s, st, al, pd, qd)
     H = on.reduced_hessian(x, u, dict(al, s=s), omega=P["omega"], pd=pd, qd=qd)
@@ -67,7 +68,7 @@ def schur_step(on, x, u, s, st, al, pd=None, qd=None):
     v = P["rd2"] / (P["rd2"] + P["sig_s"]) * P["gpsi_s"]
     _, Jtv = on.jac_prod(x, u, w=v, pd=pd, qd=qd)
     r = -P["gpsi_u"] - Jtv
-    L, delta = cholesky_with_inertia(S)
+    L, delta = cholesky_with_inertia(S, delta_start=delta_start)
     du = np.linalg.solve(L.T, np.linalg.solve(L, r))
     Jdu, _ = on.jac_prod(x, u, v=du, pd=pd, qd=qd)
     ds = (-P["gpsi_s"] + P["rd2"] * Jdu) / (P["rd2"] + P["sig_s"])
@@ -106,10 +107,10 @@ def _max_step_dual(z, dz, tau):
     return 1.0 if not neg.any() else min(1.0, float(np.min(-tau * z[neg] / dz[neg])))
 
 
-def al_step(on, x, u, s, st, al, pd=None, qd=None, max_halvings=10):
+def al_step(on, x, u, s, st, al, pd=None, qd=None, max_halvings=10, delta_start=0.0):
     """One reduced-Newton step: Schur solve, dual step, fraction to the boundary,
     power flow at the trial control with halving.  Returns the new iterate and the step data."""
-    out = schur_step(on, x, u, s, st, al, pd, qd)
+    out = schur_step(on, x, u, s, st, al, pd, qd, delta_start=delta_start)
     du, ds = out["du"], out["ds"]
     mu = st["mu"]
     tau = max(0.99, 1.0 - mu)

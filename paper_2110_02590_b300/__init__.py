@@ -71,7 +71,8 @@ class AlState(C.Structure):
 
 
 class StepOpts(C.Structure):
-    _fields_ = [("block_k", C.c_int), ("max_halvings", C.c_int), ("max_inertia", C.c_int)]
+    _fields_ = [("block_k", C.c_int), ("max_halvings", C.c_int), ("max_inertia", C.c_int),
+                ("delta_start", C.c_double)]
 
 
 class StepInfo(C.Structure):
@@ -117,6 +118,8 @@ def lib():
                                   C.POINTER(StepInfo), C.c_void_p, C.c_void_p]
         L.opf_reduced_hessian_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AlParams),
                                                   C.POINTER(C.c_void_p), C.POINTER(HessOpts), C.POINTER(HessInfo)]
+        L.opf_hessian_autotune.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(HessOpts),
+                                           C.POINTER(C.c_float)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
@@ -304,6 +307,19 @@ class OPFContext:
             raise OPFError(st, "opf_reduced_gradient")
         return out
 
+    def autotune(self, al):
+        """Pick the fastest (block_k, threads) for this context; later calls with block_k=0 use it."""
+        t = self.torch
+        self._sync_stream()
+        p, keep = self._al(al)
+        H = t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
+        best = HessOpts()
+        ms = C.c_float()
+        st = lib().opf_hessian_autotune(self.h, C.byref(p), _ptr(H), C.byref(best), C.byref(ms))
+        if st != 0:
+            raise OPFError(st, "opf_hessian_autotune")
+        return dict(block_k=best.block_k, threads=best.threads, ms=ms.value)
+
     def launch_count(self) -> int:
         v = C.c_longlong()
         lib().opf_launch_count(self.h, C.byref(v))
@@ -343,7 +359,7 @@ class OPFContext:
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
                          ms_total=info.ms_total, ms_hvp=info.ms_hvp)
 
-    def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0):
+    def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0, delta_start=0.0):
         """One reduced-Newton step (Prop. 3).  `state`: dict of cuda float64 tensors u, s, zl_u,
         zu_u, zl_s, zu_s, u_lo, u_hi, s_lo, s_hi, x and the float mu; u, s, the duals and x are
         updated in place.  Returns (du, ds, info)."""
@@ -358,7 +374,7 @@ class OPFContext:
         ds = t.empty(self.m, dtype=t.float64, device=self.device)
         info = StepInfo()
         rc = lib().opf_al_step(self.h, C.byref(p), C.byref(st),
-                               C.byref(StepOpts(int(block_k), int(max_halvings), int(max_inertia))),
+                               C.byref(StepOpts(int(block_k), int(max_halvings), int(max_inertia), float(delta_start))),
                                C.byref(info), _ptr(du), _ptr(ds))
         if rc != 0:
             raise OPFError(rc, "opf_al_step")

@@ -538,10 +538,11 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
   if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
   TRY(check_al(c, p));
-  int C = (o && o->block_k) ? o->block_k : 8;
+  const bool tuned = !(o && o->block_k) && c->tuned_k > 0;
+  int C = (o && o->block_k) ? o->block_k : (tuned ? c->tuned_k : 8);
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
     FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
-  const int nt = (o && o->threads) ? o->threads : 256;
+  const int nt = (o && o->threads) ? o->threads : (tuned ? c->tuned_threads : 256);
   if (nt != 256 && nt != 512) FAIL(OPF_EINVAL, "threads must be 256 or 512");
   c->hvp_threads = nt;
   const bool plain = o && o->plain;
@@ -576,6 +577,32 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
     cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
   }
+  return OPF_OK;
+}
+
+opf_status opf_hessian_autotune(opf_ctx* c, const opf_al_params* p, double* H, opf_hess_opts* best,
+                                float* best_ms) {
+  if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
+  static const int cand[][2] = {{4, 256}, {8, 256}, {8, 512}, {16, 256}, {16, 512}, {32, 256}};
+  float tbest = 0.f;
+  int kb = 0, tb = 0;
+  for (const auto& cd : cand) {
+    opf_hess_opts o = {cd[0], 0, 0, 0, 0, cd[1]};
+    opf_hess_info hi;
+    TRY(opf_reduced_hessian(c, p, &o, H, &hi));
+    TRY(opf_reduced_hessian(c, p, &o, H, &hi));
+    if (kb == 0 || hi.ms_total < tbest) {
+      tbest = hi.ms_total;
+      kb = cd[0];
+      tb = cd[1];
+    }
+  }
+  c->tuned_k = kb;
+  c->tuned_threads = tb;
+  if (best) {
+    *best = opf_hess_opts{kb, 0, 0, 0, 0, tb};
+  }
+  if (best_ms) *best_ms = tbest;
   return OPF_OK;
 }
 

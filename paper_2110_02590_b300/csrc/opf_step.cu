@@ -531,7 +531,8 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   neg_sum_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, w->Jtv, w->r);
   c->launches++;
   // Cholesky with inertia correction
-  double delta = 0.0;
+  const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
+  double delta = delta0;
   int tries = 0;
   for (;; tries++) {
     add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
@@ -545,7 +546,7 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
       set_last_error("S_uu not positive definite after the inertia corrections");
       return OPF_ENOTPD;
     }
-    delta = 1e-8 * std::pow(10.0, (double)tries);
+    delta = (delta0 > 0.0) ? delta0 * std::pow(10.0, (double)(tries + 1)) : 1e-8 * std::pow(10.0, (double)tries);
   }
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   launch_chol_solve(c, w->L, nu, w->du);

@@ -32,17 +32,18 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("name,mu", [("tiny30", 0.1), ("medium1400", 0.1), ("medium1400", 1e-3)])
-def test_al_step_parity(name, mu):
+@pytest.mark.parametrize("name,mu,delta_start", [("tiny30", 0.1, 0.0), ("medium1400", 0.1, 0.0),
+                                                  ("medium1400", 1e-3, 0.0), ("medium1400", 0.1, 3e4)])
+def test_al_step_parity(name, mu, delta_start):
     net = synth.workload(name)
     on, x, u, al, st = setup(net, mu=mu)
-    ref = A.al_step(on, x, u, al["s"], st, al)
+    ref = A.al_step(on, x, u, al["s"], st, al, delta_start=delta_start)
     ctx = P.OPFContext(net)
     xg, info = ctx.powerflow(dev(u))
     state = {k: dev(v) for k, v in st.items() if k != "mu"}
     state.update(u=dev(u), s=dev(al["s"]), x=xg, mu=mu)
     al_dev = {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
-    du, ds, inf = ctx.al_step(al_dev, state)
+    du, ds, inf = ctx.al_step(al_dev, state, delta_start=delta_start)
     assert inf["delta"] == ref["delta"]
     assert rel(du.cpu().numpy(), ref["du"]) < STEP_TOL
     assert rel(ds.cpu().numpy(), ref["ds"]) < STEP_TOL
