@@ -24,7 +24,12 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+if "--cpu-step" in sys.argv or "reference" in sys.argv:
+    # the CPU oracle legs run single-threaded: pin the BLAS pools before numpy loads
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -57,6 +62,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--cpu-step", action="store_true", help="internal: time one oracle tracking step")
     return ap.parse_args()
 
 
@@ -99,7 +105,6 @@ def oracle_tracking(net, nsteps, seed=100):
     one reduced-Newton step.  Returns the per-step wall times (s)."""
     import oracle
     from oracle import al_step as A
-    from threadpoolctl import threadpool_limits
     on = oracle.OracleNet(net)
     u0 = synth.flat_control(net)
     x, _ = on.powerflow(u0)
@@ -111,20 +116,22 @@ def oracle_tracking(net, nsteps, seed=100):
     x, _ = on.powerflow(u, x0=x)
     pds, qds = synth.ar1_loads(net, nsteps + 1, seed=seed)
     times, delta = [], 0.0
-    with threadpool_limits(limits=1):
-        for k in range(1, nsteps + 1):
-            t0 = time.perf_counter()
-            x, _ = on.powerflow(u, pd=pds[k], qd=qds[k], x0=x)
-            out = A.al_step(on, x, u, s, st, al, pd=pds[k], qd=qds[k], delta_start=delta)
-            times.append(time.perf_counter() - t0)
-            delta = out["delta"]
-            u, s, x = out["u"], out["s"], out["x"]
-            st.update(out["duals"])
+    for k in range(1, nsteps + 1):
+        t0 = time.perf_counter()
+        x, _ = on.powerflow(u, pd=pds[k], qd=qds[k], x0=x)
+        out = A.al_step(on, x, u, s, st, al, pd=pds[k], qd=qds[k], delta_start=delta)
+        times.append(time.perf_counter() - t0)
+        delta = out["delta"]
+        u, s, x = out["u"], out["s"], out["x"]
+        st.update(out["duals"])
     return times
 
 
 def run_cpu_baseline(net):
-    t = oracle_tracking(net, 1)[0]
+    """One oracle tracking step, in a child process whose BLAS pools are pinned to one thread."""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-step"], capture_output=True,
+                         text=True, check=True)
+    t = float(out.stdout.strip().splitlines()[-1])
     nu = 1 + 2 * (net.n_gen - 1)
     return {"value": nu / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one tracking step of the same workload ({t:.1f} s): power flow at new loads and one "
@@ -407,6 +414,9 @@ def run_gpu(args):
 
 def main():
     args = parse()
+    if args.cpu_step:
+        print(oracle_tracking(synth.workload(WORKLOAD), 1)[0], flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
