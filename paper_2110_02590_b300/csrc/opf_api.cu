@@ -142,6 +142,10 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   // dense trailing block [r0, nx): every row's upper part runs to the last column
   int r0 = nx - 1;
   while (r0 > 0 && s.rp[r0] - s.dp[r0 - 1] - 1 == nx - r0) r0--;
+  // any suffix of a dense block is dense: keep at most kMaxDenseRows rows so the
+  // packed triangle fits in shared memory (the rest join the level schedule)
+  constexpr int kMaxDenseRows = 200;
+  r0 = std::max(r0, nx - kMaxDenseRows);
   // sweep schedules of the other rows; rows of a level sorted by length (longest first)
   std::vector<int> sched_ptr_f, sched_rows_f, sched_ptr_b, sched_rows_b;
   {
@@ -241,6 +245,22 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, s.ci)); n.ci = ip;
   TRY(dupload(c, &ip, s.dp)); n.dp = ip;
   TRY(dupload(c, &ip, s.perm)); n.perm = ip;
+  {
+    std::vector<int4> mf(sched_rows_f.size()), mb(sched_rows_b.size());
+    for (size_t k = 0; k < mf.size(); k++) {
+      const int i = sched_rows_f[k];
+      mf[k] = make_int4(i, s.rp[i], s.dp[i], 0);
+    }
+    for (size_t k = 0; k < mb.size(); k++) {
+      const int i = sched_rows_b[k];
+      mb[k] = make_int4(i, s.dp[i] + 1, s.rp[i + 1], 0);
+    }
+    int4* q;
+    TRY(dupload(c, &q, mf));
+    n.lmeta_f = q;
+    TRY(dupload(c, &q, mb));
+    n.lmeta_b = q;
+  }
   TRY(dupload(c, &ip, sched_ptr_f)); n.lev_ptr_f = ip;
   TRY(dupload(c, &ip, sched_rows_f)); n.lev_rows_f = ip;
   TRY(dupload(c, &ip, sched_ptr_b)); n.lev_ptr_b = ip;
@@ -284,6 +304,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
+  TRY(setup_solve1(c));
   // the numeric refactorisation as one CUDA graph (captured once on a private stream)
   CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   {

@@ -57,6 +57,7 @@ struct DevNet {
   // execution schedule of the sweeps: level lists of the rows outside the dense
   // trailing block [r0, nx) (which is solved as a dense triangle)
   const int *lev_ptr_f, *lev_rows_f, *lev_ptr_b, *lev_rows_b;
+  const int4 *lmeta_f, *lmeta_b;   // per scheduled row: {row, first entry, end entry, 0}
   int nlev_f, nlev_b;
   int r0, nroot;
   const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
@@ -81,6 +82,7 @@ void launch_pf_eval(opf_ctx* c);
 void launch_lu(opf_ctx* c);          // replays the captured refactorisation graph
 void launch_lu_kernels(opf_ctx* c);  // the kernel sequence itself (captured at load)
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale);
+opf_status setup_solve1(opf_ctx* c);  // shared-memory size of the single-RHS sweep
 void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n);
 void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
 void launch_grad_u(opf_ctx* c, double* gu);
@@ -141,6 +143,8 @@ struct opf_ctx {
   double *btab = nullptr;         // [26 nl] per-branch Hessian table
   double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
   int hvp_threads = 256;          // threads per HVP tile CTA
+  int solve1_smem = 0;            // dynamic shared bytes of the single-RHS sweep
+  bool solve1_use_smem_rhs = false;  // the right-hand side also lives in shared memory
   double* scratch = nullptr;      // HVP per-CTA slabs
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];

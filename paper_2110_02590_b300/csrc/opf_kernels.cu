@@ -261,15 +261,15 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
   }
   const int nlev = FWD ? n.nlev_f : n.nlev_b;
   const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
-  const int* lrows = FWD ? n.lev_rows_f : n.lev_rows_b;
+  const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
   const int nwarps = blockDim.x >> 5, grp = lane / C;
   for (int lv = 0; lv < nlev; lv++) {
     const int b = lptr[lv], e = lptr[lv + 1];
     if (e - b <= nwarps && RPW > 1) {
       // narrow level: one warp per row, its lane groups split the row, shuffle reduction
       for (int k = b + warp; k < e; k += nwarps) {
-        const int i = lrows[k];
-        const int p0 = FWD ? n.rp[i] : n.dp[i] + 1, p1 = FWD ? n.dp[i] : n.rp[i + 1];
+        const int4 mt = lmeta[k];
+        const int i = mt.x, p0 = mt.y, p1 = mt.z;
         double v = 0.0;
         for (int p = p0 + grp; p < p1; p += RPW) v -= V[p] * X[(size_t)n.ci[p] * C + col];
 #pragma unroll
@@ -282,9 +282,9 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
       }
     } else {
       for (int k = b + myslot; k < e; k += nslots) {
-        const int i = lrows[k];
-        double v = FWD ? row_dot<C>(n, V, X, i, n.rp[i], n.dp[i], col)
-                       : row_dot<C>(n, V, X, i, n.dp[i] + 1, n.rp[i + 1], col);
+        const int4 mt = lmeta[k];
+        const int i = mt.x;
+        double v = row_dot<C>(n, V, X, i, mt.y, mt.z, col);
         if (DIAG) v *= invdiag[i];
         X[(size_t)i * C + col] = v;
       }
@@ -318,19 +318,123 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
   }
 }
 
+// Single-RHS sweep with the dense trailing triangle staged in shared memory:
+// levels as in sweep<1>, then (FWD) the off-block part of the trailing rows and
+// the triangle column by column reading the staged values, or (backward) the
+// triangle first.  tri holds the strictly lower (FWD) or strictly upper part of
+// the trailing block, packed by rows.
+template <bool FWD, bool DIAG>
+__device__ __forceinline__ void sweep1(const DevNet& n, const double* __restrict__ V,
+                                       const double* __restrict__ invdiag, double* X, double* tri) {
+  const int r0 = n.r0, s = n.nroot;
+  // stage the triangle: FWD row i (1..s-1), column j < i at i(i-1)/2 + j;
+  // backward row i (0..s-2), column j > i at (i(2s-i-1))/2 + (j-i-1)
+  const int ntri = s * (s - 1) / 2;
+  for (int q = threadIdx.x; q < ntri; q += blockDim.x) {
+    if (FWD) {
+      int i = (int)((1.0 + sqrt(1.0 + 8.0 * q)) * 0.5);
+      while (i * (i - 1) / 2 > q) i--;
+      while ((i + 1) * i / 2 <= q) i++;
+      const int j = q - i * (i - 1) / 2;
+      tri[q] = V[n.dp[r0 + i] - (i - j)];
+    } else {
+      int i = 0;
+      // rows of the upper part have s-1, s-2, ... entries
+      int lo = 0, hi = s - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mid * (2 * s - mid - 1) / 2 <= q) lo = mid; else hi = mid - 1;
+      }
+      i = lo;
+      const int j = i + 1 + (q - i * (2 * s - i - 1) / 2);
+      tri[q] = V[n.dp[r0 + i] + (j - i)];
+    }
+  }
+  if (!FWD) {
+    __syncthreads();
+    for (int j = s - 1; j > 0; j--) {
+      const double xj = X[r0 + j] * (DIAG ? invdiag[r0 + j] : 1.0);
+      for (int i = threadIdx.x; i < j; i += blockDim.x)
+        X[r0 + i] -= tri[i * (2 * s - i - 1) / 2 + (j - i - 1)] * xj;
+      __syncthreads();
+    }
+    if (DIAG) {
+      for (int i = threadIdx.x; i < s; i += blockDim.x) X[r0 + i] *= invdiag[r0 + i];
+      __syncthreads();
+    }
+  }
+  // levels of the other rows (thread per row, or a warp per row in narrow levels)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nlev = FWD ? n.nlev_f : n.nlev_b;
+  const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
+  const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
+  for (int lv = 0; lv < nlev; lv++) {
+    const int b = lptr[lv], e = lptr[lv + 1];
+    if (e - b <= nwarps) {
+      for (int k = b + warp; k < e; k += nwarps) {
+        const int4 mt = lmeta[k];
+        double v = 0.0;
+        for (int p = mt.y + lane; p < mt.z; p += 32) v -= V[p] * X[n.ci[p]];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) {
+          v += X[mt.x];
+          if (DIAG) v *= invdiag[mt.x];
+          X[mt.x] = v;
+        }
+      }
+    } else {
+      for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+        const int4 mt = lmeta[k];
+        double v = row_dot<1>(n, V, X, mt.x, mt.y, mt.z, 0);
+        if (DIAG) v *= invdiag[mt.x];
+        X[mt.x] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (FWD) {
+    for (int k = warp; k < s; k += nwarps) {  // off-block part of the trailing rows, a warp per row
+      const int i = r0 + k;
+      const int p1 = n.dp[i] - k;
+      double v = 0.0;
+      for (int p = n.rp[i] + lane; p < p1; p += 32) v -= V[p] * X[n.ci[p]];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) X[i] += v;
+    }
+    __syncthreads();
+    for (int j = 0; j < s - 1; j++) {
+      const double xj = X[r0 + j] * (DIAG ? invdiag[r0 + j] : 1.0);
+      for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) X[r0 + i] -= tri[i * (i - 1) / 2 + j] * xj;
+      __syncthreads();
+    }
+    if (DIAG) {
+      for (int i = threadIdx.x; i < s; i += blockDim.x) X[r0 + i] *= invdiag[r0 + i];
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+}
+
 // Single right-hand side: out = G_x^{-1} (scale b) or G_x^{-T} (scale b).  One CTA.
+// Dynamic shared memory: the packed dense triangle (s(s-1)/2 doubles) and, when
+// use_smem, the right-hand side (n_x doubles) after it.
 __global__ void __launch_bounds__(1024) solve1_kernel(DevNet n, const double* LU, const double* T,
                                                        const double* invdiag, const double* b,
-                                                       double* out, double* y, int transposed,
-                                                       double scale) {
+                                                       double* out, double* yg, int transposed,
+                                                       double scale, int use_smem) {
+  extern __shared__ double dsm[];
+  double* tri = dsm;
+  double* y = use_smem ? dsm + (n.nroot * (n.nroot - 1) / 2) : yg;
   for (int i = threadIdx.x; i < n.nx; i += blockDim.x) y[i] = scale * b[n.perm[i]];
   __syncthreads();
   if (!transposed) {
-    sweep<1, true, false>(n, LU, invdiag, y);
-    sweep<1, false, true>(n, LU, invdiag, y);
+    sweep1<true, false>(n, LU, invdiag, y, tri);
+    sweep1<false, true>(n, LU, invdiag, y, tri);
   } else {
-    sweep<1, true, true>(n, T, invdiag, y);
-    sweep<1, false, false>(n, T, invdiag, y);
+    sweep1<true, true>(n, T, invdiag, y, tri);
+    sweep1<false, false>(n, T, invdiag, y, tri);
   }
   for (int i = threadIdx.x; i < n.nx; i += blockDim.x) out[n.perm[i]] = y[i];
 }
@@ -830,8 +934,29 @@ void launch_lu(opf_ctx* c) {
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
   c->launches++;
-  solve1_kernel<<<1, 1024, 0, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
-                                           transposed ? 1 : 0, scale);
+  solve1_kernel<<<1, 1024, c->solve1_smem, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
+                                                        transposed ? 1 : 0, scale, c->solve1_use_smem_rhs ? 1 : 0);
+}
+
+opf_status setup_solve1(opf_ctx* c) {
+  const size_t tri = sizeof(double) * (size_t)c->dn.nroot * (c->dn.nroot - 1) / 2;
+  const size_t full = tri + sizeof(double) * (size_t)c->dn.nx;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  const size_t cap = (size_t)optin - 1024;
+  // the attribute is per kernel, shared by every context: raise it to the device maximum once
+  if (cudaFuncSetAttribute(solve1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("cannot raise the shared-memory limit of the single-RHS sweep");
+    return OPF_ECUDA;
+  }
+  if (tri > cap) {
+    set_last_error("dense trailing block too large for the single-RHS sweep");
+    return OPF_EINVAL;
+  }
+  c->solve1_use_smem_rhs = full <= cap;
+  c->solve1_smem = (int)(c->solve1_use_smem_rhs ? full : tri);
+  return OPF_OK;
 }
 
 void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n) {
