@@ -188,6 +188,14 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     }
     if ((int)task_col.size() > c->h_task_ptr.back()) c->h_task_ptr.push_back((int)task_col.size());
   }
+  // Schur-update targets: for task (j, r) and every entry (j, c) of row j of U, the
+  // position of (r, c) in row r (no search at factorisation time)
+  std::vector<int> task_map_off(task_col.size() + 1, 0), task_map;
+  for (size_t t = 0; t < task_col.size(); t++) {
+    const int j = task_col[t], r = lcol_row[task_k[t]];
+    for (int q = s.dp[j] + 1; q < s.rp[j + 1]; q++) task_map.push_back(find_pos(s, r, s.ci[q]));
+    task_map_off[t + 1] = (int)task_map.size();
+  }
   // control buses: slack first, then PV
   std::vector<int> gn_bus, gn_of(nb, -1), ubus(h.nu, -1);
   gn_bus.push_back(h.ref);
@@ -272,6 +280,8 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &c->lcol_pos, lcol_pos));
   TRY(dupload(c, &c->task_col, task_col));
   TRY(dupload(c, &c->task_k, task_k));
+  TRY(dupload(c, &c->task_map_off, task_map_off));
+  TRY(dupload(c, &c->task_map, task_map));
   TRY(dupload(c, &c->ubus, ubus));
   TRY(dupload(c, &c->pd_nom, h.pd));
   TRY(dupload(c, &c->qd_nom, h.qd));

@@ -120,6 +120,7 @@ struct opf_ctx {
   int *lcol_pos = nullptr;        // per lower entry (CSC order): position of L_rj in row r
   int *lcol_row = nullptr;
   int *task_col = nullptr, *task_k = nullptr;
+  int *task_map_off = nullptr, *task_map = nullptr;  // Schur-update target positions per task
   std::vector<int> h_task_ptr;    // per forward level
   std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
 

@@ -141,16 +141,16 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
 // from A_rc for every c in row j of U (lanes over c).  Columns of one level
 // never update each other's rows or columns, so only the targets race, and
 // they are combined by atomic adds.
-__global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const int* __restrict__ ci,
-                                const int* __restrict__ dp, const int* __restrict__ task_col,
-                                const int* __restrict__ task_k, const int* __restrict__ lcol_row,
-                                const int* __restrict__ lcol_pos, int t0, int t1, int* flags) {
+__global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const int* __restrict__ dp,
+                                const int* __restrict__ task_col, const int* __restrict__ task_k,
+                                const int* __restrict__ lcol_pos, const int* __restrict__ map_off,
+                                const int* __restrict__ map, int t0, int t1, int* flags) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int t = t0 + warp; t < t1; t += nw) {
     const int j = task_col[t], k = task_k[t];
-    const int r = lcol_row[k], prj = lcol_pos[k];
+    const int prj = lcol_pos[k];
     const double ujj = LU[dp[j]];
     const double l = LU[prj] / ujj;
     __syncwarp();
@@ -158,17 +158,8 @@ __global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const in
       LU[prj] = l;
       if (!(fabs(ujj) > 0.0) || !isfinite(l)) flags[0] = 1;
     }
-    const int rb = rp[r], re = rp[r + 1];
-    for (int q = dp[j] + 1 + lane; q < rp[j + 1]; q += 32) {
-      const int c = ci[q];
-      const double v = -l * LU[q];
-      int lo = rb, hi = re - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (ci[mid] < c) lo = mid + 1; else hi = mid;
-      }
-      atomicAdd(&LU[lo], v);
-    }
+    const int* tg = map + map_off[t] - (dp[j] + 1);
+    for (int q = dp[j] + 1 + lane; q < rp[j + 1]; q += 32) atomicAdd(&LU[tg[q]], -l * LU[q]);
   }
 }
 
@@ -363,35 +354,71 @@ __device__ __forceinline__ void sweep1(const DevNet& n, const double* __restrict
       __syncthreads();
     }
   }
-  // levels of the other rows (thread per row, or a warp per row in narrow levels)
+  // levels of the other rows (thread per row, or a warp per row in narrow levels).
+  // The factor data is static, so each level prefetches the next level's row
+  // record and first entry before the barrier; only X reads stay on the chain.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nlev = FWD ? n.nlev_f : n.nlev_b;
   const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
   const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
+  int4 mt = make_int4(-1, 0, 0, 0);
+  int pc = -1;
+  double pv = 0.0;
+  auto fetch = [&](int lb, int le) {
+    const bool nar = (le - lb) <= nwarps;
+    const int k = lb + (nar ? warp : (int)threadIdx.x);
+    mt = (k < le) ? lmeta[k] : make_int4(-1, 0, 0, 0);
+    const int p = nar ? mt.y + lane : mt.y;
+    pc = (k < le && p < mt.z) ? n.ci[p] : -1;
+    pv = (pc >= 0) ? V[p] : 0.0;
+  };
+  int b = nlev > 0 ? lptr[0] : 0, e = nlev > 0 ? lptr[1] : 0;
+  if (nlev > 0) fetch(b, e);
   for (int lv = 0; lv < nlev; lv++) {
-    const int b = lptr[lv], e = lptr[lv + 1];
+    const int en = (lv + 1 < nlev) ? lptr[lv + 2] : e;
     if (e - b <= nwarps) {
-      for (int k = b + warp; k < e; k += nwarps) {
-        const int4 mt = lmeta[k];
+      for (int k = b + warp, first = 1; k < e; k += nwarps, first = 0) {
+        const int4 m = first ? mt : lmeta[k];
         double v = 0.0;
-        for (int p = mt.y + lane; p < mt.z; p += 32) v -= V[p] * X[n.ci[p]];
+        int p = m.y + lane;
+        if (first) {
+          if (pc >= 0) v -= pv * X[pc];
+          p += 32;
+        }
+        for (; p < m.z; p += 32) v -= V[p] * X[n.ci[p]];
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (lane == 0) {
-          v += X[mt.x];
-          if (DIAG) v *= invdiag[mt.x];
-          X[mt.x] = v;
+          v += X[m.x];
+          if (DIAG) v *= invdiag[m.x];
+          X[m.x] = v;
         }
       }
     } else {
-      for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
-        const int4 mt = lmeta[k];
-        double v = row_dot<1>(n, V, X, mt.x, mt.y, mt.z, 0);
-        if (DIAG) v *= invdiag[mt.x];
-        X[mt.x] = v;
+      for (int k = b + threadIdx.x, first = 1; k < e; k += blockDim.x, first = 0) {
+        const int4 m = first ? mt : lmeta[k];
+        int p = m.y;
+        double s0 = X[m.x], s1 = 0.0;
+        if (first && pc >= 0) {
+          s0 -= pv * X[pc];
+          p++;
+        }
+        for (; p + 1 < m.z; p += 2) {
+          const int c0 = n.ci[p], c1 = n.ci[p + 1];
+          const double v0 = V[p], v1 = V[p + 1];
+          s0 -= v0 * X[c0];
+          s1 -= v1 * X[c1];
+        }
+        if (p < m.z) s0 -= V[p] * X[n.ci[p]];
+        double v = s0 + s1;
+        if (DIAG) v *= invdiag[m.x];
+        X[m.x] = v;
       }
     }
+    if (lv + 1 < nlev) fetch(e, en);
     __syncthreads();
+    b = e;
+    e = en;
   }
   if (FWD) {
     for (int k = warp; k < s; k += nwarps) {  // off-block part of the trailing rows, a warp per row
@@ -917,8 +944,8 @@ void launch_lu_kernels(opf_ctx* c) {
     const int warps = t1 - t0;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
     c->launches++;
-    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->dn.rp, c->dn.ci, c->dn.dp, c->task_col,
-                                                   c->task_k, c->lcol_row, c->lcol_pos, t0, t1, c->flags);
+    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->dn.rp, c->dn.dp, c->task_col, c->task_k,
+                                                   c->lcol_pos, c->task_map_off, c->task_map, t0, t1, c->flags);
   }
   c->launches++;
   lu_dense_block_kernel<<<1, 1024, 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags);
