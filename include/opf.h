@@ -173,6 +173,9 @@ typedef struct {
   int col_begin; /* first Hessian column to compute (0) */
   int col_count; /* number of columns (0 = through n_u); the others of H are left untouched */
   int threads;   /* threads per tile CTA: 256 or 512 (0 = 256) */
+  int reuse_first_order; /* 1: the context's first-order quantities (c, phi', omega, lambda)
+                            were just evaluated with these same parameters by
+                            opf_reduced_gradient: skip re-evaluating them */
 } opf_hess_opts;
 
 typedef struct {

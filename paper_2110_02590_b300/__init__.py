@@ -56,7 +56,7 @@ class AlParams(C.Structure):
 
 class HessOpts(C.Structure):
     _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int), ("col_begin", C.c_int),
-                ("col_count", C.c_int), ("threads", C.c_int)]
+                ("col_count", C.c_int), ("threads", C.c_int), ("reuse_first_order", C.c_int)]
 
 
 class HessInfo(C.Structure):
@@ -199,7 +199,7 @@ def reduced_hessian_batched(ctxs, als, block_k=8, grid=0, outs=None):
     ps = (AlParams * n)(*params)
     Hp = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
     info = HessInfo()
-    st = lib().opf_reduced_hessian_batched(hs, n, ps, Hp, C.byref(HessOpts(int(block_k), int(grid), 0, 0, 0, 0)),
+    st = lib().opf_reduced_hessian_batched(hs, n, ps, Hp, C.byref(HessOpts(int(block_k), int(grid), 0, 0, 0, 0, 0)),
                                            C.byref(info))
     if st != 0:
         raise OPFError(st, "opf_reduced_hessian_batched")
@@ -336,7 +336,7 @@ class OPFContext:
         p, keep = self._al(al)
         H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
         info = HessInfo()
-        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count), int(threads))
+        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count), int(threads), 0)
         st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(opts),
                                        _ptr(H), C.byref(info))
         if st != 0:
@@ -352,7 +352,7 @@ class OPFContext:
         p, keep = self._al(al)
         H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
         info = HessInfo()
-        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count), 0)
+        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count), 0, 0)
         st = lib().opf_reduced_hessian_noalloc(self.h, C.byref(p), C.byref(opts), _ptr(H), C.byref(info))
         if st != 0:
             raise OPFError(st, "opf_reduced_hessian_noalloc")

@@ -587,7 +587,7 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   TRY(ensure_scratch(c, hvp_stride(c, C) * (size_t)grid));
   cudaStream_t st = c->stream;
   CK(cudaEventRecord(c->ev[0], st));
-  launch_first_order(c, p, nullptr);
+  if (!(o && o->reuse_first_order)) launch_first_order(c, p, nullptr);
   launch_hess_prep(c, p->sigma_f);
   CK(cudaEventRecord(c->ev[1], st));
   int launches = 0;
@@ -618,7 +618,7 @@ opf_status opf_hessian_autotune(opf_ctx* c, const opf_al_params* p, double* H, o
   float tbest = 0.f;
   int kb = 0, tb = 0;
   for (const auto& cd : cand) {
-    opf_hess_opts o = {cd[0], 0, 0, 0, 0, cd[1]};
+    opf_hess_opts o = {cd[0], 0, 0, 0, 0, cd[1], 0};
     opf_hess_info hi;
     TRY(opf_reduced_hessian(c, p, &o, H, &hi));
     TRY(opf_reduced_hessian(c, p, &o, H, &hi));
@@ -631,7 +631,7 @@ opf_status opf_hessian_autotune(opf_ctx* c, const opf_al_params* p, double* H, o
   c->tuned_k = kb;
   c->tuned_threads = tb;
   if (best) {
-    *best = opf_hess_opts{kb, 0, 0, 0, 0, tb};
+    *best = opf_hess_opts{kb, 0, 0, 0, 0, tb, 0};
   }
   if (best_ms) *best_ms = tbest;
   return OPF_OK;

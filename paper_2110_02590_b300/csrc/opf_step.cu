@@ -242,6 +242,20 @@ __global__ void step_prep_kernel(int nu, int m, const double* u, const double* u
   }
 }
 
+__global__ void step_sigma_kernel(int nu, int m, const double* u, const double* ulo, const double* uhi,
+                                  const double* zlu, const double* zuu, const double* s, const double* slo,
+                                  const double* shi, const double* zls, const double* zus, const double* sigc,
+                                  double rho, double* sig_u, double* sig_s, double* omega) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) sig_u[i] = zlu[i] / (u[i] - ulo[i]) + zuu[i] / (uhi[i] - u[i]);
+  if (i < m) {
+    const double sg = zls[i] / (s[i] - slo[i]) + zus[i] / (shi[i] - s[i]);
+    const double rd2 = rho * sigc[i] * sigc[i];
+    sig_s[i] = sg;
+    omega[i] = rd2 * sg / (rd2 + sg);
+  }
+}
+
 __global__ void neg_sum_kernel(int n, const double* a, const double* b, double* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = -a[i] - b[i];
@@ -508,19 +522,23 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   SCK(cudaEventCreate(&e0));
   SCK(cudaEventCreate(&e1));
   SCK(cudaEventRecord(e0, stream));
-  // gradient at (u, s): grad_u, grad_s = -phi'
+  // Sigma and the Schur weights omega (state only)
+  step_sigma_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
+      nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
+      p->sigma_c, p->rho, w->sig_u, w->sig_s, w->omega);
+  c->launches++;
+  // first-order quantities once, with omega: grad_u, grad_s = -phi' (the gradient does not depend on omega)
   opf_al_params ps = *p;
   ps.s = st->s;
-  ps.omega = nullptr;
+  ps.omega = w->omega;
   rc = opf_reduced_gradient(c, &ps, nullptr, w->gu, w->gs, nullptr, nullptr, nullptr, nullptr);
   if (rc) return rc;
   step_prep_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
       nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
       w->gu, w->gs, p->sigma_c, p->rho, st->mu, w->sig_u, w->gpsi_u, w->sig_s, w->gpsi_s, w->omega, w->v);
   c->launches++;
-  // S_uu = H(omega) + Sigma_u (symmetrised)
-  ps.omega = w->omega;
-  opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0};
+  // S_uu = H(omega) + Sigma_u (symmetrised), on the first-order quantities just evaluated
+  opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0, 1};
   opf_hess_info hi;
   rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
   if (rc) return rc;
