@@ -168,11 +168,11 @@ opf_status opf_reduced_gradient(opf_ctx* ctx, const opf_al_params* p, double* F,
 typedef struct {
   int block_k;   /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32
                     (0 = the context's autotuned choice, else 8) */
-  int grid;      /* resident CTA tiles (0 = one per tile, capped at 4 per SM) */
+  int grid;      /* CTAs (0 = one per tile, capped at the resident CTAs per SM x SMs) */
   int plain;     /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
   int col_begin; /* first Hessian column to compute (0) */
   int col_count; /* number of columns (0 = through n_u); the others of H are left untouched */
-  int threads;   /* threads per tile CTA: 256 or 512 (0 = 256) */
+  int threads;   /* threads per tile CTA: 128, 256 or 512 (0 = 256) */
   int reuse_first_order; /* 1: the context's first-order quantities (c, phi', omega, lambda)
                             were just evaluated with these same parameters by
                             opf_reduced_gradient: skip re-evaluating them */

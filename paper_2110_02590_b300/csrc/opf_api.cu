@@ -273,6 +273,21 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, sched_rows_f)); n.lev_rows_f = ip;
   TRY(dupload(c, &ip, sched_ptr_b)); n.lev_ptr_b = ip;
   TRY(dupload(c, &ip, sched_rows_b)); n.lev_rows_b = ip;
+  {
+    std::vector<int4> busrec(nb), adjrec(2 * (size_t)nl);
+    auto vslot = [&](int b) { return h.type[b] == opf::PQ ? pvv[b] : -2 - h.uv[b]; };
+    for (int i = 0; i < nb; i++)
+      busrec[i] = make_int4(vslot(i), h.type[i] == opf::REF ? -1 : pth[i], gn_of[i], h.up[i]);
+    for (int q = 0; q < 2 * nl; q++) {
+      const int e = h.adj[q], l = e >> 1, o = (e & 1) ? h.f[l] : h.t[l];
+      adjrec[q] = make_int4(vslot(o), h.type[o] == opf::REF ? -1 : pth[o], gn_of[o], o == h.ref ? 1 : 0);
+    }
+    int4* q4;
+    TRY(dupload(c, &q4, busrec));
+    n.busrec = q4;
+    TRY(dupload(c, &q4, adjrec));
+    n.adjrec = q4;
+  }
   TRY(dupload(c, &ip, slot_self)); n.slot_self = ip;
   TRY(dupload(c, &ip, slot_adj)); n.slot_adj = ip;
   TRY(dupload(c, &c->tmap, tmap));
@@ -283,6 +298,113 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &c->task_map_off, task_map_off));
   TRY(dupload(c, &c->task_map, task_map));
   TRY(dupload(c, &c->ubus, ubus));
+  {
+    // elimination tree of L (parent of column j = first row below j with L_ij != 0)
+    std::vector<int> par(nx, -1);
+    for (int i = 0; i < nx; i++)
+      for (int p = s.rp[i]; p < s.dp[i]; p++) {
+        const int j = s.ci[p];
+        if (par[j] < 0 || i < par[j]) par[j] = i;
+      }
+    TRY(dupload(c, &ip, par));
+    n.eparent = ip;
+    // full-Hessian column order: v_ref, then (v_k, p_k) of the PV buses in the
+    // postorder of their theta rows, so that a tile's right-hand sides sit in
+    // one subtree and the first triangular solve reaches few rows
+    std::vector<int> kid_ptr(nx + 1, 0), kids(nx), post(nx, 0);
+    for (int j = 0; j < nx; j++)
+      if (par[j] >= 0) kid_ptr[par[j] + 1]++;
+    for (int j = 0; j < nx; j++) kid_ptr[j + 1] += kid_ptr[j];
+    {
+      std::vector<int> fill(kid_ptr.begin(), kid_ptr.end() - 1);
+      for (int j = 0; j < nx; j++)
+        if (par[j] >= 0) kids[fill[par[j]]++] = j;
+    }
+    int cnt = 0;
+    std::vector<std::pair<int, int>> stack;
+    for (int r = nx - 1; r >= 0; r--) {
+      if (par[r] >= 0) continue;
+      stack.push_back({r, 0});
+      while (!stack.empty()) {
+        auto& top = stack.back();
+        const int v = top.first, k = kid_ptr[v] + top.second;
+        if (k < kid_ptr[v + 1]) {
+          top.second++;
+          stack.push_back({kids[k], 0});
+        } else {
+          post[v] = cnt++;
+          stack.pop_back();
+        }
+      }
+    }
+    std::vector<int> pvb;
+    for (int i = 0; i < nb; i++)
+      if (h.type[i] == opf::PV) pvb.push_back(i);
+    std::stable_sort(pvb.begin(), pvb.end(), [&](int a, int b) { return post[pth[a]] < post[pth[b]]; });
+    std::vector<int> perm_cols;
+    perm_cols.push_back(h.uv[h.ref]);
+    for (int b : pvb) {
+      perm_cols.push_back(h.uv[b]);
+      perm_cols.push_back(h.up[b]);
+    }
+    // rows of the right-hand side -G_u e_j of each control (as the tile kernel scatters them)
+    auto rhs_rows = [&](int j, std::vector<int>& out) {
+      const int k = ubus[j];
+      if (j >= 1 + h.npv) {
+        out.push_back(pth[k]);
+        return;
+      }
+      for (int q = h.adj_ptr[k]; q < h.adj_ptr[k + 1]; q++) {
+        const int e = h.adj[q], l = e >> 1, o = (e & 1) ? h.f[l] : h.t[l];
+        if (h.type[o] != opf::REF) out.push_back(pth[o]);
+        if (h.type[o] == opf::PQ) out.push_back(pvv[o]);
+      }
+      if (h.type[k] == opf::PV) out.push_back(pth[k]);
+    };
+    // per block width: near-equal chunks of the order (as many tiles as a whole
+    // number of waves over the SMs when that keeps tiles at least half full),
+    // heaviest first by the reach of their first solve
+    std::vector<int> stamp(nx, -1), rows;
+    int stamp_id = 0;
+    for (int lk = 0; lk < 6; lk++)
+      for (int form = 0; form < 2; form++) {
+        const int C = 1 << lk, nu = h.nu, T0 = (nu + C - 1) / C;
+        int T = T0;
+        if (form == 1 && T0 >= c->sm_count) {
+          const int Tr = (T0 + c->sm_count - 1) / c->sm_count * c->sm_count;
+          if (2 * nu >= Tr * C) T = Tr;
+        }
+        if (form == 1 && T == T0) {  // same tiling as the ceil form
+          c->colmap[1][lk] = c->colmap[0][lk];
+          c->coltiles[1][lk] = T0;
+          continue;
+        }
+        std::vector<int> start(T + 1, 0);
+        for (int t = 0; t < T; t++) start[t + 1] = start[t] + (form ? nu / T + (t < nu % T ? 1 : 0) : C);
+        start[T] = nu;
+        std::vector<std::pair<int, int>> cost(T);
+        for (int t = 0; t < T; t++) {
+          int reach = 0;
+          rows.clear();
+          for (int q = start[t]; q < start[t + 1]; q++) rhs_rows(perm_cols[q], rows);
+          stamp_id++;
+          for (int r : rows)
+            for (int x = r; x >= 0 && stamp[x] != stamp_id; x = par[x]) {
+              stamp[x] = stamp_id;
+              reach++;
+            }
+          cost[t] = {-reach, t};
+        }
+        std::stable_sort(cost.begin(), cost.end());
+        std::vector<int> map((size_t)T * C, -1);
+        for (int t = 0; t < T; t++) {
+          const int src = cost[t].second;
+          for (int q = start[src]; q < start[src + 1]; q++) map[(size_t)t * C + (q - start[src])] = perm_cols[q];
+        }
+        TRY(dupload(c, &c->colmap[form][lk], map));
+        c->coltiles[form][lk] = T;
+      }
+  }
   TRY(dupload(c, &c->pd_nom, h.pd));
   TRY(dupload(c, &c->qd_nom, h.qd));
   // workspaces
@@ -311,10 +433,13 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->lam, nx));
   TRY(dalloc(c, &c->btab, 26 * (size_t)nl));
   TRY(dalloc(c, &c->busw, 8 * (size_t)nb));
+  TRY(dalloc(c, &c->adjE, ADJ_W * 2 * (size_t)nl));
+  TRY(dalloc(c, &c->busS, 4 * (size_t)nb));
   CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
   TRY(setup_solve1(c));
+  setup_hvp_smem();
   // the numeric refactorisation as one CUDA graph (captured once on a private stream)
   CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   {
@@ -574,15 +699,15 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
     FAIL(OPF_EINVAL, "block_k must be 1, 2, 4, 8, 16 or 32");
   const int nt = (o && o->threads) ? o->threads : (tuned ? c->tuned_threads : 256);
-  if (nt != 256 && nt != 512) FAIL(OPF_EINVAL, "threads must be 256 or 512");
+  if (nt != 128 && nt != 256 && nt != 512) FAIL(OPF_EINVAL, "threads must be 128, 256 or 512");
   c->hvp_threads = nt;
   const bool plain = o && o->plain;
   const int nu = c->h.nu;
   const int col0 = o ? o->col_begin : 0;
   const int ncol = (o && o->col_count > 0) ? o->col_count : nu - col0;
   if (col0 < 0 || col0 >= nu || ncol < 1 || col0 + ncol > nu) FAIL(OPF_EINVAL, "column range outside [0, n_u)");
-  const int ntiles = (ncol + C - 1) / C;
-  int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : std::min(ntiles, 4 * c->sm_count));
+  const int ntiles = hvp_tiles(c, C, col0, col0 + ncol, true);
+  int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : std::min(ntiles, hvp_occupancy(C, nt) * c->sm_count));
   grid = std::max(1, std::min(grid, ntiles));
   TRY(ensure_scratch(c, hvp_stride(c, C) * (size_t)grid));
   cudaStream_t st = c->stream;
@@ -667,7 +792,7 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     launch_first_order(c, &params[k], nullptr);
     launch_hess_prep(c, params[k].sigma_f);
     c->stream = keep;
-    args[k] = make_hvp_args(c, C, H[k], 0, c->h.nu);
+    args[k] = make_hvp_args(c, C, H[k], 0, c->h.nu, false);
   }
   // tile queue: contexts by decreasing factor size (longest processing time first)
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -701,7 +826,9 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
   grid = std::max(1, std::min(grid, ntot));
   TRY(ensure_scratch(c0, stride * (size_t)grid));
   CK(cudaEventRecord(c0->ev[1], st));
-  launch_hvp_batch(st, C, d_args, d_tiles, ntot, d_counter, c0->scratch, stride, grid);
+  size_t smem = 0;
+  for (int k = 0; k < n; k++) smem = std::max(smem, hvp_smem_bytes(args[k], C));
+  launch_hvp_batch(st, C, d_args, d_tiles, ntot, d_counter, c0->scratch, stride, grid, smem);
   c0->launches++;
   CK(cudaEventRecord(c0->ev[2], st));
   CK(cudaStreamSynchronize(st));

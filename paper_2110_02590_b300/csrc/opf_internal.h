@@ -17,6 +17,16 @@ namespace opf {
 #define TAB_DP(s, k) (10 + 4 * (s) + (k))
 #define TAB_DQ(s, k) (18 + 4 * (s) + (k))
 
+// Per-adjacency coefficient record (bus i at end s of branch l, o the other
+// end), ADJ_W doubles.  The branch functions depend on the angles only through
+// theta_s - theta_o, so every theta_o derivative is the negated theta_s one.
+// E_VO, E_VT, E_TO, E_TT: second derivatives of l in the rows of v_s / theta_s
+// against v_o / theta_s; E_QO*, E_PO*: dQ_o, dP_o w.r.t. (v_s, theta_s);
+// E_QS*, E_PS*: dQ_s, dP_s w.r.t. (v_s, v_o, theta_s); E_VV: d2l/dv_s^2.
+#define ADJ_W 16
+enum AdjField { E_VO = 0, E_VT = 1, E_TO = 2, E_TT = 3, E_QOV = 4, E_QOT = 5, E_POV = 6, E_POT = 7,
+                E_QSV = 8, E_QSO = 9, E_QST = 10, E_PSV = 11, E_PSO = 12, E_PST = 13, E_VV = 14 };
+
 enum BusType { REF = 0, PV = 1, PQ = 2 };
 
 // Host-side network with index maps (eq. statecontrol).
@@ -62,19 +72,37 @@ struct DevNet {
   int r0, nroot;
   const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
   const int* slot_adj;             // [4 * 2 nl]
+  // direction records of the HVP gathers.  A direction slot z >= 0 is the
+  // pivot-order row holding the value; z <= -2 encodes a control unit vector
+  // (the value is 1 in the column of control -2 - z, else 0); -1 means none.
+  const int* eparent;              // [nx] elimination-tree parent of each pivot row (-1 at a root)
+  const int4* busrec;              // [nb]: {v slot, theta slot, control-bus index or -1, up or -1}
+  const int4* adjrec;              // [2 nl], adjacency order: the other end's {v slot, theta slot,
+                                   //   control-bus index or -1, 1 if it is the slack}
 };
 
 // Arguments of the HVP tile kernels (one network, one Hessian).
 struct HvpArgs {
   DevNet n;
   const double *LU, *T, *invdiag, *tab, *busw;
+  const double* adjE;  // [2 nl][ADJ_W] per-adjacency coefficients
+  const double* busS;  // [nb] x 4 per-bus coefficient sums
   const int* ubus;  // bus of each control
+  const int* colmap;  // null: tile position p is column col0 + p; else column colmap[p] (-1: none)
   double* H;
   double* scratch;
   size_t stride;    // doubles of scratch per CTA
   int ntiles, first_tile, tile_step;
   int col0, col_end;  // columns computed: col0 .. col_end - 1
+  // dynamic shared memory of the tile (hvp_smem_bytes): reached-row values
+  // [zs_cap][C], reach mask and its word prefix [rm_words] each, reach list [list_cap]
+  int zs_cap, rm_words, list_cap;
 };
+
+// Dynamic shared memory of the HVP tile kernels (bytes; opted in at load).
+constexpr int HVP_DYN_SMEM = 56 * 1024;
+size_t hvp_smem_bytes(const HvpArgs& a, int C);
+void setup_hvp_smem();
 
 // kernel launchers (opf_kernels.cu)
 void launch_unpack(opf_ctx* c, const double* x, const double* u);
@@ -94,10 +122,13 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
                         int col_end);
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
-HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end);
+// balanced: the single-network launch (tiles in whole waves over the SMs)
+HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced);
+int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  // tiles of a column range
 int hvp_batch_occupancy(int C);  // resident CTAs per SM of the batched tile kernel
+int hvp_occupancy(int C, int nt);  // resident CTAs per SM of hvp_tile_kernel<C, nt>
 bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
-                      double* scratch, size_t stride, int grid);
+                      double* scratch, size_t stride, int grid, size_t smem);
 // J^T w for the reduced constraint Jacobian: the adjoint gradient with first-order
 // weights w and no cost (sigma_f = 0); needs the flows of the current state.
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
@@ -128,6 +159,12 @@ struct opf_ctx {
   double *x = nullptr, *u = nullptr, *pd = nullptr, *qd = nullptr;
   double *pd_nom = nullptr, *qd_nom = nullptr, *c0 = nullptr;
   int* ubus = nullptr;            // bus of each control (v_ref, v_pv, p_pv)
+  // full-Hessian tilings, per block width C = 1 << k and form f (0: ceil(n_u / C)
+  // tiles, for the batched launch; 1: whole waves over the SMs when the tiles
+  // stay at least half full): colmap[f][k] holds coltiles[f][k] x C columns
+  // (-1 = idle lane), heaviest tiles first
+  int* colmap[2][6] = {};
+  int coltiles[2][6] = {};
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
   double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...
@@ -143,6 +180,8 @@ struct opf_ctx {
   double *dFx = nullptr, *dFu = nullptr, *lam = nullptr;
   double *btab = nullptr;         // [26 nl] per-branch Hessian table
   double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
+  double* adjE = nullptr;         // [2 nl][ADJ_W] per-adjacency coefficients of the HVP gathers
+  double* busS = nullptr;         // [nb] x 4: per-bus sums of E_VV (+ omega of v_pq), E_VT, E_TT, 0
   int hvp_threads = 256;          // threads per HVP tile CTA
   int solve1_smem = 0;            // dynamic shared bytes of the single-RHS sweep
   bool solve1_use_smem_rhs = false;  // the right-hand side also lives in shared memory

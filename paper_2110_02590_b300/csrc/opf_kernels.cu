@@ -197,15 +197,16 @@ __global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, c
 
 // ------------------------------------------------------------ sweeps
 
-// Rows [p0, p1) of V against the slab: s = X[i] - sum V[p] X[ci[p]] (two partial sums
-// and four loads in flight per lane group).
+// Rows [p0, p1) of V against the slab: s = X[i] - sum V[p] X[ci[p]] (two partial
+// sums, four loads in flight per lane group; a ragged tail of one to three
+// entries is loaded in one batch, absent entries re-reading the first one).
 template <int C>
 __device__ __forceinline__ double row_dot(const DevNet& n, const double* __restrict__ V, const double* X,
                                           int i, int p0, int p1, int col) {
   double s0 = X[(size_t)i * C + col], s1 = 0.0;
   int p = p0;
   for (; p + 3 < p1; p += 4) {
-    const int c0 = n.ci[p], c1 = n.ci[p + 1], c2 = n.ci[p + 2], c3 = n.ci[p + 3];
+    const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + 1), c2 = __ldg(n.ci + p + 2), c3 = __ldg(n.ci + p + 3);
     const double v0 = V[p], v1 = V[p + 1], v2 = V[p + 2], v3 = V[p + 3];
     const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
     const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
@@ -214,7 +215,36 @@ __device__ __forceinline__ double row_dot(const DevNet& n, const double* __restr
     s0 -= v2 * x2;
     s1 -= v3 * x3;
   }
-  for (; p < p1; p++) s0 -= V[p] * X[(size_t)n.ci[p] * C + col];
+  const int r = p1 - p;
+  if (r > 0) {
+    const int q1 = p + (r > 1 ? 1 : 0), q2 = p + (r > 2 ? 2 : 0);
+    const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + q1), c2 = __ldg(n.ci + q2);
+    const double v0 = V[p], v1 = V[q1], v2 = V[q2];
+    const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col], x2 = X[(size_t)c2 * C + col];
+    s0 -= v0 * x0;
+    if (r > 1) s1 -= v1 * x1;
+    if (r > 2) s0 -= v2 * x2;
+  }
+  return s0 + s1;
+}
+
+// row_dot over the columns set in the bit mask only (the slab is zero on the
+// other columns).
+template <int C>
+__device__ __forceinline__ double row_dot_masked(const DevNet& n, const double* __restrict__ V, const double* X,
+                                                 int i, int p0, int p1, int col, const unsigned* mask) {
+  double s0 = X[(size_t)i * C + col], s1 = 0.0;
+  int p = p0;
+  for (; p + 1 < p1; p += 2) {
+    const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + 1);
+    const bool b0 = (mask[c0 >> 5] >> (c0 & 31)) & 1u, b1 = (mask[c1 >> 5] >> (c1 & 31)) & 1u;
+    if (b0) s0 -= V[p] * X[(size_t)c0 * C + col];
+    if (b1) s1 -= V[p + 1] * X[(size_t)c1 * C + col];
+  }
+  if (p < p1) {
+    const int c0 = __ldg(n.ci + p);
+    if ((mask[c0 >> 5] >> (c0 & 31)) & 1u) s0 -= V[p] * X[(size_t)c0 * C + col];
+  }
   return s0 + s1;
 }
 
@@ -223,10 +253,13 @@ __device__ __forceinline__ double row_dot(const DevNet& n, const double* __restr
 // (FWD: lower part of V, rows by ascending level; else the upper part).  The
 // dense block is solved as a dense triangle, one column per step: after x_j is
 // known every thread updates its (row, column) items below (FWD) or above it.
-// DIAG: multiply each row by 1/U_ii once its sum is complete.
+// DIAG: multiply each row by 1/U_ii once its sum is complete.  rmask (FWD
+// only): the rows below r0 are already final and the slab is zero outside the
+// rows set in the mask; only the trailing block remains.
 template <int C, bool FWD, bool DIAG>
 __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
-                                      const double* __restrict__ invdiag, double* X) {
+                                      const double* __restrict__ invdiag, double* X,
+                                      const unsigned* rmask = nullptr) {
   constexpr int RPW = 32 / C;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = lane % C;
@@ -250,43 +283,73 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
       __syncthreads();
     }
   }
-  const int nlev = FWD ? n.nlev_f : n.nlev_b;
+  const int nlev = (FWD && rmask) ? 0 : (FWD ? n.nlev_f : n.nlev_b);
   const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
   const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
   const int nwarps = blockDim.x >> 5, grp = lane / C;
+  // narrow level (at most one row per warp): one warp per row, its lane groups
+  // split the row; else one lane group per row
+  auto first_k = [&](int b, int e) { return (e - b <= nwarps && RPW > 1) ? b + warp : b + myslot; };
+  const int4 none = make_int4(0, 0, 0, 0);
+  int b = nlev > 0 ? lptr[0] : 0, e = nlev > 0 ? lptr[1] : 0;
+  int k0 = first_k(b, e);
+  int4 mt = k0 < e ? __ldg(lmeta + k0) : none;
   for (int lv = 0; lv < nlev; lv++) {
-    const int b = lptr[lv], e = lptr[lv + 1];
+    // the next level's bounds and this thread's first record of it do not
+    // depend on the slab: load them before this level's work
+    const int bn = e, en = (lv + 1 < nlev) ? lptr[lv + 2] : e;
+    const int kn0 = first_k(bn, en);
+    const int4 mtn = kn0 < en ? __ldg(lmeta + kn0) : none;
     if (e - b <= nwarps && RPW > 1) {
-      // narrow level: one warp per row, its lane groups split the row, shuffle reduction
-      for (int k = b + warp; k < e; k += nwarps) {
-        const int4 mt = lmeta[k];
-        const int i = mt.x, p0 = mt.y, p1 = mt.z;
-        double v = 0.0;
-        for (int p = p0 + grp; p < p1; p += RPW) v -= V[p] * X[(size_t)n.ci[p] * C + col];
+      for (int k = k0; k < e; k += nwarps) {
+        const int4 m = (k == k0) ? mt : __ldg(lmeta + k);
+        const int i = m.x, p1 = m.z;
+        const double xi = X[(size_t)i * C + col];
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int p = m.y + grp;
+        for (; p + 3 * RPW < p1; p += 4 * RPW) {
+          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + RPW), c2 = __ldg(n.ci + p + 2 * RPW),
+                    c3 = __ldg(n.ci + p + 3 * RPW);
+          const double a0 = V[p], a1 = V[p + RPW], a2 = V[p + 2 * RPW], a3 = V[p + 3 * RPW];
+          const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
+          const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
+          v0 -= a0 * x0;
+          v1 -= a1 * x1;
+          v2 -= a2 * x2;
+          v3 -= a3 * x3;
+        }
+        for (; p < p1; p += RPW) v0 -= V[p] * X[(size_t)__ldg(n.ci + p) * C + col];
+        double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
         for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (grp == 0) {
-          v += X[(size_t)i * C + col];
+          v += xi;
           if (DIAG) v *= invdiag[i];
           X[(size_t)i * C + col] = v;
         }
       }
     } else {
-      for (int k = b + myslot; k < e; k += nslots) {
-        const int4 mt = lmeta[k];
-        const int i = mt.x;
-        double v = row_dot<C>(n, V, X, i, mt.y, mt.z, col);
-        if (DIAG) v *= invdiag[i];
-        X[(size_t)i * C + col] = v;
+      for (int k = k0; k < e; k += nslots) {
+        const int4 m = mt;
+        if (k + nslots < e) mt = __ldg(lmeta + k + nslots);  // next row's record in flight
+        if (!DIAG && m.y == m.z) continue;                   // no entries: the row is final
+        double v = row_dot<C>(n, V, X, m.x, m.y, m.z, col);
+        if (DIAG) v *= invdiag[m.x];
+        X[(size_t)m.x * C + col] = v;
       }
     }
     __syncthreads();
+    b = bn;
+    e = en;
+    k0 = kn0;
+    mt = mtn;
   }
   if (FWD) {
     // off-block part of the trailing rows (columns < r0), all rows in parallel
     for (int k = myslot; k < s; k += nslots) {
       const int i = r0 + k;
-      X[(size_t)i * C + col] = row_dot<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col);
+      X[(size_t)i * C + col] = rmask ? row_dot_masked<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col, rmask)
+                                     : row_dot<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col);
     }
     __syncthreads();
     // dense lower triangle
@@ -727,34 +790,74 @@ __global__ void bus_weight_kernel(DevNet n, const double* om, double sigma_f, do
 }
 
 // Rows 4..7 of the bus weights: dQ_i/dv_i, dQ_i/dtheta_i, dP_i/dv_i, dP_i/dtheta_i
-// (sums over the incident branch ends, from the branch table).
-__global__ void bus_self_grad_kernel(DevNet n, const double* tab, double* w) {
+// (sums over the incident branch ends, from the branch table), and the
+// per-adjacency coefficient records of the HVP gathers.
+__global__ void bus_self_grad_kernel(DevNet n, const double* tab, double* w, double* adjE, double* busS) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n.nb) return;
   const int nl = n.nl, nb = n.nb;
-  double qv = 0, qt = 0, pv = 0, pt = 0;
+  double qv = 0, qt = 0, pv = 0, pt = 0, svv = w[2 * nb + i], svt = 0, stt = 0;
   for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
-    const int e = n.adj[q], l = e >> 1, s = e & 1;
-    qv += tab[(size_t)TAB_DQ(s, s) * nl + l];
-    qt += tab[(size_t)TAB_DQ(s, 2 + s) * nl + l];
-    pv += tab[(size_t)TAB_DP(s, s) * nl + l];
-    pt += tab[(size_t)TAB_DP(s, 2 + s) * nl + l];
+    const int e = n.adj[q], l = e >> 1, s = e & 1, o = 1 - s;
+    const double qss = tab[(size_t)TAB_DQ(s, s) * nl + l], qst = tab[(size_t)TAB_DQ(s, 2 + s) * nl + l];
+    const double pss = tab[(size_t)TAB_DP(s, s) * nl + l], pst = tab[(size_t)TAB_DP(s, 2 + s) * nl + l];
+    qv += qss;
+    qt += qst;
+    pv += pss;
+    pt += pst;
+    double E[ADJ_W];
+    E[E_VV] = tab[(size_t)pk(s, s) * nl + l];
+    E[E_VO] = tab[(size_t)pk(s, o) * nl + l];
+    E[E_VT] = tab[(size_t)pk(s, 2 + s) * nl + l];
+    E[E_TO] = tab[(size_t)pk(2 + s, o) * nl + l];
+    E[E_TT] = tab[(size_t)pk(2 + s, 2 + s) * nl + l];
+    E[E_QOV] = tab[(size_t)TAB_DQ(o, s) * nl + l];
+    E[E_QOT] = tab[(size_t)TAB_DQ(o, 2 + s) * nl + l];
+    E[E_POV] = tab[(size_t)TAB_DP(o, s) * nl + l];
+    E[E_POT] = tab[(size_t)TAB_DP(o, 2 + s) * nl + l];
+    E[E_QSV] = qss;
+    E[E_QSO] = tab[(size_t)TAB_DQ(s, o) * nl + l];
+    E[E_QST] = qst;
+    E[E_PSV] = pss;
+    E[E_PSO] = tab[(size_t)TAB_DP(s, o) * nl + l];
+    E[E_PST] = pst;
+    E[15] = 0.0;
+    svv += E[E_VV];
+    svt += E[E_VT];
+    stt += E[E_TT];
+    double2* dst = reinterpret_cast<double2*>(adjE + (size_t)q * ADJ_W);
+#pragma unroll
+    for (int k = 0; k < ADJ_W / 2; k++) dst[k] = make_double2(E[2 * k], E[2 * k + 1]);
   }
   w[4 * nb + i] = qv;
   w[5 * nb + i] = qt;
   w[6 * nb + i] = pv;
   w[7 * nb + i] = pt;
+  reinterpret_cast<double4_32a*>(busS)[i] = make_double4_32a(svv, svt, stt, 0.0);
 }
 
 // ------------------------------------------------------------ HVP tiles
 
 
 
+// Value of a direction slot (see DevNet::busrec) in column c (control j).
 template <int C>
-__device__ __forceinline__ void direction(const DevNet& n, const double* Z, int b, int c, int j,
-                                          double& vd, double& td) {
-  vd = (n.type[b] == PQ) ? Z[(size_t)n.pvv[b] * C + c] : ((n.uv[b] == j) ? 1.0 : 0.0);
-  td = (n.type[b] == REF) ? 0.0 : Z[(size_t)n.pth[b] * C + c];
+__device__ __forceinline__ double dslot(const double* Z, int z, int c, int j) {
+  return z >= 0 ? Z[(size_t)z * C + c] : ((-2 - z) == j ? 1.0 : 0.0);
+}
+
+// The other ends' direction values of up to four adjacency entries qb.. of a
+// bus (entries at or past q1 read as zero), all loads issued together.
+template <int C>
+__device__ __forceinline__ void adj_dirs4(const DevNet& n, const double* Z, int qb, int q1, int c, int j,
+                                          int4 (&ar)[4], double (&vo)[4], double (&to)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; u++) ar[u] = (qb + u < q1) ? n.adjrec[qb + u] : make_int4(-1, -1, -1, 0);
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    vo[u] = dslot<C>(Z, ar[u].x, c, j);
+    to[u] = ar[u].y >= 0 ? Z[(size_t)ar[u].y * C + c] : 0.0;
+  }
 }
 
 // One tile of C Hessian columns on one CTA: B = -G_u W, Z = G_x^{-1} B,
@@ -763,105 +866,324 @@ __device__ __forceinline__ void direction(const DevNet& n, const double* Z, int 
 template <int C>
 __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) {
   const DevNet& n = a.n;
-  const int nl = n.nl, nb = n.nb, nu = n.nu, jend = a.col_end;
+  const int nb = n.nb, nu = n.nu;
   double* R = Z + (size_t)n.nx * C;
   double* QD = R + (size_t)n.nx * C;
   double* PD = QD + (size_t)n.ngn * C;
-  const double* tab = a.tab;
+  const double* __restrict__ E = a.adjE;
+  const double* __restrict__ bw = a.busw;
+  // reach of the first triangular solve (dynamic shared memory): values of the
+  // reached rows, bit mask over the rows below the trailing block with the
+  // per-word prefix counts (the rank of a reached row), reached rows ascending
+  extern __shared__ __align__(16) unsigned char hvp_dyn[];
+  double* s_zs = reinterpret_cast<double*>(hvp_dyn);
+  unsigned* s_mask = reinterpret_cast<unsigned*>(s_zs + (size_t)a.zs_cap * C);
+  int* s_pre = reinterpret_cast<int*>(s_mask + a.rm_words);
+  int* s_list = s_pre + a.rm_words;
+  __shared__ int s_col[32];
+  __shared__ int s_nl;
+  __shared__ double s_part[2][16][32];  // per-warp partial row sums (<= 512 threads)
+  const int r0 = n.r0, nwords = (r0 + 31) >> 5;
+  const bool prune = nwords <= a.rm_words;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   {
-    const int j0 = a.col0 + tile * C;
-    // (0) right-hand side B = -G_u W, W = unit directions j0 .. j0 + C - 1
+    // column of each lane of the tile (NOCOL past the requested range)
+    constexpr int NOCOL = -(1 << 30);
+    if (threadIdx.x < C) {
+      if (a.colmap) {
+        const int j = a.colmap[tile * C + threadIdx.x];
+        s_col[threadIdx.x] = j < 0 ? NOCOL : j;
+      } else {
+        const int pos = a.col0 + tile * C + threadIdx.x;
+        s_col[threadIdx.x] = pos >= a.col_end ? NOCOL : pos;
+      }
+    }
+    // (0) right-hand side B = -G_u W, W = unit directions of the tile's columns
     for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+    if (prune)
+      for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
     __syncthreads();
+    auto mark = [&](int r) {
+      if (prune && r < r0) atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+    };
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
-      const int j = j0 + c;
-      if (j >= jend) continue;
+      const int j = s_col[c];
+      if (j < 0) continue;
       const int k = a.ubus[j];
       if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
         Z[(size_t)n.pth[k] * C + c] = 1.0;
+        mark(n.pth[k]);
         continue;
       }
-      double selfP = 0.0;
       for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
-        if (n.type[o] != REF) Z[(size_t)n.pth[o] * C + c] -= tab[(size_t)TAB_DP(1 - s, s) * nl + l];
-        if (n.type[o] == PQ) Z[(size_t)n.pvv[o] * C + c] -= tab[(size_t)TAB_DQ(1 - s, s) * nl + l];
-        selfP += tab[(size_t)TAB_DP(s, s) * nl + l];
-      }
-      if (n.type[k] == PV) Z[(size_t)n.pth[k] * C + c] -= selfP;
-    }
-    __syncthreads();
-    // (1)-(2) first second-order adjoint: L then U sweeps
-    sweep<C, true, false>(n, a.LU, a.invdiag, Z);
-    sweep<C, false, true>(n, a.LU, a.invdiag, Z);
-    // (3) directional derivatives of Q (slack and PV) and P (slack) for the Gauss-Newton terms
-    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
-      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = j0 + c;
-      double qd = 0.0, pdr = 0.0;
-      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-        const int e = n.adj[q], l = e >> 1, s = e & 1;
-        double d[4];
-        direction<C>(n, Z, n.f[l], c, j, d[0], d[2]);
-        direction<C>(n, Z, n.t[l], c, j, d[1], d[3]);
-#pragma unroll
-        for (int t = 0; t < 4; t++) qd += tab[(size_t)TAB_DQ(s, t) * nl + l] * d[t];
-        if (k == n.ref) {
-#pragma unroll
-          for (int t = 0; t < 4; t++) pdr += tab[(size_t)TAB_DP(s, t) * nl + l] * d[t];
+        const int4 ar = n.adjrec[q];
+        if (ar.y >= 0) {
+          Z[(size_t)ar.y * C + c] -= E[(size_t)q * ADJ_W + E_POV];
+          mark(ar.y);
+        }
+        if (ar.x >= 0) {
+          Z[(size_t)ar.x * C + c] -= E[(size_t)q * ADJ_W + E_QOV];
+          mark(ar.x);
         }
       }
-      QD[(size_t)gi * C + c] = qd;
-      if (k == n.ref) PD[c] = pdr;
+      if (n.type[k] == PV) {
+        Z[(size_t)n.pth[k] * C + c] -= bw[6 * nb + k];
+        mark(n.pth[k]);
+      }
     }
     __syncthreads();
-    // (4) y = (grad^2 l) (z; w) per bus; R = -y_x, H[u rows] = y_u
-    for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
-      const int i = it / C, c = it % C, j = j0 + c;
-      double vi, ti;
-      direction<C>(n, Z, i, c, j, vi, ti);
-      double yv = 0.0, yt = 0.0;
-      for (int q = n.adj_ptr[i]; q < n.adj_ptr[i + 1]; q++) {
-        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
-        double vo, to;
-        direction<C>(n, Z, o, c, j, vo, to);
-        const double d[4] = {s ? vo : vi, s ? vi : vo, s ? to : ti, s ? ti : to};
-        const int rv = s, rt = 2 + s;
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-          yv += tab[(size_t)pk(rv, t) * nl + l] * d[t];
-          yt += tab[(size_t)pk(rt, t) * nl + l] * d[t];
-        }
-        const int go = n.gn_of[o];
-        if (go >= 0) {
-          const double w = a.busw[o] * QD[(size_t)go * C + c];
-          yv += w * tab[(size_t)TAB_DQ(1 - s, rv) * nl + l];
-          yt += w * tab[(size_t)TAB_DQ(1 - s, rt) * nl + l];
-          if (o == n.ref) {
-            const double w2 = a.busw[nb + o] * PD[c];
-            yv += w2 * tab[(size_t)TAB_DP(1 - s, rv) * nl + l];
-            yt += w2 * tab[(size_t)TAB_DP(1 - s, rt) * nl + l];
+    // (1) Z = L^{-1} B.  The solution is nonzero only on the elimination-tree
+    // ancestors of the right-hand side's rows: mark them, list them in
+    // ascending order, and let one warp solve those rows one after another
+    // (no block-wide barrier); the trailing block follows as usual.
+    int nl = a.list_cap + 1;
+    if (prune) {
+      for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+        unsigned bits = s_mask[w];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          int x = n.eparent[w * 32 + b];
+          while (x >= 0 && x < r0) {  // parents increase: the walk ends
+            const unsigned m = 1u << (x & 31);
+            if (atomicOr(&s_mask[x >> 5], m) & m) break;  // the row's walk is someone else's
+            x = n.eparent[x];
           }
         }
       }
-      const int gi = n.gn_of[i];
-      if (gi >= 0) {  // own injections: the gradients dQ_i, dP_i w.r.t. (v_i, theta_i) are per-bus sums
-        const double w = a.busw[i] * QD[(size_t)gi * C + c];
-        yv += w * a.busw[4 * nb + i];
-        yt += w * a.busw[5 * nb + i];
-        if (i == n.ref) {
-          const double w2 = a.busw[nb + i] * PD[c];
-          yv += w2 * a.busw[6 * nb + i];
-          yt += w2 * a.busw[7 * nb + i];
+      __syncthreads();
+      if (warp == 0) {
+        int base = 0;
+        for (int w0 = 0; w0 < nwords; w0 += 32) {
+          const int w = w0 + lane;
+          const unsigned bits = w < nwords ? s_mask[w] : 0u;
+          const int cnt = __popc(bits);
+          int incl = cnt;
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+          }
+          int pos = base + incl - cnt;
+          if (w < nwords) s_pre[w] = pos;
+          unsigned bb = bits;
+          while (bb) {
+            const int b = __ffs(bb) - 1;
+            bb &= bb - 1;
+            if (pos < a.list_cap) s_list[pos] = w * 32 + b;
+            pos++;
+          }
+          base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) s_nl = base;
+      }
+      __syncthreads();
+      nl = s_nl;
+    }
+    const int ngrp = blockDim.x / C, g = threadIdx.x / C, nwarp = blockDim.x >> 5;
+    const double* __restrict__ Vl = a.LU;
+    if (nl <= a.zs_cap) {
+      // one reached row at a time over the whole CTA with the reached values in
+      // shared memory: the lane groups split the row (four entries each per
+      // batch, the next row's first batch and extents loaded ahead), warps
+      // reduce by shuffles, every warp sums the per-warp partials
+      // (double-buffered, one barrier per row) and stores the row (identical
+      // values from every warp)
+      const int col = threadIdx.x % C;
+      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
+        s_zs[idx] = Z[(size_t)s_list[idx / C] * C + idx % C];
+      __syncthreads();
+      auto extent = [&](int t) {
+        return t < nl ? make_int2(n.rp[s_list[t]], n.dp[s_list[t]]) : make_int2(0, 0);
+      };
+      auto load4 = [&](int p, int pe, int (&cs)[4], double (&vs)[4]) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int q = p + u * ngrp;
+          cs[u] = q < pe ? __ldg(n.ci + q) : -1;
+          vs[u] = q < pe ? Vl[q] : 0.0;
+        }
+      };
+      auto acc4 = [&](const int (&cs)[4], const double (&vs)[4], double& v) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (cs[u] >= 0) {
+            const int w = cs[u] >> 5;
+            const unsigned m = s_mask[w], bit = 1u << (cs[u] & 31);
+            if (m & bit) v -= vs[u] * s_zs[(size_t)(s_pre[w] + __popc(m & (bit - 1u))) * C + col];
+          }
+        }
+      };
+      int2 e0 = extent(0), e1 = extent(1);
+      int cs[4];
+      double vs[4];
+      load4(e0.x + g, e0.y, cs, vs);
+      for (int t = 0; t < nl; t++) {
+        const int i = s_list[t];
+        const int2 e2 = extent(t + 2);
+        int csn[4];
+        double vsn[4];
+        load4(e1.x + g, e1.y, csn, vsn);
+        double v = 0.0;
+        acc4(cs, vs, v);
+        for (int p = e0.x + g + 4 * ngrp; p < e0.y; p += 4 * ngrp) {  // rows longer than one batch
+          int cb[4];
+          double vb[4];
+          load4(p, e0.y, cb, vb);
+          acc4(cb, vb, v);
+        }
+#pragma unroll
+        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane < C) s_part[t & 1][warp][lane] = v;
+        const double zi = lane < C ? s_zs[(size_t)t * C + lane] : 0.0;  // read before any warp overwrites it
+        __syncthreads();
+        if (lane < C) {
+          double sum = zi;
+          for (int w = 0; w < nwarp; w++) sum += s_part[t & 1][w][lane];
+          s_zs[(size_t)t * C + lane] = sum;
+          if (warp == 0) Z[(size_t)i * C + lane] = sum;
+        }
+        __syncwarp();
+        e0 = e1;
+        e1 = e2;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          cs[u] = csn[u];
+          vs[u] = vsn[u];
         }
       }
-      if (n.type[i] == PQ) yv += a.busw[2 * nb + i] * vi;
-      if (n.type[i] != REF) R[(size_t)n.pth[i] * C + c] = -yt;
-      if (n.type[i] == PQ) {
-        R[(size_t)n.pvv[i] * C + c] = -yv;
-      } else if (j < jend) {
+    }
+    if (nl > a.zs_cap && nl <= a.list_cap) {
+      // the same with the reached values in the slab
+      const int col = threadIdx.x % C;
+      const double* __restrict__ V = Vl;
+      int pn0 = 0, pn1 = 0;
+      if (nl > 0) {
+        pn0 = n.rp[s_list[0]];
+        pn1 = n.dp[s_list[0]];
+      }
+      for (int t = 0; t < nl; t++) {
+        const int i = s_list[t], p0 = pn0, p1 = pn1;
+        if (t + 1 < nl) {  // the next row's extent, in flight during this row
+          pn0 = n.rp[s_list[t + 1]];
+          pn1 = n.dp[s_list[t + 1]];
+        }
+        double v0 = 0.0, v1 = 0.0;
+        int p = p0 + g;
+        for (; p + ngrp < p1; p += 2 * ngrp) {
+          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + ngrp);
+          const bool b0 = (s_mask[c0 >> 5] >> (c0 & 31)) & 1u, b1 = (s_mask[c1 >> 5] >> (c1 & 31)) & 1u;
+          if (b0) v0 -= V[p] * Z[(size_t)c0 * C + col];
+          if (b1) v1 -= V[p + ngrp] * Z[(size_t)c1 * C + col];
+        }
+        if (p < p1) {
+          const int c0 = __ldg(n.ci + p);
+          if ((s_mask[c0 >> 5] >> (c0 & 31)) & 1u) v0 -= V[p] * Z[(size_t)c0 * C + col];
+        }
+        double v = v0 + v1;
+#pragma unroll
+        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane < C) s_part[t & 1][warp][lane] = v;
+        // the row's right-hand side, read before any warp overwrites it
+        const double zi = lane < C ? Z[(size_t)i * C + lane] : 0.0;
+        __syncthreads();
+        if (lane < C) {
+          double sum = zi;
+          for (int w = 0; w < nwarp; w++) sum += s_part[t & 1][w][lane];
+          Z[(size_t)i * C + lane] = sum;
+        }
+        __syncwarp();
+      }
+    }
+    if (nl <= a.list_cap) {
+      __syncthreads();
+      sweep<C, true, false>(n, a.LU, a.invdiag, Z, s_mask);
+    } else {
+      sweep<C, true, false>(n, a.LU, a.invdiag, Z);
+    }
+    // (2) U sweep
+    sweep<C, false, true>(n, a.LU, a.invdiag, Z);
+    // (3) directional derivatives of Q (slack and PV) and P (slack) for the
+    // Gauss-Newton terms, stored pre-multiplied by their weights kQ, kP.  The
+    // own-variable parts are the per-bus sums dQ_k/dv_k, dQ_k/dtheta_k, ...
+    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
+      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = s_col[c];
+      const int4 bk = n.busrec[k];
+      const double vk = dslot<C>(Z, bk.x, c, j), tk = bk.y >= 0 ? Z[(size_t)bk.y * C + c] : 0.0;
+      const bool slack = (k == n.ref);
+      double qd = bw[4 * nb + k] * vk + bw[5 * nb + k] * tk, pdr = 0.0;
+      if (slack) pdr = bw[6 * nb + k] * vk + bw[7 * nb + k] * tk;
+      const int q1 = n.adj_ptr[k + 1];
+      for (int qb = n.adj_ptr[k]; qb < q1; qb += 4) {
+        int4 ar[4];
+        double vo[4], to[4];
+        adj_dirs4<C>(n, Z, qb, q1, c, j, ar, vo, to);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (qb + u < q1) {
+            const double* e = E + (size_t)(qb + u) * ADJ_W;
+            qd += e[E_QSO] * vo[u] - e[E_QST] * to[u];
+            if (slack) pdr += e[E_PSO] * vo[u] - e[E_PST] * to[u];
+          }
+        }
+      }
+      QD[(size_t)gi * C + c] = bw[k] * qd;
+      if (slack) PD[c] = bw[nb + k] * pdr;
+    }
+    __syncthreads();
+    // (4) y = (grad^2 l) (z; w) per bus; R = -y_x, H[u rows] = y_u.  The
+    // own-variable coefficients are summed per bus (busS), so an incident
+    // branch adds only its other end's terms.
+    for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
+      const int i = it / C, c = it % C, j = s_col[c];
+      const int4 bi = n.busrec[i];
+      const double4_32a S = reinterpret_cast<const double4_32a*>(a.busS)[i];
+      const double vi = dslot<C>(Z, bi.x, c, j), ti = bi.y >= 0 ? Z[(size_t)bi.y * C + c] : 0.0;
+      double yv = S.x * vi + S.y * ti, yt = S.y * vi + S.z * ti;
+      const int q1 = n.adj_ptr[i + 1];
+      for (int qb = n.adj_ptr[i]; qb < q1; qb += 4) {
+        int4 ar[4];
+        double vo[4], to[4];
+        adj_dirs4<C>(n, Z, qb, q1, c, j, ar, vo, to);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (qb + u < q1) {
+            const double2* e2 = reinterpret_cast<const double2*>(E + (size_t)(qb + u) * ADJ_W);
+            const double2 e01 = e2[0], e23 = e2[1];  // (VO, VT), (TO, TT)
+            yv += e01.x * vo[u] - e01.y * to[u];
+            yt += e23.x * vo[u] - e23.y * to[u];
+            if (ar[u].z >= 0) {  // Gauss-Newton terms of the other end's Q (and P at the slack)
+              const double w = QD[(size_t)ar[u].z * C + c];
+              const double2 e45 = e2[2];  // (QOV, QOT)
+              yv += w * e45.x;
+              yt += w * e45.y;
+              if (ar[u].w) {
+                const double w2 = PD[c];
+                const double2 e67 = e2[3];  // (POV, POT)
+                yv += w2 * e67.x;
+                yt += w2 * e67.y;
+              }
+            }
+          }
+        }
+      }
+      if (bi.z >= 0) {  // own injections: the gradients dQ_i, dP_i w.r.t. (v_i, theta_i) are per-bus sums
+        const double w = QD[(size_t)bi.z * C + c];
+        yv += w * bw[4 * nb + i];
+        yt += w * bw[5 * nb + i];
+        if (bi.y < 0) {
+          const double w2 = PD[c];
+          yv += w2 * bw[6 * nb + i];
+          yt += w2 * bw[7 * nb + i];
+        }
+      }
+      if (bi.y >= 0) R[(size_t)bi.y * C + c] = -yt;
+      if (bi.x >= 0) {
+        R[(size_t)bi.x * C + c] = -yv;
+      } else if (j >= 0) {
         double* Hc = a.H + (size_t)j * nu;
-        Hc[n.uv[i]] = yv;
-        if (n.type[i] == PV) Hc[n.up[i]] = (n.up[i] == j) ? a.busw[3 * nb + i] : 0.0;
+        Hc[-2 - bi.x] = yv;
+        if (bi.w >= 0) Hc[bi.w] = (bi.w == j) ? bw[3 * nb + i] : 0.0;
       }
     }
     __syncthreads();
@@ -870,22 +1192,36 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     sweep<C, false, false>(n, a.T, a.invdiag, R);
     // (7) H[:, tile] += G_u^T Psi
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
-      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = j0 + c;
-      if (j >= jend) continue;
-      double gv = 0.0, selfP = 0.0;
-      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-        const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
-        if (n.type[o] != REF) gv += R[(size_t)n.pth[o] * C + c] * tab[(size_t)TAB_DP(1 - s, s) * nl + l];
-        if (n.type[o] == PQ) gv += R[(size_t)n.pvv[o] * C + c] * tab[(size_t)TAB_DQ(1 - s, s) * nl + l];
-        selfP += tab[(size_t)TAB_DP(s, s) * nl + l];
+      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = s_col[c];
+      if (j < 0) continue;
+      double gv = 0.0;
+      const int q1 = n.adj_ptr[k + 1];
+      for (int qb = n.adj_ptr[k]; qb < q1; qb += 4) {
+        int4 ar[4];
+        double pt[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ar[u] = (qb + u < q1) ? n.adjrec[qb + u] : make_int4(-1, -1, -1, 0);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          pt[u] = ar[u].y >= 0 ? R[(size_t)ar[u].y * C + c] : 0.0;
+          pv[u] = ar[u].x >= 0 ? R[(size_t)ar[u].x * C + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (qb + u < q1) {
+            const double* e = E + (size_t)(qb + u) * ADJ_W;
+            gv += pt[u] * e[E_POV] + pv[u] * e[E_QOV];
+          }
+        }
       }
       double* Hc = a.H + (size_t)j * nu;
-      if (n.type[k] == PV) {
-        const double psi = R[(size_t)n.pth[k] * C + c];
-        gv += psi * selfP;
-        Hc[n.up[k]] -= psi;
+      const int4 bk = n.busrec[k];
+      if (bk.w >= 0) {  // PV bus
+        const double psi = R[(size_t)bk.y * C + c];
+        gv += psi * bw[6 * nb + k];
+        Hc[bk.w] -= psi;
       }
-      Hc[n.uv[k]] += gv;
+      Hc[-2 - bk.x] += gv;
     }
     __syncthreads();
   }
@@ -1040,7 +1376,7 @@ void launch_hess_prep(opf_ctx* c, double sigma_f) {
   c->launches++;
   bus_weight_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->omega, sigma_f, c->busw);
   c->launches++;
-  bus_self_grad_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->btab, c->busw);
+  bus_self_grad_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->btab, c->busw, c->adjE, c->busS);
 }
 
 size_t hvp_stride(const opf_ctx* c, int C) {
@@ -1051,27 +1387,42 @@ size_t hvp_stride(const opf_ctx* c, int C) {
 template <int C>
 static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int tile_step, int ntiles,
                          int col0, int col_end) {
-  HvpArgs a;
-  a.n = c->dn;
-  a.LU = c->LU;
-  a.T = c->T;
-  a.invdiag = c->invdiag;
-  a.tab = c->btab;
-  a.busw = c->busw;
-  a.ubus = c->ubus;
-  a.H = H;
+  HvpArgs a = make_hvp_args(c, C, H, col0, col_end, true);
   a.scratch = c->scratch;
-  a.stride = hvp_stride(c, C);
   a.ntiles = ntiles;
   a.first_tile = first_tile;
   a.tile_step = tile_step;
-  a.col0 = col0;
-  a.col_end = col_end;
+  const size_t sm = hvp_smem_bytes(a, C);
   if (c->hvp_threads == 512)
-    hvp_tile_kernel<C, 512><<<grid, 512, 0, c->stream>>>(a);
+    hvp_tile_kernel<C, 512><<<grid, 512, sm, c->stream>>>(a);
+  else if (c->hvp_threads == 128)
+    hvp_tile_kernel<C, 128><<<grid, 128, sm, c->stream>>>(a);
   else
-    hvp_tile_kernel<C, 256><<<grid, 256, 0, c->stream>>>(a);
+    hvp_tile_kernel<C, 256><<<grid, 256, sm, c->stream>>>(a);
   c->launches++;
+}
+
+template <int C>
+static int hvp_occ_t(int nt) {
+  int occ = 0;
+  if (nt == 512)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 512>, 512, HVP_DYN_SMEM);
+  else if (nt == 128)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 128>, 128, HVP_DYN_SMEM);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 256>, 256, HVP_DYN_SMEM);
+  return std::max(occ, 1);
+}
+
+int hvp_occupancy(int C, int nt) {
+  switch (C) {
+    case 1: return hvp_occ_t<1>(nt);
+    case 2: return hvp_occ_t<2>(nt);
+    case 4: return hvp_occ_t<4>(nt);
+    case 8: return hvp_occ_t<8>(nt);
+    case 16: return hvp_occ_t<16>(nt);
+    default: return hvp_occ_t<32>(nt);
+  }
 }
 
 bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
@@ -1087,7 +1438,7 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
   }
 }
 
-HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end) {
+HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced) {
   HvpArgs a;
   a.n = c->dn;
   a.LU = c->LU;
@@ -1095,22 +1446,71 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end) {
   a.invdiag = c->invdiag;
   a.tab = c->btab;
   a.busw = c->busw;
+  a.adjE = c->adjE;
+  a.busS = c->busS;
   a.ubus = c->ubus;
+  // the full Hessian is tiled in the elimination-tree order of the controls
+  const bool full = (col0 == 0 && col_end == c->h.nu);
+  int lk = 0;
+  while ((1 << lk) < C) lk++;
+  a.colmap = full ? c->colmap[balanced ? 1 : 0][lk] : nullptr;
   a.H = H;
   a.scratch = nullptr;
   a.stride = hvp_stride(c, C);
-  a.ntiles = (col_end - col0 + C - 1) / C;
+  a.ntiles = hvp_tiles(c, C, col0, col_end, balanced);
   a.first_tile = 0;
   a.tile_step = 1;
   a.col0 = col0;
   a.col_end = col_end;
+  // shared-memory layout of the first solve's reach (no pruning when the mask
+  // and list would take more than half of the budget)
+  const int nwords = (c->dn.r0 + 31) / 32;
+  a.rm_words = (nwords + 3) & ~3;
+  a.list_cap = 2048;
+  const long fixed = 8L * a.rm_words + 4L * a.list_cap;
+  if (fixed > HVP_DYN_SMEM / 2) {
+    a.rm_words = 0;
+    a.list_cap = 0;
+    a.zs_cap = 0;
+  } else {
+    a.zs_cap = (int)std::min<long>(a.list_cap, (HVP_DYN_SMEM - fixed) / (8L * C));
+  }
   return a;
+}
+
+size_t hvp_smem_bytes(const HvpArgs& a, int C) {
+  return 8 * (size_t)a.zs_cap * C + 8 * (size_t)a.rm_words + 4 * (size_t)a.list_cap;
+}
+
+template <int C>
+static void setup_hvp_smem_t() {
+  cudaFuncSetAttribute(hvp_tile_kernel<C, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
+  cudaFuncSetAttribute(hvp_tile_kernel<C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
+  cudaFuncSetAttribute(hvp_tile_kernel<C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
+  cudaFuncSetAttribute(hvp_batch_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
+}
+
+void setup_hvp_smem() {
+  setup_hvp_smem_t<1>();
+  setup_hvp_smem_t<2>();
+  setup_hvp_smem_t<4>();
+  setup_hvp_smem_t<8>();
+  setup_hvp_smem_t<16>();
+  setup_hvp_smem_t<32>();
+}
+
+int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced) {
+  int lk = 0;
+  while ((1 << lk) < C) lk++;
+  const int f = balanced ? 1 : 0;
+  if (col0 == 0 && col_end == c->h.nu && c->coltiles[f][lk] > 0) return c->coltiles[f][lk];
+  return (col_end - col0 + C - 1) / C;
 }
 
 template <int C>
 static int batch_occ() {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_batch_kernel<C>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_batch_kernel<C>, 256, HVP_DYN_SMEM);
   return occ;
 }
 
@@ -1127,14 +1527,14 @@ int hvp_batch_occupancy(int C) {
 }
 
 bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
-                      double* scratch, size_t stride, int grid) {
+                      double* scratch, size_t stride, int grid, size_t smem) {
   switch (C) {
-    case 1: hvp_batch_kernel<1><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
-    case 2: hvp_batch_kernel<2><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
-    case 4: hvp_batch_kernel<4><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
-    case 8: hvp_batch_kernel<8><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
-    case 16: hvp_batch_kernel<16><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
-    case 32: hvp_batch_kernel<32><<<grid, 256, 0, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 1: hvp_batch_kernel<1><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 2: hvp_batch_kernel<2><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 4: hvp_batch_kernel<4><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 8: hvp_batch_kernel<8><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 16: hvp_batch_kernel<16><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
+    case 32: hvp_batch_kernel<32><<<grid, 256, smem, st>>>(args, tiles, ntot, counter, scratch, stride); return true;
     default: return false;
   }
 }
@@ -1143,23 +1543,10 @@ bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* t
 template <int C>
 static void launch_hvp_scratch_t(opf_ctx* c, double* H, double* scratch, int grid, int ntiles, int col0,
                                  int col_end) {
-  HvpArgs a;
-  a.n = c->dn;
-  a.LU = c->LU;
-  a.T = c->T;
-  a.invdiag = c->invdiag;
-  a.tab = c->btab;
-  a.busw = c->busw;
-  a.ubus = c->ubus;
-  a.H = H;
+  HvpArgs a = make_hvp_args(c, C, H, col0, col_end, true);
   a.scratch = scratch;
-  a.stride = hvp_stride(c, C);
   a.ntiles = ntiles;
-  a.first_tile = 0;
-  a.tile_step = 1;
-  a.col0 = col0;
-  a.col_end = col_end;
-  hvp_tile_kernel<C, 256><<<grid, 256, 0, c->stream>>>(a);
+  hvp_tile_kernel<C, 256><<<grid, 256, hvp_smem_bytes(a, C), c->stream>>>(a);
   c->launches++;
 }
 

@@ -99,7 +99,7 @@ extern "C" opf_status opf_reduced_hessian_noalloc(opf_ctx* c, const opf_al_param
   double* scratch = nullptr;
   opf_status st = scratch_for_device(c->device, &scratch);
   if (st != OPF_OK) return st;
-  const int ntiles = (ncol + C - 1) / C;
+  const int ntiles = hvp_tiles(c, C, col0, col0 + ncol, true);
   int grid = (o && o->grid > 0) ? o->grid : ntiles;
   grid = std::min(grid, (int)(kScratchDoubles / stride));
   grid = std::max(1, std::min(grid, ntiles));
