@@ -146,6 +146,17 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   // packed triangle fits in shared memory (the rest join the level schedule)
   constexpr int kMaxDenseRows = 200;
   r0 = std::max(r0, nx - kMaxDenseRows);
+  // bus of each pivot row; a block (theta and v of a PQ bus) never straddles r0
+  std::vector<int> rowbus(nx);
+  {
+    std::vector<int> vbus(nx, -1);
+    for (int b = 0; b < nb; b++) {
+      if (h.xth[b] >= 0) vbus[h.xth[b]] = b;
+      if (h.xv[b] >= 0) vbus[h.xv[b]] = b;
+    }
+    for (int r = 0; r < nx; r++) rowbus[r] = vbus[s.perm[r]];
+  }
+  if (r0 > 0 && r0 < nx && rowbus[r0 - 1] == rowbus[r0]) r0++;
   // sweep schedules of the other rows; rows of a level sorted by length (longest first)
   std::vector<int> sched_ptr_f, sched_rows_f, sched_ptr_b, sched_rows_b;
   {
@@ -172,6 +183,59 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     }
     build(s.lev_f, true, sched_ptr_f, sched_rows_f);
     build(levb, false, sched_ptr_b, sched_rows_b);
+  }
+  // bus-block schedules of the rows below r0 (see DevNet::bmeta_f)
+  std::vector<int> bsched_ptr_f, bsched_ptr_b;
+  std::vector<int4> bmeta_f, bmeta_b;
+  {
+    std::vector<int> bfirst;  // first pivot row of each block below r0
+    for (int r = 0; r < r0; r++)
+      if (r == 0 || rowbus[r] != rowbus[r - 1]) bfirst.push_back(r);
+    const int nbk = (int)bfirst.size();
+    std::vector<int> bof(nx, -1);
+    for (int k = 0; k < nbk; k++) {
+      const int f = bfirst[k], e = (k + 1 < nbk) ? bfirst[k + 1] : r0;
+      for (int r = f; r < e; r++) bof[r] = k;
+    }
+    auto bsize = [&](int k) { return ((k + 1 < nbk) ? bfirst[k + 1] : r0) - bfirst[k]; };
+    // forward block levels (lower columns of the first row; the second row adds only the first)
+    std::vector<int> lf(nbk, 0), lb(nbk, 0);
+    for (int k = 0; k < nbk; k++) {
+      const int f = bfirst[k];
+      int lv = 0;
+      for (int p = s.rp[f]; p < s.dp[f]; p++) lv = std::max(lv, lf[bof[s.ci[p]]] + 1);
+      lf[k] = lv;
+    }
+    // backward block levels (upper columns below r0 of the last row)
+    for (int k = nbk - 1; k >= 0; k--) {
+      const int g = bfirst[k] + bsize(k) - 1;
+      int lv = 0;
+      for (int p = s.dp[g] + 1; p < s.rp[g + 1]; p++)
+        if (s.ci[p] < r0) lv = std::max(lv, lb[bof[s.ci[p]]] + 1);
+      lb[k] = lv;
+    }
+    auto rec = [&](int k, bool fwd) {
+      const int f = bfirst[k], sz = bsize(k);
+      if (fwd) return make_int4(f, s.rp[f], s.dp[f], sz == 2 ? s.rp[f + 1] - s.rp[f] : 0);
+      const int g = f + sz - 1;
+      return make_int4(g, s.dp[g] + 1, s.rp[g + 1], sz == 2 ? (s.dp[f] + 2) - (s.dp[g] + 1) : 0);
+    };
+    auto bbuild = [&](const std::vector<int>& lev, bool fwd, std::vector<int>& ptr, std::vector<int4>& meta) {
+      int nlev = 0;
+      for (int k = 0; k < nbk; k++) nlev = std::max(nlev, lev[k] + 1);
+      ptr.assign(nlev + 1, 0);
+      for (int k = 0; k < nbk; k++) ptr[lev[k] + 1]++;
+      for (int l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
+      std::vector<int> order(nbk), fill(ptr.begin(), ptr.end() - 1);
+      for (int k = 0; k < nbk; k++) order[fill[lev[k]]++] = k;
+      meta.resize(nbk);
+      for (int k = 0; k < nbk; k++) meta[k] = rec(order[k], fwd);
+      for (int l = 0; l < nlev; l++)
+        std::stable_sort(meta.begin() + ptr[l], meta.begin() + ptr[l + 1],
+                         [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+    };
+    bbuild(lf, true, bsched_ptr_f, bmeta_f);
+    bbuild(lb, false, bsched_ptr_b, bmeta_b);
   }
   // LU tasks: (column, lower entry) pairs of the columns outside the dense trailing
   // block, grouped by elimination level; the trailing block is factorised densely.
@@ -268,6 +332,15 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     n.lmeta_f = q;
     TRY(dupload(c, &q, mb));
     n.lmeta_b = q;
+  }
+  {
+    int4* q4;
+    TRY(dupload(c, &ip, bsched_ptr_f)); n.bptr_f = ip;
+    TRY(dupload(c, &ip, bsched_ptr_b)); n.bptr_b = ip;
+    TRY(dupload(c, &q4, bmeta_f)); n.bmeta_f = q4;
+    TRY(dupload(c, &q4, bmeta_b)); n.bmeta_b = q4;
+    n.nblev_f = (int)bsched_ptr_f.size() - 1;
+    n.nblev_b = (int)bsched_ptr_b.size() - 1;
   }
   TRY(dupload(c, &ip, sched_ptr_f)); n.lev_ptr_f = ip;
   TRY(dupload(c, &ip, sched_rows_f)); n.lev_rows_f = ip;

@@ -69,6 +69,15 @@ struct DevNet {
   const int *lev_ptr_f, *lev_rows_f, *lev_ptr_b, *lev_rows_b;
   const int4 *lmeta_f, *lmeta_b;   // per scheduled row: {row, first entry, end entry, 0}
   int nlev_f, nlev_b;
+  // bus-block schedules of the multi-column sweeps: the one or two pivot rows of a
+  // bus (theta, v of a PQ bus are consecutive and share their off-block pattern)
+  // are solved together.  Record {lead row, first shared entry, end, offset}: the
+  // lead row's entries [q0, q1) and the other row's entries at q + offset
+  // (offset 0: a one-row block).  Forward: other = lead + 1, coupling entry
+  // q1 + offset; backward: other = lead - 1, coupling entry q0 + offset - 1.
+  const int *bptr_f, *bptr_b;
+  const int4 *bmeta_f, *bmeta_b;
+  int nblev_f, nblev_b;
   int r0, nroot;
   const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
   const int* slot_adj;             // [4 * 2 nl]

@@ -248,6 +248,49 @@ __device__ __forceinline__ double row_dot_masked(const DevNet& n, const double* 
   return s0 + s1;
 }
 
+// Shared entries [q0, q1) of a bus block against the slab: a -= V[q] X[ci[q]] for
+// the lead row and, for a two-row block, b -= V[q + off] X[ci[q]] for the other
+// row (one index and one slab load for two products).
+template <int C>
+__device__ __forceinline__ void block_dot(const DevNet& n, const double* __restrict__ V, const double* X,
+                                          int q0, int q1, int off, bool two, int col, double& a, double& b) {
+  double a1 = 0.0, b1 = 0.0;
+  int p = q0;
+  for (; p + 3 < q1; p += 4) {
+    const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + 1), c2 = __ldg(n.ci + p + 2), c3 = __ldg(n.ci + p + 3);
+    const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
+    const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
+    a -= V[p] * x0;
+    a1 -= V[p + 1] * x1;
+    a -= V[p + 2] * x2;
+    a1 -= V[p + 3] * x3;
+    if (two) {
+      b -= V[p + off] * x0;
+      b1 -= V[p + off + 1] * x1;
+      b -= V[p + off + 2] * x2;
+      b1 -= V[p + off + 3] * x3;
+    }
+  }
+  const int r = q1 - p;
+  if (r > 0) {
+    const int p1 = p + (r > 1 ? 1 : 0), p2 = p + (r > 2 ? 2 : 0);
+    const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p1), c2 = __ldg(n.ci + p2);
+    const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col], x2 = X[(size_t)c2 * C + col];
+    a -= V[p] * x0;
+    if (two) b -= V[p + off] * x0;
+    if (r > 1) {
+      a1 -= V[p1] * x1;
+      if (two) b1 -= V[p1 + off] * x1;
+    }
+    if (r > 2) {
+      a -= V[p2] * x2;
+      if (two) b -= V[p2 + off] * x2;
+    }
+  }
+  a += a1;
+  b += b1;
+}
+
 // One triangular sweep over a CTA-private right-hand-side slab X[n_x][C].
 // Rows outside the dense trailing block [r0, n_x) follow the level schedule
 // (FWD: lower part of V, rows by ascending level; else the upper part).  The
@@ -283,12 +326,16 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
       __syncthreads();
     }
   }
-  const int nlev = (FWD && rmask) ? 0 : (FWD ? n.nlev_f : n.nlev_b);
-  const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
-  const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
+  // levels of bus blocks (one or two pivot rows each, see DevNet::bmeta_f)
+  const int nlev = (FWD && rmask) ? 0 : (FWD ? n.nblev_f : n.nblev_b);
+  const int* lptr = FWD ? n.bptr_f : n.bptr_b;
+  const int4* lmeta = FWD ? n.bmeta_f : n.bmeta_b;
   const int nwarps = blockDim.x >> 5, grp = lane / C;
-  // narrow level (at most one row per warp): one warp per row, its lane groups
-  // split the row; else one lane group per row
+  // the block's other row and its coupling entry (the diagonal block's off-diagonal)
+  auto other_of = [](const int4& m) { return FWD ? m.x + 1 : m.x - 1; };
+  auto coupling = [](const int4& m) { return FWD ? m.z + m.w : m.y + m.w - 1; };
+  // narrow level (at most one block per warp): one warp per block, its lane
+  // groups split the entries; else one lane group per block
   auto first_k = [&](int b, int e) { return (e - b <= nwarps && RPW > 1) ? b + warp : b + myslot; };
   const int4 none = make_int4(0, 0, 0, 0);
   int b = nlev > 0 ? lptr[0] : 0, e = nlev > 0 ? lptr[1] : 0;
@@ -303,39 +350,60 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
     if (e - b <= nwarps && RPW > 1) {
       for (int k = k0; k < e; k += nwarps) {
         const int4 m = (k == k0) ? mt : __ldg(lmeta + k);
-        const int i = m.x, p1 = m.z;
-        const double xi = X[(size_t)i * C + col];
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        const bool two = m.w != 0;
+        const int lead = m.x, oth = other_of(m), q1 = m.z, off = m.w;
+        const double xl = X[(size_t)lead * C + col], xo = two ? X[(size_t)oth * C + col] : 0.0;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int p = m.y + grp;
-        for (; p + 3 * RPW < p1; p += 4 * RPW) {
-          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + RPW), c2 = __ldg(n.ci + p + 2 * RPW),
-                    c3 = __ldg(n.ci + p + 3 * RPW);
-          const double a0 = V[p], a1 = V[p + RPW], a2 = V[p + 2 * RPW], a3 = V[p + 3 * RPW];
+        for (; p + RPW < q1; p += 2 * RPW) {
+          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + RPW);
           const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
-          const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
-          v0 -= a0 * x0;
-          v1 -= a1 * x1;
-          v2 -= a2 * x2;
-          v3 -= a3 * x3;
+          a0 -= V[p] * x0;
+          a1 -= V[p + RPW] * x1;
+          if (two) {
+            b0 -= V[p + off] * x0;
+            b1 -= V[p + off + RPW] * x1;
+          }
         }
-        for (; p < p1; p += RPW) v0 -= V[p] * X[(size_t)__ldg(n.ci + p) * C + col];
-        double v = (v0 + v1) + (v2 + v3);
+        if (p < q1) {
+          const double x0 = X[(size_t)__ldg(n.ci + p) * C + col];
+          a0 -= V[p] * x0;
+          if (two) b0 -= V[p + off] * x0;
+        }
+        double va = a0 + a1, vb = b0 + b1;
 #pragma unroll
-        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        for (int o = C; o < 32; o <<= 1) {
+          va += __shfl_xor_sync(0xffffffffu, va, o);
+          vb += __shfl_xor_sync(0xffffffffu, vb, o);
+        }
         if (grp == 0) {
-          v += xi;
-          if (DIAG) v *= invdiag[i];
-          X[(size_t)i * C + col] = v;
+          va += xl;
+          if (DIAG) va *= invdiag[lead];
+          X[(size_t)lead * C + col] = va;
+          if (two) {
+            vb += xo;
+            vb -= V[coupling(m)] * va;
+            if (DIAG) vb *= invdiag[oth];
+            X[(size_t)oth * C + col] = vb;
+          }
         }
       }
     } else {
       for (int k = k0; k < e; k += nslots) {
         const int4 m = mt;
-        if (k + nslots < e) mt = __ldg(lmeta + k + nslots);  // next row's record in flight
-        if (!DIAG && m.y == m.z) continue;                   // no entries: the row is final
-        double v = row_dot<C>(n, V, X, m.x, m.y, m.z, col);
-        if (DIAG) v *= invdiag[m.x];
-        X[(size_t)m.x * C + col] = v;
+        if (k + nslots < e) mt = __ldg(lmeta + k + nslots);  // next block's record in flight
+        const bool two = m.w != 0;
+        if (!DIAG && !two && m.y == m.z) continue;           // one row, no entries: final
+        const int lead = m.x, oth = other_of(m);
+        double va = X[(size_t)lead * C + col], vb = two ? X[(size_t)oth * C + col] : 0.0;
+        block_dot<C>(n, V, X, m.y, m.z, m.w, two, col, va, vb);
+        if (DIAG) va *= invdiag[lead];
+        X[(size_t)lead * C + col] = va;
+        if (two) {
+          vb -= V[coupling(m)] * va;
+          if (DIAG) vb *= invdiag[oth];
+          X[(size_t)oth * C + col] = vb;
+        }
       }
     }
     __syncthreads();
