@@ -365,6 +365,15 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, slot_adj)); n.slot_adj = ip;
   TRY(dupload(c, &c->tmap, tmap));
   TRY(dupload(c, &c->lcol_row, lcol_row));
+  {
+    std::vector<int2> lc(lcol_row.size());
+    for (size_t k = 0; k < lc.size(); k++) lc[k] = make_int2(lcol_row[k], lcol_pos[k]);
+    int2* q2;
+    TRY(dupload(c, &q2, lc));
+    n.lcol = q2;
+    TRY(dupload(c, &ip, lcnt));
+    n.lcol_ptr = ip;
+  }
   TRY(dupload(c, &c->lcol_pos, lcol_pos));
   TRY(dupload(c, &c->task_col, task_col));
   TRY(dupload(c, &c->task_k, task_k));

@@ -85,6 +85,8 @@ struct DevNet {
   // pivot-order row holding the value; z <= -2 encodes a control unit vector
   // (the value is 1 in the column of control -2 - z, else 0); -1 means none.
   const int* eparent;              // [nx] elimination-tree parent of each pivot row (-1 at a root)
+  const int* lcol_ptr;             // [nx + 1] columns of L (CSC): entries lcol_ptr[j] ..
+  const int2* lcol;                // per entry {row, position in LU}, rows ascending
   const int4* busrec;              // [nb]: {v slot, theta slot, control-bus index or -1, up or -1}
   const int4* adjrec;              // [2 nl], adjacency order: the other end's {v slot, theta slot,
                                    //   control-bus index or -1, 1 if it is the slack}

@@ -1051,75 +1051,42 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     const int ngrp = blockDim.x / C, g = threadIdx.x / C, nwarp = blockDim.x >> 5;
     const double* __restrict__ Vl = a.LU;
     if (nl <= a.zs_cap) {
-      // one reached row at a time over the whole CTA with the reached values in
-      // shared memory: the lane groups split the row (four entries each per
-      // batch, the next row's first batch and extents loaded ahead), warps
-      // reduce by shuffles, every warp sums the per-warp partials
-      // (double-buffered, one barrier per row) and stores the row (identical
-      // values from every warp)
+      // right-looking over the reached rows with their values in shared
+      // memory: once row t is final, every lane group subtracts its column's
+      // multiples from the later reached rows (all reached: ancestors of t),
+      // one barrier per row; rows of the trailing block are left to it.
       const int col = threadIdx.x % C;
       for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
         s_zs[idx] = Z[(size_t)s_list[idx / C] * C + idx % C];
+      int e0 = 0, e1 = 0;
+      if (nl > 0) {
+        e0 = n.lcol_ptr[s_list[0]];
+        e1 = n.lcol_ptr[s_list[0] + 1];
+      }
       __syncthreads();
-      auto extent = [&](int t) {
-        return t < nl ? make_int2(n.rp[s_list[t]], n.dp[s_list[t]]) : make_int2(0, 0);
-      };
-      auto load4 = [&](int p, int pe, int (&cs)[4], double (&vs)[4]) {
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int q = p + u * ngrp;
-          cs[u] = q < pe ? __ldg(n.ci + q) : -1;
-          vs[u] = q < pe ? Vl[q] : 0.0;
+      for (int t = 0; t < nl; t++) {
+        int en0 = 0, en1 = 0;
+        if (t + 1 < nl) {  // the next column's extent, in flight during this one
+          const int in = s_list[t + 1];
+          en0 = n.lcol_ptr[in];
+          en1 = n.lcol_ptr[in + 1];
         }
-      };
-      auto acc4 = [&](const int (&cs)[4], const double (&vs)[4], double& v) {
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (cs[u] >= 0) {
-            const int w = cs[u] >> 5;
-            const unsigned m = s_mask[w], bit = 1u << (cs[u] & 31);
-            if (m & bit) v -= vs[u] * s_zs[(size_t)(s_pre[w] + __popc(m & (bit - 1u))) * C + col];
+        const double xt = s_zs[(size_t)t * C + col];
+        for (int e = e0 + g; e < e1; e += ngrp) {
+          const int2 rq = __ldg(n.lcol + e);
+          if (rq.x < r0) {
+            const int w = rq.x >> 5;
+            const unsigned m = s_mask[w];
+            const int pos = s_pre[w] + __popc(m & ((1u << (rq.x & 31)) - 1u));
+            s_zs[(size_t)pos * C + col] -= Vl[rq.y] * xt;
           }
         }
-      };
-      int2 e0 = extent(0), e1 = extent(1);
-      int cs[4];
-      double vs[4];
-      load4(e0.x + g, e0.y, cs, vs);
-      for (int t = 0; t < nl; t++) {
-        const int i = s_list[t];
-        const int2 e2 = extent(t + 2);
-        int csn[4];
-        double vsn[4];
-        load4(e1.x + g, e1.y, csn, vsn);
-        double v = 0.0;
-        acc4(cs, vs, v);
-        for (int p = e0.x + g + 4 * ngrp; p < e0.y; p += 4 * ngrp) {  // rows longer than one batch
-          int cb[4];
-          double vb[4];
-          load4(p, e0.y, cb, vb);
-          acc4(cb, vb, v);
-        }
-#pragma unroll
-        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane < C) s_part[t & 1][warp][lane] = v;
-        const double zi = lane < C ? s_zs[(size_t)t * C + lane] : 0.0;  // read before any warp overwrites it
+        e0 = en0;
+        e1 = en1;
         __syncthreads();
-        if (lane < C) {
-          double sum = zi;
-          for (int w = 0; w < nwarp; w++) sum += s_part[t & 1][w][lane];
-          s_zs[(size_t)t * C + lane] = sum;
-          if (warp == 0) Z[(size_t)i * C + lane] = sum;
-        }
-        __syncwarp();
-        e0 = e1;
-        e1 = e2;
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          cs[u] = csn[u];
-          vs[u] = vsn[u];
-        }
       }
+      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
+        Z[(size_t)s_list[idx / C] * C + idx % C] = s_zs[idx];
     }
     if (nl > a.zs_cap && nl <= a.list_cap) {
       // the same with the reached values in the slab
