@@ -485,65 +485,85 @@ __device__ __forceinline__ void sweep1(const DevNet& n, const double* __restrict
       __syncthreads();
     }
   }
-  // levels of the other rows (thread per row, or a warp per row in narrow levels).
-  // The factor data is static, so each level prefetches the next level's row
-  // record and first entry before the barrier; only X reads stay on the chain.
+  // levels of bus blocks below r0 (see DevNet::bmeta_f).  A level of cnt blocks
+  // gives each block G lanes (the largest power of two <= min(32, threads / cnt)):
+  // the lanes split the block's entries and reduce by shuffles.  The factor
+  // data is static, so each level prefetches the next level's block record and
+  // first entry before the barrier; only X reads stay on the chain.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int nlev = FWD ? n.nlev_f : n.nlev_b;
-  const int* lptr = FWD ? n.lev_ptr_f : n.lev_ptr_b;
-  const int4* lmeta = FWD ? n.lmeta_f : n.lmeta_b;
-  int4 mt = make_int4(-1, 0, 0, 0);
+  const int nlev = FWD ? n.nblev_f : n.nblev_b;
+  const int* lptr = FWD ? n.bptr_f : n.bptr_b;
+  const int4* lmeta = FWD ? n.bmeta_f : n.bmeta_b;
+  auto other_of = [](const int4& m) { return FWD ? m.x + 1 : m.x - 1; };
+  auto coupling = [](const int4& m) { return FWD ? m.z + m.w : m.y + m.w - 1; };
+  auto lanes_for = [&](int cnt) {
+    int g = (int)blockDim.x / (cnt > 0 ? cnt : 1);
+    g = g > 32 ? 32 : (g < 1 ? 1 : g);
+    return 1 << (31 - __clz(g));
+  };
+  const int4 none = make_int4(0, 0, 0, 0);
+  int4 mt = none;
   int pc = -1;
-  double pv = 0.0;
+  double pva = 0.0, pvb = 0.0;
   auto fetch = [&](int lb, int le) {
-    const bool nar = (le - lb) <= nwarps;
-    const int k = lb + (nar ? warp : (int)threadIdx.x);
-    mt = (k < le) ? lmeta[k] : make_int4(-1, 0, 0, 0);
-    const int p = nar ? mt.y + lane : mt.y;
+    const int G = lanes_for(le - lb);
+    const int k = lb + warp * (32 / G) + lane / G;
+    mt = (k < le) ? lmeta[k] : none;
+    const int p = mt.y + (lane & (G - 1));
     pc = (k < le && p < mt.z) ? n.ci[p] : -1;
-    pv = (pc >= 0) ? V[p] : 0.0;
+    pva = (pc >= 0) ? V[p] : 0.0;
+    pvb = (pc >= 0 && mt.w) ? V[p + mt.w] : 0.0;
   };
   int b = nlev > 0 ? lptr[0] : 0, e = nlev > 0 ? lptr[1] : 0;
   if (nlev > 0) fetch(b, e);
   for (int lv = 0; lv < nlev; lv++) {
     const int en = (lv + 1 < nlev) ? lptr[lv + 2] : e;
-    if (e - b <= nwarps) {
-      for (int k = b + warp, first = 1; k < e; k += nwarps, first = 0) {
-        const int4 m = first ? mt : lmeta[k];
-        double v = 0.0;
-        int p = m.y + lane;
-        if (first) {
-          if (pc >= 0) v -= pv * X[pc];
-          p += 32;
+    const int G = lanes_for(e - b), gpw = 32 / G, ngroups = (int)blockDim.x / G, li = lane & (G - 1);
+    for (int base = b + warp * gpw, first = 1; base < e; base += ngroups, first = 0) {
+      const int k = base + lane / G;
+      const bool act = k < e;
+      const int4 m = act ? (first ? mt : lmeta[k]) : none;
+      const bool two = m.w != 0;
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+      int p = m.y + li;
+      if (first) {
+        if (pc >= 0) {
+          const double x = X[pc];
+          a0 -= pva * x;
+          b0 -= pvb * x;
         }
-        for (; p < m.z; p += 32) v -= V[p] * X[n.ci[p]];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) {
-          v += X[m.x];
-          if (DIAG) v *= invdiag[m.x];
-          X[m.x] = v;
+        p += G;
+      }
+      for (; p + G < m.z; p += 2 * G) {
+        const int c0 = n.ci[p], c1 = n.ci[p + G];
+        const double x0 = X[c0], x1 = X[c1];
+        a0 -= V[p] * x0;
+        a1 -= V[p + G] * x1;
+        if (two) {
+          b0 -= V[p + m.w] * x0;
+          b1 -= V[p + m.w + G] * x1;
         }
       }
-    } else {
-      for (int k = b + threadIdx.x, first = 1; k < e; k += blockDim.x, first = 0) {
-        const int4 m = first ? mt : lmeta[k];
-        int p = m.y;
-        double s0 = X[m.x], s1 = 0.0;
-        if (first && pc >= 0) {
-          s0 -= pv * X[pc];
-          p++;
+      if (p < m.z) {
+        const double x0 = X[n.ci[p]];
+        a0 -= V[p] * x0;
+        if (two) b0 -= V[p + m.w] * x0;
+      }
+      double va = a0 + a1, vb = b0 + b1;
+      for (int off = 1; off < G; off <<= 1) {
+        va += __shfl_xor_sync(0xffffffffu, va, off);
+        vb += __shfl_xor_sync(0xffffffffu, vb, off);
+      }
+      if (act && li == 0) {
+        va += X[m.x];
+        if (DIAG) va *= invdiag[m.x];
+        X[m.x] = va;
+        if (two) {
+          const int o = other_of(m);
+          vb += X[o] - V[coupling(m)] * va;
+          if (DIAG) vb *= invdiag[o];
+          X[o] = vb;
         }
-        for (; p + 1 < m.z; p += 2) {
-          const int c0 = n.ci[p], c1 = n.ci[p + 1];
-          const double v0 = V[p], v1 = V[p + 1];
-          s0 -= v0 * X[c0];
-          s1 -= v1 * X[c1];
-        }
-        if (p < m.z) s0 -= V[p] * X[n.ci[p]];
-        double v = s0 + s1;
-        if (DIAG) v *= invdiag[m.x];
-        X[m.x] = v;
       }
     }
     if (lv + 1 < nlev) fetch(e, en);
