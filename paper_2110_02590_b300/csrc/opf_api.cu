@@ -375,9 +375,14 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     n.lcol_ptr = ip;
   }
   TRY(dupload(c, &c->lcol_pos, lcol_pos));
-  TRY(dupload(c, &c->task_col, task_col));
-  TRY(dupload(c, &c->task_k, task_k));
-  TRY(dupload(c, &c->task_map_off, task_map_off));
+  {
+    std::vector<int4> trec(task_col.size());
+    for (size_t t = 0; t < task_col.size(); t++) {
+      const int j = task_col[t];
+      trec[t] = make_int4(lcol_pos[task_k[t]], s.dp[j], s.rp[j + 1], task_map_off[t]);
+    }
+    TRY(dupload(c, &c->task_rec, trec));
+  }
   TRY(dupload(c, &c->task_map, task_map));
   TRY(dupload(c, &c->ubus, ubus));
   {

@@ -110,6 +110,10 @@ struct HvpArgs {
   int zs_cap, rm_words, list_cap;
 };
 
+// Shared memory of the trailing dense block's LU (the whole block; larger blocks
+// are factorised in global memory).
+constexpr int kDenseLuSmem = 200 * 1024;
+
 // Dynamic shared memory of the HVP tile kernels (bytes; opted in at load).
 constexpr int HVP_DYN_SMEM = 56 * 1024;
 size_t hvp_smem_bytes(const HvpArgs& a, int C);
@@ -161,8 +165,8 @@ struct opf_ctx {
   int* tmap = nullptr;
   int *lcol_pos = nullptr;        // per lower entry (CSC order): position of L_rj in row r
   int *lcol_row = nullptr;
-  int *task_col = nullptr, *task_k = nullptr;
-  int *task_map_off = nullptr, *task_map = nullptr;  // Schur-update target positions per task
+  int4* task_rec = nullptr;       // per LU task: {pos of A_rj, pos of U_jj, end of U row j, target offset}
+  int* task_map = nullptr;        // Schur-update target positions per task
   std::vector<int> h_task_ptr;    // per forward level
   std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
 

@@ -141,33 +141,63 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
 // from A_rc for every c in row j of U (lanes over c).  Columns of one level
 // never update each other's rows or columns, so only the targets race, and
 // they are combined by atomic adds.
-__global__ void lu_level_kernel(double* LU, const int* __restrict__ rp, const int* __restrict__ dp,
-                                const int* __restrict__ task_col, const int* __restrict__ task_k,
-                                const int* __restrict__ lcol_pos, const int* __restrict__ map_off,
-                                const int* __restrict__ map, int t0, int t1, int* flags) {
+// One elimination level of the right-looking LU on the fixed pattern: a warp
+// per task (column j, lower entry (r, j)) forms l = A_rj / U_jj and subtracts
+// l * U_j* from row r at the precomputed target positions (atomics: tasks of a
+// level may share targets).  Task record {position of A_rj, of U_jj, end of U
+// row j, offset of the task's targets}.
+__global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const int* __restrict__ map,
+                                int t0, int t1, int* flags) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int t = t0 + warp; t < t1; t += nw) {
-    const int j = task_col[t], k = task_k[t];
-    const int prj = lcol_pos[k];
-    const double ujj = LU[dp[j]];
-    const double l = LU[prj] / ujj;
+    const int4 tr = __ldg(trec + t);
+    const double ujj = LU[tr.y];
+    const double l = LU[tr.x] / ujj;
     __syncwarp();
     if (lane == 0) {
-      LU[prj] = l;
+      LU[tr.x] = l;
       if (!(fabs(ujj) > 0.0) || !isfinite(l)) flags[0] = 1;
     }
-    const int* tg = map + map_off[t] - (dp[j] + 1);
-    for (int q = dp[j] + 1 + lane; q < rp[j + 1]; q += 32) atomicAdd(&LU[tg[q]], -l * LU[q]);
+    const int* tg = map + tr.w - (tr.y + 1);
+    for (int q = tr.y + 1 + lane; q < tr.z; q += 32) atomicAdd(&LU[tg[q]], -l * LU[q]);
   }
 }
 
-// In-place LU without pivoting of the dense trailing block [r0, r0 + s) once every
-// other column has been eliminated (all its Schur updates applied).  Entry
-// (i, j) of the block sits at dp[r0+i] + (j - i) of row r0 + i.  One CTA.
+// Dense LU of the trailing block [r0, r0 + s) (rows of it are contiguous in LU:
+// row i holds columns r0 .. r0 + s - 1 from position dp[r0 + i] - i).  With
+// smem, the block is factorised in shared memory (a warp per row of the
+// trailing submatrix, lanes along the row).
 __global__ void __launch_bounds__(1024) lu_dense_block_kernel(double* LU, const int* __restrict__ dp,
-                                                              int r0, int s, int* flags) {
+                                                              int r0, int s, int* flags, int smem) {
+  extern __shared__ double A[];
+  if (smem) {
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx - i * s;
+      A[idx] = LU[dp[r0 + i] - i + j];
+    }
+    __syncthreads();
+    // threads as 32 x (blockDim / 32): lane -> column, warp -> row
+    const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5, nti = blockDim.x >> 5;
+    for (int k = 0; k < s - 1; k++) {
+      const double ukk = A[k * s + k];
+      if (threadIdx.x == 0 && (!(fabs(ukk) > 0.0) || !isfinite(ukk))) flags[0] = 1;
+      const double inv = 1.0 / ukk;
+      for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[i * s + k] *= inv;
+      __syncthreads();
+      for (int i = k + 1 + ti; i < s; i += nti) {
+        const double l = A[i * s + k];
+        for (int j = k + 1 + tj; j < s; j += 32) A[i * s + j] -= l * A[k * s + j];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx - i * s;
+      LU[dp[r0 + i] - i + j] = A[idx];
+    }
+    return;
+  }
   for (int k = 0; k < s - 1; k++) {
     const int rk = r0 + k;
     const double ukk = LU[dp[rk]];
@@ -183,7 +213,6 @@ __global__ void __launch_bounds__(1024) lu_dense_block_kernel(double* LU, const 
     __syncthreads();
   }
 }
-
 __global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, const int* tmap,
                                  const int* dp, int nx, int nnz, int* flags) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -1335,11 +1364,13 @@ void launch_lu_kernels(opf_ctx* c) {
     const int warps = t1 - t0;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
     c->launches++;
-    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->dn.rp, c->dn.dp, c->task_col, c->task_k,
-                                                   c->lcol_pos, c->task_map_off, c->task_map, t0, t1, c->flags);
+    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->task_rec, c->task_map, t0, t1, c->flags);
   }
   c->launches++;
-  lu_dense_block_kernel<<<1, 1024, 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags);
+  const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
+  const int use_smem = dense_smem <= (size_t)kDenseLuSmem ? 1 : 0;
+  lu_dense_block_kernel<<<1, 1024, use_smem ? dense_smem : 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0,
+                                                                          c->dn.nroot, c->flags, use_smem);
   c->launches++;
   lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
                                                            c->dn.nx, c->dn.nnz, c->flags);
@@ -1357,6 +1388,7 @@ void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, do
 }
 
 opf_status setup_solve1(opf_ctx* c) {
+  cudaFuncSetAttribute(lu_dense_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseLuSmem);
   const size_t tri = sizeof(double) * (size_t)c->dn.nroot * (c->dn.nroot - 1) / 2;
   const size_t full = tri + sizeof(double) * (size_t)c->dn.nx;
   int optin = 0;
