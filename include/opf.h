@@ -298,6 +298,10 @@ typedef struct {
   double alpha_p, alpha_d, delta, du_inf, ds_inf;
   int halvings, inertia_tries, pf_iterations;
   float ms_hessian, ms_total;
+  /* device time of the phases (ms): first-order quantities and Sigma; Schur
+   * right-hand side; Cholesky with its inertia corrections; the two triangular
+   * solves, J d_u and the fraction to the boundary; trial power flows and update */
+  float ms_first_order, ms_rhs, ms_cholesky, ms_solve, ms_trial;
 } opf_step_info;
 
 /* p supplies sigma_f, rho, sigma_c and y (its s and omega are ignored: s comes

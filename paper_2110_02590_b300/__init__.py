@@ -79,7 +79,8 @@ class StepInfo(C.Structure):
     _fields_ = [("alpha_p", C.c_double), ("alpha_d", C.c_double), ("delta", C.c_double),
                 ("du_inf", C.c_double), ("ds_inf", C.c_double), ("halvings", C.c_int),
                 ("inertia_tries", C.c_int), ("pf_iterations", C.c_int), ("ms_hessian", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("ms_first_order", C.c_float), ("ms_rhs", C.c_float),
+                ("ms_cholesky", C.c_float), ("ms_solve", C.c_float), ("ms_trial", C.c_float)]
 
 
 class OPFError(RuntimeError):

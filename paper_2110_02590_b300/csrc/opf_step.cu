@@ -29,6 +29,7 @@ struct StepWork {
   double* h_red;
   int* h_flag;
   void* block = nullptr;
+  cudaEvent_t ev[7] = {};  // phase boundaries of a step
 };
 
 void free_step_work(opf_ctx* c) {
@@ -37,6 +38,8 @@ void free_step_work(opf_ctx* c) {
   if (w->block) cudaFree(w->block);
   if (w->h_red) cudaFreeHost(w->h_red);
   if (w->h_flag) cudaFreeHost(w->h_flag);
+  for (cudaEvent_t e : w->ev)
+    if (e) cudaEventDestroy(e);
   delete w;
   c->stepw = nullptr;
 }
@@ -518,9 +521,11 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   const int max_halvings = (o && o->max_halvings) ? o->max_halvings : 10;
   const int max_inertia = (o && o->max_inertia) ? o->max_inertia : 24;
   cudaStream_t stream = c->stream;
-  cudaEvent_t e0, e1;
-  SCK(cudaEventCreate(&e0));
-  SCK(cudaEventCreate(&e1));
+  // phase boundaries: start, first order, Hessian, Schur rhs, Cholesky, solves, end of step (trial PF)
+  cudaEvent_t* ev = w->ev;
+  if (!ev[0])
+    for (int k = 0; k < 7; k++) SCK(cudaEventCreate(&ev[k]));
+  cudaEvent_t e0 = ev[0], e1 = ev[5];
   SCK(cudaEventRecord(e0, stream));
   // Sigma and the Schur weights omega (state only)
   step_sigma_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
@@ -533,6 +538,7 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   ps.omega = w->omega;
   rc = opf_reduced_gradient(c, &ps, nullptr, w->gu, w->gs, nullptr, nullptr, nullptr, nullptr);
   if (rc) return rc;
+  SCK(cudaEventRecord(ev[1], stream));
   step_prep_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
       nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
       w->gu, w->gs, p->sigma_c, p->rho, st->mu, w->sig_u, w->gpsi_u, w->sig_s, w->gpsi_s, w->omega, w->v);
@@ -542,12 +548,14 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   opf_hess_info hi;
   rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
   if (rc) return rc;
+  SCK(cudaEventRecord(ev[2], stream));
   sym_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->S, nu, w->sig_u);
   c->launches++;
   // r = -grad_u psi - J^T v  (state quantities of this point are still in the context)
   launch_weighted_grad(c, w->v, w->Jtv);
   neg_sum_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, w->Jtv, w->r);
   c->launches++;
+  SCK(cudaEventRecord(ev[3], stream));
   // Cholesky with inertia correction
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double delta = delta0;
@@ -566,6 +574,7 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     }
     delta = (delta0 > 0.0) ? delta0 * std::pow(10.0, (double)(tries + 1)) : 1e-8 * std::pow(10.0, (double)tries);
   }
+  SCK(cudaEventRecord(ev[4], stream));
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   launch_chol_solve(c, w->L, nu, w->du);
   // J d_u: z = -G_x^{-1} G_u d_u, then the directional derivatives of c
@@ -615,9 +624,17 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
                                                                 st->zu_u, st->zl_s, st->zu_s, w->dz, ap, ad);
   c->launches++;
   SCK(cudaMemcpyAsync(st->x, w->xt, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaEventRecord(ev[6], stream));
   SCK(cudaStreamSynchronize(stream));
   SCK(cudaGetLastError());
   if (info) {
+    float t[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; k++) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+    info->ms_first_order = t[0];
+    info->ms_rhs = t[2];
+    info->ms_cholesky = t[3];
+    info->ms_solve = t[4];
+    info->ms_trial = t[5];
     info->alpha_p = ap;
     info->alpha_d = ad;
     info->delta = delta;
@@ -630,7 +647,5 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     info->ms_total = ms;
     info->du_inf = info->ds_inf = 0.0;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return OPF_OK;
 }
