@@ -30,6 +30,8 @@ struct StepWork {
   int* h_flag;
   void* block = nullptr;
   cudaEvent_t ev[7] = {};  // phase boundaries of a step
+  cudaStream_t s2 = nullptr;  // second stream of the Cholesky look-ahead
+  cudaEvent_t ch_start = nullptr, ch_panel = nullptr, ch_rest = nullptr;
 };
 
 void free_step_work(opf_ctx* c) {
@@ -40,6 +42,9 @@ void free_step_work(opf_ctx* c) {
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {w->ch_start, w->ch_panel, w->ch_rest})
+    if (e) cudaEventDestroy(e);
+  if (w->s2) cudaStreamDestroy(w->s2);
   delete w;
   c->stepw = nullptr;
 }
@@ -119,15 +124,25 @@ __global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* fl
     if (j < kb) A[(size_t)(k0 + j) * n + i] = x[j];
 }
 
-// trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one 64x64 tile per CTA (16x16 threads, 4x4 each)
-__global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag) {
+// trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one 64x64 tile per CTA (16x16 threads, 4x4 each).
+// first_col: only the first tile column (bj = 0, the next panels' columns);
+// else the tiles with 1 <= bj <= bi.
+__global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag,
+                                                        int first_col) {
   if (*flag) return;
   const int r0 = k0 + kb;
-  const int t = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
-  while (bi * (bi + 1) / 2 > t) bi--;
-  const int bj = t - bi * (bi + 1) / 2;
+  int bi, bj;
+  if (first_col) {
+    bi = blockIdx.x;
+    bj = 0;
+  } else {
+    const int t = blockIdx.x;
+    bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+    while (bi * (bi + 1) / 2 > t) bi--;
+    bj = t - bi * (bi + 1) / 2 + 1;
+    bi += 1;
+  }
   __shared__ double Pa[64][NB + 1], Pb[64][NB + 1];
   for (int q = threadIdx.x; q < 64 * NB; q += blockDim.x) {
     const int rr = q % 64, k = q / 64;
@@ -455,23 +470,53 @@ opf_status alloc_step(opf_ctx* c) {
     set_last_error("cannot allocate pinned step buffers");
     return OPF_ENOMEM;
   }
+  if (cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ch_start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ch_panel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ch_rest, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c->stepw = w;
+    free_step_work(c);
+    set_last_error("cannot create the step's streams and events");
+    return OPF_ECUDA;
+  }
   c->stepw = w;
   return OPF_OK;
 }
 
-void launch_cholesky(opf_ctx* c, double* A, int n, int* flag) {
+// Right-looking with look-ahead: the diagonal block and panel of the next
+// column block run on the step's stream as soon as the first tile column of
+// the trailing update is done, while the rest of the trailing update runs on
+// a second stream.
+opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag) {
+  cudaStream_t s1 = c->stream, s2 = w->s2;
+  SCK(cudaEventRecord(w->ch_start, s1));
+  SCK(cudaStreamWaitEvent(s2, w->ch_start, 0));
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
-    chol_diag_kernel<<<1, 256, 0, c->stream>>>(A, n, k0, kb, flag);
+    chol_diag_kernel<<<1, 256, 0, s1>>>(A, n, k0, kb, flag);
     c->launches++;
     const int rest = n - k0 - kb;
     if (rest > 0) {
-      chol_trsm_kernel<<<nblk(rest, 128), 128, 0, c->stream>>>(A, n, k0, kb, flag);
+      chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s1>>>(A, n, k0, kb, flag);
+      c->launches++;
       const int nt = nblk(rest, 64);
-      chol_syrk_kernel<<<nt * (nt + 1) / 2, 256, 0, c->stream>>>(A, n, k0, kb, flag);
-      c->launches += 2;
+      // the rest of the previous trailing update covers this first tile column
+      if (k0 > 0) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
+      chol_syrk_kernel<<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
+      c->launches++;
+      if (nt > 1) {
+        SCK(cudaEventRecord(w->ch_panel, s1));
+        SCK(cudaStreamWaitEvent(s2, w->ch_panel, 0));
+        chol_syrk_kernel<<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
+        c->launches++;
+      }
+      SCK(cudaEventRecord(w->ch_rest, s2));
     }
   }
+  SCK(cudaEventRecord(w->ch_rest, s2));
+  SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
+  return OPF_OK;
 }
 
 void launch_chol_solve(opf_ctx* c, const double* A, int n, double* b) {
@@ -564,7 +609,8 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
     SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
     c->launches++;
-    launch_cholesky(c, w->L, nu, w->flag);
+    rc = launch_cholesky(c, w, w->L, nu, w->flag);
+    if (rc) return rc;
     SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
     SCK(cudaStreamSynchronize(stream));
     if (!*w->h_flag) break;
