@@ -25,12 +25,16 @@ struct StepWork {
   double *b, *z, *ut, *xt, *pd, *qd;
   double *dz;                                   // 2 n_u + 2 m: zl_u, zu_u, zl_s, zu_s steps
   double* red;                                  // [2]: alpha_p, alpha_d (as ordered bits)
+  double* Dinv;                                 // [ceil(n_u / 32)][32][32]: inverses of the factor's diagonal blocks
   int* flag;
   double* h_red;
   int* h_flag;
   void* block = nullptr;
   cudaEvent_t ev[7] = {};  // phase boundaries of a step
   cudaStream_t s2 = nullptr;  // second stream of the Cholesky look-ahead
+  unsigned* trsv_flags = nullptr;  // [ceil(n_u / 32)] block flags of the dense solves (epochs)
+  int* trsv_err = nullptr;         // a dense-solve wait timed out
+  unsigned trsv_epoch = 0;
   cudaEvent_t ch_start = nullptr, ch_panel = nullptr, ch_rest = nullptr;
 };
 
@@ -176,44 +180,134 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
 
 // ---------------------------------------------------------------- dense triangular solves
 
-// forward: L y = b on the diagonal block (one warp), then the rows below
-__global__ void tri_fwd_diag_kernel(const double* A, int n, int k0, int kb, double* b) {
-  const int t = threadIdx.x;
-  double bt = (t < kb) ? b[k0 + t] : 0.0;
-  for (int j = 0; j < kb; j++) {
-    const double yj = __shfl_sync(0xffffffffu, bt, j) / A[(size_t)(k0 + j) * n + k0 + j];
-    if (t == j) bt = yj;
-    else if (t > j && t < kb) bt -= A[(size_t)(k0 + j) * n + k0 + t] * yj;
+// Inverses of the 32 x 32 diagonal blocks of the Cholesky factor (FP64 has a
+// long dependent-operation latency on this part, so the solves below multiply
+// by these instead of running 32-step substitutions with divisions).  One warp
+// per block: lane c builds column c of X = L_ii^{-1} (X[k][c] for k >= c).
+// Dinv[blk][r][c] = X[r][c] (row-major, zero above the diagonal).
+__global__ void chol_diag_inv_kernel(const double* __restrict__ L, int n, double* Dinv) {
+  __shared__ double T[32][33];
+  __shared__ double rinv[32];
+  const int blk = blockIdx.x, lane = threadIdx.x, r0 = blk * 32, kb = min(32, n - r0);
+  for (int j = 0; j < 32; j++) T[lane][j] = (lane < kb && j < kb) ? L[(size_t)(r0 + j) * n + r0 + lane] : 0.0;
+  rinv[lane] = lane < kb ? 1.0 / L[(size_t)(r0 + lane) * n + r0 + lane] : 1.0;
+  __syncwarp();
+  double x[32];
+#pragma unroll
+  for (int k = 0; k < 32; k++) x[k] = (k == lane) ? 1.0 : 0.0;
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    x[k] *= rinv[k];  // x[k] final (zero for k < lane)
+#pragma unroll
+    for (int i = k + 1; i < 32; i++) x[i] -= T[i][k] * x[k];
   }
-  if (t < kb) b[k0 + t] = bt;
+  double* D = Dinv + (size_t)blk * 1024;
+#pragma unroll
+  for (int k = 0; k < 32; k++) D[k * 32 + lane] = x[k];
 }
 
-__global__ void tri_fwd_gemv_kernel(const double* A, int n, int k0, int kb, double* b) {
-  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = b[i];
-  for (int j = 0; j < kb; j++) s -= A[(size_t)(k0 + j) * n + i] * b[k0 + j];
-  b[i] = s;
+// Dense triangular solve with the Cholesky factor in one cooperative launch
+// per direction (forward L y = b, backward L^T x = y; L lower, column-major,
+// leading dimension n; b is overwritten with the solution).  Row block i (32
+// rows) belongs to CTA i mod gridDim.x, which takes its blocks in solve order.
+// The warps of the CTA split the finished blocks k the block depends on (k < i
+// forward, k > i backward): each waits for block k's flag, then accumulates the
+// 32 x 32 block product; warp 0 applies the diagonal block's inverse and
+// publishes the block with the call's epoch (store, fence, release flag).
+// Every wait is bounded: on timeout the kernel sets err and stops waiting (the
+// result is then void).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// backward: L^T x = y on the diagonal block, then the rows above
-__global__ void tri_bwd_diag_kernel(const double* A, int n, int k0, int kb, double* b) {
-  const int t = threadIdx.x;
-  double bt = (t < kb) ? b[k0 + t] : 0.0;
-  for (int j = kb - 1; j >= 0; j--) {
-    const double xj = __shfl_sync(0xffffffffu, bt, j) / A[(size_t)(k0 + j) * n + k0 + j];
-    if (t == j) bt = xj;
-    else if (t < j) bt -= A[(size_t)(k0 + t) * n + k0 + j] * xj;
+template <bool FWD>
+__global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict__ L, int n,
+                                                        const double* __restrict__ Dinv, double* b,
+                                                        unsigned* flags, unsigned epoch, int* err) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = (n + 31) >> 5;
+  for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+    const int i = FWD ? q : nb - 1 - q;
+    const int row = i * 32 + lane;
+    const bool live = row < n;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    const int k_lo = FWD ? 0 : i + 1, k_hi = FWD ? i : nb;
+    for (int k = k_lo + warp; k < k_hi; k += 8) {
+      long long spins = 0;
+      while (ld_acquire_u32(flags + k) != epoch) {
+        if (++spins > (1ll << 24) || *(volatile int*)err) {
+          if (lane == 0) atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      const int col0 = k * 32;
+      const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
+      const int kc = min(32, n - col0);  // uniform over the warp: every lane shuffles
+      if (kc == 32) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          const double x0 = __shfl_sync(0xffffffffu, xk, c), x1 = __shfl_sync(0xffffffffu, xk, c + 1);
+          const double x2 = __shfl_sync(0xffffffffu, xk, c + 2), x3 = __shfl_sync(0xffffffffu, xk, c + 3);
+          if (live) {
+            if (FWD) {
+              p0 += L[(size_t)(col0 + c) * n + row] * x0;
+              p1 += L[(size_t)(col0 + c + 1) * n + row] * x1;
+              p2 += L[(size_t)(col0 + c + 2) * n + row] * x2;
+              p3 += L[(size_t)(col0 + c + 3) * n + row] * x3;
+            } else {
+              p0 += L[(size_t)row * n + col0 + c] * x0;
+              p1 += L[(size_t)row * n + col0 + c + 1] * x1;
+              p2 += L[(size_t)row * n + col0 + c + 2] * x2;
+              p3 += L[(size_t)row * n + col0 + c + 3] * x3;
+            }
+          }
+        }
+      } else {
+        for (int c = 0; c < kc; c++) {
+          const double xc = __shfl_sync(0xffffffffu, xk, c);
+          if (live) p0 += (FWD ? L[(size_t)(col0 + c) * n + row] : L[(size_t)row * n + col0 + c]) * xc;
+        }
+      }
+    }
+    part[warp][lane] = (p0 + p1) + (p2 + p3);
+    __syncthreads();
+    if (warp == 0) {
+      double acc = live ? b[row] : 0.0;
+      acc -= ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+             ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+      // x_i = L_ii^{-1} acc (forward) or L_ii^{-T} acc (backward)
+      const double* D = Dinv + (size_t)i * 1024;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        const double a0 = __shfl_sync(0xffffffffu, acc, c), a1 = __shfl_sync(0xffffffffu, acc, c + 1);
+        const double a2 = __shfl_sync(0xffffffffu, acc, c + 2), a3 = __shfl_sync(0xffffffffu, acc, c + 3);
+        if (FWD) {
+          s0 += D[lane * 32 + c] * a0;
+          s1 += D[lane * 32 + c + 1] * a1;
+          s2 += D[lane * 32 + c + 2] * a2;
+          s3 += D[lane * 32 + c + 3] * a3;
+        } else {
+          s0 += D[c * 32 + lane] * a0;
+          s1 += D[(c + 1) * 32 + lane] * a1;
+          s2 += D[(c + 2) * 32 + lane] * a2;
+          s3 += D[(c + 3) * 32 + lane] * a3;
+        }
+      }
+      if (live) b[row] = (s0 + s1) + (s2 + s3);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release_u32(flags + i, epoch);
+    }
+    __syncthreads();
   }
-  if (t < kb) b[k0 + t] = bt;
-}
-
-__global__ void tri_bwd_gemv_kernel(const double* A, int n, int k0, int kb, double* b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k0) return;
-  double s = b[i];
-  for (int j = 0; j < kb; j++) s -= A[(size_t)i * n + k0 + j] * b[k0 + j];
-  b[i] = s;
 }
 
 // ---------------------------------------------------------------- step kernels
@@ -442,14 +536,14 @@ opf_status alloc_step(opf_ctx* c) {
   const size_t sizes[] = {(size_t)nu * nu, (size_t)nu * nu, (size_t)nu, (size_t)m, (size_t)nu, (size_t)nu,
                           (size_t)m, (size_t)m, (size_t)m, (size_t)m, (size_t)nu, (size_t)nu, (size_t)m,
                           (size_t)nu, (size_t)m, (size_t)nx, (size_t)nx, (size_t)nu, (size_t)nx, (size_t)nb,
-                          (size_t)nb, 2 * (size_t)nu + 2 * (size_t)m, 2};
+                          (size_t)nb, 2 * (size_t)nu + 2 * (size_t)m, 2, ((size_t)nu + 31) / 32 * 1024};
   double** ptrs[] = {&w->S, &w->L, &w->gu, &w->gs, &w->sig_u, &w->gpsi_u, &w->sig_s, &w->gpsi_s, &w->omega,
                      &w->v, &w->r, &w->du, &w->ds, &w->Jtv, &w->Jdu, &w->b, &w->z, &w->ut, &w->xt,
-                     &w->pd, &w->qd, &w->dz, &w->red};
+                     &w->pd, &w->qd, &w->dz, &w->red, &w->Dinv};
   const int np = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (int k = 0; k < np; k++) total += (sizes[k] + 31) & ~(size_t)31;
-  total += 32;  // flag
+  total += 32 + (size_t)nu / 32 + 16;  // flag, dense-solve error and block flags (ints)
   if (cudaMalloc(&w->block, total * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete w;
@@ -462,6 +556,15 @@ opf_status alloc_step(opf_ctx* c) {
     p += (sizes[k] + 31) & ~(size_t)31;
   }
   w->flag = reinterpret_cast<int*>(p);
+  w->trsv_err = w->flag + 1;
+  w->trsv_flags = reinterpret_cast<unsigned*>(w->flag + 8);
+  if (cudaMemset(w->flag, 0, (8 + (size_t)nu / 32 + 1) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(w->block);
+    delete w;
+    set_last_error("cannot initialise the reduced-Newton step workspace");
+    return OPF_ECUDA;
+  }
   if (cudaMallocHost(&w->h_red, 2 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&w->h_flag, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -519,25 +622,23 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
   return OPF_OK;
 }
 
-void launch_chol_solve(opf_ctx* c, const double* A, int n, double* b) {
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
-    tri_fwd_diag_kernel<<<1, 32, 0, c->stream>>>(A, n, k0, kb, b);
+opf_status launch_chol_solve(opf_ctx* c, StepWork* w, const double* A, int n, double* b) {
+  const int nb = (n + 31) / 32;
+  chol_diag_inv_kernel<<<nb, 32, 0, c->stream>>>(A, n, w->Dinv);
+  c->launches++;
+  int occ = 0;
+  SCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_trsv_kernel<true>, 256, 0));
+  const int grid = std::max(1, std::min(nb, occ * c->sm_count));
+  for (int dir = 0; dir < 2; dir++) {
+    unsigned epoch = ++w->trsv_epoch;
+    const double* Dv = w->Dinv;
+    void* args[] = {(void*)&A, (void*)&n, (void*)&Dv, (void*)&b, (void*)&w->trsv_flags, (void*)&epoch,
+                    (void*)&w->trsv_err};
+    SCK(cudaLaunchCooperativeKernel(dir == 0 ? (const void*)chol_trsv_kernel<true> : (const void*)chol_trsv_kernel<false>,
+                                    dim3(grid), dim3(256), args, 0, c->stream));
     c->launches++;
-    if (n - k0 - kb > 0) {
-      tri_fwd_gemv_kernel<<<nblk(n - k0 - kb, 256), 256, 0, c->stream>>>(A, n, k0, kb, b);
-      c->launches++;
-    }
   }
-  for (int k0 = ((n - 1) / NB) * NB; k0 >= 0; k0 -= NB) {
-    const int kb = std::min(NB, n - k0);
-    tri_bwd_diag_kernel<<<1, 32, 0, c->stream>>>(A, n, k0, kb, b);
-    c->launches++;
-    if (k0 > 0) {
-      tri_bwd_gemv_kernel<<<nblk(k0, 256), 256, 0, c->stream>>>(A, n, k0, kb, b);
-      c->launches++;
-    }
-  }
+  return OPF_OK;
 }
 
 }  // namespace
@@ -622,7 +723,8 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   }
   SCK(cudaEventRecord(ev[4], stream));
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  launch_chol_solve(c, w->L, nu, w->du);
+  rc = launch_chol_solve(c, w, w->L, nu, w->du);
+  if (rc) return rc;
   // J d_u: z = -G_x^{-1} G_u d_u, then the directional derivatives of c
   gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
   c->launches++;
@@ -640,8 +742,13 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
       st->zu_s, w->gpsi_s, w->sig_s, w->Jdu, p->sigma_c, p->rho, st->mu, tau, w->ds, w->dz, w->red);
   c->launches++;
   SCK(cudaMemcpyAsync(w->h_red, w->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  SCK(cudaMemcpyAsync(w->h_flag, w->trsv_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   SCK(cudaStreamSynchronize(stream));
   SCK(cudaGetLastError());
+  if (*w->h_flag) {
+    set_last_error("dense triangular solve: a block wait timed out");
+    return OPF_ECUDA;
+  }
   double ap = w->h_red[0];
   const double ad = w->h_red[1];
   SCK(cudaEventRecord(e1, stream));
