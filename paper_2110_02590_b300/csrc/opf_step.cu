@@ -128,12 +128,15 @@ __global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* fl
     if (j < kb) A[(size_t)(k0 + j) * n + i] = x[j];
 }
 
-// trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one 64x64 tile per CTA (16x16 threads, 4x4 each).
-// first_col: only the first tile column (bj = 0, the next panels' columns);
-// else the tiles with 1 <= bj <= bi.
+// trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one TS x TS tile per CTA
+// (16 x 16 threads, (TS/16)^2 outputs each; TS = 32 when the trailing matrix is
+// small, so that more CTAs share the FP64 pipes).  first_col: only the first
+// tile column (bj = 0, the next panels' columns); else the tiles 1 <= bj <= bi.
+template <int TS>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag,
                                                         int first_col) {
   if (*flag) return;
+  constexpr int R = TS / 16;
   const int r0 = k0 + kb;
   int bi, bj;
   if (first_col) {
@@ -147,33 +150,33 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
     bj = t - bi * (bi + 1) / 2 + 1;
     bi += 1;
   }
-  __shared__ double Pa[64][NB + 1], Pb[64][NB + 1];
-  for (int q = threadIdx.x; q < 64 * NB; q += blockDim.x) {
-    const int rr = q % 64, k = q / 64;
-    const int ga = r0 + bi * 64 + rr, gb = r0 + bj * 64 + rr;
+  __shared__ double Pa[TS][NB + 1], Pb[TS][NB + 1];
+  for (int q = threadIdx.x; q < TS * NB; q += blockDim.x) {
+    const int rr = q % TS, k = q / TS;
+    const int ga = r0 + bi * TS + rr, gb = r0 + bj * TS + rr;
     Pa[rr][k] = (k < kb && ga < n) ? A[(size_t)(k0 + k) * n + ga] : 0.0;
     Pb[rr][k] = (k < kb && gb < n) ? A[(size_t)(k0 + k) * n + gb] : 0.0;
   }
   __syncthreads();
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  double acc[4][4] = {};
+  double acc[R][R] = {};
   for (int k = 0; k < kb; k++) {
-    double a[4], b[4];
+    double a[R], b[R];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      a[q] = Pa[ty * 4 + q][k];
-      b[q] = Pb[tx * 4 + q][k];
+    for (int q = 0; q < R; q++) {
+      a[q] = Pa[ty * R + q][k];
+      b[q] = Pb[tx * R + q][k];
     }
 #pragma unroll
-    for (int p = 0; p < 4; p++)
+    for (int p = 0; p < R; p++)
 #pragma unroll
-      for (int q = 0; q < 4; q++) acc[p][q] += a[p] * b[q];
+      for (int q = 0; q < R; q++) acc[p][q] += a[p] * b[q];
   }
 #pragma unroll
-  for (int p = 0; p < 4; p++)
+  for (int p = 0; p < R; p++)
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int gi = r0 + bi * 64 + ty * 4 + p, gj = r0 + bj * 64 + tx * 4 + q;
+    for (int q = 0; q < R; q++) {
+      const int gi = r0 + bi * TS + ty * R + p, gj = r0 + bj * TS + tx * R + q;
       if (gi < n && gj <= gi) A[(size_t)gj * n + gi] -= acc[p][q];
     }
 }
@@ -603,15 +606,25 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
     if (rest > 0) {
       chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s1>>>(A, n, k0, kb, flag);
       c->launches++;
-      const int nt = nblk(rest, 64);
+      // tile width: 64, or 32 once the trailing triangle has fewer 64-tiles than
+      // two per SM (the first tile column then holds the next two panels)
+      const int nt64 = nblk(rest, 64);
+      const bool small = nt64 * (nt64 + 1) / 2 < 2 * c->sm_count;
+      const int nt = small ? nblk(rest, 32) : nt64;
       // the rest of the previous trailing update covers this first tile column
       if (k0 > 0) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
-      chol_syrk_kernel<<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
+      if (small)
+        chol_syrk_kernel<32><<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
+      else
+        chol_syrk_kernel<64><<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
       c->launches++;
       if (nt > 1) {
         SCK(cudaEventRecord(w->ch_panel, s1));
         SCK(cudaStreamWaitEvent(s2, w->ch_panel, 0));
-        chol_syrk_kernel<<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
+        if (small)
+          chol_syrk_kernel<32><<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
+        else
+          chol_syrk_kernel<64><<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
         c->launches++;
       }
       SCK(cudaEventRecord(w->ch_rest, s2));
