@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--cpu-step", action="store_true", help="internal: time one oracle tracking step")
     return ap.parse_args()
 
@@ -212,10 +214,13 @@ class ClockSampler:
 
 
 def hvp_flops_per_column(sym, nx, nl):
-    """Algorithmic FP64 flops of one HVP column: four triangular sweeps (2 per strictly
-    triangular entry, 1 per diagonal scaling) and the branch second-order products (32 per branch)."""
+    """Algorithmic FP64 flops of one HVP column: the three full triangular sweeps (U, U^T,
+    L^T; 2 per strictly triangular entry, 1 per diagonal scaling) and the branch
+    second-order products (32 per branch).  The first L sweep is counted as zero: its
+    right-hand side is sparse and the kernel only visits the reached rows (a few per cent
+    of the entries), so counting the full sweep would overstate the work."""
     nnz_strict = (len(sym["colidx"]) - nx) // 2
-    return 8 * nnz_strict + 2 * nx + 32 * nl
+    return 6 * nnz_strict + 2 * nx + 32 * nl
 
 
 def hbm_bytes_per_hessian(sym, nx, nu, k):
@@ -310,12 +315,16 @@ def run_gpu(args):
     launches0 = ctx.launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        if args.profile_step:
+            torch.cuda.profiler.start()
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             infos.append(step(k, pds[args.warmup + 1 + k], qds[args.warmup + 1 + k]))
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+        if args.profile_step:
+            torch.cuda.profiler.stop()
     launches = ctx.launch_count() - launches0
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:

@@ -200,8 +200,8 @@ opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_h
 
 /*
  * opf_hessian_autotune: time opf_reduced_hessian on the context's current state
- * for each (block_k, threads) in {(4,256), (8,256), (8,512), (16,256),
- * (16,512), (32,256)} (one untimed and one timed call each, CUDA events on the
+ * for each (block_k, threads) in {(4,128), (4,256), (8,128), (8,256), (8,512),
+ * (16,256), (16,512), (32,256)} (one untimed and one timed call each, CUDA events on the
  * context stream), keep the fastest as the context's choice for block_k = 0,
  * and return it in best (host) with its time in best_ms (host, may be NULL).
  * H (device, n_u x n_u) is scratch for the trial calls.  Errors as

@@ -826,7 +826,7 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
 opf_status opf_hessian_autotune(opf_ctx* c, const opf_al_params* p, double* H, opf_hess_opts* best,
                                 float* best_ms) {
   if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
-  static const int cand[][2] = {{4, 256}, {8, 256}, {8, 512}, {16, 256}, {16, 512}, {32, 256}};
+  static const int cand[][2] = {{4, 128}, {4, 256}, {8, 128}, {8, 256}, {8, 512}, {16, 256}, {16, 512}, {32, 256}};
   float tbest = 0.f;
   int kb = 0, tb = 0;
   for (const auto& cd : cand) {

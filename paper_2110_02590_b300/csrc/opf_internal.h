@@ -117,6 +117,7 @@ constexpr int kDenseLuSmem = 200 * 1024;
 // Dynamic shared memory of the HVP tile kernels (bytes; opted in at load).
 constexpr int HVP_DYN_SMEM = 56 * 1024;
 size_t hvp_smem_bytes(const HvpArgs& a, int C);
+int hvp_smem_budget(int C);  // dynamic shared memory a tile of width C may use (<= HVP_DYN_SMEM)
 void setup_hvp_smem();
 
 // kernel launchers (opf_kernels.cu)

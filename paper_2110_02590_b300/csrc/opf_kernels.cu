@@ -1493,11 +1493,11 @@ template <int C>
 static int hvp_occ_t(int nt) {
   int occ = 0;
   if (nt == 512)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 512>, 512, HVP_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 512>, 512, hvp_smem_budget(C));
   else if (nt == 128)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 128>, 128, HVP_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 128>, 128, hvp_smem_budget(C));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 256>, 256, HVP_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_tile_kernel<C, 256>, 256, hvp_smem_budget(C));
   return std::max(occ, 1);
 }
 
@@ -1555,15 +1555,18 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   a.rm_words = (nwords + 3) & ~3;
   a.list_cap = 2048;
   const long fixed = 8L * a.rm_words + 4L * a.list_cap;
-  if (fixed > HVP_DYN_SMEM / 2) {
+  const int budget = hvp_smem_budget(C);
+  if (fixed > budget / 2) {
     a.rm_words = 0;
     a.list_cap = 0;
     a.zs_cap = 0;
   } else {
-    a.zs_cap = (int)std::min<long>(a.list_cap, (HVP_DYN_SMEM - fixed) / (8L * C));
+    a.zs_cap = (int)std::min<long>(a.list_cap, (budget - fixed) / (8L * C));
   }
   return a;
 }
+
+int hvp_smem_budget(int C) { return C <= 4 ? 34 * 1024 : HVP_DYN_SMEM; }
 
 size_t hvp_smem_bytes(const HvpArgs& a, int C) {
   return 8 * (size_t)a.zs_cap * C + 8 * (size_t)a.rm_words + 4 * (size_t)a.list_cap;
@@ -1597,7 +1600,7 @@ int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced) {
 template <int C>
 static int batch_occ() {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_batch_kernel<C>, 256, HVP_DYN_SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hvp_batch_kernel<C>, 256, hvp_smem_budget(C));
   return occ;
 }
 
