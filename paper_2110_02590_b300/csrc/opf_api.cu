@@ -491,6 +491,43 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
         TRY(dupload(c, &c->colmap[form][lk], map));
         c->coltiles[form][lk] = T;
       }
+    // split tilings: k waves of full-width tiles, then at most one half-width
+    // tile per SM for the remaining columns (every SM carries about the same
+    // number of columns, with no idle lanes in the full-width tiles)
+    for (int lk = 1; lk < 6; lk++) {
+      const int C = 1 << lk, nu = h.nu, S = c->sm_count;
+      const int waves = nu / (C * S);
+      const int n1 = waves * S, rem = nu - n1 * C, n2 = (rem + C / 2 - 1) / (C / 2);
+      if (waves < 1 || rem <= 0 || n2 > S) continue;
+      auto order = [&](int q0, int w, int T) {  // chunks of width w from q0, heaviest reach first
+        std::vector<std::pair<int, int>> cost(T);
+        for (int t = 0; t < T; t++) {
+          int reach = 0;
+          rows.clear();
+          for (int q = q0 + t * w; q < std::min(nu, q0 + (t + 1) * w); q++) rhs_rows(perm_cols[q], rows);
+          stamp_id++;
+          for (int r : rows)
+            for (int x = r; x >= 0 && stamp[x] != stamp_id; x = par[x]) {
+              stamp[x] = stamp_id;
+              reach++;
+            }
+          cost[t] = {-reach, t};
+        }
+        std::stable_sort(cost.begin(), cost.end());
+        std::vector<int> m((size_t)T * w, -1);
+        for (int t = 0; t < T; t++) {
+          const int src = cost[t].second;
+          for (int q = q0 + src * w; q < std::min(nu, q0 + (src + 1) * w); q++)
+            m[(size_t)t * w + (q - q0 - src * w)] = perm_cols[q];
+        }
+        return m;
+      };
+      std::vector<int> map = order(0, C, n1), m2 = order(n1 * C, C / 2, n2);
+      map.insert(map.end(), m2.begin(), m2.end());
+      TRY(dupload(c, &c->colmap_split[lk], map));
+      c->split_n1[lk] = n1;
+      c->split_n2[lk] = n2;
+    }
   }
   TRY(dupload(c, &c->pd_nom, h.pd));
   TRY(dupload(c, &c->qd_nom, h.qd));
@@ -793,10 +830,17 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   const int col0 = o ? o->col_begin : 0;
   const int ncol = (o && o->col_count > 0) ? o->col_count : nu - col0;
   if (col0 < 0 || col0 >= nu || ncol < 1 || col0 + ncol > nu) FAIL(OPF_EINVAL, "column range outside [0, n_u)");
-  const int ntiles = hvp_tiles(c, C, col0, col0 + ncol, true);
+  int lk = 0;
+  while ((1 << lk) < C) lk++;
+  // the full Hessian at the default launch shape runs the split tiling when
+  // the context has one for this width
+  const bool split = !plain && !(o && o->grid > 0) && col0 == 0 && ncol == nu && nt == 256 &&
+                     c->split_n1[lk] > 0;
+  const int ntiles = split ? c->split_n1[lk] + c->split_n2[lk] : hvp_tiles(c, C, col0, col0 + ncol, true);
   int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : std::min(ntiles, hvp_occupancy(C, nt) * c->sm_count));
   grid = std::max(1, std::min(grid, ntiles));
-  TRY(ensure_scratch(c, hvp_stride(c, C) * (size_t)grid));
+  if (split) grid = ntiles;
+  TRY(ensure_scratch(c, split ? hvp_split_scratch(c, C) : hvp_stride(c, C) * (size_t)grid));
   cudaStream_t st = c->stream;
   CK(cudaEventRecord(c->ev[0], st));
   if (!(o && o->reuse_first_order)) launch_first_order(c, p, nullptr);
@@ -805,6 +849,9 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   int launches = 0;
   if (plain) {
     for (int t = 0; t < ntiles; t++, launches++) launch_hvp(c, C, H, 1, t, 1, t + 1, col0, col0 + ncol);
+  } else if (split) {
+    launch_hvp_split(c, C, H);
+    launches = 1;
   } else {
     launch_hvp(c, C, H, grid, 0, 1, ntiles, col0, col0 + ncol);
     launches = 1;

@@ -141,6 +141,10 @@ void set_last_error(const std::string& msg);  // message returned by opf_last_er
 // balanced: the single-network launch (tiles in whole waves over the SMs)
 HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced);
 int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  // tiles of a column range
+// The full Hessian as split_n1 tiles of width C and split_n2 of width C / 2 in
+// one launch (false when the context has no split tiling at this width).
+bool launch_hvp_split(opf_ctx* c, int C, double* H);
+size_t hvp_split_scratch(const opf_ctx* c, int C);  // doubles of workspace it needs
 int hvp_batch_occupancy(int C);  // resident CTAs per SM of the batched tile kernel
 int hvp_occupancy(int C, int nt);  // resident CTAs per SM of hvp_tile_kernel<C, nt>
 bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
@@ -181,6 +185,11 @@ struct opf_ctx {
   // (-1 = idle lane), heaviest tiles first
   int* colmap[2][6] = {};
   int coltiles[2][6] = {};
+  // split tiling of the full Hessian at width C = 1 << k: split_n1[k] tiles of
+  // width C (whole waves over the SMs) then split_n2[k] <= SMs tiles of width
+  // C / 2 for the rest; colmap_split[k] holds n1 x C then n2 x C/2 columns
+  int* colmap_split[6] = {};
+  int split_n1[6] = {}, split_n2[6] = {};
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
   double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...

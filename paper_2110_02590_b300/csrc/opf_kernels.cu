@@ -1318,6 +1318,18 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
     hvp_tile<C>(a, Z, tile);
 }
 
+// Split tiling: CTAs [0, n1) run tiles of width C with a1, the others tiles of
+// width C / 2 with a2 (each part with its own column map and workspace).
+template <int C, int NT>
+__global__ void __launch_bounds__(NT) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int n1) {
+  if ((int)blockIdx.x < n1) {
+    hvp_tile<C>(a1, a1.scratch + a1.stride * blockIdx.x, blockIdx.x);
+  } else {
+    const int t = blockIdx.x - n1;
+    hvp_tile<C / 2>(a2, a2.scratch + a2.stride * t, t);
+  }
+}
+
 // Persistent batched form: CTAs pull (context, tile) pairs from a queue (ordered
 // largest network first) and run the same tile body with that context's
 // arguments staged in shared memory.  No CTA waits on another.
@@ -1566,6 +1578,42 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   return a;
 }
 
+size_t hvp_split_scratch(const opf_ctx* c, int C) {
+  int lk = 0;
+  while ((1 << lk) < C) lk++;
+  return hvp_stride(c, C) * (size_t)c->split_n1[lk] + hvp_stride(c, C / 2) * (size_t)c->split_n2[lk];
+}
+
+template <int C>
+static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
+  const int n1 = c->split_n1[lk], n2 = c->split_n2[lk];
+  HvpArgs a1 = make_hvp_args(c, C, H, 0, c->h.nu, true);
+  HvpArgs a2 = make_hvp_args(c, C / 2, H, 0, c->h.nu, true);
+  a1.colmap = c->colmap_split[lk];
+  a1.ntiles = n1;
+  a1.scratch = c->scratch;
+  a2.colmap = c->colmap_split[lk] + (size_t)n1 * C;
+  a2.ntiles = n2;
+  a2.scratch = c->scratch + a1.stride * (size_t)n1;
+  const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
+  hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, n1);
+  c->launches++;
+}
+
+bool launch_hvp_split(opf_ctx* c, int C, double* H) {
+  int lk = 0;
+  while ((1 << lk) < C) lk++;
+  if (c->split_n1[lk] <= 0) return false;
+  switch (C) {
+    case 2: launch_hvp_split_t<2>(c, H, lk); return true;
+    case 4: launch_hvp_split_t<4>(c, H, lk); return true;
+    case 8: launch_hvp_split_t<8>(c, H, lk); return true;
+    case 16: launch_hvp_split_t<16>(c, H, lk); return true;
+    case 32: launch_hvp_split_t<32>(c, H, lk); return true;
+    default: return false;
+  }
+}
+
 int hvp_smem_budget(int C) { return C <= 4 ? 34 * 1024 : HVP_DYN_SMEM; }
 
 size_t hvp_smem_bytes(const HvpArgs& a, int C) {
@@ -1578,6 +1626,9 @@ static void setup_hvp_smem_t() {
   cudaFuncSetAttribute(hvp_tile_kernel<C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
   cudaFuncSetAttribute(hvp_tile_kernel<C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
   cudaFuncSetAttribute(hvp_batch_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
+  if (C >= 2)
+    cudaFuncSetAttribute(hvp_split_kernel<(C >= 2 ? C : 2), 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         HVP_DYN_SMEM);
 }
 
 void setup_hvp_smem() {
