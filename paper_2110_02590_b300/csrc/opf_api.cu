@@ -187,8 +187,9 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   // bus-block schedules of the rows below r0 (see DevNet::bmeta_f)
   std::vector<int> bsched_ptr_f, bsched_ptr_b;
   std::vector<int4> bmeta_f, bmeta_b;
+  std::vector<int> bfirst;          // first pivot row of each block below r0
+  std::vector<int> blev_f;          // forward level of each block
   {
-    std::vector<int> bfirst;  // first pivot row of each block below r0
     for (int r = 0; r < r0; r++)
       if (r == 0 || rowbus[r] != rowbus[r - 1]) bfirst.push_back(r);
     const int nbk = (int)bfirst.size();
@@ -236,29 +237,41 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     };
     bbuild(lf, true, bsched_ptr_f, bmeta_f);
     bbuild(lb, false, bsched_ptr_b, bmeta_b);
+    blev_f = lf;
   }
-  // LU tasks: (column, lower entry) pairs of the columns outside the dense trailing
-  // block, grouped by elimination level; the trailing block is factorised densely.
-  std::vector<int> task_col, task_k;
+  // LU tasks by bus block, grouped by block level: for block J (first pivot row
+  // f, one or two rows) and each lower entry (r, f) of column f other than the
+  // block's own second row, one task eliminates both columns of J from row r.
+  // Record {position of A_rf, dp[f], rp[f + 1], dp[f + 1] or -1}; its Schur-update
+  // targets are the positions in row r of the columns of f's upper entries past
+  // the block.  A two-row block's second row is finished (L, U_vv and its U row
+  // after eliminating f) by a finish record {dp[f], rp[f + 1], dp[f + 1], 0} in
+  // the next level's launch, when no task reads it any more.
+  std::vector<int4> btask, bfin;
+  std::vector<int> btask_off(1, 0), task_map;
   c->h_task_ptr.assign(1, 0);
-  for (int lv = 0; lv < s.nlev_f; lv++) {
-    for (int q = c->h_lev_ptr_f[lv]; q < c->h_lev_ptr_f[lv + 1]; q++) {
-      const int j = lrows_f[q];
-      if (j >= r0) continue;
-      for (int k = lcnt[j]; k < lcnt[j + 1]; k++) {
-        task_col.push_back(j);
-        task_k.push_back(k);
+  c->h_fin_ptr.assign(1, 0);
+  {
+    const int nbk = (int)bfirst.size();
+    int nl = 0;
+    for (int k = 0; k < nbk; k++) nl = std::max(nl, blev_f[k] + 1);
+    std::vector<std::vector<int>> at(nl);
+    for (int k = 0; k < nbk; k++) at[blev_f[k]].push_back(k);
+    for (int lv = 0; lv < nl; lv++) {
+      for (int k : at[lv]) {
+        const int f = bfirst[k], sz = ((k + 1 < nbk) ? bfirst[k + 1] : r0) - f;
+        for (int q = lcnt[f]; q < lcnt[f + 1]; q++) {
+          const int r = lcol_row[q];
+          if (sz == 2 && r == f + 1) continue;
+          btask.push_back(make_int4(lcol_pos[q], s.dp[f], s.rp[f + 1], sz == 2 ? s.dp[f + 1] : -1));
+          for (int p = s.dp[f] + sz; p < s.rp[f + 1]; p++) task_map.push_back(find_pos(s, r, s.ci[p]));
+          btask_off.push_back((int)task_map.size());
+        }
+        if (sz == 2) bfin.push_back(make_int4(s.dp[f], s.rp[f + 1], s.dp[f + 1], 0));
       }
+      c->h_task_ptr.push_back((int)btask.size());
+      c->h_fin_ptr.push_back((int)bfin.size());
     }
-    if ((int)task_col.size() > c->h_task_ptr.back()) c->h_task_ptr.push_back((int)task_col.size());
-  }
-  // Schur-update targets: for task (j, r) and every entry (j, c) of row j of U, the
-  // position of (r, c) in row r (no search at factorisation time)
-  std::vector<int> task_map_off(task_col.size() + 1, 0), task_map;
-  for (size_t t = 0; t < task_col.size(); t++) {
-    const int j = task_col[t], r = lcol_row[task_k[t]];
-    for (int q = s.dp[j] + 1; q < s.rp[j + 1]; q++) task_map.push_back(find_pos(s, r, s.ci[q]));
-    task_map_off[t + 1] = (int)task_map.size();
   }
   // control buses: slack first, then PV
   std::vector<int> gn_bus, gn_of(nb, -1), ubus(h.nu, -1);
@@ -375,14 +388,9 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     n.lcol_ptr = ip;
   }
   TRY(dupload(c, &c->lcol_pos, lcol_pos));
-  {
-    std::vector<int4> trec(task_col.size());
-    for (size_t t = 0; t < task_col.size(); t++) {
-      const int j = task_col[t];
-      trec[t] = make_int4(lcol_pos[task_k[t]], s.dp[j], s.rp[j + 1], task_map_off[t]);
-    }
-    TRY(dupload(c, &c->task_rec, trec));
-  }
+  TRY(dupload(c, &c->task_rec, btask));
+  TRY(dupload(c, &c->task_off, btask_off));
+  TRY(dupload(c, &c->fin_rec, bfin));
   TRY(dupload(c, &c->task_map, task_map));
   TRY(dupload(c, &c->ubus, ubus));
   {

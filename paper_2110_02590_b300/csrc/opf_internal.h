@@ -170,9 +170,13 @@ struct opf_ctx {
   int* tmap = nullptr;
   int *lcol_pos = nullptr;        // per lower entry (CSC order): position of L_rj in row r
   int *lcol_row = nullptr;
-  int4* task_rec = nullptr;       // per LU task: {pos of A_rj, pos of U_jj, end of U row j, target offset}
-  int* task_map = nullptr;        // Schur-update target positions per task
-  std::vector<int> h_task_ptr;    // per forward level
+  // LU by bus blocks (see load_impl): task records, target offsets and targets,
+  // finish records of two-row blocks; per block level the task and finish ranges
+  int4* task_rec = nullptr;
+  int* task_off = nullptr;
+  int* task_map = nullptr;
+  int4* fin_rec = nullptr;
+  std::vector<int> h_task_ptr, h_fin_ptr;
   std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
 
   // device: state of the last converged power flow

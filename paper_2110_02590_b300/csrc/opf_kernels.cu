@@ -141,27 +141,63 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
 // from A_rc for every c in row j of U (lanes over c).  Columns of one level
 // never update each other's rows or columns, so only the targets race, and
 // they are combined by atomic adds.
-// One elimination level of the right-looking LU on the fixed pattern: a warp
-// per task (column j, lower entry (r, j)) forms l = A_rj / U_jj and subtracts
-// l * U_j* from row r at the precomputed target positions (atomics: tasks of a
-// level may share targets).  Task record {position of A_rj, of U_jj, end of U
-// row j, offset of the task's targets}.
-__global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const int* __restrict__ map,
-                                int t0, int t1, int* flags) {
+// One level of the right-looking LU on the fixed pattern, by bus blocks (one or
+// two pivot rows f, f + 1 whose off-block patterns coincide).  Warps [0, t1 - t0)
+// take a task each: for row r below the block, l_f = A_rf / U_ff and, for a
+// two-row block, l_v = (A_r,f+1 - l_f U_f,f+1) / U_vv with the block's own
+// U_vv = A_vv - (A_vf / U_ff) U_f,f+1 formed on the fly; then every column c of
+// row f past the block gets A_rc -= l_f U_fc + l_v (A_vc - L_vf U_fc) at the
+// precomputed target (atomics: tasks of a level may share targets).  The other
+// warps finish the second rows of the previous level's two-row blocks (L_vf,
+// U_vv, U_vc), which no task of this level reads.
+__global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const int* __restrict__ toff,
+                                const int* __restrict__ map, int t0, int t1, const int4* __restrict__ frec,
+                                int f0, int f1, int* flags) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int t = t0 + warp; t < t1; t += nw) {
-    const int4 tr = __ldg(trec + t);
-    const double ujj = LU[tr.y];
-    const double l = LU[tr.x] / ujj;
-    __syncwarp();
-    if (lane == 0) {
-      LU[tr.x] = l;
-      if (!(fabs(ujj) > 0.0) || !isfinite(l)) flags[0] = 1;
+  const int ntask = t1 - t0, nall = ntask + (f1 - f0);
+  for (int w = warp; w < nall; w += nw) {
+    if (w < ntask) {
+      const int t = t0 + w;
+      const int4 tr = __ldg(trec + t);
+      const bool two = tr.w >= 0;
+      const double uff = LU[tr.y];
+      const double inv_ff = 1.0 / uff;
+      const double lf = LU[tr.x] * inv_ff;
+      double lv = 0.0, lvf = 0.0, uvv = 1.0;
+      if (two) {
+        const double ufv = LU[tr.y + 1];
+        lvf = LU[tr.w - 1] * inv_ff;
+        uvv = LU[tr.w] - lvf * ufv;
+        lv = (LU[tr.x + 1] - lf * ufv) / uvv;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        LU[tr.x] = lf;
+        if (two) LU[tr.x + 1] = lv;
+        if (!(fabs(uff) > 0.0) || !isfinite(lf) || !isfinite(lv)) flags[0] = 1;
+      }
+      const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
+      const int* tg = map + toff[t] - q0;
+      for (int q = q0 + lane; q < tr.z; q += 32) {
+        const double ufc = LU[q];
+        double d = lf * ufc;
+        if (two) d += lv * (LU[qv + (q - q0)] - lvf * ufc);
+        atomicAdd(&LU[tg[q]], -d);
+      }
+    } else {
+      const int4 fr = __ldg(frec + f0 + (w - ntask));  // {dp[f], rp[f + 1], dp[f + 1]}
+      const double uff = LU[fr.x];
+      const double lvf = LU[fr.z - 1] / uff;
+      const double ufv = LU[fr.x + 1];
+      for (int q = fr.x + 2 + lane; q < fr.y; q += 32) LU[fr.z + 1 + (q - fr.x - 2)] -= lvf * LU[q];
+      __syncwarp();
+      if (lane == 0) {
+        LU[fr.z - 1] = lvf;
+        LU[fr.z] -= lvf * ufv;
+      }
     }
-    const int* tg = map + tr.w - (tr.y + 1);
-    for (int q = tr.y + 1 + lane; q < tr.z; q += 32) atomicAdd(&LU[tg[q]], -l * LU[q]);
   }
 }
 
@@ -1370,13 +1406,18 @@ void launch_pf_eval(opf_ctx* c) {
 }
 
 void launch_lu_kernels(opf_ctx* c) {
-  const int nlev = (int)c->h_task_ptr.size() - 1;  // elimination levels of the non-trailing columns
-  for (int lv = 0; lv < nlev; lv++) {
-    const int t0 = c->h_task_ptr[lv], t1 = c->h_task_ptr[lv + 1];
-    const int warps = t1 - t0;
+  const int nlev = (int)c->h_task_ptr.size() - 1;  // block levels of the non-trailing columns
+  // level lv's tasks with the finish records of level lv - 1; one more launch
+  // finishes the last level
+  for (int lv = 0; lv <= nlev; lv++) {
+    const int t0 = lv < nlev ? c->h_task_ptr[lv] : 0, t1 = lv < nlev ? c->h_task_ptr[lv + 1] : 0;
+    const int f0 = lv > 0 ? c->h_fin_ptr[lv - 1] : 0, f1 = lv > 0 ? c->h_fin_ptr[lv] : 0;
+    const int warps = (t1 - t0) + (f1 - f0);
+    if (warps == 0) continue;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
     c->launches++;
-    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->task_rec, c->task_map, t0, t1, c->flags);
+    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->task_rec, c->task_off, c->task_map, t0, t1,
+                                                   c->fin_rec, f0, f1, c->flags);
   }
   c->launches++;
   const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
