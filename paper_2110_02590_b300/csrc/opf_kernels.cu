@@ -1242,8 +1242,8 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
         for (int u = 0; u < 4; u++) {
           if (qb + u < q1) {
             const double* e = E + (size_t)(qb + u) * ADJ_W;
-            qd += e[E_QSO] * vo[u] - e[E_QST] * to[u];
-            if (slack) pdr += e[E_PSO] * vo[u] - e[E_PST] * to[u];
+            qd = fma(e[E_QSO], vo[u], fma(-e[E_QST], to[u], qd));  // chained FMAs, no DMUL/DADD
+            if (slack) pdr = fma(e[E_PSO], vo[u], fma(-e[E_PST], to[u], pdr));
           }
         }
       }
@@ -1270,8 +1270,8 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
           if (qb + u < q1) {
             const double2* e2 = reinterpret_cast<const double2*>(E + (size_t)(qb + u) * ADJ_W);
             const double2 e01 = e2[0], e23 = e2[1];  // (VO, VT), (TO, TT)
-            yv += e01.x * vo[u] - e01.y * to[u];
-            yt += e23.x * vo[u] - e23.y * to[u];
+            yv = fma(e01.x, vo[u], fma(-e01.y, to[u], yv));  // chained FMAs, no DMUL/DADD
+            yt = fma(e23.x, vo[u], fma(-e23.y, to[u], yt));
             if (ar[u].z >= 0) {  // Gauss-Newton terms of the other end's Q (and P at the slack)
               const double w = QD[(size_t)ar[u].z * C + c];
               const double2 e45 = e2[2];  // (QOV, QOT)
@@ -1330,7 +1330,7 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
         for (int u = 0; u < 4; u++) {
           if (qb + u < q1) {
             const double* e = E + (size_t)(qb + u) * ADJ_W;
-            gv += pt[u] * e[E_POV] + pv[u] * e[E_QOV];
+            gv = fma(pt[u], e[E_POV], fma(pv[u], e[E_QOV], gv));
           }
         }
       }
