@@ -63,41 +63,42 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- Cholesky
 
+// Diagonal block [k0, k0 + kb) by one warp, no barriers: lane i holds row i of
+// the block in registers; column j's pivot uses one reciprocal square root
+// (d = a * rsqrt(a), 1/d = rsqrt(a)) and the column is broadcast by shuffles.
 __global__ void chol_diag_kernel(double* A, int n, int k0, int kb, int* flag) {
   if (*flag) return;
-  __shared__ double T[NB][NB + 1];
-  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
-    const int i = t % kb, j = t / kb;
-    T[i][j] = A[(size_t)(k0 + j) * n + k0 + i];
-  }
-  __syncthreads();
-  for (int j = 0; j < kb; j++) {
-    if (threadIdx.x == 0) {
-      double d = T[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        *flag = 1;
-        d = 1.0;
+  const int lane = threadIdx.x;
+  double t[NB];
+#pragma unroll
+  for (int j = 0; j < NB; j++) t[j] = (lane < kb && j <= lane) ? A[(size_t)(k0 + j) * n + k0 + lane] : 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    if (j < kb) {
+      double a = __shfl_sync(0xffffffffu, t[j], j);
+      if (!(a > 0.0) || !isfinite(a)) {
+        bad = true;
+        a = 1.0;
       }
-      T[j][j] = sqrt(d);
+      const double r = rsqrt(a);
+      if (lane == j) t[j] = a * r;
+      if (lane > j) t[j] *= r;
+      // trailing update: row lane, columns c in (j, lane]: t[c] -= l_lane * l_c
+      const double li = t[j];
+#pragma unroll
+      for (int c = j + 1; c < NB; c++) {
+        const double lc = __shfl_sync(0xffffffffu, li, c);
+        if (lane >= c && lane < kb) t[c] -= li * lc;
+      }
     }
-    __syncthreads();
-    const double inv = 1.0 / T[j][j];
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) T[i][j] *= inv;
-    __syncthreads();
-    const int w = kb - j - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      const int i = j + 1 + t % w, cc = j + 1 + t / w;
-      if (cc <= i) T[i][cc] -= T[i][j] * T[cc][j];
-    }
-    __syncthreads();
   }
-  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
-    const int i = t % kb, j = t / kb;
-    if (i >= j) A[(size_t)(k0 + j) * n + k0 + i] = T[i][j];
-  }
+  if (lane == 0 && bad) *flag = 1;
+#pragma unroll
+  for (int j = 0; j < NB; j++)
+    if (lane < kb && j <= lane) A[(size_t)(k0 + j) * n + k0 + lane] = t[j];
 }
 
-// rows below the diagonal block: x L_kk^T = a
 __global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag) {
   if (*flag) return;
   __shared__ double T[NB][NB + 1];
@@ -600,7 +601,7 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
   SCK(cudaStreamWaitEvent(s2, w->ch_start, 0));
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
-    chol_diag_kernel<<<1, 256, 0, s1>>>(A, n, k0, kb, flag);
+    chol_diag_kernel<<<1, 32, 0, s1>>>(A, n, k0, kb, flag);
     c->launches++;
     const int rest = n - k0 - kb;
     if (rest > 0) {
