@@ -75,6 +75,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device=None):
+    """The maximum of a host number over the ranks of the default process group (the
+    number itself without one): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(nu, world, total_ms, steps):
+    """(ms per step, whole-job HVP/s): every rank runs its own replica on its own load
+    trajectory (weak scaling), so the job processes world * n_u HVPs per step."""
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * nu / (ms_per_step * 1e-3)
+
+
 def workload_config(nu, extra=None):
     cfg = {"workload": "9.2k-bus synthetic grid (9,200 buses, 1,450 generators, 16,000 branches, "
                        "20% transformers), AR(1) load snapshots",
@@ -326,13 +345,8 @@ def run_gpu(args):
         if args.profile_step:
             torch.cuda.profiler.stop()
     launches = ctx.launch_count() - launches0
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * nu / (ms_per_step * 1e-3)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    ms_per_step, value = job_value(nu, world, total_ms, args.steps)
 
     # the Hessian alone (exact weights) at the current state, and the HVP kernel phase
     alh = dict(al, s=state["s"])
