@@ -239,3 +239,28 @@ def test_nonconvergent_powerflow_reports_status():
     # the context recovers with a feasible solve
     x, info = ctx.powerflow(u)
     assert info["status"] == 0
+
+
+def test_hessian_large_launch_forms_agree():
+    """The 9.2k-bus Hessian by every launch form: the split tiling (default: waves
+    of 8-wide tiles plus one 4-wide tile per SM), the balanced form (explicit grid),
+    512-thread tiles, 4-wide tiles and column ranges in natural order; each tile
+    computes its columns independently, so all agree to rounding."""
+    c = case("large9200")
+    nu = c.on.nu
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    H0, i0 = c.ctx.reduced_hessian(c.al_dev, block_k=8)
+    waves = nu // (8 * sm)
+    rem = nu - waves * sm * 8
+    if waves >= 1 and 0 < rem and -(-rem // 4) <= sm:
+        assert i0["tiles"] == waves * sm + -(-rem // 4) and i0["launches"] == 1
+    H0 = H0.cpu().numpy()
+    ref = np.linalg.norm(H0)
+    for kw in (dict(block_k=8, grid=sm), dict(block_k=8, threads=512), dict(block_k=4)):
+        H, _ = c.ctx.reduced_hessian(c.al_dev, **kw)
+        assert np.linalg.norm(H.cpu().numpy() - H0) <= 1e-12 * ref, kw
+    pieces = np.zeros_like(H0)
+    for a, b in ((0, 1000), (1000, 1001), (1001, nu)):
+        Hp, _ = c.ctx.reduced_hessian(c.al_dev, block_k=8, col_begin=a, col_count=b - a)
+        pieces[:, a:b] = Hp.cpu().numpy()[:, a:b]
+    assert np.linalg.norm(pieces - H0) <= 1e-12 * ref
