@@ -773,8 +773,9 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   opf_pf_info pfi = {0, 0.0, 0.0};
   for (;;) {
     axpy2_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, st->u, w->du, ap, w->ut);
-    c->launches++;
-    SCK(cudaMemcpyAsync(w->xt, st->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    // first-order predictor of the new state: x + alpha z, z = dx/du d_u (from J d_u)
+    axpy2_kernel<<<nblk(nx, 256), 256, 0, stream>>>(nx, st->x, w->z, ap, w->xt);
+    c->launches += 2;
     opf_status prc = opf_powerflow(c, w->ut, w->pd, w->qd, w->xt, nullptr, &pfi);
     if (prc == OPF_OK) break;
     if (prc != OPF_ENOCONV && prc != OPF_ESINGULAR) return prc;
