@@ -131,8 +131,11 @@ typedef struct {
  * (NULL = the nominal loads of the description), starting from
  * x_inout[n_x] and overwriting it.  Each iteration evaluates g and the
  * Jacobian values into the fixed pattern, refactorises, and solves; the
- * factors of the Jacobian at the returned x stay in the context for the
- * gradient and Hessian.  opts NULL = {1e-10, 20}.  info (host) may be NULL.
+ * Jacobian at the returned x stays in the context and is factorised by the
+ * first call that needs it (gradient, Hessian, step), so a power flow whose
+ * factors are never used costs no refactorisation at the solution; a
+ * singular Jacobian there is reported by that call (OPF_ESINGULAR).
+ * opts NULL = {1e-10, 20}.  info (host) may be NULL.
  * Errors: OPF_ENOCONV, OPF_ESINGULAR (the context then has no valid state).
  */
 opf_status opf_powerflow(opf_ctx* ctx, const double* u, const double* pd, const double* qd,

@@ -682,6 +682,25 @@ struct opf_symbolic {
   Symbolic s;
 };
 
+// Factorise the Jacobian of the converged state if opf_powerflow left it
+// unfactorised (it does, so that a power flow whose factors nobody uses, such
+// as a trial point followed by another power flow, skips the refactorisation).
+opf_status opf::ensure_factors(opf_ctx* c) {
+  if (!c->factors_stale) return OPF_OK;
+  cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
+  launch_lu(c);
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaGetLastError());
+  c->factors_stale = false;
+  if (c->h_flags[0]) {
+    c->have_state = false;
+    FAIL(OPF_ESINGULAR, "singular Jacobian at the power-flow solution");
+  }
+  return OPF_OK;
+}
+
 extern "C" {
 
 opf_status opf_symbolic_analyze(const opf_network_desc* desc, opf_symbolic** out) {
@@ -734,32 +753,33 @@ opf_status opf_powerflow(opf_ctx* c, const double* u, const double* pd, const do
   opf_status result = OPF_ENOCONV;
   int it = 0;
   double res2 = NAN, resinf = NAN;
+  c->factors_stale = false;
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
   for (it = 0;; it++) {
     launch_unpack(c, c->x, c->u);
     CK(cudaMemsetAsync(c->LU, 0, c->dn.nnz * sizeof(double), st));
     CK(cudaMemsetAsync(c->scal, 0, 2 * sizeof(double), st));
-    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
     launch_pf_eval(c);
-    launch_lu(c);
     CK(cudaMemcpyAsync(c->h_scal, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     res2 = std::sqrt(c->h_scal[0]);
     resinf = c->h_scal[1];
+    if (c->h_flags[0]) {  // the previous iteration's refactorisation
+      result = OPF_ESINGULAR;
+      g_err = "zero or non-finite pivot in the LU refactorisation";
+      break;
+    }
     if (!std::isfinite(res2)) {
       result = OPF_ENOCONV;
       g_err = "non-finite power-flow residual";
       break;
     }
     if (res2 < tol) {
-      result = c->h_flags[0] ? OPF_ESINGULAR : OPF_OK;
-      if (result) g_err = "singular Jacobian at the solution";
-      break;
-    }
-    if (c->h_flags[0]) {
-      result = OPF_ESINGULAR;
-      g_err = "zero or non-finite pivot in the LU refactorisation";
+      // the Jacobian at the solution is in LU, factorised on first use
+      result = OPF_OK;
+      c->factors_stale = true;
       break;
     }
     if (it >= max_it) {
@@ -767,6 +787,7 @@ opf_status opf_powerflow(opf_ctx* c, const double* u, const double* pd, const do
       g_err = "Newton-Raphson reached max_it";
       break;
     }
+    launch_lu(c);
     launch_solve1(c, c->g, c->dvec, false, 1.0);
     launch_axpy(c, c->x, c->dvec, -1.0, nx);
   }
@@ -793,6 +814,7 @@ opf_status opf_reduced_gradient(opf_ctx* c, const opf_al_params* p, double* F, d
                                 double* grad_qd) {
   if (!c) FAIL(OPF_EINVAL, "ctx is NULL");
   if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  TRY(ensure_factors(c));
   TRY(check_al(c, p));
   cudaStream_t st = c->stream;
   launch_first_order(c, p, grad_s);
@@ -825,6 +847,7 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
                                double* H, opf_hess_info* info) {
   if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
   if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  TRY(ensure_factors(c));
   TRY(check_al(c, p));
   const bool tuned = !(o && o->block_k) && c->tuned_k > 0;
   int C = (o && o->block_k) ? o->block_k : (tuned ? c->tuned_k : 8);
@@ -919,6 +942,7 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     if (!c || !H[k]) FAIL(OPF_EINVAL, "null context or Hessian pointer in the batch");
     if (c->device != c0->device) FAIL(OPF_EINVAL, "all contexts of a batch must be on one device");
     if (!c->have_state) FAIL(OPF_ESTATE, "a context of the batch has no converged power flow");
+    TRY(ensure_factors(c));
     TRY(check_al(c, &params[k]));
     stride = std::max(stride, hvp_stride(c, C));
     order[k] = k;

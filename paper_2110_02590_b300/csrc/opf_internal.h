@@ -138,6 +138,7 @@ bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
                         int col_end);
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
+opf_status ensure_factors(opf_ctx* c);  // factorise the converged state's Jacobian if still pending
 // balanced: the single-network launch (tiles in whole waves over the SMs)
 HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced);
 int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  // tiles of a column range
@@ -201,6 +202,7 @@ struct opf_ctx {
   double* h_scal = nullptr;       // pinned host mirror of scal
   int* h_flags = nullptr;         // pinned host mirror of flags
   bool have_state = false;
+  bool factors_stale = false;     // LU holds the unfactorised Jacobian of the converged state
 
   // gradient / Hessian workspaces
   double *flows = nullptr;        // [4 nl]: Pf, Qf, Pt, Qt

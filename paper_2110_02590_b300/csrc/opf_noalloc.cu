@@ -73,6 +73,10 @@ extern "C" opf_status opf_reduced_hessian_noalloc(opf_ctx* c, const opf_al_param
     set_last_error("no converged power flow on this context");
     return OPF_ESTATE;
   }
+  {
+    const opf_status fs = ensure_factors(c);
+    if (fs != OPF_OK) return fs;
+  }
   if (!p || !p->sigma_c || !p->y || !p->s || !(p->rho >= 0.0)) {
     set_last_error("AL parameters need sigma_c, y, s and rho >= 0");
     return OPF_EINVAL;

@@ -668,6 +668,10 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     set_last_error("no converged power flow on this context");
     return OPF_ESTATE;
   }
+  {
+    const opf_status fs = ensure_factors(c);
+    if (fs != OPF_OK) return fs;
+  }
   if (!p->sigma_c || !p->y || !st->u || !st->s || !st->zl_u || !st->zu_u || !st->zl_s || !st->zu_s ||
       !st->u_lo || !st->u_hi || !st->s_lo || !st->s_hi || !st->x || !(st->mu >= 0.0) || !(p->rho > 0.0)) {
     set_last_error("opf_al_step needs every state array, mu >= 0 and rho > 0");
