@@ -131,14 +131,15 @@ __global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* fl
 
 // trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one TS x TS tile per CTA
 // (16 x 16 threads, (TS/16)^2 outputs each; TS = 32 when the trailing matrix is
-// small, so that more CTAs share the FP64 pipes).  first_col: only the first
-// tile column (bj = 0, the next panels' columns); else the tiles 1 <= bj <= bi.
+// small, so that more CTAs share the FP64 pipes).  The tiles are laid from the
+// origin k0 + kb + off: first_col, the first tile column only; else every
+// tile bj <= bi of the triangle.
 template <int TS>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag,
-                                                        int first_col) {
+                                                        int first_col, int off) {
   if (*flag) return;
   constexpr int R = TS / 16;
-  const int r0 = k0 + kb;
+  const int r0 = k0 + kb + off;  // origin of the tiled triangle
   int bi, bj;
   if (first_col) {
     bi = blockIdx.x;
@@ -148,8 +149,7 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
     bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
     while (bi * (bi + 1) / 2 > t) bi--;
-    bj = t - bi * (bi + 1) / 2 + 1;
-    bi += 1;
+    bj = t - bi * (bi + 1) / 2;
   }
   __shared__ double Pa[TS][NB + 1], Pb[TS][NB + 1];
   for (int q = threadIdx.x; q < TS * NB; q += blockDim.x) {
@@ -591,48 +591,52 @@ opf_status alloc_step(opf_ctx* c) {
   return OPF_OK;
 }
 
-// Right-looking with look-ahead: the diagonal block and panel of the next
-// column block run on the step's stream as soon as the first tile column of
-// the trailing update is done, while the rest of the trailing update runs on
-// a second stream.
+// Right-looking with look-ahead.  Per panel p: on the step's stream the
+// diagonal block, the panel and the update of the next panel's 32 columns;
+// on a second stream the update of the panel after that (published by an
+// event) and then the rest of the trailing triangle.  So the next panel's
+// update waits only for the strip it touches, and the bulk of each trailing
+// update overlaps the following panels' chain.
 opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag) {
   cudaStream_t s1 = c->stream, s2 = w->s2;
   SCK(cudaEventRecord(w->ch_start, s1));
   SCK(cudaStreamWaitEvent(s2, w->ch_start, 0));
+  bool strip_pending = false;  // ch_rest marks the previous panel's strip update
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
     chol_diag_kernel<<<1, 32, 0, s1>>>(A, n, k0, kb, flag);
     c->launches++;
     const int rest = n - k0 - kb;
-    if (rest > 0) {
-      chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s1>>>(A, n, k0, kb, flag);
+    if (rest <= 0) break;
+    chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s1>>>(A, n, k0, kb, flag);
+    c->launches++;
+    if (strip_pending) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
+    chol_syrk_kernel<32><<<nblk(rest, 32), 256, 0, s1>>>(A, n, k0, kb, flag, 1, 0);  // next panel
+    c->launches++;
+    strip_pending = false;
+    if (rest > NB) {
+      SCK(cudaEventRecord(w->ch_panel, s1));
+      SCK(cudaStreamWaitEvent(s2, w->ch_panel, 0));
+      // the panel after next (32 columns), published for the next panel's strip update
+      chol_syrk_kernel<32><<<nblk(rest - NB, 32), 256, 0, s2>>>(A, n, k0, kb, flag, 1, NB);
       c->launches++;
-      // tile width: 64, or 32 once the trailing triangle has fewer 64-tiles than
-      // two per SM (the first tile column then holds the next two panels)
-      const int nt64 = nblk(rest, 64);
-      const bool small = nt64 * (nt64 + 1) / 2 < 2 * c->sm_count;
-      const int nt = small ? nblk(rest, 32) : nt64;
-      // the rest of the previous trailing update covers this first tile column
-      if (k0 > 0) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
-      if (small)
-        chol_syrk_kernel<32><<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
-      else
-        chol_syrk_kernel<64><<<nt, 256, 0, s1>>>(A, n, k0, kb, flag, 1);
-      c->launches++;
-      if (nt > 1) {
-        SCK(cudaEventRecord(w->ch_panel, s1));
-        SCK(cudaStreamWaitEvent(s2, w->ch_panel, 0));
+      SCK(cudaEventRecord(w->ch_rest, s2));
+      strip_pending = true;
+      const int rest3 = rest - 2 * NB;  // the rest of the trailing triangle
+      if (rest3 > 0) {
+        const int nt64 = nblk(rest3, 64);
+        const bool small = nt64 * (nt64 + 1) / 2 < 2 * c->sm_count;
+        const int nt = small ? nblk(rest3, 32) : nt64;
         if (small)
-          chol_syrk_kernel<32><<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
+          chol_syrk_kernel<32><<<nt * (nt + 1) / 2, 256, 0, s2>>>(A, n, k0, kb, flag, 0, 2 * NB);
         else
-          chol_syrk_kernel<64><<<nt * (nt + 1) / 2 - nt, 256, 0, s2>>>(A, n, k0, kb, flag, 0);
+          chol_syrk_kernel<64><<<nt * (nt + 1) / 2, 256, 0, s2>>>(A, n, k0, kb, flag, 0, 2 * NB);
         c->launches++;
       }
-      SCK(cudaEventRecord(w->ch_rest, s2));
     }
   }
-  SCK(cudaEventRecord(w->ch_rest, s2));
-  SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
+  SCK(cudaEventRecord(w->ch_start, s2));
+  SCK(cudaStreamWaitEvent(s1, w->ch_start, 0));
   return OPF_OK;
 }
 
