@@ -663,7 +663,7 @@ __device__ __forceinline__ void sweep1(const DevNet& n, const double* __restrict
 // Single right-hand side: out = G_x^{-1} (scale b) or G_x^{-T} (scale b).  One CTA.
 // Dynamic shared memory: the packed dense triangle (s(s-1)/2 doubles) and, when
 // use_smem, the right-hand side (n_x doubles) after it.
-__global__ void __launch_bounds__(1024) solve1_kernel(DevNet n, const double* LU, const double* T,
+__global__ void __launch_bounds__(512) solve1_kernel(DevNet n, const double* LU, const double* T,
                                                        const double* invdiag, const double* b,
                                                        double* out, double* yg, int transposed,
                                                        double scale, int use_smem) {
@@ -1436,7 +1436,7 @@ void launch_lu(opf_ctx* c) {
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
   c->launches++;
-  solve1_kernel<<<1, 1024, c->solve1_smem, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
+  solve1_kernel<<<1, 512, c->solve1_smem, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
                                                         transposed ? 1 : 0, scale, c->solve1_use_smem_rhs ? 1 : 0);
 }
 
