@@ -156,6 +156,36 @@ void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
 struct StepWork;
 void free_step_work(opf_ctx* c);
 
+// Level-packed single-RHS sweeps (opf_sweep.cu).  The factor entries a sweep
+// reads are copied after each refactorisation into one contiguous stream per
+// (factor, direction): first the dense trailing triangle (packed by rows) and
+// 1 / U_rr of the trailing rows, then the levels, cut into chunks at block
+// boundaries so that each chunk fits a shared-memory ring slot.  Chunk c holds
+// a 32-byte header {records, warp tasks, padded entries, padded record values,
+// offset and length of chunk c + 2}, per warp task the record and group lane
+// of each of its 32 lanes, the records {lead row, entries, second row or -1,
+// first entry}, per record {coupling, scale of the lead row, scale of the
+// second row}, and the entries' columns, lead-row values and second-row values.
+struct SweepStream {
+  const unsigned char* base = nullptr;  // device bytes of the stream
+  int tri_len = 0;                      // bytes of the trailing-triangle segment at the start
+  int nch = 0;                          // chunks
+  int off0 = 0, len0 = 0, off1 = 0, len1 = 0;  // the first two chunks (bytes)
+};
+struct SweepStreams {
+  bool ok = false;       // false: the sweep keeps the level-record form (sweep1)
+  int slot = 0;          // ring slot bytes
+  int smem = 0;          // dynamic shared bytes of the streamed solve
+  SweepStream s[4];      // L of LU (forward), U of LU (backward), U^T from T (forward), L^T from T (backward)
+  int2* map = nullptr;   // {destination double, source}: source 2p (LU) / 2p + 1 (T), or -1 - row (1 / U_rr)
+  int nmap = 0;
+  double* values = nullptr;  // the streams' bytes, as doubles for the gather
+};
+opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
+                               const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b);
+void launch_sweep_pack(opf_ctx* c);  // after a refactorisation (captured in the LU graph)
+void launch_solve1_streamed(opf_ctx* c, const double* b, double* out, bool transposed, double scale);
+
 }  // namespace opf
 
 struct opf_ctx {
@@ -227,4 +257,5 @@ struct opf_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t lu_exec = nullptr;
   long long lu_graph_kernels = 0;
+  opf::SweepStreams sw;            // level-packed single-RHS sweep streams
 };

@@ -1427,6 +1427,7 @@ void launch_lu_kernels(opf_ctx* c) {
   c->launches++;
   lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
                                                            c->dn.nx, c->dn.nnz, c->flags);
+  launch_sweep_pack(c);
 }
 
 void launch_lu(opf_ctx* c) {
@@ -1435,6 +1436,10 @@ void launch_lu(opf_ctx* c) {
 }
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
+  if (c->sw.ok) {
+    launch_solve1_streamed(c, b, out, transposed, scale);
+    return;
+  }
   c->launches++;
   solve1_kernel<<<1, 512, c->solve1_smem, c->stream>>>(c->dn, c->LU, c->T, c->invdiag, b, out, c->yvec,
                                                         transposed ? 1 : 0, scale, c->solve1_use_smem_rhs ? 1 : 0);
