@@ -63,70 +63,87 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- Cholesky
 
-// Diagonal block [k0, k0 + kb) by one warp, no barriers: lane i holds row i of
-// the block in registers; column j's pivot uses one reciprocal square root
-// (d = a * rsqrt(a), 1/d = rsqrt(a)) and the column is broadcast by shuffles.
-__global__ void chol_diag_kernel(double* A, int n, int k0, int kb, int* flag) {
+// Diagonal block [k0, k0 + kb) and its inverse, one CTA of 32 warps: warp i
+// holds row i of the block (lane c: L_ic) and row i of X = L_kk^{-1} in
+// registers.  Step j: warp j's lane j forms the pivot with one reciprocal
+// square root (L_jj = a r, r = rsqrt(a)); the warps scale column j of L and row
+// j of X by r and publish them (double-buffered shared rows, two barriers per
+// step); then warp i > j updates its row: L_ic -= L_ij L_cj (j < c <= i) and
+// X_ic -= L_ij X_jc (c <= j), one FMA per lane.  X goes to Dinv (row-major),
+// used by the panel solve below and by the dense triangular solves.
+__global__ void __launch_bounds__(1024) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
+                                                         double* Dinv) {
   if (*flag) return;
-  const int lane = threadIdx.x;
-  double t[NB];
-#pragma unroll
-  for (int j = 0; j < NB; j++) t[j] = (lane < kb && j <= lane) ? A[(size_t)(k0 + j) * n + k0 + lane] : 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int j = 0; j < NB; j++) {
-    if (j < kb) {
-      double a = __shfl_sync(0xffffffffu, t[j], j);
+  __shared__ double s_r[2];
+  __shared__ double colj[2][NB], xrow[2][NB];
+  __shared__ int s_bad;
+  const int c = threadIdx.x & 31, i = threadIdx.x >> 5;
+  double t = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
+  double x = (i == c) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int j = 0; j < kb; j++) {
+    const int b = j & 1;
+    if (i == j && c == j) {
+      double a = t;
       if (!(a > 0.0) || !isfinite(a)) {
-        bad = true;
+        s_bad = 1;
         a = 1.0;
       }
       const double r = rsqrt(a);
-      if (lane == j) t[j] = a * r;
-      if (lane > j) t[j] *= r;
-      // trailing update: row lane, columns c in (j, lane]: t[c] -= l_lane * l_c
-      const double li = t[j];
-#pragma unroll
-      for (int c = j + 1; c < NB; c++) {
-        const double lc = __shfl_sync(0xffffffffu, li, c);
-        if (lane >= c && lane < kb) t[c] -= li * lc;
-      }
+      t = a * r;
+      s_r[b] = r;
+    }
+    __syncthreads();
+    const double r = s_r[b];
+    if (i > j && c == j) t *= r;  // L_ij
+    if (i == j && c <= j) x *= r;  // X_jc final
+    if (c == j && i < kb) colj[b][i] = t;  // column j of L (L_jj at i = j)
+    if (i == j) xrow[b][c] = x;
+    __syncthreads();
+    if (i > j && i < kb) {
+      const double lij = __shfl_sync(0xffffffffu, t, j);
+      if (c <= j)
+        x = fma(-lij, xrow[b][c], x);
+      else if (c <= i)
+        t = fma(-lij, colj[b][c], t);
     }
   }
-  if (lane == 0 && bad) *flag = 1;
-#pragma unroll
-  for (int j = 0; j < NB; j++)
-    if (lane < kb && j <= lane) A[(size_t)(k0 + j) * n + k0 + lane] = t[j];
+  __syncthreads();
+  if (threadIdx.x == 0 && s_bad) *flag = 1;
+  if (i < kb && c <= i) A[(size_t)(k0 + c) * n + k0 + i] = t;
+  Dinv[(size_t)(k0 / NB) * NB * NB + i * NB + c] = (i < kb && c <= i) ? x : 0.0;
 }
 
-__global__ void chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag) {
+// Panel below the diagonal block: X21 = A21 L_kk^{-T} = A21 Dinv^T as a small
+// GEMM (16 rows x 32 columns per CTA, 2 outputs per thread), written in place.
+__global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag,
+                                                        const double* __restrict__ Dinv) {
   if (*flag) return;
-  __shared__ double T[NB][NB + 1];
-  __shared__ double inv[NB];
-  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
-    const int i = t % kb, j = t / kb;
-    T[i][j] = A[(size_t)(k0 + j) * n + k0 + i];
+  __shared__ double M[NB][NB + 1];  // M[c][t] = (L_kk^{-1})_ct
+  __shared__ double P[16][NB + 1];  // P[r][t] = A21[row r][t]
+  const double* D = Dinv + (size_t)(k0 / NB) * NB * NB;
+  const int row0 = k0 + kb + blockIdx.x * 16;
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) M[q >> 5][q & 31] = D[q];
+  for (int q = threadIdx.x; q < 16 * NB; q += blockDim.x) {
+    const int r = q & 15, tt = q >> 4, g = row0 + r;
+    P[r][tt] = (tt < kb && g < n) ? A[(size_t)(k0 + tt) * n + g] : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x < kb) inv[threadIdx.x] = 1.0 / T[threadIdx.x][threadIdx.x];
-  __syncthreads();
-  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[NB];
+  const int r = threadIdx.x >> 4, c0 = (threadIdx.x & 15) * 2;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-  for (int j = 0; j < NB; j++) x[j] = (j < kb) ? A[(size_t)(k0 + j) * n + i] : 0.0;
-#pragma unroll
-  for (int j = 0; j < NB; j++) {
-    if (j < kb) {
-      double s = x[j];
-#pragma unroll
-      for (int t = 0; t < j; t++) s -= x[t] * T[j][t];
-      x[j] = s * inv[j];
-    }
+  for (int tt = 0; tt < NB; tt += 2) {
+    const double p0 = P[r][tt], p1 = P[r][tt + 1];
+    s0 = fma(p0, M[c0][tt], s0);
+    s1 = fma(p0, M[c0 + 1][tt], s1);
+    s2 = fma(p1, M[c0][tt + 1], s2);
+    s3 = fma(p1, M[c0 + 1][tt + 1], s3);
   }
-#pragma unroll
-  for (int j = 0; j < NB; j++)
-    if (j < kb) A[(size_t)(k0 + j) * n + i] = x[j];
+  const int g = row0 + r;
+  if (g < n) {
+    if (c0 < kb) A[(size_t)(k0 + c0) * n + g] = s0 + s2;
+    if (c0 + 1 < kb) A[(size_t)(k0 + c0 + 1) * n + g] = s1 + s3;
+  }
 }
 
 // trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one TS x TS tile per CTA
@@ -184,42 +201,22 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
 
 // ---------------------------------------------------------------- dense triangular solves
 
-// Inverses of the 32 x 32 diagonal blocks of the Cholesky factor (FP64 has a
-// long dependent-operation latency on this part, so the solves below multiply
-// by these instead of running 32-step substitutions with divisions).  One warp
-// per block: lane c builds column c of X = L_ii^{-1} (X[k][c] for k >= c).
-// Dinv[blk][r][c] = X[r][c] (row-major, zero above the diagonal).
-__global__ void chol_diag_inv_kernel(const double* __restrict__ L, int n, double* Dinv) {
-  __shared__ double T[32][33];
-  __shared__ double rinv[32];
-  const int blk = blockIdx.x, lane = threadIdx.x, r0 = blk * 32, kb = min(32, n - r0);
-  for (int j = 0; j < 32; j++) T[lane][j] = (lane < kb && j < kb) ? L[(size_t)(r0 + j) * n + r0 + lane] : 0.0;
-  rinv[lane] = lane < kb ? 1.0 / L[(size_t)(r0 + lane) * n + r0 + lane] : 1.0;
-  __syncwarp();
-  double x[32];
-#pragma unroll
-  for (int k = 0; k < 32; k++) x[k] = (k == lane) ? 1.0 : 0.0;
-#pragma unroll
-  for (int k = 0; k < 32; k++) {
-    x[k] *= rinv[k];  // x[k] final (zero for k < lane)
-#pragma unroll
-    for (int i = k + 1; i < 32; i++) x[i] -= T[i][k] * x[k];
-  }
-  double* D = Dinv + (size_t)blk * 1024;
-#pragma unroll
-  for (int k = 0; k < 32; k++) D[k * 32 + lane] = x[k];
-}
-
 // Dense triangular solve with the Cholesky factor in one cooperative launch
-// per direction (forward L y = b, backward L^T x = y; L lower, column-major,
-// leading dimension n; b is overwritten with the solution).  Row block i (32
-// rows) belongs to CTA i mod gridDim.x, which takes its blocks in solve order.
-// The warps of the CTA split the finished blocks k the block depends on (k < i
-// forward, k > i backward): each waits for block k's flag, then accumulates the
-// 32 x 32 block product; warp 0 applies the diagonal block's inverse and
-// publishes the block with the call's epoch (store, fence, release flag).
-// Every wait is bounded: on timeout the kernel sets err and stops waiting (the
-// result is then void).
+// per direction (forward L y = b, backward L^T x = y; b is overwritten with the
+// solution).  L is lower, column-major with leading dimension n, and its
+// transpose is copied into the strict upper triangle (chol_upper_copy_kernel),
+// so both directions read the off-diagonal block (row block i, column block k)
+// at (32 k + c) n + 32 i + lane: lanes along rows, coalesced.  Row block i
+// (32 rows) belongs to CTA i mod gridDim.x, which takes its blocks in solve
+// order.  Block i depends on the finished blocks k < i (forward) or k > i
+// (backward); the neighbour i -+ 1, the last to finish, is split over the 8
+// warps (4 columns each), the others go whole to the warps in turn, earliest
+// finished first.  Each
+// warp loads its tile before it waits for the block's flag; then it reads the
+// block's solution and accumulates.  The diagonal block's inverse (prefetched,
+// 4 columns per warp) gives the block's solution, which warp 0 publishes with
+// the call's epoch (store, fence, release flag).  Every wait is bounded: on
+// timeout the kernel sets err and stops waiting (the result is then void).
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -228,84 +225,104 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void wait_block(const unsigned* flag, unsigned epoch, int* err, int lane) {
+  long long spins = 0;
+  while (ld_acquire_u32(flag) != epoch) {
+    if (++spins > (1ll << 24) || *(volatile int*)err) {
+      if (lane == 0) atomicExch(err, 1);
+      break;
+    }
+    __nanosleep(32);
+  }
+}
+
+// L^T into the strict upper triangle, 32 x 32 tiles through shared memory.
+__global__ void chol_upper_copy_kernel(double* A, int n) {
+  __shared__ double T[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // tile of rows bi, columns bj of L (bi > bj)
+  if (bi <= bj) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += blockDim.x >> 5) {
+    const int row = bi * 32 + tx, col = bj * 32 + r;
+    T[r][tx] = (row < n && col < n) ? A[(size_t)col * n + row] : 0.0;  // L(row, col)
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += blockDim.x >> 5) {
+    const int col = bi * 32 + r, row = bj * 32 + tx;  // upper position (row, col) holds L(col, row)
+    if (row < n && col < n) A[(size_t)col * n + row] = T[tx][r];
+  }
+}
 
 template <bool FWD>
 __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict__ L, int n,
                                                         const double* __restrict__ Dinv, double* b,
                                                         unsigned* flags, unsigned epoch, int* err) {
   __shared__ double part[8][32];
+  __shared__ double accs[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = (n + 31) >> 5;
   for (int q = blockIdx.x; q < nb; q += gridDim.x) {
     const int i = FWD ? q : nb - 1 - q;
     const int row = i * 32 + lane;
     const bool live = row < n;
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-    const int k_lo = FWD ? 0 : i + 1, k_hi = FWD ? i : nb;
-    for (int k = k_lo + warp; k < k_hi; k += 8) {
-      long long spins = 0;
-      while (ld_acquire_u32(flags + k) != epoch) {
-        if (++spins > (1ll << 24) || *(volatile int*)err) {
-          if (lane == 0) atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-      const int col0 = k * 32;
-      const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
-      const int kc = min(32, n - col0);  // uniform over the warp: every lane shuffles
-      if (kc == 32) {
+    const double* D = Dinv + (size_t)i * 1024;
+    double dv[4];
 #pragma unroll
-        for (int c = 0; c < 32; c += 4) {
-          const double x0 = __shfl_sync(0xffffffffu, xk, c), x1 = __shfl_sync(0xffffffffu, xk, c + 1);
-          const double x2 = __shfl_sync(0xffffffffu, xk, c + 2), x3 = __shfl_sync(0xffffffffu, xk, c + 3);
-          if (live) {
-            if (FWD) {
-              p0 += L[(size_t)(col0 + c) * n + row] * x0;
-              p1 += L[(size_t)(col0 + c + 1) * n + row] * x1;
-              p2 += L[(size_t)(col0 + c + 2) * n + row] * x2;
-              p3 += L[(size_t)(col0 + c + 3) * n + row] * x3;
-            } else {
-              p0 += L[(size_t)row * n + col0 + c] * x0;
-              p1 += L[(size_t)row * n + col0 + c + 1] * x1;
-              p2 += L[(size_t)row * n + col0 + c + 2] * x2;
-              p3 += L[(size_t)row * n + col0 + c + 3] * x3;
-            }
-          }
-        }
-      } else {
-        for (int c = 0; c < kc; c++) {
-          const double xc = __shfl_sync(0xffffffffu, xk, c);
-          if (live) p0 += (FWD ? L[(size_t)(col0 + c) * n + row] : L[(size_t)row * n + col0 + c]) * xc;
-        }
+    for (int cc = 0; cc < 4; cc++) {
+      const int c = 4 * warp + cc;
+      dv[cc] = FWD ? D[lane * 32 + c] : D[c * 32 + lane];
+    }
+    const double bi = live ? b[row] : 0.0;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    // whole blocks, the earliest finished first: forward 0 .. i - 2, backward
+    // nb - 1 down to i + 2
+    const int nwhole = FWD ? i - 1 : nb - i - 2;
+    for (int m = warp; m < nwhole; m += 8) {
+      const int k = FWD ? m : nb - 1 - m;
+      const int col0 = k * 32, kc = min(32, n - col0);
+      double t[32];
+#pragma unroll
+      for (int c = 0; c < 32; c++) t[c] = (live && c < kc) ? L[(size_t)(col0 + c) * n + row] : 0.0;
+      wait_block(flags + k, epoch, err, lane);
+      const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        p0 = fma(t[c], __shfl_sync(0xffffffffu, xk, c), p0);
+        p1 = fma(t[c + 1], __shfl_sync(0xffffffffu, xk, c + 1), p1);
+        p2 = fma(t[c + 2], __shfl_sync(0xffffffffu, xk, c + 2), p2);
+        p3 = fma(t[c + 3], __shfl_sync(0xffffffffu, xk, c + 3), p3);
       }
+    }
+    // the neighbour block, 4 columns per warp
+    if (FWD ? i > 0 : i < nb - 1) {
+      const int k = FWD ? i - 1 : i + 1, col0 = k * 32, kc = min(32, n - col0);
+      double t4[4];
+#pragma unroll
+      for (int cc = 0; cc < 4; cc++) {
+        const int c = 4 * warp + cc;
+        t4[cc] = (live && c < kc) ? L[(size_t)(col0 + c) * n + row] : 0.0;
+      }
+      wait_block(flags + k, epoch, err, lane);
+      const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
+      p0 = fma(t4[0], __shfl_sync(0xffffffffu, xk, 4 * warp), p0);
+      p1 = fma(t4[1], __shfl_sync(0xffffffffu, xk, 4 * warp + 1), p1);
+      p2 = fma(t4[2], __shfl_sync(0xffffffffu, xk, 4 * warp + 2), p2);
+      p3 = fma(t4[3], __shfl_sync(0xffffffffu, xk, 4 * warp + 3), p3);
     }
     part[warp][lane] = (p0 + p1) + (p2 + p3);
     __syncthreads();
+    if (warp == 0)
+      accs[lane] = bi - (((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                         ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane])));
+    __syncthreads();
+    // x_i = L_ii^{-1} acc (forward) or L_ii^{-T} acc (backward), 4 columns per warp
+    part[warp][lane] = fma(dv[0], accs[4 * warp], dv[1] * accs[4 * warp + 1]) +
+                       fma(dv[2], accs[4 * warp + 2], dv[3] * accs[4 * warp + 3]);
+    __syncthreads();
     if (warp == 0) {
-      double acc = live ? b[row] : 0.0;
-      acc -= ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
-             ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
-      // x_i = L_ii^{-1} acc (forward) or L_ii^{-T} acc (backward)
-      const double* D = Dinv + (size_t)i * 1024;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll
-      for (int c = 0; c < 32; c += 4) {
-        const double a0 = __shfl_sync(0xffffffffu, acc, c), a1 = __shfl_sync(0xffffffffu, acc, c + 1);
-        const double a2 = __shfl_sync(0xffffffffu, acc, c + 2), a3 = __shfl_sync(0xffffffffu, acc, c + 3);
-        if (FWD) {
-          s0 += D[lane * 32 + c] * a0;
-          s1 += D[lane * 32 + c + 1] * a1;
-          s2 += D[lane * 32 + c + 2] * a2;
-          s3 += D[lane * 32 + c + 3] * a3;
-        } else {
-          s0 += D[c * 32 + lane] * a0;
-          s1 += D[(c + 1) * 32 + lane] * a1;
-          s2 += D[(c + 2) * 32 + lane] * a2;
-          s3 += D[(c + 3) * 32 + lane] * a3;
-        }
-      }
-      if (live) b[row] = (s0 + s1) + (s2 + s3);
+      const double x = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                       ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+      if (live) b[row] = x;
       __threadfence();
       __syncwarp();
       if (lane == 0) st_release_u32(flags + i, epoch);
@@ -604,11 +621,11 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
   bool strip_pending = false;  // ch_rest marks the previous panel's strip update
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = std::min(NB, n - k0);
-    chol_diag_kernel<<<1, 32, 0, s1>>>(A, n, k0, kb, flag);
+    chol_diag_kernel<<<1, 1024, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
     c->launches++;
     const int rest = n - k0 - kb;
     if (rest <= 0) break;
-    chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s1>>>(A, n, k0, kb, flag);
+    chol_trsm_kernel<<<nblk(rest, 16), 256, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
     c->launches++;
     if (strip_pending) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
     chol_syrk_kernel<32><<<nblk(rest, 32), 256, 0, s1>>>(A, n, k0, kb, flag, 1, 0);  // next panel
@@ -640,9 +657,9 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
   return OPF_OK;
 }
 
-opf_status launch_chol_solve(opf_ctx* c, StepWork* w, const double* A, int n, double* b) {
-  const int nb = (n + 31) / 32;
-  chol_diag_inv_kernel<<<nb, 32, 0, c->stream>>>(A, n, w->Dinv);
+opf_status launch_chol_solve(opf_ctx* c, StepWork* w, double* A, int n, double* b) {
+  const int nb = (n + 31) / 32;  // Dinv holds the diagonal blocks' inverses from the factorisation
+  chol_upper_copy_kernel<<<dim3(nb, nb), 256, 0, c->stream>>>(A, n);
   c->launches++;
   int occ = 0;
   SCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_trsv_kernel<true>, 256, 0));
