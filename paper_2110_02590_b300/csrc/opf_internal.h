@@ -181,6 +181,12 @@ struct SweepStreams {
   int nmap = 0;
   double* values = nullptr;  // the streams' bytes, as doubles for the gather
 };
+// FP64 rank-K update of a lower triangle emulated on bf16 tensor cores
+// (opf_ozaki.cu): A[r0 :, r0 :] -= P P^T with P = A[r0 : n, c0 : c0 + K],
+// K <= 128 a multiple of 32; E: n - r0 ints, D: 8 (n - r0) K bf16 workspace.
+opf_status setup_oz();
+void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag);
+
 opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
                                const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b);
 void launch_sweep_pack(opf_ctx* c);  // after a refactorisation (captured in the LU graph)

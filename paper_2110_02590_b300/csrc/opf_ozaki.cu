@@ -1,0 +1,282 @@
+// FP64 rank-K updates of a lower triangle, C -= P P^T, emulated exactly on the
+// bf16 tensor cores (the trailing updates of the Schur-complement Cholesky in
+// the reduced-Newton step, Prop. 3).
+//
+// Ozaki splitting: every row r of P (K <= 128 columns) is written in fixed
+// point against its own power of two, |P_rk| < 2^E_r, as eight signed 7-bit
+// digits, P_rk = sum_s d_s(r, k) 2^(E_r - 7 (s + 1)) + tail, |tail| < 2^(E_r - 56).
+// The digits are integers of magnitude <= 127, exact in bf16, and a product
+// of two is below 2^14, so for each level t = s + s' (eight levels, at most
+// eight digit pairs each) the sum over the K <= 128 columns stays below 2^24:
+// the tensor core's FP32 accumulation is exact in any order.  The FP64 result
+// is then sum_t 2^(E_r + E_c - 14 - 7 t) acc_t, summed in FP64.  Levels t >= 8
+// and the digit tails are dropped: each term of the update carries an error
+// below ~2^-53 |P_r|max |P_c|max, the order of an FP64 dot product's own
+// rounding bound.
+//
+// The digits are computed with integer shifts of the FP64 bit patterns (no
+// rounding step), and the tensor-core work is 36 digit pairs per output: the
+// B300's bf16 rate (~1.1 PFLOP/s for mma.sync in registers) against its FP64
+// rate (~1 TFLOP/s) makes this ~10-30 times faster than FP64 FMAs.
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "opf_internal.h"
+
+namespace opf {
+
+namespace {
+
+constexpr int OZ_S = 8;       // digits per value
+constexpr int OZ_TILE = 64;   // output tile (rows and columns)
+constexpr int OZ_KC = 32;     // columns staged per pass
+constexpr int OZ_PAD = 40;    // bf16 per staged row (32 + 8: conflict-free fragment loads)
+
+// |x| < 2^E for x != 0: the exponent of the bit above the leading one
+__device__ __forceinline__ int exp_bound(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const int ef = (int)(b >> 52);
+  if (ef) return ef - 1022;
+  return (64 - __clzll((long long)b)) - 1074;  // subnormal
+}
+
+// floor(|x| 2^(56 - E)) for |x| < 2^E, from the bit pattern
+__device__ __forceinline__ unsigned long long fixed56(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const int ef = (int)(b >> 52);
+  const unsigned long long mant = (b & 0x000fffffffffffffull) | (ef ? (1ull << 52) : 0ull);
+  const int ex = ef ? ef - 1075 : -1074;  // |x| = mant 2^ex
+  const int sh = ex + 56 - E;
+  if (sh >= 0) return mant << sh;
+  return (-sh >= 64) ? 0ull : (mant >> (-sh));
+}
+
+}  // namespace
+
+// Digits of P = A[r0 : r0 + M, c0 : c0 + K] (column-major A, leading dimension
+// n): E[r] and D[s][r][k] (bf16, row-major, K per row).  One CTA per 32 rows,
+// warps over the columns; the digits pass through shared memory so that both
+// the reads (along rows) and the writes (along columns) coalesce.
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, int n, int c0, int K, int r0,
+                                                      int M, int* __restrict__ E, __nv_bfloat16* __restrict__ D,
+                                                      const int* flag) {
+  if (*flag) return;
+  __shared__ int emax_s[8][32];
+  __shared__ __nv_bfloat16 dig[OZ_S][32][33];  // [digit][column in the pass][row]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  const bool live = r < M;
+  int em = -4096;
+  for (int k = w; k < K; k += 8) {
+    const double x = live ? A[(size_t)(c0 + k) * n + r0 + r] : 0.0;
+    if (x != 0.0) em = max(em, exp_bound(x));
+  }
+  emax_s[w][lane] = em;
+  __syncthreads();
+  if (w == 0) {
+    int m = emax_s[0][lane];
+    for (int q = 1; q < 8; q++) m = max(m, emax_s[q][lane]);
+    if (live) E[r] = m;
+    emax_s[0][lane] = m;
+  }
+  __syncthreads();
+  const int er = emax_s[0][lane];
+  for (int kt = 0; kt < K; kt += 32) {
+    for (int kk = w; kk < 32; kk += 8) {
+      const int k = kt + kk;
+      const double x = (live && k < K) ? A[(size_t)(c0 + k) * n + r0 + r] : 0.0;
+      const unsigned long long q = (x != 0.0) ? fixed56(x, er) : 0ull;
+      const bool neg = x < 0.0;
+#pragma unroll
+      for (int s = 0; s < OZ_S; s++) {
+        const int d = (int)((q >> (49 - 7 * s)) & 127ull);
+        dig[s][kk][lane] = __int2bfloat16_rn(neg ? -d : d);
+      }
+    }
+    __syncthreads();
+    for (int q = w; q < OZ_S * 32; q += 8) {
+      const int s = q >> 5, rr = q & 31, row = blockIdx.x * 32 + rr;
+      if (row < M && kt + lane < K) D[((size_t)s * M + row) * K + kt + lane] = dig[s][lane][rr];
+    }
+    __syncthreads();
+  }
+}
+
+namespace {
+
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned* r, const unsigned short* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void cp16(unsigned short* dst, const void* src, bool in) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = in ? 16 : 0;  // zero fill past the last row
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+
+constexpr int OZ_STAGE = 2 * OZ_S * OZ_TILE * OZ_PAD;  // bf16 per pipeline stage (tiles A and B)
+
+// Digits [0, NSL) of 64 rows from row0, columns [kt, kt + 32), into one stage.
+template <int NSL>
+__device__ __forceinline__ void oz_issue(unsigned short* S, const __nv_bfloat16* __restrict__ D, int M, int K,
+                                         int rowA, int rowB, int kt) {
+  constexpr int pieces = 2 * NSL * OZ_TILE * 4;  // 16-byte pieces (4 per staged row)
+  for (int q = threadIdx.x; q < pieces; q += blockDim.x) {
+    const int half = q / (NSL * OZ_TILE * 4), rem = q - half * NSL * OZ_TILE * 4;
+    const int s = rem / (OZ_TILE * 4), rem2 = rem - s * OZ_TILE * 4, rr = rem2 >> 2, pc = rem2 & 3;
+    const int row = (half ? rowB : rowA) + rr;
+    const bool in = row < M;
+    const __nv_bfloat16* src = D + ((size_t)s * M + (in ? row : 0)) * K + kt + pc * 8;
+    cp16(S + ((size_t)(half * OZ_S + s) * OZ_TILE + rr) * OZ_PAD + pc * 8, src, in);
+  }
+}
+
+// Levels TLO .. TLO + 3 (digit pairs i + j in that range, digits < NSL) over
+// all K columns, double-buffered; acc[l] holds level TLO + l (exact integers).
+template <int NSL, int TLO>
+__device__ __forceinline__ void oz_levels(float (&acc)[4][2][2][4], unsigned short* sm,
+                                          const __nv_bfloat16* __restrict__ D, int M, int K, int rowA, int rowB) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wr = warp >> 2, wc = warp & 3;
+#pragma unroll
+  for (int l = 0; l < 4; l++)
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+      for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[l][m][q][v] = 0.f;
+  const int nch = K / OZ_KC;
+  oz_issue<NSL>(sm, D, M, K, rowA, rowB, 0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int c = 0; c < nch; c++) {
+    if (c + 1 < nch) oz_issue<NSL>(sm + ((c + 1) & 1) * OZ_STAGE, D, M, K, rowA, rowB, (c + 1) * OZ_KC);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    const unsigned short* SA = sm + (c & 1) * OZ_STAGE;
+    const unsigned short* SB = SA + OZ_S * OZ_TILE * OZ_PAD;
+#pragma unroll
+    for (int ks = 0; ks < OZ_KC; ks += 16) {
+      unsigned b[NSL][4];  // per digit: columns wc*16 + [0, 8) and [8, 16), k halves
+#pragma unroll
+      for (int j = 0; j < NSL; j++)
+        ldsm_x4(b[j], SB + ((size_t)j * OZ_TILE + wc * 16 + (lane & 7) + ((lane >> 4) << 3)) * OZ_PAD + ks +
+                          ((lane >> 3) & 1) * 8);
+#pragma unroll
+      for (int i = 0; i < NSL; i++) {
+        unsigned a[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; m++)
+          ldsm_x4(a[m], SA + ((size_t)i * OZ_TILE + wr * 32 + m * 16 + (lane & 15)) * OZ_PAD + ks + (lane >> 4) * 8);
+#pragma unroll
+        for (int j = 0; j < NSL; j++) {
+          if (i + j < TLO || i + j > TLO + 3) continue;
+#pragma unroll
+          for (int m = 0; m < 2; m++)
+#pragma unroll
+            for (int q = 0; q < 2; q++) mma_bf16(acc[i + j - TLO][m][q], a[m], &b[j][2 * q]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// sum_l acc[l] 2^(7 (3 - l)) as an exact 64-bit integer (< 2^46); the level
+// sums are integers below 2^24
+__device__ __forceinline__ long long oz_fold(const float (&acc)[4][2][2][4], int m, int q, int v) {
+  long long s = 0;
+#pragma unroll
+  for (int l = 0; l < 4; l++) s += (long long)__float2int_rz(acc[l][m][q][v]) * (1ll << (7 * (3 - l)));
+  return s;
+}
+
+}  // namespace
+
+// C -= P P^T on the lower triangle of the trailing block A[r0 : r0 + M, r0 : r0 + M]
+// from the digits of P (oz_slice_kernel), one 64 x 64 tile (bi >= bj) per CTA.
+// Warps 2 x 4, each 32 x 16 outputs as 2 x 2 m16n8k16 tiles; fragments by
+// ldmatrix, digit tiles staged by cp.async (two stages).  Levels 0-3 use digits
+// 0-3 and levels 4-7 all eight; within each group the four FP32 level sums
+// (exact integers) fold into an exact 64-bit integer, which converts to FP64
+// exactly; the two groups meet in one FP64 fma.  Dynamic shared memory: two
+// stages of 2 x 8 x 64 x 40 bf16.
+__global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
+                                                     const __nv_bfloat16* __restrict__ D, const int* __restrict__ E,
+                                                     const int* flag) {
+  if (*flag) return;
+  extern __shared__ __align__(16) unsigned short oz_sm[];
+  const int t = blockIdx.x;
+  int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (bi * (bi + 1) / 2 > t) bi--;
+  while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+  const int bj = t - bi * (bi + 1) / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wr = warp >> 2, wc = warp & 3, g = lane >> 2, tq = lane & 3;
+  float acc[4][2][2][4];
+  double hi[2][2][4];
+  oz_levels<4, 0>(acc, oz_sm, D, M, K, bi * OZ_TILE, bj * OZ_TILE);
+#pragma unroll
+  for (int m = 0; m < 2; m++)
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) hi[m][q][v] = (double)oz_fold(acc, m, q, v);  // levels 0-3 x 2^21
+  oz_levels<8, 4>(acc, oz_sm, D, M, K, bi * OZ_TILE, bj * OZ_TILE);
+  const double s28 = __longlong_as_double((long long)(1023 - 28) << 52);  // 2^-28: levels 4-7 against 0-3
+#pragma unroll
+  for (int m = 0; m < 2; m++)
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        const int lr = bi * OZ_TILE + wr * 32 + m * 16 + g + (v >= 2 ? 8 : 0);
+        const int lc = bj * OZ_TILE + wc * 16 + q * 8 + 2 * tq + (v & 1);
+        if (lr < M && lc <= lr) {
+          const double sum = fma((double)oz_fold(acc, m, q, v), s28, hi[m][q][v]);  // x 2^21
+          const int e = E[lr] + E[lc] - 35;
+          const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                                      : ldexp(1.0, e);
+          double* p = A + (size_t)(r0 + lc) * n + r0 + lr;
+          *p = fma(-sum, sc, *p);
+        }
+      }
+}
+
+size_t oz_syrk_smem() { return 2 * sizeof(unsigned short) * (size_t)OZ_STAGE; }
+
+opf_status setup_oz() {
+  if (cudaFuncSetAttribute(oz_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_syrk_smem()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("cannot raise the shared-memory limit of the emulated FP64 update");
+    return OPF_ECUDA;
+  }
+  return OPF_OK;
+}
+
+// A[r0 :, r0 :] (lower) -= P P^T, P = A[r0 : n, c0 : c0 + K], K <= 128 and a
+// multiple of 32; E holds n - r0 ints, D 8 (n - r0) K bf16.
+void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag) {
+  const int M = n - r0;
+  if (M <= 0 || K <= 0) return;
+  __nv_bfloat16* Db = static_cast<__nv_bfloat16*>(D);
+  oz_slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(A, n, c0, K, r0, M, E, Db, flag);
+  const int nt = (M + OZ_TILE - 1) / OZ_TILE;
+  oz_syrk_kernel<<<nt * (nt + 1) / 2, 256, oz_syrk_smem(), st>>>(A, n, r0, M, K, Db, E, flag);
+}
+
+}  // namespace opf

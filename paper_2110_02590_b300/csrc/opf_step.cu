@@ -26,6 +26,8 @@ struct StepWork {
   double *dz;                                   // 2 n_u + 2 m: zl_u, zu_u, zl_s, zu_s steps
   double* red;                                  // [2]: alpha_p, alpha_d (as ordered bits)
   double* Dinv;                                 // [ceil(n_u / 32)][32][32]: inverses of the factor's diagonal blocks
+  int* oz_e = nullptr;                          // [n_u] row exponents of the emulated trailing update
+  void* oz_d = nullptr;                         // [8][n_u][128] bf16 digits of the emulated trailing update
   int* flag;
   double* h_red;
   int* h_flag;
@@ -42,6 +44,8 @@ void free_step_work(opf_ctx* c) {
   if (!c->stepw) return;
   StepWork* w = c->stepw;
   if (w->block) cudaFree(w->block);
+  if (w->oz_e) cudaFree(w->oz_e);
+  if (w->oz_d) cudaFree(w->oz_d);
   if (w->h_red) cudaFreeHost(w->h_red);
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
@@ -57,61 +61,98 @@ void free_step_work(opf_ctx* c) {
 
 namespace {
 
-constexpr int NB = 32;
+constexpr int NB = 32;   // panel width of the Cholesky
+constexpr int GB = 128;  // columns per group: rank of one emulated trailing update
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- Cholesky
 
-// Diagonal block [k0, k0 + kb) and its inverse, one CTA of 32 warps: warp i
-// holds row i of the block (lane c: L_ic) and row i of X = L_kk^{-1} in
-// registers.  Step j: warp j's lane j forms the pivot with one reciprocal
-// square root (L_jj = a r, r = rsqrt(a)); the warps scale column j of L and row
-// j of X by r and publish them (double-buffered shared rows, two barriers per
-// step); then warp i > j updates its row: L_ic -= L_ij L_cj (j < c <= i) and
-// X_ic -= L_ij X_jc (c <= j), one FMA per lane.  X goes to Dinv (row-major),
+// Diagonal block [k0, k0 + kb) and its inverse X = L_kk^{-1} in shared memory,
+// one CTA of 16 warps.  The chain per column is the pivot's reciprocal square
+// root: in step j, phase A scales column j of L and row j of X by r_j and
+// thread 0 forms the next pivot A_{j+1,j+1} - L_{j+1,j}^2; phase B applies the
+// rank-one update to the rest of the trailing triangle (L_ic -= L_ij L_cj) and
+// to X (X_ic -= L_ij X_jc, c <= j), packed over the threads, while thread 0
+// takes the next pivot's rsqrt.  A warp FP64 instruction costs the SM the same
+// whatever its active lanes, hence the packing.  X goes to Dinv (row-major),
 // used by the panel solve below and by the dense triangular solves.
-__global__ void __launch_bounds__(1024) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
-                                                         double* Dinv) {
+__global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
+                                                        double* Dinv) {
   if (*flag) return;
+  __shared__ double T[NB][NB + 1], X[NB][NB + 1];
   __shared__ double s_r[2];
-  __shared__ double colj[2][NB], xrow[2][NB];
+  __shared__ unsigned short tbl[NB * (NB + 1) / 2];  // packed (row, column) offsets of a triangle
   __shared__ int s_bad;
-  const int c = threadIdx.x & 31, i = threadIdx.x >> 5;
-  double t = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
-  double x = (i == c) ? 1.0 : 0.0;
-  if (threadIdx.x == 0) s_bad = 0;
-  for (int j = 0; j < kb; j++) {
-    const int b = j & 1;
-    if (i == j && c == j) {
-      double a = t;
-      if (!(a > 0.0) || !isfinite(a)) {
-        s_bad = 1;
-        a = 1.0;
-      }
-      const double r = rsqrt(a);
-      t = a * r;
-      s_r[b] = r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < NB * NB; q += nt) {
+    const int i = q >> 5, c = q & 31;
+    T[i][c] = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
+    X[i][c] = (i == c) ? 1.0 : 0.0;
+  }
+  for (int e = tid; e < NB * (NB + 1) / 2; e += nt) {
+    int ri = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    while (ri * (ri + 1) / 2 > e) ri--;
+    while ((ri + 1) * (ri + 2) / 2 <= e) ri++;
+    tbl[e] = (unsigned short)((ri << 8) | (e - ri * (ri + 1) / 2));
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  if (tid == 0) {
+    double a = T[0][0];
+    if (!(a > 0.0) || !isfinite(a)) {
+      s_bad = 1;
+      a = 1.0;
     }
-    __syncthreads();
-    const double r = s_r[b];
-    if (i > j && c == j) t *= r;  // L_ij
-    if (i == j && c <= j) x *= r;  // X_jc final
-    if (c == j && i < kb) colj[b][i] = t;  // column j of L (L_jj at i = j)
-    if (i == j) xrow[b][c] = x;
-    __syncthreads();
-    if (i > j && i < kb) {
-      const double lij = __shfl_sync(0xffffffffu, t, j);
-      if (c <= j)
-        x = fma(-lij, xrow[b][c], x);
-      else if (c <= i)
-        t = fma(-lij, colj[b][c], t);
-    }
+    const double r = rsqrt(a);
+    T[0][0] = a * r;
+    s_r[0] = r;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && s_bad) *flag = 1;
-  if (i < kb && c <= i) A[(size_t)(k0 + c) * n + k0 + i] = t;
-  Dinv[(size_t)(k0 / NB) * NB * NB + i * NB + c] = (i < kb && c <= i) ? x : 0.0;
+  for (int j = 0; j < kb; j++) {
+    const double r = s_r[j & 1];
+    const int m = kb - 1 - j;  // rows below the pivot
+    // phase A: column j of L, row j of X; thread 0 forms the next pivot
+    if (tid < m) {
+      const double l = T[j + 1 + tid][j] * r;
+      T[j + 1 + tid][j] = l;
+      if (tid == 0) T[j + 1][j + 1] = fma(-l, l, T[j + 1][j + 1]);
+    } else if (tid >= 32 && tid <= 32 + j) {
+      X[j][tid - 32] *= r;
+    }
+    __syncthreads();
+    // phase B: the rest of the trailing triangle and X; thread 0: the next pivot's rsqrt
+    if (tid == 0) {
+      if (m > 0) {
+        double a = T[j + 1][j + 1];
+        if (!(a > 0.0) || !isfinite(a)) {
+          s_bad = 1;
+          a = 1.0;
+        }
+        const double rn = rsqrt(a);
+        T[j + 1][j + 1] = a * rn;
+        s_r[(j + 1) & 1] = rn;
+      }
+    } else {
+      const int nT = m * (m + 1) / 2, nX = m * (j + 1);
+      for (int e = tid; e < nT + nX; e += nt - 1) {  // threads 1 .. nt - 1; e = 0 is the next pivot
+        if (e < nT) {
+          const int t = tbl[e], ii = j + 1 + (t >> 8), cc = j + 1 + (t & 255);
+          T[ii][cc] = fma(-T[ii][j], T[cc][j], T[ii][cc]);
+        } else {
+          const int e2 = e - nT, ri = e2 / (j + 1), cc = e2 - ri * (j + 1), ii = j + 1 + ri;
+          X[ii][cc] = fma(-T[ii][j], X[j][cc], X[ii][cc]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) *flag = 1;
+  for (int q = tid; q < NB * NB; q += nt) {
+    const int i = q >> 5, c = q & 31;
+    if (i < kb && c <= i) A[(size_t)(k0 + c) * n + k0 + i] = T[i][c];
+    Dinv[(size_t)(k0 / NB) * NB * NB + q] = (i < kb && c <= i) ? X[i][c] : 0.0;
+  }
 }
 
 // Panel below the diagonal block: X21 = A21 L_kk^{-T} = A21 Dinv^T as a small
@@ -147,18 +188,23 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0
 }
 
 // trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one TS x TS tile per CTA
-// (16 x 16 threads, (TS/16)^2 outputs each; TS = 32 when the trailing matrix is
-// small, so that more CTAs share the FP64 pipes).  The tiles are laid from the
-// origin k0 + kb + off: first_col, the first tile column only; else every
-// tile bj <= bi of the triangle.
+// (16 x 16 threads, (TS/16)^2 outputs each).  The tiles are laid from the
+// origin r0 = k0 + kb + off: first_col = 1, the first tile column only; 2, a
+// grid of tile columns x tile rows (blockIdx.x, blockIdx.y; tiles above the
+// diagonal skipped); else every tile bj <= bi of the triangle.  Columns at or
+// past col_end are left alone.
 template <int TS>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag,
-                                                        int first_col, int off) {
+                                                        int first_col, int off, int col_end) {
   if (*flag) return;
   constexpr int R = TS / 16;
   const int r0 = k0 + kb + off;  // origin of the tiled triangle
   int bi, bj;
-  if (first_col) {
+  if (first_col == 2) {  // rectangle of tile rows x tile columns, upper tiles skipped
+    bi = blockIdx.y;
+    bj = blockIdx.x;
+    if (bi < bj) return;
+  } else if (first_col) {
     bi = blockIdx.x;
     bj = 0;
   } else {
@@ -195,7 +241,7 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
 #pragma unroll
     for (int q = 0; q < R; q++) {
       const int gi = r0 + bi * TS + ty * R + p, gj = r0 + bj * TS + tx * R + q;
-      if (gi < n && gj <= gi) A[(size_t)gj * n + gi] -= acc[p][q];
+      if (gi < n && gj <= gi && gj < col_end) A[(size_t)gj * n + gi] -= acc[p][q];
     }
 }
 
@@ -594,6 +640,22 @@ opf_status alloc_step(opf_ctx* c) {
     set_last_error("cannot allocate pinned step buffers");
     return OPF_ENOMEM;
   }
+  if (cudaMalloc(&w->oz_e, sizeof(int) * (size_t)nu) != cudaSuccess ||
+      cudaMalloc(&w->oz_d, (size_t)2 * 8 * GB * (size_t)nu) != cudaSuccess) {
+    cudaGetLastError();
+    c->stepw = w;
+    free_step_work(c);
+    set_last_error("cannot allocate the emulated-update workspace");
+    return OPF_ENOMEM;
+  }
+  {
+    const opf_status so = setup_oz();
+    if (so != OPF_OK) {
+      c->stepw = w;
+      free_step_work(c);
+      return so;
+    }
+  }
   if (cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ch_start, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ch_panel, cudaEventDisableTiming) != cudaSuccess ||
@@ -608,52 +670,34 @@ opf_status alloc_step(opf_ctx* c) {
   return OPF_OK;
 }
 
-// Right-looking with look-ahead.  Per panel p: on the step's stream the
-// diagonal block, the panel and the update of the next panel's 32 columns;
-// on a second stream the update of the panel after that (published by an
-// event) and then the rest of the trailing triangle.  So the next panel's
-// update waits only for the strip it touches, and the bulk of each trailing
-// update overlaps the following panels' chain.
+// Blocked Cholesky in groups of GB = 128 columns.  Inside a group, 32-wide
+// panels run right-looking in FP64 (diagonal block with its inverse, panel
+// solve, update of the group's remaining columns); after the group, the rest of
+// the trailing triangle takes the group's rank-128 update at once, emulated on
+// the tensor cores (launch_oz_update: exact digit products, FP64 sums).
 opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag) {
-  cudaStream_t s1 = c->stream, s2 = w->s2;
-  SCK(cudaEventRecord(w->ch_start, s1));
-  SCK(cudaStreamWaitEvent(s2, w->ch_start, 0));
-  bool strip_pending = false;  // ch_rest marks the previous panel's strip update
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
-    chol_diag_kernel<<<1, 1024, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
-    c->launches++;
-    const int rest = n - k0 - kb;
-    if (rest <= 0) break;
-    chol_trsm_kernel<<<nblk(rest, 16), 256, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
-    c->launches++;
-    if (strip_pending) SCK(cudaStreamWaitEvent(s1, w->ch_rest, 0));
-    chol_syrk_kernel<32><<<nblk(rest, 32), 256, 0, s1>>>(A, n, k0, kb, flag, 1, 0);  // next panel
-    c->launches++;
-    strip_pending = false;
-    if (rest > NB) {
-      SCK(cudaEventRecord(w->ch_panel, s1));
-      SCK(cudaStreamWaitEvent(s2, w->ch_panel, 0));
-      // the panel after next (32 columns), published for the next panel's strip update
-      chol_syrk_kernel<32><<<nblk(rest - NB, 32), 256, 0, s2>>>(A, n, k0, kb, flag, 1, NB);
+  cudaStream_t s1 = c->stream;
+  for (int c0 = 0; c0 < n; c0 += GB) {
+    const int c1 = std::min(n, c0 + GB);
+    for (int k0 = c0; k0 < c1; k0 += NB) {
+      const int kb = std::min(NB, n - k0);
+      chol_diag_kernel<<<1, 512, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
       c->launches++;
-      SCK(cudaEventRecord(w->ch_rest, s2));
-      strip_pending = true;
-      const int rest3 = rest - 2 * NB;  // the rest of the trailing triangle
-      if (rest3 > 0) {
-        const int nt64 = nblk(rest3, 64);
-        const bool small = nt64 * (nt64 + 1) / 2 < 2 * c->sm_count;
-        const int nt = small ? nblk(rest3, 32) : nt64;
-        if (small)
-          chol_syrk_kernel<32><<<nt * (nt + 1) / 2, 256, 0, s2>>>(A, n, k0, kb, flag, 0, 2 * NB);
-        else
-          chol_syrk_kernel<64><<<nt * (nt + 1) / 2, 256, 0, s2>>>(A, n, k0, kb, flag, 0, 2 * NB);
+      const int rest = n - k0 - kb;
+      if (rest <= 0) break;
+      chol_trsm_kernel<<<nblk(rest, 16), 256, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
+      c->launches++;
+      if (k0 + kb < c1) {  // the group's remaining columns, all rows below
+        const dim3 grid(nblk(c1 - k0 - kb, 32), nblk(rest, 32));
+        chol_syrk_kernel<32><<<grid, 256, 0, s1>>>(A, n, k0, kb, flag, 2, 0, c1);
         c->launches++;
       }
     }
+    if (c1 < n) {
+      launch_oz_update(s1, A, n, c0, c1 - c0, c1, w->oz_e, w->oz_d, flag);
+      c->launches += 2;
+    }
   }
-  SCK(cudaEventRecord(w->ch_start, s2));
-  SCK(cudaStreamWaitEvent(s1, w->ch_start, 0));
   return OPF_OK;
 }
 
