@@ -186,6 +186,12 @@ struct SweepStreams {
 // K <= 128 a multiple of 32; E: n - r0 ints, D: 8 (n - r0) K bf16 workspace.
 opf_status setup_oz();
 void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag);
+// the two halves of launch_oz_update: digits, then the tiles of one part (0 all,
+// 1 the first 128 columns, 2 the rest) on at most grid CTAs (0: one per tile)
+void launch_oz_slice(cudaStream_t st, const double* A, int n, int c0, int K, int r0, int* E, void* D,
+                     const int* flag);
+void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D, const int* flag,
+                    int part, int grid);
 
 opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
                                const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b);

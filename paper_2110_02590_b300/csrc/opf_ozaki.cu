@@ -21,6 +21,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "opf_internal.h"
@@ -57,19 +59,20 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int E) {
 
 // Digits of P = A[r0 : r0 + M, c0 : c0 + K] (column-major A, leading dimension
 // n): E[r] and D[s][r][k] (bf16, row-major, K per row).  One CTA per 32 rows,
-// warps over the columns; the digits pass through shared memory so that both
+// its 32 warps over the columns; the digits pass through shared memory so that both
 // the reads (along rows) and the writes (along columns) coalesce.
-__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, int n, int c0, int K, int r0,
+__global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict__ A, int n, int c0, int K, int r0,
                                                       int M, int* __restrict__ E, __nv_bfloat16* __restrict__ D,
                                                       const int* flag) {
   if (*flag) return;
-  __shared__ int emax_s[8][32];
+  __shared__ int emax_s[32][32];
   __shared__ __nv_bfloat16 dig[OZ_S][32][33];  // [digit][column in the pass][row]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int r = blockIdx.x * 32 + lane;
   const bool live = r < M;
   int em = -4096;
-  for (int k = w; k < K; k += 8) {
+  const int nw = blockDim.x >> 5;
+  for (int k = w; k < K; k += nw) {
     const double x = live ? A[(size_t)(c0 + k) * n + r0 + r] : 0.0;
     if (x != 0.0) em = max(em, exp_bound(x));
   }
@@ -77,14 +80,14 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
   __syncthreads();
   if (w == 0) {
     int m = emax_s[0][lane];
-    for (int q = 1; q < 8; q++) m = max(m, emax_s[q][lane]);
+    for (int q = 1; q < nw; q++) m = max(m, emax_s[q][lane]);
     if (live) E[r] = m;
     emax_s[0][lane] = m;
   }
   __syncthreads();
   const int er = emax_s[0][lane];
   for (int kt = 0; kt < K; kt += 32) {
-    for (int kk = w; kk < 32; kk += 8) {
+    for (int kk = w; kk < 32; kk += nw) {
       const int k = kt + kk;
       const double x = (live && k < K) ? A[(size_t)(c0 + k) * n + r0 + r] : 0.0;
       const unsigned long long q = (x != 0.0) ? fixed56(x, er) : 0ull;
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
       }
     }
     __syncthreads();
-    for (int q = w; q < OZ_S * 32; q += 8) {
+    for (int q = w; q < OZ_S * 32; q += nw) {
       const int s = q >> 5, rr = q & 31, row = blockIdx.x * 32 + rr;
       if (row < M && kt + lane < K) D[((size_t)s * M + row) * K + kt + lane] = dig[s][lane][rr];
     }
@@ -214,16 +217,8 @@ __device__ __forceinline__ long long oz_fold(const float (&acc)[4][2][2][4], int
 // (exact integers) fold into an exact 64-bit integer, which converts to FP64
 // exactly; the two groups meet in one FP64 fma.  Dynamic shared memory: two
 // stages of 2 x 8 x 64 x 40 bf16.
-__global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
-                                                     const __nv_bfloat16* __restrict__ D, const int* __restrict__ E,
-                                                     const int* flag) {
-  if (*flag) return;
-  extern __shared__ __align__(16) unsigned short oz_sm[];
-  const int t = blockIdx.x;
-  int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-  while (bi * (bi + 1) / 2 > t) bi--;
-  while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
-  const int bj = t - bi * (bi + 1) / 2;
+__device__ __forceinline__ void oz_tile(double* A, int n, int r0, int M, int K, const __nv_bfloat16* __restrict__ D,
+                                        const int* __restrict__ E, unsigned short* oz_sm, int bi, int bj) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wr = warp >> 2, wc = warp & 3, g = lane >> 2, tq = lane & 3;
   float acc[4][2][2][4];
@@ -256,6 +251,29 @@ __global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r
       }
 }
 
+// The tiles of one launch: strip = 0, the lower triangle of tile rows and
+// columns from toff on; strip = 1, tile columns toff and toff + 1 (the next
+// 128 columns), every row tile at or below them.  CTAs loop over the tiles.
+__global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
+                                                     const __nv_bfloat16* __restrict__ D, const int* __restrict__ E,
+                                                     const int* flag, int strip, int toff, int ntiles) {
+  if (*flag) return;
+  extern __shared__ __align__(16) unsigned short oz_sm[];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int bi, bj;
+    if (strip) {  // (0, 0), then (1, 0), (1, 1), (2, 0), (2, 1), ...
+      bi = t == 0 ? 0 : (t + 1) >> 1;
+      bj = t == 0 ? 0 : (t + 1) & 1;
+    } else {
+      bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+      while (bi * (bi + 1) / 2 > t) bi--;
+      while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+      bj = t - bi * (bi + 1) / 2;
+    }
+    oz_tile(A, n, r0, M, K, D, E, oz_sm, bi + toff, bj + toff);
+  }
+}
+
 size_t oz_syrk_smem() { return 2 * sizeof(unsigned short) * (size_t)OZ_STAGE; }
 
 opf_status setup_oz() {
@@ -268,15 +286,42 @@ opf_status setup_oz() {
   return OPF_OK;
 }
 
-// A[r0 :, r0 :] (lower) -= P P^T, P = A[r0 : n, c0 : c0 + K], K <= 128 and a
-// multiple of 32; E holds n - r0 ints, D 8 (n - r0) K bf16.
-void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag) {
+// Digits of P = A[r0 : n, c0 : c0 + K] (K <= 128, a multiple of 32) into E
+// (n - r0 ints) and D (8 (n - r0) K bf16).
+void launch_oz_slice(cudaStream_t st, const double* A, int n, int c0, int K, int r0, int* E, void* D,
+                     const int* flag) {
   const int M = n - r0;
   if (M <= 0 || K <= 0) return;
-  __nv_bfloat16* Db = static_cast<__nv_bfloat16*>(D);
-  oz_slice_kernel<<<(M + 31) / 32, 256, 0, st>>>(A, n, c0, K, r0, M, E, Db, flag);
+  oz_slice_kernel<<<(M + 31) / 32, 1024, 0, st>>>(A, n, c0, K, r0, M, E, static_cast<__nv_bfloat16*>(D), flag);
+}
+
+// A[r0 :, r0 :] (lower) -= P P^T from the digits: part = 0 the whole triangle,
+// 1 the first 128 columns (all rows below), 2 the columns after them; grid 0
+// takes one CTA per tile, else at most grid CTAs.
+void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D, const int* flag,
+                    int part, int grid) {
+  const int M = n - r0;
+  if (M <= 0 || K <= 0) return;
   const int nt = (M + OZ_TILE - 1) / OZ_TILE;
-  oz_syrk_kernel<<<nt * (nt + 1) / 2, 256, oz_syrk_smem(), st>>>(A, n, r0, M, K, Db, E, flag);
+  int ntiles = 0, strip = 0, toff = 0;
+  if (part == 0) {
+    ntiles = nt * (nt + 1) / 2;
+  } else if (part == 1) {
+    strip = 1;
+    ntiles = 2 * nt - 1;
+  } else {
+    toff = 2;
+    ntiles = nt > 2 ? (nt - 2) * (nt - 1) / 2 : 0;
+  }
+  if (ntiles <= 0) return;
+  const int g = grid > 0 ? std::min(grid, ntiles) : ntiles;
+  oz_syrk_kernel<<<g, 256, oz_syrk_smem(), st>>>(A, n, r0, M, K, static_cast<const __nv_bfloat16*>(D), E, flag,
+                                                strip, toff, ntiles);
+}
+
+void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag) {
+  launch_oz_slice(st, A, n, c0, K, r0, E, D, flag);
+  launch_oz_syrk(st, A, n, K, r0, E, D, flag, 0, 0);
 }
 
 }  // namespace opf

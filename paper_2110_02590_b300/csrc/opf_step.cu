@@ -33,11 +33,9 @@ struct StepWork {
   int* h_flag;
   void* block = nullptr;
   cudaEvent_t ev[7] = {};  // phase boundaries of a step
-  cudaStream_t s2 = nullptr;  // second stream of the Cholesky look-ahead
   unsigned* trsv_flags = nullptr;  // [ceil(n_u / 32)] block flags of the dense solves (epochs)
   int* trsv_err = nullptr;         // a dense-solve wait timed out
   unsigned trsv_epoch = 0;
-  cudaEvent_t ch_start = nullptr, ch_panel = nullptr, ch_rest = nullptr;
 };
 
 void free_step_work(opf_ctx* c) {
@@ -50,9 +48,6 @@ void free_step_work(opf_ctx* c) {
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {w->ch_start, w->ch_panel, w->ch_rest})
-    if (e) cudaEventDestroy(e);
-  if (w->s2) cudaStreamDestroy(w->s2);
   delete w;
   c->stepw = nullptr;
 }
@@ -69,22 +64,24 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 // ---------------------------------------------------------------- Cholesky
 
 // Diagonal block [k0, k0 + kb) and its inverse X = L_kk^{-1} in shared memory,
-// one CTA of 16 warps.  The chain per column is the pivot's reciprocal square
-// root: in step j, phase A scales column j of L and row j of X by r_j and
-// thread 0 forms the next pivot A_{j+1,j+1} - L_{j+1,j}^2; phase B applies the
-// rank-one update to the rest of the trailing triangle (L_ic -= L_ij L_cj) and
-// to X (X_ic -= L_ij X_jc, c <= j), packed over the threads, while thread 0
-// takes the next pivot's rsqrt.  A warp FP64 instruction costs the SM the same
-// whatever its active lanes, hence the packing.  X goes to Dinv (row-major),
-// used by the panel solve below and by the dense triangular solves.
+// one CTA of 16 warps in two roles.  Warp 0 carries the pivot chain in
+// registers (lane i: row i of the current column): column j's pivot takes one
+// reciprocal square root, the scaled column is published, and after the step's
+// barrier warp 0 loads column j + 1 (updated by the other warps through column
+// j - 1) and applies column j's rank-one term to it itself.  The other 15 warps
+// lag one column: after barrier j they scale row j of X and apply column j to
+// the columns from j + 2 on and to X (L_ic -= L_ij L_cj, X_ic -= L_ij X_jc),
+// packed over their threads.  So the chain per column is rsqrt + two FP64 ops
+// + one barrier.  X goes to Dinv (row-major), used by the panel solve below and
+// by the dense triangular solves.
 __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
                                                         double* Dinv) {
   if (*flag) return;
   __shared__ double T[NB][NB + 1], X[NB][NB + 1];
-  __shared__ double s_r[2];
+  __shared__ double s_r[NB];
   __shared__ unsigned short tbl[NB * (NB + 1) / 2];  // packed (row, column) offsets of a triangle
   __shared__ int s_bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   for (int q = tid; q < NB * NB; q += nt) {
     const int i = q >> 5, c = q & 31;
     T[i][c] = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
@@ -98,46 +95,39 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
   }
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  if (tid == 0) {
-    double a = T[0][0];
-    if (!(a > 0.0) || !isfinite(a)) {
-      s_bad = 1;
-      a = 1.0;
-    }
-    const double r = rsqrt(a);
-    T[0][0] = a * r;
-    s_r[0] = r;
-  }
-  __syncthreads();
-  for (int j = 0; j < kb; j++) {
-    const double r = s_r[j & 1];
-    const int m = kb - 1 - j;  // rows below the pivot
-    // phase A: column j of L, row j of X; thread 0 forms the next pivot
-    if (tid < m) {
-      const double l = T[j + 1 + tid][j] * r;
-      T[j + 1 + tid][j] = l;
-      if (tid == 0) T[j + 1][j + 1] = fma(-l, l, T[j + 1][j + 1]);
-    } else if (tid >= 32 && tid <= 32 + j) {
-      X[j][tid - 32] *= r;
-    }
-    __syncthreads();
-    // phase B: the rest of the trailing triangle and X; thread 0: the next pivot's rsqrt
-    if (tid == 0) {
-      if (m > 0) {
-        double a = T[j + 1][j + 1];
-        if (!(a > 0.0) || !isfinite(a)) {
-          s_bad = 1;
-          a = 1.0;
-        }
-        const double rn = rsqrt(a);
-        T[j + 1][j + 1] = a * rn;
-        s_r[(j + 1) & 1] = rn;
+  if (warp == 0) {
+    double col = T[lane][0];
+    for (int j = 0; j < kb; j++) {
+      double a = __shfl_sync(0xffffffffu, col, j);
+      const bool bad = !(a > 0.0) || !isfinite(a);
+      double r = rsqrt(a);
+      if (bad) {
+        a = 1.0;
+        r = 1.0;
       }
-    } else {
-      const int nT = m * (m + 1) / 2, nX = m * (j + 1);
-      for (int e = tid; e < nT + nX; e += nt - 1) {  // threads 1 .. nt - 1; e = 0 is the next pivot
+      const double l = (lane == j) ? a * r : col * r;
+      if (lane >= j && lane < kb) T[lane][j] = l;
+      if (lane == 0) {
+        s_r[j] = r;
+        if (bad) s_bad = 1;
+      }
+      __syncthreads();  // column j published; the other warps' column j - 1 applied
+      if (j + 1 < kb) {
+        const double lj1 = __shfl_sync(0xffffffffu, l, j + 1);
+        col = fma(-l, lj1, T[lane][j + 1]);
+      }
+    }
+  } else {
+    const int bt = tid - 32, nbt = nt - 32;
+    for (int j = 0; j < kb; j++) {
+      __syncthreads();
+      if (warp == 1 && lane <= j) X[j][lane] *= s_r[j];
+      asm volatile("bar.sync 1, %0;" ::"r"(nbt) : "memory");
+      const int m2 = kb - 2 - j;  // columns j + 2 .. kb - 1 of the trailing triangle
+      const int nT = m2 > 0 ? m2 * (m2 + 1) / 2 : 0, nX = (kb - 1 - j) * (j + 1);
+      for (int e = bt; e < nT + nX; e += nbt) {
         if (e < nT) {
-          const int t = tbl[e], ii = j + 1 + (t >> 8), cc = j + 1 + (t & 255);
+          const int t = tbl[e], ii = j + 2 + (t >> 8), cc = j + 2 + (t & 255);
           T[ii][cc] = fma(-T[ii][j], T[cc][j], T[ii][cc]);
         } else {
           const int e2 = e - nT, ri = e2 / (j + 1), cc = e2 - ri * (j + 1), ii = j + 1 + ri;
@@ -145,8 +135,8 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
         }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();  // the last column's updates
   if (tid == 0 && s_bad) *flag = 1;
   for (int q = tid; q < NB * NB; q += nt) {
     const int i = q >> 5, c = q & 31;
@@ -655,16 +645,6 @@ opf_status alloc_step(opf_ctx* c) {
       free_step_work(c);
       return so;
     }
-  }
-  if (cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ch_start, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ch_panel, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ch_rest, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    c->stepw = w;
-    free_step_work(c);
-    set_last_error("cannot create the step's streams and events");
-    return OPF_ECUDA;
   }
   c->stepw = w;
   return OPF_OK;
