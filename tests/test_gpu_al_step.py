@@ -3,7 +3,10 @@
 Tolerance: the step solves S_uu d_u = r with S_uu from the Hessian (parity
 ~1e-12 relative between the two sides) and cond(S_uu + delta I) below ~1e4 at
 these points, so d_u agrees to ~1e-8; the test uses 1e-6 relative (infinity
-norm).  The inertia correction, step lengths and halvings must coincide.
+norm).  The inertia correction, step lengths and halvings must coincide.  The
+9.2k-bus case (n_u = 2899, 23 column groups of the Cholesky, so 22 rank-128
+trailing updates emulated on the tensor cores) checks the factorisation at
+full size, including which inertia corrections fail.
 """
 import numpy as np
 import pytest
@@ -33,7 +36,8 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("name,mu,delta_start", [("tiny30", 0.1, 0.0), ("medium1400", 0.1, 0.0),
-                                                  ("medium1400", 1e-3, 0.0), ("medium1400", 0.1, 3e4)])
+                                                  ("medium1400", 1e-3, 0.0), ("medium1400", 0.1, 3e4),
+                                                  ("large9200", 0.1, 0.0)])
 def test_al_step_parity(name, mu, delta_start):
     net = synth.workload(name)
     on, x, u, al, st = setup(net, mu=mu)
