@@ -572,6 +572,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));
   TRY(setup_solve1(c));
   TRY(setup_sweep_streams(c, bsched_ptr_f, bmeta_f, bsched_ptr_b, bmeta_b));
+  c->lu_dense_cluster = setup_lu_dense_cluster(c->dn.nroot);
   setup_hvp_smem();
   // the numeric refactorisation as one CUDA graph (captured once on a private stream)
   CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));

@@ -184,6 +184,11 @@ struct SweepStreams {
 // FP64 rank-K update of a lower triangle emulated on bf16 tensor cores
 // (opf_ozaki.cu): A[r0 :, r0 :] -= P P^T with P = A[r0 : n, c0 : c0 + K],
 // K <= 128 a multiple of 32; E: n - r0 ints, D: 8 (n - r0) K bf16 workspace.
+// Dense LU of the trailing block on one thread-block cluster (opf_lu_dense.cu):
+// the cluster size for a block of s rows (0: the one-CTA kernel), and the launch.
+int setup_lu_dense_cluster(int s);
+void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, int r0, int s, int* flags);
+
 opf_status setup_oz();
 void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag);
 // the two halves of launch_oz_update: digits, then the tiles of one part (0 all,
@@ -270,4 +275,5 @@ struct opf_ctx {
   cudaGraphExec_t lu_exec = nullptr;
   long long lu_graph_kernels = 0;
   opf::SweepStreams sw;            // level-packed single-RHS sweep streams
+  int lu_dense_cluster = 0;        // CTAs of the trailing block's cluster LU (0: one CTA)
 };

@@ -1422,7 +1422,10 @@ void launch_lu_kernels(opf_ctx* c) {
   c->launches++;
   const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
   const int use_smem = dense_smem <= (size_t)kDenseLuSmem ? 1 : 0;
-  lu_dense_block_kernel<<<1, 1024, use_smem ? dense_smem : 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0,
+  if (c->lu_dense_cluster > 0)
+    launch_lu_dense_cluster(c->stream, c->lu_dense_cluster, c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags);
+  else
+    lu_dense_block_kernel<<<1, 1024, use_smem ? dense_smem : 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0,
                                                                           c->dn.nroot, c->flags, use_smem);
   c->launches++;
   lu_finish_kernel<<<2 * c->sm_count, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->tmap, c->dn.dp,
