@@ -157,10 +157,14 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int ntask = t1 - t0, nall = ntask + (f1 - f0);
+  // the task records are static: the first one is read before the wait for the
+  // previous level (programmatic dependent launch)
+  const int4 tr_first = warp < ntask ? __ldg(trec + t0 + warp) : make_int4(0, 0, 0, 0);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int w = warp; w < nall; w += nw) {
     if (w < ntask) {
       const int t = t0 + w;
-      const int4 tr = __ldg(trec + t);
+      const int4 tr = (w == warp) ? tr_first : __ldg(trec + t);
       const bool two = tr.w >= 0;
       const double uff = LU[tr.y];
       const double inv_ff = 1.0 / uff;
@@ -199,6 +203,7 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
       }
     }
   }
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // Dense LU of the trailing block [r0, r0 + s) (rows of it are contiguous in LU:
@@ -1416,8 +1421,19 @@ void launch_lu_kernels(opf_ctx* c) {
     if (warps == 0) continue;
     const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
     c->launches++;
-    lu_level_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->task_rec, c->task_off, c->task_map, t0, t1,
-                                                   c->fin_rec, f0, f1, c->flags);
+    // programmatic dependent launch: the next level's grid starts while this
+    // one drains and waits in-kernel (griddepcontrol.wait) for its results
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, lu_level_kernel, c->LU, (const int4*)c->task_rec, (const int*)c->task_off,
+                       (const int*)c->task_map, t0, t1, (const int4*)c->fin_rec, f0, f1, c->flags);
   }
   c->launches++;
   const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
