@@ -156,6 +156,30 @@ void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
 struct StepWork;
 void free_step_work(opf_ctx* c);
 
+#ifdef __CUDACC__
+// Programmatic dependent launch: a kernel launched by launch_pdl may start while
+// the previous kernel on its stream drains; it must call pdl_wait() before it
+// reads anything that kernel writes, and calls pdl_trigger() once its own work
+// is issued (exiting counts as the trigger).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
+
 // Level-packed single-RHS sweeps (opf_sweep.cu).  The factor entries a sweep
 // reads are copied after each refactorisation into one contiguous stream per
 // (factor, direction): first the dense trailing triangle (packed by rows) and

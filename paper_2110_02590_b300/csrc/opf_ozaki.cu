@@ -64,6 +64,7 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int E) {
 __global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict__ A, int n, int c0, int K, int r0,
                                                       int M, int* __restrict__ E, __nv_bfloat16* __restrict__ D,
                                                       const int* flag) {
+  pdl_wait();
   if (*flag) return;
   __shared__ int emax_s[32][32];
   __shared__ __nv_bfloat16 dig[OZ_S][32][33];  // [digit][column in the pass][row]
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict
     }
     __syncthreads();
   }
+  pdl_trigger();
 }
 
 namespace {
@@ -257,6 +259,7 @@ __device__ __forceinline__ void oz_tile(double* A, int n, int r0, int M, int K, 
 __global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
                                                      const __nv_bfloat16* __restrict__ D, const int* __restrict__ E,
                                                      const int* flag, int strip, int toff, int ntiles) {
+  pdl_wait();
   if (*flag) return;
   extern __shared__ __align__(16) unsigned short oz_sm[];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r
     }
     oz_tile(A, n, r0, M, K, D, E, oz_sm, bi + toff, bj + toff);
   }
+  pdl_trigger();
 }
 
 size_t oz_syrk_smem() { return 2 * sizeof(unsigned short) * (size_t)OZ_STAGE; }
@@ -292,7 +296,8 @@ void launch_oz_slice(cudaStream_t st, const double* A, int n, int c0, int K, int
                      const int* flag) {
   const int M = n - r0;
   if (M <= 0 || K <= 0) return;
-  oz_slice_kernel<<<(M + 31) / 32, 1024, 0, st>>>(A, n, c0, K, r0, M, E, static_cast<__nv_bfloat16*>(D), flag);
+  launch_pdl(oz_slice_kernel, dim3((M + 31) / 32), dim3(1024), 0, st, A, n, c0, K, r0, M, E,
+             static_cast<__nv_bfloat16*>(D), flag);
 }
 
 // A[r0 :, r0 :] (lower) -= P P^T from the digits: part = 0 the whole triangle,
@@ -315,8 +320,8 @@ void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int*
   }
   if (ntiles <= 0) return;
   const int g = grid > 0 ? std::min(grid, ntiles) : ntiles;
-  oz_syrk_kernel<<<g, 256, oz_syrk_smem(), st>>>(A, n, r0, M, K, static_cast<const __nv_bfloat16*>(D), E, flag,
-                                                strip, toff, ntiles);
+  launch_pdl(oz_syrk_kernel, dim3(g), dim3(256), oz_syrk_smem(), st, A, n, r0, M, K,
+             static_cast<const __nv_bfloat16*>(D), E, flag, strip, toff, ntiles);
 }
 
 void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag) {

@@ -76,6 +76,7 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 // by the dense triangular solves.
 __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
                                                         double* Dinv) {
+  pdl_wait();
   if (*flag) return;
   __shared__ double T[NB][NB + 1], X[NB][NB + 1];
   __shared__ double s_r[NB];
@@ -143,12 +144,14 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
     if (i < kb && c <= i) A[(size_t)(k0 + c) * n + k0 + i] = T[i][c];
     Dinv[(size_t)(k0 / NB) * NB * NB + q] = (i < kb && c <= i) ? X[i][c] : 0.0;
   }
+  pdl_trigger();
 }
 
 // Panel below the diagonal block: X21 = A21 L_kk^{-T} = A21 Dinv^T as a small
 // GEMM (16 rows x 32 columns per CTA, 2 outputs per thread), written in place.
 __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag,
                                                         const double* __restrict__ Dinv) {
+  pdl_wait();
   if (*flag) return;
   __shared__ double M[NB][NB + 1];  // M[c][t] = (L_kk^{-1})_ct
   __shared__ double P[16][NB + 1];  // P[r][t] = A21[row r][t]
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0
     if (c0 < kb) A[(size_t)(k0 + c0) * n + g] = s0 + s2;
     if (c0 + 1 < kb) A[(size_t)(k0 + c0 + 1) * n + g] = s1 + s3;
   }
+  pdl_trigger();
 }
 
 // trailing lower triangle -= P P^T, P = A[r0:, k0:k0+kb]; one TS x TS tile per CTA
@@ -186,6 +190,7 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0
 template <int TS>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0, int kb, const int* flag,
                                                         int first_col, int off, int col_end) {
+  pdl_wait();
   if (*flag) return;
   constexpr int R = TS / 16;
   const int r0 = k0 + kb + off;  // origin of the tiled triangle
@@ -233,6 +238,7 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* A, int n, int k0
       const int gi = r0 + bi * TS + ty * R + p, gj = r0 + bj * TS + tx * R + q;
       if (gi < n && gj <= gi && gj < col_end) A[(size_t)gj * n + gi] -= acc[p][q];
     }
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------- dense triangular solves
@@ -661,15 +667,15 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
     const int c1 = std::min(n, c0 + GB);
     for (int k0 = c0; k0 < c1; k0 += NB) {
       const int kb = std::min(NB, n - k0);
-      chol_diag_kernel<<<1, 512, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
+      SCK(launch_pdl(chol_diag_kernel, dim3(1), dim3(512), 0, s1, A, n, k0, kb, flag, w->Dinv));
       c->launches++;
       const int rest = n - k0 - kb;
       if (rest <= 0) break;
-      chol_trsm_kernel<<<nblk(rest, 16), 256, 0, s1>>>(A, n, k0, kb, flag, w->Dinv);
+      SCK(launch_pdl(chol_trsm_kernel, dim3(nblk(rest, 16)), dim3(256), 0, s1, A, n, k0, kb, flag, w->Dinv));
       c->launches++;
       if (k0 + kb < c1) {  // the group's remaining columns, all rows below
         const dim3 grid(nblk(c1 - k0 - kb, 32), nblk(rest, 32));
-        chol_syrk_kernel<32><<<grid, 256, 0, s1>>>(A, n, k0, kb, flag, 2, 0, c1);
+        SCK(launch_pdl(chol_syrk_kernel<32>, grid, dim3(256), 0, s1, A, n, k0, kb, flag, 2, 0, c1));
         c->launches++;
       }
     }
