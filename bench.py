@@ -40,6 +40,9 @@ WORKLOAD = "large9200"
 METRIC = "HVPs/s and ms per full reduced Hessian (9.2k-bus, FP64); batched vs plain"
 UNIT = "HVP/s"
 FP64_PEAK_TFLOPS = 1.25        # B300 FP64 (vector and tensor) nominal rate of the pool's recipe
+# DRAM bytes (read + write) of one hvp_split_kernel<8, 256> launch on the 9.2k grid,
+# from the ncu capture summarised in profiles/hvp_split_kernel_large9200.md
+HVP_SPLIT_TRAFFIC_9200 = 7.58e9
 HBM_FALLBACK_GBS = 6400.0
 
 
@@ -416,8 +419,11 @@ def run_gpu(args):
         "batched_over_plain": (nu / (hvp_ms * 1e-3)) / (1e3 / plain_ms_per_col),
         "batched_snapshots": batch,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "hvp_tile_kernel", "flops_per_launch": flops,
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": (HVP_SPLIT_TRAFFIC_9200 if (tune["block_k"], tune["threads"]) == (8, 256)
+                                 and WORKLOAD == "large9200" else None),
+                     "kernel": ("hvp_split_kernel" if (tune["block_k"], tune["threads"]) == (8, 256)
+                                else "hvp_tile_kernel"), "flops_per_launch": flops,
                      "peak_note": "FP64 FMA pipe, nominal 1.25 TFLOP/s (microbenchmark on this pool: 1.12)",
                      "hbm": {"bytes_per_hessian": hbm_b, "achieved_gbs": hbm_b / (hvp_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
