@@ -272,6 +272,23 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
       c->h_task_ptr.push_back((int)btask.size());
       c->h_fin_ptr.push_back((int)bfin.size());
     }
+    // lanes per work item of each level launch (tasks of level lv, finish records
+    // of level lv - 1): enough that the longest row takes at most four passes
+    const int nlv = (int)c->h_task_ptr.size() - 1;
+    c->h_lu_lanes.assign(nlv + 1, 32);
+    for (int lv = 0; lv <= nlv; lv++) {
+      int mx = 1;
+      if (lv < nlv)
+        for (int t = c->h_task_ptr[lv]; t < c->h_task_ptr[lv + 1]; t++) {
+          const int4 r = btask[t];
+          mx = std::max(mx, r.z - (r.y + (r.w >= 0 ? 2 : 1)));
+        }
+      if (lv > 0)
+        for (int f = c->h_fin_ptr[lv - 1]; f < c->h_fin_ptr[lv]; f++) mx = std::max(mx, bfin[f].y - bfin[f].x - 2);
+      int g = 1;
+      while (g < 32 && 4 * g < mx) g *= 2;
+      c->h_lu_lanes[lv] = g;
+    }
   }
   // control buses: slack first, then PV
   std::vector<int> gn_bus, gn_of(nb, -1), ubus(h.nu, -1);

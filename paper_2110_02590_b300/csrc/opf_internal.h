@@ -249,6 +249,7 @@ struct opf_ctx {
   int* task_map = nullptr;
   int4* fin_rec = nullptr;
   std::vector<int> h_task_ptr, h_fin_ptr;
+  std::vector<int> h_lu_lanes;      // per launch of the LU levels: lanes per work item
   std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
 
   // device: state of the last converged power flow

@@ -152,19 +152,25 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
 // U_vv, U_vc), which no task of this level reads.
 __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const int* __restrict__ toff,
                                 const int* __restrict__ map, int t0, int t1, const int4* __restrict__ frec,
-                                int f0, int f1, int* flags) {
-  const int lane = threadIdx.x & 31;
+                                int f0, int f1, int* flags, int G) {
+  // G lanes per work item (a power of two set per level from its longest row):
+  // short rows share a warp, so the per-item scalar FP64 work (the pivots'
+  // divisions) is not repeated by 32 lanes for one item
+  const int lane = threadIdx.x & 31, li = lane & (G - 1), ipw = 32 / G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int ntask = t1 - t0, nall = ntask + (f1 - f0);
   // the task records are static: the first one is read before the wait for the
   // previous level (programmatic dependent launch)
-  const int4 tr_first = warp < ntask ? __ldg(trec + t0 + warp) : make_int4(0, 0, 0, 0);
+  const int wfirst = warp * ipw + lane / G;
+  const int4 tr_first = wfirst < ntask ? __ldg(trec + t0 + wfirst) : make_int4(0, 0, 0, 0);
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int w = warp; w < nall; w += nw) {
+  for (int base = warp * ipw; base < nall; base += nw * ipw) {
+    const int w = base + lane / G;
     if (w < ntask) {
       const int t = t0 + w;
-      const int4 tr = (w == warp) ? tr_first : __ldg(trec + t);
+      const int4 tr = (w == wfirst) ? tr_first : __ldg(trec + t);
       const bool two = tr.w >= 0;
       const double uff = LU[tr.y];
       const double inv_ff = 1.0 / uff;
@@ -176,28 +182,28 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
         uvv = LU[tr.w] - lvf * ufv;
         lv = (LU[tr.x + 1] - lf * ufv) / uvv;
       }
-      __syncwarp();
-      if (lane == 0) {
+      __syncwarp(gmask);
+      if (li == 0) {
         LU[tr.x] = lf;
         if (two) LU[tr.x + 1] = lv;
         if (!(fabs(uff) > 0.0) || !isfinite(lf) || !isfinite(lv)) flags[0] = 1;
       }
       const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
       const int* tg = map + toff[t] - q0;
-      for (int q = q0 + lane; q < tr.z; q += 32) {
+      for (int q = q0 + li; q < tr.z; q += G) {
         const double ufc = LU[q];
         double d = lf * ufc;
         if (two) d += lv * (LU[qv + (q - q0)] - lvf * ufc);
         atomicAdd(&LU[tg[q]], -d);
       }
-    } else {
+    } else if (w < nall) {
       const int4 fr = __ldg(frec + f0 + (w - ntask));  // {dp[f], rp[f + 1], dp[f + 1]}
       const double uff = LU[fr.x];
       const double lvf = LU[fr.z - 1] / uff;
       const double ufv = LU[fr.x + 1];
-      for (int q = fr.x + 2 + lane; q < fr.y; q += 32) LU[fr.z + 1 + (q - fr.x - 2)] -= lvf * LU[q];
-      __syncwarp();
-      if (lane == 0) {
+      for (int q = fr.x + 2 + li; q < fr.y; q += G) LU[fr.z + 1 + (q - fr.x - 2)] -= lvf * LU[q];
+      __syncwarp(gmask);
+      if (li == 0) {
         LU[fr.z - 1] = lvf;
         LU[fr.z] -= lvf * ufv;
       }
@@ -1417,9 +1423,10 @@ void launch_lu_kernels(opf_ctx* c) {
   for (int lv = 0; lv <= nlev; lv++) {
     const int t0 = lv < nlev ? c->h_task_ptr[lv] : 0, t1 = lv < nlev ? c->h_task_ptr[lv + 1] : 0;
     const int f0 = lv > 0 ? c->h_fin_ptr[lv - 1] : 0, f1 = lv > 0 ? c->h_fin_ptr[lv] : 0;
-    const int warps = (t1 - t0) + (f1 - f0);
-    if (warps == 0) continue;
-    const int blocks = std::min(nblk(warps, 8), 4 * c->sm_count);
+    const int items = (t1 - t0) + (f1 - f0);
+    if (items == 0) continue;
+    const int G = lv < (int)c->h_lu_lanes.size() ? c->h_lu_lanes[lv] : 32;
+    const int blocks = std::min(nblk(nblk(items, 32 / G), 8), 4 * c->sm_count);
     c->launches++;
     // programmatic dependent launch: the next level's grid starts while this
     // one drains and waits in-kernel (griddepcontrol.wait) for its results
@@ -1433,7 +1440,7 @@ void launch_lu_kernels(opf_ctx* c) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, lu_level_kernel, c->LU, (const int4*)c->task_rec, (const int*)c->task_off,
-                       (const int*)c->task_map, t0, t1, (const int4*)c->fin_rec, f0, f1, c->flags);
+                       (const int*)c->task_map, t0, t1, (const int4*)c->fin_rec, f0, f1, c->flags, G);
   }
   c->launches++;
   const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
