@@ -584,6 +584,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->busw, 8 * (size_t)nb));
   TRY(dalloc(c, &c->adjE, ADJ_W * 2 * (size_t)nl));
   TRY(dalloc(c, &c->busS, 4 * (size_t)nb));
+  TRY(dalloc(c, &c->endflow, 20 * (size_t)nl));
   CK(cudaMallocHost(&c->h_scal, 8 * sizeof(double)));
   CK(cudaMallocHost(&c->h_flags, 4 * sizeof(int)));
   for (int k = 0; k < 4; k++) CK(cudaEventCreate(&c->ev[k]));

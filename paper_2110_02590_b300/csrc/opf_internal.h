@@ -285,6 +285,7 @@ struct opf_ctx {
   double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
   double* adjE = nullptr;         // [2 nl][ADJ_W] per-adjacency coefficients of the HVP gathers
   double* busS = nullptr;         // [nb] x 4: per-bus sums of E_VV (+ omega of v_pq), E_VT, E_TT, 0
+  double* endflow = nullptr;      // [2 nl][10] branch-end terms of the power-flow residual and Jacobian
   int hvp_threads = 256;          // threads per HVP tile CTA
   int solve1_smem = 0;            // dynamic shared bytes of the single-RHS sweep
   bool solve1_use_smem_rhs = false;  // the right-hand side also lives in shared memory

@@ -43,12 +43,20 @@ __device__ __forceinline__ void side_coeffs(const DevNet& n, int l, int s, doubl
 }
 
 // Flow out of one end of a branch (pi model, polar form) and its gradient.
+__device__ __forceinline__ void side_flow_sc(const DevNet& n, int l, int s, double vs, double vo, double sn,
+                                             double cs, Flow& o);
 __device__ __forceinline__ void side_flow(const DevNet& n, int l, int s, double vs, double vo,
                                           double ang, Flow& o) {
-  double Gss, Bss, Gso, Bso;
-  side_coeffs(n, l, s, Gss, Bss, Gso, Bso);
   double sn, cs;
   sincos(ang, &sn, &cs);
+  side_flow_sc(n, l, s, vs, vo, sn, cs, o);
+}
+
+// side_flow with sin and cos of the angle difference given
+__device__ __forceinline__ void side_flow_sc(const DevNet& n, int l, int s, double vs, double vo, double sn,
+                                             double cs, Flow& o) {
+  double Gss, Bss, Gso, Bso;
+  side_coeffs(n, l, s, Gss, Bss, Gso, Bso);
   const double A = Gso * cs + Bso * sn;   // d A / d ang = -Bq
   const double Bq = Gso * sn - Bso * cs;  // d Bq / d ang = A
   const double vv = vs * vo;
@@ -81,30 +89,59 @@ __global__ void unpack_kernel(DevNet n, const double* x, const double* u, double
 }
 
 // g and the values of G_x in the fixed pattern; one thread owns the rows of its bus.
+// Branch terms of the power-flow residual and Jacobian, one thread per branch:
+// one sincos serves both ends (the to side's angle is the negated from side's),
+// and each end's ten terms {P, Q, dP/dv_s, dP/dth_s, dQ/dv_s, dQ/dth_s, dP/dth_o,
+// dP/dv_o, dQ/dth_o, dQ/dv_o} go to ef[e] (e = 2 l + side), which the bus
+// kernels (residual and Jacobian, first-order weights, control gradient) sum
+// in adjacency order.
+__global__ void pf_branch_kernel(DevNet n, const double* vb, const double* tb, double* ef) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n.nl) return;
+  const int a = n.f[l], b = n.t[l];
+  double sn, cs;
+  sincos(tb[a] - tb[b], &sn, &cs);
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+    const int i = s ? b : a, o = s ? a : b;
+    Flow fl;
+    side_flow_sc(n, l, s, vb[i], vb[o], s ? -sn : sn, cs, fl);
+    double* r = ef + 10 * (size_t)(2 * l + s);
+    r[0] = fl.P;
+    r[1] = fl.Q;
+    r[2] = fl.dP[0];
+    r[3] = fl.dP[2];
+    r[4] = fl.dQ[0];
+    r[5] = fl.dQ[2];
+    r[6] = fl.dP[3];
+    r[7] = fl.dP[1];
+    r[8] = fl.dQ[3];
+    r[9] = fl.dQ[1];
+  }
+}
+
 __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, const double* u,
                                const double* pd, const double* qd, double* g, double* LU,
-                               double* scal) {
+                               double* scal, const double* ef) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double g2 = 0.0, gi = 0.0;
   if (i < n.nb && n.type[i] != REF) {
     const bool pq = n.type[i] == PQ;
     double P = 0, Q = 0, dPv = 0, dPt = 0, dQv = 0, dQt = 0;
-    const double vi = vb[i], ti = tb[i];
     for (int k = n.adj_ptr[i]; k < n.adj_ptr[i + 1]; k++) {
-      const int e = n.adj[k], l = e >> 1, s = e & 1, o = other_end(n, e);
-      Flow fl;
-      side_flow(n, l, s, vi, vb[o], ti - tb[o], fl);
-      P += fl.P;
-      Q += fl.Q;
-      dPv += fl.dP[0];
-      dPt += fl.dP[2];
-      dQv += fl.dQ[0];
-      dQt += fl.dQ[2];
+      const int e = n.adj[k];
+      const double* r = ef + 10 * (size_t)e;
+      P += r[0];
+      Q += r[1];
+      dPv += r[2];
+      dPt += r[3];
+      dQv += r[4];
+      dQt += r[5];
       const int* sl = n.slot_adj + 4 * (size_t)e;
-      if (sl[0] >= 0) LU[sl[0]] += fl.dP[3];
-      if (sl[1] >= 0) LU[sl[1]] += fl.dP[1];
-      if (sl[2] >= 0) LU[sl[2]] += fl.dQ[3];
-      if (sl[3] >= 0) LU[sl[3]] += fl.dQ[1];
+      if (sl[0] >= 0) LU[sl[0]] += r[6];
+      if (sl[1] >= 0) LU[sl[1]] += r[7];
+      if (sl[2] >= 0) LU[sl[2]] += r[8];
+      if (sl[3] >= 0) LU[sl[3]] += r[9];
     }
     const int* ss = n.slot_self + 4 * (size_t)i;
     LU[ss[0]] += dPt;
@@ -123,24 +160,35 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
       gi = fmax(gi, fabs(gq));
     }
   }
+  // block reduction, then one atomic pair per block (same-address atomics serialise)
+  __shared__ double r2[32], ri[32];
   for (int off = 16; off > 0; off >>= 1) {
     g2 += __shfl_down_sync(0xffffffffu, g2, off);
     gi = fmax(gi, __shfl_down_sync(0xffffffffu, gi, off));
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&scal[0], g2);
-    // non-negative doubles order like their bit patterns
-    atomicMax(reinterpret_cast<unsigned long long*>(&scal[1]), (unsigned long long)__double_as_longlong(gi));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    r2[wid] = g2;
+    ri[wid] = gi;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    g2 = lane < nw ? r2[lane] : 0.0;
+    gi = lane < nw ? ri[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      g2 += __shfl_down_sync(0xffffffffu, g2, off);
+      gi = fmax(gi, __shfl_down_sync(0xffffffffu, gi, off));
+    }
+    if (lane == 0) {
+      atomicAdd(&scal[0], g2);
+      // non-negative doubles order like their bit patterns
+      atomicMax(reinterpret_cast<unsigned long long*>(&scal[1]), (unsigned long long)__double_as_longlong(gi));
+    }
   }
 }
 
 // ------------------------------------------------------------ numeric LU
 
-// Right-looking elimination of the columns of one level: each warp takes one
-// (column j, row r) pair, forms L_rj = A_rj / U_jj and subtracts L_rj U_j,c
-// from A_rc for every c in row j of U (lanes over c).  Columns of one level
-// never update each other's rows or columns, so only the targets race, and
-// they are combined by atomic adds.
 // One level of the right-looking LU on the fixed pattern, by bus blocks (one or
 // two pivot rows f, f + 1 whose off-block patterns coincide).  Warps [0, t1 - t0)
 // take a task each: for row r below the block, l_f = A_rf / U_ff and, for a
@@ -779,9 +827,8 @@ __device__ __forceinline__ void f_weights(const DevNet& n, int b, const double* 
 }
 
 // Partial derivatives of F w.r.t. (v_i, theta_i), gathered over the incident branches.
-__global__ void dF_bus_kernel(DevNet n, const double* vb, const double* tb, const double* u,
-                              const double* phid, const double* Pb, const double* pd,
-                              double sigma_f, double* dFx, double* dFu) {
+__global__ void dF_bus_kernel(DevNet n, const double* u, const double* phid, const double* Pb, const double* pd,
+                              double sigma_f, double* dFx, double* dFu, const double* __restrict__ ef) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n.nb) return;
   const double pref = Pb[n.ref] + pd[n.ref];
@@ -790,16 +837,15 @@ __global__ void dF_bus_kernel(DevNet n, const double* vb, const double* tb, cons
   double dv = 0.0, dt = 0.0;
   for (int k = n.adj_ptr[i]; k < n.adj_ptr[i + 1]; k++) {
     const int e = n.adj[k], l = e >> 1, s = e & 1, o = other_end(n, e);
-    Flow fi, fo;
-    side_flow(n, l, s, vb[i], vb[o], tb[i] - tb[o], fi);
-    side_flow(n, l, 1 - s, vb[o], vb[i], tb[o] - tb[i], fo);
+    const double* fi = ef + 10 * (size_t)e;        // this end
+    const double* fo = ef + 10 * (size_t)(e ^ 1);  // the other end
     const double phi_i = phid[s * n.nl + l], phi_o = phid[(1 - s) * n.nl + l];
     double wPo, wQo;
     f_weights(n, o, phid, sigma_f, pref, wPo, wQo);
-    const double ai = 2.0 * phi_i * fi.P + wPi, bi = 2.0 * phi_i * fi.Q + wQi;
-    const double ao = 2.0 * phi_o * fo.P + wPo, bo = 2.0 * phi_o * fo.Q + wQo;
-    dv += ai * fi.dP[0] + bi * fi.dQ[0] + ao * fo.dP[1] + bo * fo.dQ[1];
-    dt += ai * fi.dP[2] + bi * fi.dQ[2] + ao * fo.dP[3] + bo * fo.dQ[3];
+    const double ai = 2.0 * phi_i * fi[0] + wPi, bi = 2.0 * phi_i * fi[1] + wQi;
+    const double ao = 2.0 * phi_o * fo[0] + wPo, bo = 2.0 * phi_o * fo[1] + wQo;
+    dv += ai * fi[2] + bi * fi[4] + ao * fo[7] + bo * fo[9];
+    dt += ai * fi[3] + bi * fi[5] + ao * fo[6] + bo * fo[8];
   }
   if (n.type[i] == PQ) dv += phid[2 * n.nl + n.pqpos[i]];
   if (n.type[i] != REF) dFx[n.xth[i]] = dt;
@@ -813,23 +859,18 @@ __global__ void dF_bus_kernel(DevNet n, const double* vb, const double* tb, cons
 }
 
 // grad_u = d_u F + G_u^T lambda, one thread per control bus (slack and PV).
-__global__ void grad_u_kernel(DevNet n, const double* vb, const double* tb, const double* lam,
-                              const double* dFu, double* gu) {
+__global__ void grad_u_kernel(DevNet n, const double* lam, const double* dFu, double* gu,
+                              const double* __restrict__ ef) {
   int gidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= n.ngn) return;
   const int k = n.gn_bus[gidx];
   double gv = dFu[n.uv[k]], selfP = 0.0;
   for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-    const int e = n.adj[q], l = e >> 1, s = e & 1, o = other_end(n, e);
-    Flow fo;
-    side_flow(n, l, 1 - s, vb[o], vb[k], tb[o] - tb[k], fo);
-    if (n.type[o] != REF) gv += lam[n.xth[o]] * fo.dP[1];
-    if (n.type[o] == PQ) gv += lam[n.xv[o]] * fo.dQ[1];
-    if (n.type[k] == PV) {
-      Flow fk;
-      side_flow(n, l, s, vb[k], vb[o], tb[k] - tb[o], fk);
-      selfP += fk.dP[0];
-    }
+    const int e = n.adj[q], o = other_end(n, e);
+    const double* fo = ef + 10 * (size_t)(e ^ 1);  // the other end: its derivatives by v_k
+    if (n.type[o] != REF) gv += lam[n.xth[o]] * fo[7];
+    if (n.type[o] == PQ) gv += lam[n.xv[o]] * fo[9];
+    if (n.type[k] == PV) selfP += ef[10 * (size_t)e + 2];
   }
   if (n.type[k] == PV) {
     gv += lam[n.xth[k]] * selfP;
@@ -1411,9 +1452,10 @@ void launch_unpack(opf_ctx* c, const double* x, const double* u) {
 }
 
 void launch_pf_eval(opf_ctx* c) {
-  c->launches++;
+  c->launches += 2;
+  pf_branch_kernel<<<nblk(c->dn.nl, 128), 128, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->endflow);
   pf_eval_kernel<<<nblk(c->dn.nb, 256), 256, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->u, c->pd,
-                                                               c->qd, c->g, c->LU, c->scal);
+                                                               c->qd, c->g, c->LU, c->scal, c->endflow);
 }
 
 void launch_lu_kernels(opf_ctx* c) {
@@ -1502,7 +1544,8 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
   const DevNet& n = c->dn;
   cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
   launch_unpack(c, c->x, c->u);
-  c->launches++;
+  c->launches += 2;
+  pf_branch_kernel<<<nblk(n.nl, 128), 128, 0, c->stream>>>(n, c->vbus, c->thbus, c->endflow);
   branch_flow_kernel<<<nblk(n.nl, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->flows, c->cvec);
   c->launches++;
   bus_inj_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->flows, c->pd, c->qd, c->Pbus,
@@ -1513,24 +1556,24 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
       n, c->cvec, p->sigma_c, p->y, p->s, p->omega, p->rho, p->sigma_f, c->Pbus, c->u, c->pd,
       c->c0, c->phid, grad_s, c->omega, c->scal);
   c->launches++;
-  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, c->phid, c->Pbus,
-                                                        c->pd, p->sigma_f, c->dFx, c->dFu);
+  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->u, c->phid, c->Pbus, c->pd, p->sigma_f, c->dFx,
+                                                        c->dFu, c->endflow);
   launch_solve1(c, c->dFx, c->lam, true, -1.0);
 }
 
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out) {
   const DevNet& n = c->dn;
   c->launches++;
-  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->u, w, c->Pbus, c->pd, 0.0,
-                                                        c->dFx, c->dFu);
+  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->u, w, c->Pbus, c->pd, 0.0, c->dFx, c->dFu,
+                                                        c->endflow);
   launch_solve1(c, c->dFx, c->lam, true, -1.0);
   c->launches++;
-  grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->vbus, c->thbus, c->lam, c->dFu, out);
+  grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->lam, c->dFu, out, c->endflow);
 }
 
 void launch_grad_u(opf_ctx* c, double* gu) {
   c->launches++;
-  grad_u_kernel<<<nblk(c->dn.ngn, 128), 128, 0, c->stream>>>(c->dn, c->vbus, c->thbus, c->lam, c->dFu, gu);
+  grad_u_kernel<<<nblk(c->dn.ngn, 128), 128, 0, c->stream>>>(c->dn, c->lam, c->dFu, gu, c->endflow);
 }
 
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd) {

@@ -375,15 +375,24 @@ __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict
 
 // ---------------------------------------------------------------- step kernels
 
+// S <- (S + S^T) / 2 + diag(sig_u) on the lower triangle (the factorisation reads
+// no other part), 32 x 32 tile pairs through shared memory so both reads coalesce.
 __global__ void sym_diag_kernel(double* S, int n, const double* sig_u) {
-  const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || i < j) return;
-  if (i == j) {
-    S[(size_t)j * n + j] += sig_u[j];
-  } else {
-    const double a = 0.5 * (S[(size_t)j * n + i] + S[(size_t)i * n + j]);
-    S[(size_t)j * n + i] = a;
-    S[(size_t)i * n + j] = a;
+  __shared__ double T[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // tile of rows bi, columns bj (bi >= bj)
+  if (bi < bj) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += blockDim.x >> 5) {  // T[c][tx] = S(row bj*32 + tx, col bi*32 + c)
+    const int row = bj * 32 + tx, col = bi * 32 + r;
+    T[r][tx] = (row < n && col < n) ? S[(size_t)col * n + row] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += blockDim.x >> 5) {  // element (row bi*32 + tx, col bj*32 + r)
+    const int row = bi * 32 + tx, col = bj * 32 + r;
+    if (row < n && col <= row) {
+      double* p = S + (size_t)col * n + row;
+      *p = (row == col) ? *p + sig_u[row] : 0.5 * (*p + T[tx][r]);
+    }
   }
 }
 
@@ -764,7 +773,7 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
   if (rc) return rc;
   SCK(cudaEventRecord(ev[2], stream));
-  sym_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->S, nu, w->sig_u);
+  sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
   c->launches++;
   // r = -grad_u psi - J^T v  (state quantities of this point are still in the context)
   launch_weighted_grad(c, w->v, w->Jtv);
