@@ -380,6 +380,26 @@ __device__ __forceinline__ void block_dot(const DevNet& n, const double* __restr
                                           int q0, int q1, int off, bool two, int col, double& a, double& b) {
   double a1 = 0.0, b1 = 0.0;
   int p = q0;
+  for (; p + 7 < q1; p += 8) {  // eight slab reads in flight per lane
+    int ci[8];
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) ci[k] = __ldg(n.ci + p + k);
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = X[(size_t)ci[k] * C + col];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      a -= V[p + k] * x[k];
+      a1 -= V[p + k + 1] * x[k + 1];
+    }
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        b -= V[p + off + k] * x[k];
+        b1 -= V[p + off + k + 1] * x[k + 1];
+      }
+    }
+  }
   for (; p + 3 < q1; p += 4) {
     const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + 1), c2 = __ldg(n.ci + p + 2), c3 = __ldg(n.ci + p + 3);
     const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
@@ -479,6 +499,22 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
         const double xl = X[(size_t)lead * C + col], xo = two ? X[(size_t)oth * C + col] : 0.0;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int p = m.y + grp;
+        for (; p + 3 * RPW < q1; p += 4 * RPW) {  // four slab reads in flight per lane
+          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + RPW);
+          const int c2 = __ldg(n.ci + p + 2 * RPW), c3 = __ldg(n.ci + p + 3 * RPW);
+          const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
+          const double x2 = X[(size_t)c2 * C + col], x3 = X[(size_t)c3 * C + col];
+          a0 -= V[p] * x0;
+          a1 -= V[p + RPW] * x1;
+          a0 -= V[p + 2 * RPW] * x2;
+          a1 -= V[p + 3 * RPW] * x3;
+          if (two) {
+            b0 -= V[p + off] * x0;
+            b1 -= V[p + off + RPW] * x1;
+            b0 -= V[p + off + 2 * RPW] * x2;
+            b1 -= V[p + off + 3 * RPW] * x3;
+          }
+        }
         for (; p + RPW < q1; p += 2 * RPW) {
           const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + RPW);
           const double x0 = X[(size_t)c0 * C + col], x1 = X[(size_t)c1 * C + col];
