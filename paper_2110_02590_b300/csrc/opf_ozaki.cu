@@ -149,25 +149,32 @@ __device__ __forceinline__ void oz_issue(unsigned short* S, const __nv_bfloat16*
   }
 }
 
-// Levels TLO .. TLO + 3 (digit pairs i + j in that range, digits < NSL) over
-// all K columns, double-buffered; acc[l] holds level TLO + l (exact integers).
-template <int NSL, int TLO>
-__device__ __forceinline__ void oz_levels(float (&acc)[4][2][2][4], unsigned short* sm,
-                                          const __nv_bfloat16* __restrict__ D, int M, int K, int rowA, int rowB) {
+}  // namespace
+
+// One 64 x 64 tile: all eight levels in one pass over the K columns (two
+// cp.async stages of all eight digit planes of both row blocks).  Warps 4 x 4,
+// each 16 x 16 outputs as one m16 x two n8 tiles: per 16 columns a warp holds
+// the eight digits' B fragments in registers, then takes each A digit once and
+// issues its pairs (digit i with digits j <= 7 - i) into acc[i + j].  The
+// FP32 level sums are exact integers; levels 0-3 and 4-7 fold into exact
+// 64-bit integers, which convert to FP64 exactly and meet in one FMA.
+__device__ __forceinline__ void oz_tile(double* A, int n, int r0, int M, int K, const __nv_bfloat16* __restrict__ D,
+                                        const int* __restrict__ E, unsigned short* sm, int bi, int bj) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wr = warp >> 2, wc = warp & 3;
+  const int g = lane >> 2, tq = lane & 3;
+  const int rowA = bi * OZ_TILE, rowB = bj * OZ_TILE;
+  float acc[OZ_S][2][4];
 #pragma unroll
-  for (int l = 0; l < 4; l++)
+  for (int l = 0; l < OZ_S; l++)
 #pragma unroll
-    for (int m = 0; m < 2; m++)
+    for (int q = 0; q < 2; q++)
 #pragma unroll
-      for (int q = 0; q < 2; q++)
-#pragma unroll
-        for (int v = 0; v < 4; v++) acc[l][m][q][v] = 0.f;
+      for (int v = 0; v < 4; v++) acc[l][q][v] = 0.f;
   const int nch = K / OZ_KC;
-  oz_issue<NSL>(sm, D, M, K, rowA, rowB, 0);
+  oz_issue<OZ_S>(sm, D, M, K, rowA, rowB, 0);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int c = 0; c < nch; c++) {
-    if (c + 1 < nch) oz_issue<NSL>(sm + ((c + 1) & 1) * OZ_STAGE, D, M, K, rowA, rowB, (c + 1) * OZ_KC);
+    if (c + 1 < nch) oz_issue<OZ_S>(sm + ((c + 1) & 1) * OZ_STAGE, D, M, K, rowA, rowB, (c + 1) * OZ_KC);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
@@ -175,88 +182,52 @@ __device__ __forceinline__ void oz_levels(float (&acc)[4][2][2][4], unsigned sho
     const unsigned short* SB = SA + OZ_S * OZ_TILE * OZ_PAD;
 #pragma unroll
     for (int ks = 0; ks < OZ_KC; ks += 16) {
-      unsigned b[NSL][4];  // per digit: columns wc*16 + [0, 8) and [8, 16), k halves
+      unsigned b[OZ_S][4];  // per digit: columns wc*16 + [0, 8) and [8, 16), k halves
 #pragma unroll
-      for (int j = 0; j < NSL; j++)
+      for (int j = 0; j < OZ_S; j++)
         ldsm_x4(b[j], SB + ((size_t)j * OZ_TILE + wc * 16 + (lane & 7) + ((lane >> 4) << 3)) * OZ_PAD + ks +
                           ((lane >> 3) & 1) * 8);
 #pragma unroll
-      for (int i = 0; i < NSL; i++) {
-        unsigned a[2][4];
+      for (int i = 0; i < OZ_S; i++) {
+        unsigned a[4];
+        ldsm_x4(a, SA + ((size_t)i * OZ_TILE + wr * 16 + (lane & 15)) * OZ_PAD + ks + (lane >> 4) * 8);
 #pragma unroll
-        for (int m = 0; m < 2; m++)
-          ldsm_x4(a[m], SA + ((size_t)i * OZ_TILE + wr * 32 + m * 16 + (lane & 15)) * OZ_PAD + ks + (lane >> 4) * 8);
-#pragma unroll
-        for (int j = 0; j < NSL; j++) {
-          if (i + j < TLO || i + j > TLO + 3) continue;
-#pragma unroll
-          for (int m = 0; m < 2; m++)
-#pragma unroll
-            for (int q = 0; q < 2; q++) mma_bf16(acc[i + j - TLO][m][q], a[m], &b[j][2 * q]);
+        for (int j = 0; j + i < OZ_S; j++) {
+          mma_bf16(acc[i + j][0], a, &b[j][0]);
+          mma_bf16(acc[i + j][1], a, &b[j][2]);
         }
       }
     }
     __syncthreads();
   }
-}
-
-// sum_l acc[l] 2^(7 (3 - l)) as an exact 64-bit integer (< 2^46); the level
-// sums are integers below 2^24
-__device__ __forceinline__ long long oz_fold(const float (&acc)[4][2][2][4], int m, int q, int v) {
-  long long s = 0;
-#pragma unroll
-  for (int l = 0; l < 4; l++) s += (long long)__float2int_rz(acc[l][m][q][v]) * (1ll << (7 * (3 - l)));
-  return s;
-}
-
-}  // namespace
-
-// C -= P P^T on the lower triangle of the trailing block A[r0 : r0 + M, r0 : r0 + M]
-// from the digits of P (oz_slice_kernel), one 64 x 64 tile (bi >= bj) per CTA.
-// Warps 2 x 4, each 32 x 16 outputs as 2 x 2 m16n8k16 tiles; fragments by
-// ldmatrix, digit tiles staged by cp.async (two stages).  Levels 0-3 use digits
-// 0-3 and levels 4-7 all eight; within each group the four FP32 level sums
-// (exact integers) fold into an exact 64-bit integer, which converts to FP64
-// exactly; the two groups meet in one FP64 fma.  Dynamic shared memory: two
-// stages of 2 x 8 x 64 x 40 bf16.
-__device__ __forceinline__ void oz_tile(double* A, int n, int r0, int M, int K, const __nv_bfloat16* __restrict__ D,
-                                        const int* __restrict__ E, unsigned short* oz_sm, int bi, int bj) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wr = warp >> 2, wc = warp & 3, g = lane >> 2, tq = lane & 3;
-  float acc[4][2][2][4];
-  double hi[2][2][4];
-  oz_levels<4, 0>(acc, oz_sm, D, M, K, bi * OZ_TILE, bj * OZ_TILE);
-#pragma unroll
-  for (int m = 0; m < 2; m++)
-#pragma unroll
-    for (int q = 0; q < 2; q++)
-#pragma unroll
-      for (int v = 0; v < 4; v++) hi[m][q][v] = (double)oz_fold(acc, m, q, v);  // levels 0-3 x 2^21
-  oz_levels<8, 4>(acc, oz_sm, D, M, K, bi * OZ_TILE, bj * OZ_TILE);
   const double s28 = __longlong_as_double((long long)(1023 - 28) << 52);  // 2^-28: levels 4-7 against 0-3
 #pragma unroll
-  for (int m = 0; m < 2; m++)
+  for (int q = 0; q < 2; q++)
 #pragma unroll
-    for (int q = 0; q < 2; q++)
+    for (int v = 0; v < 4; v++) {
+      const int lr = rowA + wr * 16 + g + (v >= 2 ? 8 : 0);
+      const int lc = rowB + wc * 16 + q * 8 + 2 * tq + (v & 1);
+      if (lr < M && lc <= lr) {
+        long long hi = 0, lo = 0;  // sum_l acc[l] 2^(7 (3 - l)), sum_l acc[4 + l] 2^(7 (3 - l))
 #pragma unroll
-      for (int v = 0; v < 4; v++) {
-        const int lr = bi * OZ_TILE + wr * 32 + m * 16 + g + (v >= 2 ? 8 : 0);
-        const int lc = bj * OZ_TILE + wc * 16 + q * 8 + 2 * tq + (v & 1);
-        if (lr < M && lc <= lr) {
-          const double sum = fma((double)oz_fold(acc, m, q, v), s28, hi[m][q][v]);  // x 2^21
-          const int e = E[lr] + E[lc] - 35;
-          const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
-                                                      : ldexp(1.0, e);
-          double* p = A + (size_t)(r0 + lc) * n + r0 + lr;
-          *p = fma(-sum, sc, *p);
+        for (int l = 0; l < 4; l++) {
+          hi += (long long)__float2int_rz(acc[l][q][v]) * (1ll << (7 * (3 - l)));
+          lo += (long long)__float2int_rz(acc[4 + l][q][v]) * (1ll << (7 * (3 - l)));
         }
+        const double sum = fma((double)lo, s28, (double)hi);  // x 2^21
+        const int e = E[lr] + E[lc] - 35;
+        const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                                    : ldexp(1.0, e);
+        double* p = A + (size_t)(r0 + lc) * n + r0 + lr;
+        *p = fma(-sum, sc, *p);
       }
+    }
 }
 
 // The tiles of one launch: strip = 0, the lower triangle of tile rows and
 // columns from toff on; strip = 1, tile columns toff and toff + 1 (the next
 // 128 columns), every row tile at or below them.  CTAs loop over the tiles.
-__global__ void __launch_bounds__(256, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
+__global__ void __launch_bounds__(512, 1) oz_syrk_kernel(double* A, int n, int r0, int M, int K,
                                                      const __nv_bfloat16* __restrict__ D, const int* __restrict__ E,
                                                      const int* flag, int strip, int toff, int ntiles) {
   pdl_wait();
@@ -320,7 +291,7 @@ void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int*
   }
   if (ntiles <= 0) return;
   const int g = grid > 0 ? std::min(grid, ntiles) : ntiles;
-  launch_pdl(oz_syrk_kernel, dim3(g), dim3(256), oz_syrk_smem(), st, A, n, r0, M, K,
+  launch_pdl(oz_syrk_kernel, dim3(g), dim3(512), oz_syrk_smem(), st, A, n, r0, M, K,
              static_cast<const __nv_bfloat16*>(D), E, flag, strip, toff, ntiles);
 }
 
