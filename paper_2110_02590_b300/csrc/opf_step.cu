@@ -33,6 +33,8 @@ struct StepWork {
   int* h_flag;
   void* block = nullptr;
   cudaEvent_t ev[7] = {};  // phase boundaries of a step
+  cudaStream_t aux = nullptr;       // the right-hand side J^T v runs here beside the Cholesky
+  cudaEvent_t aux_go = nullptr, aux_done = nullptr;
   unsigned* trsv_flags = nullptr;  // [ceil(n_u / 32)] block flags of the dense solves (epochs)
   int* trsv_err = nullptr;         // a dense-solve wait timed out
   unsigned trsv_epoch = 0;
@@ -42,6 +44,9 @@ void free_step_work(opf_ctx* c) {
   if (!c->stepw) return;
   StepWork* w = c->stepw;
   if (w->block) cudaFree(w->block);
+  if (w->aux_go) cudaEventDestroy(w->aux_go);
+  if (w->aux_done) cudaEventDestroy(w->aux_done);
+  if (w->aux) cudaStreamDestroy(w->aux);
   if (w->oz_e) cudaFree(w->oz_e);
   if (w->oz_d) cudaFree(w->oz_d);
   if (w->h_red) cudaFreeHost(w->h_red);
@@ -661,6 +666,15 @@ opf_status alloc_step(opf_ctx* c) {
       return so;
     }
   }
+  if (cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->aux_go, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->aux_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c->stepw = w;
+    free_step_work(c);
+    set_last_error("cannot create the step's second stream");
+    return OPF_ECUDA;
+  }
   c->stepw = w;
   return OPF_OK;
 }
@@ -775,10 +789,17 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   SCK(cudaEventRecord(ev[2], stream));
   sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
   c->launches++;
-  // r = -grad_u psi - J^T v  (state quantities of this point are still in the context)
+  // r = -grad_u psi - J^T v on the second stream, beside the Cholesky (it reads
+  // the state and v, and writes the adjoint buffers, which the factorisation
+  // does not touch); the solves below wait for it
+  SCK(cudaEventRecord(w->aux_go, stream));
+  SCK(cudaStreamWaitEvent(w->aux, w->aux_go, 0));
+  c->stream = w->aux;
   launch_weighted_grad(c, w->v, w->Jtv);
-  neg_sum_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, w->Jtv, w->r);
+  neg_sum_kernel<<<nblk(nu, 256), 256, 0, w->aux>>>(nu, w->gpsi_u, w->Jtv, w->r);
   c->launches++;
+  c->stream = stream;
+  SCK(cudaEventRecord(w->aux_done, w->aux));
   SCK(cudaEventRecord(ev[3], stream));
   // Cholesky with inertia correction
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
@@ -789,16 +810,21 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
     c->launches++;
     rc = launch_cholesky(c, w, w->L, nu, w->flag);
-    if (rc) return rc;
+    if (rc) {
+      cudaStreamWaitEvent(stream, w->aux_done, 0);  // no work of this call outlives it
+      return rc;
+    }
     SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
     SCK(cudaStreamSynchronize(stream));
     if (!*w->h_flag) break;
     if (tries >= max_inertia) {
+      cudaStreamWaitEvent(stream, w->aux_done, 0);
       set_last_error("S_uu not positive definite after the inertia corrections");
       return OPF_ENOTPD;
     }
     delta = (delta0 > 0.0) ? delta0 * std::pow(10.0, (double)(tries + 1)) : 1e-8 * std::pow(10.0, (double)tries);
   }
+  SCK(cudaStreamWaitEvent(stream, w->aux_done, 0));
   SCK(cudaEventRecord(ev[4], stream));
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   rc = launch_chol_solve(c, w, w->L, nu, w->du);
