@@ -56,8 +56,9 @@ struct Built {
 // issues at most one per ~67 cycles, so the model counts warp FP64
 // instructions: per task the most entries of a lane (twice when the task has a
 // two-row block), one shuffle-add round per doubling of its largest group and
-// the finishing operations, plus ~70 cycles of shared-memory latency per pass
-// of the entry loop; task t runs on warp t mod 16.  k minimises the larger of
+// the finishing operations, plus the latencies of a task's chain: ~60 cycles
+// of shared-memory reads per pass of the entry loop, ~110 per shuffle round,
+// ~300 to finish; task t runs on warp t mod 16.  k minimises the larger of
 // the SM's FP64 time and the busiest warp's time.  Returns the lane map: per
 // task and lane, record | lane in the group << 16 | log2 of the group << 21,
 // or -1.
@@ -75,7 +76,7 @@ std::vector<int> plan_lanes(const std::vector<Rec>& L, size_t i, int nrec) {
     auto close = [&]() {
       if (map.empty()) return;
       ins.push_back((long)(two ? 2 : 1) * mx + lgmax + 3);
-      lat.push_back(70L * (mx / 4 + mx % 4 + 1));
+      lat.push_back(60L * (mx / 4 + mx % 4 + 1) + 110L * lgmax + 300);
     };
     for (int r = 0; r < nrec; r++) {
       const int len = L[i + r].q1 - L[i + r].q0;
