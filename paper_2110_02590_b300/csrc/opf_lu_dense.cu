@@ -77,11 +77,10 @@ __global__ void __launch_bounds__(256) lu_dense_cluster_kernel(double* LU, const
   // row k (owned here) with its reciprocal into every CTA's pivot slot k, then the flags
   auto publish = [&](int k) {
     const double* row = mine + (size_t)(k / K) * s;
-    if (tid == 0) {
+    if (tid < K) {  // one thread per destination: the reciprocal
       const double u = row[k];
-      if (!(fabs(u) > 0.0) || !isfinite(u)) flags[0] = 1;
-      const double inv = 1.0 / u;
-      for (int p = 0; p < K; p++) cl_st_f64(cl_map(pinv + k, p), inv);
+      if (tid == 0 && (!(fabs(u) > 0.0) || !isfinite(u))) flags[0] = 1;
+      cl_st_f64(cl_map(pinv + k, tid), 1.0 / u);
     }
     const int w = s - k;
     for (int e = tid; e < K * w; e += nt) {
@@ -89,10 +88,8 @@ __global__ void __launch_bounds__(256) lu_dense_cluster_kernel(double* LU, const
       cl_st_f64(cl_map(piv + (size_t)k * s + j, p), row[j]);
     }
     __syncthreads();
-    if (tid < K) {
-      asm volatile("fence.acq_rel.cluster;" ::: "memory");
-      cl_release_u32(cl_map(flag + k, tid), (unsigned)(k + 1));
-    }
+    // the release store orders this CTA's writes above (ordered before it by the barrier)
+    if (tid < K) cl_release_u32(cl_map(flag + k, tid), (unsigned)(k + 1));
   };
   if (q == 0 && s > 0) publish(0);
   for (int k = 0; k + 1 < s; k++) {
