@@ -222,13 +222,15 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
       const bool two = tr.w >= 0;
       const double uff = LU[tr.y];
       const double inv_ff = 1.0 / uff;
-      const double lf = LU[tr.x] * inv_ff;
-      double lv = 0.0, lvf = 0.0, uvv = 1.0;
+      const double arf = LU[tr.x];
+      const double lf = arf * inv_ff;
+      double lv = 0.0, lvf = 0.0;
       if (two) {
-        const double ufv = LU[tr.y + 1];
-        lvf = LU[tr.w - 1] * inv_ff;
-        uvv = LU[tr.w] - lvf * ufv;
-        lv = (LU[tr.x + 1] - lf * ufv) / uvv;
+        // l_v = (A_rv - l_f U_fv) / (A_vv - L_vf U_fv), both scaled by U_ff so that
+        // its division runs beside 1 / U_ff instead of after it
+        const double ufv = LU[tr.y + 1], avf = LU[tr.w - 1], avv = LU[tr.w], arv = LU[tr.x + 1];
+        lvf = avf * inv_ff;
+        lv = fma(arv, uff, -arf * ufv) / fma(avv, uff, -avf * ufv);
       }
       __syncwarp(gmask);
       if (li == 0) {
@@ -322,13 +324,26 @@ __global__ void lu_finish_kernel(const double* LU, double* T, double* invdiag, c
 // ------------------------------------------------------------ sweeps
 
 // Rows [p0, p1) of V against the slab: s = X[i] - sum V[p] X[ci[p]] (two partial
-// sums, four loads in flight per lane group; a ragged tail of one to three
-// entries is loaded in one batch, absent entries re-reading the first one).
+// sums, eight then four loads in flight per lane group; a ragged tail of one to
+// three entries is loaded in one batch, absent entries re-reading the first one).
 template <int C>
 __device__ __forceinline__ double row_dot(const DevNet& n, const double* __restrict__ V, const double* X,
                                           int i, int p0, int p1, int col) {
   double s0 = X[(size_t)i * C + col], s1 = 0.0;
   int p = p0;
+  for (; p + 7 < p1; p += 8) {  // eight slab reads in flight
+    int ci[8];
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) ci[k] = __ldg(n.ci + p + k);
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = X[(size_t)ci[k] * C + col];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      s0 -= V[p + k] * x[k];
+      s1 -= V[p + k + 1] * x[k + 1];
+    }
+  }
   for (; p + 3 < p1; p += 4) {
     const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + 1), c2 = __ldg(n.ci + p + 2), c3 = __ldg(n.ci + p + 3);
     const double v0 = V[p], v1 = V[p + 1], v2 = V[p + 2], v3 = V[p + 3];

@@ -370,8 +370,7 @@ __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict
       const double x = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
                        ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
       if (live) b[row] = x;
-      __threadfence();
-      __syncwarp();
+      __syncwarp();  // orders the warp's stores before lane 0's release
       if (lane == 0) st_release_u32(flags + i, epoch);
     }
     __syncthreads();
