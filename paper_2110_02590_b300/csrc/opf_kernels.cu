@@ -450,6 +450,57 @@ __device__ __forceinline__ void block_dot(const DevNet& n, const double* __restr
   b += b1;
 }
 
+// Dense trailing triangle of a sweep with each (row, column) value held in one
+// thread's registers: thread t owns column t % C of rows t / C + m (blockDim / C),
+// m < MR.  Step j: the owner of row j writes x_j (times 1/U_jj when DIAG) into
+// its own slot of tb[s][C], one barrier, then every owner of a later (FWD) or
+// earlier row subtracts its entry of V times that value.  The entries of V are
+// loaded before the barrier, so their latency hides behind it; the slots are
+// written once each, so one barrier per step suffices.  from_tb: the starting
+// values are in tb (else in X); the results go to X, scaled by 1/U_ii when DIAG.
+// Needs s C <= MR blockDim and tb holding s C doubles.
+template <int C, bool FWD, bool DIAG, int MR>
+__device__ __forceinline__ void tri_regs(const DevNet& n, const double* __restrict__ V,
+                                         const double* __restrict__ invdiag, double* X, double* tb,
+                                         bool from_tb) {
+  const int r0 = n.r0, s = n.nroot;
+  const int c = threadIdx.x % C, i0 = threadIdx.x / C, di = blockDim.x / C;
+  double x[MR], dg[MR];
+  int dpi[MR];
+#pragma unroll
+  for (int m = 0; m < MR; m++) {
+    const int i = i0 + m * di;
+    const bool own = i < s;
+    x[m] = own ? (from_tb ? tb[i * C + c] : X[(size_t)(r0 + i) * C + c]) : 0.0;
+    dpi[m] = own ? n.dp[r0 + i] : 0;
+    dg[m] = (DIAG && own) ? invdiag[r0 + i] : 1.0;
+  }
+  for (int st = 0; st + 1 < s; st++) {
+    const int j = FWD ? st : s - 1 - st;
+    double v[MR];
+#pragma unroll
+    for (int m = 0; m < MR; m++) {
+      const int i = i0 + m * di;
+      const bool act = FWD ? (i > j && i < s) : (i < j);
+      v[m] = act ? V[dpi[m] + (j - i)] : 0.0;  // entry (i, j): dp[i] + (j - i)
+      if (i == j) tb[j * C + c] = x[m] * dg[m];
+    }
+    __syncthreads();
+    const double xj = tb[j * C + c];
+#pragma unroll
+    for (int m = 0; m < MR; m++) {
+      const int i = i0 + m * di;
+      if (FWD ? (i > j && i < s) : (i < j)) x[m] = fma(-v[m], xj, x[m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MR; m++) {
+    const int i = i0 + m * di;
+    if (i < s) X[(size_t)(r0 + i) * C + c] = x[m] * dg[m];
+  }
+  __syncthreads();
+}
+
 // One triangular sweep over a CTA-private right-hand-side slab X[n_x][C].
 // Rows outside the dense trailing block [r0, n_x) follow the level schedule
 // (FWD: lower part of V, rows by ascending level; else the upper part).  The
@@ -461,13 +512,17 @@ __device__ __forceinline__ void block_dot(const DevNet& n, const double* __restr
 template <int C, bool FWD, bool DIAG>
 __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
                                       const double* __restrict__ invdiag, double* X,
-                                      const unsigned* rmask = nullptr) {
+                                      const unsigned* rmask = nullptr, double* tb = nullptr) {
   constexpr int RPW = 32 / C;
+  constexpr int TRI_MR = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = lane % C;
   const int nslots = (blockDim.x >> 5) * RPW, myslot = warp * RPW + lane / C;
   const int r0 = n.r0, s = n.nroot;
-  if (!FWD) {  // dense upper triangle of the trailing block first
+  // the triangle in registers when the caller lends shared memory for it
+  const bool treg = tb != nullptr && s * C <= TRI_MR * (int)blockDim.x;
+  if (!FWD && treg) tri_regs<C, false, DIAG, TRI_MR>(n, V, invdiag, X, tb, false);
+  if (!FWD && !treg) {  // dense upper triangle of the trailing block first
     for (int j = s - 1; j > 0; j--) {
       const int rj = r0 + j;
       const double dj = DIAG ? invdiag[rj] : 1.0;
@@ -591,10 +646,19 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
     // off-block part of the trailing rows (columns < r0), all rows in parallel
     for (int k = myslot; k < s; k += nslots) {
       const int i = r0 + k;
-      X[(size_t)i * C + col] = rmask ? row_dot_masked<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col, rmask)
-                                     : row_dot<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col);
+      const double xi = rmask ? row_dot_masked<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col, rmask)
+                              : row_dot<C>(n, V, X, i, n.rp[i], n.dp[i] - k, col);
+      if (treg) {
+        tb[k * C + col] = xi;
+      } else {
+        X[(size_t)i * C + col] = xi;
+      }
     }
     __syncthreads();
+    if (treg) {
+      tri_regs<C, true, DIAG, TRI_MR>(n, V, invdiag, X, tb, true);
+      return;
+    }
     // dense lower triangle
     for (int j = 0; j < s - 1; j++) {
       const int rj = r0 + j;
@@ -1136,6 +1200,9 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
   unsigned* s_mask = reinterpret_cast<unsigned*>(s_zs + (size_t)a.zs_cap * C);
   int* s_pre = reinterpret_cast<int*>(s_mask + a.rm_words);
   int* s_list = s_pre + a.rm_words;
+  // the values region, free outside the first solve's reach phase, serves the
+  // sweeps' dense trailing triangles
+  double* s_tb = a.zs_cap >= n.nroot ? s_zs : nullptr;
   __shared__ int s_col[32];
   __shared__ int s_nl;
   __shared__ double s_part[2][16][32];  // per-warp partial row sums (<= 512 threads)
@@ -1320,12 +1387,12 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     }
     if (nl <= a.list_cap) {
       __syncthreads();
-      sweep<C, true, false>(n, a.LU, a.invdiag, Z, s_mask);
+      sweep<C, true, false>(n, a.LU, a.invdiag, Z, s_mask, s_tb);
     } else {
-      sweep<C, true, false>(n, a.LU, a.invdiag, Z);
+      sweep<C, true, false>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
     }
     // (2) U sweep
-    sweep<C, false, true>(n, a.LU, a.invdiag, Z);
+    sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
     // (3) directional derivatives of Q (slack and PV) and P (slack) for the
     // Gauss-Newton terms, stored pre-multiplied by their weights kQ, kP.  The
     // own-variable parts are the per-bus sums dQ_k/dv_k, dQ_k/dtheta_k, ...
@@ -1411,8 +1478,8 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     }
     __syncthreads();
     // (5)-(6) second second-order adjoint: U^T then L^T sweeps
-    sweep<C, true, true>(n, a.T, a.invdiag, R);
-    sweep<C, false, false>(n, a.T, a.invdiag, R);
+    sweep<C, true, true>(n, a.T, a.invdiag, R, nullptr, s_tb);
+    sweep<C, false, false>(n, a.T, a.invdiag, R, nullptr, s_tb);
     // (7) H[:, tile] += G_u^T Psi
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
       const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = s_col[c];
