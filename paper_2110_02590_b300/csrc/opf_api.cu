@@ -591,6 +591,30 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(setup_solve1(c));
   TRY(setup_sweep_streams(c, bsched_ptr_f, bmeta_f, bsched_ptr_b, bmeta_b));
   c->lu_dense_cluster = setup_lu_dense_cluster(c->dn.nroot);
+  {
+    // the trailing levels that the cluster's warps take in one pass each run
+    // inside the cluster's launch (one cluster barrier per level)
+    const int nlev = (int)c->h_task_ptr.size() - 1;
+    std::vector<int4> lvrec(nlev + 1);
+    for (int lv = 0; lv <= nlev; lv++) {
+      lvrec[lv].x = lv < nlev ? c->h_task_ptr[lv] : 0;
+      lvrec[lv].y = lv < nlev ? c->h_task_ptr[lv + 1] : 0;
+      lvrec[lv].z = lv > 0 ? c->h_fin_ptr[lv - 1] : 0;
+      lvrec[lv].w = lv > 0 ? c->h_fin_ptr[lv] : 0;
+    }
+    c->lu_tail_from = nlev + 1;
+    if (c->lu_dense_cluster > 0) {
+      const long warps = (long)c->lu_dense_cluster * kLuClusterThreads / 32;
+      for (int lv = nlev; lv >= 0; lv--) {
+        const long items = (lvrec[lv].y - lvrec[lv].x) + (lvrec[lv].w - lvrec[lv].z);
+        const long per_warp = 32 / std::max(1, c->h_lu_lanes[lv]);
+        if (items > warps * per_warp) break;
+        c->lu_tail_from = lv;
+      }
+    }
+    TRY(dupload(c, &c->lu_lvrec, lvrec));
+    TRY(dupload(c, &c->lu_lanes, c->h_lu_lanes));
+  }
   setup_hvp_smem();
   // the numeric refactorisation as one CUDA graph (captured once on a private stream)
   CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));

@@ -178,6 +178,84 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+
+// 1 / u by the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - u r)
+// (each step squares the relative error), from the hardware's approximate FP64
+// reciprocal: two steps reach full double precision for normal u.  It issues
+// one MUFU and four DFMA where the IEEE division issues a longer FP64 sequence,
+// which matters where many warps each divide once (the FP64 pipe runs one warp
+// instruction per ~20 cycles whatever the active lanes).
+__device__ __forceinline__ double recip_nr(double u) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(u));
+  double e = fma(-u, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-u, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Work items of the right-looking LU by bus blocks (one level's tasks, and the
+// finish records of the previous level's two-row blocks), each on a lane group
+// of G lanes (li: lane in the group; gmask: the group's lanes).  CG: the factor
+// is read past L1 (a launch that runs several levels, where other CTAs' updates
+// of one level land in L2 before the next).
+template <bool CG>
+__device__ __forceinline__ double lu_ld(const double* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+// Task {position of A_rf, dp[f], rp[f + 1], dp[f + 1] or -1}: for row r below the
+// block, l_f = A_rf / U_ff and, for a two-row block, l_v = (A_r,f+1 - l_f U_f,f+1)
+// / U_vv with the block's own U_vv = A_vv - (A_vf / U_ff) U_f,f+1 formed on the
+// fly; then every column c of row f past the block gets A_rc -= l_f U_fc +
+// l_v (A_vc - L_vf U_fc) at its precomputed target tg[c - first] (atomics: the
+// tasks of a level may share targets).
+template <bool CG>
+__device__ __forceinline__ void lu_task(double* LU, const int4 tr, const int* __restrict__ tg, int li, int G,
+                                        unsigned gmask, int* flags) {
+  const bool two = tr.w >= 0;
+  const double uff = lu_ld<CG>(LU + tr.y);
+  const double inv_ff = recip_nr(uff);
+  const double arf = lu_ld<CG>(LU + tr.x);
+  const double lf = arf * inv_ff;
+  double lv = 0.0, lvf = 0.0;
+  if (two) {
+    // l_v = (A_rv - l_f U_fv) / (A_vv - L_vf U_fv), both scaled by U_ff so that
+    // its reciprocal runs beside 1 / U_ff instead of after it
+    const double ufv = lu_ld<CG>(LU + tr.y + 1), avf = lu_ld<CG>(LU + tr.w - 1);
+    const double avv = lu_ld<CG>(LU + tr.w), arv = lu_ld<CG>(LU + tr.x + 1);
+    lvf = avf * inv_ff;
+    lv = fma(arv, uff, -arf * ufv) * recip_nr(fma(avv, uff, -avf * ufv));
+  }
+  __syncwarp(gmask);
+  if (li == 0) {
+    LU[tr.x] = lf;
+    if (two) LU[tr.x + 1] = lv;
+    if (!(fabs(uff) > 0.0) || !isfinite(lf) || !isfinite(lv)) flags[0] = 1;
+  }
+  const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
+  for (int q = q0 + li; q < tr.z; q += G) {
+    const double ufc = lu_ld<CG>(LU + q);
+    double d = lf * ufc;
+    if (two) d += lv * (lu_ld<CG>(LU + qv + (q - q0)) - lvf * ufc);
+    atomicAdd(&LU[tg[q - q0]], -d);
+  }
+}
+// Finish record {dp[f], rp[f + 1], dp[f + 1]} of a two-row block: L_vf, U_vv and
+// the second row's upper entries after eliminating f (no task reads them any more).
+template <bool CG>
+__device__ __forceinline__ void lu_finish(double* LU, const int4 fr, int li, int G, unsigned gmask) {
+  const double uff = lu_ld<CG>(LU + fr.x);
+  const double lvf = lu_ld<CG>(LU + fr.z - 1) * recip_nr(uff);
+  const double ufv = lu_ld<CG>(LU + fr.x + 1);
+  for (int q = fr.x + 2 + li; q < fr.y; q += G)
+    LU[fr.z + 1 + (q - fr.x - 2)] = lu_ld<CG>(LU + fr.z + 1 + (q - fr.x - 2)) - lvf * lu_ld<CG>(LU + q);
+  __syncwarp(gmask);
+  if (li == 0) {
+    LU[fr.z - 1] = lvf;
+    LU[fr.z] = lu_ld<CG>(LU + fr.z) - lvf * ufv;
+  }
+}
 #endif
 
 // Level-packed single-RHS sweeps (opf_sweep.cu).  The factor entries a sweep
@@ -210,8 +288,22 @@ struct SweepStreams {
 // K <= 128 a multiple of 32; E: n - r0 ints, D: 8 (n - r0) K bf16 workspace.
 // Dense LU of the trailing block on one thread-block cluster (opf_lu_dense.cu):
 // the cluster size for a block of s rows (0: the one-CTA kernel), and the launch.
+// The cluster also runs the last sparse levels [lv0, nlev] first (lvrec: per
+// level {t0, t1, f0, f1} task and finish ranges, lanes: lane-group width), one
+// cluster barrier per level instead of one launch.
+constexpr int kLuClusterThreads = 256;
 int setup_lu_dense_cluster(int s);
-void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, int r0, int s, int* flags);
+struct LuTail {
+  const int4* task_rec = nullptr;
+  const int* task_off = nullptr;
+  const int* task_map = nullptr;
+  const int4* fin_rec = nullptr;
+  const int4* lvrec = nullptr;  // indexed by level
+  const int* lanes = nullptr;   // indexed by level
+  int lv0 = 0, lv1 = 0;         // levels [lv0, lv1) run in the cluster
+};
+void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, int r0, int s, int* flags,
+                             const LuTail& tail);
 
 opf_status setup_oz();
 void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag);
@@ -250,6 +342,9 @@ struct opf_ctx {
   int4* fin_rec = nullptr;
   std::vector<int> h_task_ptr, h_fin_ptr;
   std::vector<int> h_lu_lanes;      // per launch of the LU levels: lanes per work item
+  int4* lu_lvrec = nullptr;         // per launch {t0, t1, f0, f1}
+  int* lu_lanes = nullptr;          // h_lu_lanes on the device
+  int lu_tail_from = 0;             // first level launch run inside the dense block's cluster
   std::vector<int> h_lev_ptr_f, h_lev_ptr_b;
 
   // device: state of the last converged power flow

@@ -190,14 +190,10 @@ __global__ void pf_eval_kernel(DevNet n, const double* vb, const double* tb, con
 // ------------------------------------------------------------ numeric LU
 
 // One level of the right-looking LU on the fixed pattern, by bus blocks (one or
-// two pivot rows f, f + 1 whose off-block patterns coincide).  Warps [0, t1 - t0)
-// take a task each: for row r below the block, l_f = A_rf / U_ff and, for a
-// two-row block, l_v = (A_r,f+1 - l_f U_f,f+1) / U_vv with the block's own
-// U_vv = A_vv - (A_vf / U_ff) U_f,f+1 formed on the fly; then every column c of
-// row f past the block gets A_rc -= l_f U_fc + l_v (A_vc - L_vf U_fc) at the
-// precomputed target (atomics: tasks of a level may share targets).  The other
-// warps finish the second rows of the previous level's two-row blocks (L_vf,
-// U_vv, U_vc), which no task of this level reads.
+// two pivot rows f, f + 1 whose off-block patterns coincide).  Work items: the
+// level's tasks (lu_task: eliminate the block's pivots from one row below it),
+// then the finish records of the previous level's two-row blocks (lu_finish),
+// which no task of this level reads.
 __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const int* __restrict__ toff,
                                 const int* __restrict__ map, int t0, int t1, const int4* __restrict__ frec,
                                 int f0, int f1, int* flags, int G) {
@@ -219,44 +215,9 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
     if (w < ntask) {
       const int t = t0 + w;
       const int4 tr = (w == wfirst) ? tr_first : __ldg(trec + t);
-      const bool two = tr.w >= 0;
-      const double uff = LU[tr.y];
-      const double inv_ff = 1.0 / uff;
-      const double arf = LU[tr.x];
-      const double lf = arf * inv_ff;
-      double lv = 0.0, lvf = 0.0;
-      if (two) {
-        // l_v = (A_rv - l_f U_fv) / (A_vv - L_vf U_fv), both scaled by U_ff so that
-        // its division runs beside 1 / U_ff instead of after it
-        const double ufv = LU[tr.y + 1], avf = LU[tr.w - 1], avv = LU[tr.w], arv = LU[tr.x + 1];
-        lvf = avf * inv_ff;
-        lv = fma(arv, uff, -arf * ufv) / fma(avv, uff, -avf * ufv);
-      }
-      __syncwarp(gmask);
-      if (li == 0) {
-        LU[tr.x] = lf;
-        if (two) LU[tr.x + 1] = lv;
-        if (!(fabs(uff) > 0.0) || !isfinite(lf) || !isfinite(lv)) flags[0] = 1;
-      }
-      const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
-      const int* tg = map + toff[t] - q0;
-      for (int q = q0 + li; q < tr.z; q += G) {
-        const double ufc = LU[q];
-        double d = lf * ufc;
-        if (two) d += lv * (LU[qv + (q - q0)] - lvf * ufc);
-        atomicAdd(&LU[tg[q]], -d);
-      }
+      lu_task<false>(LU, tr, map + toff[t], li, G, gmask, flags);
     } else if (w < nall) {
-      const int4 fr = __ldg(frec + f0 + (w - ntask));  // {dp[f], rp[f + 1], dp[f + 1]}
-      const double uff = LU[fr.x];
-      const double lvf = LU[fr.z - 1] / uff;
-      const double ufv = LU[fr.x + 1];
-      for (int q = fr.x + 2 + li; q < fr.y; q += G) LU[fr.z + 1 + (q - fr.x - 2)] -= lvf * LU[q];
-      __syncwarp(gmask);
-      if (li == 0) {
-        LU[fr.z - 1] = lvf;
-        LU[fr.z] -= lvf * ufv;
-      }
+      lu_finish<false>(LU, __ldg(frec + f0 + (w - ntask)), li, G, gmask);
     }
   }
   asm volatile("griddepcontrol.launch_dependents;");
@@ -1580,7 +1541,8 @@ void launch_lu_kernels(opf_ctx* c) {
   const int nlev = (int)c->h_task_ptr.size() - 1;  // block levels of the non-trailing columns
   // level lv's tasks with the finish records of level lv - 1; one more launch
   // finishes the last level
-  for (int lv = 0; lv <= nlev; lv++) {
+  const int lv_end = c->lu_dense_cluster > 0 ? c->lu_tail_from : nlev + 1;
+  for (int lv = 0; lv < lv_end; lv++) {
     const int t0 = lv < nlev ? c->h_task_ptr[lv] : 0, t1 = lv < nlev ? c->h_task_ptr[lv + 1] : 0;
     const int f0 = lv > 0 ? c->h_fin_ptr[lv - 1] : 0, f1 = lv > 0 ? c->h_fin_ptr[lv] : 0;
     const int items = (t1 - t0) + (f1 - f0);
@@ -1605,9 +1567,19 @@ void launch_lu_kernels(opf_ctx* c) {
   c->launches++;
   const size_t dense_smem = sizeof(double) * (size_t)c->dn.nroot * c->dn.nroot;
   const int use_smem = dense_smem <= (size_t)kDenseLuSmem ? 1 : 0;
-  if (c->lu_dense_cluster > 0)
-    launch_lu_dense_cluster(c->stream, c->lu_dense_cluster, c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags);
-  else
+  if (c->lu_dense_cluster > 0) {
+    LuTail tail;
+    tail.task_rec = c->task_rec;
+    tail.task_off = c->task_off;
+    tail.task_map = c->task_map;
+    tail.fin_rec = c->fin_rec;
+    tail.lvrec = c->lu_lvrec;
+    tail.lanes = c->lu_lanes;
+    tail.lv0 = lv_end;
+    tail.lv1 = nlev + 1;
+    launch_lu_dense_cluster(c->stream, c->lu_dense_cluster, c->LU, c->dn.dp, c->dn.r0, c->dn.nroot, c->flags,
+                            tail);
+  } else
     lu_dense_block_kernel<<<1, 1024, use_smem ? dense_smem : 0, c->stream>>>(c->LU, c->dn.dp, c->dn.r0,
                                                                           c->dn.nroot, c->flags, use_smem);
   c->launches++;

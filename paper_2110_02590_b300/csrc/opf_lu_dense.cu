@@ -57,19 +57,45 @@ __device__ __forceinline__ void cl_sync() {
 
 // Dynamic shared memory per CTA: own rows [nr][s], pivot rows [s][s] and their
 // reciprocals [s] (doubles), then the step flags [s] (u32); nr = ceil(s / K).
-__global__ void __launch_bounds__(256) lu_dense_cluster_kernel(double* LU, const int* __restrict__ dp, int r0,
-                                                               int s, int* flags) {
+// Before the trailing block, the cluster runs the last, narrow levels of the
+// sparse LU (tail): their work items are spread over all warps of the cluster
+// as in one level launch, the factor is read through L2 (lu_ld<true>), and a
+// cluster barrier (release / acquire) separates the levels, in place of a
+// kernel boundary each.
+__global__ void __launch_bounds__(kLuClusterThreads, 1)
+    lu_dense_cluster_kernel(double* LU, const int* __restrict__ dp, int r0, int s, int* flags, LuTail tail) {
   extern __shared__ __align__(16) double dsm[];
   const int K = (int)cl_size(), q = (int)cl_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tail.lv0 < tail.lv1) {
+    const int lane = tid & 31;
+    const int warp = (q * nt + tid) >> 5, nw = (K * nt) >> 5;
+    for (int lv = tail.lv0; lv < tail.lv1; lv++) {
+      const int4 rg = __ldg(tail.lvrec + lv);  // {t0, t1, f0, f1}
+      const int G = __ldg(tail.lanes + lv), li = lane & (G - 1), ipw = 32 / G;
+      const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+      const int ntask = rg.y - rg.x, nall = ntask + (rg.w - rg.z);
+      for (int base = warp * ipw; base < nall; base += nw * ipw) {
+        const int w = base + lane / G;
+        if (w < ntask) {
+          const int t = rg.x + w;
+          lu_task<true>(LU, __ldg(tail.task_rec + t), tail.task_map + __ldg(tail.task_off + t), li, G, gmask,
+                        flags);
+        } else if (w < nall) {
+          lu_finish<true>(LU, __ldg(tail.fin_rec + rg.z + (w - ntask)), li, G, gmask);
+        }
+      }
+      cl_sync();
+    }
+  }
   const int nr = (s + K - 1) / K;
   double* mine = dsm;                    // row q + K t at mine[t * s]
   double* piv = mine + (size_t)nr * s;   // row k at piv[k * s]
   double* pinv = piv + (size_t)s * s;    // 1 / U_kk
   unsigned* flag = reinterpret_cast<unsigned*>(pinv + s);
-  const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < nr * s; e += nt) {
     const int t = e / s, j = e - t * s, i = q + K * t;
-    mine[e] = (i < s) ? LU[dp[r0 + i] - i + j] : 0.0;
+    mine[e] = (i < s) ? __ldcg(LU + dp[r0 + i] - i + j) : 0.0;
   }
   for (int k = tid; k < s; k += nt) flag[k] = 0u;
   __syncthreads();
@@ -166,7 +192,7 @@ int setup_lu_dense_cluster(int s) {
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(K);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(kLuClusterThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -177,7 +203,8 @@ int setup_lu_dense_cluster(int s) {
   return 0;
 }
 
-void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, int r0, int s, int* flags) {
+void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, int r0, int s, int* flags,
+                             const LuTail& tail) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -185,12 +212,12 @@ void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, 
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(K);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kLuClusterThreads);
   cfg.dynamicSmemBytes = lu_dense_cluster_smem(s, K);
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, lu_dense_cluster_kernel, LU, dp, r0, s, flags);
+  cudaLaunchKernelEx(&cfg, lu_dense_cluster_kernel, LU, dp, r0, s, flags, tail);
 }
 
 }  // namespace opf
