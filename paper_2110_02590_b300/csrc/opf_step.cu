@@ -81,16 +81,14 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 // by the dense triangular solves.
 __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0, int kb, int* flag,
                                                         double* Dinv) {
-  pdl_wait();
-  if (*flag) return;
   __shared__ double T[NB][NB + 1], X[NB][NB + 1];
   __shared__ double s_r[NB];
   __shared__ unsigned short tbl[NB * (NB + 1) / 2];  // packed (row, column) offsets of a triangle
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  // what does not depend on the previous kernel runs before the wait for it
   for (int q = tid; q < NB * NB; q += nt) {
     const int i = q >> 5, c = q & 31;
-    T[i][c] = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
     X[i][c] = (i == c) ? 1.0 : 0.0;
   }
   for (int e = tid; e < NB * (NB + 1) / 2; e += nt) {
@@ -100,6 +98,12 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
     tbl[e] = (unsigned short)((ri << 8) | (e - ri * (ri + 1) / 2));
   }
   if (tid == 0) s_bad = 0;
+  pdl_wait();
+  if (*flag) return;
+  for (int q = tid; q < NB * NB; q += nt) {  // lanes along a column of A (coalesced)
+    const int i = q & 31, c = q >> 5;
+    T[i][c] = (i < kb && c <= i) ? A[(size_t)(k0 + c) * n + k0 + i] : 0.0;
+  }
   __syncthreads();
   if (warp == 0) {
     double col = T[lane][0];
@@ -146,8 +150,9 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
   if (tid == 0 && s_bad) *flag = 1;
   for (int q = tid; q < NB * NB; q += nt) {
     const int i = q >> 5, c = q & 31;
-    if (i < kb && c <= i) A[(size_t)(k0 + c) * n + k0 + i] = T[i][c];
     Dinv[(size_t)(k0 / NB) * NB * NB + q] = (i < kb && c <= i) ? X[i][c] : 0.0;
+    const int ia = q & 31, ca = q >> 5;  // lanes along a column of A
+    if (ia < kb && ca <= ia) A[(size_t)(k0 + ca) * n + k0 + ia] = T[ia][ca];
   }
   pdl_trigger();
 }

@@ -482,18 +482,25 @@ __device__ __forceinline__ void sweep_prefetch(const SweepStream& st, unsigned c
 // Substitution through the staged trailing triangle (rows r0 .. r0 + s - 1), a
 // column per step, then the diagonal scaling (DIAG); dinv holds 1 / U_rr of
 // the trailing rows.
+// Only the threads with a row to update form x_j: an FP64 instruction costs the
+// pipe the same for a warp whatever its active lanes, so idle warps issue none.
 template <bool FWD, bool DIAG>
 __device__ __forceinline__ void tri_solve(int r0, int s, const double* tri, const double* dinv, double* X) {
+  const int tid = threadIdx.x;
   if (FWD) {
     for (int j = 0; j < s - 1; j++) {
-      const double xj = DIAG ? X[r0 + j] * dinv[j] : X[r0 + j];
-      for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) X[r0 + i] -= tri[i * (i - 1) / 2 + j] * xj;
+      if (tid < s - 1 - j) {
+        const double xj = DIAG ? X[r0 + j] * dinv[j] : X[r0 + j];
+        for (int i = j + 1 + tid; i < s; i += blockDim.x) X[r0 + i] -= tri[i * (i - 1) / 2 + j] * xj;
+      }
       __syncthreads();
     }
   } else {
     for (int j = s - 1; j > 0; j--) {
-      const double xj = DIAG ? X[r0 + j] * dinv[j] : X[r0 + j];
-      for (int i = threadIdx.x; i < j; i += blockDim.x) X[r0 + i] -= tri[i * (2 * s - i - 1) / 2 + (j - i - 1)] * xj;
+      if (tid < j) {
+        const double xj = DIAG ? X[r0 + j] * dinv[j] : X[r0 + j];
+        for (int i = tid; i < j; i += blockDim.x) X[r0 + i] -= tri[i * (2 * s - i - 1) / 2 + (j - i - 1)] * xj;
+      }
       __syncthreads();
     }
   }
