@@ -209,11 +209,26 @@ __device__ __forceinline__ double lu_ld(const double* p) {
 // / U_vv with the block's own U_vv = A_vv - (A_vf / U_ff) U_f,f+1 formed on the
 // fly; then every column c of row f past the block gets A_rc -= l_f U_fc +
 // l_v (A_vc - L_vf U_fc) at its precomputed target tg[c - first] (atomics: the
-// tasks of a level may share targets).
+// tasks of a level may share targets).  The lane groups are sized so that a
+// lane takes at most LU_PRE columns: their entries and targets are read in the
+// same round as the pivots (nothing the task writes aliases them), so the task
+// waits for L2 once instead of once per column step.
+constexpr int LU_PRE = 4;
 template <bool CG>
 __device__ __forceinline__ void lu_task(double* LU, const int4 tr, const int* __restrict__ tg, int li, int G,
                                         unsigned gmask, int* flags) {
   const bool two = tr.w >= 0;
+  const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
+  double ufc[LU_PRE], avc[LU_PRE];
+  int tgt[LU_PRE];
+#pragma unroll
+  for (int k = 0; k < LU_PRE; k++) {
+    const int q = q0 + li + k * G;
+    const bool in = q < tr.z;
+    ufc[k] = in ? lu_ld<CG>(LU + q) : 0.0;
+    avc[k] = (in && two) ? lu_ld<CG>(LU + qv + (q - q0)) : 0.0;
+    tgt[k] = in ? tg[q - q0] : 0;
+  }
   const double uff = lu_ld<CG>(LU + tr.y);
   const double inv_ff = recip_nr(uff);
   const double arf = lu_ld<CG>(LU + tr.x);
@@ -233,27 +248,50 @@ __device__ __forceinline__ void lu_task(double* LU, const int4 tr, const int* __
     if (two) LU[tr.x + 1] = lv;
     if (!(fabs(uff) > 0.0) || !isfinite(lf) || !isfinite(lv)) flags[0] = 1;
   }
-  const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
-  for (int q = q0 + li; q < tr.z; q += G) {
-    const double ufc = lu_ld<CG>(LU + q);
-    double d = lf * ufc;
-    if (two) d += lv * (lu_ld<CG>(LU + qv + (q - q0)) - lvf * ufc);
+#pragma unroll
+  for (int k = 0; k < LU_PRE; k++) {
+    if (q0 + li + k * G < tr.z) {
+      double d = lf * ufc[k];
+      if (two) d += lv * (avc[k] - lvf * ufc[k]);
+      atomicAdd(&LU[tgt[k]], -d);
+    }
+  }
+  for (int q = q0 + li + LU_PRE * G; q < tr.z; q += G) {  // wider rows than the lane sizing gives
+    const double u = lu_ld<CG>(LU + q);
+    double d = lf * u;
+    if (two) d += lv * (lu_ld<CG>(LU + qv + (q - q0)) - lvf * u);
     atomicAdd(&LU[tg[q - q0]], -d);
   }
 }
 // Finish record {dp[f], rp[f + 1], dp[f + 1]} of a two-row block: L_vf, U_vv and
-// the second row's upper entries after eliminating f (no task reads them any more).
+// the second row's upper entries after eliminating f (no task reads them any
+// more); the row entries are read in the pivots' round as in lu_task.
 template <bool CG>
 __device__ __forceinline__ void lu_finish(double* LU, const int4 fr, int li, int G, unsigned gmask) {
+  const int p0 = fr.x + 2, w0 = fr.z + 1;
+  double uq[LU_PRE], vq[LU_PRE];
+#pragma unroll
+  for (int k = 0; k < LU_PRE; k++) {
+    const int q = p0 + li + k * G;
+    const bool in = q < fr.y;
+    uq[k] = in ? lu_ld<CG>(LU + q) : 0.0;
+    vq[k] = in ? lu_ld<CG>(LU + w0 + (q - p0)) : 0.0;
+  }
   const double uff = lu_ld<CG>(LU + fr.x);
   const double lvf = lu_ld<CG>(LU + fr.z - 1) * recip_nr(uff);
   const double ufv = lu_ld<CG>(LU + fr.x + 1);
-  for (int q = fr.x + 2 + li; q < fr.y; q += G)
-    LU[fr.z + 1 + (q - fr.x - 2)] = lu_ld<CG>(LU + fr.z + 1 + (q - fr.x - 2)) - lvf * lu_ld<CG>(LU + q);
+  const double avv = lu_ld<CG>(LU + fr.z);
+#pragma unroll
+  for (int k = 0; k < LU_PRE; k++) {
+    const int q = p0 + li + k * G;
+    if (q < fr.y) LU[w0 + (q - p0)] = vq[k] - lvf * uq[k];
+  }
+  for (int q = p0 + li + LU_PRE * G; q < fr.y; q += G)
+    LU[w0 + (q - p0)] = lu_ld<CG>(LU + w0 + (q - p0)) - lvf * lu_ld<CG>(LU + q);
   __syncwarp(gmask);
   if (li == 0) {
     LU[fr.z - 1] = lvf;
-    LU[fr.z] = lu_ld<CG>(LU + fr.z) - lvf * ufv;
+    LU[fr.z] = avv - lvf * ufv;
   }
 }
 #endif
