@@ -214,20 +214,29 @@ __device__ __forceinline__ double lu_ld(const double* p) {
 // same round as the pivots (nothing the task writes aliases them), so the task
 // waits for L2 once instead of once per column step.
 constexpr int LU_PRE = 4;
+// The task's first LU_PRE targets per lane (static: a launch may read them
+// before it waits for the previous level).
+__device__ __forceinline__ void lu_targets(const int4 tr, const int* __restrict__ tg, int li, int G,
+                                           int (&tgt)[LU_PRE]) {
+  const int q0 = tr.y + (tr.w >= 0 ? 2 : 1);
+#pragma unroll
+  for (int k = 0; k < LU_PRE; k++) {
+    const int q = q0 + li + k * G;
+    tgt[k] = q < tr.z ? __ldg(tg + (q - q0)) : 0;
+  }
+}
 template <bool CG>
-__device__ __forceinline__ void lu_task(double* LU, const int4 tr, const int* __restrict__ tg, int li, int G,
-                                        unsigned gmask, int* flags) {
+__device__ __forceinline__ void lu_task(double* LU, const int4 tr, const int* __restrict__ tg,
+                                        const int (&tgt)[LU_PRE], int li, int G, unsigned gmask, int* flags) {
   const bool two = tr.w >= 0;
   const int q0 = tr.y + (two ? 2 : 1), qv = tr.w + 1;
   double ufc[LU_PRE], avc[LU_PRE];
-  int tgt[LU_PRE];
 #pragma unroll
   for (int k = 0; k < LU_PRE; k++) {
     const int q = q0 + li + k * G;
     const bool in = q < tr.z;
     ufc[k] = in ? lu_ld<CG>(LU + q) : 0.0;
     avc[k] = (in && two) ? lu_ld<CG>(LU + qv + (q - q0)) : 0.0;
-    tgt[k] = in ? tg[q - q0] : 0;
   }
   const double uff = lu_ld<CG>(LU + tr.y);
   const double inv_ff = recip_nr(uff);

@@ -205,17 +205,31 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int ntask = t1 - t0, nall = ntask + (f1 - f0);
-  // the task records are static: the first one is read before the wait for the
-  // previous level (programmatic dependent launch)
+  // the task records and targets are static: the first task's are read before
+  // the wait for the previous level (programmatic dependent launch)
   const int wfirst = warp * ipw + lane / G;
-  const int4 tr_first = wfirst < ntask ? __ldg(trec + t0 + wfirst) : make_int4(0, 0, 0, 0);
+  int4 tr_first = make_int4(0, 0, 0, 0);
+  const int* tg_first = map;
+  int tgt_first[LU_PRE] = {0, 0, 0, 0};
+  if (wfirst < ntask) {
+    tr_first = __ldg(trec + t0 + wfirst);
+    tg_first = map + __ldg(toff + t0 + wfirst);
+    lu_targets(tr_first, tg_first, li, G, tgt_first);
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int base = warp * ipw; base < nall; base += nw * ipw) {
     const int w = base + lane / G;
     if (w < ntask) {
-      const int t = t0 + w;
-      const int4 tr = (w == wfirst) ? tr_first : __ldg(trec + t);
-      lu_task<false>(LU, tr, map + toff[t], li, G, gmask, flags);
+      if (w == wfirst) {
+        lu_task<false>(LU, tr_first, tg_first, tgt_first, li, G, gmask, flags);
+      } else {
+        const int t = t0 + w;
+        const int4 tr = __ldg(trec + t);
+        const int* tg = map + __ldg(toff + t);
+        int tgt[LU_PRE];
+        lu_targets(tr, tg, li, G, tgt);
+        lu_task<false>(LU, tr, tg, tgt, li, G, gmask, flags);
+      }
     } else if (w < nall) {
       lu_finish<false>(LU, __ldg(frec + f0 + (w - ntask)), li, G, gmask);
     }

@@ -79,8 +79,11 @@ __global__ void __launch_bounds__(kLuClusterThreads, 1)
         const int w = base + lane / G;
         if (w < ntask) {
           const int t = rg.x + w;
-          lu_task<true>(LU, __ldg(tail.task_rec + t), tail.task_map + __ldg(tail.task_off + t), li, G, gmask,
-                        flags);
+          const int4 tr = __ldg(tail.task_rec + t);
+          const int* tg = tail.task_map + __ldg(tail.task_off + t);
+          int tgt[LU_PRE];
+          lu_targets(tr, tg, li, G, tgt);
+          lu_task<true>(LU, tr, tg, tgt, li, G, gmask, flags);
         } else if (w < nall) {
           lu_finish<true>(LU, __ldg(tail.fin_rec + rg.z + (w - ntask)), li, G, gmask);
         }
