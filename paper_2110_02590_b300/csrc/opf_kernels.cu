@@ -217,6 +217,8 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
     lu_targets(tr_first, tg_first, li, G, tgt_first);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next level's grid may launch now (it waits for this one to finish)
+  asm volatile("griddepcontrol.launch_dependents;");
   for (int base = warp * ipw; base < nall; base += nw * ipw) {
     const int w = base + lane / G;
     if (w < ntask) {
@@ -234,7 +236,6 @@ __global__ void lu_level_kernel(double* LU, const int4* __restrict__ trec, const
       lu_finish<false>(LU, __ldg(frec + f0 + (w - ntask)), li, G, gmask);
     }
   }
-  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // Dense LU of the trailing block [r0, r0 + s) (rows of it are contiguous in LU:
