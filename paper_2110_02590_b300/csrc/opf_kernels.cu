@@ -1516,7 +1516,7 @@ __global__ void __launch_bounds__(NT) hvp_split_kernel(HvpArgs a1, HvpArgs a2, i
 // largest network first) and run the same tile body with that context's
 // arguments staged in shared memory.  No CTA waits on another.
 template <int C>
-__global__ void __launch_bounds__(256) hvp_batch_kernel(const HvpArgs* __restrict__ args,
+__global__ void __launch_bounds__(256, 3) hvp_batch_kernel(const HvpArgs* __restrict__ args,
                                                         const int2* __restrict__ tiles, int ntot,
                                                         int* counter, double* scratch, size_t stride) {
   __shared__ HvpArgs sa;
