@@ -27,7 +27,7 @@ constexpr int kHdr = 32;
 
 inline int pad4(int e) { return (e + 3) & ~3; }
 inline int rv_count(int nrec) { return (3 * nrec + 1) & ~1; }
-constexpr int kMaxTasks = 32;  // warp tasks of a chunk (two passes of the CTA's 16 warps)
+constexpr int kMaxTasks = 2 * kSweepThreads / 32;  // warp tasks of a chunk (two passes of the CTA's warps)
 inline size_t chunk_bytes(int nrec, int ent, int ntask) {
   return kHdr + 128 * (size_t)ntask + 16 * (size_t)nrec + 8 * (size_t)rv_count(nrec) + 20 * (size_t)pad4(ent);
 }
@@ -516,7 +516,7 @@ __device__ __forceinline__ void tri_solve(int r0, int s, const double* tri, cons
 // (TR = true: U^T then L^T from T).  One CTA of 512 threads; dynamic shared
 // memory: the solution (n_x doubles) and the ring.
 template <bool TR>
-__global__ void __launch_bounds__(512) solve1s_kernel(DevNet n, SweepStream sf, SweepStream sb, const double* b,
+__global__ void __launch_bounds__(kSweepThreads) solve1s_kernel(DevNet n, SweepStream sf, SweepStream sb, const double* b,
                                                       double* out, double scale, int slot) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int nx = n.nx, r0 = n.r0, s = n.nroot;
@@ -597,9 +597,9 @@ void launch_solve1_streamed(opf_ctx* c, const double* b, double* out, bool trans
   c->launches++;
   const SweepStreams& sw = c->sw;
   if (!transposed)
-    solve1s_kernel<false><<<1, 512, sw.smem, c->stream>>>(c->dn, sw.s[0], sw.s[1], b, out, scale, sw.slot);
+    solve1s_kernel<false><<<1, kSweepThreads, sw.smem, c->stream>>>(c->dn, sw.s[0], sw.s[1], b, out, scale, sw.slot);
   else
-    solve1s_kernel<true><<<1, 512, sw.smem, c->stream>>>(c->dn, sw.s[2], sw.s[3], b, out, scale, sw.slot);
+    solve1s_kernel<true><<<1, kSweepThreads, sw.smem, c->stream>>>(c->dn, sw.s[2], sw.s[3], b, out, scale, sw.slot);
 }
 
 }  // namespace opf
