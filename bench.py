@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-cols", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
@@ -314,7 +314,8 @@ def run_gpu(args):
     state.update(u=d(u_h), s=d(s_h), mu=st_h["mu"])
     state["x"], _ = ctx.powerflow(state["u"], x0=x0)
     tune = ctx.autotune(dict(al, s=state["s"]))
-    nsnap = args.warmup + args.steps + 1
+    ke = max(1, min(args.steps, args.e2e_steps))  # end-to-end steps, on the snapshots after the timed ones
+    nsnap = args.warmup + args.steps + 1 + ke
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
     pds, qds = d(pds_h), d(qds_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -378,11 +379,11 @@ def run_gpu(args):
     host_s = torch.empty(ctx.m, dtype=torch.float64).pin_memory()
     dev_pd = torch.empty(net.n_bus, dtype=torch.float64, device=dev)
     dev_qd = torch.empty_like(dev_pd)
-    ks = max(1, min(args.steps, args.e2e_steps))
+    ks = ke
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(ks):
-        sidx = 1 + (k % (nsnap - 1))
+        sidx = args.warmup + args.steps + 1 + k  # the load sequence goes on from the timed steps
         dev_pd.copy_(host_pd[sidx], non_blocking=True)
         dev_qd.copy_(host_qd[sidx], non_blocking=True)
         step(k, dev_pd, dev_qd)
