@@ -556,6 +556,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   }
   TRY(dupload(c, &c->pd_nom, h.pd));
   TRY(dupload(c, &c->qd_nom, h.qd));
+  TRY(dupload(c, &c->split_ctr, std::vector<int>(2 + kSplitMaxSm, 0)));
   // workspaces
   TRY(dalloc(c, &c->LU, nnz));
   TRY(dalloc(c, &c->T, nnz));

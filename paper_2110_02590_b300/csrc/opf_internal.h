@@ -116,6 +116,7 @@ constexpr int kDenseLuSmem = 200 * 1024;
 
 // Dynamic shared memory of the HVP tile kernels (bytes; opted in at load).
 constexpr int HVP_DYN_SMEM = 56 * 1024;
+constexpr int kSplitMaxSm = 1024;  // SM ids the split launch counts CTAs for
 size_t hvp_smem_bytes(const HvpArgs& a, int C);
 int hvp_smem_budget(int C);  // dynamic shared memory a tile of width C may use (<= HVP_DYN_SMEM)
 void setup_hvp_smem();
@@ -412,6 +413,7 @@ struct opf_ctx {
   // C / 2 for the rest; colmap_split[k] holds n1 x C then n2 x C/2 columns
   int* colmap_split[6] = {};
   int split_n1[6] = {}, split_n2[6] = {};
+  int* split_ctr = nullptr;  // the split launch's tile queues and per-SM CTA counts (2 + kSplitMaxSm)
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
   double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...

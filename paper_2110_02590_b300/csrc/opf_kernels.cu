@@ -1500,15 +1500,35 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
     hvp_tile<C>(a, Z, tile);
 }
 
-// Split tiling: CTAs [0, n1) run tiles of width C with a1, the others tiles of
-// width C / 2 with a2 (each part with its own column map and workspace).
+// Split tiling: a1.ntiles tiles of width C and a2.ntiles of width C / 2 (each
+// part with its own column map and workspace), one per CTA, all CTAs resident.
+// The hardware's CTA-to-SM placement is not round robin (some SMs were given
+// three of the first CTAs), so a CTA takes its tile by its rank on its SM: the
+// first per_sm CTAs of an SM take the next wide tile, the others the next
+// narrow one (each queue heaviest first; an empty queue sends the CTA to the
+// other).  ctr: [0] wide queue, [1] narrow queue, [2 + smid] CTAs seen per SM;
+// zero before the launch.
 template <int C, int NT>
-__global__ void __launch_bounds__(NT) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int n1) {
-  if ((int)blockIdx.x < n1) {
-    hvp_tile<C>(a1, a1.scratch + a1.stride * blockIdx.x, blockIdx.x);
+__global__ void __launch_bounds__(NT) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int per_sm, int* ctr) {
+  __shared__ int s_pick;
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int rank = smid < (unsigned)kSplitMaxSm ? atomicAdd(ctr + 2 + smid, 1) : 0;
+    int kind = rank < per_sm ? 0 : 1;
+    int t = atomicAdd(ctr + kind, 1);
+    if (t >= (kind == 0 ? a1.ntiles : a2.ntiles)) {
+      kind ^= 1;
+      t = atomicAdd(ctr + kind, 1);
+    }
+    s_pick = (t << 1) | kind;
+  }
+  __syncthreads();
+  const int t = s_pick >> 1;
+  if ((s_pick & 1) == 0) {
+    if (t < a1.ntiles) hvp_tile<C>(a1, a1.scratch + a1.stride * t, t);
   } else {
-    const int t = blockIdx.x - n1;
-    hvp_tile<C / 2>(a2, a2.scratch + a2.stride * t, t);
+    if (t < a2.ntiles) hvp_tile<C / 2>(a2, a2.scratch + a2.stride * t, t);
   }
 }
 
@@ -1816,7 +1836,9 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   a2.ntiles = n2;
   a2.scratch = c->scratch + a1.stride * (size_t)n1;
   const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
-  hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, n1);
+  const int per_sm = std::max(1, n1 / c->sm_count);
+  cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (2 + kSplitMaxSm), c->stream);
+  hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, per_sm, c->split_ctr);
   c->launches++;
 }
 
