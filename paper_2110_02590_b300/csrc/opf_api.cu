@@ -338,6 +338,14 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, pvv)); n.pvv = ip;
   TRY(dupload(c, &ip, h.adj_ptr)); n.adj_ptr = ip;
   TRY(dupload(c, &ip, h.adj)); n.adj = ip;
+  {
+    std::vector<int> order(nb);
+    for (int i = 0; i < nb; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return h.adj_ptr[a + 1] - h.adj_ptr[a] > h.adj_ptr[b + 1] - h.adj_ptr[b];
+    });
+    TRY(dupload(c, &ip, order)); n.bus_by_deg = ip;
+  }
   TRY(dupload(c, &ip, gn_of)); n.gn_of = ip;
   TRY(dupload(c, &ip, gn_bus)); n.gn_bus = ip;
   TRY(dupload(c, &dptr, h.c2)); n.c2 = dptr;

@@ -59,6 +59,7 @@ struct DevNet {
   const int *type, *gen_at, *pvpos, *pqpos, *xth, *xv, *uv, *up;
   const int *pth, *pvv;            // pivot-order index of theta / v of each bus (-1)
   const int *adj_ptr, *adj;
+  const int* bus_by_deg;           // [nb] buses by descending degree (ties: ascending id)
   const int* gn_of;                // per bus: index among ref + PV buses (-1)
   const int* gn_bus;               // [ngn]
   const double *c2, *c1;

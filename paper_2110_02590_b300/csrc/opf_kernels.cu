@@ -1399,9 +1399,10 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     __syncthreads();
     // (4) y = (grad^2 l) (z; w) per bus; R = -y_x, H[u rows] = y_u.  The
     // own-variable coefficients are summed per bus (busS), so an incident
-    // branch adds only its other end's terms.
+    // branch adds only its other end's terms.  Buses are taken by descending
+    // degree, so the buses sharing a warp loop over the same number of entries.
     for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
-      const int i = it / C, c = it % C, j = s_col[c];
+      const int i = n.bus_by_deg[it / C], c = it % C, j = s_col[c];
       const int4 bi = n.busrec[i];
       const double4_32a S = reinterpret_cast<const double4_32a*>(a.busS)[i];
       const double vi = dslot<C>(Z, bi.x, c, j), ti = bi.y >= 0 ? Z[(size_t)bi.y * C + c] : 0.0;
