@@ -348,6 +348,13 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   }
   TRY(dupload(c, &ip, gn_of)); n.gn_of = ip;
   TRY(dupload(c, &ip, gn_bus)); n.gn_bus = ip;
+  {
+    std::vector<int> order(gn_bus.size());
+    for (size_t g = 0; g < order.size(); g++) order[g] = (int)g;
+    auto deg = [&](int g) { return h.adj_ptr[gn_bus[g] + 1] - h.adj_ptr[gn_bus[g]]; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg(a) > deg(b); });
+    TRY(dupload(c, &ip, order)); n.gn_by_deg = ip;
+  }
   TRY(dupload(c, &dptr, h.c2)); n.c2 = dptr;
   TRY(dupload(c, &dptr, h.c1)); n.c1 = dptr;
   TRY(dupload(c, &c->c0, h.c0));

@@ -62,6 +62,7 @@ struct DevNet {
   const int* bus_by_deg;           // [nb] buses by descending degree (ties: ascending id)
   const int* gn_of;                // per bus: index among ref + PV buses (-1)
   const int* gn_bus;               // [ngn]
+  const int* gn_by_deg;            // [ngn] indices into gn_bus by descending degree of the bus
   const double *c2, *c1;
   // LU pattern
   const int *rp, *ci, *dp, *perm;

@@ -1372,8 +1372,8 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     // (3) directional derivatives of Q (slack and PV) and P (slack) for the
     // Gauss-Newton terms, stored pre-multiplied by their weights kQ, kP.  The
     // own-variable parts are the per-bus sums dQ_k/dv_k, dQ_k/dtheta_k, ...
-    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
-      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = s_col[c];
+    for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {  // buses by descending degree
+      const int gi = n.gn_by_deg[it / C], c = it % C, k = n.gn_bus[gi], j = s_col[c];
       const int4 bk = n.busrec[k];
       const double vk = dslot<C>(Z, bk.x, c, j), tk = bk.y >= 0 ? Z[(size_t)bk.y * C + c] : 0.0;
       const bool slack = (k == n.ref);
@@ -1457,9 +1457,9 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     // (5)-(6) second second-order adjoint: U^T then L^T sweeps
     sweep<C, true, true>(n, a.T, a.invdiag, R, nullptr, s_tb);
     sweep<C, false, false>(n, a.T, a.invdiag, R, nullptr, s_tb);
-    // (7) H[:, tile] += G_u^T Psi
+    // (7) H[:, tile] += G_u^T Psi (buses by descending degree)
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
-      const int gi = it / C, c = it % C, k = n.gn_bus[gi], j = s_col[c];
+      const int gi = n.gn_by_deg[it / C], c = it % C, k = n.gn_bus[gi], j = s_col[c];
       if (j < 0) continue;
       double gv = 0.0;
       const int q1 = n.adj_ptr[k + 1];
