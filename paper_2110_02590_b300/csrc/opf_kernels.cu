@@ -1156,6 +1156,44 @@ __device__ __forceinline__ void adj_dirs4(const DevNet& n, const double* Z, int 
   }
 }
 
+// N incident branch ends qb .. qb + N - 1 of a bus in the second-order gather:
+// the other ends' terms of y = (grad^2 l)(z; w) (see hvp_tile, phase 4).  The
+// callers split a bus's ends into groups of 4, 2 and 1, so no FP64 instruction
+// is issued for an absent end.
+template <int C, int N>
+__device__ __forceinline__ void gather_ends(const DevNet& n, const double* Z, const double* __restrict__ E,
+                                            const double* QD, const double* PD, int qb, int c, int j,
+                                            double& yv, double& yt) {
+  int4 ar[N];
+  double vo[N], to[N];
+#pragma unroll
+  for (int u = 0; u < N; u++) ar[u] = n.adjrec[qb + u];
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    vo[u] = dslot<C>(Z, ar[u].x, c, j);
+    to[u] = ar[u].y >= 0 ? Z[(size_t)ar[u].y * C + c] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    const double2* e2 = reinterpret_cast<const double2*>(E + (size_t)(qb + u) * ADJ_W);
+    const double2 e01 = e2[0], e23 = e2[1];  // (VO, VT), (TO, TT)
+    yv = fma(e01.x, vo[u], fma(-e01.y, to[u], yv));  // chained FMAs, no DMUL/DADD
+    yt = fma(e23.x, vo[u], fma(-e23.y, to[u], yt));
+    if (ar[u].z >= 0) {  // Gauss-Newton terms of the other end's Q (and P at the slack)
+      const double w = QD[(size_t)ar[u].z * C + c];
+      const double2 e45 = e2[2];  // (QOV, QOT)
+      yv += w * e45.x;
+      yt += w * e45.y;
+      if (ar[u].w) {
+        const double w2 = PD[c];
+        const double2 e67 = e2[3];  // (POV, POT)
+        yv += w2 * e67.x;
+        yt += w2 * e67.y;
+      }
+    }
+  }
+}
+
 // One tile of C Hessian columns on one CTA: B = -G_u W, Z = G_x^{-1} B,
 // second-order terms, Psi = G_x^{-T} R, H[:, tile] = T + G_u^T Psi (Prop. 2).
 // Z is the CTA's workspace (2 n_x C + n_ctrl C + C doubles).
@@ -1408,32 +1446,13 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       const double vi = dslot<C>(Z, bi.x, c, j), ti = bi.y >= 0 ? Z[(size_t)bi.y * C + c] : 0.0;
       double yv = S.x * vi + S.y * ti, yt = S.y * vi + S.z * ti;
       const int q1 = n.adj_ptr[i + 1];
-      for (int qb = n.adj_ptr[i]; qb < q1; qb += 4) {
-        int4 ar[4];
-        double vo[4], to[4];
-        adj_dirs4<C>(n, Z, qb, q1, c, j, ar, vo, to);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (qb + u < q1) {
-            const double2* e2 = reinterpret_cast<const double2*>(E + (size_t)(qb + u) * ADJ_W);
-            const double2 e01 = e2[0], e23 = e2[1];  // (VO, VT), (TO, TT)
-            yv = fma(e01.x, vo[u], fma(-e01.y, to[u], yv));  // chained FMAs, no DMUL/DADD
-            yt = fma(e23.x, vo[u], fma(-e23.y, to[u], yt));
-            if (ar[u].z >= 0) {  // Gauss-Newton terms of the other end's Q (and P at the slack)
-              const double w = QD[(size_t)ar[u].z * C + c];
-              const double2 e45 = e2[2];  // (QOV, QOT)
-              yv += w * e45.x;
-              yt += w * e45.y;
-              if (ar[u].w) {
-                const double w2 = PD[c];
-                const double2 e67 = e2[3];  // (POV, POT)
-                yv += w2 * e67.x;
-                yt += w2 * e67.y;
-              }
-            }
-          }
-        }
+      int qb = n.adj_ptr[i];
+      for (; qb + 4 <= q1; qb += 4) gather_ends<C, 4>(n, Z, E, QD, PD, qb, c, j, yv, yt);
+      if (qb + 2 <= q1) {
+        gather_ends<C, 2>(n, Z, E, QD, PD, qb, c, j, yv, yt);
+        qb += 2;
       }
+      if (qb < q1) gather_ends<C, 1>(n, Z, E, QD, PD, qb, c, j, yv, yt);
       if (bi.z >= 0) {  // own injections: the gradients dQ_i, dP_i w.r.t. (v_i, theta_i) are per-bus sums
         const double w = QD[(size_t)bi.z * C + c];
         yv += w * bw[4 * nb + i];
