@@ -1142,20 +1142,6 @@ __device__ __forceinline__ double dslot(const double* Z, int z, int c, int j) {
   return z >= 0 ? Z[(size_t)z * C + c] : ((-2 - z) == j ? 1.0 : 0.0);
 }
 
-// The other ends' direction values of up to four adjacency entries qb.. of a
-// bus (entries at or past q1 read as zero), all loads issued together.
-template <int C>
-__device__ __forceinline__ void adj_dirs4(const DevNet& n, const double* Z, int qb, int q1, int c, int j,
-                                          int4 (&ar)[4], double (&vo)[4], double (&to)[4]) {
-#pragma unroll
-  for (int u = 0; u < 4; u++) ar[u] = (qb + u < q1) ? n.adjrec[qb + u] : make_int4(-1, -1, -1, 0);
-#pragma unroll
-  for (int u = 0; u < 4; u++) {
-    vo[u] = dslot<C>(Z, ar[u].x, c, j);
-    to[u] = ar[u].y >= 0 ? Z[(size_t)ar[u].y * C + c] : 0.0;
-  }
-}
-
 // N incident branch ends qb .. qb + N - 1 of a bus in the second-order gather:
 // the other ends' terms of y = (grad^2 l)(z; w) (see hvp_tile, phase 4).  The
 // callers split a bus's ends into groups of 4, 2 and 1, so no FP64 instruction
@@ -1191,6 +1177,48 @@ __device__ __forceinline__ void gather_ends(const DevNet& n, const double* Z, co
         yt += w2 * e67.y;
       }
     }
+  }
+}
+
+// N ends of a control bus for its Q (and, at the slack, P) directional
+// derivatives (hvp_tile, phase 3); groups of 4, 2 and 1 as in gather_ends.
+template <int C, int N>
+__device__ __forceinline__ void qd_ends(const DevNet& n, const double* Z, const double* __restrict__ E, int qb,
+                                        int c, int j, bool slack, double& qd, double& pdr) {
+  int4 ar[N];
+  double vo[N], to[N];
+#pragma unroll
+  for (int u = 0; u < N; u++) ar[u] = n.adjrec[qb + u];
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    vo[u] = dslot<C>(Z, ar[u].x, c, j);
+    to[u] = ar[u].y >= 0 ? Z[(size_t)ar[u].y * C + c] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    const double* e = E + (size_t)(qb + u) * ADJ_W;
+    qd = fma(e[E_QSO], vo[u], fma(-e[E_QST], to[u], qd));  // chained FMAs, no DMUL/DADD
+    if (slack) pdr = fma(e[E_PSO], vo[u], fma(-e[E_PST], to[u], pdr));
+  }
+}
+
+// N ends of a control bus in H[:, tile] += G_u^T Psi (hvp_tile, phase 7).
+template <int C, int N>
+__device__ __forceinline__ void gu_ends(const DevNet& n, const double* R, const double* __restrict__ E, int qb,
+                                        int c, double& gv) {
+  int4 ar[N];
+  double pt[N], pv[N];
+#pragma unroll
+  for (int u = 0; u < N; u++) ar[u] = n.adjrec[qb + u];
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    pt[u] = ar[u].y >= 0 ? R[(size_t)ar[u].y * C + c] : 0.0;
+    pv[u] = ar[u].x >= 0 ? R[(size_t)ar[u].x * C + c] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    const double* e = E + (size_t)(qb + u) * ADJ_W;
+    gv = fma(pt[u], e[E_POV], fma(pv[u], e[E_QOV], gv));
   }
 }
 
@@ -1418,19 +1446,13 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       double qd = bw[4 * nb + k] * vk + bw[5 * nb + k] * tk, pdr = 0.0;
       if (slack) pdr = bw[6 * nb + k] * vk + bw[7 * nb + k] * tk;
       const int q1 = n.adj_ptr[k + 1];
-      for (int qb = n.adj_ptr[k]; qb < q1; qb += 4) {
-        int4 ar[4];
-        double vo[4], to[4];
-        adj_dirs4<C>(n, Z, qb, q1, c, j, ar, vo, to);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (qb + u < q1) {
-            const double* e = E + (size_t)(qb + u) * ADJ_W;
-            qd = fma(e[E_QSO], vo[u], fma(-e[E_QST], to[u], qd));  // chained FMAs, no DMUL/DADD
-            if (slack) pdr = fma(e[E_PSO], vo[u], fma(-e[E_PST], to[u], pdr));
-          }
-        }
+      int qb = n.adj_ptr[k];
+      for (; qb + 4 <= q1; qb += 4) qd_ends<C, 4>(n, Z, E, qb, c, j, slack, qd, pdr);
+      if (qb + 2 <= q1) {
+        qd_ends<C, 2>(n, Z, E, qb, c, j, slack, qd, pdr);
+        qb += 2;
       }
+      if (qb < q1) qd_ends<C, 1>(n, Z, E, qb, c, j, slack, qd, pdr);
       QD[(size_t)gi * C + c] = bw[k] * qd;
       if (slack) PD[c] = bw[nb + k] * pdr;
     }
@@ -1482,24 +1504,13 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       if (j < 0) continue;
       double gv = 0.0;
       const int q1 = n.adj_ptr[k + 1];
-      for (int qb = n.adj_ptr[k]; qb < q1; qb += 4) {
-        int4 ar[4];
-        double pt[4], pv[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) ar[u] = (qb + u < q1) ? n.adjrec[qb + u] : make_int4(-1, -1, -1, 0);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          pt[u] = ar[u].y >= 0 ? R[(size_t)ar[u].y * C + c] : 0.0;
-          pv[u] = ar[u].x >= 0 ? R[(size_t)ar[u].x * C + c] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          if (qb + u < q1) {
-            const double* e = E + (size_t)(qb + u) * ADJ_W;
-            gv = fma(pt[u], e[E_POV], fma(pv[u], e[E_QOV], gv));
-          }
-        }
+      int qb = n.adj_ptr[k];
+      for (; qb + 4 <= q1; qb += 4) gu_ends<C, 4>(n, R, E, qb, c, gv);
+      if (qb + 2 <= q1) {
+        gu_ends<C, 2>(n, R, E, qb, c, gv);
+        qb += 2;
       }
+      if (qb < q1) gu_ends<C, 1>(n, R, E, qb, c, gv);
       double* Hc = a.H + (size_t)j * nu;
       const int4 bk = n.busrec[k];
       if (bk.w >= 0) {  // PV bus
