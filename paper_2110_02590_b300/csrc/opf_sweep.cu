@@ -50,8 +50,7 @@ struct Built {
 
 // Lanes of a chunk.  Record r gets g_r lanes, the power of two that gives
 // each lane at most k of its entries (at most 32); the groups are packed into
-// warp tasks of 32 lanes in order (records are sorted by length, so each group
-// sits at a multiple of its size).  The SM's FP64 unit takes one warp
+// warp tasks of 32 lanes in order, each at a multiple of its size.  The SM's FP64 unit takes one warp
 // instruction per ~20 cycles whatever the number of active lanes, and one warp
 // issues at most one per ~67 cycles, so the model counts warp FP64
 // instructions: per task the most entries of a lane (twice when the task has a
@@ -83,6 +82,7 @@ std::vector<int> plan_lanes(const std::vector<Rec>& L, size_t i, int nrec) {
       int lg = 0;
       while (lg < 5 && (1 << lg) * k < len) lg++;
       const int g = 1 << lg;
+      used = (used + g - 1) / g * g;  // a group sits at a multiple of its size (the shuffle reduction)
       if (used + g > 32) {
         close();
         map.resize(map.size() + 32, -1);
