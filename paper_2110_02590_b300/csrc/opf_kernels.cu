@@ -1461,14 +1461,34 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     // own-variable coefficients are summed per bus (busS), so an incident
     // branch adds only its other end's terms.  Buses are taken by descending
     // degree, so the buses sharing a warp loop over the same number of entries.
-    for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
-      const int i = n.bus_by_deg[it / C], c = it % C, j = s_col[c];
-      const int4 bi = n.busrec[i];
-      const double4_32a S = reinterpret_cast<const double4_32a*>(a.busS)[i];
+    // The bus's static records (its slots, coefficients, entry range) are read
+    // one item ahead, so an item waits for the slab only.
+    const int nitem = nb * C;
+    int i_n = 0, q0_n = 0, q1_n = 0;
+    int4 bi_n = make_int4(-1, -1, -1, -1);
+    double4_32a S_n = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if ((int)threadIdx.x < nitem) {
+      i_n = n.bus_by_deg[threadIdx.x / C];
+      bi_n = n.busrec[i_n];
+      S_n = reinterpret_cast<const double4_32a*>(a.busS)[i_n];
+      q0_n = n.adj_ptr[i_n];
+      q1_n = n.adj_ptr[i_n + 1];
+    }
+    for (int it = threadIdx.x; it < nitem; it += blockDim.x) {
+      const int i = i_n, c = it % C, j = s_col[c];
+      const int4 bi = bi_n;
+      const double4_32a S = S_n;
+      const int q1 = q1_n;
+      int qb = q0_n;
+      if (it + (int)blockDim.x < nitem) {
+        i_n = n.bus_by_deg[(it + blockDim.x) / C];
+        bi_n = n.busrec[i_n];
+        S_n = reinterpret_cast<const double4_32a*>(a.busS)[i_n];
+        q0_n = n.adj_ptr[i_n];
+        q1_n = n.adj_ptr[i_n + 1];
+      }
       const double vi = dslot<C>(Z, bi.x, c, j), ti = bi.y >= 0 ? Z[(size_t)bi.y * C + c] : 0.0;
       double yv = S.x * vi + S.y * ti, yt = S.y * vi + S.z * ti;
-      const int q1 = n.adj_ptr[i + 1];
-      int qb = n.adj_ptr[i];
       for (; qb + 4 <= q1; qb += 4) gather_ends<C, 4>(n, Z, E, QD, PD, qb, c, j, yv, yt);
       if (qb + 2 <= q1) {
         gather_ends<C, 2>(n, Z, E, QD, PD, qb, c, j, yv, yt);
