@@ -1560,7 +1560,7 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
 // other).  ctr: [0] wide queue, [1] narrow queue, [2 + smid] CTAs seen per SM;
 // zero before the launch.
 template <int C, int NT>
-__global__ void __launch_bounds__(NT) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int per_sm, int* ctr) {
+__global__ void __launch_bounds__(NT, 3) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int per_sm, int* ctr) {
   __shared__ int s_pick;
   if (threadIdx.x == 0) {
     unsigned smid;
