@@ -42,7 +42,7 @@ UNIT = "HVP/s"
 FP64_PEAK_TFLOPS = 1.25        # B300 FP64 (vector and tensor) nominal rate of the pool's recipe
 # DRAM bytes (read + write) of one hvp_split_kernel<8, 256> launch on the 9.2k grid,
 # from the ncu capture summarised in profiles/hvp_split_kernel_large9200.md
-HVP_SPLIT_TRAFFIC_9200 = 8.13e9
+HVP_SPLIT_TRAFFIC_9200 = 8.10e9
 HBM_FALLBACK_GBS = 6400.0
 
 
