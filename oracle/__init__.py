@@ -9,7 +9,9 @@ names of the synthetic generator's ``Network`` (duck typing: this package
 imports nothing from the library).
 
 Functions without an independent pin are marked in their docstring
-("parity unpinned"); at present every exported function has one.
+("parity unpinned"); at present every exported function has one.  The
+Hessian's columns are shared out over OpenMP threads (OMP_NUM_THREADS; the
+arithmetic of a column does not depend on the thread count).
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable flags: the .so may run on another host)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "opf_oracle.h"))):
-        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -59,7 +61,6 @@ def _load():
         lib.orc_reduced_jac_prod.argtypes = [C.c_void_p] + [_dp] * 8
         lib.orc_bruteforce.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.orc_cholesky_solve.argtypes = [C.c_int, _dp, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -221,14 +222,3 @@ class OracleNet:
         _check(lib.orc_bruteforce(self.h, _pd(_d(x)), _pd(_d(u)), _pd(pd), _pd(qd), sf, rho, _pd(sc), _pd(y),
                                   _pd(s), _pd(_d(omega)), _pd(H), _pd(J), _pd(gu)), "bruteforce")
         return dict(H=H.T.copy(), J=J.T.copy(), grad_u=gu)
-
-
-def cholesky_solve(A, b):
-    lib = _load()
-    A = np.asfortranarray(A, dtype=np.float64)
-    b = _d(b)
-    x = np.zeros_like(b)
-    n = A.shape[0]
-    Ac = np.ascontiguousarray(A.T.reshape(-1))  # column-major storage
-    _check(lib.orc_cholesky_solve(n, _pd(Ac), _pd(b), _pd(x)), "cholesky")
-    return x

@@ -1086,21 +1086,32 @@ int orc_reduced_hessian(orc_net* n, const double* x, const double* u, const doub
     return rc;
   }
   int nx = n->nx, nu = n->nu;
-  csr_t K = hess_l(n, &S, u, pd, sigma_f, rho, sigma_c, omega);
-  double* work = (double*)xcalloc((size_t)(4 * nx + 2 * (nx + nu)), sizeof(double));
-  double* w = (double*)xcalloc((size_t)nu, sizeof(double));
   for (int c = 0; c < ncols; c++) {
     int j = cols ? cols[c] : c;
-    if (j < 0 || j >= nu) {
-      rc = ORC_EINVAL;
-      break;
-    }
-    memset(w, 0, sizeof(double) * (size_t)nu);
-    w[j] = 1.0;
-    hvp_one(n, &S, &K, w, H + (size_t)c * (size_t)nu, work);
+    if (j < 0 || j >= nu) rc = ORC_EINVAL;
   }
-  free(work);
-  free(w);
+  if (rc) {
+    state_free(&S);
+    return rc;
+  }
+  csr_t K = hess_l(n, &S, u, pd, sigma_f, rho, sigma_c, omega);
+  /* The columns are independent HVPs with the same factors (Sec. III-C); with
+   * OpenMP (OMP_NUM_THREADS) they are shared out over threads, each with its own
+   * work vectors; the arithmetic of a column does not depend on the thread. */
+#pragma omp parallel
+  {
+    double* work = (double*)xcalloc((size_t)(4 * nx + 2 * (nx + nu)), sizeof(double));
+    double* w = (double*)xcalloc((size_t)nu, sizeof(double));
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < ncols; c++) {
+      int j = cols ? cols[c] : c;
+      memset(w, 0, sizeof(double) * (size_t)nu);
+      w[j] = 1.0;
+      hvp_one(n, &S, &K, w, H + (size_t)c * (size_t)nu, work);
+    }
+    free(work);
+    free(w);
+  }
   csr_free(&K);
   state_free(&S);
   return rc;
@@ -1484,37 +1495,4 @@ int orc_bruteforce(orc_net* n, const double* x, const double* u, const double* p
   free(Smat);
   free(K);
   return rc;
-}
-
-/* ------------------------------------------------------------ dense Cholesky */
-
-int orc_cholesky_solve(int n, const double* A, const double* b, double* x) {
-  double* L = (double*)xcalloc((size_t)n * n, sizeof(double));
-  memcpy(L, A, sizeof(double) * (size_t)n * n);
-  for (int j = 0; j < n; j++) { /* column-major, lower */
-    double d = L[(size_t)j * n + j];
-    for (int k = 0; k < j; k++) d -= L[(size_t)k * n + j] * L[(size_t)k * n + j];
-    if (!(d > 0.0)) {
-      free(L);
-      return ORC_ENOTPD;
-    }
-    d = sqrt(d);
-    L[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; i++) {
-      double sacc = L[(size_t)j * n + i];
-      for (int k = 0; k < j; k++) sacc -= L[(size_t)k * n + i] * L[(size_t)k * n + j];
-      L[(size_t)j * n + i] = sacc / d;
-    }
-  }
-  for (int i = 0; i < n; i++) x[i] = b[i];
-  for (int i = 0; i < n; i++) {
-    for (int k = 0; k < i; k++) x[i] -= L[(size_t)k * n + i] * x[k];
-    x[i] /= L[(size_t)i * n + i];
-  }
-  for (int i = n - 1; i >= 0; i--) {
-    for (int k = i + 1; k < n; k++) x[i] -= L[(size_t)i * n + k] * x[k];
-    x[i] /= L[(size_t)i * n + i];
-  }
-  free(L);
-  return ORC_OK;
 }

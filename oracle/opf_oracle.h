@@ -81,9 +81,6 @@ int orc_bruteforce(orc_net* net, const double* x, const double* u, const double*
                    const double* y, const double* s, const double* omega, double* H, double* J,
                    double* grad_u);
 
-/* Dense symmetric positive-definite solve by Cholesky (in place on a copy). */
-int orc_cholesky_solve(int n, const double* A, const double* b, double* x);
-
 #ifdef __cplusplus
 }
 #endif
