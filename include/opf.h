@@ -47,7 +47,7 @@ typedef enum {
   OPF_ESINGULAR = 5,  /* a zero or non-finite pivot in the LU refactorisation */
   OPF_ENOTPD = 6,     /* dense Cholesky failed after the inertia corrections */
   OPF_ESTATE = 7,     /* gradient/Hessian requested without a converged power flow */
-  OPF_ETIMEOUT = 8    /* a bounded device-side wait gave up */
+  OPF_ETIMEOUT = 8    /* a bounded device-side wait gave up (opf_set_wait_limit) */
 } opf_status;
 
 typedef struct opf_ctx opf_ctx;
@@ -172,19 +172,31 @@ typedef struct {
   int block_k;   /* Hessian columns per CTA tile: 1, 2, 4, 8, 16 or 32
                     (0 = the context's autotuned choice, else 8) */
   int grid;      /* CTAs (0 = one per tile, capped at the resident CTAs per SM x SMs) */
-  int plain;     /* 1: one direction per launch, launches in sequence (k = 1 baseline) */
+  int plain;     /* 1: the k = 1 baseline: one direction per launch sequence, each column by
+                    device-wide launches around two streamed single-RHS solves (block_k,
+                    grid and threads are ignored; info->launches counts the kernels) */
   int col_begin; /* first Hessian column to compute (0) */
   int col_count; /* number of columns (0 = through n_u); the others of H are left untouched */
   int threads;   /* threads per tile CTA: 128, 256 or 512 (0 = 256) */
   int reuse_first_order; /* 1: the context's first-order quantities (c, phi', omega, lambda)
                             were just evaluated with these same parameters by
                             opf_reduced_gradient: skip re-evaluating them */
+  int asymmetry; /* 1: report ||H - H^T||_F / ||H||_F of a full Hessian in info (one more
+                    kernel after the timed region) */
+  int phase_profile; /* 1: the tiles record the global timer at their phase boundaries and
+                        info->phase_ms apportions the HVP time to the phases (diagnostics) */
 } opf_hess_opts;
 
 typedef struct {
   int block_k, grid, tiles, launches;
   float ms_total;  /* device time of the call (CUDA events on the context stream) */
   float ms_hvp;    /* device time of the HVP phase alone */
+  double asymmetry; /* ||H - H^T||_F / ||H||_F when requested for a full Hessian, else -1
+                       (H is assembled column block by column block and not symmetrised) */
+  float phase_ms[5]; /* with phase_profile: ms_hvp times each phase's share of the tiles'
+                        summed durations -- (1) pruned L solve of Z, (2) U sweep of Z,
+                        (3)-(4) second-order terms, (5)-(6) U^T and L^T sweeps of Psi,
+                        (7) assembly of H; else 0 */
 } opf_hess_info;
 
 /*
@@ -234,24 +246,30 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
 
 /*
  * opf_reduced_hessian_noalloc: the same reduced Hessian as opf_reduced_hessian
- * (same kernels, same options and outputs), for callers that must not allocate
- * device memory during the call -- a real-time tracking loop that cannot stall
- * on the allocator (cudaMalloc may synchronise the device), a caller inside
- * stream capture, or a process with a device-memory budget fixed at start-up.
+ * (same tile kernel and output), for callers that must not allocate device
+ * memory during the call: a real-time tracking loop that cannot stall on the
+ * allocator (cudaMalloc may synchronise the device and its latency is
+ * unbounded), or a process whose device-memory budget is fixed at start-up.
  * The paper has no counterpart: this is an interface choice of this library.
+ *   - Options: block_k (0 = 8; the autotuned choice is not used), grid and the
+ *     column range; plain, threads and reuse_first_order must be 0
+ *     (OPF_EINVAL otherwise).  The first-order quantities are always evaluated.
  *   - Workspace: a fixed array of OPF_NOALLOC_SCRATCH_BYTES (32 MiB) in device
  *     memory, which every GPU that loads the library holds until the process
  *     exits.  No call allocates or frees anything.
  *   - Limit: one tile needs (2 n_x + n_ctrl + 1) block_k doubles, n_ctrl =
  *     n_pv + 1, rounded up to 32; a network/block_k whose tile does not fit is
- *     rejected with OPF_EINVAL and a message.  As many tiles run at once as fit
- *     (fewer than opf_reduced_hessian may use, so it can be slower).
+ *     rejected with OPF_EINVAL and a message (checked before the state).  The
+ *     grid is capped at the tiles that fit at once (32 MiB / tile bytes), and
+ *     its CTAs loop over the remaining tiles, so it can be slower than
+ *     opf_reduced_hessian.
  *   - The first call on a device looks up the array's device address (once per
- *     device); make that first call before any stream capture.
+ *     device, with that device current); make that first call before any
+ *     stream capture.
  *   - All calls share the one array and it keeps the last call's contents; the
  *     kernel clears what it needs per tile.  Calls that overlap on the GPU (two
  *     streams, two contexts, two threads) race on it: serialise them.
- * Errors: as opf_reduced_hessian, plus OPF_EINVAL for the size limit.
+ * Errors: OPF_EINVAL (arguments, size limit), OPF_ESTATE, OPF_ESINGULAR, OPF_ECUDA.
  */
 #define OPF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 opf_status opf_reduced_hessian_noalloc(opf_ctx* ctx, const opf_al_params* p,
@@ -312,6 +330,141 @@ typedef struct {
 opf_status opf_al_step(opf_ctx* ctx, const opf_al_params* p, opf_al_state* st,
                        const opf_step_opts* opts, opf_step_info* info, double* du_out,
                        double* ds_out);
+
+/*
+ * opf_al_solve: the static OPF by the augmented-Lagrangian method (Sec. IV-B
+ * "Static OPF algorithm", the scaled AL of Sec. IV-A).  Outer iteration k
+ * solves the AL subproblem for fixed rho and y by barrier steps (opf_al_step),
+ * warm-started from the previous primal-dual point, then updates y.  The paper
+ * leaves the IPM's internals and the AL schedule unstated; the readings:
+ *   E_mu = max(|grad_u L - zl_u + zu_u|_inf, |grad_s L - zl_s + zu_s|_inf,
+ *              |(w - w_lo) zl - mu|_inf, |(w_hi - w) zu - mu|_inf)   (w = (u, s)),
+ *   E_0 = the same at mu = 0 (the subproblem's own KKT error);
+ *   inner loop: evaluate the gradient at the current point; stop when
+ *     E_0 <= omega_k = max(eta_dual, 10^-(k+1)) or after max_inner steps; when
+ *     E_mu <= 10 mu, mu <- max(eta_dual / 10, min(0.2 mu, mu^1.5)); then one
+ *     opf_al_step whose inertia correction starts at delta/10 of the previous
+ *     step's delta when that was at least 1e-7, else at 0;
+ *   outer update: eta_p = |sigma_c (c - s)|_inf; stop when eta_p <= eta_primal
+ *     and E_0 <= eta_dual; else y <- y + rho sigma_c (c - s), and rho <-
+ *     min(10 rho, rho_max) when eta_p fell by less than a factor 4.
+ * p: sigma_f, rho (the initial penalty), sigma_c (its y, s and omega are
+ * ignored); y [m] (device) the multipliers, updated in place; st the primal-
+ * dual state and bounds as for opf_al_step (u, s, duals, x and mu updated in
+ * place).  Requires a converged opf_powerflow at st->u.  history (host, may be
+ * NULL): 8 doubles per outer iteration {steps, mu, rho, eta_p, E_0, F, delta,
+ * 0}.  Errors: those of opf_al_step (the state is then the last accepted
+ * iterate), OPF_EINVAL, OPF_ESTATE, OPF_ENOMEM.
+ */
+typedef struct {
+  int max_outer;      /* outer iterations (0 = 20) */
+  int max_inner;      /* reduced-Newton steps per subproblem (0 = 10) */
+  double eta_primal;  /* stopping tolerance on |sigma_c (c - s)|_inf (0 = 1e-5) */
+  double eta_dual;    /* stopping tolerance on E_0 (0 = 1e-4) */
+  double rho_max;     /* penalty cap (0 = 1e6) */
+  int block_k;        /* Hessian tile width of the steps (0 = autotuned, else 8) */
+} opf_al_opts;
+
+typedef struct {
+  int outer, steps, converged;
+  double primal_inf, dual_inf, F, rho, mu;
+  float ms_total;  /* device time of the whole loop */
+} opf_al_info;
+
+opf_status opf_al_solve(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_state* st,
+                        const opf_al_opts* opts, opf_al_info* info, double* history);
+
+/*
+ * opf_tracking_update: one real-time OPF update (Sec. IV-C "Real-time optimal
+ * power flow"), after opf_powerflow at the new loads and the current controls:
+ *   1. g_t = grad L_rho,t(w_t; y) and the constant Hessian H_t of eq.
+ *      hessian_auglag (scaled, Sec. IV-A) at w_t = (u_t, s_t);
+ *   2. the bounded QP of eq. qp_rto, min g_t^T d + 1/2 d^T (H_t + delta I_u) d
+ *      over w_lo <= w_t + d <= w_hi, solved by a primal-dual interior-point
+ *      method whose Newton systems go through the Schur complement of Prop. 3
+ *      (S = H(omega) + Sigma_u + delta I, H(omega) from opf_reduced_hessian at the
+ *      fixed point w_t with the iteration's omega; dense Cholesky);
+ *   3. w_{t+1} = the QP solution (the step from w_t halved until the power flow
+ *      at u_{t+1} converges), then y <- y + rho D_c (c_t(u_{t+1}) - s_{t+1}).
+ * Readings (the paper names the IPM, not its rules): KKT error of the QP as for
+ * opf_al_solve with grad q(d) = g_t + (H_t + delta I_u) d in place of grad L;
+ * stop when E_0 <= tol or after max_it iterations; mu <- max(tol / 10,
+ * min(0.2 mu, mu^1.5)) when E_mu <= 10 mu; fraction to the boundary tau =
+ * max(0.99, 1 - mu); delta is the smallest of 0 (or opts->delta_start), 1e-8,
+ * 1e-7, ... that makes S positive definite, and it only grows within a QP (so
+ * the QP stays one convex problem).  grad q is carried from iteration to
+ * iteration through the Newton system: H d = -grad psi - Sigma d.
+ * p: sigma_f, rho, sigma_c (y, s, omega ignored); y [m] updated in place; st:
+ * u, s (w_t in, w_{t+1} out), bound duals (the QP's, warm start in, final out),
+ * bounds, x (the state at u_t in, at u_{t+1} out), mu (the QP's first barrier
+ * in, its last out).  Errors: OPF_ESTATE, OPF_EINVAL, OPF_ENOTPD, OPF_ENOCONV,
+ * OPF_ETIMEOUT.
+ */
+typedef struct {
+  int max_it;         /* QP iterations (0 = 50) */
+  double tol;         /* stop when the QP's KKT error E_0 <= tol (0 = 1e-6) */
+  int block_k;        /* Hessian tile width (0 = autotuned, else 8) */
+  int max_halvings;   /* (0 = 10) */
+  int max_inertia;    /* inertia-correction increases per factorisation (0 = 24) */
+  double delta_start; /* the QP's first delta (0 = start at 0) */
+} opf_qp_opts;
+
+typedef struct {
+  int qp_iterations, halvings, pf_iterations, inertia_increases;
+  double delta, kkt, mu, alpha_p;
+  float ms_total;     /* the whole update */
+  float ms_qp;        /* gradient at w_t and the QP iterations */
+  float ms_hessian;   /* summed device time of the QP's Hessians H(omega) */
+  float ms_cholesky;  /* summed device time of its factorisations */
+} opf_qp_info;
+
+opf_status opf_tracking_update(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_state* st,
+                               const opf_qp_opts* opts, opf_qp_info* info);
+
+/*
+ * opf_set_wait_limit: iteration limit of every bounded device-side wait of
+ * this context (the flag polls of the dense block's cluster LU and of the
+ * dense triangular solves of opf_al_step); 0 restores each kernel's default
+ * (2^22 and 2^24 polls).  A wait that reaches the limit stops waiting, records
+ * the timeout and lets its kernel finish; the call then returns OPF_ETIMEOUT
+ * (a refactorisation also drops the context's state, as OPF_ESINGULAR does)
+ * and the context stays usable.  Errors: OPF_EINVAL (spins < 0), OPF_ECUDA.
+ */
+opf_status opf_set_wait_limit(opf_ctx* ctx, int spins);
+
+/*
+ * Measurement and verification entry points (no context; ordered on `stream`,
+ * a cudaStream_t, NULL = legacy default stream; each call synchronises it).
+ *
+ * opf_fp64_peak: the device's FP64 FMA rate, the denominator of the FP64
+ * roofline of the solves and second-order terms (Sec. V-A runs them in FP64):
+ * every resident thread runs eight independent chains of dependent FMAs; the
+ * fastest of five timed launches (CUDA events) after one warm-up.  tflops
+ * (host) receives 2 x FMAs / time in TFLOP/s, ms_out (host, may be NULL) that
+ * launch's time.  Errors: OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA.
+ *
+ * opf_pivot_reciprocal: r[i] = 1 / u[i] (device arrays of n doubles) computed
+ * as the LU refactorisation computes its pivots' reciprocals (hardware
+ * approximate reciprocal, flushing subnormal inputs to zero, then two
+ * Newton-Raphson steps), so that the tests can compare it with IEEE division:
+ * equal except for u just below a power of two (every mantissa bit set: one
+ * unit in the last place off); NaN
+ * for zero and subnormal u.
+ *
+ * opf_dense_syrk_emulated: the trailing update of one column group of the
+ * Schur-complement Cholesky (Prop. 3; dense FP64 Cholesky on the device):
+ * A[r0:n, r0:n] (lower triangle) -= P P^T with P = A[r0:n, c0:c0+K], A column-
+ * major n x n on the device, K in {32, 64, 96, 128}, c0 + K <= r0 < n,
+ * emulated in FP64 on the bf16 tensor cores (rows of P in eight signed 7-bit
+ * digits against a per-row power of two; digit products accumulated exactly;
+ * levels i + j >= 8 and the digit tails dropped).  Element (r, c) of the
+ * update then errs by less than 5 K 2^-53 max_k |P_rk| max_k |P_ck| before the
+ * final FP64 roundings.  Allocates and frees its workspace.  Errors:
+ * OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA.
+ */
+opf_status opf_fp64_peak(void* stream, double* tflops, float* ms_out);
+opf_status opf_pivot_reciprocal(void* stream, const double* u, double* r, int n);
+opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0);
 
 /* Number of kernels this context has launched since it was created (host output). */
 opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);

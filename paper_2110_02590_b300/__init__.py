@@ -56,12 +56,14 @@ class AlParams(C.Structure):
 
 class HessOpts(C.Structure):
     _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("plain", C.c_int), ("col_begin", C.c_int),
-                ("col_count", C.c_int), ("threads", C.c_int), ("reuse_first_order", C.c_int)]
+                ("col_count", C.c_int), ("threads", C.c_int), ("reuse_first_order", C.c_int),
+                ("asymmetry", C.c_int), ("phase_profile", C.c_int)]
 
 
 class HessInfo(C.Structure):
     _fields_ = [("block_k", C.c_int), ("grid", C.c_int), ("tiles", C.c_int), ("launches", C.c_int),
-                ("ms_total", C.c_float), ("ms_hvp", C.c_float)]
+                ("ms_total", C.c_float), ("ms_hvp", C.c_float), ("asymmetry", C.c_double),
+                ("phase_ms", C.c_float * 5)]
 
 
 class AlState(C.Structure):
@@ -81,6 +83,29 @@ class StepInfo(C.Structure):
                 ("inertia_tries", C.c_int), ("pf_iterations", C.c_int), ("ms_hessian", C.c_float),
                 ("ms_total", C.c_float), ("ms_first_order", C.c_float), ("ms_rhs", C.c_float),
                 ("ms_cholesky", C.c_float), ("ms_solve", C.c_float), ("ms_trial", C.c_float)]
+
+
+class AlOpts(C.Structure):
+    _fields_ = [("max_outer", C.c_int), ("max_inner", C.c_int), ("eta_primal", C.c_double),
+                ("eta_dual", C.c_double), ("rho_max", C.c_double), ("block_k", C.c_int)]
+
+
+class AlInfo(C.Structure):
+    _fields_ = [("outer", C.c_int), ("steps", C.c_int), ("converged", C.c_int), ("primal_inf", C.c_double),
+                ("dual_inf", C.c_double), ("F", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+                ("ms_total", C.c_float)]
+
+
+class QpOpts(C.Structure):
+    _fields_ = [("max_it", C.c_int), ("tol", C.c_double), ("block_k", C.c_int), ("max_halvings", C.c_int),
+                ("max_inertia", C.c_int), ("delta_start", C.c_double)]
+
+
+class QpInfo(C.Structure):
+    _fields_ = [("qp_iterations", C.c_int), ("halvings", C.c_int), ("pf_iterations", C.c_int),
+                ("inertia_increases", C.c_int), ("delta", C.c_double), ("kkt", C.c_double), ("mu", C.c_double),
+                ("alpha_p", C.c_double), ("ms_total", C.c_float), ("ms_qp", C.c_float), ("ms_hessian", C.c_float),
+                ("ms_cholesky", C.c_float)]
 
 
 class OPFError(RuntimeError):
@@ -122,6 +147,14 @@ def lib():
         L.opf_hessian_autotune.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(HessOpts),
                                            C.POINTER(C.c_float)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
+        L.opf_set_wait_limit.argtypes = [C.c_void_p, C.c_int]
+        L.opf_tracking_update.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
+                                          C.POINTER(QpOpts), C.POINTER(QpInfo)]
+        L.opf_al_solve.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
+                                   C.POINTER(AlOpts), C.POINTER(AlInfo), C.POINTER(C.c_double)]
+        L.opf_fp64_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)]
+        L.opf_pivot_reciprocal.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.opf_dense_syrk_emulated.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
         L.opf_last_error.restype = C.c_char_p
@@ -208,6 +241,45 @@ def reduced_hessian_batched(ctxs, als, block_k=8, grid=0, outs=None):
                                      launches=info.launches, ms_total=info.ms_total, ms_hvp=info.ms_hvp)
 
 
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def fp64_peak():
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = C.c_double(), C.c_float()
+    st = lib().opf_fp64_peak(_stream(), C.byref(tf), C.byref(ms))
+    if st != 0:
+        raise OPFError(st, "opf_fp64_peak")
+    return tf.value, ms.value
+
+
+def pivot_reciprocal(u):
+    """1 / u as the LU refactorisation computes its pivots' reciprocals (cuda float64 tensor)."""
+    import torch
+    if u.dtype != torch.float64 or not u.is_cuda or not u.is_contiguous():
+        raise ValueError("expected a contiguous cuda float64 tensor")
+    r = torch.empty_like(u)
+    st = lib().opf_pivot_reciprocal(_stream(), C.c_void_p(u.data_ptr()), C.c_void_p(r.data_ptr()), u.numel())
+    if st != 0:
+        raise OPFError(st, "opf_pivot_reciprocal")
+    return r
+
+
+def dense_syrk_emulated(A, c0, K, r0):
+    """A[r0:, r0:] (lower) -= P P^T, P = A[r0:, c0:c0+K], in place on a column-major n x n
+    cuda float64 matrix given as its transpose view (A_t[j] = column j), emulated on tensor cores."""
+    import torch
+    if A.dtype != torch.float64 or not A.is_cuda or not A.is_contiguous() or A.dim() != 2 or \
+            A.shape[0] != A.shape[1]:
+        raise ValueError("expected a square contiguous cuda float64 tensor")
+    st = lib().opf_dense_syrk_emulated(_stream(), C.c_void_p(A.data_ptr()), A.shape[0], int(c0), int(K), int(r0))
+    if st != 0:
+        raise OPFError(st, "opf_dense_syrk_emulated")
+    return A
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -247,6 +319,15 @@ class OPFContext:
                 raise ValueError("expected a contiguous float64 tensor on the context's device")
             return v
         return t.as_tensor(np.ascontiguousarray(v, dtype=np.float64), device=self.device)
+
+    def _out_hessian(self, out):
+        """The n_u x n_u output buffer of a Hessian call (checked: the kernels write all of it)."""
+        if out is None:
+            return self.torch.empty((self.nu, self.nu), dtype=self.torch.float64, device=self.device)
+        self._dev(out)
+        if tuple(out.shape) != (self.nu, self.nu):
+            raise ValueError(f"out must have shape ({self.nu}, {self.nu}), got {tuple(out.shape)}")
+        return out
 
     # ---------------------------------------------------------------- symbolic
     def symbolic(self) -> dict:
@@ -321,37 +402,49 @@ class OPFContext:
             raise OPFError(st, "opf_hessian_autotune")
         return dict(block_k=best.block_k, threads=best.threads, ms=ms.value)
 
+    def set_wait_limit(self, spins: int) -> None:
+        """Iteration limit of the context's bounded device waits (0 = the kernels' defaults)."""
+        self._sync_stream()
+        st = lib().opf_set_wait_limit(self.h, int(spins))
+        if st != 0:
+            raise OPFError(st, "opf_set_wait_limit")
+
     def launch_count(self) -> int:
         v = C.c_longlong()
         lib().opf_launch_count(self.h, C.byref(v))
         return v.value
 
     def reduced_hessian(self, al, block_k=8, grid=0, plain=False, out=None, col_begin=0, col_count=0,
-                        threads=0):
+                        threads=0, asymmetry=False, phase_profile=False):
         """Dense reduced Hessian (n_u x n_u) by adjoint-adjoint HVPs (Prop. 2).
 
-        Returns (H, info); H is column-major in memory, i.e. H_t[j] is column j.
+        Returns (H, info); H is column-major in memory, i.e. H_t[j] is column j.  With
+        asymmetry=True (full Hessian) info["asymmetry"] = ||H - H^T||_F / ||H||_F; with
+        phase_profile=True info["phase_ms"] apportions the HVP time to the tile phases (first L
+        solve, U sweep, second-order terms, U^T + L^T sweeps, assembly).
         """
         t = self.torch
         self._sync_stream()
         p, keep = self._al(al)
-        H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
+        H = self._out_hessian(out)
         info = HessInfo()
-        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count), int(threads), 0)
+        opts = HessOpts(int(block_k), int(grid), int(plain), int(col_begin), int(col_count), int(threads), 0,
+                        int(bool(asymmetry)), int(bool(phase_profile)))
         st = lib().opf_reduced_hessian(self.h, C.byref(p), C.byref(opts),
                                        _ptr(H), C.byref(info))
         if st != 0:
             raise OPFError(st, "opf_reduced_hessian")
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
-                         ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+                         ms_total=info.ms_total, ms_hvp=info.ms_hvp, asymmetry=info.asymmetry,
+                         phase_ms=list(info.phase_ms))
 
     def reduced_hessian_noalloc(self, al, block_k=8, grid=0, out=None, col_begin=0, col_count=0):
         """Reduced Hessian through opf_reduced_hessian_noalloc (fixed static workspace, no allocation
-        inside the call).  `out` should be preallocated by callers that cannot allocate."""
+        inside the call).  Callers that cannot allocate pass a preallocated n_u x n_u float64 `out`."""
         t = self.torch
         self._sync_stream()
         p, keep = self._al(al)
-        H = out if out is not None else t.empty((self.nu, self.nu), dtype=t.float64, device=self.device)
+        H = self._out_hessian(out)
         info = HessInfo()
         opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count), 0, 0)
         st = lib().opf_reduced_hessian_noalloc(self.h, C.byref(p), C.byref(opts), _ptr(H), C.byref(info))
@@ -359,6 +452,55 @@ class OPFContext:
             raise OPFError(st, "opf_reduced_hessian_noalloc")
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
                          ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+
+    def _state(self, state):
+        for k in ("u", "s", "zl_u", "zu_u", "zl_s", "zu_s", "u_lo", "u_hi", "s_lo", "s_hi", "x"):
+            self._dev(state[k])
+        return AlState(*[state[k].data_ptr() for k in ("u", "s", "zl_u", "zu_u", "zl_s", "zu_s", "u_lo", "u_hi",
+                                                        "s_lo", "s_hi", "x")], float(state["mu"]))
+
+    def al_solve(self, al, state, y, max_outer=20, max_inner=10, eta_primal=1e-5, eta_dual=1e-4, rho_max=1e6,
+                 block_k=0):
+        """Static OPF by the augmented-Lagrangian outer loop (opf_al_solve).  `al`: sigma_f, the initial
+        rho and sigma_c; `y` (cuda float64 [m]) and the state tensors are updated in place, and
+        state["mu"] is set to the final barrier parameter.  Returns (info dict, history array
+        [outer, 8]: steps, mu, rho, eta_p, E_0, F, delta, 0)."""
+        self._sync_stream()
+        y = self._dev(y)
+        keep = [self._dev(al["sigma_c"])]
+        p = AlParams(float(al["sigma_f"]), float(al["rho"]), keep[0].data_ptr(), y.data_ptr(), None, None)
+        st = self._state(state)
+        hist = np.zeros((max(1, int(max_outer)), 8))
+        info = AlInfo()
+        rc = lib().opf_al_solve(self.h, C.byref(p), C.c_void_p(y.data_ptr()), C.byref(st),
+                                C.byref(AlOpts(int(max_outer), int(max_inner), float(eta_primal), float(eta_dual),
+                                               float(rho_max), int(block_k))),
+                                C.byref(info), hist.ctypes.data_as(_dp))
+        state["mu"] = st.mu
+        if rc != 0:
+            raise OPFError(rc, "opf_al_solve")
+        out = {k: getattr(info, k) for k, _ in AlInfo._fields_}
+        return out, hist[:info.outer].copy()
+
+    def tracking_update(self, al, state, y, max_it=50, tol=1e-6, block_k=0, max_halvings=0, max_inertia=0,
+                        delta_start=0.0):
+        """One real-time update (opf_tracking_update): gradient and Hessian at the current point, the
+        bounded QP of eq. qp_rto by an interior-point method on the Schur complement, the power flow
+        at the new controls and the multiplier update.  `al`: sigma_f, rho, sigma_c; y and the state
+        tensors are updated in place, state["mu"] is set to the QP's last barrier.  Returns info."""
+        self._sync_stream()
+        y = self._dev(y)
+        keep = [self._dev(al["sigma_c"])]
+        p = AlParams(float(al["sigma_f"]), float(al["rho"]), keep[0].data_ptr(), y.data_ptr(), None, None)
+        st = self._state(state)
+        info = QpInfo()
+        rc = lib().opf_tracking_update(self.h, C.byref(p), C.c_void_p(y.data_ptr()), C.byref(st),
+                                       C.byref(QpOpts(int(max_it), float(tol), int(block_k), int(max_halvings),
+                                                      int(max_inertia), float(delta_start))), C.byref(info))
+        state["mu"] = st.mu
+        if rc != 0:
+            raise OPFError(rc, "opf_tracking_update")
+        return {k: getattr(info, k) for k, _ in QpInfo._fields_}
 
     def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0, delta_start=0.0):
         """One reduced-Newton step (Prop. 3).  `state`: dict of cuda float64 tensors u, s, zl_u,

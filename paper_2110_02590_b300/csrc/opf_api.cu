@@ -587,6 +587,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->yvec, nx));
   TRY(dalloc(c, &c->scal, 8));
   TRY(dalloc(c, &c->flags, 4));
+  CK(cudaMemset(c->flags, 0, 4 * sizeof(int)));  // no error, default wait limits
   TRY(dalloc(c, &c->flows, 4 * (size_t)nl));
   TRY(dalloc(c, &c->Pbus, nb));
   TRY(dalloc(c, &c->Qbus, nb));
@@ -660,6 +661,7 @@ static void free_impl(opf_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (void* p : c->allocs) cudaFree(p);
   if (c->scratch) cudaFree(c->scratch);
+  if (c->stamps) cudaFree(c->stamps);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   for (int k = 0; k < 4; k++)
@@ -748,16 +750,27 @@ struct opf_symbolic {
 opf_status opf::ensure_factors(opf_ctx* c) {
   if (!c->factors_stale) return OPF_OK;
   cudaStream_t st = c->stream;
-  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), st));
   launch_lu(c);
-  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
   c->factors_stale = false;
+  if (c->h_flags[1]) {
+    c->have_state = false;
+    FAIL(OPF_ETIMEOUT, "a bounded wait of the LU refactorisation gave up");
+  }
   if (c->h_flags[0]) {
     c->have_state = false;
     FAIL(OPF_ESINGULAR, "singular Jacobian at the power-flow solution");
   }
+  return OPF_OK;
+}
+
+opf_status opf::check_al(const opf_ctx* c, const opf_al_params* p) {
+  (void)c;
+  if (!p || !p->sigma_c || !p->y || !p->s) FAIL(OPF_EINVAL, "AL parameters need sigma_c, y and s");
+  if (!(p->rho >= 0.0) || !std::isfinite(p->sigma_f)) FAIL(OPF_EINVAL, "rho must be >= 0, sigma_f finite");
   return OPF_OK;
 }
 
@@ -814,18 +827,23 @@ opf_status opf_powerflow(opf_ctx* c, const double* u, const double* pd, const do
   int it = 0;
   double res2 = NAN, resinf = NAN;
   c->factors_stale = false;
-  CK(cudaMemsetAsync(c->flags, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), st));
   for (it = 0;; it++) {
     launch_unpack(c, c->x, c->u);
     CK(cudaMemsetAsync(c->LU, 0, c->dn.nnz * sizeof(double), st));
     CK(cudaMemsetAsync(c->scal, 0, 2 * sizeof(double), st));
     launch_pf_eval(c);
     CK(cudaMemcpyAsync(c->h_scal, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_flags, c->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     res2 = std::sqrt(c->h_scal[0]);
     resinf = c->h_scal[1];
+    if (c->h_flags[1]) {  // the previous iteration's refactorisation
+      result = OPF_ETIMEOUT;
+      g_err = "a bounded wait of the LU refactorisation gave up";
+      break;
+    }
     if (c->h_flags[0]) {  // the previous iteration's refactorisation
       result = OPF_ESINGULAR;
       g_err = "zero or non-finite pivot in the LU refactorisation";
@@ -860,13 +878,6 @@ opf_status opf_powerflow(opf_ctx* c, const double* u, const double* pd, const do
   }
   c->have_state = (result == OPF_OK);
   return result;
-}
-
-static opf_status check_al(const opf_ctx* c, const opf_al_params* p) {
-  (void)c;
-  if (!p || !p->sigma_c || !p->y || !p->s) FAIL(OPF_EINVAL, "AL parameters need sigma_c, y and s");
-  if (!(p->rho >= 0.0) || !std::isfinite(p->sigma_f)) FAIL(OPF_EINVAL, "rho must be >= 0, sigma_f finite");
-  return OPF_OK;
 }
 
 opf_status opf_reduced_gradient(opf_ctx* c, const opf_al_params* p, double* F, double* grad_u,
@@ -917,6 +928,7 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   if (nt != 128 && nt != 256 && nt != 512) FAIL(OPF_EINVAL, "threads must be 128, 256 or 512");
   c->hvp_threads = nt;
   const bool plain = o && o->plain;
+  if (plain) C = 1;  // one direction per launch sequence
   const int nu = c->h.nu;
   const int col0 = o ? o->col_begin : 0;
   const int ncol = (o && o->col_count > 0) ? o->col_count : nu - col0;
@@ -927,19 +939,37 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   // the context has one for this width
   const bool split = !plain && !(o && o->grid > 0) && col0 == 0 && ncol == nu && nt == 256 &&
                      c->split_n1[lk] > 0;
-  const int ntiles = split ? c->split_n1[lk] + c->split_n2[lk] : hvp_tiles(c, C, col0, col0 + ncol, true);
+  const int ntiles = plain ? ncol
+                           : (split ? c->split_n1[lk] + c->split_n2[lk] : hvp_tiles(c, C, col0, col0 + ncol, true));
   int grid = plain ? 1 : ((o && o->grid > 0) ? o->grid : std::min(ntiles, hvp_occupancy(C, nt) * c->sm_count));
   grid = std::max(1, std::min(grid, ntiles));
   if (split) grid = ntiles;
-  TRY(ensure_scratch(c, split ? hvp_split_scratch(c, C) : hvp_stride(c, C) * (size_t)grid));
+  TRY(ensure_scratch(c, plain ? hvp_plain_scratch(c)
+                              : (split ? hvp_split_scratch(c, C) : hvp_stride(c, C) * (size_t)grid)));
   cudaStream_t st = c->stream;
+  const bool prof = info && o && o->phase_profile && !plain;
+  if (prof) {
+    if (c->stamps_cap < (size_t)ntiles) {
+      CK(cudaStreamSynchronize(st));
+      if (c->stamps) cudaFree(c->stamps);
+      c->stamps = nullptr;
+      c->stamps_cap = 0;
+      if (cudaMalloc(&c->stamps, sizeof(unsigned long long) * 8 * (size_t)ntiles) != cudaSuccess) {
+        cudaGetLastError();
+        FAIL(OPF_ENOMEM, "cannot allocate the phase stamps");
+      }
+      c->stamps_cap = ntiles;
+    }
+    CK(cudaMemsetAsync(c->stamps, 0, sizeof(unsigned long long) * 8 * (size_t)ntiles, st));
+    c->stamps_on = true;
+  }
   CK(cudaEventRecord(c->ev[0], st));
   if (!(o && o->reuse_first_order)) launch_first_order(c, p, nullptr);
   launch_hess_prep(c, p->sigma_f);
   CK(cudaEventRecord(c->ev[1], st));
   int launches = 0;
   if (plain) {
-    for (int t = 0; t < ntiles; t++, launches++) launch_hvp(c, C, H, 1, t, 1, t + 1, col0, col0 + ncol);
+    launches = launch_hvp_plain(c, H, col0, col0 + ncol, c->scratch);
   } else if (split) {
     launch_hvp_split(c, C, H);
     launches = 1;
@@ -948,6 +978,19 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
     launches = 1;
   }
   CK(cudaEventRecord(c->ev[2], st));
+  c->stamps_on = false;
+  std::vector<unsigned long long> stamps;
+  if (prof) {
+    stamps.resize(8 * (size_t)ntiles);
+    CK(cudaMemcpyAsync(stamps.data(), c->stamps, sizeof(unsigned long long) * stamps.size(),
+                       cudaMemcpyDeviceToHost, st));
+  }
+  const bool asym = info && o && o->asymmetry && col0 == 0 && ncol == nu;
+  if (asym) {  // after the timed region
+    CK(cudaMemsetAsync(c->scal + 4, 0, 2 * sizeof(double), st));
+    launch_hess_asymmetry(c, H, nu, c->scal + 4);
+    CK(cudaMemcpyAsync(c->h_scal + 4, c->scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
   if (info) {
@@ -957,6 +1000,21 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
     info->launches = launches;
     cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
+    info->asymmetry = -1.0;
+    if (asym)
+      info->asymmetry = c->h_scal[5] > 0.0 ? std::sqrt(c->h_scal[4] / c->h_scal[5]) : 0.0;
+    for (int k = 0; k < 5; k++) info->phase_ms[k] = 0.f;
+    if (prof) {  // the HVP time apportioned to the phases by their share of the tiles' summed time
+      double part[5] = {0, 0, 0, 0, 0}, tot = 0.0;
+      for (int t = 0; t < ntiles; t++) {
+        const unsigned long long* q = stamps.data() + 8 * (size_t)t;
+        if (!(q[0] > 0 && q[5] >= q[0])) continue;
+        for (int k = 0; k < 5; k++) part[k] += (double)(q[k + 1] - q[k]);
+        tot += (double)(q[5] - q[0]);
+      }
+      if (tot > 0.0)
+        for (int k = 0; k < 5; k++) info->phase_ms[k] = (float)(info->ms_hvp * part[k] / tot);
+    }
   }
   return OPF_OK;
 }
@@ -1064,9 +1122,19 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     info->grid = grid;
     info->tiles = ntot;
     info->launches = 1;
+    info->asymmetry = -1.0;
+    for (int k = 0; k < 5; k++) info->phase_ms[k] = 0.f;
     cudaEventElapsedTime(&info->ms_total, c0->ev[0], c0->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c0->ev[1], c0->ev[2]);
   }
+  return OPF_OK;
+}
+
+opf_status opf_set_wait_limit(opf_ctx* c, int spins) {
+  if (!c || spins < 0) FAIL(OPF_EINVAL, "ctx is NULL or spins < 0");
+  CK(cudaMemcpyAsync(c->flags + 2, &spins, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->wait_limit = spins;
   return OPF_OK;
 }
 

@@ -104,6 +104,7 @@ struct HvpArgs {
   const int* colmap;  // null: tile position p is column col0 + p; else column colmap[p] (-1: none)
   double* H;
   double* scratch;
+  unsigned long long* stamps;  // null, or [tiles][8] phase stamps per tile (hvp_stamp)
   size_t stride;    // doubles of scratch per CTA
   int ntiles, first_tile, tile_step;
   int col0, col_end;  // columns computed: col0 .. col_end - 1
@@ -136,12 +137,15 @@ void launch_grad_u(opf_ctx* c, double* gu);
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
 void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);
+// sums[0] += ||H - H^T||_F^2, sums[1] += ||H||_F^2 (H: n x n column-major)
+void launch_hess_asymmetry(opf_ctx* c, const double* H, int n, double* sums);
 bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
                 int col0, int col_end);
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
                         int col_end);
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
 opf_status ensure_factors(opf_ctx* c);  // factorise the converged state's Jacobian if still pending
+opf_status check_al(const opf_ctx* c, const opf_al_params* p);  // AL inputs present, rho >= 0, sigma_f finite
 // balanced: the single-network launch (tiles in whole waves over the SMs)
 HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced);
 int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  // tiles of a column range
@@ -149,6 +153,11 @@ int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  /
 // one launch (false when the context has no split tiling at this width).
 bool launch_hvp_split(opf_ctx* c, int C, double* H);
 size_t hvp_split_scratch(const opf_ctx* c, int C);  // doubles of workspace it needs
+// The plain form: Hessian columns col0 .. col_end - 1 one at a time, each a
+// sequence of device-wide launches around two streamed single-RHS solves;
+// work holds hvp_plain_scratch doubles.  Returns the kernels launched.
+size_t hvp_plain_scratch(const opf_ctx* c);
+int launch_hvp_plain(opf_ctx* c, double* H, int col0, int col_end, double* work);
 int hvp_batch_occupancy(int C);  // resident CTAs per SM of the batched tile kernel
 int hvp_occupancy(int C, int nt);  // resident CTAs per SM of hvp_tile_kernel<C, nt>
 bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* tiles, int ntot, int* counter,
@@ -158,6 +167,14 @@ bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* t
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
 struct StepWork;
 void free_step_work(opf_ctx* c);
+// KKT errors of a barrier subproblem at st with gradient (gu, gs) (opf_al.cu):
+// red[0..3] (zeroed by the caller) = max |g - z_lo + z_hi|, max complementarity
+// error at mu, at 0, and max |sigma_c (c - s)| (0 when cv is null).
+void launch_al_kkt(opf_ctx* c, const double* gu, const double* gs, const opf_al_state* st, const double* cv,
+                   const double* sig, double mu, double* red);
+// y += rho sigma_c (c - s)
+void launch_al_dual_update(opf_ctx* c, double* y, double rho, const double* sig, const double* cv,
+                           const double* s);
 
 #ifdef __CUDACC__
 // Programmatic dependent launch: a kernel launched by launch_pdl may start while
@@ -187,7 +204,10 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 // 1 / u by the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - u r)
 // (each step squares the relative error), from the hardware's approximate FP64
-// reciprocal: two steps reach full double precision for normal u.  It issues
+// reciprocal: two steps reach full double precision for normal u (equal to
+// IEEE 1 / u except for u just below a power of two (every mantissa bit set),
+// where the result is one unit in the last place off; subnormal and zero u give NaN, which the pivot checks catch,
+// and so does a subnormal result).  It issues
 // one MUFU and four DFMA where the IEEE division issues a longer FP64 sequence,
 // which matters where many warps each divide once (the FP64 pipe runs one warp
 // instruction per ~20 cycles whatever the active lanes).
@@ -419,7 +439,9 @@ struct opf_ctx {
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
   double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...
-  int* flags = nullptr;           // [4] error flags set by kernels
+  int* flags = nullptr;           // [4] set by kernels: [0] bad pivot, [1] a bounded wait gave up;
+                                  // [2] spin limit of the bounded waits (0: each kernel's default)
+  int wait_limit = 0;             // host copy of flags[2] (opf_set_wait_limit)
   double* h_scal = nullptr;       // pinned host mirror of scal
   int* h_flags = nullptr;         // pinned host mirror of flags
   bool have_state = false;
@@ -439,6 +461,9 @@ struct opf_ctx {
   int solve1_smem = 0;            // dynamic shared bytes of the single-RHS sweep
   bool solve1_use_smem_rhs = false;  // the right-hand side also lives in shared memory
   double* scratch = nullptr;      // HVP per-CTA slabs
+  unsigned long long* stamps = nullptr;  // phase stamps of a profiling Hessian call
+  size_t stamps_cap = 0;          // tiles the stamps array holds
+  bool stamps_on = false;         // the HVP launches of this call record phase stamps
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];
   long long launches = 0;         // kernels launched by this context

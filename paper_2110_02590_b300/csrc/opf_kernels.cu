@@ -1225,8 +1225,20 @@ __device__ __forceinline__ void gu_ends(const DevNet& n, const double* R, const 
 // One tile of C Hessian columns on one CTA: B = -G_u W, Z = G_x^{-1} B,
 // second-order terms, Psi = G_x^{-T} R, H[:, tile] = T + G_u^T Psi (Prop. 2).
 // Z is the CTA's workspace (2 n_x C + n_ctrl C + C doubles).
+// Phase stamps of one tile (a.stamps non-null only in a profiling call): the
+// global nanosecond timer at the tile's start and after phases (1), (2), (4),
+// (6) and (7), read by thread 0 after the phase's last barrier.
+__device__ __forceinline__ void hvp_stamp(const HvpArgs& a, int tile, int k) {
+  if (a.stamps && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    a.stamps[(size_t)tile * 8 + k] = t;
+  }
+}
+
 template <int C>
 __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) {
+  hvp_stamp(a, tile, 0);
   const DevNet& n = a.n;
   const int nb = n.nb, nu = n.nu;
   double* R = Z + (size_t)n.nx * C;
@@ -1433,8 +1445,10 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     } else {
       sweep<C, true, false>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
     }
+    hvp_stamp(a, tile, 1);
     // (2) U sweep
     sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
+    hvp_stamp(a, tile, 2);
     // (3) directional derivatives of Q (slack and PV) and P (slack) for the
     // Gauss-Newton terms, stored pre-multiplied by their weights kQ, kP.  The
     // own-variable parts are the per-bus sums dQ_k/dv_k, dQ_k/dtheta_k, ...
@@ -1515,9 +1529,11 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       }
     }
     __syncthreads();
+    hvp_stamp(a, tile, 3);
     // (5)-(6) second second-order adjoint: U^T then L^T sweeps
     sweep<C, true, true>(n, a.T, a.invdiag, R, nullptr, s_tb);
     sweep<C, false, false>(n, a.T, a.invdiag, R, nullptr, s_tb);
+    hvp_stamp(a, tile, 4);
     // (7) H[:, tile] += G_u^T Psi (buses by descending degree)
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
       const int gi = n.gn_by_deg[it / C], c = it % C, k = n.gn_bus[gi], j = s_col[c];
@@ -1541,6 +1557,7 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       Hc[-2 - bk.x] += gv;
     }
     __syncthreads();
+    hvp_stamp(a, tile, 5);
   }
 }
 
@@ -1604,6 +1621,138 @@ __global__ void __launch_bounds__(256, 3) hvp_batch_kernel(const HvpArgs* __rest
     for (int k = threadIdx.x; k < (int)(sizeof(HvpArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
     __syncthreads();
     hvp_tile<C>(sa, Z, ct.y);
+  }
+}
+
+// ------------------------------------------------------------ plain form
+// One Hessian column per launch sequence (the k = 1 baseline of the batched
+// tiles, Sec. III-C computes the Hessian one HVP at a time in its plain form):
+// the steps of hvp_tile with C = 1, each a device-wide launch, and the two
+// solves on the streamed single-RHS sweeps (the library's fastest
+// one-direction solve).  The solves take and return vectors in x order; the
+// second-order gathers index pivot-order slots, so the vectors are permuted
+// between them.
+
+// B = -G_u e_j into the zeroed x-order vector bx (phase (0) of hvp_tile, one thread).
+__global__ void plain_rhs_kernel(HvpArgs a, int j, double* bx) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const DevNet& n = a.n;
+  const double* __restrict__ E = a.adjE;
+  const int k = a.ubus[j];
+  if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
+    bx[n.perm[n.pth[k]]] = 1.0;
+    return;
+  }
+  for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+    const int4 ar = n.adjrec[q];
+    if (ar.y >= 0) bx[n.perm[ar.y]] -= E[(size_t)q * ADJ_W + E_POV];
+    if (ar.x >= 0) bx[n.perm[ar.x]] -= E[(size_t)q * ADJ_W + E_QOV];
+  }
+  if (n.type[k] == PV) bx[n.perm[n.pth[k]]] -= a.busw[6 * n.nb + k];
+}
+
+// to_pivot: dst[k] = src[perm[k]]; else dst[perm[k]] = src[k].
+__global__ void plain_permute_kernel(const int* __restrict__ perm, const double* __restrict__ src,
+                                     double* __restrict__ dst, int nx, int to_pivot) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nx; k += gridDim.x * blockDim.x) {
+    if (to_pivot)
+      dst[k] = src[perm[k]];
+    else
+      dst[perm[k]] = src[k];
+  }
+}
+
+// Phase (3): directional derivatives of Q (and P at the slack) at the control buses.
+__global__ void plain_qd_kernel(HvpArgs a, int j, const double* __restrict__ Z, double* QD, double* PD) {
+  const DevNet& n = a.n;
+  const int nb = n.nb;
+  const double* __restrict__ E = a.adjE;
+  const double* __restrict__ bw = a.busw;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < n.ngn; gi += gridDim.x * blockDim.x) {
+    const int k = n.gn_bus[gi];
+    const int4 bk = n.busrec[k];
+    const double vk = dslot<1>(Z, bk.x, 0, j), tk = bk.y >= 0 ? Z[bk.y] : 0.0;
+    const bool slack = (k == n.ref);
+    double qd = bw[4 * nb + k] * vk + bw[5 * nb + k] * tk, pdr = 0.0;
+    if (slack) pdr = bw[6 * nb + k] * vk + bw[7 * nb + k] * tk;
+    const int q1 = n.adj_ptr[k + 1];
+    int qb = n.adj_ptr[k];
+    for (; qb + 4 <= q1; qb += 4) qd_ends<1, 4>(n, Z, E, qb, 0, j, slack, qd, pdr);
+    if (qb + 2 <= q1) {
+      qd_ends<1, 2>(n, Z, E, qb, 0, j, slack, qd, pdr);
+      qb += 2;
+    }
+    if (qb < q1) qd_ends<1, 1>(n, Z, E, qb, 0, j, slack, qd, pdr);
+    QD[gi] = bw[k] * qd;
+    if (slack) PD[0] = bw[nb + k] * pdr;
+  }
+}
+
+// Phase (4): y = (grad^2 l)(z; w) per bus; R = -y_x (pivot order), H[u rows, j] = y_u.
+__global__ void plain_gather_kernel(HvpArgs a, int j, const double* __restrict__ Z, const double* __restrict__ QD,
+                                    const double* __restrict__ PD, double* R) {
+  const DevNet& n = a.n;
+  const int nb = n.nb;
+  const double* __restrict__ E = a.adjE;
+  const double* __restrict__ bw = a.busw;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int4 bi = n.busrec[i];
+    const double4_32a S = reinterpret_cast<const double4_32a*>(a.busS)[i];
+    const double vi = dslot<1>(Z, bi.x, 0, j), ti = bi.y >= 0 ? Z[bi.y] : 0.0;
+    double yv = S.x * vi + S.y * ti, yt = S.y * vi + S.z * ti;
+    const int q1 = n.adj_ptr[i + 1];
+    int qb = n.adj_ptr[i];
+    for (; qb + 4 <= q1; qb += 4) gather_ends<1, 4>(n, Z, E, QD, PD, qb, 0, j, yv, yt);
+    if (qb + 2 <= q1) {
+      gather_ends<1, 2>(n, Z, E, QD, PD, qb, 0, j, yv, yt);
+      qb += 2;
+    }
+    if (qb < q1) gather_ends<1, 1>(n, Z, E, QD, PD, qb, 0, j, yv, yt);
+    if (bi.z >= 0) {
+      const double w = QD[bi.z];
+      yv += w * bw[4 * nb + i];
+      yt += w * bw[5 * nb + i];
+      if (bi.y < 0) {
+        const double w2 = PD[0];
+        yv += w2 * bw[6 * nb + i];
+        yt += w2 * bw[7 * nb + i];
+      }
+    }
+    if (bi.y >= 0) R[bi.y] = -yt;
+    if (bi.x >= 0) {
+      R[bi.x] = -yv;
+    } else {
+      double* Hc = a.H + (size_t)j * n.nu;
+      Hc[-2 - bi.x] = yv;
+      if (bi.w >= 0) Hc[bi.w] = (bi.w == j) ? bw[3 * nb + i] : 0.0;
+    }
+  }
+}
+
+// Phase (7): H[:, j] += G_u^T Psi (Psi in pivot order).
+__global__ void plain_assemble_kernel(HvpArgs a, int j, const double* __restrict__ Psi) {
+  const DevNet& n = a.n;
+  const int nb = n.nb;
+  const double* __restrict__ E = a.adjE;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < n.ngn; gi += gridDim.x * blockDim.x) {
+    const int k = n.gn_bus[gi];
+    double gv = 0.0;
+    const int q1 = n.adj_ptr[k + 1];
+    int qb = n.adj_ptr[k];
+    for (; qb + 4 <= q1; qb += 4) gu_ends<1, 4>(n, Psi, E, qb, 0, gv);
+    if (qb + 2 <= q1) {
+      gu_ends<1, 2>(n, Psi, E, qb, 0, gv);
+      qb += 2;
+    }
+    if (qb < q1) gu_ends<1, 1>(n, Psi, E, qb, 0, gv);
+    double* Hc = a.H + (size_t)j * n.nu;
+    const int4 bk = n.busrec[k];
+    if (bk.w >= 0) {  // PV bus
+      const double psi = Psi[bk.y];
+      gv += psi * a.busw[6 * nb + k];
+      Hc[bk.w] -= psi;
+    }
+    Hc[-2 - bk.x] += gv;
   }
 }
 
@@ -1846,6 +1995,7 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   a.colmap = full ? c->colmap[balanced ? 1 : 0][lk] : nullptr;
   a.H = H;
   a.scratch = nullptr;
+  a.stamps = c->stamps_on ? c->stamps : nullptr;
   a.stride = hvp_stride(c, C);
   a.ntiles = hvp_tiles(c, C, col0, col_end, balanced);
   a.first_tile = 0;
@@ -1886,6 +2036,7 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   a2.colmap = c->colmap_split[lk] + (size_t)n1 * C;
   a2.ntiles = n2;
   a2.scratch = c->scratch + a1.stride * (size_t)n1;
+  if (a2.stamps) a2.stamps += (size_t)n1 * 8;
   const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
   const int per_sm = std::max(1, n1 / c->sm_count);
   cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (2 + kSplitMaxSm), c->stream);
@@ -1995,6 +2146,76 @@ bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid,
     case 32: launch_hvp_scratch_t<32>(c, H, scratch, grid, ntiles, col0, col_end); return true;
     default: return false;
   }
+}
+
+// Asymmetry of a computed Hessian (Sec. III-C assembles H column block by
+// column block; in exact arithmetic it is symmetric): sums[0] += sum_ij (H_ij -
+// H_ji)^2 and sums[1] += sum_ij H_ij^2 over one 32 x 32 tile per CTA, the tile
+// and its mirror read through shared memory so both loads are coalesced
+// (column-major H, leading dimension n).
+__global__ void __launch_bounds__(256) hess_asym_kernel(const double* __restrict__ H, int n, double* sums) {
+  __shared__ double A[32][33], B[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + tx, j = bj * 32 + r;  // A[r][tx] = H(i, j); B[r][tx] = H(j', i') of the mirror
+    A[r][tx] = (i < n && j < n) ? H[(size_t)j * n + i] : 0.0;
+    const int i2 = bj * 32 + tx, j2 = bi * 32 + r;
+    B[r][tx] = (i2 < n && j2 < n) ? H[(size_t)j2 * n + i2] : 0.0;
+  }
+  __syncthreads();
+  double d2 = 0.0, h2 = 0.0;
+  for (int r = ty; r < 32; r += 8) {
+    const double a = A[r][tx];       // H(bi*32 + tx, bj*32 + r)
+    const double b = B[tx][r];       // H(bj*32 + r, bi*32 + tx)
+    d2 = fma(a - b, a - b, d2);
+    h2 = fma(a, a, h2);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+  }
+  if (tx == 0) {
+    atomicAdd(sums, d2);
+    atomicAdd(sums + 1, h2);
+  }
+}
+
+void launch_hess_asymmetry(opf_ctx* c, const double* H, int n, double* sums) {
+  const int nb = (n + 31) / 32;
+  hess_asym_kernel<<<dim3(nb, nb), 256, 0, c->stream>>>(H, n, sums);
+  c->launches++;
+}
+
+size_t hvp_plain_scratch(const opf_ctx* c) { return 4 * (size_t)c->dn.nx + (size_t)c->dn.ngn + 32; }
+
+int launch_hvp_plain(opf_ctx* c, double* H, int col0, int col_end, double* work) {
+  HvpArgs a = make_hvp_args(c, 1, H, col0, col_end, true);
+  const int nx = c->dn.nx;
+  double* bx = work;          // right-hand side, then R in x order
+  double* zx = bx + nx;       // Z, then Psi in x order
+  double* zp = zx + nx;       // Z, then Psi in pivot order
+  double* rp = zp + nx;       // R in pivot order
+  double* QD = rp + nx;
+  double* PD = QD + c->dn.ngn;
+  const int gb = std::max(1, std::min(nblk(nx, 256), 2 * c->sm_count));
+  const int gn = std::max(1, nblk(c->dn.ngn, 128)), gbus = std::max(1, nblk(c->dn.nb, 128));
+  const int* perm = c->dn.perm;
+  int launches = 0;
+  for (int j = col0; j < col_end; j++) {
+    cudaMemsetAsync(bx, 0, sizeof(double) * nx, c->stream);
+    plain_rhs_kernel<<<1, 32, 0, c->stream>>>(a, j, bx);
+    launch_solve1(c, bx, zx, false, 1.0);
+    plain_permute_kernel<<<gb, 256, 0, c->stream>>>(perm, zx, zp, nx, 1);
+    plain_qd_kernel<<<gn, 128, 0, c->stream>>>(a, j, zp, QD, PD);
+    plain_gather_kernel<<<gbus, 128, 0, c->stream>>>(a, j, zp, QD, PD, rp);
+    plain_permute_kernel<<<gb, 256, 0, c->stream>>>(perm, rp, bx, nx, 0);
+    launch_solve1(c, bx, zx, true, 1.0);
+    plain_permute_kernel<<<gb, 256, 0, c->stream>>>(perm, zx, zp, nx, 1);
+    plain_assemble_kernel<<<gn, 128, 0, c->stream>>>(a, j, zp);
+    launches += 9;
+  }
+  c->launches += 7LL * (col_end - col0);  // the two solves count themselves
+  return launches;
 }
 
 }  // namespace opf

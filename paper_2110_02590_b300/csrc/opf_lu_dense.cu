@@ -13,8 +13,10 @@
 // memory, one slot per row, so no slot is ever reused), then raises each
 // CTA's flag for step k + 1 with release semantics at cluster scope; the other
 // rows follow.  A CTA waits for a step's flag by polling its own shared memory
-// (acquire); each wait is bounded and, on timeout, sets the error flag and
-// goes on (the factor is then void and reported as singular).
+// (acquire); each wait is bounded (flags[2] spins, else 2^22) and, on timeout,
+// sets the timeout flag flags[1] and goes on, so that every CTA still reaches
+// the final cluster barrier (the factor is then void and the call reports
+// OPF_ETIMEOUT).
 
 #include "opf_internal.h"
 
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(kLuClusterThreads, 1)
       cl_sync();
     }
   }
+  const long long lim = flags[2] > 0 ? (long long)flags[2] : (1ll << 22);
   const int nr = (s + K - 1) / K;
   double* mine = dsm;                    // row q + K t at mine[t * s]
   double* piv = mine + (size_t)nr * s;   // row k at piv[k * s]
@@ -126,8 +129,8 @@ __global__ void __launch_bounds__(kLuClusterThreads, 1)
     if (tid == 0) {
       long long spins = 0;
       while (cl_acquire_u32(flag + k) != (unsigned)(k + 1)) {
-        if (++spins > (1ll << 22)) {
-          atomicExch(flags, 1);
+        if (++spins > lim) {
+          atomicExch(flags + 1, 1);
           break;
         }
       }

@@ -3,11 +3,11 @@
 // opf_reduced_hessian sizes its per-tile workspace on the first call and
 // allocates it with cudaMalloc.  Some callers cannot allow that: a real-time
 // control loop that must not stall on the allocator (cudaMalloc can
-// synchronise the whole device and its latency is unbounded), code that runs
-// while a stream is being captured, or a host process whose device-memory
-// budget is fixed once at start-up.  opf_reduced_hessian_noalloc computes the
-// same Hessian with the same tile kernel, but its workspace is the fixed
-// array below, so the call itself allocates nothing.
+// synchronise the whole device and its latency is unbounded), or a host
+// process whose device-memory budget is fixed once at start-up.
+// opf_reduced_hessian_noalloc computes the same Hessian with the same tile
+// kernel, but its workspace is the fixed array below, so the call itself
+// allocates nothing.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -69,16 +69,9 @@ extern "C" opf_status opf_reduced_hessian_noalloc(opf_ctx* c, const opf_al_param
     set_last_error("ctx and H are required");
     return OPF_EINVAL;
   }
-  if (!c->have_state) {
-    set_last_error("no converged power flow on this context");
-    return OPF_ESTATE;
-  }
-  {
-    const opf_status fs = ensure_factors(c);
-    if (fs != OPF_OK) return fs;
-  }
-  if (!p || !p->sigma_c || !p->y || !p->s || !(p->rho >= 0.0)) {
-    set_last_error("AL parameters need sigma_c, y, s and rho >= 0");
+  if (o && (o->plain || o->threads || o->reuse_first_order)) {
+    set_last_error("opf_reduced_hessian_noalloc supports block_k, grid and the column range only "
+                   "(plain, threads and reuse_first_order must be 0)");
     return OPF_EINVAL;
   }
   const int C = (o && o->block_k) ? o->block_k : 8;
@@ -93,12 +86,25 @@ extern "C" opf_status opf_reduced_hessian_noalloc(opf_ctx* c, const opf_al_param
     set_last_error("column range outside [0, n_u)");
     return OPF_EINVAL;
   }
+  // the size limit depends on the network and block_k only
   const size_t stride = hvp_stride(c, C);
   if (stride > kScratchDoubles) {
     set_last_error("one tile of this network needs " + std::to_string(stride * sizeof(double)) +
                    " bytes of workspace, more than the " + std::to_string(kScratchBytes) +
                    "-byte static workspace; use a smaller block_k or opf_reduced_hessian");
     return OPF_EINVAL;
+  }
+  if (!c->have_state) {
+    set_last_error("no converged power flow on this context");
+    return OPF_ESTATE;
+  }
+  {
+    const opf_status fs = ensure_factors(c);
+    if (fs != OPF_OK) return fs;
+  }
+  {
+    const opf_status ps = check_al(c, p);
+    if (ps != OPF_OK) return ps;
   }
   double* scratch = nullptr;
   opf_status st = scratch_for_device(c->device, &scratch);
@@ -124,6 +130,8 @@ extern "C" opf_status opf_reduced_hessian_noalloc(opf_ctx* c, const opf_al_param
     info->grid = grid;
     info->tiles = ntiles;
     info->launches = 1;
+    info->asymmetry = -1.0;
+    for (int k = 0; k < 5; k++) info->phase_ms[k] = 0.f;
     cudaEventElapsedTime(&info->ms_total, c->ev[0], c->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c->ev[1], c->ev[2]);
   }

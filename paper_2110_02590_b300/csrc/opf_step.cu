@@ -38,6 +38,11 @@ struct StepWork {
   unsigned* trsv_flags = nullptr;  // [ceil(n_u / 32)] block flags of the dense solves (epochs)
   int* trsv_err = nullptr;         // a dense-solve wait timed out
   unsigned trsv_epoch = 0;
+  // tracking QP (opf_tracking_update): grad q, the linearisation point w_t and its
+  // state, the KKT reductions and the constraint values at the new point
+  void* qp_block = nullptr;
+  double *gqu = nullptr, *gqs = nullptr, *u0 = nullptr, *s0 = nullptr, *x0 = nullptr, *kred = nullptr,
+         *cv = nullptr, *h_kred = nullptr;
 };
 
 void free_step_work(opf_ctx* c) {
@@ -49,6 +54,8 @@ void free_step_work(opf_ctx* c) {
   if (w->aux) cudaStreamDestroy(w->aux);
   if (w->oz_e) cudaFree(w->oz_e);
   if (w->oz_d) cudaFree(w->oz_d);
+  if (w->qp_block) cudaFree(w->qp_block);
+  if (w->h_kred) cudaFreeHost(w->h_kred);
   if (w->h_red) cudaFreeHost(w->h_red);
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
@@ -277,10 +284,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void wait_block(const unsigned* flag, unsigned epoch, int* err, int lane) {
+__device__ __forceinline__ void wait_block(const unsigned* flag, unsigned epoch, int* err, int lane,
+                                           long long lim) {
   long long spins = 0;
   while (ld_acquire_u32(flag) != epoch) {
-    if (++spins > (1ll << 24) || *(volatile int*)err) {
+    if (++spins > lim || *(volatile int*)err) {
       if (lane == 0) atomicExch(err, 1);
       break;
     }
@@ -308,7 +316,8 @@ __global__ void chol_upper_copy_kernel(double* A, int n) {
 template <bool FWD>
 __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict__ L, int n,
                                                         const double* __restrict__ Dinv, double* b,
-                                                        unsigned* flags, unsigned epoch, int* err) {
+                                                        unsigned* flags, unsigned epoch, int* err,
+                                                        long long lim) {
   __shared__ double part[8][32];
   __shared__ double accs[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict
       double t[32];
 #pragma unroll
       for (int c = 0; c < 32; c++) t[c] = (live && c < kc) ? L[(size_t)(col0 + c) * n + row] : 0.0;
-      wait_block(flags + k, epoch, err, lane);
+      wait_block(flags + k, epoch, err, lane, lim);
       const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
 #pragma unroll
       for (int c = 0; c < 32; c += 4) {
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(256) chol_trsv_kernel(const double* __restrict
         const int c = 4 * warp + cc;
         t4[cc] = (live && c < kc) ? L[(size_t)(col0 + c) * n + row] : 0.0;
       }
-      wait_block(flags + k, epoch, err, lane);
+      wait_block(flags + k, epoch, err, lane, lim);
       const double xk = (col0 + lane < n) ? __ldcg(b + col0 + lane) : 0.0;
       p0 = fma(t4[0], __shfl_sync(0xffffffffu, xk, 4 * warp), p0);
       p1 = fma(t4[1], __shfl_sync(0xffffffffu, xk, 4 * warp + 1), p1);
@@ -599,6 +608,29 @@ __global__ void update_kernel(int nu, int m, double* u, const double* du, double
   }
 }
 
+// QP gradient after a step of the tracking QP (Sec. IV-C): the Hessian is
+// constant, and the Newton system (H + Sigma) d = -grad psi gives H d =
+// -grad psi - Sigma d, so grad q <- grad q + alpha (-grad psi - Sigma d).
+__global__ void qp_grad_update_kernel(int nu, int m, double* gqu, double* gqs, const double* gpsi_u,
+                                      const double* gpsi_s, const double* sig_u, const double* sig_s,
+                                      const double* du, const double* ds, double alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nu) gqu[i] += alpha * (-gpsi_u[i] - sig_u[i] * du[i]);
+  if (i < m) gqs[i] += alpha * (-gpsi_s[i] - sig_s[i] * ds[i]);
+}
+
+// out[i] += a (x[i] - x0[i])  (the u-block regularisation delta enters grad q as delta (u - u_t))
+__global__ void add_scaled_diff_kernel(int n, double* out, double a, const double* x, const double* x0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += a * (x[i] - x0[i]);
+}
+
+// w <- w0 + alpha (w - w0)  (a shortened tracking step)
+__global__ void shrink_kernel(int n, double* w, const double* w0, double alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = w0[i] + alpha * (w[i] - w0[i]);
+}
+
 #define SCK(call)                                                                   \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \
@@ -724,8 +756,9 @@ opf_status launch_chol_solve(opf_ctx* c, StepWork* w, double* A, int n, double* 
   for (int dir = 0; dir < 2; dir++) {
     unsigned epoch = ++w->trsv_epoch;
     const double* Dv = w->Dinv;
+    long long lim = c->wait_limit > 0 ? (long long)c->wait_limit : (1ll << 24);
     void* args[] = {(void*)&A, (void*)&n, (void*)&Dv, (void*)&b, (void*)&w->trsv_flags, (void*)&epoch,
-                    (void*)&w->trsv_err};
+                    (void*)&w->trsv_err, (void*)&lim};
     SCK(cudaLaunchCooperativeKernel(dir == 0 ? (const void*)chol_trsv_kernel<true> : (const void*)chol_trsv_kernel<false>,
                                     dim3(grid), dim3(256), args, 0, c->stream));
     c->launches++;
@@ -854,8 +887,9 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   SCK(cudaStreamSynchronize(stream));
   SCK(cudaGetLastError());
   if (*w->h_flag) {
-    set_last_error("dense triangular solve: a block wait timed out");
-    return OPF_ECUDA;
+    SCK(cudaMemsetAsync(w->trsv_err, 0, sizeof(int), stream));  // the next call starts clean
+    set_last_error("dense triangular solve: a bounded block wait gave up");
+    return OPF_ETIMEOUT;
   }
   double ap = w->h_red[0];
   const double ad = w->h_red[1];
@@ -908,6 +942,235 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     cudaEventElapsedTime(&ms, e0, e1);
     info->ms_total = ms;
     info->du_inf = info->ds_inf = 0.0;
+  }
+  return OPF_OK;
+}
+
+// ---------------------------------------------------------------- tracking QP
+
+namespace {
+
+opf_status alloc_qp(opf_ctx* c, StepWork* w) {
+  if (w->qp_block) return OPF_OK;
+  const size_t nu = c->h.nu, m = c->h.m, nx = c->h.nx;
+  const size_t n = 2 * (nu + 32) + 3 * (m + 32) + nx + 32 + 8;
+  if (cudaMalloc(&w->qp_block, n * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&w->h_kred, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (w->qp_block) cudaFree(w->qp_block);
+    w->qp_block = nullptr;
+    set_last_error("cannot allocate the tracking QP workspace");
+    return OPF_ENOMEM;
+  }
+  double* q = static_cast<double*>(w->qp_block);
+  auto take = [&](size_t k) {
+    double* r = q;
+    q += (k + 31) & ~(size_t)31;
+    return r;
+  };
+  w->gqu = take(nu);
+  w->u0 = take(nu);
+  w->gqs = take(m);
+  w->s0 = take(m);
+  w->cv = take(m);
+  w->x0 = take(nx);
+  w->kred = take(8);
+  return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, double* y, opf_al_state* st,
+                                          const opf_qp_opts* o, opf_qp_info* info) {
+  if (!c || !p || !y || !st || !p->sigma_c || !st->u || !st->s || !st->zl_u || !st->zu_u || !st->zl_s ||
+      !st->zu_s || !st->u_lo || !st->u_hi || !st->s_lo || !st->s_hi || !st->x) {
+    set_last_error("ctx, params (with sigma_c), y and every state array are required");
+    return OPF_EINVAL;
+  }
+  if (!c->have_state) {
+    set_last_error("no converged power flow on this context");
+    return OPF_ESTATE;
+  }
+  if (!(p->rho > 0.0) || !(st->mu > 0.0)) {
+    set_last_error("opf_tracking_update needs rho > 0 and mu > 0");
+    return OPF_EINVAL;
+  }
+  {
+    const opf_status fs = ensure_factors(c);
+    if (fs != OPF_OK) return fs;
+  }
+  opf_status rc = alloc_step(c);
+  if (rc) return rc;
+  StepWork* w = c->stepw;
+  rc = alloc_qp(c, w);
+  if (rc) return rc;
+  const int nu = c->h.nu, m = c->h.m, nx = c->h.nx, nb = c->h.nb;
+  const int max_it = (o && o->max_it > 0) ? o->max_it : 50;
+  const double tol = (o && o->tol > 0.0) ? o->tol : 1e-6;
+  const int block_k = o ? o->block_k : 0;
+  const int max_halvings = (o && o->max_halvings) ? o->max_halvings : 10;
+  const int max_inertia = (o && o->max_inertia) ? o->max_inertia : 24;
+  cudaStream_t stream = c->stream;
+  cudaEvent_t* ev = w->ev;
+  if (!ev[0])
+    for (int k = 0; k < 7; k++) SCK(cudaEventCreate(&ev[k]));
+  SCK(cudaEventRecord(ev[0], stream));
+  const int gb = nblk(std::max(nu, m), 256);
+  // the linearisation point w_t, its state, and g_t = grad L_rho(w_t; y) = grad q(0)
+  opf_al_params pt = *p;
+  pt.y = y;
+  pt.s = st->s;
+  pt.omega = nullptr;
+  rc = opf_reduced_gradient(c, &pt, nullptr, w->gqu, w->gqs, nullptr, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  SCK(cudaMemcpyAsync(w->u0, st->u, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaMemcpyAsync(w->s0, st->s, m * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaMemcpyAsync(w->x0, st->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  pt.s = w->s0;  // the Hessian's first-order weights stay those of w_t
+  double mu = st->mu, delta = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
+  double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0;
+  float ms_hess = 0.f, ms_chol = 0.f;
+  int it = 0, increases = 0;
+  for (it = 0;; it++) {
+    SCK(cudaMemsetAsync(w->kred, 0, 4 * sizeof(double), stream));
+    launch_al_kkt(c, w->gqu, w->gqs, st, nullptr, nullptr, mu, w->kred);
+    SCK(cudaMemcpyAsync(w->h_kred, w->kred, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    e_mu = std::max(w->h_kred[0], w->h_kred[1]);
+    e_0 = std::max(w->h_kred[0], w->h_kred[2]);
+    if (e_0 <= tol || it == max_it) break;
+    if (e_mu <= 10.0 * mu) mu = std::max(tol / 10.0, std::min(0.2 * mu, std::pow(mu, 1.5)));
+    step_prep_kernel<<<gb, 256, 0, stream>>>(nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo,
+                                             st->s_hi, st->zl_s, st->zu_s, w->gqu, w->gqs, p->sigma_c, p->rho, mu,
+                                             w->sig_u, w->gpsi_u, w->sig_s, w->gpsi_s, w->omega, w->v);
+    c->launches++;
+    // S = H(omega) + Sigma_u at the fixed linearisation point (eq. schur_matrix)
+    opf_al_params ps = pt;
+    ps.omega = w->omega;
+    opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0, 0};
+    opf_hess_info hi;
+    rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
+    if (rc) return rc;
+    ms_hess += hi.ms_total;
+    sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
+    // r = -grad_u psi - J^T v
+    launch_weighted_grad(c, w->v, w->Jtv);
+    neg_sum_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, w->Jtv, w->r);
+    c->launches += 2;
+    // Cholesky; the QP's u-block regularisation delta only grows
+    SCK(cudaEventRecord(ev[1], stream));
+    const double d_old = delta;
+    for (int tries = 0;; tries++) {
+      add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
+      SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
+      c->launches++;
+      rc = launch_cholesky(c, w, w->L, nu, w->flag);
+      if (rc) return rc;
+      SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      SCK(cudaStreamSynchronize(stream));
+      if (!*w->h_flag) break;
+      if (tries >= max_inertia) {
+        set_last_error("tracking QP: S_uu not positive definite after the inertia corrections");
+        return OPF_ENOTPD;
+      }
+      delta = (delta > 0.0) ? 10.0 * delta : 1e-8;
+      increases++;
+    }
+    SCK(cudaEventRecord(ev[2], stream));
+    {
+      float t = 0.f;
+      cudaEventSynchronize(ev[2]);
+      cudaEventElapsedTime(&t, ev[1], ev[2]);
+      ms_chol += t;
+    }
+    if (delta != d_old) {  // the QP's Hessian gained (delta - d_old) I on the u-block
+      const double dd = delta - d_old;
+      add_scaled_diff_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gqu, dd, st->u, w->u0);
+      add_scaled_diff_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->gpsi_u, dd, st->u, w->u0);
+      add_scaled_diff_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, w->r, -dd, st->u, w->u0);
+      c->launches += 3;
+    }
+    SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    rc = launch_chol_solve(c, w, w->L, nu, w->du);
+    if (rc) return rc;
+    // J d_u
+    gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
+    c->launches++;
+    launch_solve1(c, w->b, w->z, false, -1.0);
+    jvp_branch_kernel<<<nblk(c->dn.nl, 256), 256, 0, stream>>>(c->dn, c->btab, c->flows, w->z, w->du, w->Jdu);
+    jvp_bus_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->z, w->du, w->Jdu);
+    c->launches += 2;
+    const double tau = std::max(0.99, 1.0 - mu);
+    const double one = 1.0;
+    SCK(cudaMemcpyAsync(w->red, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+    SCK(cudaMemcpyAsync(w->red + 1, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+    step_finish_kernel<<<gb, 256, 0, stream>>>(nu, m, st->u, w->du, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s,
+                                               st->s_lo, st->s_hi, st->zl_s, st->zu_s, w->gpsi_s, w->sig_s, w->Jdu,
+                                               p->sigma_c, p->rho, mu, tau, w->ds, w->dz, w->red);
+    c->launches++;
+    SCK(cudaMemcpyAsync(w->h_red, w->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaMemcpyAsync(w->h_flag, w->trsv_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    if (*w->h_flag) {
+      SCK(cudaMemsetAsync(w->trsv_err, 0, sizeof(int), stream));
+      set_last_error("dense triangular solve: a bounded block wait gave up");
+      return OPF_ETIMEOUT;
+    }
+    ap = w->h_red[0];
+    ad = w->h_red[1];
+    update_kernel<<<gb, 256, 0, stream>>>(nu, m, st->u, w->du, st->s, w->ds, st->zl_u, st->zu_u, st->zl_s, st->zu_s,
+                                          w->dz, ap, ad);
+    qp_grad_update_kernel<<<gb, 256, 0, stream>>>(nu, m, w->gqu, w->gqs, w->gpsi_u, w->gpsi_s, w->sig_u, w->sig_s,
+                                                  w->du, w->ds, ap);
+    c->launches += 2;
+  }
+  SCK(cudaEventRecord(ev[3], stream));
+  // w_{t+1}: the power flow at the QP's controls (loads of the current state), the
+  // step toward it halved until it converges
+  SCK(cudaMemcpyAsync(w->pd, c->pd, nb * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  SCK(cudaMemcpyAsync(w->qd, c->qd, nb * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  int halvings = 0;
+  opf_pf_info pfi = {0, 0.0, 0.0};
+  for (;;) {
+    SCK(cudaMemcpyAsync(w->xt, w->x0, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    const opf_status prc = opf_powerflow(c, st->u, w->pd, w->qd, w->xt, nullptr, &pfi);
+    if (prc == OPF_OK) break;
+    if (prc != OPF_ENOCONV && prc != OPF_ESINGULAR) return prc;
+    if (halvings >= max_halvings) {
+      set_last_error("tracking update: no control toward the QP solution with a converged power flow");
+      return OPF_ENOCONV;
+    }
+    shrink_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, st->u, w->u0, 0.5);
+    shrink_kernel<<<nblk(m, 256), 256, 0, stream>>>(m, st->s, w->s0, 0.5);
+    c->launches += 2;
+    halvings++;
+  }
+  SCK(cudaMemcpyAsync(st->x, w->xt, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  // y_{t+1} = y_t + rho D_c (c_t(u_{t+1}) - s_{t+1})
+  opf_al_params pn = *p;
+  pn.y = y;
+  pn.s = st->s;
+  pn.omega = nullptr;
+  rc = opf_reduced_gradient(c, &pn, nullptr, nullptr, nullptr, w->cv, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  launch_al_dual_update(c, y, p->rho, p->sigma_c, w->cv, st->s);
+  SCK(cudaEventRecord(ev[4], stream));
+  SCK(cudaStreamSynchronize(stream));
+  SCK(cudaGetLastError());
+  st->mu = mu;
+  if (info) {
+    info->qp_iterations = it;
+    info->halvings = halvings;
+    info->pf_iterations = pfi.iterations;
+    info->inertia_increases = increases;
+    info->delta = delta;
+    info->kkt = e_0;
+    info->mu = mu;
+    info->alpha_p = ap;
+    info->ms_hessian = ms_hess;
+    info->ms_cholesky = ms_chol;
+    cudaEventElapsedTime(&info->ms_total, ev[0], ev[4]);
+    cudaEventElapsedTime(&info->ms_qp, ev[0], ev[3]);
   }
   return OPF_OK;
 }

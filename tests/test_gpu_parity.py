@@ -128,13 +128,31 @@ def test_hessian_parity_tiny_all_tiles(block_k):
 
 
 def test_hessian_plain_equals_batched():
+    """The plain form (one direction per launch sequence: device-wide kernels around two
+    streamed single-RHS solves, 9 kernels per column) against the oracle and the tiles."""
     c = case("tiny30")
     Hp, ip = c.ctx.reduced_hessian(c.al_dev, block_k=1, plain=True)
     Hb, _ = c.ctx.reduced_hessian(c.al_dev, block_k=8)
     Ho = c.on.reduced_hessian(c.x_orc, c.u, c.al)
-    assert ip["launches"] == c.on.nu
+    assert ip["launches"] == 9 * c.on.nu and ip["block_k"] == 1 and ip["tiles"] == c.on.nu
     assert rel_fro(Hp.cpu().numpy(), Ho) < HESS_TOL
     assert rel_fro(Hp.cpu().numpy(), Hb.cpu().numpy()) < 1e-12
+
+
+@pytest.mark.parametrize("name,col0,ncol", [("medium1400", 0, 40), ("large9200", 1500, 24)])
+def test_hessian_plain_columns_match_tiles(name, col0, ncol):
+    """Plain-form columns on the larger grids (the streamed solves, the dense trailing
+    triangles and the PV/slack cases of the gathers) equal the tiled Hessian's; the other
+    columns of the output are left untouched."""
+    c = case(name)
+    Hb, _ = c.ctx.reduced_hessian(c.al_dev, block_k=8)
+    Hb = Hb.cpu().numpy()
+    out = torch.full((c.ctx.nu, c.ctx.nu), 7.0, dtype=torch.float64, device=DEV)
+    Hp, ip = c.ctx.reduced_hessian(c.al_dev, plain=True, col_begin=col0, col_count=ncol, out=out)
+    Hp = Hp.cpu().numpy()
+    cols = slice(col0, col0 + ncol)
+    assert rel_fro(Hp[:, cols], Hb[:, cols]) < 1e-11
+    assert np.all(np.delete(Hp, np.arange(col0, col0 + ncol), axis=1) == 7.0)
 
 
 @pytest.mark.parametrize("name,block_k,grid", [("medium1400", 8, 0), ("medium1400", 16, 37),
