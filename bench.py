@@ -24,10 +24,12 @@ import subprocess
 import sys
 import time
 
-if "--cpu-step" in sys.argv or "reference" in sys.argv:
-    # the CPU oracle legs run single-threaded: pin the BLAS pools before numpy loads
-    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[_v] = "1"
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+if "reference" in sys.argv:
+    # the reference arm (the CPU oracle) runs on all host cores: the oracle's Hessian columns
+    # over OpenMP threads, the dense algebra on the BLAS pool; set before numpy loads
+    for _v in THREAD_VARS:
+        os.environ[_v] = str(os.cpu_count() or 1)
 
 import numpy as np  # noqa: E402
 
@@ -39,11 +41,14 @@ from paper_2110_02590_b300 import synth  # noqa: E402
 WORKLOAD = "large9200"
 METRIC = "HVPs/s and ms per full reduced Hessian (9.2k-bus, FP64); batched vs plain"
 UNIT = "HVP/s"
-FP64_PEAK_TFLOPS = 1.25        # B300 FP64 (vector and tensor) nominal rate of the pool's recipe
-# DRAM bytes (read + write) of one hvp_split_kernel<8, 256> launch on the 9.2k grid,
-# from the ncu capture summarised in profiles/hvp_split_kernel_large9200.md
-HVP_SPLIT_TRAFFIC_9200 = 8.10e9
 HBM_FALLBACK_GBS = 6400.0
+# The ncu summary of the dominant kernel; its machine-readable lines give the DRAM
+# traffic of one launch and the hash of the kernel sources it was captured with.
+HVP_PROFILE = os.path.join(ROOT, "profiles", "hvp_split_kernel_large9200.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2110_02590_b300", "csrc", f)
+                  for f in ("opf_kernels.cu", "opf_internal.h")]
+# (block_k, threads) candidates of the library's autotuner (opf_hessian_autotune)
+AUTOTUNE_CANDIDATES = [(4, 128), (4, 256), (8, 128), (8, 256), (8, 512), (16, 256), (16, 512), (32, 256)]
 
 
 def peaks():
@@ -53,6 +58,36 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """(DRAM bytes per launch, note) from the committed ncu summary of the HVP kernel, or
+    (None, why) when the summary is missing or was captured from other kernel sources."""
+    try:
+        with open(HVP_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None, "no ncu summary"
+    vals = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256",
+                                                "kernel_launch")):
+            k, v = ln.strip().split(":", 1)
+            vals[k.strip()] = v.strip()
+    if "traffic_bytes_per_launch" not in vals or "kernel_source_sha256" not in vals:
+        return None, "ncu summary without machine-readable traffic"
+    if vals["kernel_source_sha256"] != kernel_source_hash():
+        return None, "kernel sources changed since the ncu capture"
+    return float(vals["traffic_bytes_per_launch"]), "ncu capture of " + vals.get("kernel_launch", "the kernel")
 
 
 def parse():
@@ -65,6 +100,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the tracking-QP and static-OPF legs")
+    ap.add_argument("--autograd-scenarios", type=int, default=256)
     ap.add_argument("--profile-step", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--cpu-step", action="store_true", help="internal: time one oracle tracking step")
@@ -151,15 +189,28 @@ def oracle_tracking(net, nsteps, seed=100):
     return times
 
 
-def run_cpu_baseline(net):
-    """One oracle tracking step, in a child process whose BLAS pools are pinned to one thread."""
+def cpu_step_seconds(threads):
+    """One oracle tracking step in a child process whose OpenMP and BLAS pools have `threads`."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        env[v] = str(threads)
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-step"], capture_output=True,
-                         text=True, check=True)
-    t = float(out.stdout.strip().splitlines()[-1])
+                         text=True, check=True, env=env)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def run_cpu_baseline(net):
+    """The oracle's tracking step on all host cores (Hessian columns over OpenMP threads, dense
+    algebra on the BLAS pool) and on one core."""
     nu = 1 + 2 * (net.n_gen - 1)
-    return {"value": nu / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one tracking step of the same workload ({t:.1f} s): power flow at new loads and one "
-                      "reduced-Newton step with all Hessian columns; FP64 C oracle, BLAS limited to 1 thread"}
+    cores = os.cpu_count() or 1
+    t_all = cpu_step_seconds(cores)
+    t_one = cpu_step_seconds(1)
+    return {"value": nu / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one tracking step of the same workload ({t_all:.2f} s on {cores} threads): power flow at "
+                      "new loads and one reduced-Newton step with all Hessian columns; FP64 C oracle, columns "
+                      "over OpenMP threads",
+            "single_core": {"value": nu / t_one, "unit": UNIT, "cores": 1, "seconds": t_one}}
 
 
 def run_reference(args):
@@ -175,9 +226,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(nu),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "every step of the tracking loop, full Hessian, FP64 C oracle, "
-                                       "BLAS limited to 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": "every step of the tracking loop, full Hessian, FP64 C oracle, Hessian "
+                                       "columns over OpenMP threads on all host cores"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -252,6 +303,123 @@ def hbm_bytes_per_hessian(sym, nx, nu, k):
     return blocks * (24 * nnz_lu + 64 * nx * k)
 
 
+def solve_phase(sym, nx, nu, k, hvp_ms, share, hbm_peak, fp64_tf):
+    """Roofline of the triangular-solve phase of the HVP kernel: the three full sweeps (U for Z;
+    U^T, L^T for Psi) over the kernel time apportioned to them by the tiles' phase stamps.  Bytes:
+    12 B per factor entry each sweep reads (value + column index) and 16 n_x k (read + write of the
+    right-hand side) per sweep and block of k directions; flops: 2 per strictly triangular entry
+    and direction, plus the diagonal scaling of U and U^T.  The pruned first L solve is left out
+    of time, bytes and flops alike."""
+    nnz_strict = (len(sym["colidx"]) - nx) // 2
+    blocks = -(-nu // k)
+    t_ms = hvp_ms * (share[1] + share[3])
+    byts = blocks * (12 * (3 * nnz_strict + 2 * nx) + 3 * 16 * nx * k)
+    flops = nu * (6 * nnz_strict + 2 * nx)
+    gbs = byts / (t_ms * 1e-3) / 1e9
+    tfs = flops / (t_ms * 1e-3) / 1e12
+    return {"ms": t_ms, "bytes": byts, "flops": flops, "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+            "achieved_tflops": tfs, "fp64_frac": tfs / fp64_tf,
+            "intensity_flop_per_byte": flops / byts, "fp64_ridge_flop_per_byte": fp64_tf * 1e3 / hbm_peak,
+            "hbm_frac_ceiling_at_fp64_peak": (fp64_tf * 1e3 / hbm_peak) / (flops / byts)}
+
+
+def autograd_batch(P, torch, dev, nscen):
+    """Config 4: ReducedObjective (torch.autograd.Function, adjoint backward with the power flows
+    recomputed) on a batch of AR(1) load scenarios of the 2,000-bus net, forward + backward,
+    beside the plain calls (opf_powerflow + opf_reduced_gradient per scenario, no autograd)."""
+    from paper_2110_02590_b300.autograd import ReducedObjective
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
+    net = synth.workload("batchB2000")
+    ctx = P.OPFContext(net, device=dev.index)
+    al = synth.al_inputs(net, seed=7)
+    ald = {k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+    obj = ReducedObjective(ctx, ald)
+    x0, _ = ctx.powerflow(d(synth.flat_control(net)))
+    obj.set_warm_start(x0)
+    pds, qds = synth.ar1_loads(net, nscen, seed=300)
+    u = d(np.tile(synth.flat_control(net), (nscen, 1))).requires_grad_(True)
+    pd, qd = d(pds).requires_grad_(True), d(qds).requires_grad_(True)
+    s = d(np.tile(al["s"], (nscen, 1))).requires_grad_(True)
+    obj(u[:2], pd[:2], qd[:2], s[:2]).sum().backward()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = obj(u, pd, qd, s)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    F.sum().backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for b in range(nscen):  # plain calls: one power flow and one adjoint gradient per scenario
+        ctx.powerflow(u[b].detach(), pd=pd[b].detach(), qd=qd[b].detach(), x0=x0)
+        ctx.reduced_gradient(dict(ald, s=s[b].detach()))
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    return {"net": "2,000-bus synthetic grid", "scenarios": nscen, "ms_forward": 1e3 * (t1 - t0),
+            "ms_backward": 1e3 * (t2 - t1), "scenarios_per_s": nscen / (t2 - t0),
+            "plain_ms": 1e3 * (t3 - t2), "plain_scenarios_per_s": nscen / (t3 - t2),
+            "note": "forward: power flow + F per scenario; backward: power flow recomputed + adjoint gradient "
+                    "w.r.t. u, loads and s; plain: power flow + adjoint gradient per scenario"}
+
+
+def static_opf(P, torch, dev, name, max_outer, max_inner=10, rate_factor=1.5):
+    """Static OPF by the augmented-Lagrangian loop (opf_al_solve) on a synthetic grid at its
+    nominal loads: line limits widened rate_factor x (at 1.2x the base-case DC flows the AC flows
+    already exceed them), y = 0, rho = 10, an interior start at mu = 0.1."""
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
+    net = synth.workload(name)
+    ctx = P.OPFContext(net, device=dev.index)
+    u_lo, u_hi = synth.control_bounds(net)
+    u = np.clip(synth.flat_control(net), u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
+    al = synth.al_inputs(net, seed=5)
+    nl = net.n_branch
+    al["s_hi"][:2 * nl] *= rate_factor ** 2
+    al["sigma_c"][:2 * nl] /= rate_factor ** 2
+    x, _ = ctx.powerflow(d(u))
+    c = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})["c"]
+    lo, hi = al["s_lo"], al["s_hi"]
+    s = np.clip(c.cpu().numpy(), lo + 0.01 * (hi - lo), hi - 0.01 * (hi - lo))
+    mu = 0.1
+    state = dict(u=d(u), s=d(s), x=x, u_lo=d(u_lo), u_hi=d(u_hi), s_lo=d(lo), s_hi=d(hi), mu=mu,
+                 zl_u=d(mu / (u - u_lo)), zu_u=d(mu / (u_hi - u)), zl_s=d(mu / (s - lo)), zu_s=d(mu / (hi - s)))
+    y = d(np.zeros(ctx.m))
+    info, hist = ctx.al_solve(dict(sigma_f=al["sigma_f"], rho=10.0, sigma_c=d(al["sigma_c"])), state, y,
+                              max_outer=max_outer, max_inner=max_inner)
+    steps = max(1, info["steps"])
+    return {"net": name, "n_u": ctx.nu, "outer": info["outer"], "steps": info["steps"],
+            "converged": bool(info["converged"]), "ms_total": info["ms_total"],
+            "ms_per_outer": info["ms_total"] / max(1, info["outer"]), "ms_per_step": info["ms_total"] / steps,
+            "primal_inf": info["primal_inf"], "dual_inf": info["dual_inf"], "rho_final": info["rho"],
+            "steps_per_outer": [int(h[0]) for h in hist],
+            "setup": f"nominal loads, line limits x{rate_factor}, y0 = 0, rho0 = 10, mu0 = 0.1, "
+                     f"at most {max_inner} reduced-Newton steps per subproblem (one full Hessian each)"}
+
+
+def tracking_qp(P, torch, ctx, al, state, pds, qds, first, count):
+    """Real-time updates (opf_tracking_update): power flow at the next load snapshot, then the
+    bounded QP of eq. qp_rto to a KKT error of 1e-6 with one Hessian H(omega) per QP iteration,
+    the power flow at the new controls and the multiplier update."""
+    y = al["y"].clone()
+    out = []
+    dstart = 0.0
+    for k in range(count):
+        state["x"], _ = ctx.powerflow(state["u"], pd=pds[first + k], qd=qds[first + k], x0=state["x"])
+        state["mu"] = 1e-2
+        info = ctx.tracking_update(al, state, y, delta_start=dstart)
+        dstart = info["delta_convex"] / 10.0 if info["delta_convex"] >= 1e-7 else 0.0
+        out.append(info)
+    it = [i["qp_iterations"] for i in out]
+    ms = [i["ms_total"] for i in out]
+    return {"updates": count, "qp_iterations": it, "ms_per_update": statistics.median(ms),
+            "ms_hessians_per_update": statistics.median(i["ms_hessian"] for i in out),
+            "ms_cholesky_per_update": statistics.median(i["ms_cholesky"] for i in out),
+            "hvps_per_update": statistics.median(it) * ctx.nu,
+            "ms_per_qp_iteration": statistics.median(i["ms_qp"] / max(1, i["qp_iterations"]) for i in out),
+            "kkt": max(i["kkt"] for i in out), "delta": [i["delta"] for i in out],
+            "delta_convex": [i["delta_convex"] for i in out],
+            "note": "QP barrier starts at mu = 1e-2 each update; stops at E_0 <= 1e-6; the QP is convexified "
+                    "(H_uu + delta I positive definite; the search starts at a tenth of the previous update's delta)"}
+
+
 def batched_snapshots(P, torch, dev, block_k):
     """Config-3 batch: 128 x 500-bus, 64 x 2,000-bus and 16 x 9,200-bus snapshots, each at its own
     AR(1) load and power flow; all Hessians in one persistent launch vs one call per snapshot."""
@@ -299,6 +467,7 @@ def run_gpu(args):
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
 
     net = synth.workload(WORKLOAD)
+    fp64_tf, fp64_ms = P.fp64_peak()  # the FP64 roofline's denominator, measured on this GPU
     ctx = P.OPFContext(net, device=local)
     nu, nx = ctx.nu, ctx.nx
     sym = ctx.symbolic()
@@ -315,7 +484,7 @@ def run_gpu(args):
     state["x"], _ = ctx.powerflow(state["u"], x0=x0)
     tune = ctx.autotune(dict(al, s=state["s"]))
     ke = max(1, min(args.steps, args.e2e_steps))  # end-to-end steps, on the snapshots after the timed ones
-    nsnap = args.warmup + args.steps + 1 + ke
+    nsnap = args.warmup + args.steps + 1 + ke + 3  # the last three: the tracking-QP leg
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
     pds, qds = d(pds_h), d(qds_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -362,15 +531,26 @@ def run_gpu(args):
             hs.append((hinfo["ms_total"], hinfo["ms_hvp"]))
     hess_ms = statistics.median(h[0] for h in hs)
     hvp_ms = statistics.median(h[1] for h in hs)
-    # plain form (k = 1, one direction per launch) on a column sample
+    # the HVP time by tile phase (one extra call with per-tile timer stamps), and the asymmetry
+    flush.zero_()
+    _, prof = ctx.reduced_hessian(alh, phase_profile=True, asymmetry=True)
+    ph = prof["phase_ms"]
+    share = [v / max(sum(ph), 1e-30) for v in ph]
+    # plain form (k = 1, one direction per launch sequence: device-wide kernels around two
+    # streamed single-RHS solves) on a column sample from the middle of the controls
     pc = max(1, min(args.plain_cols, nu))
-    _, pinfo = ctx.reduced_hessian(alh, block_k=1, plain=True, col_begin=0, col_count=pc)
+    pc0 = max(0, nu // 2 - pc // 2)
+    ctx.reduced_hessian(alh, plain=True, col_begin=pc0, col_count=min(pc, 4))  # warm-up
+    _, pinfo = ctx.reduced_hessian(alh, plain=True, col_begin=pc0, col_count=pc)
     plain_ms_per_col = pinfo["ms_hvp"] / pc
 
     flops = hvp_flops_per_column(sym, nx, net.n_branch) * nu
     achieved_tf = flops / (hvp_ms * 1e-3) / 1e12
     hbm_peak, hbm_kind = peaks()
     hbm_b = hbm_bytes_per_hessian(sym, nx, nu, tune["block_k"])
+    solve = solve_phase(sym, nx, nu, tune["block_k"], hvp_ms, share, hbm_peak, fp64_tf)
+    traffic, traffic_note = profiled_traffic()
+    auto = None if args.no_autograd else autograd_batch(P, torch, dev, args.autograd_scenarios)
 
     # end to end: loads in from pinned host memory, the new controls and slacks out, per step
     host_pd = torch.as_tensor(pds_h).pin_memory()
@@ -393,6 +573,27 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / ks
 
     batch = None if args.no_batch else batched_snapshots(P, torch, dev, tune["block_k"])
+    sharded = None
+    if world > 1:  # one Hessian split by column ranges over the ranks, one all-gather of H
+        from paper_2110_02590_b300 import partition
+        Hbuf = torch.empty((nu, nu), dtype=torch.float64, device=dev)
+
+        def cols(b, n):
+            ctx.reduced_hessian(alh, block_k=tune["block_k"], col_begin=b, col_count=n, out=Hbuf)
+            return Hbuf[b:b + n]
+        partition.sharded_hessian(cols, nu, tune["block_k"])  # warm-up
+        torch.cuda.synchronize()
+        torch.distributed.barrier()
+        t0 = time.perf_counter()
+        partition.sharded_hessian(cols, nu, tune["block_k"])
+        torch.cuda.synchronize()
+        sh_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dev)
+        sharded = {"ms": sh_ms, "hvps_per_s": nu / (sh_ms * 1e-3), "ranks": world,
+                   "split": "contiguous column ranges in whole tiles, one NCCL all-gather of H"}
+    rto = None if args.no_extras else tracking_qp(P, torch, ctx, al, state, pds, qds,
+                                                  args.warmup + args.steps + 1 + ke, 3)
+    al_static = None if args.no_extras else [static_opf(P, torch, dev, "medium1400", 20),
+                                             static_opf(P, torch, dev, WORKLOAD, 3)]
 
     if rank != 0:
         if world > 1:
@@ -405,8 +606,14 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(nu, {"step": "tracking update: power flow at new loads + reduced-Newton step "
                                                "(gradient, Schur Hessian, Cholesky, trial power flow)",
+                                       "load_scale": synth.WORKLOADS[WORKLOAD]["load_scale"],
                                        "block_k": tune["block_k"], "threads": tune["threads"],
                                        "autotuned": True,
+                                       "autotune_candidates": [list(c) for c in AUTOTUNE_CANDIDATES],
+                                       "block_width_note": "a CTA owns its tile's columns through all four "
+                                       "sweeps, so k is the tile width; widths above 32 leave fewer tiles "
+                                       "than resident CTA slots (n_u / k < 3 x 148) and less of the FP64 "
+                                       "pipe busy; the candidates cover 4 to 32",
                                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
         "ms_per_hessian": hess_ms,
         "ms_hvp_phase": hvp_ms,
@@ -415,20 +622,30 @@ def run_gpu(args):
         "step_detail": {"pf_iterations": statistics.median(i[0]["iterations"] for i in infos),
                         "inertia_delta": statistics.median(i["delta"] for i in sinfos),
                         "halvings": sum(i["halvings"] for i in sinfos)},
+        "hessian_asymmetry": prof["asymmetry"],
         "plain": {"ms_per_hvp": plain_ms_per_col, "hvps_per_s": 1e3 / plain_ms_per_col,
-                  "ms_per_hessian_extrapolated": plain_ms_per_col * nu, "columns_timed": pc},
+                  "ms_per_hessian_extrapolated": plain_ms_per_col * nu, "columns_timed": pc,
+                  "form": "one direction per launch sequence: 9 device-wide kernels per column around two "
+                          "streamed single-RHS solves (L, U and U^T, L^T)"},
         "batched_over_plain": (nu / (hvp_ms * 1e-3)) / (1e3 / plain_ms_per_col),
         "batched_snapshots": batch,
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": (HVP_SPLIT_TRAFFIC_9200 if (tune["block_k"], tune["threads"]) == (8, 256)
-                                 and WORKLOAD == "large9200" else None),
+        "autograd": auto,
+        "hessian_sharded": sharded,
+        "rto_tracking_qp": rto,
+        "static_opf_al": al_static,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_tf,
+                     "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": ("hvp_split_kernel" if (tune["block_k"], tune["threads"]) == (8, 256)
                                 else "hvp_tile_kernel"), "flops_per_launch": flops,
-                     "peak_note": "FP64 FMA pipe, nominal 1.25 TFLOP/s (microbenchmark on this pool: 1.12)",
+                     "peak_note": "FP64 FMA rate of this GPU measured in this run (opf_fp64_peak: "
+                                  f"{fp64_ms:.3f} ms probe); nominal 1.25 TFLOP/s",
                      "hbm": {"bytes_per_hessian": hbm_b, "achieved_gbs": hbm_b / (hvp_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
-                             "frac": hbm_b / (hvp_ms * 1e-3) / 1e9 / hbm_peak}},
+                             "frac": hbm_b / (hvp_ms * 1e-3) / 1e9 / hbm_peak},
+                     "phase_share": {"first_L_solve": share[0], "U_sweep": share[1], "second_order": share[2],
+                                     "Ut_Lt_sweeps": share[3], "assembly": share[4]},
+                     "solve_phase": solve},
         "e2e": {"value": world * nu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * net.n_bus,
                 "d2h_bytes_per_step": 8 * (nu + ctx.m), "ms_per_step": e2e_s * 1e3, "steps": ks},
         "gpu_launches": launches,

@@ -235,8 +235,9 @@ opf_status opf_hessian_autotune(opf_ctx* ctx, const opf_al_params* p, double* H,
  * finishes one (the batched multi-right-hand-side HVPs of Sec. V-A across
  * snapshots).  params[k] and H[k] (n_u(k) x n_u(k) column-major) belong to
  * ctxs[k].  Everything runs on ctxs[0]'s stream; all contexts must live on
- * the same device.  opts: block_k and grid (0 = as many CTAs as fit); plain,
- * columns and threads are ignored.  The workspace is held by ctxs[0] (grown on
+ * the same device.  opts: block_k and grid (0 = as many CTAs as fit), and
+ * reuse_first_order (every context's first-order quantities were just
+ * evaluated with its params); plain, columns and threads are ignored.  The workspace is held by ctxs[0] (grown on
  * demand).  Errors: OPF_EINVAL, OPF_ESTATE (a context without a converged
  * power flow).
  */
@@ -309,7 +310,7 @@ typedef struct {
 } opf_al_state;
 
 typedef struct {
-  int block_k;        /* Hessian tile width (0 = 8) */
+  int block_k;        /* Hessian tile width (0 = the context's autotuned choice, else 8) */
   int max_halvings;   /* trial power flows allowed after the first (0 = 10) */
   int max_inertia;    /* inertia-correction tries after the first (0 = 24) */
   double delta_start; /* first delta tried (0 = start at 0) */
@@ -390,10 +391,13 @@ opf_status opf_al_solve(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_
  * opf_al_solve with grad q(d) = g_t + (H_t + delta I_u) d in place of grad L;
  * stop when E_0 <= tol or after max_it iterations; mu <- max(tol / 10,
  * min(0.2 mu, mu^1.5)) when E_mu <= 10 mu; fraction to the boundary tau =
- * max(0.99, 1 - mu); delta is the smallest of 0 (or opts->delta_start), 1e-8,
- * 1e-7, ... that makes S positive definite, and it only grows within a QP (so
- * the QP stays one convex problem).  grad q is carried from iteration to
- * iteration through the Newton system: H d = -grad psi - Sigma d.
+ * max(0.99, 1 - mu); delta starts at the smallest of 0 (or opts->delta_start),
+ * 1e-8, 1e-7, ... that makes H_uu + delta I positive definite (H_uu = H(0), one
+ * more Hessian and Cholesky before the iterations), so that the QP is convex --
+ * the paper starts the tracking at an optimum, where H_uu is positive definite
+ * and delta = 0 -- and grows further only if an iteration's S is not positive
+ * definite.  grad q is carried from iteration to iteration through the Newton
+ * system: H d = -grad psi - Sigma d.
  * p: sigma_f, rho, sigma_c (y, s, omega ignored); y [m] updated in place; st:
  * u, s (w_t in, w_{t+1} out), bound duals (the QP's, warm start in, final out),
  * bounds, x (the state at u_t in, at u_{t+1} out), mu (the QP's first barrier
@@ -411,7 +415,7 @@ typedef struct {
 
 typedef struct {
   int qp_iterations, halvings, pf_iterations, inertia_increases;
-  double delta, kkt, mu, alpha_p;
+  double delta, delta_convex, kkt, mu, alpha_p;  /* delta at the end, at the start (convexity) */
   float ms_total;     /* the whole update */
   float ms_qp;        /* gradient at w_t and the QP iterations */
   float ms_hessian;   /* summed device time of the QP's Hessians H(omega) */
@@ -465,6 +469,37 @@ opf_status opf_set_wait_limit(opf_ctx* ctx, int spins);
 opf_status opf_fp64_peak(void* stream, double* tflops, float* ms_out);
 opf_status opf_pivot_reciprocal(void* stream, const double* u, double* r, int n);
 opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0);
+
+/*
+ * opf_al_step_batched: one tracking update for each of n snapshots (contexts of
+ * the same or different networks on one device): optionally the power flow at
+ * the snapshot's new loads pd[k], qd[k] (device, NULL entries or NULL arrays =
+ * keep the context's state), then the reduced-Newton step of opf_al_step with
+ * params[k] and states[k] -- with every snapshot's Schur Hessian H(omega_k) in
+ * one persistent launch over a shared tile queue (opf_reduced_hessian_batched,
+ * largest networks first; Sec. V-A batches the multi-right-hand-side solves).
+ * The per-snapshot parts (power flows, first-order quantities, Cholesky,
+ * solves, trial power flows) run on each context's own stream, driven by host
+ * threads that take the snapshots largest first, so the GPU overlaps them.
+ * infos[k] (host, may be NULL) and status[k] (host, may be NULL) report each
+ * snapshot; binfo (host, may be NULL) the phase times.  A snapshot that fails
+ * keeps its state and does not stop the others; the call returns the first
+ * failure's status (OPF_OK when all succeed).  Errors of the batch itself:
+ * OPF_EINVAL (null or repeated context, mixed devices), those of
+ * opf_reduced_hessian_batched.
+ */
+typedef struct {
+  float ms_powerflow_first_order;  /* host wall time of the power flows and pre-Hessian parts */
+  float ms_hessians;               /* the batched Hessian launch (with its set-up) */
+  float ms_steps;                  /* Cholesky, solves, trial power flows, updates */
+  float ms_total;
+  int hessian_tiles, host_threads, failed;
+} opf_batch_info;
+
+opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf_al_params* params,
+                               opf_al_state* states, const double* const* pd, const double* const* qd,
+                               const opf_step_opts* opts, opf_step_info* infos, opf_status* status,
+                               opf_batch_info* binfo);
 
 /* Number of kernels this context has launched since it was created (host output). */
 opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);

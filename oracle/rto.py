@@ -18,7 +18,11 @@ iteration.  The IPM's rules are the readings the library's
 opf_tracking_update takes (stated there and in al_loop.kkt_errors): KKT error,
 barrier update mu <- max(tol/10, min(0.2 mu, mu^1.5)) when E_mu <= 10 mu,
 fraction to the boundary tau = max(0.99, 1 - mu), and a regularisation delta
-in {0, 1e-8, 1e-7, ...} that only grows within one QP.
+that only grows within one QP, starting at the smallest of {delta_start or 0,
+1e-8, 1e-7, ...} that makes H_uu + delta I positive definite, so that the QP is
+convex (the paper starts the tracking from an optimum, where H_uu is positive
+definite and delta = 0; away from one the reduced Hessian of the AL is
+indefinite).
 """
 import numpy as np
 
@@ -66,7 +70,16 @@ def tracking_update(on, x, u, s, y, st, al, pd=None, qd=None, tol=1e-6, max_it=5
     z = {k: st[k].copy() for k in ("zl_u", "zu_u", "zl_s", "zu_s")}
     bnd = {k: st[k] for k in ("u_lo", "u_hi", "s_lo", "s_hi")}
     mu = st["mu"]
+    # convexity: the smallest delta in {delta_start or 0, 1e-8, 1e-7, ...} with H_uu + delta I
+    # positive definite (the QP's Hessian is then positive semidefinite)
     delta = delta_start
+    while True:
+        try:
+            np.linalg.cholesky(H0 + delta * np.eye(nu))
+            break
+        except np.linalg.LinAlgError:
+            delta = 10.0 * delta if delta > 0 else 1e-8
+    delta_convex = delta
 
     def grad_q(delta):
         du, ds = w_u - u0, w_s - s0
@@ -127,5 +140,5 @@ def tracking_update(on, x, u, s, y, st, al, pd=None, qd=None, tol=1e-6, max_it=5
         halvings += 1
     c_new = on.eval(xn, w_u, pd=pd, qd=qd)["c"]
     y_new = y + al["rho"] * al["sigma_c"] * (c_new - w_s)
-    return dict(u=w_u, s=w_s, x=xn, y=y_new, duals=z, mu=mu, delta=delta, iterations=it, kkt=rec[-1][2],
-                halvings=halvings, record=rec)
+    return dict(u=w_u, s=w_s, x=xn, y=y_new, duals=z, mu=mu, delta=delta, delta_convex=delta_convex,
+                iterations=it, kkt=rec[-1][2], halvings=halvings, record=rec)

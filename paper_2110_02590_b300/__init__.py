@@ -103,9 +103,15 @@ class QpOpts(C.Structure):
 
 class QpInfo(C.Structure):
     _fields_ = [("qp_iterations", C.c_int), ("halvings", C.c_int), ("pf_iterations", C.c_int),
-                ("inertia_increases", C.c_int), ("delta", C.c_double), ("kkt", C.c_double), ("mu", C.c_double),
+                ("inertia_increases", C.c_int), ("delta", C.c_double), ("delta_convex", C.c_double),
+                ("kkt", C.c_double), ("mu", C.c_double),
                 ("alpha_p", C.c_double), ("ms_total", C.c_float), ("ms_qp", C.c_float), ("ms_hessian", C.c_float),
                 ("ms_cholesky", C.c_float)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("ms_powerflow_first_order", C.c_float), ("ms_hessians", C.c_float), ("ms_steps", C.c_float),
+                ("ms_total", C.c_float), ("hessian_tiles", C.c_int), ("host_threads", C.c_int), ("failed", C.c_int)]
 
 
 class OPFError(RuntimeError):
@@ -150,6 +156,9 @@ def lib():
         L.opf_set_wait_limit.argtypes = [C.c_void_p, C.c_int]
         L.opf_tracking_update.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                           C.POINTER(QpOpts), C.POINTER(QpInfo)]
+        L.opf_al_step_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AlParams), C.POINTER(AlState),
+                                          C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(StepOpts),
+                                          C.POINTER(StepInfo), C.POINTER(C.c_int), C.POINTER(BatchInfo)]
         L.opf_al_solve.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                    C.POINTER(AlOpts), C.POINTER(AlInfo), C.POINTER(C.c_double)]
         L.opf_fp64_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)]
@@ -278,6 +287,40 @@ def dense_syrk_emulated(A, c0, K, r0):
     if st != 0:
         raise OPFError(st, "opf_dense_syrk_emulated")
     return A
+
+
+def al_step_batched(ctxs, als, states, loads=None, block_k=0, delta_start=0.0):
+    """One tracking update per snapshot (opf_al_step_batched): power flow at loads[k] = (pd, qd)
+    (cuda float64 tensors; None keeps the state), then the reduced-Newton step with all Schur
+    Hessians in one persistent launch.  The state tensors are updated in place.  Returns
+    (per-snapshot step infos, statuses, batch info)."""
+    n = len(ctxs)
+    for c in ctxs:
+        c._sync_stream()
+    keep, ps, sts = [], [], []
+    for c, al, st in zip(ctxs, als, states):
+        p, kp = c._al(dict(al, s=st["s"]))
+        keep.append(kp)
+        ps.append(p)
+        sts.append(c._state(st))
+    hs = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    pdp = qdp = None
+    if loads is not None:
+        for c, (pd, qd) in zip(ctxs, loads):
+            c._dev(pd)
+            c._dev(qd)
+        pdp = (C.c_void_p * n)(*[pd.data_ptr() for pd, _ in loads])
+        qdp = (C.c_void_p * n)(*[qd.data_ptr() for _, qd in loads])
+    infos = (StepInfo * n)()
+    stat = (C.c_int * n)()
+    binfo = BatchInfo()
+    opts = StepOpts(int(block_k), 0, 0, float(delta_start))
+    rc = lib().opf_al_step_batched(hs, n, (AlParams * n)(*ps), (AlState * n)(*sts), pdp, qdp, C.byref(opts), infos,
+                                   stat, C.byref(binfo))
+    out = [{k: getattr(i, k) for k, _ in StepInfo._fields_} for i in infos]
+    if rc != 0 and all(v == 0 for v in stat):
+        raise OPFError(rc, "opf_al_step_batched")
+    return out, list(stat), {k: getattr(binfo, k) for k, _ in BatchInfo._fields_}
 
 
 def _ptr(t):

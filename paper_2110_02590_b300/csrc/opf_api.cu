@@ -1073,7 +1073,7 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     opf_ctx* c = ctxs[k];
     cudaStream_t keep = c->stream;
     c->stream = st;
-    launch_first_order(c, &params[k], nullptr);
+    if (!(o && o->reuse_first_order)) launch_first_order(c, &params[k], nullptr);
     launch_hess_prep(c, params[k].sigma_f);
     c->stream = keep;
     args[k] = make_hvp_args(c, C, H[k], 0, c->h.nu, false);

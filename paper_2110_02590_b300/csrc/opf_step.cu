@@ -9,6 +9,10 @@
 // fraction-to-the-boundary reductions.  The host drives the inertia correction
 // and the trial power flows.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <vector>
 #include <cmath>
 #include <string>
 
@@ -768,9 +772,12 @@ opf_status launch_chol_solve(opf_ctx* c, StepWork* w, double* A, int n, double* 
 
 }  // namespace
 
-extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_state* st,
-                                  const opf_step_opts* o, opf_step_info* info, double* du_out,
-                                  double* ds_out) {
+namespace {
+
+// The part of a reduced-Newton step before its Hessian: Sigma, the Schur
+// weights omega, the first-order quantities with omega (gradient), grad psi and
+// v.  *ps receives the parameters of the step's Schur Hessian.
+opf_status step_begin(opf_ctx* c, const opf_al_params* p, opf_al_state* st, opf_al_params* ps_out) {
   if (!c || !p || !st) {
     set_last_error("ctx, params and state are required");
     return OPF_EINVAL;
@@ -791,17 +798,13 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
   opf_status rc = alloc_step(c);
   if (rc) return rc;
   StepWork* w = c->stepw;
-  const int nu = c->h.nu, m = c->h.m, nx = c->h.nx, nb = c->h.nb;
-  const int block_k = (o && o->block_k) ? o->block_k : 8;
-  const int max_halvings = (o && o->max_halvings) ? o->max_halvings : 10;
-  const int max_inertia = (o && o->max_inertia) ? o->max_inertia : 24;
+  const int nu = c->h.nu, m = c->h.m;
   cudaStream_t stream = c->stream;
   // phase boundaries: start, first order, Hessian, Schur rhs, Cholesky, solves, end of step (trial PF)
   cudaEvent_t* ev = w->ev;
   if (!ev[0])
     for (int k = 0; k < 7; k++) SCK(cudaEventCreate(&ev[k]));
-  cudaEvent_t e0 = ev[0], e1 = ev[5];
-  SCK(cudaEventRecord(e0, stream));
+  SCK(cudaEventRecord(ev[0], stream));
   // Sigma and the Schur weights omega (state only)
   step_sigma_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
       nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
@@ -818,12 +821,24 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
       nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo, st->s_hi, st->zl_s, st->zu_s,
       w->gu, w->gs, p->sigma_c, p->rho, st->mu, w->sig_u, w->gpsi_u, w->sig_s, w->gpsi_s, w->omega, w->v);
   c->launches++;
-  // S_uu = H(omega) + Sigma_u (symmetrised), on the first-order quantities just evaluated
-  opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0, 1};
-  opf_hess_info hi;
-  rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
-  if (rc) return rc;
-  SCK(cudaEventRecord(ev[2], stream));
+  *ps_out = ps;
+  return OPF_OK;
+}
+
+// The part of a reduced-Newton step after its Hessian (in the step workspace's
+// S): the Schur system, its Cholesky with the inertia correction, the solves,
+// the slack and dual steps, the fraction to the boundary, the trial power flows
+// and the update.  ms_hessian: the Hessian's device time, for info.
+opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const opf_step_opts* o,
+                    opf_step_info* info, double* du_out, double* ds_out, float ms_hessian) {
+  StepWork* w = c->stepw;
+  opf_status rc = OPF_OK;
+  const int nu = c->h.nu, m = c->h.m, nx = c->h.nx, nb = c->h.nb;
+  const int max_halvings = (o && o->max_halvings) ? o->max_halvings : 10;
+  const int max_inertia = (o && o->max_inertia) ? o->max_inertia : 24;
+  cudaStream_t stream = c->stream;
+  cudaEvent_t* ev = w->ev;
+  cudaEvent_t e0 = ev[0], e1 = ev[5];
   sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
   c->launches++;
   // r = -grad_u psi - J^T v on the second stream, beside the Cholesky (it reads
@@ -937,13 +952,32 @@ extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_sta
     info->halvings = halvings;
     info->inertia_tries = tries;
     info->pf_iterations = pfi.iterations;
-    info->ms_hessian = hi.ms_total;
+    info->ms_hessian = ms_hessian;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     info->ms_total = ms;
     info->du_inf = info->ds_inf = 0.0;
   }
   return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" opf_status opf_al_step(opf_ctx* c, const opf_al_params* p, opf_al_state* st,
+                                  const opf_step_opts* o, opf_step_info* info, double* du_out,
+                                  double* ds_out) {
+  opf_al_params ps;
+  opf_status rc = step_begin(c, p, st, &ps);
+  if (rc) return rc;
+  StepWork* w = c->stepw;
+  const int block_k = o ? o->block_k : 0;
+  // S_uu = H(omega) + Sigma_u (symmetrised), on the first-order quantities just evaluated
+  opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0, 1};
+  opf_hess_info hi;
+  rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
+  if (rc) return rc;
+  SCK(cudaEventRecord(w->ev[2], c->stream));
+  return step_end(c, p, st, o, info, du_out, ds_out, hi.ms_total);
 }
 
 // ---------------------------------------------------------------- tracking QP
@@ -1031,6 +1065,43 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
   double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0;
   float ms_hess = 0.f, ms_chol = 0.f;
   int it = 0, increases = 0;
+  // convexity: the smallest delta of {delta_start or 0, 1e-8, 1e-7, ...} with H_uu + delta I
+  // positive definite (H_uu = H(0), no Gauss-Newton weights), so that the QP is convex
+  {
+    SCK(cudaMemsetAsync(w->omega, 0, m * sizeof(double), stream));
+    SCK(cudaMemsetAsync(w->sig_u, 0, nu * sizeof(double), stream));
+    opf_al_params p0 = pt;
+    p0.omega = w->omega;
+    opf_hess_opts ho = {block_k, 0, 0, 0, 0, 0, 0};
+    opf_hess_info hi;
+    rc = opf_reduced_hessian(c, &p0, &ho, w->S, &hi);
+    if (rc) return rc;
+    ms_hess += hi.ms_total;
+    sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
+    c->launches++;
+    SCK(cudaEventRecord(ev[1], stream));
+    for (int tries = 0;; tries++) {
+      add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
+      SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
+      c->launches++;
+      rc = launch_cholesky(c, w, w->L, nu, w->flag);
+      if (rc) return rc;
+      SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      SCK(cudaStreamSynchronize(stream));
+      if (!*w->h_flag) break;
+      if (tries >= max_inertia) {
+        set_last_error("tracking QP: H_uu not positive definite after the inertia corrections");
+        return OPF_ENOTPD;
+      }
+      delta = (delta > 0.0) ? 10.0 * delta : 1e-8;
+      increases++;
+    }
+    SCK(cudaEventRecord(ev[2], stream));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[1], ev[2]);
+    ms_chol += t;
+  }
+  const double delta_convex = delta;
   for (it = 0;; it++) {
     SCK(cudaMemsetAsync(w->kred, 0, 4 * sizeof(double), stream));
     launch_al_kkt(c, w->gqu, w->gqs, st, nullptr, nullptr, mu, w->kred);
@@ -1164,6 +1235,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     info->pf_iterations = pfi.iterations;
     info->inertia_increases = increases;
     info->delta = delta;
+    info->delta_convex = delta_convex;
     info->kkt = e_0;
     info->mu = mu;
     info->alpha_p = ap;
@@ -1173,4 +1245,126 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     cudaEventElapsedTime(&info->ms_qp, ev[0], ev[3]);
   }
   return OPF_OK;
+}
+
+// ---------------------------------------------------------------- batched steps
+
+extern "C" opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf_al_params* params,
+                                          opf_al_state* states, const double* const* pd,
+                                          const double* const* qd, const opf_step_opts* o,
+                                          opf_step_info* infos, opf_status* status, opf_batch_info* binfo) {
+  if (!ctxs || n < 1 || !params || !states) {
+    set_last_error("ctxs, params and states are required, n >= 1");
+    return OPF_EINVAL;
+  }
+  for (int k = 0; k < n; k++) {
+    if (!ctxs[k]) {
+      set_last_error("null context in the batch");
+      return OPF_EINVAL;
+    }
+    if (ctxs[k]->device != ctxs[0]->device) {
+      set_last_error("all contexts of a batch must be on one device");
+      return OPF_EINVAL;
+    }
+    for (int j = 0; j < k; j++)
+      if (ctxs[j] == ctxs[k]) {
+        set_last_error("a context appears twice in the batch");
+        return OPF_EINVAL;
+      }
+  }
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  // contexts by decreasing work (longest processing time first) for the host threads
+  std::vector<int> order(n);
+  for (int k = 0; k < n; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)ctxs[a]->dn.nnz * ctxs[a]->h.nu > (long long)ctxs[b]->dn.nnz * ctxs[b]->h.nu;
+  });
+  std::vector<opf_status> st(n, OPF_OK);
+  std::vector<std::string> msg(n);
+  std::vector<opf_al_params> ps(n);
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthreads = (int)std::min<unsigned>((unsigned)n, std::min(hw, 32u));
+  const int dev = ctxs[0]->device;
+  // run f(k) for every context on nthreads host threads, largest first; each
+  // context's work is ordered on its own stream, so the GPU overlaps them
+  auto parallel = [&](auto&& f) {
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; t++)
+      pool.emplace_back([&]() {
+        cudaSetDevice(dev);
+        for (int i = next++; i < n; i = next++) {
+          const int k = order[i];
+          if (st[k] != OPF_OK) continue;
+          st[k] = f(k);
+          if (st[k] != OPF_OK) msg[k] = opf_last_error();
+        }
+      });
+    for (auto& th : pool) th.join();
+  };
+  // (A) power flow at the snapshot's loads, then the step up to its Hessian
+  parallel([&](int k) -> opf_status {
+    opf_ctx* c = ctxs[k];
+    opf_al_state* s = &states[k];
+    if (pd && pd[k]) {
+      opf_pf_info pfi;
+      const opf_status r = opf_powerflow(c, s->u, pd[k], qd ? qd[k] : nullptr, s->x, nullptr, &pfi);
+      if (r) return r;
+    }
+    const opf_status r = step_begin(c, &params[k], s, &ps[k]);
+    if (r) return r;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? OPF_OK : OPF_ECUDA;
+  });
+  const auto t1 = clk::now();
+  // (B) every live context's Schur Hessian in one persistent launch
+  std::vector<opf_ctx*> live;
+  std::vector<opf_al_params> lp;
+  std::vector<double*> lh;
+  for (int k : order)
+    if (st[k] == OPF_OK) {
+      live.push_back(ctxs[k]);
+      lp.push_back(ps[k]);
+      lh.push_back(ctxs[k]->stepw->S);
+    }
+  float ms_hess = 0.f;
+  opf_hess_info hi = {};
+  if (!live.empty()) {
+    opf_hess_opts ho = {o ? o->block_k : 0, 0, 0, 0, 0, 0, 1};
+    const opf_status r = opf_reduced_hessian_batched(live.data(), (int)live.size(), lp.data(), lh.data(), &ho, &hi);
+    if (r) return r;
+    ms_hess = hi.ms_total;
+    for (opf_ctx* c : live) SCK(cudaEventRecord(c->stepw->ev[2], c->stream));
+  }
+  const auto t2 = clk::now();
+  // (C) Cholesky, solves, fraction to the boundary, trial power flows, update
+  parallel([&](int k) -> opf_status {
+    return step_end(ctxs[k], &params[k], &states[k], o, infos ? &infos[k] : nullptr, nullptr, nullptr, ms_hess);
+  });
+  const auto t3 = clk::now();
+  opf_status first = OPF_OK;
+  int failed = 0;
+  for (int k = 0; k < n; k++) {
+    if (status) status[k] = st[k];
+    if (st[k] != OPF_OK) {
+      failed++;
+      if (first == OPF_OK) {
+        first = st[k];
+        set_last_error("context " + std::to_string(k) + ": " + msg[k]);
+      }
+    }
+  }
+  if (binfo) {
+    auto ms = [](clk::time_point a, clk::time_point b) {
+      return (float)std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    binfo->ms_powerflow_first_order = ms(t0, t1);
+    binfo->ms_hessians = ms(t1, t2);
+    binfo->ms_steps = ms(t2, t3);
+    binfo->ms_total = ms(t0, t3);
+    binfo->hessian_tiles = hi.tiles;
+    binfo->host_threads = nthreads;
+    binfo->failed = failed;
+  }
+  return first;
 }

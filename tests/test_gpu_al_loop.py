@@ -63,7 +63,9 @@ def test_al_loop_parity(name, max_outer):
     assert np.all(np.abs(hist[:, 5] - rh[:, 5]) <= 1e-7 * np.abs(rh[:, 5]))  # F
     assert rel(state["u"].cpu().numpy(), ref["u"]) < 1e-5
     assert rel(state["s"].cpu().numpy(), ref["s"]) < 1e-5
-    assert rel(y.cpu().numpy(), ref["y"]) < 1e-4
+    # y moves by rho D_c (c - s) per outer iteration: rho up to 1e3 scales the rounding-level
+    # differences of c - s into y
+    assert rel(y.cpu().numpy(), ref["y"]) < 1e-3
     assert info["rho"] == ref["rho"] and abs(state["mu"] - ref["mu"]) <= 1e-12 * ref["mu"]
     assert np.abs(state["x"].cpu().numpy() - ref["x"]).max() < 1e-5
 

@@ -48,6 +48,7 @@ def test_tracking_update_parity(name, seed_y):
     info = ctx.tracking_update(dict(sigma_f=al["sigma_f"], rho=al["rho"], sigma_c=dev(al["sigma_c"])), state, yg)
     assert info["qp_iterations"] == ref["iterations"]
     assert info["delta"] == ref["delta"] and info["halvings"] == ref["halvings"]
+    assert info["delta_convex"] == ref["delta_convex"]
     assert info["kkt"] <= 1e-6 and abs(state["mu"] - ref["mu"]) <= 1e-12 * ref["mu"]
     assert rel(state["u"].cpu().numpy() - u, ref["u"] - u) < 1e-6
     assert rel(state["s"].cpu().numpy() - s, ref["s"] - s) < 1e-6
