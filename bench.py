@@ -361,20 +361,26 @@ def autograd_batch(P, torch, dev, nscen):
                     "w.r.t. u, loads and s; plain: power flow + adjoint gradient per scenario"}
 
 
-def static_opf(P, torch, dev, name, max_outer, max_inner=10, rate_factor=1.5):
+def static_opf(P, torch, dev, name, max_outer, max_inner=30, margin=1.2):
     """Static OPF by the augmented-Lagrangian loop (opf_al_solve) on a synthetic grid at its
-    nominal loads: line limits widened rate_factor x (at 1.2x the base-case DC flows the AC flows
-    already exceed them), y = 0, rho = 10, an interior start at mu = 0.1."""
+    nominal loads: line limits max(rate, margin |S|) from the AC base case (the generator's own
+    limits follow its DC flows, which the AC flows exceed on up to a third of the branches), y = 0,
+    rho = 10, an interior start at mu = 0.1."""
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
     net = synth.workload(name)
     ctx = P.OPFContext(net, device=dev.index)
     u_lo, u_hi = synth.control_bounds(net)
-    u = np.clip(synth.flat_control(net), u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
     al = synth.al_inputs(net, seed=5)
     nl = net.n_branch
-    al["s_hi"][:2 * nl] *= rate_factor ** 2
-    al["sigma_c"][:2 * nl] /= rate_factor ** 2
-    x, _ = ctx.powerflow(d(u))
+    u0 = synth.flat_control(net)
+    x0, _ = ctx.powerflow(d(u0))
+    c0 = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})["c"]
+    c0 = c0.cpu().numpy()
+    r2 = np.maximum(net.br_rate ** 2, margin ** 2 * np.maximum(c0[:nl], c0[nl:2 * nl]))
+    al["s_hi"][:2 * nl] = np.concatenate([r2, r2])
+    al["sigma_c"][:2 * nl] = np.concatenate([1.0 / r2, 1.0 / r2])
+    u = np.clip(u0, u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
+    x, _ = ctx.powerflow(d(u), x0=x0)
     c = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})["c"]
     lo, hi = al["s_lo"], al["s_hi"]
     s = np.clip(c.cpu().numpy(), lo + 0.01 * (hi - lo), hi - 0.01 * (hi - lo))
@@ -390,7 +396,8 @@ def static_opf(P, torch, dev, name, max_outer, max_inner=10, rate_factor=1.5):
             "ms_per_outer": info["ms_total"] / max(1, info["outer"]), "ms_per_step": info["ms_total"] / steps,
             "primal_inf": info["primal_inf"], "dual_inf": info["dual_inf"], "rho_final": info["rho"],
             "steps_per_outer": [int(h[0]) for h in hist],
-            "setup": f"nominal loads, line limits x{rate_factor}, y0 = 0, rho0 = 10, mu0 = 0.1, "
+            "setup": f"nominal loads, line limits max(rate, {margin} |S| of the AC base case), y0 = 0, rho0 = 10, "
+                     "mu0 = 0.1, "
                      f"at most {max_inner} reduced-Newton steps per subproblem (one full Hessian each)"}
 
 

@@ -314,6 +314,11 @@ typedef struct {
   int max_halvings;   /* trial power flows allowed after the first (0 = 10) */
   int max_inertia;    /* inertia-correction tries after the first (0 = 24) */
   double delta_start; /* first delta tried (0 = start at 0) */
+  int line_search;    /* 1: also halve the step until the barrier function psi_mu = F - mu sum
+                         log(w - w_lo) - mu sum log(w_hi - w) satisfies the Armijo rule
+                         psi(w + a d) <= psi(w) + 1e-4 a grad psi^T d (the inertia-corrected
+                         system makes d a descent direction); after max_halvings the last trial
+                         with a converged power flow is taken.  0: accept the first one. */
 } opf_step_opts;
 
 typedef struct {
@@ -344,8 +349,10 @@ opf_status opf_al_step(opf_ctx* ctx, const opf_al_params* p, opf_al_state* st,
  *   inner loop: evaluate the gradient at the current point; stop when
  *     E_0 <= omega_k = max(eta_dual, 10^-(k+1)) or after max_inner steps; when
  *     E_mu <= 10 mu, mu <- max(eta_dual / 10, min(0.2 mu, mu^1.5)); then one
- *     opf_al_step whose inertia correction starts at delta/10 of the previous
- *     step's delta when that was at least 1e-7, else at 0;
+ *     opf_al_step with the Armijo line search on psi_mu (the subproblems are
+ *     nonconvex away from a solution and full steps can diverge), its inertia
+ *     correction starting at delta/10 of the previous step's delta when that was
+ *     at least 1e-7, else at 0;
  *   outer update: eta_p = |sigma_c (c - s)|_inf; stop when eta_p <= eta_primal
  *     and E_0 <= eta_dual; else y <- y + rho sigma_c (c - s), and rho <-
  *     min(10 rho, rho_max) when eta_p fell by less than a factor 4.
@@ -359,7 +366,7 @@ opf_status opf_al_step(opf_ctx* ctx, const opf_al_params* p, opf_al_state* st,
  */
 typedef struct {
   int max_outer;      /* outer iterations (0 = 20) */
-  int max_inner;      /* reduced-Newton steps per subproblem (0 = 10) */
+  int max_inner;      /* reduced-Newton steps per subproblem (0 = 30) */
   double eta_primal;  /* stopping tolerance on |sigma_c (c - s)|_inf (0 = 1e-5) */
   double eta_dual;    /* stopping tolerance on E_0 (0 = 1e-4) */
   double rho_max;     /* penalty cap (0 = 1e6) */
@@ -500,6 +507,28 @@ opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf_al_params*
                                opf_al_state* states, const double* const* pd, const double* const* qd,
                                const opf_step_opts* opts, opf_step_info* infos, opf_status* status,
                                opf_batch_info* binfo);
+
+/*
+ * opf_objective_batched: for n load scenarios of one network, the power flow
+ * (from the common warm start x0 [n_x]) at u[k], pd[k], qd[k] and the reduced
+ * objective F[k] of the scaled AL with slacks s[k] -- and, for every non-NULL
+ * gradient array, its adjoint gradient (Prop. 1): grad_u [n][n_u], grad_pd and
+ * grad_qd [n][n_bus] (total derivatives through g and the slack generation),
+ * grad_s [n][m] = -phi'.  Row-major device arrays, scenario k at offset k times
+ * the row length; pd/qd NULL = nominal loads; x_out [n][n_x] (may be NULL)
+ * receives the states.  p: sigma_f, rho, sigma_c, y shared by the scenarios
+ * (its s and omega are ignored).  The scenarios are spread over a pool of nctx
+ * contexts of that network, each on its own stream and host thread (give each
+ * its own stream with opf_set_stream for the GPU to overlap them); the outputs
+ * are complete when the call returns.  status[k] (host, may be NULL) reports
+ * each scenario; the call returns the first failure.  Errors: OPF_EINVAL
+ * (contexts of different networks or devices, a repeated context), those of
+ * opf_powerflow and opf_reduced_gradient.
+ */
+opf_status opf_objective_batched(opf_ctx* const* ctxs, int nctx, int n, const opf_al_params* p,
+                                 const double* u, const double* pd, const double* qd, const double* s,
+                                 const double* x0, double* x_out, double* F, double* grad_u,
+                                 double* grad_pd, double* grad_qd, double* grad_s, opf_status* status);
 
 /* Number of kernels this context has launched since it was created (host output). */
 opf_status opf_launch_count(const opf_ctx* ctx, long long* launches);

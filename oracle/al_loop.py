@@ -18,7 +18,10 @@ textbook; the readings (the same ones the library's opf_al_solve takes):
     barrier drops to max(eta_dual / 10, min(0.2 mu, mu^1.5)) (Wachter &
     Biegler's rule); then one reduced-Newton step;
   * inertia correction of a step starts at delta/10 of the previous step's
-    delta when that was at least 1e-7, else at 0;
+    delta when that was at least 1e-7, else at 0; each step backtracks on the
+    barrier function (Armijo rule, al_step's line_search): the subproblems are
+    nonconvex away from a solution, and full Newton steps there can increase
+    psi_mu and diverge;
   * after the subproblem: primal infeasibility eta_p = |D_c (c - s)|_inf; stop
     when eta_p <= eta_primal and E_0 <= eta_dual; else y <- y + rho D_c (c - s),
     and rho <- min(10 rho, rho_max) when eta_p fell by less than a factor 4.
@@ -43,7 +46,7 @@ def kkt_errors(g, u, s, st, mu):
     return max(dual, comp[0]), max(dual, comp[1]), dual
 
 
-def al_solve(on, x, u, s, y, st, al, rho, max_outer=20, max_inner=10, eta_primal=1e-5, eta_dual=1e-4,
+def al_solve(on, x, u, s, y, st, al, rho, max_outer=20, max_inner=30, eta_primal=1e-5, eta_dual=1e-4,
              rho_max=1e6):
     """Run the outer loop from (x, u, s, y, duals in st, st['mu'], rho).  Returns the final point and
     one history row per outer iteration: (inner steps, mu, rho, eta_p, E_0, F)."""
@@ -67,7 +70,8 @@ def al_solve(on, x, u, s, y, st, al, rho, max_outer=20, max_inner=10, eta_primal
             if e_mu <= 10.0 * mu:
                 mu = max(eta_dual / 10.0, min(0.2 * mu, mu ** 1.5))
             st["mu"] = mu
-            out = A.al_step(on, x, u, s, st, alk, delta_start=(delta / 10.0 if delta >= 1e-7 else 0.0))
+            out = A.al_step(on, x, u, s, st, alk, delta_start=(delta / 10.0 if delta >= 1e-7 else 0.0),
+                            line_search=True)
             delta = out["delta"]
             u, s, x = out["u"], out["s"], out["x"]
             st.update(out["duals"])

@@ -107,9 +107,22 @@ def _max_step_dual(z, dz, tau):
     return 1.0 if not neg.any() else min(1.0, float(np.min(-tau * z[neg] / dz[neg])))
 
 
-def al_step(on, x, u, s, st, al, pd=None, qd=None, max_halvings=10, delta_start=0.0):
+def barrier(u, s, st, mu):
+    """-mu sum log(w - w_lo) - mu sum log(w_hi - w) over w = (u, s) (eq. ipm_subproblem)."""
+    t = 0.0
+    for w, nm in ((u, "u"), (s, "s")):
+        t += np.log(w - st[nm + "_lo"]).sum() + np.log(st[nm + "_hi"] - w).sum()
+    return -mu * t
+
+
+def al_step(on, x, u, s, st, al, pd=None, qd=None, max_halvings=10, delta_start=0.0, line_search=False):
     """One reduced-Newton step: Schur solve, dual step, fraction to the boundary,
-    power flow at the trial control with halving.  Returns the new iterate and the step data."""
+    power flow at the trial control with halving.  Returns the new iterate and the step data.
+
+    line_search: also halve the step until the barrier function psi_mu = F + barrier
+    decreases by the Armijo rule psi(w + a d) <= psi(w) + 1e-4 a grad psi^T d (the step
+    solves a positive definite system, so it is a descent direction); after max_halvings
+    the last trial with a converged power flow is taken."""
     out = schur_step(on, x, u, s, st, al, pd, qd, delta_start=delta_start)
     du, ds = out["du"], out["ds"]
     mu = st["mu"]
@@ -124,12 +137,20 @@ def al_step(on, x, u, s, st, al, pd=None, qd=None, max_halvings=10, delta_start=
     ad = min(_max_step_dual(st[k], dz[k], tau) for k in dz)
     x_new = None
     halvings = 0
+    P = out["pieces"]
+    psi0 = P["g"]["F"] + barrier(u, s, st, mu)
+    slope = float(P["gpsi_u"] @ du + P["gpsi_s"] @ ds)
     while True:
         xt, info = on.powerflow(u + ap * du, pd=pd, qd=qd, x0=x)
         if info["rc"] == 0:
             x_new = xt
-            break
-        if halvings >= max_halvings:
+            if not line_search or halvings >= max_halvings:
+                break
+            st_ = s + ap * ds
+            F_t = on.reduced_gradient(xt, u + ap * du, dict(al, s=st_), pd=pd, qd=qd)["F"]
+            if F_t + barrier(u + ap * du, st_, st, mu) <= psi0 + 1e-4 * ap * slope:
+                break
+        elif halvings >= max_halvings:
             raise RuntimeError("no feasible trial point after halvings")
         ap *= 0.5
         halvings += 1

@@ -74,7 +74,7 @@ class AlState(C.Structure):
 
 class StepOpts(C.Structure):
     _fields_ = [("block_k", C.c_int), ("max_halvings", C.c_int), ("max_inertia", C.c_int),
-                ("delta_start", C.c_double)]
+                ("delta_start", C.c_double), ("line_search", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -159,6 +159,8 @@ def lib():
         L.opf_al_step_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AlParams), C.POINTER(AlState),
                                           C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(StepOpts),
                                           C.POINTER(StepInfo), C.POINTER(C.c_int), C.POINTER(BatchInfo)]
+        L.opf_objective_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(AlParams)] + \
+            [C.c_void_p] * 11 + [C.POINTER(C.c_int)]
         L.opf_al_solve.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                    C.POINTER(AlOpts), C.POINTER(AlInfo), C.POINTER(C.c_double)]
         L.opf_fp64_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)]
@@ -323,6 +325,33 @@ def al_step_batched(ctxs, als, states, loads=None, block_k=0, delta_start=0.0):
     return out, list(stat), {k: getattr(binfo, k) for k, _ in BatchInfo._fields_}
 
 
+def objective_batched(ctxs, al, u, pd, qd, s, x0, grads=False):
+    """F (and with grads=True the adjoint gradients w.r.t. u, pd, qd, s) for the scenarios
+    u [n, n_u], pd/qd [n, n_bus], s [n, m] of one network, spread over the contexts `ctxs`
+    (each should own a stream: OPFContext.use_own_stream).  Returns a dict of cuda tensors."""
+    import torch
+    c0 = ctxs[0]
+    n = u.shape[0]
+    torch.cuda.current_stream(c0.device).synchronize()  # the inputs are on torch's stream
+    keep = [c0._dev(al["sigma_c"]), c0._dev(al["y"])]
+    p = AlParams(float(al["sigma_f"]), float(al["rho"]), keep[0].data_ptr(), keep[1].data_ptr(), None, None)
+    z = lambda *sh: torch.empty(sh, dtype=torch.float64, device=c0.device)  # noqa: E731
+    out = dict(F=z(n))
+    if grads:
+        out.update(grad_u=z(n, c0.nu), grad_pd=z(n, c0.net.n_bus), grad_qd=z(n, c0.net.n_bus), grad_s=z(n, c0.m))
+    for t in (u, pd, qd, s, x0):
+        if t is not None:
+            c0._dev(t)
+    hs = (C.c_void_p * len(ctxs))(*[c.h.value for c in ctxs])
+    stat = (C.c_int * max(1, n))()
+    rc = lib().opf_objective_batched(hs, len(ctxs), n, C.byref(p), _ptr(u), _ptr(pd), _ptr(qd), _ptr(s), _ptr(x0),
+                                     None, _ptr(out["F"]), _ptr(out.get("grad_u")), _ptr(out.get("grad_pd")),
+                                     _ptr(out.get("grad_qd")), _ptr(out.get("grad_s")), stat)
+    if rc != 0:
+        raise OPFError(rc, "opf_objective_batched")
+    return out
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -353,7 +382,17 @@ class OPFContext:
             self.h = None
 
     def _sync_stream(self):
+        if getattr(self, "_own_stream", None) is not None:
+            return
         lib().opf_set_stream(self.h, C.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream))
+
+    def use_own_stream(self):
+        """Bind the context to a stream of its own (for scenario pools that run concurrently);
+        the context's calls then no longer follow torch's current stream."""
+        self._own_stream = self.torch.cuda.Stream(device=self.device)
+        st = lib().opf_set_stream(self.h, C.c_void_p(self._own_stream.cuda_stream))
+        if st != 0:
+            raise OPFError(st, "opf_set_stream")
 
     def _dev(self, v):
         t = self.torch
@@ -502,7 +541,7 @@ class OPFContext:
         return AlState(*[state[k].data_ptr() for k in ("u", "s", "zl_u", "zu_u", "zl_s", "zu_s", "u_lo", "u_hi",
                                                         "s_lo", "s_hi", "x")], float(state["mu"]))
 
-    def al_solve(self, al, state, y, max_outer=20, max_inner=10, eta_primal=1e-5, eta_dual=1e-4, rho_max=1e6,
+    def al_solve(self, al, state, y, max_outer=20, max_inner=30, eta_primal=1e-5, eta_dual=1e-4, rho_max=1e6,
                  block_k=0):
         """Static OPF by the augmented-Lagrangian outer loop (opf_al_solve).  `al`: sigma_f, the initial
         rho and sigma_c; `y` (cuda float64 [m]) and the state tensors are updated in place, and
@@ -545,7 +584,7 @@ class OPFContext:
             raise OPFError(rc, "opf_tracking_update")
         return {k: getattr(info, k) for k, _ in QpInfo._fields_}
 
-    def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0, delta_start=0.0):
+    def al_step(self, al, state, block_k=8, max_halvings=0, max_inertia=0, delta_start=0.0, line_search=False):
         """One reduced-Newton step (Prop. 3).  `state`: dict of cuda float64 tensors u, s, zl_u,
         zu_u, zl_s, zu_s, u_lo, u_hi, s_lo, s_hi, x and the float mu; u, s, the duals and x are
         updated in place.  Returns (du, ds, info)."""
@@ -560,7 +599,8 @@ class OPFContext:
         ds = t.empty(self.m, dtype=t.float64, device=self.device)
         info = StepInfo()
         rc = lib().opf_al_step(self.h, C.byref(p), C.byref(st),
-                               C.byref(StepOpts(int(block_k), int(max_halvings), int(max_inertia), float(delta_start))),
+                               C.byref(StepOpts(int(block_k), int(max_halvings), int(max_inertia), float(delta_start),
+                                                int(bool(line_search)))),
                                C.byref(info), _ptr(du), _ptr(ds))
         if rc != 0:
             raise OPFError(rc, "opf_al_step")

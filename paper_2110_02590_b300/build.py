@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libopf.so")
-SOURCES = ["symbolic.cpp", "opf_kernels.cu", "opf_api.cu", "opf_noalloc.cu", "opf_step.cu", "opf_sweep.cu", "opf_ozaki.cu", "opf_lu_dense.cu", "opf_diag.cu", "opf_al.cu"]
+SOURCES = ["symbolic.cpp", "opf_kernels.cu", "opf_api.cu", "opf_noalloc.cu", "opf_step.cu", "opf_sweep.cu", "opf_ozaki.cu", "opf_lu_dense.cu", "opf_diag.cu", "opf_al.cu", "opf_scenarios.cu"]
 HEADERS = ["opf_internal.h", os.path.join("..", "..", "include", "opf.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--threads", "0"]

@@ -139,7 +139,7 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
     return OPF_EINVAL;
   }
   const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 20;
-  const int max_inner = (o && o->max_inner > 0) ? o->max_inner : 10;
+  const int max_inner = (o && o->max_inner > 0) ? o->max_inner : 30;
   const double eta_p = (o && o->eta_primal > 0.0) ? o->eta_primal : 1e-5;
   const double eta_d = (o && o->eta_dual > 0.0) ? o->eta_dual : 1e-4;
   const double rho_max = (o && o->rho_max > 0.0) ? o->rho_max : 1e6;
@@ -185,7 +185,7 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
       if (E[1] <= omega_k || j == max_inner) break;
       if (E[0] <= 10.0 * mu) mu = std::max(eta_d / 10.0, std::min(0.2 * mu, std::pow(mu, 1.5)));
       st->mu = mu;
-      opf_step_opts so = {block_k, 0, 0, delta >= 1e-7 ? delta / 10.0 : 0.0};
+      opf_step_opts so = {block_k, 0, 0, delta >= 1e-7 ? delta / 10.0 : 0.0, 1};
       rc = opf_al_step(c, &pk, st, &so, &si, nullptr, nullptr);
       if (rc) break;
       delta = si.delta;

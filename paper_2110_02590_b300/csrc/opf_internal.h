@@ -133,6 +133,7 @@ void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, do
 opf_status setup_solve1(opf_ctx* c);  // shared-memory size of the single-RHS sweep
 void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n);
 void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
+void launch_eval_F(opf_ctx* c, const opf_al_params* p, double* F_out);  // F only, into device F_out
 void launch_grad_u(opf_ctx* c, double* gu);
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
 void launch_hess_prep(opf_ctx* c, double sigma_f);

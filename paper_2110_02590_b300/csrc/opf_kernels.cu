@@ -1886,6 +1886,23 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s) {
   launch_solve1(c, c->dFx, c->lam, true, -1.0);
 }
 
+// F alone at the context's state (flows, constraint values and the AL sums;
+// no adjoint solve), into F_out (device).
+void launch_eval_F(opf_ctx* c, const opf_al_params* p, double* F_out) {
+  const DevNet& n = c->dn;
+  cudaMemsetAsync(c->scal + 2, 0, sizeof(double), c->stream);
+  launch_unpack(c, c->x, c->u);
+  branch_flow_kernel<<<nblk(n.nl, 256), 256, 0, c->stream>>>(n, c->vbus, c->thbus, c->flows, c->cvec);
+  bus_inj_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->vbus, c->flows, c->pd, c->qd, c->Pbus,
+                                                         c->Qbus, c->cvec);
+  const int mm = std::max(n.m, n.ng);
+  al_weights_kernel<<<nblk(mm, 256), 256, 0, c->stream>>>(
+      n, c->cvec, p->sigma_c, p->y, p->s, p->omega, p->rho, p->sigma_f, c->Pbus, c->u, c->pd,
+      c->c0, c->phid, nullptr, c->omega, c->scal);
+  c->launches += 3;
+  cudaMemcpyAsync(F_out, c->scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+}
+
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out) {
   const DevNet& n = c->dn;
   c->launches++;

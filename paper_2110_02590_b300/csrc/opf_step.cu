@@ -27,6 +27,7 @@ struct StepWork {
   double *S = nullptr, *L = nullptr;           // n_u x n_u column-major
   double *gu, *gs, *sig_u, *gpsi_u, *sig_s, *gpsi_s, *omega, *v, *r, *du, *ds, *Jtv, *Jdu;
   double *b, *z, *ut, *xt, *pd, *qd;
+  double *strial, *lsv;                         // line search: trial s; [0] F, [1] barrier sum, [2] slope, [3] F_t, [4] barrier sum at the trial
   double *dz;                                   // 2 n_u + 2 m: zl_u, zu_u, zl_s, zu_s steps
   double* red;                                  // [2]: alpha_p, alpha_d (as ordered bits)
   double* Dinv;                                 // [ceil(n_u / 32)][32][32]: inverses of the factor's diagonal blocks
@@ -34,6 +35,7 @@ struct StepWork {
   void* oz_d = nullptr;                         // [8][n_u][128] bf16 digits of the emulated trailing update
   int* flag;
   double* h_red;
+  double* h_ls = nullptr;  // pinned [8]: the line search's reductions
   int* h_flag;
   void* block = nullptr;
   cudaEvent_t ev[7] = {};  // phase boundaries of a step
@@ -61,6 +63,7 @@ void free_step_work(opf_ctx* c) {
   if (w->qp_block) cudaFree(w->qp_block);
   if (w->h_kred) cudaFreeHost(w->h_kred);
   if (w->h_red) cudaFreeHost(w->h_red);
+  if (w->h_ls) cudaFreeHost(w->h_ls);
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
     if (e) cudaEventDestroy(e);
@@ -612,6 +615,32 @@ __global__ void update_kernel(int nu, int m, double* u, const double* du, double
   }
 }
 
+// Line-search terms: out[0] += sum log(w - w_lo) + log(w_hi - w) over w = (u, s)
+// (the barrier is -mu times it), and, when gu is given, out[1] += grad psi^T d.
+__global__ void ls_terms_kernel(int nu, int m, const double* u, const double* s, const double* ulo,
+                                const double* uhi, const double* slo, const double* shi, const double* gu,
+                                const double* du, const double* gs, const double* ds, double* out) {
+  double b = 0.0, sl = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nu + m; i += gridDim.x * blockDim.x) {
+    if (i < nu) {
+      b += log(u[i] - ulo[i]) + log(uhi[i] - u[i]);
+      if (gu) sl += gu[i] * du[i];
+    } else {
+      const int k = i - nu;
+      b += log(s[k] - slo[k]) + log(shi[k] - s[k]);
+      if (gu) sl += gs[k] * ds[k];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, b);
+    if (gu) atomicAdd(out + 1, sl);
+  }
+}
+
 // QP gradient after a step of the tracking QP (Sec. IV-C): the Hessian is
 // constant, and the Newton system (H + Sigma) d = -grad psi gives H d =
 // -grad psi - Sigma d, so grad q <- grad q + alpha (-grad psi - Sigma d).
@@ -653,10 +682,11 @@ opf_status alloc_step(opf_ctx* c) {
   const size_t sizes[] = {(size_t)nu * nu, (size_t)nu * nu, (size_t)nu, (size_t)m, (size_t)nu, (size_t)nu,
                           (size_t)m, (size_t)m, (size_t)m, (size_t)m, (size_t)nu, (size_t)nu, (size_t)m,
                           (size_t)nu, (size_t)m, (size_t)nx, (size_t)nx, (size_t)nu, (size_t)nx, (size_t)nb,
-                          (size_t)nb, 2 * (size_t)nu + 2 * (size_t)m, 2, ((size_t)nu + 31) / 32 * 1024};
+                          (size_t)nb, 2 * (size_t)nu + 2 * (size_t)m, 2, ((size_t)nu + 31) / 32 * 1024,
+                          (size_t)m, 8};
   double** ptrs[] = {&w->S, &w->L, &w->gu, &w->gs, &w->sig_u, &w->gpsi_u, &w->sig_s, &w->gpsi_s, &w->omega,
                      &w->v, &w->r, &w->du, &w->ds, &w->Jtv, &w->Jdu, &w->b, &w->z, &w->ut, &w->xt,
-                     &w->pd, &w->qd, &w->dz, &w->red, &w->Dinv};
+                     &w->pd, &w->qd, &w->dz, &w->red, &w->Dinv, &w->strial, &w->lsv};
   const int np = sizeof(sizes) / sizeof(sizes[0]);
   size_t total = 0;
   for (int k = 0; k < np; k++) total += (sizes[k] + 31) & ~(size_t)31;
@@ -683,6 +713,7 @@ opf_status alloc_step(opf_ctx* c) {
     return OPF_ECUDA;
   }
   if (cudaMallocHost(&w->h_red, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&w->h_ls, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&w->h_flag, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     c->stepw = w;
@@ -814,7 +845,7 @@ opf_status step_begin(opf_ctx* c, const opf_al_params* p, opf_al_state* st, opf_
   opf_al_params ps = *p;
   ps.s = st->s;
   ps.omega = w->omega;
-  rc = opf_reduced_gradient(c, &ps, nullptr, w->gu, w->gs, nullptr, nullptr, nullptr, nullptr);
+  rc = opf_reduced_gradient(c, &ps, w->lsv, w->gu, w->gs, nullptr, nullptr, nullptr, nullptr);
   if (rc) return rc;
   SCK(cudaEventRecord(ev[1], stream));
   step_prep_kernel<<<nblk(std::max(nu, m), 256), 256, 0, stream>>>(
@@ -914,17 +945,47 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   SCK(cudaMemcpyAsync(w->qd, c->qd, nb * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   int halvings = 0;
   opf_pf_info pfi = {0, 0.0, 0.0};
+  const bool ls = o && o->line_search;
+  const int glg = std::max(1, std::min(nblk(nu + m, 256), 4 * c->sm_count));
+  double psi0 = 0.0, slope = 0.0;
+  if (ls) {  // psi at the current point and its slope along the step
+    SCK(cudaMemsetAsync(w->lsv + 1, 0, 2 * sizeof(double), stream));
+    ls_terms_kernel<<<glg, 256, 0, stream>>>(nu, m, st->u, st->s, st->u_lo, st->u_hi, st->s_lo, st->s_hi,
+                                             w->gpsi_u, w->du, w->gpsi_s, w->ds, w->lsv + 1);
+    c->launches++;
+    SCK(cudaMemcpyAsync(w->h_ls, w->lsv, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    psi0 = w->h_ls[0] - st->mu * w->h_ls[1];
+    slope = w->h_ls[2];
+  }
+  opf_al_params pt = *p;  // the AL at the trial point's slacks
+  pt.s = w->strial;
+  pt.omega = nullptr;
   for (;;) {
     axpy2_kernel<<<nblk(nu, 256), 256, 0, stream>>>(nu, st->u, w->du, ap, w->ut);
     // first-order predictor of the new state: x + alpha z, z = dx/du d_u (from J d_u)
     axpy2_kernel<<<nblk(nx, 256), 256, 0, stream>>>(nx, st->x, w->z, ap, w->xt);
     c->launches += 2;
     opf_status prc = opf_powerflow(c, w->ut, w->pd, w->qd, w->xt, nullptr, &pfi);
-    if (prc == OPF_OK) break;
-    if (prc != OPF_ENOCONV && prc != OPF_ESINGULAR) return prc;
-    if (halvings >= max_halvings) {
-      set_last_error("no trial control with a converged power flow after the halvings");
-      return OPF_ENOCONV;
+    if (prc == OPF_OK) {
+      if (!ls || halvings >= max_halvings) break;
+      // Armijo on the barrier function psi_mu = F + barrier at the trial point
+      axpy2_kernel<<<nblk(m, 256), 256, 0, stream>>>(m, st->s, w->ds, ap, w->strial);
+      c->launches++;
+      launch_eval_F(c, &pt, w->lsv + 3);
+      SCK(cudaMemsetAsync(w->lsv + 4, 0, sizeof(double), stream));
+      ls_terms_kernel<<<glg, 256, 0, stream>>>(nu, m, w->ut, w->strial, st->u_lo, st->u_hi, st->s_lo, st->s_hi,
+                                               nullptr, nullptr, nullptr, nullptr, w->lsv + 4);
+      c->launches++;
+      SCK(cudaMemcpyAsync(w->h_ls + 3, w->lsv + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+      SCK(cudaStreamSynchronize(stream));
+      if (w->h_ls[3] - st->mu * w->h_ls[4] <= psi0 + 1e-4 * ap * slope) break;
+    } else {
+      if (prc != OPF_ENOCONV && prc != OPF_ESINGULAR) return prc;
+      if (halvings >= max_halvings) {
+        set_last_error("no trial control with a converged power flow after the halvings");
+        return OPF_ENOCONV;
+      }
     }
     ap *= 0.5;
     halvings++;

@@ -22,11 +22,12 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
 
 
-def make(name, nscen, seed=200):
+def make(name, nscen, seed=200, pool=4):
     net = synth.workload(name)
     ctx = P.OPFContext(net)
     al = synth.al_inputs(net, seed=7)
-    obj = ReducedObjective(ctx, {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})
+    obj = ReducedObjective(ctx, {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()},
+                           pool=pool)
     x0, _ = ctx.powerflow(dev(synth.flat_control(net)))
     obj.set_warm_start(x0)
     pds, qds = synth.ar1_loads(net, nscen, seed=seed)
@@ -36,13 +37,14 @@ def make(name, nscen, seed=200):
 
 
 def test_autograd_matches_oracle_gradient():
-    net, ctx, al, obj, u, pd, qd, s = make("batchB2000", 4)
+    """Six scenarios over a pool of four contexts (two workers take two scenarios each)."""
+    net, ctx, al, obj, u, pd, qd, s = make("batchB2000", 6)
     for t in (u, pd, qd, s):
         t.requires_grad_(True)
     F = obj(u, pd, qd, s)
     F.sum().backward()
     on = oracle.OracleNet(net)
-    for b in range(4):
+    for b in range(6):
         xo, io = on.powerflow(u[b].detach().cpu().numpy(), pd=pd[b].detach().cpu().numpy(),
                               qd=qd[b].detach().cpu().numpy())
         assert io["rc"] == 0
@@ -82,7 +84,7 @@ def test_autograd_central_fd():
 
 def test_autograd_big_grid_single_scenario():
     """The 20,000-bus grid: one scenario, gradient against the oracle."""
-    net, ctx, al, obj, u, pd, qd, s = make("big20000", 1)
+    net, ctx, al, obj, u, pd, qd, s = make("big20000", 1, pool=1)
     u1 = u[0].clone().requires_grad_(True)
     F = obj(u1, pd[0], qd[0], s[0])
     F.backward()

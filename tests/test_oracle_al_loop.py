@@ -6,9 +6,15 @@ independent method finds too: scipy's SLSQP on the reduced problem
 with f and c evaluated through the oracle's power flow and constraint
 functions (their definitions, pinned elsewhere).  A wrong sign or weight in
 the multiplier update, the penalty rule or the step would leave the loop
-infeasible or at another cost.  The 30-bus grid's line limits are widened
-1.5x for this instance: at 1.2x the base-case DC flows the AC flows of the
-base case exceed them and the loop stalls at a primal infeasibility of 0.8.
+infeasible or at another cost.
+
+The static OPF instances take their line limits from the AC base case:
+rate = max(the generator's rate, 1.2 |S| of the base-case AC flow at each
+end).  The generator's own limits are 1.2x the DC flows of the base case, and
+the AC flows exceed them on 7% of the 30-bus grid's branches (up to 1.55x),
+21% of the 1,400-bus grid's (up to 13x) and 35% of the 9,200-bus grid's (up to
+33x), so those instances have no feasible point near the base case and the
+loop stalls at a primal infeasibility of 0.8 to 100.
 """
 import numpy as np
 import pytest
@@ -19,20 +25,32 @@ from oracle import al_step as A
 from paper_2110_02590_b300 import synth
 
 
-def static_setup(name, rate_factor=1.5, mu=0.1, seed=5):
-    """Static OPF instance: nominal loads, line limits rate_factor x the generator's, y = 0,
-    rho = 10; controls 2% inside their bounds, slacks at c clipped 1% inside theirs, duals on
-    the central path at mu."""
+def static_limits(net, c_base, margin=1.2):
+    """Squared line limits of a static OPF instance: max(rate, margin |S|)^2 per branch, |S| the
+    larger end's apparent flow of the base case (c_base: constraint values there)."""
+    nl = net.n_branch
+    s2 = np.maximum(c_base[:nl], c_base[nl:2 * nl])
+    return np.maximum(net.br_rate ** 2, margin ** 2 * s2)
+
+
+def static_setup(name, mu=0.1, seed=5):
+    """Static OPF instance: nominal loads, line limits from the AC base case (static_limits),
+    y = 0, rho = 10; controls 2% inside their bounds, slacks at c clipped 1% inside theirs,
+    duals on the central path at mu."""
     net = synth.workload(name)
     on = oracle.OracleNet(net)
     u_lo, u_hi = synth.control_bounds(net)
-    u = np.clip(synth.flat_control(net), u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
-    x, info = on.powerflow(u)
+    u0 = synth.flat_control(net)
+    x0, info = on.powerflow(u0)
+    assert info["rc"] == 0
+    r2 = static_limits(net, on.eval(x0, u0)["c"])
+    u = np.clip(u0, u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
+    x, info = on.powerflow(u, x0=x0)
     assert info["rc"] == 0
     al = synth.al_inputs(net, seed=seed)
     nl = net.n_branch
-    al["s_hi"][:2 * nl] *= rate_factor ** 2
-    al["sigma_c"][:2 * nl] /= rate_factor ** 2
+    al["s_hi"][:2 * nl] = np.concatenate([r2, r2])
+    al["sigma_c"][:2 * nl] = np.concatenate([1.0 / r2, 1.0 / r2])
     al["y"] = np.zeros(on.m)
     al["rho"] = 10.0
     lo, hi = al["s_lo"], al["s_hi"]
@@ -45,33 +63,47 @@ def static_setup(name, rate_factor=1.5, mu=0.1, seed=5):
 @pytest.fixture(scope="module")
 def tiny_run():
     net, on, x, u, s, al, st = static_setup("tiny30")
-    out = L.al_solve(on, x, u, s, al["y"], st, al, rho=10.0, max_outer=40, max_inner=10)
+    out = L.al_solve(on, x, u, s, al["y"], st, al, rho=10.0, max_outer=40, max_inner=30)
     return net, on, x, u, al, st, out
 
 
 def test_al_loop_converges_to_the_slsqp_optimum(tiny_run):
+    """SLSQP with exact derivatives: the objective's gradient from the oracle's adjoint with the
+    AL terms switched off (y = 0, rho = 0), the constraints' Jacobian from the hyper-dual brute
+    force (independent of the adjoint code)."""
     from scipy.optimize import minimize
     net, on, x, u0, al, st, out = tiny_run
     assert out["converged"]
-    lo, hi = al["s_lo"], al["s_hi"]
+    lo, hi, sc = al["s_lo"], al["s_hi"], al["sigma_c"]
 
     def ev(uu):
         xx, info = on.powerflow(uu, x0=x)
         assert info["rc"] == 0
-        return on.eval(xx, uu)
+        return xx, on.eval(xx, uu)
 
-    res = minimize(lambda uu: al["sigma_f"] * ev(uu)["cost"], u0, method="SLSQP",
+    def grad(uu):
+        xx, e = ev(uu)
+        return on.reduced_gradient(xx, uu, dict(al, y=np.zeros(on.m), rho=0.0, s=e["c"]))["grad_u"]
+
+    def cons(uu):
+        c = ev(uu)[1]["c"]
+        return np.concatenate([(c - lo) * sc, (hi - c) * sc])
+
+    def cons_jac(uu):
+        xx, e = ev(uu)
+        J = on.bruteforce(xx, uu, dict(al, s=e["c"]))["J"] * sc[:, None]
+        return np.vstack([J, -J])
+
+    res = minimize(lambda uu: al["sigma_f"] * ev(uu)[1]["cost"], u0, jac=grad, method="SLSQP",
                    bounds=list(zip(st["u_lo"], st["u_hi"])),
-                   constraints=[{"type": "ineq",
-                                 "fun": lambda uu: np.concatenate([(ev(uu)["c"] - lo) * al["sigma_c"],
-                                                                   (hi - ev(uu)["c"]) * al["sigma_c"]])}],
-                   options=dict(maxiter=500, ftol=1e-12))
-    c_sq = ev(res.x)["c"]
-    assert np.all((c_sq - lo) * al["sigma_c"] > -1e-6) and np.all((hi - c_sq) * al["sigma_c"] > -1e-6)
-    f_al = al["sigma_f"] * ev(out["u"])["cost"]
+                   constraints=[{"type": "ineq", "fun": cons, "jac": cons_jac}],
+                   options=dict(maxiter=1000, ftol=1e-14))
+    assert res.success, res.message
+    assert cons(res.x).min() > -1e-9
+    f_al = al["sigma_f"] * ev(out["u"])[1]["cost"]
     # the barrier (mu = 1e-5 at the end) and eta_p <= 1e-5 keep the AL point within ~1e-4 of the optimum
     assert abs(f_al - res.fun) <= 2e-4 * abs(res.fun), (f_al, res.fun)
-    assert np.abs(out["u"] - res.x).max() < 2e-2
+    assert np.abs(out["u"] - res.x).max() < 3e-2
 
 
 def test_al_loop_invariants(tiny_run):
