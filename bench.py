@@ -401,30 +401,54 @@ def static_opf(P, torch, dev, name, max_outer, max_inner=30, margin=1.2):
                      f"at most {max_inner} reduced-Newton steps per subproblem (one full Hessian each)"}
 
 
+def mean_complementarity(st):
+    """Mean of (w - w_lo) z_lo and (w_hi - w) z_hi over w = (u, s): the barrier a warm-started
+    interior-point solve starts from."""
+    t, n = 0.0, 0
+    for nm in ("u", "s"):
+        w, lo, hi = st[nm], st[nm + "_lo"], st[nm + "_hi"]
+        t += float(((w - lo) * st["zl_" + nm]).sum() + ((hi - w) * st["zu_" + nm]).sum())
+        n += 2 * w.numel()
+    return t / n
+
+
 def tracking_qp(P, torch, ctx, al, state, pds, qds, first, count):
-    """Real-time updates (opf_tracking_update): power flow at the next load snapshot, then the
-    bounded QP of eq. qp_rto to a KKT error of 1e-6 with one Hessian H(omega) per QP iteration,
-    the power flow at the new controls and the multiplier update."""
+    """Real-time updates (opf_tracking_update), one after another: power flow at the next load
+    snapshot, then the bounded QP of eq. qp_rto to a KKT error of 1e-6 (one Hessian H(omega) per
+    QP iteration), the power flow at the new controls and the multiplier update.  Each QP starts
+    from the previous update's point (pushed 1e-4 of the bounds' range inside them) and duals, with
+    its barrier at their mean complementarity."""
     y = al["y"].clone()
     out = []
     dstart = 0.0
     for k in range(count):
+        # a warm start is pushed 1e-4 of its range off the bounds (a QP solved to mu ~ 1e-7 leaves
+        # active slacks ~1e-10 from them, and Sigma ~1e13 then breaks the next Schur factorisation)
+        for nm in ("u", "s"):
+            lo, hi = state[nm + "_lo"], state[nm + "_hi"]
+            gap = 1e-4 * (hi - lo)
+            state[nm].copy_(torch.minimum(torch.maximum(state[nm], lo + gap), hi - gap))
         state["x"], _ = ctx.powerflow(state["u"], pd=pds[first + k], qd=qds[first + k], x0=state["x"])
-        state["mu"] = 1e-2
-        info = ctx.tracking_update(al, state, y, delta_start=dstart)
+        state["mu"] = mean_complementarity(state)
+        mu0 = state["mu"]
+        info = ctx.tracking_update(al, state, y, max_it=100, delta_start=dstart)
         dstart = info["delta_convex"] / 10.0 if info["delta_convex"] >= 1e-7 else 0.0
+        info["mu0"] = mu0
         out.append(info)
     it = [i["qp_iterations"] for i in out]
-    ms = [i["ms_total"] for i in out]
-    return {"updates": count, "qp_iterations": it, "ms_per_update": statistics.median(ms),
-            "ms_hessians_per_update": statistics.median(i["ms_hessian"] for i in out),
-            "ms_cholesky_per_update": statistics.median(i["ms_cholesky"] for i in out),
-            "hvps_per_update": statistics.median(it) * ctx.nu,
+    return {"updates": count, "qp_iterations": it, "ms_per_update": [i["ms_total"] for i in out],
+            "ms_hessians_per_update": [i["ms_hessian"] for i in out],
+            "ms_cholesky_per_update": [i["ms_cholesky"] for i in out],
+            "hvps_per_update": [(n + 1) * ctx.nu for n in it],
             "ms_per_qp_iteration": statistics.median(i["ms_qp"] / max(1, i["qp_iterations"]) for i in out),
-            "kkt": max(i["kkt"] for i in out), "delta": [i["delta"] for i in out],
-            "delta_convex": [i["delta_convex"] for i in out],
-            "note": "QP barrier starts at mu = 1e-2 each update; stops at E_0 <= 1e-6; the QP is convexified "
-                    "(H_uu + delta I positive definite; the search starts at a tenth of the previous update's delta)"}
+            "kkt_first": [i["kkt_first"] for i in out], "kkt": [i["kkt"] for i in out],
+            "mu0": [i["mu0"] for i in out], "delta_convex": [i["delta_convex"] for i in out],
+            "halvings": [i["halvings"] for i in out],
+            "note": "the first update starts from the bench's tracking state (not an optimum: slacks within "
+                    "1e-6 of their bounds, KKT error ~1e9); the later ones from the previous QP solution; "
+                    "stop at E_0 <= 1e-6 or 100 iterations; the QP is convexified (H_uu + delta I positive "
+                    "definite, the search starting at a tenth of the previous update's delta); HVPs per update "
+                    "count the convexity Hessian H(0) and one H(omega) per iteration"}
 
 
 def batched_snapshots(P, torch, dev, block_k):
@@ -457,9 +481,58 @@ def batched_snapshots(P, torch, dev, block_k):
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
     bms = statistics.median(ms)
-    return {"snapshots": len(snaps), "hvps": nhvp, "launches": 1, "tiles": info["tiles"], "grid": info["grid"],
-            "ms_batched": bms, "hvps_per_s_batched": nhvp / (bms * 1e-3),
-            "ms_per_snapshot_calls": seq_s * 1e3, "hvps_per_s_per_snapshot_calls": nhvp / seq_s}
+    out = {"snapshots": len(snaps), "hvps": nhvp, "launches": 1, "tiles": info["tiles"], "grid": info["grid"],
+           "ms_batched": bms, "hvps_per_s_batched": nhvp / (bms * 1e-3),
+           "ms_per_snapshot_calls": seq_s * 1e3, "hvps_per_s_per_snapshot_calls": nhvp / seq_s}
+    out["batched_steps"] = batched_steps(P, torch, dev, snaps)
+    return out
+
+
+def batched_steps(P, torch, dev, snaps):
+    """The whole config-3 tracking update batched (opf_al_step_batched): every snapshot from an
+    interior primal-dual point, the power flow at its next load snapshot, then one reduced-Newton
+    step, all Schur Hessians in one launch; against the same updates snapshot by snapshot."""
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
+
+    def states():
+        sts, loads = [], []
+        for c, al in snaps:
+            net = c.net
+            u_lo, u_hi = synth.control_bounds(net)
+            u = np.clip(synth.flat_control(net), u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
+            x, _ = c.powerflow(d(u))
+            cc = c.reduced_gradient(al)["c"].cpu().numpy()
+            lo, hi = al["s_lo"].cpu().numpy(), al["s_hi"].cpu().numpy()
+            sv = np.clip(cc, lo + 0.01 * (hi - lo), hi - 0.01 * (hi - lo))
+            mu = 0.1
+            sts.append(dict(u=d(u), s=d(sv), x=x, u_lo=d(u_lo), u_hi=d(u_hi), s_lo=d(lo), s_hi=d(hi), mu=mu,
+                            zl_u=d(mu / (u - u_lo)), zu_u=d(mu / (u_hi - u)), zl_s=d(mu / (sv - lo)),
+                            zu_s=d(mu / (hi - sv))))
+            pds, qds = synth.ar1_loads(net, 3, seed=500 + len(loads))
+            loads.append((d(pds[2]), d(qds[2])))
+        return sts, loads
+
+    ctxs, als = [c for c, _ in snaps], [a for _, a in snaps]
+    sts, loads = states()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos, stat, binfo = P.al_step_batched(ctxs, als, sts, loads=loads)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    sts, loads = states()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, al, st, (pd, qd) in zip(ctxs, als, sts, loads):
+        st["x"], _ = c.powerflow(st["u"], pd=pd, qd=qd, x0=st["x"])
+        c.al_step(al, st, block_k=0)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    return {"snapshots": len(ctxs), "failed": binfo["failed"], "ms_batched": tb * 1e3,
+            "snapshots_per_s_batched": len(ctxs) / tb, "ms_per_snapshot_calls": ts * 1e3,
+            "snapshots_per_s_per_snapshot_calls": len(ctxs) / ts, "phases_ms": {
+                "powerflow_first_order": binfo["ms_powerflow_first_order"], "hessians": binfo["ms_hessians"],
+                "steps": binfo["ms_steps"]}, "host_threads": binfo["host_threads"],
+            "hessian_tiles": binfo["hessian_tiles"]}
 
 
 def run_gpu(args):
@@ -491,7 +564,7 @@ def run_gpu(args):
     state["x"], _ = ctx.powerflow(state["u"], x0=x0)
     tune = ctx.autotune(dict(al, s=state["s"]))
     ke = max(1, min(args.steps, args.e2e_steps))  # end-to-end steps, on the snapshots after the timed ones
-    nsnap = args.warmup + args.steps + 1 + ke + 3  # the last three: the tracking-QP leg
+    nsnap = args.warmup + args.steps + 1 + ke + 4  # the last four: the tracking-QP leg
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
     pds, qds = d(pds_h), d(qds_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -598,7 +671,7 @@ def run_gpu(args):
         sharded = {"ms": sh_ms, "hvps_per_s": nu / (sh_ms * 1e-3), "ranks": world,
                    "split": "contiguous column ranges in whole tiles, one NCCL all-gather of H"}
     rto = None if args.no_extras else tracking_qp(P, torch, ctx, al, state, pds, qds,
-                                                  args.warmup + args.steps + 1 + ke, 3)
+                                                  args.warmup + args.steps + 1 + ke, 4)
     al_static = None if args.no_extras else [static_opf(P, torch, dev, "medium1400", 20),
                                              static_opf(P, torch, dev, WORKLOAD, 3)]
 

@@ -423,6 +423,7 @@ typedef struct {
 typedef struct {
   int qp_iterations, halvings, pf_iterations, inertia_increases;
   double delta, delta_convex, kkt, mu, alpha_p;  /* delta at the end, at the start (convexity) */
+  double kkt_first, alpha_p_min;  /* the QP's KKT error at d = 0; its smallest primal step length */
   float ms_total;     /* the whole update */
   float ms_qp;        /* gradient at w_t and the QP iterations */
   float ms_hessian;   /* summed device time of the QP's Hessians H(omega) */

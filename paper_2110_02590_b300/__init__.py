@@ -105,7 +105,8 @@ class QpInfo(C.Structure):
     _fields_ = [("qp_iterations", C.c_int), ("halvings", C.c_int), ("pf_iterations", C.c_int),
                 ("inertia_increases", C.c_int), ("delta", C.c_double), ("delta_convex", C.c_double),
                 ("kkt", C.c_double), ("mu", C.c_double),
-                ("alpha_p", C.c_double), ("ms_total", C.c_float), ("ms_qp", C.c_float), ("ms_hessian", C.c_float),
+                ("alpha_p", C.c_double), ("kkt_first", C.c_double), ("alpha_p_min", C.c_double),
+                ("ms_total", C.c_float), ("ms_qp", C.c_float), ("ms_hessian", C.c_float),
                 ("ms_cholesky", C.c_float)]
 
 

@@ -10,9 +10,14 @@
 // eight digit pairs each) the sum over the K <= 128 columns stays below 2^24:
 // the tensor core's FP32 accumulation is exact in any order.  The FP64 result
 // is then sum_t 2^(E_r + E_c - 14 - 7 t) acc_t, summed in FP64.  Levels t >= 8
-// and the digit tails are dropped: each term of the update carries an error
-// below ~2^-53 |P_r|max |P_c|max, the order of an FP64 dot product's own
-// rounding bound.
+// (at most 7 digit pairs at level 8, each further level 2^-7 smaller) and the
+// digit tails (below 2^(E_r - 56)) are dropped: each of the K products errs by
+// less than 9.1 2^(E_r + E_c - 56) < 4.6 u max_k|P_rk| max_k|P_ck| (u = 2^-53,
+// 2^E_r <= 2 max_k|P_rk|), so an element of the update errs by less than
+// 5 K u max_k|P_rk| max_k|P_ck| before the final FP64 roundings.  The bound is
+// relative to the rows' largest entries, not to sum_k |P_rk P_ck| as an FP64
+// dot product's: the small entries of a row with a wide dynamic range lose
+// relative accuracy.
 //
 // The digits are computed with integer shifts of the FP64 bit patterns (no
 // rounding step), and the tensor-core work is 36 digit pairs per output: the

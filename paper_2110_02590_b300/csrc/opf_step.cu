@@ -1123,7 +1123,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
   SCK(cudaMemcpyAsync(w->x0, st->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   pt.s = w->s0;  // the Hessian's first-order weights stay those of w_t
   double mu = st->mu, delta = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
-  double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0;
+  double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0, kkt_first = 0.0, ap_min = 1.0;
   float ms_hess = 0.f, ms_chol = 0.f;
   int it = 0, increases = 0;
   // convexity: the smallest delta of {delta_start or 0, 1e-8, 1e-7, ...} with H_uu + delta I
@@ -1170,6 +1170,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     SCK(cudaStreamSynchronize(stream));
     e_mu = std::max(w->h_kred[0], w->h_kred[1]);
     e_0 = std::max(w->h_kred[0], w->h_kred[2]);
+    if (it == 0) kkt_first = e_0;
     if (e_0 <= tol || it == max_it) break;
     if (e_mu <= 10.0 * mu) mu = std::max(tol / 10.0, std::min(0.2 * mu, std::pow(mu, 1.5)));
     step_prep_kernel<<<gb, 256, 0, stream>>>(nu, m, st->u, st->u_lo, st->u_hi, st->zl_u, st->zu_u, st->s, st->s_lo,
@@ -1250,6 +1251,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     }
     ap = w->h_red[0];
     ad = w->h_red[1];
+    ap_min = std::min(ap_min, ap);
     update_kernel<<<gb, 256, 0, stream>>>(nu, m, st->u, w->du, st->s, w->ds, st->zl_u, st->zu_u, st->zl_s, st->zu_s,
                                           w->dz, ap, ad);
     qp_grad_update_kernel<<<gb, 256, 0, stream>>>(nu, m, w->gqu, w->gqs, w->gpsi_u, w->gpsi_s, w->sig_u, w->sig_s,
@@ -1298,6 +1300,8 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     info->delta = delta;
     info->delta_convex = delta_convex;
     info->kkt = e_0;
+    info->kkt_first = kkt_first;
+    info->alpha_p_min = ap_min;
     info->mu = mu;
     info->alpha_p = ap;
     info->ms_hessian = ms_hess;
