@@ -339,10 +339,25 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dupload(c, &ip, h.adj_ptr)); n.adj_ptr = ip;
   TRY(dupload(c, &ip, h.adj)); n.adj = ip;
   {
-    std::vector<int> order(nb);
-    for (int i = 0; i < nb; i++) order[i] = i;
+    // buses by descending degree, then by the kind of bus (a generator's own
+    // injection terms) and by their ends toward generator buses (last in each
+    // adjacency list): four buses with the same key share a warp in the gathers
+    std::vector<int> order(nb), gen_ends(nb, 0), slack_end(nb, 0);
+    for (int i = 0; i < nb; i++) {
+      order[i] = i;
+      for (int k = h.adj_ptr[i]; k < h.adj_ptr[i + 1]; k++) {
+        const int e = h.adj[k], l = e >> 1, o = (e & 1) ? h.f[l] : h.t[l];
+        if (h.type[o] != PQ) gen_ends[i]++;
+        if (o == h.ref) slack_end[i] = 1;
+      }
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      return h.adj_ptr[a + 1] - h.adj_ptr[a] > h.adj_ptr[b + 1] - h.adj_ptr[b];
+      const int da = h.adj_ptr[a + 1] - h.adj_ptr[a], db = h.adj_ptr[b + 1] - h.adj_ptr[b];
+      if (da != db) return da > db;
+      const int ca = gn_of[a] >= 0, cb = gn_of[b] >= 0;
+      if (ca != cb) return ca > cb;
+      if (gen_ends[a] != gen_ends[b]) return gen_ends[a] > gen_ends[b];
+      return slack_end[a] > slack_end[b];
     });
     TRY(dupload(c, &ip, order)); n.bus_by_deg = ip;
   }
@@ -670,6 +685,9 @@ static void free_impl(opf_ctx* c) {
   if (c->batch_buf) cudaFree(c->batch_buf);
   if (c->lu_exec) cudaGraphExecDestroy(c->lu_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->worker) cudaStreamDestroy(c->worker);
+  for (cudaEvent_t e : c->worker_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 

@@ -473,6 +473,8 @@ struct opf_ctx {
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t worker = nullptr;   // the context's own stream inside a batched call (created on first use)
+  cudaEvent_t worker_ev[2] = {};   // ordering between the caller's stream and the worker stream
   cudaGraphExec_t lu_exec = nullptr;
   long long lu_graph_kernels = 0;
   opf::SweepStreams sw;            // level-packed single-RHS sweep streams

@@ -1339,6 +1339,34 @@ extern "C" opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf
   }
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
+  // every context works on a stream of its own during the call (contexts created on
+  // one stream would otherwise serialise the host threads' work): it starts after
+  // the work already on the context's stream, and that stream waits for it at the end
+  std::vector<cudaStream_t> caller(n);
+  for (int k = 0; k < n; k++) {
+    opf_ctx* c = ctxs[k];
+    if (!c->worker) {
+      if (cudaStreamCreateWithFlags(&c->worker, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->worker_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->worker_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("cannot create a context's worker stream");
+        return OPF_ECUDA;
+      }
+    }
+    caller[k] = c->stream;
+    SCK(cudaEventRecord(c->worker_ev[0], c->stream));
+    SCK(cudaStreamWaitEvent(c->worker, c->worker_ev[0], 0));
+    c->stream = c->worker;
+  }
+  auto restore = [&]() {
+    for (int k = 0; k < n; k++) {
+      opf_ctx* c = ctxs[k];
+      cudaEventRecord(c->worker_ev[1], c->worker);
+      cudaStreamWaitEvent(caller[k], c->worker_ev[1], 0);
+      c->stream = caller[k];
+    }
+  };
   // contexts by decreasing work (longest processing time first) for the host threads
   std::vector<int> order(n);
   for (int k = 0; k < n; k++) order[k] = k;
@@ -1397,9 +1425,12 @@ extern "C" opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf
   if (!live.empty()) {
     opf_hess_opts ho = {o ? o->block_k : 0, 0, 0, 0, 0, 0, 1};
     const opf_status r = opf_reduced_hessian_batched(live.data(), (int)live.size(), lp.data(), lh.data(), &ho, &hi);
-    if (r) return r;
+    if (r) {
+      restore();
+      return r;
+    }
     ms_hess = hi.ms_total;
-    for (opf_ctx* c : live) SCK(cudaEventRecord(c->stepw->ev[2], c->stream));
+    for (opf_ctx* c : live) cudaEventRecord(c->stepw->ev[2], c->stream);
   }
   const auto t2 = clk::now();
   // (C) Cholesky, solves, fraction to the boundary, trial power flows, update
@@ -1407,6 +1438,7 @@ extern "C" opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf
     return step_end(ctxs[k], &params[k], &states[k], o, infos ? &infos[k] : nullptr, nullptr, nullptr, ms_hess);
   });
   const auto t3 = clk::now();
+  restore();
   opf_status first = OPF_OK;
   int failed = 0;
   for (int k = 0; k < n; k++) {

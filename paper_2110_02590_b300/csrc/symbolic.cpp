@@ -114,6 +114,18 @@ std::string build_hostnet(const opf_network_desc* d, HostNet& h) {
     h.adj[fill[h.f[l]]++] = 2 * l;
     h.adj[fill[h.t[l]]++] = 2 * l + 1;
   }
+  // within each bus, the ends whose other bus carries a generator come last (the
+  // slack's last of all): the HVP gathers add Gauss-Newton terms for exactly those
+  // ends, so buses with the same degree and the same count of such ends (which
+  // the gathers take side by side) run those terms in step
+  for (int b = 0; b < nb; b++) {
+    auto key = [&](int e) {
+      const int l = e >> 1, o = (e & 1) ? h.f[l] : h.t[l];
+      return h.type[o] == PQ ? 0 : (h.type[o] == PV ? 1 : 2);
+    };
+    std::stable_sort(h.adj.begin() + h.adj_ptr[b], h.adj.begin() + h.adj_ptr[b + 1],
+                     [&](int a, int c) { return key(a) < key(c); });
+  }
   // every bus must reach the slack
   std::vector<char> seen(nb, 0);
   std::queue<int> q;
