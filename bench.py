@@ -325,6 +325,37 @@ def solve_phase(sym, nx, nu, k, hvp_ms, share, hbm_peak, fp64_tf):
             "hbm_frac_ceiling_at_fp64_peak": (fp64_tf * 1e3 / hbm_peak) / (flops / byts)}
 
 
+def reduced_jacobian_leg(ctx, alh, flush, hess_ms):
+    """The reduced constraint Jacobian (m x n_u) from the HVP tiles' first adjoint: alone (the
+    tiles stop after the L and U sweeps), beside the Hessian in the same launch, and the
+    gradient-based scaling built on it (medians of 3 after one warm-up)."""
+    import torch
+    Jt = torch.empty((ctx.nu, ctx.m), dtype=torch.float64, device=ctx.device)
+    alone, both, scal = [], [], []
+    for r in range(4):
+        flush.zero_()
+        _, _, i1 = ctx.reduced_jacobian(None, block_k=8, out=Jt)
+        flush.zero_()
+        _, _, i2 = ctx.reduced_jacobian(alh, hessian=True, block_k=8, out=Jt)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, sf, _ = ctx.gradient_scaling(out_jacobian=Jt)
+        torch.cuda.synchronize()
+        if r:
+            alone.append(i1["ms_total"])
+            both.append(i2["ms_total"])
+            scal.append(1e3 * (time.perf_counter() - t0))
+    del Jt
+    ms_alone, ms_both = statistics.median(alone), statistics.median(both)
+    return {"rows_m": ctx.m, "columns": ctx.nu, "bytes": 8 * ctx.m * ctx.nu,
+            "ms_jacobian_only": ms_alone, "ms_with_hessian": ms_both, "ms_hessian_alone": hess_ms,
+            "byproduct_ms": ms_both - hess_ms,
+            "ms_gradient_scaling_host": statistics.median(scal), "sigma_f": sf,
+            "form": "J e_j = d_u c e_j + d_x c z_j from each tile's first adjoint z (Sec. III-B); "
+                    "written column-major, m x n_u"}
+
+
 def autograd_batch(P, torch, dev, nscen):
     """Config 4: ReducedObjective (torch.autograd.Function, adjoint backward with the power flows
     recomputed) on a batch of AR(1) load scenarios of the 2,000-bus net, forward + backward,
@@ -628,6 +659,8 @@ def run_gpu(args):
     _, pinfo = ctx.reduced_hessian(alh, plain=True, col_begin=pc0, col_count=pc)
     plain_ms_per_col = pinfo["ms_hvp"] / pc
 
+    jac = None if args.no_extras else reduced_jacobian_leg(ctx, alh, flush, hess_ms)
+
     flops = hvp_flops_per_column(sym, nx, net.n_branch) * nu
     achieved_tf = flops / (hvp_ms * 1e-3) / 1e12
     hbm_peak, hbm_kind = peaks()
@@ -716,6 +749,7 @@ def run_gpu(args):
         "autograd": auto,
         "hessian_sharded": sharded,
         "rto_tracking_qp": rto,
+        "reduced_jacobian": jac,
         "static_opf_al": al_static,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp64_tf,

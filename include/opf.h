@@ -214,6 +214,51 @@ opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_h
                                double* H, opf_hess_info* info);
 
 /*
+ * opf_reduced_jacobian: the reduced constraint Jacobian J = dc/du on the
+ * manifold g = 0 (Sec. III-B, "Reduced sensitivities"), at the state of the
+ * last converged power flow.  Column j is d_u c e_j + d_x c z_j with
+ * z_j = -G_x^{-1} G_u e_j: the first adjoint of the HVP tiles (Prop. 2), so J
+ * is a by-product of the Hessian's tiles.  The paper forms the reduced
+ * Jacobians of h and r from m transposed solves; the tiles need the n_u
+ * forward solves the Hessian already makes (n_u < m on every network here).
+ *   J (device, required): m x n_u column-major, column j at J + j m; rows in
+ *     the order of c (|S_f|^2 and |S_t|^2 per branch, v of each PQ bus, p_ref,
+ *     q_ref, q of each PV unit).
+ *   H (device, may be NULL): non-NULL computes the Hessian columns in the same
+ *     launch, exactly as opf_reduced_hessian (p required).  NULL stops the
+ *     tiles after the first adjoint (the L and U sweeps only); p may then be
+ *     NULL (the branch tables are evaluated with zero multipliers; J does not
+ *     depend on them).
+ *   opts: as opf_reduced_hessian (block_k, grid, columns, threads,
+ *     reuse_first_order, phase_profile); plain must be 0, and asymmetry is
+ *     ignored without H.  Only the requested columns of J are written.
+ * The call replaces the context's first-order quantities unless
+ * reuse_first_order.  Errors: OPF_EINVAL, OPF_ESTATE, OPF_ESINGULAR.
+ */
+opf_status opf_reduced_jacobian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts, double* J,
+                                double* H, opf_hess_info* info);
+
+/*
+ * opf_gradient_scaling: the scaling of the AL problem by the size of its
+ * gradients (Sec. IV-A, "Scaling", where the paper cites the gradient-based
+ * rule of interior-point codes without stating it), at the state of the last
+ * converged power flow:
+ *   sigma_c[i] = 1 if ||dc_i/du||_inf <= g_max, else max(s_min, g_max / ||dc_i/du||_inf)
+ *   sigma_f    = the same with the reduced gradient of the generation cost
+ * Both derivatives are reduced ones (on g = 0): J from opf_reduced_jacobian,
+ * the cost gradient from Prop. 1.  The usual values are g_max = 100 and
+ * s_min = 1e-8.
+ *   J (device, m x n_u column-major, 8 m n_u bytes): receives the Jacobian
+ *     (the caller's workspace).
+ *   sigma_c (device [m]): the constraint scales.  sigma_f (host, may be NULL).
+ * The call replaces the context's first-order quantities (evaluated with zero
+ * multipliers).  Errors: OPF_EINVAL (g_max <= 0 or not finite, s_min outside
+ * (0, 1]), OPF_ESTATE, OPF_ESINGULAR.
+ */
+opf_status opf_gradient_scaling(opf_ctx* ctx, double g_max, double s_min, double* J, double* sigma_c,
+                                double* sigma_f);
+
+/*
  * opf_hessian_autotune: time opf_reduced_hessian on the context's current state
  * for each (block_k, threads) in {(4,128), (4,256), (8,128), (8,256), (8,512),
  * (16,256), (16,512), (32,256)} (one untimed and one timed call each, CUDA events on the

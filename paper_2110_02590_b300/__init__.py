@@ -154,6 +154,10 @@ def lib():
         L.opf_hessian_autotune.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(HessOpts),
                                            C.POINTER(C.c_float)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
+        L.opf_reduced_jacobian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
+                                           C.c_void_p, C.POINTER(HessInfo)]
+        L.opf_gradient_scaling.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                           C.POINTER(C.c_double)]
         L.opf_set_wait_limit.argtypes = [C.c_void_p, C.c_int]
         L.opf_tracking_update.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                           C.POINTER(QpOpts), C.POINTER(QpInfo)]
@@ -520,6 +524,53 @@ class OPFContext:
         return H.T, dict(block_k=info.block_k, grid=info.grid, tiles=info.tiles, launches=info.launches,
                          ms_total=info.ms_total, ms_hvp=info.ms_hvp, asymmetry=info.asymmetry,
                          phase_ms=list(info.phase_ms))
+
+    def reduced_jacobian(self, al=None, hessian=False, block_k=8, grid=0, col_begin=0, col_count=0, threads=0,
+                         out=None, out_hessian=None):
+        """Reduced constraint Jacobian J = dc/du (m x n_u) from the HVP tiles' first adjoint
+        (opf_reduced_jacobian).  With hessian=True the same launch also returns the reduced Hessian
+        (as reduced_hessian; `al` required), else `al` may be None.  `out`: a preallocated
+        (n_u, m) float64 buffer whose row j receives column j of J.  Returns (J, H or None, info)
+        with J an (m, n_u) view."""
+        t = self.torch
+        self._sync_stream()
+        if hessian and al is None:
+            raise ValueError("the Hessian needs the AL parameters")
+        p, keep = self._al(al) if al is not None else (None, [])
+        if out is None:
+            Jt = t.empty((self.nu, self.m), dtype=t.float64, device=self.device)
+        else:
+            Jt = self._dev(out)
+            if tuple(Jt.shape) != (self.nu, self.m):
+                raise ValueError(f"out must have shape ({self.nu}, {self.m}), got {tuple(Jt.shape)}")
+        H = self._out_hessian(out_hessian) if hessian else None
+        info = HessInfo()
+        opts = HessOpts(int(block_k), int(grid), 0, int(col_begin), int(col_count), int(threads), 0, 0, 0)
+        st = lib().opf_reduced_jacobian(self.h, C.byref(p) if p is not None else None, C.byref(opts), _ptr(Jt),
+                                        _ptr(H) if H is not None else None, C.byref(info))
+        if st != 0:
+            raise OPFError(st, "opf_reduced_jacobian")
+        return Jt.T, (H.T if H is not None else None), dict(block_k=info.block_k, grid=info.grid,
+                                                             tiles=info.tiles, launches=info.launches,
+                                                             ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+
+    def gradient_scaling(self, g_max=100.0, s_min=1e-8, out_jacobian=None):
+        """Gradient-based scales of the AL problem (opf_gradient_scaling): returns (sigma_c [m] on the
+        device, sigma_f, J as an (m, n_u) view)."""
+        t = self.torch
+        self._sync_stream()
+        if out_jacobian is None:
+            Jt = t.empty((self.nu, self.m), dtype=t.float64, device=self.device)
+        else:
+            Jt = self._dev(out_jacobian)
+            if tuple(Jt.shape) != (self.nu, self.m):
+                raise ValueError(f"out_jacobian must have shape ({self.nu}, {self.m})")
+        sig = t.empty(self.m, dtype=t.float64, device=self.device)
+        sf = C.c_double(0.0)
+        st = lib().opf_gradient_scaling(self.h, float(g_max), float(s_min), _ptr(Jt), _ptr(sig), C.byref(sf))
+        if st != 0:
+            raise OPFError(st, "opf_gradient_scaling")
+        return sig, sf.value, Jt.T
 
     def reduced_hessian_noalloc(self, al, block_k=8, grid=0, out=None, col_begin=0, col_count=0):
         """Reduced Hessian through opf_reduced_hessian_noalloc (fixed static workspace, no allocation

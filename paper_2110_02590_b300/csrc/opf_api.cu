@@ -932,12 +932,34 @@ static opf_status ensure_scratch(opf_ctx* c, size_t doubles) {
   return OPF_OK;
 }
 
-opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hess_opts* o,
-                               double* H, opf_hess_info* info) {
-  if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
+}  // extern "C"
+
+// Zero multipliers, slacks and scalings [m] (first use): the AL inputs of the
+// evaluations that need the branch tables but no multiplier (J alone, the
+// generation cost's gradient).
+opf_status opf::zero_params(opf_ctx* c, opf_al_params* q) {
+  if (!c->zeros_m) {
+    TRY(dalloc(c, &c->zeros_m, (size_t)std::max(c->h.m, 1)));
+    CK(cudaMemsetAsync(c->zeros_m, 0, sizeof(double) * std::max(c->h.m, 1), c->stream));
+  }
+  *q = opf_al_params{0.0, 0.0, c->zeros_m, c->zeros_m, c->zeros_m, nullptr};
+  return OPF_OK;
+}
+
+// The tiled Hessian and, with J, the reduced constraint Jacobian of the same
+// columns (jac_only: J alone, the tiles stop after the first adjoint).
+static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hess_opts* o, double* H, double* J,
+                               bool jac_only, opf_hess_info* info) {
   if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
   TRY(ensure_factors(c));
+  opf_al_params p0;
+  if (!p && jac_only) {
+    if (o && o->reuse_first_order) FAIL(OPF_EINVAL, "reuse_first_order needs the parameters");
+    TRY(zero_params(c, &p0));
+    p = &p0;
+  }
   TRY(check_al(c, p));
+  if (J && o && o->plain) FAIL(OPF_EINVAL, "the plain form does not compute J");
   const bool tuned = !(o && o->block_k) && c->tuned_k > 0;
   int C = (o && o->block_k) ? o->block_k : (tuned ? c->tuned_k : 8);
   if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32)
@@ -986,6 +1008,8 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   launch_hess_prep(c, p->sigma_f);
   CK(cudaEventRecord(c->ev[1], st));
   int launches = 0;
+  c->jac_out = J;
+  c->jac_only = jac_only;
   if (plain) {
     launches = launch_hvp_plain(c, H, col0, col0 + ncol, c->scratch);
   } else if (split) {
@@ -997,13 +1021,15 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
   }
   CK(cudaEventRecord(c->ev[2], st));
   c->stamps_on = false;
+  c->jac_out = nullptr;
+  c->jac_only = false;
   std::vector<unsigned long long> stamps;
   if (prof) {
     stamps.resize(8 * (size_t)ntiles);
     CK(cudaMemcpyAsync(stamps.data(), c->stamps, sizeof(unsigned long long) * stamps.size(),
                        cudaMemcpyDeviceToHost, st));
   }
-  const bool asym = info && o && o->asymmetry && col0 == 0 && ncol == nu;
+  const bool asym = info && o && o->asymmetry && col0 == 0 && ncol == nu && !jac_only;
   if (asym) {  // after the timed region
     CK(cudaMemsetAsync(c->scal + 4, 0, 2 * sizeof(double), st));
     launch_hess_asymmetry(c, H, nu, c->scal + 4);
@@ -1034,6 +1060,48 @@ opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hes
         for (int k = 0; k < 5; k++) info->phase_ms[k] = (float)(info->ms_hvp * part[k] / tot);
     }
   }
+  return OPF_OK;
+}
+
+extern "C" {
+
+opf_status opf_reduced_hessian(opf_ctx* c, const opf_al_params* p, const opf_hess_opts* o,
+                               double* H, opf_hess_info* info) {
+  if (!c || !H) FAIL(OPF_EINVAL, "ctx and H are required");
+  return hessian_impl(c, p, o, H, nullptr, false, info);
+}
+
+opf_status opf_reduced_jacobian(opf_ctx* c, const opf_al_params* p, const opf_hess_opts* o, double* J,
+                                double* H, opf_hess_info* info) {
+  if (!c || !J) FAIL(OPF_EINVAL, "ctx and J are required");
+  if (H && !p) FAIL(OPF_EINVAL, "the Hessian needs the AL parameters");
+  return hessian_impl(c, p, o, H, J, H == nullptr, info);
+}
+
+opf_status opf_gradient_scaling(opf_ctx* c, double g_max, double s_min, double* J, double* sigma_c,
+                                double* sigma_f) {
+  if (!c || !J || !sigma_c) FAIL(OPF_EINVAL, "ctx, J and sigma_c are required");
+  if (!(g_max > 0.0) || !std::isfinite(g_max) || !(s_min > 0.0 && s_min <= 1.0))
+    FAIL(OPF_EINVAL, "g_max must be positive and finite, s_min in (0, 1]");
+  if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  if (!c->gscale) TRY(dalloc(c, &c->gscale, (size_t)c->h.nu + 1));
+  // the generation cost's reduced gradient: the AL functional with sigma_f = 1
+  // and no multiplier or penalty term is the cost itself (Prop. 1)
+  TRY(ensure_factors(c));
+  opf_al_params p;
+  TRY(zero_params(c, &p));
+  p.sigma_f = 1.0;
+  launch_first_order(c, &p, nullptr);
+  launch_grad_u(c, c->gscale);
+  opf_hess_opts o{};
+  o.reuse_first_order = 1;
+  TRY(hessian_impl(c, &p, &o, nullptr, J, true, nullptr));
+  launch_grad_scaling(c, J, c->gscale, g_max, s_min, sigma_c, c->gscale + c->h.nu);
+  double sf = 1.0;
+  CK(cudaMemcpyAsync(&sf, c->gscale + c->h.nu, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  if (sigma_f) *sigma_f = sf;
   return OPF_OK;
 }
 

@@ -103,6 +103,9 @@ struct HvpArgs {
   const int* ubus;  // bus of each control
   const int* colmap;  // null: tile position p is column col0 + p; else column colmap[p] (-1: none)
   double* H;
+  const double* flows;  // [4 nl] end flows Pf, Qf, Pt, Qt at the state (the |S|^2 rows of J)
+  double* J;            // null, or the reduced constraint Jacobian [n_u][m] (column j at J + j m)
+  int jac_only;         // 1: the tiles stop after J (H untouched, may be null)
   double* scratch;
   unsigned long long* stamps;  // null, or [tiles][8] phase stamps per tile (hvp_stamp)
   size_t stride;    // doubles of scratch per CTA
@@ -135,6 +138,10 @@ void launch_axpy(opf_ctx* c, double* x, const double* d, double a, int n);
 void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
 void launch_eval_F(opf_ctx* c, const opf_al_params* p, double* F_out);  // F only, into device F_out
 void launch_grad_u(opf_ctx* c, double* gu);
+// sigma_c [m] and sigma_f [1] (device) of the gradient-based scaling from J
+// (m x n_u column-major) and the cost gradient gf [n_u]
+void launch_grad_scaling(opf_ctx* c, const double* J, const double* gf, double g_max, double s_min,
+                         double* sigma_c, double* sigma_f);
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
 void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);
@@ -147,6 +154,7 @@ bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid,
 void set_last_error(const std::string& msg);  // message returned by opf_last_error
 opf_status ensure_factors(opf_ctx* c);  // factorise the converged state's Jacobian if still pending
 opf_status check_al(const opf_ctx* c, const opf_al_params* p);  // AL inputs present, rho >= 0, sigma_f finite
+opf_status zero_params(opf_ctx* c, opf_al_params* q);  // sigma_f = rho = 0, zero [m] arrays
 // balanced: the single-network launch (tiles in whole waves over the SMs)
 HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool balanced);
 int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  // tiles of a column range
@@ -465,6 +473,10 @@ struct opf_ctx {
   unsigned long long* stamps = nullptr;  // phase stamps of a profiling Hessian call
   size_t stamps_cap = 0;          // tiles the stamps array holds
   bool stamps_on = false;         // the HVP launches of this call record phase stamps
+  double* jac_out = nullptr;      // the HVP launches of this call also write J columns here
+  bool jac_only = false;          // ... and stop after them (opf_reduced_jacobian without H)
+  double* zeros_m = nullptr;      // [m] zeros: AL inputs of the multiplier-free evaluations (first use)
+  double* gscale = nullptr;       // [n_u + 1]: cost gradient and sigma_f of opf_gradient_scaling (first use)
   size_t scratch_bytes = 0;
   cudaEvent_t ev[4];
   long long launches = 0;         // kernels launched by this context

@@ -1449,6 +1449,40 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     // (2) U sweep
     sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
     hvp_stamp(a, tile, 2);
+    // (2b) on request, the reduced constraint Jacobian of the tile's columns,
+    // J W = d_x c Z + d_u c W (Sec. III-B), from the first adjoint Z just
+    // computed: the |S|^2 rows of both branch ends and the PQ voltages here
+    // (branch or bus index fastest, so the table reads and the column writes
+    // are coalesced), the generator P/Q rows in phase (3), which forms their
+    // directional derivatives anyway.
+    if (a.J) {
+      const int nl = n.nl, m = n.m;
+      for (int it = threadIdx.x; it < nl * C; it += blockDim.x) {
+        const int l = it % nl, c = it / nl, j = s_col[c];
+        if (j < 0) continue;
+        const int4 bf = n.busrec[n.f[l]], bt = n.busrec[n.t[l]];
+        // branch-local direction (v_f, v_t, theta_f, theta_t)
+        const double d[4] = {dslot<C>(Z, bf.x, c, j), dslot<C>(Z, bt.x, c, j),
+                             bf.y >= 0 ? Z[(size_t)bf.y * C + c] : 0.0, bt.y >= 0 ? Z[(size_t)bt.y * C + c] : 0.0};
+        double* Jc = a.J + (size_t)j * m;
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+          double pdot = 0.0, qdot = 0.0;
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            pdot = fma(a.tab[(size_t)TAB_DP(s, k) * nl + l], d[k], pdot);
+            qdot = fma(a.tab[(size_t)TAB_DQ(s, k) * nl + l], d[k], qdot);
+          }
+          Jc[(size_t)s * nl + l] = 2.0 * (a.flows[(size_t)(2 * s) * nl + l] * pdot +
+                                          a.flows[(size_t)(2 * s + 1) * nl + l] * qdot);
+        }
+      }
+      for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
+        const int i = it % nb, c = it / nb, j = s_col[c];
+        if (j < 0 || n.type[i] != PQ) continue;
+        a.J[(size_t)j * m + 2 * nl + n.pqpos[i]] = Z[(size_t)n.busrec[i].x * C + c];
+      }
+    }
     // (3) directional derivatives of Q (slack and PV) and P (slack) for the
     // Gauss-Newton terms, stored pre-multiplied by their weights kQ, kP.  The
     // own-variable parts are the per-bus sums dQ_k/dv_k, dQ_k/dtheta_k, ...
@@ -1469,8 +1503,23 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       if (qb < q1) qd_ends<C, 1>(n, Z, E, qb, c, j, slack, qd, pdr);
       QD[(size_t)gi * C + c] = bw[k] * qd;
       if (slack) PD[c] = bw[nb + k] * pdr;
+      if (a.J && j >= 0) {  // generator rows of J: p_ref, q_ref, q of a PV unit
+        double* Jc = a.J + (size_t)j * n.m + 2 * n.nl + n.npq;
+        if (slack) {
+          Jc[0] = pdr;
+          Jc[1] = qd;
+        } else {
+          Jc[2 + n.pvpos[k]] = qd;
+        }
+      }
     }
     __syncthreads();
+    if (a.jac_only) {
+      hvp_stamp(a, tile, 3);
+      hvp_stamp(a, tile, 4);
+      hvp_stamp(a, tile, 5);
+      return;
+    }
     // (4) y = (grad^2 l) (z; w) per bus; R = -y_x, H[u rows] = y_u.  The
     // own-variable coefficients are summed per bus (busS), so an incident
     // branch adds only its other end's terms.  Buses are taken by descending
@@ -1935,6 +1984,58 @@ void launch_hess_prep(opf_ctx* c, double sigma_f) {
   bus_self_grad_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->btab, c->busw, c->adjE, c->busS);
 }
 
+// ------------------------------------------------------------ gradient scaling
+// The scale of a row whose largest derivative is mx: g_max / mx when mx
+// exceeds g_max (floored at s_min), else 1 (Sec. IV-A, "Scaling").
+__device__ __forceinline__ double grad_scale(double mx, double g_max, double s_min) {
+  return mx > g_max ? fmax(s_min, g_max / mx) : 1.0;
+}
+
+// sig[i] from max_j |J[j m + i]| (J column-major m x nu).  Block (32, 8): the
+// x threads take 32 consecutive rows (one coalesced 256-byte load per column),
+// the y threads every 8th column; the eight partial maxima meet in shared memory.
+__global__ void __launch_bounds__(256) jac_row_scale_kernel(const double* __restrict__ J, int m, int nu,
+                                                          double g_max, double s_min, double* sig) {
+  __shared__ double part[8][32];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  double mx = 0.0;
+  if (i < m)
+    for (int j = threadIdx.y; j < nu; j += 8) mx = fmax(mx, fabs(J[(size_t)j * m + i]));
+  part[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < m) {
+#pragma unroll
+    for (int y = 1; y < 8; y++) mx = fmax(mx, part[y][threadIdx.x]);
+    sig[i] = grad_scale(mx, g_max, s_min);
+  }
+}
+
+// out[0] = the scale of max_i |g[i]| (one block).
+__global__ void __launch_bounds__(256) vec_scale_kernel(const double* __restrict__ g, int n, double g_max,
+                                                      double s_min, double* out) {
+  __shared__ double part[8];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(g[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, part[w]);
+    out[0] = grad_scale(fmax(mx, part[0]), g_max, s_min);
+  }
+}
+
+void launch_grad_scaling(opf_ctx* c, const double* J, const double* gf, double g_max, double s_min,
+                         double* sigma_c, double* sigma_f) {
+  const int m = c->h.m, nu = c->h.nu;
+  if (m > 0) {
+    jac_row_scale_kernel<<<(m + 31) / 32, dim3(32, 8), 0, c->stream>>>(J, m, nu, g_max, s_min, sigma_c);
+    c->launches++;
+  }
+  vec_scale_kernel<<<1, 256, 0, c->stream>>>(gf, nu, g_max, s_min, sigma_f);
+  c->launches++;
+}
+
 size_t hvp_stride(const opf_ctx* c, int C) {
   size_t s = 2 * (size_t)c->dn.nx * C + (size_t)c->dn.ngn * C + C;
   return (s + 31) & ~(size_t)31;
@@ -2011,6 +2112,9 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   while ((1 << lk) < C) lk++;
   a.colmap = full ? c->colmap[balanced ? 1 : 0][lk] : nullptr;
   a.H = H;
+  a.flows = c->flows;
+  a.J = c->jac_out;
+  a.jac_only = c->jac_only ? 1 : 0;
   a.scratch = nullptr;
   a.stamps = c->stamps_on ? c->stamps : nullptr;
   a.stride = hvp_stride(c, C);
