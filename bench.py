@@ -598,6 +598,8 @@ def run_gpu(args):
     state.update(u=d(u_h), s=d(s_h), mu=st_h["mu"])
     state["x"], _ = ctx.powerflow(state["u"], x0=x0)
     tune = ctx.autotune(dict(al, s=state["s"]))
+    # level-merge schedule of the single-RHS solves (look-ahead distance, largest merged chunk)
+    sw_d, sw_w, sw_ms, sw_table = ctx.sweep_autotune(table=True)
     ke = max(1, min(args.steps, args.e2e_steps))  # end-to-end steps, on the snapshots after the timed ones
     nsnap = args.warmup + args.steps + 1 + ke + 4  # the last four: the tracking-QP leg
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
@@ -725,6 +727,10 @@ def run_gpu(args):
                                                "(gradient, Schur Hessian, Cholesky, trial power flow)",
                                        "load_scale": synth.WORKLOADS[WORKLOAD]["load_scale"],
                                        "block_k": tune["block_k"], "threads": tune["threads"],
+                                       "sweep_merge": {"lookahead": sw_d, "narrow": sw_w,
+                                                       "ms_solve_pair": sw_ms,
+                                                       "ms_by_schedule": {f"{a},{b}": v for (a, b), v
+                                                                          in sw_table.items()}},
                                        "autotuned": True,
                                        "autotune_candidates": [list(c) for c in AUTOTUNE_CANDIDATES],
                                        "block_width_note": "a CTA owns its tile's columns through all four "

@@ -271,6 +271,40 @@ opf_status opf_hessian_autotune(opf_ctx* ctx, const opf_al_params* p, double* H,
                                 float* best_ms);
 
 /*
+ * opf_set_sweep_merge: the level-merge schedule of the single-right-hand-side
+ * solves (the Newton updates of the power flow, Sec. III-A, and the adjoint
+ * solves of Prop. 1 and Prop. 3).  Their level loop is a chain of dependent
+ * steps; a narrow level (a few blocks of 100-250 entries on the large grids)
+ * costs a long dependent sum.  With lookahead = D > 0 each block of a level
+ * chunk with at most `narrow` blocks keeps only the entries whose column the
+ * chunk just before it writes; each other entry is summed in one of the D
+ * chunks before it that already has its column (spread evenly over them),
+ * beside those chunks' own work, and subtracted from the block's right-hand
+ * side there.  D = 0: no merging.  The streams are rebuilt in place on the
+ * host (tens of ms on the 9,200-bus grid; the context's stream is
+ * synchronised first); results change only through the order of the sums.
+ * A context whose solves use the level-record form (solution too large for
+ * shared memory) ignores the call.  The schedule at load is (4, 4), the
+ * fastest of the autotuner's candidates on the 9,200-bus grid.
+ * Errors: OPF_EINVAL (D < 0, narrow < 1 with D > 0, a merged chunk too large
+ * for the buffers), OPF_ECUDA.
+ */
+opf_status opf_set_sweep_merge(opf_ctx* ctx, int lookahead, int narrow);
+
+/*
+ * opf_sweep_autotune: for each level-merge schedule (lookahead, narrow) in
+ * {(0, 0), (1, 4), (2, 4), (4, 4), (6, 4), (8, 4), (4, 2), (4, 8)}, time one
+ * forward and one transposed single-right-hand-side solve at the current
+ * factors (CUDA events on the context stream, best of three after a warm-up),
+ * keep the fastest schedule (opf_set_sweep_merge) and return it (host
+ * pointers, each may be NULL) with its time per forward + transposed pair;
+ * ms_all (host [8], may be NULL) receives every candidate's time in the order
+ * above.  Requires a converged power flow.  Errors: OPF_ESTATE,
+ * OPF_ESINGULAR, OPF_ECUDA.
+ */
+opf_status opf_sweep_autotune(opf_ctx* ctx, int* lookahead, int* narrow, float* ms_pair, float* ms_all);
+
+/*
  * opf_reduced_hessian_batched: the dense reduced Hessians of n contexts
  * (snapshots: the same or different networks, each at its own converged power
  * flow) in one persistent launch.  Per context the first-order quantities and

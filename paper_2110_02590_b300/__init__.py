@@ -154,6 +154,9 @@ def lib():
         L.opf_hessian_autotune.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(HessOpts),
                                            C.POINTER(C.c_float)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
+        L.opf_set_sweep_merge.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.opf_sweep_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                         C.POINTER(C.c_float)]
         L.opf_reduced_jacobian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
                                            C.c_void_p, C.POINTER(HessInfo)]
         L.opf_gradient_scaling.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -553,6 +556,29 @@ class OPFContext:
         return Jt.T, (H.T if H is not None else None), dict(block_k=info.block_k, grid=info.grid,
                                                              tiles=info.tiles, launches=info.launches,
                                                              ms_total=info.ms_total, ms_hvp=info.ms_hvp)
+
+    def set_sweep_merge(self, lookahead, narrow=4):
+        """Level-merge schedule of the single-right-hand-side solves (opf_set_sweep_merge)."""
+        self._sync_stream()
+        st = lib().opf_set_sweep_merge(self.h, int(lookahead), int(narrow))
+        if st != 0:
+            raise OPFError(st, "opf_set_sweep_merge")
+
+    SWEEP_MERGE_CANDIDATES = ((0, 0), (1, 4), (2, 4), (4, 4), (6, 4), (8, 4), (4, 2), (4, 8))
+
+    def sweep_autotune(self, table=False):
+        """Time the level-merge schedules of the single-RHS solve and keep the fastest
+        (opf_sweep_autotune).  Returns (lookahead, narrow, ms per forward + transposed solve), and
+        with table=True also {(lookahead, narrow): ms} over SWEEP_MERGE_CANDIDATES."""
+        self._sync_stream()
+        d, w, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
+        allms = (C.c_float * 8)()
+        st = lib().opf_sweep_autotune(self.h, C.byref(d), C.byref(w), C.byref(ms), allms)
+        if st != 0:
+            raise OPFError(st, "opf_sweep_autotune")
+        if table:
+            return d.value, w.value, ms.value, dict(zip(self.SWEEP_MERGE_CANDIDATES, list(allms)))
+        return d.value, w.value, ms.value
 
     def gradient_scaling(self, g_max=100.0, s_min=1e-8, out_jacobian=None):
         """Gradient-based scales of the AL problem (opf_gradient_scaling): returns (sigma_c [m] on the

@@ -612,7 +612,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->dFx, nx));
   TRY(dalloc(c, &c->dFu, h.nu));
   TRY(dalloc(c, &c->lam, nx));
-  TRY(dalloc(c, &c->btab, 26 * (size_t)nl));
+  TRY(dalloc(c, &c->btab, TAB_ROWS * (size_t)nl));
   TRY(dalloc(c, &c->busw, 8 * (size_t)nb));
   TRY(dalloc(c, &c->adjE, ADJ_W * 2 * (size_t)nl));
   TRY(dalloc(c, &c->busS, 4 * (size_t)nb));
@@ -1128,6 +1128,59 @@ opf_status opf_hessian_autotune(opf_ctx* c, const opf_al_params* p, double* H, o
     *best = opf_hess_opts{kb, 0, 0, 0, 0, tb, 0};
   }
   if (best_ms) *best_ms = tbest;
+  return OPF_OK;
+}
+
+opf_status opf_set_sweep_merge(opf_ctx* c, int lookahead, int narrow) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is required");
+  return set_sweep_merge(c, lookahead, narrow);
+}
+
+opf_status opf_sweep_autotune(opf_ctx* c, int* lookahead, int* narrow, float* ms_pair, float* ms_all) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is required");
+  if (!c->have_state) FAIL(OPF_ESTATE, "no converged power flow on this context");
+  TRY(ensure_factors(c));
+  if (!c->sw.ok) {  // level-record form: no schedule to choose
+    if (lookahead) *lookahead = 0;
+    if (narrow) *narrow = 0;
+    if (ms_pair) *ms_pair = 0.f;
+    if (ms_all)
+      for (int k = 0; k < 8; k++) ms_all[k] = 0.f;
+    return OPF_OK;
+  }
+  static const int cand[][2] = {{0, 0}, {1, 4}, {2, 4}, {4, 4}, {6, 4}, {8, 4}, {4, 2}, {4, 8}};
+  cudaStream_t st = c->stream;
+  float tbest = 0.f;
+  int db = 0, wb = 0, ic = 0;
+  for (const auto& cd : cand) {
+    TRY(set_sweep_merge(c, cd[0], cd[1]));
+    // one forward and one transposed solve per pair (the residual vector as input)
+    launch_solve1(c, c->g, c->dvec, false, 1.0);
+    launch_solve1(c, c->g, c->dvec, true, 1.0);
+    float best = 0.f;
+    for (int r = 0; r < 3; r++) {
+      CK(cudaEventRecord(c->ev[0], st));
+      launch_solve1(c, c->g, c->dvec, false, 1.0);
+      launch_solve1(c, c->g, c->dvec, true, 1.0);
+      CK(cudaEventRecord(c->ev[1], st));
+      CK(cudaEventSynchronize(c->ev[1]));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      if (r == 0 || ms < best) best = ms;
+    }
+    if (ms_all) ms_all[ic] = best;
+    ic++;
+    if (tbest == 0.f || best < tbest) {
+      tbest = best;
+      db = cd[0];
+      wb = cd[1];
+    }
+  }
+  TRY(set_sweep_merge(c, db, wb));
+  CK(cudaGetLastError());
+  if (lookahead) *lookahead = db;
+  if (narrow) *narrow = wb;
+  if (ms_pair) *ms_pair = tbest;
   return OPF_OK;
 }
 

@@ -13,9 +13,13 @@ namespace opf {
 
 // Per-branch Hessian table rows (each row holds n_l doubles): 0..9 the packed
 // symmetric 4x4 second derivative in branch-local order (v_f, v_t, theta_f,
-// theta_t); 10+4s+k = dP of end s w.r.t. local variable k; 18+4s+k = dQ.
+// theta_t); 10+4s+k = dP of end s w.r.t. local variable k; 18+4s+k = dQ;
+// 26+4s+k = d|S_s|^2 = 2 (P_s dP_s + Q_s dQ_s), the gradient of the end's
+// flow constraint (the rows of the reduced Jacobian).
 #define TAB_DP(s, k) (10 + 4 * (s) + (k))
 #define TAB_DQ(s, k) (18 + 4 * (s) + (k))
+#define TAB_DS(s, k) (26 + 4 * (s) + (k))
+#define TAB_ROWS 34
 
 // Per-adjacency coefficient record (bus i at end s of branch l, o the other
 // end), ADJ_W doubles.  The branch functions depend on the angles only through
@@ -103,7 +107,6 @@ struct HvpArgs {
   const int* ubus;  // bus of each control
   const int* colmap;  // null: tile position p is column col0 + p; else column colmap[p] (-1: none)
   double* H;
-  const double* flows;  // [4 nl] end flows Pf, Qf, Pt, Qt at the state (the |S|^2 rows of J)
   double* J;            // null, or the reduced constraint Jacobian [n_u][m] (column j at J + j m)
   int jac_only;         // 1: the tiles stop after J (H untouched, may be null)
   double* scratch;
@@ -363,8 +366,18 @@ struct SweepStreams {
   SweepStream s[4];      // L of LU (forward), U of LU (backward), U^T from T (forward), L^T from T (backward)
   int2* map = nullptr;   // {destination double, source}: source 2p (LU) / 2p + 1 (T), or -1 - row (1 / U_rr)
   int nmap = 0;
+  int* d_nmap = nullptr;     // nmap on the device (read by the captured gather)
   double* values = nullptr;  // the streams' bytes, as doubles for the gather
+  size_t cap_bytes = 0, cap_map = 0;  // capacity of values (bytes) and map (entries)
+  size_t fixed = 0, tri_bytes = 0, max_slot = 0;  // solution bytes, triangle segment, largest ring slot
+  int lookahead = 0, narrow = 0;  // level-merge schedule of the streams (set_sweep_merge)
+  std::vector<int> h_bptr_f, h_bptr_b;  // the bus-block level schedules the streams are built from
+  std::vector<int4> h_bmeta_f, h_bmeta_b;
 };
+// Default level-merge schedule of the streamed sweeps: look-ahead distance in
+// chunks and the largest chunk (records) that is merged.
+constexpr int kSweepLookahead = 4;
+constexpr int kSweepNarrow = 4;
 // FP64 rank-K update of a lower triangle emulated on bf16 tensor cores
 // (opf_ozaki.cu): A[r0 :, r0 :] -= P P^T with P = A[r0 : n, c0 : c0 + K],
 // K <= 128 a multiple of 32; E: n - r0 ints, D: 8 (n - r0) K bf16 workspace.
@@ -399,6 +412,7 @@ void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int*
 opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
                                const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b);
 void launch_sweep_pack(opf_ctx* c);  // after a refactorisation (captured in the LU graph)
+opf_status set_sweep_merge(opf_ctx* c, int lookahead, int narrow);  // rebuild the streams in place
 void launch_solve1_streamed(opf_ctx* c, const double* b, double* out, bool transposed, double scale);
 
 }  // namespace opf
@@ -461,7 +475,7 @@ struct opf_ctx {
   double *Pbus = nullptr, *Qbus = nullptr;
   double *cvec = nullptr, *phid = nullptr, *omega = nullptr;
   double *dFx = nullptr, *dFu = nullptr, *lam = nullptr;
-  double *btab = nullptr;         // [26 nl] per-branch Hessian table
+  double *btab = nullptr;         // [TAB_ROWS nl] per-branch Hessian table
   double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
   double* adjE = nullptr;         // [2 nl][ADJ_W] per-adjacency coefficients of the HVP gathers
   double* busS = nullptr;         // [nb] x 4: per-bus sums of E_VV (+ omega of v_pq), E_VT, E_TT, 0

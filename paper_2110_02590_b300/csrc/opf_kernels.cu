@@ -1057,6 +1057,7 @@ __global__ void hess_prep_kernel(DevNet n, const double* vb, const double* tb, c
     for (int k = 0; k < 4; k++) {
       tab[(size_t)TAB_DP(s, map[k]) * nl + l] = F.dP[k];
       tab[(size_t)TAB_DQ(s, map[k]) * nl + l] = F.dQ[k];
+      tab[(size_t)TAB_DS(s, map[k]) * nl + l] = gh[k];
     }
   }
 #pragma unroll
@@ -1451,14 +1452,15 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     hvp_stamp(a, tile, 2);
     // (2b) on request, the reduced constraint Jacobian of the tile's columns,
     // J W = d_x c Z + d_u c W (Sec. III-B), from the first adjoint Z just
-    // computed: the |S|^2 rows of both branch ends and the PQ voltages here
-    // (branch or bus index fastest, so the table reads and the column writes
-    // are coalesced), the generator P/Q rows in phase (3), which forms their
-    // directional derivatives anyway.
+    // computed: the |S|^2 rows of both branch ends and the PQ voltages here,
+    // the generator P/Q rows in phase (3), which forms their directional
+    // derivatives anyway.  Column fastest: the C lanes of a slab row read one
+    // contiguous segment, and a warp's 32 / C consecutive branches give each
+    // column one contiguous run of J.
     if (a.J) {
       const int nl = n.nl, m = n.m;
       for (int it = threadIdx.x; it < nl * C; it += blockDim.x) {
-        const int l = it % nl, c = it / nl, j = s_col[c];
+        const int l = it / C, c = it % C, j = s_col[c];
         if (j < 0) continue;
         const int4 bf = n.busrec[n.f[l]], bt = n.busrec[n.t[l]];
         // branch-local direction (v_f, v_t, theta_f, theta_t)
@@ -1466,19 +1468,15 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
                              bf.y >= 0 ? Z[(size_t)bf.y * C + c] : 0.0, bt.y >= 0 ? Z[(size_t)bt.y * C + c] : 0.0};
         double* Jc = a.J + (size_t)j * m;
 #pragma unroll
-        for (int s = 0; s < 2; s++) {
-          double pdot = 0.0, qdot = 0.0;
+        for (int s = 0; s < 2; s++) {  // d|S_s|^2 . d, the end's gradient from the branch table
+          double v = 0.0;
 #pragma unroll
-          for (int k = 0; k < 4; k++) {
-            pdot = fma(a.tab[(size_t)TAB_DP(s, k) * nl + l], d[k], pdot);
-            qdot = fma(a.tab[(size_t)TAB_DQ(s, k) * nl + l], d[k], qdot);
-          }
-          Jc[(size_t)s * nl + l] = 2.0 * (a.flows[(size_t)(2 * s) * nl + l] * pdot +
-                                          a.flows[(size_t)(2 * s + 1) * nl + l] * qdot);
+          for (int k = 0; k < 4; k++) v = fma(a.tab[(size_t)TAB_DS(s, k) * nl + l], d[k], v);
+          Jc[(size_t)s * nl + l] = v;
         }
       }
       for (int it = threadIdx.x; it < nb * C; it += blockDim.x) {
-        const int i = it % nb, c = it / nb, j = s_col[c];
+        const int i = it / C, c = it % C, j = s_col[c];
         if (j < 0 || n.type[i] != PQ) continue;
         a.J[(size_t)j * m + 2 * nl + n.pqpos[i]] = Z[(size_t)n.busrec[i].x * C + c];
       }
@@ -2112,7 +2110,6 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   while ((1 << lk) < C) lk++;
   a.colmap = full ? c->colmap[balanced ? 1 : 0][lk] : nullptr;
   a.H = H;
-  a.flows = c->flows;
   a.J = c->jac_out;
   a.jac_only = c->jac_only ? 1 : 0;
   a.scratch = nullptr;

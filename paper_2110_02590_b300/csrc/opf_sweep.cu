@@ -35,10 +35,13 @@ inline size_t chunk_bytes(int nrec, int ent, int ntask) {
 // One block of a level in factor positions.
 struct Rec {
   int lead, other;  // rows (other = -1: a single row)
-  int q0, q1;       // the lead row's entries [q0, q1)
+  int q0, q1;       // the lead row's entries [q0, q1) (when pos is empty)
   int off;          // the second row's entry of position p is p + off
-  int coup;         // position of the coupling entry (other >= 0)
+  int coup;         // position of the coupling entry (other >= 0; -1 with other >= 0: none, a partial sum)
   bool scale;       // multiply by 1 / U_rr of the rows (the sweep's diagonal)
+  std::vector<int> pos;  // explicit entry positions of the lead row (replaces [q0, q1))
+  int count() const { return pos.empty() ? q1 - q0 : (int)pos.size(); }
+  int at(int t) const { return pos.empty() ? q0 + t : pos[t]; }
 };
 
 struct Built {
@@ -78,7 +81,7 @@ std::vector<int> plan_lanes(const std::vector<Rec>& L, size_t i, int nrec) {
       lat.push_back(60L * (mx / 4 + mx % 4 + 1) + 110L * lgmax + 300);
     };
     for (int r = 0; r < nrec; r++) {
-      const int len = L[i + r].q1 - L[i + r].q0;
+      const int len = L[i + r].count();
       int lg = 0;
       while (lg < 5 && (1 << lg) * k < len) lg++;
       const int g = 1 << lg;
@@ -135,68 +138,156 @@ void build_tri(const Symbolic& s, int r0, int sr, bool fwd, bool use_t, Built& o
   for (int i = 0; i < sr; i++) out.map.push_back(make_int2((int)(nt2 + i), -1 - (r0 + i)));
 }
 
-// Appends the levels, each cut into chunks of at most slot bytes; false if a
-// block alone does not fit.
-bool build_stream(const std::vector<std::vector<Rec>>& levels, const Symbolic& s, bool use_t, size_t slot,
-                  Built& out) {
+// Level merging by look-ahead (lookahead = D > 0): a record of a narrow chunk
+// t (at most `narrow` records) keeps only its late entries, those whose
+// column is written by chunk t - 1; each other entry, whose column is written
+// by a chunk q (or is final before the stream), is summed in one of the
+// chunks max(q + 1, t - D) .. t - 1, spread so that each of those chunks takes
+// about as many of the record's entries (one partial record per chunk and
+// record: the same rows, no coupling, no scaling, its sum subtracted from the
+// rows' right-hand side).  The rows of chunk t are read by no chunk before t
+// and written by none but t and its partial records (each in its own chunk),
+// so every partial sum lands before chunk t needs it, and the chain of a
+// narrow level shrinks to its late entries while its earlier sums run beside
+// the work of the chunks before it.  A partial record needs at least kMinMove
+// entries and room in its chunk; otherwise its entries stay with the record.
+constexpr int kMinMove = 4;
+
+void lookahead_merge(std::vector<std::vector<Rec>>& ch, const Symbolic& s, int nx, int D, int narrow,
+                     size_t slot) {
+  if (D <= 0) return;
+  const int nch = (int)ch.size();
+  std::vector<int> prod(nx, -1);  // chunk writing each row (-1: final before the stream)
+  std::vector<int> nrec(nch), ent(nch);
+  for (int c = 0; c < nch; c++) {
+    nrec[c] = (int)ch[c].size();
+    ent[c] = 0;
+    for (const Rec& R : ch[c]) {
+      prod[R.lead] = c;
+      if (R.other >= 0) prod[R.other] = c;
+      ent[c] += R.count();
+    }
+  }
+  std::vector<std::vector<Rec>> add(nch);  // partial records, appended after the pass
+  for (int t = 1; t < nch; t++) {
+    if ((int)ch[t].size() > narrow) continue;
+    const int h0 = std::max(0, t - D);
+    for (Rec& R : ch[t]) {
+      std::vector<std::vector<int>> part(t - h0);
+      std::vector<int> late;
+      for (int k = 0; k < R.count(); k++) {
+        const int p = R.at(k), lo = std::max(h0, prod[s.ci[p]] + 1);
+        if (lo > t - 1) {
+          late.push_back(p);
+          continue;
+        }
+        int best = lo;  // the least loaded of the chunks that may take it
+        for (int h = lo + 1; h < t; h++)
+          if (part[h - h0].size() < part[best - h0].size()) best = h;
+        part[best - h0].push_back(p);
+      }
+      for (int h = h0; h < t; h++) {
+        std::vector<int>& v = part[h - h0];
+        if (v.empty()) continue;
+        if ((int)v.size() < kMinMove || nrec[h] + 1 > 32 * kMaxTasks ||
+            chunk_bytes(nrec[h] + 1, ent[h] + (int)v.size(), kMaxTasks) > slot) {
+          late.insert(late.end(), v.begin(), v.end());
+          continue;
+        }
+        Rec P = R;
+        P.coup = -1;
+        P.scale = false;
+        P.pos = v;
+        add[h].push_back(P);
+        nrec[h]++;
+        ent[h] += (int)v.size();
+      }
+      if ((int)late.size() == R.count()) continue;  // nothing moved
+      std::sort(late.begin(), late.end());
+      R.pos = late;
+      if (late.empty()) R.q1 = R.q0;  // no late entry: the record only finishes its rows
+    }
+  }
+  for (int h = 0; h < nch; h++) ch[h].insert(ch[h].end(), add[h].begin(), add[h].end());
+}
+
+// Appends the levels, each cut into chunks of at most slot bytes (merged by
+// look-ahead when D > 0); false if a block alone does not fit.
+bool build_stream(const std::vector<std::vector<Rec>>& levels, const Symbolic& s, int nx, bool use_t, size_t slot,
+                  int D, int narrow, Built& out) {
   auto code = [&](int p) { return 2 * p + (use_t ? 1 : 0); };
   const size_t first = out.off.size();
+  // 1. chunks: each level cut at block boundaries
+  std::vector<std::vector<Rec>> chunks;
   for (const auto& L : levels) {
     size_t i = 0;
     while (i < L.size()) {
       int nrec = 0, ent = 0;
       size_t j = i;
       while (j < L.size() && nrec < 32 * kMaxTasks) {
-        const int e = L[j].q1 - L[j].q0;
+        const int e = L[j].count();
         if (chunk_bytes(nrec + 1, ent + e, kMaxTasks) > slot) break;
         nrec++;
         ent += e;
         j++;
       }
       if (nrec == 0) return false;
-      const std::vector<int> lanes = plan_lanes(L, i, nrec);
-      const int ntask = (int)lanes.size() / 32;
-      if (ntask == 0) return false;
-      const size_t off = out.bytes.size(), len = chunk_bytes(nrec, ent, ntask);
-      out.bytes.resize(off + len, 0);
-      out.off.push_back((int)off);
-      out.len.push_back((int)len);
-      unsigned char* B = out.bytes.data() + off;
-      const int E4 = pad4(ent), nrv = rv_count(nrec);
-      const int hdr[8] = {nrec, ntask, E4, nrv, 0, 0, 0, 0};
-      std::memcpy(B, hdr, sizeof(hdr));
-      std::memcpy(B + kHdr, lanes.data(), 4 * lanes.size());
-      const size_t o_rec = kHdr + 128 * (size_t)ntask, o_rv = o_rec + 16 * (size_t)nrec;
-      const size_t o_ci = o_rv + 8 * (size_t)nrv;
-      const size_t o_va = o_ci + 4 * (size_t)E4, o_vb = o_va + 8 * (size_t)E4;
-      auto put_map = [&](size_t byte_off, int src) {
-        out.map.push_back(make_int2((int)((off + byte_off) / 8), src));
-      };
-      int eoff = 0;
-      for (int r = 0; r < nrec; r++) {
-        const Rec& R = L[i + r];
-        const int cnt = R.q1 - R.q0;
-        const int rec[4] = {R.lead, cnt, R.other, eoff};
-        std::memcpy(B + o_rec + 16 * (size_t)r, rec, sizeof(rec));
-        const double one = 1.0;
-        if (R.other >= 0) put_map(o_rv + 8 * (size_t)(3 * r), code(R.coup));
-        if (R.scale)
-          put_map(o_rv + 8 * (size_t)(3 * r + 1), -1 - R.lead);
-        else
-          std::memcpy(B + o_rv + 8 * (size_t)(3 * r + 1), &one, 8);
-        if (R.scale && R.other >= 0)
-          put_map(o_rv + 8 * (size_t)(3 * r + 2), -1 - R.other);
-        else
-          std::memcpy(B + o_rv + 8 * (size_t)(3 * r + 2), &one, 8);
-        for (int t = 0; t < cnt; t++) {
-          const int p = R.q0 + t, e = eoff + t;
-          std::memcpy(B + o_ci + 4 * (size_t)e, &s.ci[p], 4);
-          put_map(o_va + 8 * (size_t)e, code(p));
-          if (R.other >= 0) put_map(o_vb + 8 * (size_t)e, code(p + R.off));
-        }
-        eoff += cnt;
-      }
+      chunks.emplace_back(L.begin() + i, L.begin() + j);
       i = j;
+    }
+  }
+  // 2. level merging
+  lookahead_merge(chunks, s, nx, D, narrow, slot);
+  // 3. lanes and bytes of each chunk
+  for (const auto& L : chunks) {
+    const int nrec = (int)L.size();
+    int ent = 0;
+    for (const Rec& R : L) ent += R.count();
+    const std::vector<int> lanes = plan_lanes(L, 0, nrec);
+    const int ntask = (int)lanes.size() / 32;
+    if (ntask == 0) return false;
+    const size_t off = out.bytes.size(), len = chunk_bytes(nrec, ent, ntask);
+    if (len > slot) return false;
+    out.bytes.resize(off + len, 0);
+    out.off.push_back((int)off);
+    out.len.push_back((int)len);
+    unsigned char* B = out.bytes.data() + off;
+    const int E4 = pad4(ent), nrv = rv_count(nrec);
+    const int hdr[8] = {nrec, ntask, E4, nrv, 0, 0, 0, 0};
+    std::memcpy(B, hdr, sizeof(hdr));
+    std::memcpy(B + kHdr, lanes.data(), 4 * lanes.size());
+    const size_t o_rec = kHdr + 128 * (size_t)ntask, o_rv = o_rec + 16 * (size_t)nrec;
+    const size_t o_ci = o_rv + 8 * (size_t)nrv;
+    const size_t o_va = o_ci + 4 * (size_t)E4, o_vb = o_va + 8 * (size_t)E4;
+    auto put_map = [&](size_t byte_off, int src) {
+      out.map.push_back(make_int2((int)((off + byte_off) / 8), src));
+    };
+    int eoff = 0;
+    for (int r = 0; r < nrec; r++) {
+      const Rec& R = L[r];
+      const int cnt = R.count();
+      const int rec[4] = {R.lead, cnt, R.other, eoff};
+      std::memcpy(B + o_rec + 16 * (size_t)r, rec, sizeof(rec));
+      const double one = 1.0, zero = 0.0;
+      if (R.other >= 0 && R.coup >= 0)
+        put_map(o_rv + 8 * (size_t)(3 * r), code(R.coup));
+      else
+        std::memcpy(B + o_rv + 8 * (size_t)(3 * r), &zero, 8);
+      if (R.scale)
+        put_map(o_rv + 8 * (size_t)(3 * r + 1), -1 - R.lead);
+      else
+        std::memcpy(B + o_rv + 8 * (size_t)(3 * r + 1), &one, 8);
+      if (R.scale && R.other >= 0)
+        put_map(o_rv + 8 * (size_t)(3 * r + 2), -1 - R.other);
+      else
+        std::memcpy(B + o_rv + 8 * (size_t)(3 * r + 2), &one, 8);
+      for (int t = 0; t < cnt; t++) {
+        const int p = R.at(t), e = eoff + t;
+        std::memcpy(B + o_ci + 4 * (size_t)e, &s.ci[p], 4);
+        put_map(o_va + 8 * (size_t)e, code(p));
+        if (R.other >= 0) put_map(o_vb + 8 * (size_t)e, code(p + R.off));
+      }
+      eoff += cnt;
     }
   }
   // each chunk names the chunk two places after it (the one it prefetches)
@@ -215,29 +306,31 @@ template <bool TR>
 __global__ void solve1s_kernel(DevNet n, SweepStream sf, SweepStream sb, const double* b, double* out,
                                double scale, int slot);
 
-opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
-                               const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b) {
-  SweepStreams& sw = c->sw;
-  sw = SweepStreams();
+namespace {
+
+// The four streams of one merge schedule: bytes, chunk table and gather map.
+struct StreamSet {
+  Built B[4];
+  std::vector<unsigned char> all;
+  std::vector<int2> map;
+  std::vector<size_t> base;
+  size_t maxlen = 16;
+};
+
+// Records of the level schedules: L (LU, forward, unit diagonal), U (LU,
+// backward, scaled), U^T (T, forward, scaled), L^T (T, backward, unit
+// diagonal).  The forward schedules end with the off-block part of the
+// trailing rows (no scaling: the triangle applies it).
+bool build_all(const opf_ctx* c, int D, int W, size_t slot, StreamSet& S) {
+  const SweepStreams& sw = c->sw;
   const Symbolic& s = c->s;
   const int nx = c->dn.nx, r0 = c->dn.r0, sr = c->dn.nroot;
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  const size_t cap = (size_t)optin - 1024;
-  const size_t ntri = (size_t)sr * (sr > 0 ? sr - 1 : 0) / 2;
-  const size_t fixed = 8 * (((size_t)nx + 1) & ~(size_t)1);
-  const size_t tri_bytes = 8 * ((ntri + 1) & ~(size_t)1) + 8 * (((size_t)sr + 1) & ~(size_t)1);
-  if (fixed + kRing * (size_t)4096 > cap) return OPF_OK;  // the solution does not fit: level-record form
-  size_t slot = (cap - fixed) / kRing / 16 * 16;
-  if (tri_bytes > 2 * slot) return OPF_OK;  // the triangle segment must fit ring slots 1 and 2
-  // levels of blocks per direction; the forward sweep ends with the off-block
-  // part of the trailing rows (no scaling: the triangle applies it)
   std::vector<std::vector<Rec>> lev_f, lev_b;
-  for (size_t l = 0; l + 1 < bptr_f.size(); l++) {
+  for (size_t l = 0; l + 1 < sw.h_bptr_f.size(); l++) {
     std::vector<Rec> L;
-    for (int k = bptr_f[l]; k < bptr_f[l + 1]; k++) {
-      const int4 m = bmeta_f[k];
-      L.push_back({m.x, m.w ? m.x + 1 : -1, m.y, m.z, m.w, m.w ? m.z + m.w : -1, true});
+    for (int k = sw.h_bptr_f[l]; k < sw.h_bptr_f[l + 1]; k++) {
+      const int4 m = sw.h_bmeta_f[k];
+      L.push_back({m.x, m.w ? m.x + 1 : -1, m.y, m.z, m.w, m.w ? m.z + m.w : -1, true, {}});
     }
     lev_f.push_back(L);
   }
@@ -245,21 +338,19 @@ opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const
     std::vector<Rec> L;
     for (int i = r0; i < nx; i++) {
       const int q1 = s.dp[i] - (i - r0);
-      if (q1 > s.rp[i]) L.push_back({i, -1, s.rp[i], q1, 0, -1, false});
+      if (q1 > s.rp[i]) L.push_back({i, -1, s.rp[i], q1, 0, -1, false, {}});
     }
     std::stable_sort(L.begin(), L.end(), [](const Rec& a, const Rec& b) { return a.q1 - a.q0 > b.q1 - b.q0; });
     if (!L.empty()) lev_f.push_back(L);
   }
-  for (size_t l = 0; l + 1 < bptr_b.size(); l++) {
+  for (size_t l = 0; l + 1 < sw.h_bptr_b.size(); l++) {
     std::vector<Rec> L;
-    for (int k = bptr_b[l]; k < bptr_b[l + 1]; k++) {
-      const int4 m = bmeta_b[k];
-      L.push_back({m.x, m.w ? m.x - 1 : -1, m.y, m.z, m.w, m.w ? m.y + m.w - 1 : -1, true});
+    for (int k = sw.h_bptr_b[l]; k < sw.h_bptr_b[l + 1]; k++) {
+      const int4 m = sw.h_bmeta_b[k];
+      L.push_back({m.x, m.w ? m.x - 1 : -1, m.y, m.z, m.w, m.w ? m.y + m.w - 1 : -1, true, {}});
     }
     lev_b.push_back(L);
   }
-  // L (LU, forward, unit diagonal), U (LU, backward, scaled), U^T (T, forward,
-  // scaled), L^T (T, backward, unit diagonal)
   auto with_scale = [](const std::vector<std::vector<Rec>>& lv, bool on) {
     std::vector<std::vector<Rec>> out;
     for (const auto& L : lv) {
@@ -273,66 +364,113 @@ opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const
     }
     return out;
   };
-  Built B[4];
   const std::vector<std::vector<Rec>> src[4] = {with_scale(lev_f, false), with_scale(lev_b, true),
                                                 with_scale(lev_f, true), with_scale(lev_b, false)};
   for (int k = 0; k < 4; k++) {
-    build_tri(s, r0, sr, k % 2 == 0, k >= 2, B[k]);
-    B[k].tri_len = (int)B[k].bytes.size();
-    if (!build_stream(src[k], s, k >= 2, slot, B[k])) return OPF_OK;
+    build_tri(s, r0, sr, k % 2 == 0, k >= 2, S.B[k]);
+    S.B[k].tri_len = (int)S.B[k].bytes.size();
+    if (!build_stream(src[k], s, nx, k >= 2, slot, D, W, S.B[k])) return false;
   }
-  size_t total = 0, maxlen = 16;
-  std::vector<size_t> base(4);
+  size_t total = 0;
+  S.base.assign(4, 0);
   for (int k = 0; k < 4; k++) {
-    base[k] = total;
-    total += B[k].bytes.size();
-    for (int l : B[k].len) maxlen = std::max(maxlen, (size_t)l);
+    S.base[k] = total;
+    total += S.B[k].bytes.size();
+    for (int l : S.B[k].len) S.maxlen = std::max(S.maxlen, (size_t)l);
   }
-  std::vector<unsigned char> all(std::max<size_t>(total, 16), 0);
-  std::vector<int2> map;
+  S.all.assign(std::max<size_t>(total, 16), 0);
   for (int k = 0; k < 4; k++) {
-    if (!B[k].bytes.empty()) std::memcpy(all.data() + base[k], B[k].bytes.data(), B[k].bytes.size());
-    for (const int2& e : B[k].map) map.push_back(make_int2(e.x + (int)(base[k] / 8), e.y));
+    if (!S.B[k].bytes.empty()) std::memcpy(S.all.data() + S.base[k], S.B[k].bytes.data(), S.B[k].bytes.size());
+    for (const int2& e : S.B[k].map) S.map.push_back(make_int2(e.x + (int)(S.base[k] / 8), e.y));
   }
-  void* dv = nullptr;
-  if (cudaMalloc(&dv, all.size()) != cudaSuccess) {
-    cudaGetLastError();
-    set_last_error("cannot allocate the single-RHS sweep streams");
-    return OPF_ENOMEM;
+  return true;
+}
+
+// Copies a built set into the context's stream buffers (in place: the LU
+// graph's gather keeps its pointers and reads the entry count from the device).
+opf_status upload_streams(opf_ctx* c, const StreamSet& S) {
+  SweepStreams& sw = c->sw;
+  if (S.all.size() > sw.cap_bytes || S.map.size() > sw.cap_map) {
+    set_last_error("the merged sweep streams exceed the buffers allocated at load");
+    return OPF_EINVAL;
   }
-  c->allocs.push_back(dv);
-  void* dm = nullptr;
-  if (cudaMalloc(&dm, std::max<size_t>(map.size(), 1) * sizeof(int2)) != cudaSuccess) {
-    cudaGetLastError();
-    set_last_error("cannot allocate the single-RHS sweep gather map");
-    return OPF_ENOMEM;
-  }
-  c->allocs.push_back(dm);
-  if (cudaMemcpy(dv, all.data(), all.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      (!map.empty() && cudaMemcpy(dm, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)) {
+  const int nmap = (int)S.map.size();
+  if (cudaMemcpy(sw.values, S.all.data(), S.all.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (nmap > 0 && cudaMemcpy(sw.map, S.map.data(), S.map.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
+                       cudaSuccess) ||
+      cudaMemcpy(sw.d_nmap, &nmap, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     set_last_error("cannot upload the single-RHS sweep streams");
     return OPF_ECUDA;
   }
-  sw.values = static_cast<double*>(dv);
-  sw.map = static_cast<int2*>(dm);
-  sw.nmap = (int)map.size();
+  sw.nmap = nmap;
   for (int k = 0; k < 4; k++) {
     SweepStream& st = sw.s[k];
-    st.base = static_cast<const unsigned char*>(dv) + base[k];
-    st.tri_len = B[k].tri_len;
-    st.nch = (int)B[k].off.size();
+    st = SweepStream();
+    st.base = reinterpret_cast<const unsigned char*>(sw.values) + S.base[k];
+    st.tri_len = S.B[k].tri_len;
+    st.nch = (int)S.B[k].off.size();
     if (st.nch > 0) {
-      st.off0 = B[k].off[0];
-      st.len0 = B[k].len[0];
+      st.off0 = S.B[k].off[0];
+      st.len0 = S.B[k].len[0];
     }
     if (st.nch > 1) {
-      st.off1 = B[k].off[1];
-      st.len1 = B[k].len[1];
+      st.off1 = S.B[k].off[1];
+      st.len1 = S.B[k].len[1];
     }
   }
-  sw.slot = (int)std::max((maxlen + 15) / 16 * 16, (tri_bytes + 31) / 32 * 16);
-  sw.smem = (int)(fixed + kRing * (size_t)sw.slot);
+  sw.slot = (int)std::max((S.maxlen + 15) / 16 * 16, (sw.tri_bytes + 31) / 32 * 16);
+  sw.smem = (int)(sw.fixed + kRing * (size_t)sw.slot);
+  return OPF_OK;
+}
+
+}  // namespace
+
+opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
+                               const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b) {
+  SweepStreams& sw = c->sw;
+  sw = SweepStreams();
+  const int nx = c->dn.nx, sr = c->dn.nroot;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  const size_t cap = (size_t)optin - 1024;
+  const size_t ntri = (size_t)sr * (sr > 0 ? sr - 1 : 0) / 2;
+  sw.fixed = 8 * (((size_t)nx + 1) & ~(size_t)1);
+  sw.tri_bytes = 8 * ((ntri + 1) & ~(size_t)1) + 8 * (((size_t)sr + 1) & ~(size_t)1);
+  if (sw.fixed + kRing * (size_t)4096 > cap) return OPF_OK;  // the solution does not fit: level-record form
+  sw.max_slot = (cap - sw.fixed) / kRing / 16 * 16;
+  if (sw.tri_bytes > 2 * sw.max_slot) return OPF_OK;  // the triangle segment must fit ring slots 1 and 2
+  sw.h_bptr_f = bptr_f;
+  sw.h_bmeta_f = bmeta_f;
+  sw.h_bptr_b = bptr_b;
+  sw.h_bmeta_b = bmeta_b;
+  int D = kSweepLookahead, W = kSweepNarrow;
+  StreamSet S;
+  if (!build_all(c, D, W, sw.max_slot, S)) {
+    S = StreamSet();
+    D = W = 0;
+    if (!build_all(c, 0, 0, sw.max_slot, S)) return OPF_OK;
+  }
+  // buffers with room for the other merge schedules (a merge adds records and
+  // padding, never entries)
+  sw.cap_bytes = S.all.size() + S.all.size() / 4 + 65536;
+  sw.cap_map = S.map.size() + S.map.size() / 4 + 4096;
+  void *dv = nullptr, *dm = nullptr, *dn = nullptr;
+  if (cudaMalloc(&dv, sw.cap_bytes) != cudaSuccess || cudaMalloc(&dm, sw.cap_map * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&dn, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (dv) cudaFree(dv);
+    if (dm) cudaFree(dm);
+    set_last_error("cannot allocate the single-RHS sweep streams");
+    return OPF_ENOMEM;
+  }
+  c->allocs.push_back(dv);
+  c->allocs.push_back(dm);
+  c->allocs.push_back(dn);
+  sw.values = static_cast<double*>(dv);
+  sw.map = static_cast<int2*>(dm);
+  sw.d_nmap = static_cast<int*>(dn);
+  if (opf_status rc = upload_streams(c, S)) return rc;
   if (cudaFuncSetAttribute(solve1s_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) !=
           cudaSuccess ||
       cudaFuncSetAttribute(solve1s_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) !=
@@ -341,7 +479,35 @@ opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const
     set_last_error("cannot raise the shared-memory limit of the streamed single-RHS sweep");
     return OPF_ECUDA;
   }
+  sw.lookahead = D;
+  sw.narrow = W;
   sw.ok = true;
+  return OPF_OK;
+}
+
+opf_status set_sweep_merge(opf_ctx* c, int D, int W) {
+  SweepStreams& sw = c->sw;
+  if (D < 0 || W < 0 || (D > 0 && W < 1)) {
+    set_last_error("lookahead must be >= 0 and narrow >= 1 with a lookahead");
+    return OPF_EINVAL;
+  }
+  if (!sw.ok) return OPF_OK;  // level-record form: nothing to merge
+  StreamSet S;
+  if (!build_all(c, D, W, sw.max_slot, S)) {
+    set_last_error("a merged chunk does not fit a ring slot");
+    return OPF_EINVAL;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // no solve still reads the old streams
+    cudaGetLastError();
+    set_last_error("stream synchronisation failed");
+    return OPF_ECUDA;
+  }
+  if (opf_status rc = upload_streams(c, S)) return rc;
+  sw.lookahead = D;
+  sw.narrow = W;
+  // the values of the new layout: gathered now from factors that are current,
+  // else by the next refactorisation
+  if (c->have_state && !c->factors_stale) launch_sweep_pack(c);
   return OPF_OK;
 }
 
@@ -578,8 +744,9 @@ __global__ void __launch_bounds__(kSweepThreads) solve1s_kernel(DevNet n, SweepS
 }
 
 __global__ void sweep_pack_kernel(const double* __restrict__ LU, const double* __restrict__ T,
-                                  const double* __restrict__ invdiag, const int2* __restrict__ map, int nmap,
-                                  double* __restrict__ dst) {
+                                  const double* __restrict__ invdiag, const int2* __restrict__ map,
+                                  const int* __restrict__ nmap_dev, double* __restrict__ dst) {
+  const int nmap = *nmap_dev;  // read at run time: a new merge schedule keeps the captured launch valid
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nmap; k += gridDim.x * blockDim.x) {
     const int2 e = map[k];
     dst[e.x] = e.y >= 0 ? ((e.y & 1) ? T[e.y >> 1] : LU[e.y >> 1]) : invdiag[-1 - e.y];
@@ -587,10 +754,11 @@ __global__ void sweep_pack_kernel(const double* __restrict__ LU, const double* _
 }
 
 void launch_sweep_pack(opf_ctx* c) {
-  if (!c->sw.ok || c->sw.nmap == 0) return;
+  if (!c->sw.ok) return;
   c->launches++;
-  const int blocks = std::min((c->sw.nmap + 255) / 256, 2 * c->sm_count);
-  sweep_pack_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->sw.map, c->sw.nmap, c->sw.values);
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((c->sw.cap_map + 255) / 256, 2 * (size_t)c->sm_count));
+  sweep_pack_kernel<<<blocks, 256, 0, c->stream>>>(c->LU, c->T, c->invdiag, c->sw.map, c->sw.d_nmap,
+                                                   c->sw.values);
 }
 
 void launch_solve1_streamed(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
