@@ -394,24 +394,21 @@ def autograd_batch(P, torch, dev, nscen):
                     "w.r.t. u, loads and s; plain: power flow + adjoint gradient per scenario"}
 
 
-def static_opf(P, torch, dev, name, max_outer, max_inner=30, margin=1.2):
-    """Static OPF by the augmented-Lagrangian loop (opf_al_solve) on a synthetic grid at its
-    nominal loads: line limits max(rate, margin |S|) from the AC base case (the generator's own
-    limits follow its DC flows, which the AC flows exceed on up to a third of the branches), y = 0,
-    rho = 10, an interior start at mu = 0.1."""
+def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100.0):
+    """Static OPF by the augmented-Lagrangian loop (opf_al_solve) on a synthetic grid at its nominal
+    loads, on an instance whose AC base case is feasible (synth.static_instance: line limits
+    max(rate, 1.2 |S|) with an inactive lower bound, reactive and PQ-voltage bounds widened around
+    the base case), y = 0, rho = 10, an interior start at mu = 0.1, and with scaling_gmax > 0 the
+    gradient-based scaling of Sec. IV-A at the start."""
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)  # noqa: E731
     net = synth.workload(name)
     ctx = P.OPFContext(net, device=dev.index)
     u_lo, u_hi = synth.control_bounds(net)
-    al = synth.al_inputs(net, seed=5)
-    nl = net.n_branch
+    al0 = synth.al_inputs(net, seed=5)
     u0 = synth.flat_control(net)
     x0, _ = ctx.powerflow(d(u0))
-    c0 = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})["c"]
-    c0 = c0.cpu().numpy()
-    r2 = np.maximum(net.br_rate ** 2, margin ** 2 * np.maximum(c0[:nl], c0[nl:2 * nl]))
-    al["s_hi"][:2 * nl] = np.concatenate([r2, r2])
-    al["sigma_c"][:2 * nl] = np.concatenate([1.0 / r2, 1.0 / r2])
+    c0 = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al0.items()})["c"]
+    al = synth.static_instance(net, al0, c0.cpu().numpy())
     u = np.clip(u0, u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
     x, _ = ctx.powerflow(d(u), x0=x0)
     c = ctx.reduced_gradient({k: (d(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()})["c"]
@@ -422,16 +419,20 @@ def static_opf(P, torch, dev, name, max_outer, max_inner=30, margin=1.2):
                  zl_u=d(mu / (u - u_lo)), zu_u=d(mu / (u_hi - u)), zl_s=d(mu / (s - lo)), zu_s=d(mu / (hi - s)))
     y = d(np.zeros(ctx.m))
     info, hist = ctx.al_solve(dict(sigma_f=al["sigma_f"], rho=10.0, sigma_c=d(al["sigma_c"])), state, y,
-                              max_outer=max_outer, max_inner=max_inner)
+                              max_outer=max_outer, max_inner=max_inner, scaling_gmax=scaling_gmax)
     steps = max(1, info["steps"])
     return {"net": name, "n_u": ctx.nu, "outer": info["outer"], "steps": info["steps"],
             "converged": bool(info["converged"]), "ms_total": info["ms_total"],
             "ms_per_outer": info["ms_total"] / max(1, info["outer"]), "ms_per_step": info["ms_total"] / steps,
             "primal_inf": info["primal_inf"], "dual_inf": info["dual_inf"], "rho_final": info["rho"],
+            "F_final": info["F"], "sigma_f": info["sigma_f"], "scaling_gmax": scaling_gmax,
             "steps_per_outer": [int(h[0]) for h in hist],
-            "setup": f"nominal loads, line limits max(rate, {margin} |S| of the AC base case), y0 = 0, rho0 = 10, "
-                     "mu0 = 0.1, "
-                     f"at most {max_inner} reduced-Newton steps per subproblem (one full Hessian each)"}
+            "setup": "nominal loads; bounds widened around the AC base case (line limits max(rate, 1.2 |S|), "
+                     "inactive flow lower bound, reactive limits to 1.2 |q|, PQ voltages to 2% around the base "
+                     f"case); y0 = 0, rho0 = 10, mu0 = 0.1; at most {max_inner} reduced-Newton steps per "
+                     "subproblem (one full Hessian each); "
+                     + (f"gradient-based scaling with g_max = {scaling_gmax:g}" if scaling_gmax > 0
+                        else "the instance's own scales (1/limit^2 on the flows, 1 elsewhere, sigma_f = 1e-4)")}
 
 
 def mean_complementarity(st):
@@ -711,8 +712,9 @@ def run_gpu(args):
                    "split": "contiguous column ranges in whole tiles, one NCCL all-gather of H"}
     rto = None if args.no_extras else tracking_qp(P, torch, ctx, al, state, pds, qds,
                                                   args.warmup + args.steps + 1 + ke, 4)
-    al_static = None if args.no_extras else [static_opf(P, torch, dev, "medium1400", 20),
-                                             static_opf(P, torch, dev, WORKLOAD, 3)]
+    al_static = None if args.no_extras else [static_opf(P, torch, dev, "medium1400"),
+                                             static_opf(P, torch, dev, "medium1400", scaling_gmax=0.0),
+                                             static_opf(P, torch, dev, WORKLOAD)]
 
     if rank != 0:
         if world > 1:

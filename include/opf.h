@@ -243,11 +243,14 @@ opf_status opf_reduced_jacobian(opf_ctx* ctx, const opf_al_params* p, const opf_
  * gradients (Sec. IV-A, "Scaling", where the paper cites the gradient-based
  * rule of interior-point codes without stating it), at the state of the last
  * converged power flow:
- *   sigma_c[i] = 1 if ||dc_i/du||_inf <= g_max, else max(s_min, g_max / ||dc_i/du||_inf)
- *   sigma_f    = the same with the reduced gradient of the generation cost
+ *   scale(n)   = 1 if n <= g_max, else max(s_min, g_max / n)
+ *   sigma_c[i] = p_i scale(p_i ||dc_i/du||_inf)  (p = prior, or 1: the rule on
+ *                the constraint as the caller writes it, p_i c_i)
+ *   sigma_f    = scale(||df/du||_inf), f the generation cost
  * Both derivatives are reduced ones (on g = 0): J from opf_reduced_jacobian,
  * the cost gradient from Prop. 1.  The usual values are g_max = 100 and
  * s_min = 1e-8.
+ *   prior (device [m], may be NULL): the caller's own constraint scales.
  *   J (device, m x n_u column-major, 8 m n_u bytes): receives the Jacobian
  *     (the caller's workspace).
  *   sigma_c (device [m]): the constraint scales.  sigma_f (host, may be NULL).
@@ -255,8 +258,8 @@ opf_status opf_reduced_jacobian(opf_ctx* ctx, const opf_al_params* p, const opf_
  * multipliers).  Errors: OPF_EINVAL (g_max <= 0 or not finite, s_min outside
  * (0, 1]), OPF_ESTATE, OPF_ESINGULAR.
  */
-opf_status opf_gradient_scaling(opf_ctx* ctx, double g_max, double s_min, double* J, double* sigma_c,
-                                double* sigma_f);
+opf_status opf_gradient_scaling(opf_ctx* ctx, double g_max, double s_min, const double* prior, double* J,
+                                double* sigma_c, double* sigma_f);
 
 /*
  * opf_hessian_autotune: time opf_reduced_hessian on the context's current state
@@ -440,8 +443,15 @@ opf_status opf_al_step(opf_ctx* ctx, const opf_al_params* p, opf_al_state* st,
  * dual state and bounds as for opf_al_step (u, s, duals, x and mu updated in
  * place).  Requires a converged opf_powerflow at st->u.  history (host, may be
  * NULL): 8 doubles per outer iteration {steps, mu, rho, eta_p, E_0, F, delta,
- * 0}.  Errors: those of opf_al_step (the state is then the last accepted
- * iterate), OPF_EINVAL, OPF_ESTATE, OPF_ENOMEM.
+ * 0}.  With opts->scaling_gmax > 0 the loop first scales the problem by its
+ * gradients at the starting point (Sec. IV-A "Scaling", opf_gradient_scaling
+ * with p->sigma_c as the prior and g_max = scaling_gmax): the constraint
+ * scales become p->sigma_c times the rule's factors and sigma_f the rule's
+ * scale of the cost (p->sigma_f is then unused); y, eta_p and E_0 refer to
+ * the scaled problem.  The Jacobian this needs (8 m n_u bytes) is allocated
+ * for the scaling and freed before the iterations.  Errors: those of
+ * opf_al_step (the state is then the last accepted iterate), OPF_EINVAL,
+ * OPF_ESTATE, OPF_ENOMEM.
  */
 typedef struct {
   int max_outer;      /* outer iterations (0 = 20) */
@@ -450,12 +460,15 @@ typedef struct {
   double eta_dual;    /* stopping tolerance on E_0 (0 = 1e-4) */
   double rho_max;     /* penalty cap (0 = 1e6) */
   int block_k;        /* Hessian tile width of the steps (0 = autotuned, else 8) */
+  double scaling_gmax;   /* > 0: gradient-based scaling at the start (above); 0: p's scales */
+  double* sigma_c_used;  /* device [m], may be NULL: receives the constraint scales the loop used */
 } opf_al_opts;
 
 typedef struct {
   int outer, steps, converged;
   double primal_inf, dual_inf, F, rho, mu;
-  float ms_total;  /* device time of the whole loop */
+  float ms_total;  /* device time of the whole loop (the scaling included) */
+  double sigma_f;  /* the objective scale the loop used */
 } opf_al_info;
 
 opf_status opf_al_solve(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_state* st,

@@ -24,11 +24,15 @@ textbook; the readings (the same ones the library's opf_al_solve takes):
     psi_mu and diverge;
   * after the subproblem: primal infeasibility eta_p = |D_c (c - s)|_inf; stop
     when eta_p <= eta_primal and E_0 <= eta_dual; else y <- y + rho D_c (c - s),
-    and rho <- min(10 rho, rho_max) when eta_p fell by less than a factor 4.
+    and rho <- min(10 rho, rho_max) when eta_p fell by less than a factor 4;
+  * optional gradient-based scaling before the first iteration (Sec. IV-A
+    "Scaling", `scaling.gradient_scaling` at the starting point with the
+    caller's sigma_c as the prior; sigma_f from the cost gradient alone).
 """
 import numpy as np
 
 from oracle import al_step as A
+from oracle import scaling as S
 
 
 def kkt_errors(g, u, s, st, mu):
@@ -47,9 +51,13 @@ def kkt_errors(g, u, s, st, mu):
 
 
 def al_solve(on, x, u, s, y, st, al, rho, max_outer=20, max_inner=30, eta_primal=1e-5, eta_dual=1e-4,
-             rho_max=1e6):
-    """Run the outer loop from (x, u, s, y, duals in st, st['mu'], rho).  Returns the final point and
-    one history row per outer iteration: (inner steps, mu, rho, eta_p, E_0, F)."""
+             rho_max=1e6, scaling_gmax=0.0):
+    """Run the outer loop from (x, u, s, y, duals in st, st['mu'], rho).  Returns the final point, the
+    scales used and one history row per outer iteration: (inner steps, mu, rho, eta_p, E_0, F)."""
+    if scaling_gmax > 0.0:
+        J = S.explicit_jacobian(on, x, u)
+        sig, sf = S.gradient_scaling(J, S.cost_gradient(on, x, u), g_max=scaling_gmax, prior=al["sigma_c"])
+        al = dict(al, sigma_c=sig, sigma_f=sf)
     st = dict(st)
     u, s, y, x = u.copy(), s.copy(), y.copy(), x.copy()
     mu = st["mu"]
@@ -88,4 +96,5 @@ def al_solve(on, x, u, s, y, st, al, rho, max_outer=20, max_inner=30, eta_primal
         prev_eta = eta_p
     st["mu"] = mu
     return dict(x=x, u=u, s=s, y=y, rho=rho, mu=mu, duals={k: st[k] for k in ("zl_u", "zu_u", "zl_s", "zu_s")},
-                history=hist, converged=converged, steps=steps_total, delta=delta)
+                history=hist, converged=converged, steps=steps_total, delta=delta,
+                sigma_c=np.asarray(al["sigma_c"], dtype=np.float64).copy(), sigma_f=float(al["sigma_f"]))

@@ -87,13 +87,14 @@ class StepInfo(C.Structure):
 
 class AlOpts(C.Structure):
     _fields_ = [("max_outer", C.c_int), ("max_inner", C.c_int), ("eta_primal", C.c_double),
-                ("eta_dual", C.c_double), ("rho_max", C.c_double), ("block_k", C.c_int)]
+                ("eta_dual", C.c_double), ("rho_max", C.c_double), ("block_k", C.c_int),
+                ("scaling_gmax", C.c_double), ("sigma_c_used", C.c_void_p)]
 
 
 class AlInfo(C.Structure):
     _fields_ = [("outer", C.c_int), ("steps", C.c_int), ("converged", C.c_int), ("primal_inf", C.c_double),
                 ("dual_inf", C.c_double), ("F", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("sigma_f", C.c_double)]
 
 
 class QpOpts(C.Structure):
@@ -160,7 +161,7 @@ def lib():
         L.opf_reduced_jacobian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
                                            C.c_void_p, C.POINTER(HessInfo)]
         L.opf_gradient_scaling.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
-                                           C.POINTER(C.c_double)]
+                                           C.c_void_p, C.POINTER(C.c_double)]
         L.opf_set_wait_limit.argtypes = [C.c_void_p, C.c_int]
         L.opf_tracking_update.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                           C.POINTER(QpOpts), C.POINTER(QpInfo)]
@@ -580,11 +581,13 @@ class OPFContext:
             return d.value, w.value, ms.value, dict(zip(self.SWEEP_MERGE_CANDIDATES, list(allms)))
         return d.value, w.value, ms.value
 
-    def gradient_scaling(self, g_max=100.0, s_min=1e-8, out_jacobian=None):
-        """Gradient-based scales of the AL problem (opf_gradient_scaling): returns (sigma_c [m] on the
-        device, sigma_f, J as an (m, n_u) view)."""
+    def gradient_scaling(self, g_max=100.0, s_min=1e-8, prior=None, out_jacobian=None):
+        """Gradient-based scales of the AL problem (opf_gradient_scaling), with the caller's own
+        constraint scales `prior` (optional, [m]): returns (sigma_c [m] on the device, sigma_f, J as an
+        (m, n_u) view)."""
         t = self.torch
         self._sync_stream()
+        prior = None if prior is None else self._dev(prior)
         if out_jacobian is None:
             Jt = t.empty((self.nu, self.m), dtype=t.float64, device=self.device)
         else:
@@ -593,7 +596,8 @@ class OPFContext:
                 raise ValueError(f"out_jacobian must have shape ({self.nu}, {self.m})")
         sig = t.empty(self.m, dtype=t.float64, device=self.device)
         sf = C.c_double(0.0)
-        st = lib().opf_gradient_scaling(self.h, float(g_max), float(s_min), _ptr(Jt), _ptr(sig), C.byref(sf))
+        st = lib().opf_gradient_scaling(self.h, float(g_max), float(s_min), _ptr(prior), _ptr(Jt), _ptr(sig),
+                                        C.byref(sf))
         if st != 0:
             raise OPFError(st, "opf_gradient_scaling")
         return sig, sf.value, Jt.T
@@ -620,11 +624,13 @@ class OPFContext:
                                                         "s_lo", "s_hi", "x")], float(state["mu"]))
 
     def al_solve(self, al, state, y, max_outer=20, max_inner=30, eta_primal=1e-5, eta_dual=1e-4, rho_max=1e6,
-                 block_k=0):
+                 block_k=0, scaling_gmax=0.0):
         """Static OPF by the augmented-Lagrangian outer loop (opf_al_solve).  `al`: sigma_f, the initial
         rho and sigma_c; `y` (cuda float64 [m]) and the state tensors are updated in place, and
-        state["mu"] is set to the final barrier parameter.  Returns (info dict, history array
-        [outer, 8]: steps, mu, rho, eta_p, E_0, F, delta, 0)."""
+        state["mu"] is set to the final barrier parameter.  scaling_gmax > 0 scales the problem by its
+        gradients first (sigma_c as the prior).  Returns (info dict with "sigma_c" the constraint
+        scales used, history array [outer, 8]: steps, mu, rho, eta_p, E_0, F, delta, 0)."""
+        t = self.torch
         self._sync_stream()
         y = self._dev(y)
         keep = [self._dev(al["sigma_c"])]
@@ -632,14 +638,17 @@ class OPFContext:
         st = self._state(state)
         hist = np.zeros((max(1, int(max_outer)), 8))
         info = AlInfo()
+        sig_used = t.empty(self.m, dtype=t.float64, device=self.device)
         rc = lib().opf_al_solve(self.h, C.byref(p), C.c_void_p(y.data_ptr()), C.byref(st),
                                 C.byref(AlOpts(int(max_outer), int(max_inner), float(eta_primal), float(eta_dual),
-                                               float(rho_max), int(block_k))),
+                                               float(rho_max), int(block_k), float(scaling_gmax),
+                                               sig_used.data_ptr())),
                                 C.byref(info), hist.ctypes.data_as(_dp))
         state["mu"] = st.mu
         if rc != 0:
             raise OPFError(rc, "opf_al_solve")
         out = {k: getattr(info, k) for k, _ in AlInfo._fields_}
+        out["sigma_c"] = sig_used
         return out, hist[:info.outer].copy()
 
     def tracking_update(self, al, state, y, max_it=50, tol=1e-6, block_k=0, max_halvings=0, max_inertia=0,

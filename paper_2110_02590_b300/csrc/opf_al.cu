@@ -144,10 +144,15 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
   const double eta_d = (o && o->eta_dual > 0.0) ? o->eta_dual : 1e-4;
   const double rho_max = (o && o->rho_max > 0.0) ? o->rho_max : 1e6;
   const int block_k = o ? o->block_k : 0;
+  const double gmax = o ? o->scaling_gmax : 0.0;
+  if (!(gmax >= 0.0) || !std::isfinite(gmax)) {
+    set_last_error("scaling_gmax must be >= 0 and finite");
+    return OPF_EINVAL;
+  }
   const int nu = c->h.nu, m = c->h.m;
   AlWork w;
   void* block = nullptr;
-  const size_t nd = (size_t)nu + 2 * (size_t)m + 8;
+  const size_t nd = (size_t)nu + 3 * (size_t)m + 8;
   if (cudaMalloc(&block, nd * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&w.h_red, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -161,12 +166,35 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
   w.c = q + nu + m;
   w.red = q + nu + 2 * (size_t)m;
   w.F = w.red + 4;
+  double* sig_scaled = w.F + 4;  // [m]
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, c->stream);
 
   opf_status rc = OPF_OK;
+  // the problem's scales: the caller's, or scaled by its gradients at the start
+  const double* sigma_c = p->sigma_c;
+  double sigma_f = p->sigma_f;
+  if (gmax > 0.0) {
+    void* J = nullptr;
+    if (cudaMalloc(&J, sizeof(double) * (size_t)m * (size_t)nu) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("cannot allocate the Jacobian of the gradient scaling");
+      rc = OPF_ENOMEM;
+    } else {
+      rc = opf_gradient_scaling(c, gmax, 1e-8, p->sigma_c, static_cast<double*>(J), sig_scaled, &sigma_f);
+      cudaFree(J);
+      sigma_c = sig_scaled;
+    }
+  }
+  if (rc == OPF_OK && o && o->sigma_c_used)
+    if (cudaMemcpyAsync(o->sigma_c_used, sigma_c, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("cannot copy the constraint scales");
+      rc = OPF_ECUDA;
+    }
   double rho = p->rho, mu = st->mu, prev_eta = INFINITY, delta = 0.0;
   double E[4] = {0, 0, 0, 0};
   int outer = 0, steps_total = 0, converged = 0;
@@ -174,6 +202,8 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
   for (int k = 0; k < max_outer && rc == OPF_OK; k++) {
     const double omega_k = std::max(eta_d, std::pow(10.0, -(double)(k + 1)));
     opf_al_params pk = *p;
+    pk.sigma_c = sigma_c;
+    pk.sigma_f = sigma_f;
     pk.y = y;
     pk.rho = rho;
     pk.s = st->s;
@@ -209,7 +239,7 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
       converged = 1;
       break;
     }
-    launch_al_dual_update(c, y, rho, p->sigma_c, w.c, st->s);
+    launch_al_dual_update(c, y, rho, sigma_c, w.c, st->s);
     if (E[2] > 0.25 * prev_eta) rho = std::min(10.0 * rho, rho_max);
     prev_eta = E[2];
   }
@@ -229,6 +259,7 @@ extern "C" opf_status opf_al_solve(opf_ctx* c, const opf_al_params* p, double* y
     info->F = E[3];
     info->rho = rho;
     info->mu = mu;
+    info->sigma_f = sigma_f;
     info->ms_total = 0.f;
     cudaEventElapsedTime(&info->ms_total, e0, e1);
   }

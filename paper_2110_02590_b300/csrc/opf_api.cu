@@ -1078,8 +1078,8 @@ opf_status opf_reduced_jacobian(opf_ctx* c, const opf_al_params* p, const opf_he
   return hessian_impl(c, p, o, H, J, H == nullptr, info);
 }
 
-opf_status opf_gradient_scaling(opf_ctx* c, double g_max, double s_min, double* J, double* sigma_c,
-                                double* sigma_f) {
+opf_status opf_gradient_scaling(opf_ctx* c, double g_max, double s_min, const double* prior, double* J,
+                                double* sigma_c, double* sigma_f) {
   if (!c || !J || !sigma_c) FAIL(OPF_EINVAL, "ctx, J and sigma_c are required");
   if (!(g_max > 0.0) || !std::isfinite(g_max) || !(s_min > 0.0 && s_min <= 1.0))
     FAIL(OPF_EINVAL, "g_max must be positive and finite, s_min in (0, 1]");
@@ -1096,7 +1096,7 @@ opf_status opf_gradient_scaling(opf_ctx* c, double g_max, double s_min, double* 
   opf_hess_opts o{};
   o.reuse_first_order = 1;
   TRY(hessian_impl(c, &p, &o, nullptr, J, true, nullptr));
-  launch_grad_scaling(c, J, c->gscale, g_max, s_min, sigma_c, c->gscale + c->h.nu);
+  launch_grad_scaling(c, J, c->gscale, g_max, s_min, prior, sigma_c, c->gscale + c->h.nu);
   double sf = 1.0;
   CK(cudaMemcpyAsync(&sf, c->gscale + c->h.nu, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -142,9 +142,9 @@ void launch_first_order(opf_ctx* c, const opf_al_params* p, double* grad_s);
 void launch_eval_F(opf_ctx* c, const opf_al_params* p, double* F_out);  // F only, into device F_out
 void launch_grad_u(opf_ctx* c, double* gu);
 // sigma_c [m] and sigma_f [1] (device) of the gradient-based scaling from J
-// (m x n_u column-major) and the cost gradient gf [n_u]
+// (m x n_u column-major), the cost gradient gf [n_u] and an optional prior [m]
 void launch_grad_scaling(opf_ctx* c, const double* J, const double* gf, double g_max, double s_min,
-                         double* sigma_c, double* sigma_f);
+                         const double* prior, double* sigma_c, double* sigma_f);
 void launch_grad_load(opf_ctx* c, double sigma_f, double* gpd, double* gqd);
 void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);

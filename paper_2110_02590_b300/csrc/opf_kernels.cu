@@ -1992,8 +1992,11 @@ __device__ __forceinline__ double grad_scale(double mx, double g_max, double s_m
 // sig[i] from max_j |J[j m + i]| (J column-major m x nu).  Block (32, 8): the
 // x threads take 32 consecutive rows (one coalesced 256-byte load per column),
 // the y threads every 8th column; the eight partial maxima meet in shared memory.
+// With a prior scale p_i (prior non-null) the rule applies to the row as
+// written, p_i dc_i/du, and the result is p_i times its scale.
 __global__ void __launch_bounds__(256) jac_row_scale_kernel(const double* __restrict__ J, int m, int nu,
-                                                          double g_max, double s_min, double* sig) {
+                                                          double g_max, double s_min,
+                                                          const double* __restrict__ prior, double* sig) {
   __shared__ double part[8][32];
   const int i = blockIdx.x * 32 + threadIdx.x;
   double mx = 0.0;
@@ -2004,7 +2007,8 @@ __global__ void __launch_bounds__(256) jac_row_scale_kernel(const double* __rest
   if (threadIdx.y == 0 && i < m) {
 #pragma unroll
     for (int y = 1; y < 8; y++) mx = fmax(mx, part[y][threadIdx.x]);
-    sig[i] = grad_scale(mx, g_max, s_min);
+    const double p = prior ? prior[i] : 1.0;
+    sig[i] = p * grad_scale(p * mx, g_max, s_min);
   }
 }
 
@@ -2024,10 +2028,10 @@ __global__ void __launch_bounds__(256) vec_scale_kernel(const double* __restrict
 }
 
 void launch_grad_scaling(opf_ctx* c, const double* J, const double* gf, double g_max, double s_min,
-                         double* sigma_c, double* sigma_f) {
+                         const double* prior, double* sigma_c, double* sigma_f) {
   const int m = c->h.m, nu = c->h.nu;
   if (m > 0) {
-    jac_row_scale_kernel<<<(m + 31) / 32, dim3(32, 8), 0, c->stream>>>(J, m, nu, g_max, s_min, sigma_c);
+    jac_row_scale_kernel<<<(m + 31) / 32, dim3(32, 8), 0, c->stream>>>(J, m, nu, g_max, s_min, prior, sigma_c);
     c->launches++;
   }
   vec_scale_kernel<<<1, 256, 0, c->stream>>>(gf, nu, g_max, s_min, sigma_f);

@@ -399,6 +399,39 @@ def al_inputs(net: Network, seed: int, rho: float = 10.0, sigma_f: float = 1e-4,
     return dict(sigma_f=float(sigma_f), sigma_c=sigma_c, y=y, s=s, rho=float(rho), s_lo=lo, s_hi=hi)
 
 
+def static_instance(net: Network, al: dict, c_base: np.ndarray, margin: float = 1.2,
+                    v_margin: float = 0.02) -> dict:
+    """Bounds of a static OPF instance whose AC base case is feasible (a copy of `al` with new s_lo,
+    s_hi and sigma_c).  c_base: the constraint values at the base case (the flat control's power
+    flow at nominal loads, computed by the caller).
+
+    - line flows: limit r^2 = max(rate, margin |S|)^2, |S| the larger end's base-case flow; the
+      squared flows have only this upper limit, so their lower bound is the inactive -r^2 (a bound
+      of 0 is degenerate on a zero-flow branch); sigma_c = 1 / r^2;
+    - reactive generation (q_ref, q_pv): limits widened to cover margin |q| of the base case;
+    - PQ voltages: bounds widened to cover (1 -/+ v_margin) times the base-case voltage.
+    """
+    nl = net.n_branch
+    npv = len([b for b in net.gen_bus if int(b) != net.ref_bus])
+    m = constraint_count(net)
+    npq = m - 2 * nl - 2 - npv
+    c_base = np.asarray(c_base, dtype=np.float64)
+    out = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+    lo, hi, sig = out["s_lo"], out["s_hi"], out["sigma_c"]
+    r2 = np.maximum(net.br_rate ** 2, margin ** 2 * np.maximum(c_base[:nl], c_base[nl:2 * nl]))
+    hi[:2 * nl] = np.concatenate([r2, r2])
+    lo[:2 * nl] = -hi[:2 * nl]
+    sig[:2 * nl] = 1.0 / hi[:2 * nl]
+    v = slice(2 * nl, 2 * nl + npq)
+    lo[v] = np.minimum(lo[v], (1.0 - v_margin) * c_base[v])
+    hi[v] = np.maximum(hi[v], (1.0 + v_margin) * c_base[v])
+    q = slice(2 * nl + npq + 1, m)
+    qb = margin * np.abs(c_base[q])
+    lo[q] = np.minimum(lo[q], -qb)
+    hi[q] = np.maximum(hi[q], qb)
+    return out
+
+
 def control_bounds(net: Network):
     """Bounds of u = (v_ref, v_pv, p_pv)."""
     pv = sorted(int(b) for b in net.gen_bus if int(b) != net.ref_bus)

@@ -31,28 +31,33 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def run_both(name, max_outer, max_inner=30):
+def run_both(name, max_outer, max_inner=30, scaling_gmax=0.0):
     net, on, x, u, s, al, st = static_setup(name)
-    ref = L.al_solve(on, x, u, s, al["y"], st, al, rho=10.0, max_outer=max_outer, max_inner=max_inner)
+    ref = L.al_solve(on, x, u, s, al["y"], st, al, rho=10.0, max_outer=max_outer, max_inner=max_inner,
+                     scaling_gmax=scaling_gmax)
     ctx = P.OPFContext(net)
     xg, _ = ctx.powerflow(dev(u))
     state = {k: dev(v) for k, v in st.items() if k != "mu"}
     state.update(u=dev(u), s=dev(s), x=xg, mu=st["mu"])
     y = dev(al["y"])
     info, hist = ctx.al_solve(dict(sigma_f=al["sigma_f"], rho=10.0, sigma_c=dev(al["sigma_c"])), state, y,
-                              max_outer=max_outer, max_inner=max_inner)
+                              max_outer=max_outer, max_inner=max_inner, scaling_gmax=scaling_gmax)
     return ref, info, hist, state, y
 
 
-@pytest.mark.parametrize("name,max_outer", [("tiny30", 1), ("tiny30", 3), ("medium1400", 2)])
-def test_al_loop_parity(name, max_outer):
+@pytest.mark.parametrize("name,max_outer,gmax", [("tiny30", 1, 0.0), ("tiny30", 3, 0.0), ("medium1400", 2, 0.0),
+                                                 ("tiny30", 3, 100.0), ("medium1400", 2, 100.0)])
+def test_al_loop_parity(name, max_outer, gmax):
     """Iterate by iterate over the first outer iterations (a few dozen line-searched steps): the
     decisions (steps per subproblem, mu, rho, stop) coincide exactly.  E_0 is the infinity norm of
     grad L - z_lo + z_hi, a difference of bound-dual terms of up to ~1e4 near the bounds, so
     rounding-level differences of the iterates show in it at ~1e-4; eta_p, F and the iterates agree
     far more closely.  (Over longer runs an Armijo test or a subproblem stop that falls within
     rounding of its threshold can go the other way; the converged run is compared at its end.)"""
-    ref, info, hist, state, y = run_both(name, max_outer)
+    ref, info, hist, state, y = run_both(name, max_outer, scaling_gmax=gmax)
+    # the scales (the caller's, or the gradient rule's at the start) agree first
+    assert rel(info["sigma_c"].cpu().numpy(), ref["sigma_c"]) < 1e-12
+    assert abs(info["sigma_f"] - ref["sigma_f"]) <= 1e-12 * ref["sigma_f"]
     rh = np.array(ref["history"])
     assert info["outer"] == len(rh)
     assert info["converged"] == int(ref["converged"])
@@ -72,13 +77,36 @@ def test_al_loop_parity(name, max_outer):
     assert np.abs(state["x"].cpu().numpy() - ref["x"]).max() < 1e-5
 
 
-def test_al_loop_reaches_the_oracle_optimum():
+@pytest.mark.parametrize("gmax", [0.0, 100.0])
+def test_al_loop_reaches_the_oracle_optimum(gmax):
     """To convergence (rho climbs to 1e6, where the subproblems are ill conditioned and
     rounding-level differences change how many outer iterations each side takes): both
     sides stop at the tolerances, at the same point and cost."""
-    ref, info, hist, state, y = run_both("tiny30", 40)
+    ref, info, hist, state, y = run_both("tiny30", 40, scaling_gmax=gmax)
     assert ref["converged"] and info["converged"]
     assert info["primal_inf"] <= 1e-5 and info["dual_inf"] <= 1e-4
     assert abs(len(ref["history"]) - info["outer"]) <= 3
     assert rel(state["u"].cpu().numpy(), ref["u"]) < 1e-4
     assert abs(info["F"] - ref["history"][-1][5]) <= 1e-5 * abs(ref["history"][-1][5])
+
+
+@pytest.mark.parametrize("name", ["medium1400", "large9200"])
+def test_scaled_static_opf_converges(name):
+    """The static OPF of the 1,400- and 9,200-bus instances with the gradient-based scaling runs to
+    the tolerances (eta_p <= 1e-5, E_0 <= 1e-4) at a feasible, interior point of the manifold."""
+    net, on, x, u, s, al, st = static_setup(name)
+    ctx = P.OPFContext(net)
+    xg, _ = ctx.powerflow(dev(u))
+    state = {k: dev(v) for k, v in st.items() if k != "mu"}
+    state.update(u=dev(u), s=dev(s), x=xg, mu=st["mu"])
+    y = dev(al["y"])
+    info, hist = ctx.al_solve(dict(sigma_f=al["sigma_f"], rho=10.0, sigma_c=dev(al["sigma_c"])), state, y,
+                              max_outer=20, max_inner=60, scaling_gmax=100.0)
+    assert info["converged"], (info, hist)
+    assert info["primal_inf"] <= 1e-5 and info["dual_inf"] <= 1e-4
+    uu, ss = state["u"].cpu().numpy(), state["s"].cpu().numpy()
+    assert np.all(uu > st["u_lo"]) and np.all(uu < st["u_hi"])
+    assert np.all(ss > st["s_lo"]) and np.all(ss < st["s_hi"])
+    # the state is the power flow at the final controls
+    x2, pinfo = ctx.powerflow(state["u"], x0=state["x"])
+    assert pinfo["iterations"] == 0 and np.abs(x2.cpu().numpy() - state["x"].cpu().numpy()).max() == 0.0

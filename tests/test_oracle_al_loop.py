@@ -8,13 +8,14 @@ functions (their definitions, pinned elsewhere).  A wrong sign or weight in
 the multiplier update, the penalty rule or the step would leave the loop
 infeasible or at another cost.
 
-The static OPF instances take their line limits from the AC base case:
-rate = max(the generator's rate, 1.2 |S| of the base-case AC flow at each
-end).  The generator's own limits are 1.2x the DC flows of the base case, and
-the AC flows exceed them on 7% of the 30-bus grid's branches (up to 1.55x),
-21% of the 1,400-bus grid's (up to 13x) and 35% of the 9,200-bus grid's (up to
-33x), so those instances have no feasible point near the base case and the
-loop stalls at a primal infeasibility of 0.8 to 100.
+The static OPF instances are built so that their AC base case is feasible
+(`synth.static_instance`): line limits max(rate, 1.2 |S| of the base-case
+flow) with an inactive lower bound, reactive limits widened to 1.2 |q| of the
+base case, PQ voltage bounds widened to 2% around the base-case voltages.
+The generator's own limits come from DC flows and per-unit bounds that the AC
+base case violates (line flows up to 33x on the 9,200-bus grid, reactive
+output up to 2x, voltages down to 0.81), and with them the loop stalled at a
+primal infeasibility of 0.05 to 100.
 """
 import numpy as np
 import pytest
@@ -25,16 +26,8 @@ from oracle import al_step as A
 from paper_2110_02590_b300 import synth
 
 
-def static_limits(net, c_base, margin=1.2):
-    """Squared line limits of a static OPF instance: max(rate, margin |S|)^2 per branch, |S| the
-    larger end's apparent flow of the base case (c_base: constraint values there)."""
-    nl = net.n_branch
-    s2 = np.maximum(c_base[:nl], c_base[nl:2 * nl])
-    return np.maximum(net.br_rate ** 2, margin ** 2 * s2)
-
-
 def static_setup(name, mu=0.1, seed=5):
-    """Static OPF instance: nominal loads, line limits from the AC base case (static_limits),
+    """Static OPF instance: nominal loads, bounds from the AC base case (synth.static_instance),
     y = 0, rho = 10; controls 2% inside their bounds, slacks at c clipped 1% inside theirs,
     duals on the central path at mu."""
     net = synth.workload(name)
@@ -43,14 +36,10 @@ def static_setup(name, mu=0.1, seed=5):
     u0 = synth.flat_control(net)
     x0, info = on.powerflow(u0)
     assert info["rc"] == 0
-    r2 = static_limits(net, on.eval(x0, u0)["c"])
+    al = synth.static_instance(net, synth.al_inputs(net, seed=seed), on.eval(x0, u0)["c"])
     u = np.clip(u0, u_lo + 0.02 * (u_hi - u_lo), u_hi - 0.02 * (u_hi - u_lo))
     x, info = on.powerflow(u, x0=x0)
     assert info["rc"] == 0
-    al = synth.al_inputs(net, seed=seed)
-    nl = net.n_branch
-    al["s_hi"][:2 * nl] = np.concatenate([r2, r2])
-    al["sigma_c"][:2 * nl] = np.concatenate([1.0 / r2, 1.0 / r2])
     al["y"] = np.zeros(on.m)
     al["rho"] = 10.0
     lo, hi = al["s_lo"], al["s_hi"]
@@ -97,13 +86,31 @@ def test_al_loop_converges_to_the_slsqp_optimum(tiny_run):
     res = minimize(lambda uu: al["sigma_f"] * ev(uu)[1]["cost"], u0, jac=grad, method="SLSQP",
                    bounds=list(zip(st["u_lo"], st["u_hi"])),
                    constraints=[{"type": "ineq", "fun": cons, "jac": cons_jac}],
-                   options=dict(maxiter=1000, ftol=1e-14))
+                   options=dict(maxiter=1000, ftol=1e-12))  # 1e-14 ends on its line-search precision limit
     assert res.success, res.message
     assert cons(res.x).min() > -1e-9
     f_al = al["sigma_f"] * ev(out["u"])[1]["cost"]
     # the barrier (mu = 1e-5 at the end) and eta_p <= 1e-5 keep the AL point within ~1e-4 of the optimum
     assert abs(f_al - res.fun) <= 2e-4 * abs(res.fun), (f_al, res.fun)
     assert np.abs(out["u"] - res.x).max() < 3e-2
+
+
+def test_scaled_loop_reaches_the_same_optimum(tiny_run):
+    """The gradient-based scaling (Sec. IV-A) changes the path of the loop, not the OPF it solves: the
+    scaled loop stops at the same controls and generation cost (the SLSQP pin above fixes that
+    point), with the rule's scales: the caller's sigma_c times factors in (0, 1], sigma_f from the
+    cost gradient."""
+    net, on, x, u0, al, st, out = tiny_run
+    s0 = np.clip(on.eval(x, u0)["c"], al["s_lo"] + 0.01 * (al["s_hi"] - al["s_lo"]),
+                 al["s_hi"] - 0.01 * (al["s_hi"] - al["s_lo"]))
+    sc = L.al_solve(on, x, u0, s0, np.zeros(on.m), st, al, rho=10.0, max_outer=40, max_inner=30,
+                    scaling_gmax=100.0)
+    assert sc["converged"]
+    assert np.all(sc["sigma_c"] <= al["sigma_c"]) and np.all(sc["sigma_c"] > 0)
+    assert 0 < sc["sigma_f"] <= 1
+    cost = lambda uu: on.eval(on.powerflow(uu, x0=x)[0], uu)["cost"]  # noqa: E731
+    assert abs(cost(sc["u"]) - cost(out["u"])) <= 2e-4 * abs(cost(out["u"]))
+    assert np.abs(sc["u"] - out["u"]).max() < 3e-2
 
 
 def test_al_loop_invariants(tiny_run):

@@ -36,6 +36,11 @@ def test_scaling_rule_by_hand():
     sig2, sf2 = scaling.gradient_scaling(J, np.array([0.0, 0.0]), g_max=10.0, s_min=1e-3)
     assert sig2.tolist() == [0.04, 1.0, 10.0 / 99.9, 1e-3, 0.1, 0.025]
     assert sf2 == 1.0
+    # with the caller's own scales the rule applies to the rows as written, p_i dc_i/du
+    prior = np.array([2.0, 5.0, 0.1, 1e-9, 0.5, 0.25])
+    sig3, _ = scaling.gradient_scaling(J, np.array([1.0]), prior=prior)
+    assert sig3[[0, 1, 2, 4, 5]].tolist() == [2.0 * (100.0 / 500.0), 5.0, 0.1, 0.5, 0.25]
+    assert sig3[3] == pytest.approx(1e-10, rel=1e-15)  # 1e-9 * 1e12 = 1000 > 100: scaled by 0.1
 
 
 def test_explicit_jacobian_matches_finite_differences():
