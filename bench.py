@@ -394,7 +394,7 @@ def autograd_batch(P, torch, dev, nscen):
                     "w.r.t. u, loads and s; plain: power flow + adjoint gradient per scenario"}
 
 
-def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100.0):
+def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100.0, keep_state=False):
     """Static OPF by the augmented-Lagrangian loop (opf_al_solve) on a synthetic grid at its nominal
     loads, on an instance whose AC base case is feasible (synth.static_instance: line limits
     max(rate, 1.2 |S|) with an inactive lower bound, reactive and PQ-voltage bounds widened around
@@ -421,7 +421,11 @@ def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100
     info, hist = ctx.al_solve(dict(sigma_f=al["sigma_f"], rho=10.0, sigma_c=d(al["sigma_c"])), state, y,
                               max_outer=max_outer, max_inner=max_inner, scaling_gmax=scaling_gmax)
     steps = max(1, info["steps"])
-    return {"net": name, "n_u": ctx.nu, "outer": info["outer"], "steps": info["steps"],
+    solved = None
+    if keep_state:  # the optimum the real-time tracking starts from, with the scales the loop used
+        solved = dict(ctx=ctx, net=net, state=state, y=y,
+                      al=dict(sigma_f=info["sigma_f"], rho=info["rho"], sigma_c=info["sigma_c"], y=y))
+    summary = {"net": name, "n_u": ctx.nu, "outer": info["outer"], "steps": info["steps"],
             "converged": bool(info["converged"]), "ms_total": info["ms_total"],
             "ms_per_outer": info["ms_total"] / max(1, info["outer"]), "ms_per_step": info["ms_total"] / steps,
             "primal_inf": info["primal_inf"], "dual_inf": info["dual_inf"], "rho_final": info["rho"],
@@ -433,6 +437,7 @@ def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100
                      "subproblem (one full Hessian each); "
                      + (f"gradient-based scaling with g_max = {scaling_gmax:g}" if scaling_gmax > 0
                         else "the instance's own scales (1/limit^2 on the flows, 1 elsewhere, sigma_f = 1e-4)")}
+    return (summary, solved) if keep_state else summary
 
 
 def mean_complementarity(st):
@@ -446,13 +451,23 @@ def mean_complementarity(st):
     return t / n
 
 
-def tracking_qp(P, torch, ctx, al, state, pds, qds, first, count):
-    """Real-time updates (opf_tracking_update), one after another: power flow at the next load
-    snapshot, then the bounded QP of eq. qp_rto to a KKT error of 1e-6 (one Hessian H(omega) per
-    QP iteration), the power flow at the new controls and the multiplier update.  Each QP starts
-    from the previous update's point (pushed 1e-4 of the bounds' range inside them) and duals, with
-    its barrier at their mean complementarity."""
-    y = al["y"].clone()
+def tracking_qp(P, torch, solved, count, seed=300, inertia_only=True, rho=10.0, reset_slacks=True):
+    """Real-time OPF (Sec. IV-C) from the static optimum of the 9.2k-bus instance (the scaled AL
+    loop's end point, its scales and multipliers) at a fixed penalty rho (the loop's initial one;
+    None: its final one): one update per AR(1) load snapshot (opf_tracking_update: power flow at
+    the new loads, the bounded QP of eq. qp_rto to a KKT error of 1e-6 with one Hessian H(omega)
+    per QP iteration, the power flow at the new controls and the multiplier update).  Each QP
+    starts from the previous point (pushed 1e-4 of the bounds' range inside them; with
+    reset_slacks the slacks restart at the constraints' values at the new loads) and duals, with
+    its barrier at their mean complementarity; inertia_only: no convexity search before the QP."""
+    ctx, net, state, y = solved["ctx"], solved["net"], solved["state"], solved["y"].clone()
+    al = dict(solved["al"])
+    if rho is not None:
+        al["rho"] = float(rho)
+    pds_h, qds_h = synth.ar1_loads(net, count, seed=seed)
+    dev = ctx.device
+    pds = torch.as_tensor(pds_h, device=dev)
+    qds = torch.as_tensor(qds_h, device=dev)
     out = []
     dstart = 0.0
     for k in range(count):
@@ -462,27 +477,36 @@ def tracking_qp(P, torch, ctx, al, state, pds, qds, first, count):
             lo, hi = state[nm + "_lo"], state[nm + "_hi"]
             gap = 1e-4 * (hi - lo)
             state[nm].copy_(torch.minimum(torch.maximum(state[nm], lo + gap), hi - gap))
-        state["x"], _ = ctx.powerflow(state["u"], pd=pds[first + k], qd=qds[first + k], x0=state["x"])
+        state["x"], _ = ctx.powerflow(state["u"], pd=pds[k], qd=qds[k], x0=state["x"])
+        if reset_slacks:  # the slacks restart at the constraints' values at the new loads, inside their bounds
+            c = ctx.reduced_gradient(dict(al, y=y, s=state["s"]))["c"]
+            lo, hi = state["s_lo"], state["s_hi"]
+            gap = 1e-4 * (hi - lo)
+            state["s"].copy_(torch.minimum(torch.maximum(c, lo + gap), hi - gap))
         state["mu"] = mean_complementarity(state)
         mu0 = state["mu"]
-        info = ctx.tracking_update(al, state, y, max_it=100, delta_start=dstart)
-        dstart = info["delta_convex"] / 10.0 if info["delta_convex"] >= 1e-7 else 0.0
+        info = ctx.tracking_update(al, state, y, max_it=100, delta_start=dstart, inertia_only=inertia_only)
+        dstart = info["delta_convex"] / 10.0 if (not inertia_only and info["delta_convex"] >= 1e-7) else 0.0
         info["mu0"] = mu0
         out.append(info)
     it = [i["qp_iterations"] for i in out]
-    return {"updates": count, "qp_iterations": it, "ms_per_update": [i["ms_total"] for i in out],
+    return {"net": "large9200", "updates": count, "qp_iterations": it,
+            "converged": [bool(i["kkt"] <= 1e-6) for i in out],
+            "ms_per_update": [i["ms_total"] for i in out],
             "ms_hessians_per_update": [i["ms_hessian"] for i in out],
             "ms_cholesky_per_update": [i["ms_cholesky"] for i in out],
-            "hvps_per_update": [(n + 1) * ctx.nu for n in it],
+            "hvps_per_update": [(n + (0 if inertia_only else 1)) * ctx.nu for n in it],
             "ms_per_qp_iteration": statistics.median(i["ms_qp"] / max(1, i["qp_iterations"]) for i in out),
             "kkt_first": [i["kkt_first"] for i in out], "kkt": [i["kkt"] for i in out],
             "mu0": [i["mu0"] for i in out], "delta_convex": [i["delta_convex"] for i in out],
+            "delta_end": [i["delta"] for i in out], "inertia_only": bool(inertia_only),
             "halvings": [i["halvings"] for i in out],
-            "note": "the first update starts from the bench's tracking state (not an optimum: slacks within "
-                    "1e-6 of their bounds, KKT error ~1e9); the later ones from the previous QP solution; "
-                    "stop at E_0 <= 1e-6 or 100 iterations; the QP is convexified (H_uu + delta I positive "
-                    "definite, the search starting at a tenth of the previous update's delta); HVPs per update "
-                    "count the convexity Hessian H(0) and one H(omega) per iteration"}
+            "rho": al["rho"], "reset_slacks": bool(reset_slacks),
+            "note": "starts from the static OPF optimum (scaled AL loop, the static_opf_al entry of the same "
+                    "grid) and tracks AR(1) loads (1% innovations per snapshot) at a fixed penalty; the slacks "
+                    "restart at the constraints' values at the new loads (clipped into their bounds); stop at "
+                    "E_0 <= 1e-6 or 100 iterations; delta grows only where a QP iteration's Schur complement is "
+                    "not positive definite; HVPs per update: one H(omega) per QP iteration"}
 
 
 def batched_snapshots(P, torch, dev, block_k):
@@ -602,7 +626,7 @@ def run_gpu(args):
     # level-merge schedule of the single-RHS solves (look-ahead distance, largest merged chunk)
     sw_d, sw_w, sw_ms, sw_table = ctx.sweep_autotune(table=True)
     ke = max(1, min(args.steps, args.e2e_steps))  # end-to-end steps, on the snapshots after the timed ones
-    nsnap = args.warmup + args.steps + 1 + ke + 4  # the last four: the tracking-QP leg
+    nsnap = args.warmup + args.steps + 1 + ke
     pds_h, qds_h = synth.ar1_loads(net, nsnap, seed=100 + rank)
     pds, qds = d(pds_h), d(qds_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -710,11 +734,13 @@ def run_gpu(args):
         sh_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dev)
         sharded = {"ms": sh_ms, "hvps_per_s": nu / (sh_ms * 1e-3), "ranks": world,
                    "split": "contiguous column ranges in whole tiles, one NCCL all-gather of H"}
-    rto = None if args.no_extras else tracking_qp(P, torch, ctx, al, state, pds, qds,
-                                                  args.warmup + args.steps + 1 + ke, 4)
-    al_static = None if args.no_extras else [static_opf(P, torch, dev, "medium1400"),
-                                             static_opf(P, torch, dev, "medium1400", scaling_gmax=0.0),
-                                             static_opf(P, torch, dev, WORKLOAD)]
+    al_static = rto = None
+    if not args.no_extras:
+        big, solved = static_opf(P, torch, dev, WORKLOAD, keep_state=True)
+        al_static = [static_opf(P, torch, dev, "medium1400"),
+                     static_opf(P, torch, dev, "medium1400", scaling_gmax=0.0), big]
+        rto = tracking_qp(P, torch, solved, 4) if big["converged"] else None
+        del solved
 
     if rank != 0:
         if world > 1:

@@ -411,6 +411,7 @@ typedef struct {
    * right-hand side; Cholesky with its inertia corrections; the two triangular
    * solves, J d_u and the fraction to the boundary; trial power flows and update */
   float ms_first_order, ms_rhs, ms_cholesky, ms_solve, ms_trial;
+  int cholesky_fp64;  /* factorisations run with FP64 trailing updates (opf_set_cholesky_mode) */
 } opf_step_info;
 
 /* p supplies sigma_f, rho, sigma_c and y (its s and omega are ignored: s comes
@@ -492,10 +493,11 @@ opf_status opf_al_solve(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_
  * min(0.2 mu, mu^1.5)) when E_mu <= 10 mu; fraction to the boundary tau =
  * max(0.99, 1 - mu); delta starts at the smallest of 0 (or opts->delta_start),
  * 1e-8, 1e-7, ... that makes H_uu + delta I positive definite (H_uu = H(0), one
- * more Hessian and Cholesky before the iterations), so that the QP is convex --
- * the paper starts the tracking at an optimum, where H_uu is positive definite
- * and delta = 0 -- and grows further only if an iteration's S is not positive
- * definite.  grad q is carried from iteration to iteration through the Newton
+ * more Hessian and Cholesky before the iterations), so that the QP is convex,
+ * and grows further only if an iteration's S is not positive definite; with
+ * opts->inertia_only the convexity search is skipped (H_uu is indefinite even
+ * at an OPF optimum, along the directions that move active constraints, while
+ * S, which holds the barrier terms of those bounds, is not).  grad q is carried from iteration to iteration through the Newton
  * system: H d = -grad psi - Sigma d.
  * p: sigma_f, rho, sigma_c (y, s, omega ignored); y [m] updated in place; st:
  * u, s (w_t in, w_{t+1} out), bound duals (the QP's, warm start in, final out),
@@ -510,6 +512,10 @@ typedef struct {
   int max_halvings;   /* (0 = 10) */
   int max_inertia;    /* inertia-correction increases per factorisation (0 = 24) */
   double delta_start; /* the QP's first delta (0 = start at 0) */
+  int inertia_only;   /* 1: no convexity search before the iterations: delta starts at delta_start
+                         (or 0) and grows only where an iteration's S is not positive definite (the
+                         usual inertia correction of an interior-point method; the barrier terms
+                         Sigma of the active bounds supply the curvature H_uu lacks at an optimum) */
 } opf_qp_opts;
 
 typedef struct {
@@ -520,10 +526,33 @@ typedef struct {
   float ms_qp;        /* gradient at w_t and the QP iterations */
   float ms_hessian;   /* summed device time of the QP's Hessians H(omega) */
   float ms_cholesky;  /* summed device time of its factorisations */
+  int cholesky_fp64;  /* factorisations run with FP64 trailing updates (opf_set_cholesky_mode) */
 } opf_qp_info;
 
 opf_status opf_tracking_update(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_state* st,
                                const opf_qp_opts* opts, opf_qp_info* info);
+
+/*
+ * opf_set_cholesky_mode: how the dense Cholesky of the reduced-Newton step and
+ * of the tracking QP (the Schur complement of Prop. 3) applies its trailing
+ * updates.  The updates of each 128-column group are emulated in FP64 on the
+ * tensor cores (exact digit products, FP64 sums), whose error per element is
+ * below ~5 K u max_k|P_rk| max_k|P_ck| -- relative to the rows' largest panel
+ * entries -- where an FP64 update errs by ~K u sum_k |P_rk P_ck|; on a Schur
+ * complement whose rows span many decades (penalty weights rho sigma^2 of
+ * 1e9 beside O(1) curvature) the emulation could make a pivot of a positive
+ * definite matrix non-positive, and the inertia correction would then raise
+ * delta for nothing.
+ *   mode 1 (default): emulated only;
+ *   mode 0: emulated; a failed pivot is re-checked with FP64 updates at the
+ *     same delta before delta grows (the step and QP infos count them);
+ *   mode 2: FP64 only (slower: four rank-32 updates of the trailing triangle
+ *     per group).
+ * On the workloads here modes 1 and 2 took the same inertia corrections, so
+ * the default keeps the emulation; mode 0 costs an FP64 factorisation for
+ * every genuine failure.  Errors: OPF_EINVAL.
+ */
+opf_status opf_set_cholesky_mode(opf_ctx* ctx, int mode);
 
 /*
  * opf_set_wait_limit: iteration limit of every bounded device-side wait of

@@ -20,9 +20,13 @@ barrier update mu <- max(tol/10, min(0.2 mu, mu^1.5)) when E_mu <= 10 mu,
 fraction to the boundary tau = max(0.99, 1 - mu), and a regularisation delta
 that only grows within one QP, starting at the smallest of {delta_start or 0,
 1e-8, 1e-7, ...} that makes H_uu + delta I positive definite, so that the QP is
-convex (the paper starts the tracking from an optimum, where H_uu is positive
-definite and delta = 0; away from one the reduced Hessian of the AL is
-indefinite).
+convex (away from an optimum the reduced Hessian of the AL is indefinite and
+the bounded QP unbounded along negative curvature).  Option inertia_only: no
+convexity search; delta starts at delta_start and grows only where an
+iteration's Schur complement S is not positive definite, as in an
+interior-point method's inertia correction (H_uu lacks curvature along the
+directions that move active constraints even at an optimum; S holds the
+barrier terms of those bounds).
 """
 import numpy as np
 
@@ -55,7 +59,7 @@ def explicit_jacobian(on, x, u, pd=None, qd=None):
 
 
 def tracking_update(on, x, u, s, y, st, al, pd=None, qd=None, tol=1e-6, max_it=50, max_halvings=10,
-                    delta_start=0.0):
+                    delta_start=0.0, inertia_only=False):
     """One update from w_t = (u, s) with the state x at u and the new loads.  st: bounds, bound duals
     and mu (the QP's first barrier).  Returns the new point, duals, y, and the QP's record."""
     alt = dict(al, y=y, s=s)
@@ -71,9 +75,10 @@ def tracking_update(on, x, u, s, y, st, al, pd=None, qd=None, tol=1e-6, max_it=5
     bnd = {k: st[k] for k in ("u_lo", "u_hi", "s_lo", "s_hi")}
     mu = st["mu"]
     # convexity: the smallest delta in {delta_start or 0, 1e-8, 1e-7, ...} with H_uu + delta I
-    # positive definite (the QP's Hessian is then positive semidefinite)
+    # positive definite (the QP's Hessian is then positive semidefinite); with inertia_only delta
+    # grows only where an iteration's Schur complement S is not positive definite
     delta = delta_start
-    while True:
+    while not inertia_only:
         try:
             np.linalg.cholesky(H0 + delta * np.eye(nu))
             break

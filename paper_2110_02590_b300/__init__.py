@@ -82,7 +82,8 @@ class StepInfo(C.Structure):
                 ("du_inf", C.c_double), ("ds_inf", C.c_double), ("halvings", C.c_int),
                 ("inertia_tries", C.c_int), ("pf_iterations", C.c_int), ("ms_hessian", C.c_float),
                 ("ms_total", C.c_float), ("ms_first_order", C.c_float), ("ms_rhs", C.c_float),
-                ("ms_cholesky", C.c_float), ("ms_solve", C.c_float), ("ms_trial", C.c_float)]
+                ("ms_cholesky", C.c_float), ("ms_solve", C.c_float), ("ms_trial", C.c_float),
+                ("cholesky_fp64", C.c_int)]
 
 
 class AlOpts(C.Structure):
@@ -99,7 +100,7 @@ class AlInfo(C.Structure):
 
 class QpOpts(C.Structure):
     _fields_ = [("max_it", C.c_int), ("tol", C.c_double), ("block_k", C.c_int), ("max_halvings", C.c_int),
-                ("max_inertia", C.c_int), ("delta_start", C.c_double)]
+                ("max_inertia", C.c_int), ("delta_start", C.c_double), ("inertia_only", C.c_int)]
 
 
 class QpInfo(C.Structure):
@@ -108,7 +109,7 @@ class QpInfo(C.Structure):
                 ("kkt", C.c_double), ("mu", C.c_double),
                 ("alpha_p", C.c_double), ("kkt_first", C.c_double), ("alpha_p_min", C.c_double),
                 ("ms_total", C.c_float), ("ms_qp", C.c_float), ("ms_hessian", C.c_float),
-                ("ms_cholesky", C.c_float)]
+                ("ms_cholesky", C.c_float), ("cholesky_fp64", C.c_int)]
 
 
 class BatchInfo(C.Structure):
@@ -156,6 +157,7 @@ def lib():
                                            C.POINTER(C.c_float)]
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_set_sweep_merge.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.opf_set_cholesky_mode.argtypes = [C.c_void_p, C.c_int]
         L.opf_sweep_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
                                          C.POINTER(C.c_float)]
         L.opf_reduced_jacobian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
@@ -558,6 +560,13 @@ class OPFContext:
                                                              tiles=info.tiles, launches=info.launches,
                                                              ms_total=info.ms_total, ms_hvp=info.ms_hvp)
 
+    def set_cholesky_mode(self, mode):
+        """Trailing updates of the dense Cholesky (opf_set_cholesky_mode): 1 emulated only (the
+        default), 0 emulated with an FP64 re-check of a failed pivot, 2 FP64 only."""
+        st = lib().opf_set_cholesky_mode(self.h, int(mode))
+        if st != 0:
+            raise OPFError(st, "opf_set_cholesky_mode")
+
     def set_sweep_merge(self, lookahead, narrow=4):
         """Level-merge schedule of the single-right-hand-side solves (opf_set_sweep_merge)."""
         self._sync_stream()
@@ -652,7 +661,7 @@ class OPFContext:
         return out, hist[:info.outer].copy()
 
     def tracking_update(self, al, state, y, max_it=50, tol=1e-6, block_k=0, max_halvings=0, max_inertia=0,
-                        delta_start=0.0):
+                        delta_start=0.0, inertia_only=False):
         """One real-time update (opf_tracking_update): gradient and Hessian at the current point, the
         bounded QP of eq. qp_rto by an interior-point method on the Schur complement, the power flow
         at the new controls and the multiplier update.  `al`: sigma_f, rho, sigma_c; y and the state
@@ -665,7 +674,8 @@ class OPFContext:
         info = QpInfo()
         rc = lib().opf_tracking_update(self.h, C.byref(p), C.c_void_p(y.data_ptr()), C.byref(st),
                                        C.byref(QpOpts(int(max_it), float(tol), int(block_k), int(max_halvings),
-                                                      int(max_inertia), float(delta_start))), C.byref(info))
+                                                      int(max_inertia), float(delta_start),
+                                                      int(bool(inertia_only)))), C.byref(info))
         state["mu"] = st.mu
         if rc != 0:
             raise OPFError(rc, "opf_tracking_update")

@@ -496,6 +496,7 @@ struct opf_ctx {
   long long launches = 0;         // kernels launched by this context
   opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
   int tuned_k = 0, tuned_threads = 0;  // opf_hessian_autotune's choice (0 = none)
+  int chol_mode = 1;               // dense Cholesky trailing updates (opf_set_cholesky_mode)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;
   cudaStream_t cap_stream = nullptr;

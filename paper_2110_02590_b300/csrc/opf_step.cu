@@ -754,8 +754,10 @@ opf_status alloc_step(opf_ctx* c) {
 // panels run right-looking in FP64 (diagonal block with its inverse, panel
 // solve, update of the group's remaining columns); after the group, the rest of
 // the trailing triangle takes the group's rank-128 update at once, emulated on
-// the tensor cores (launch_oz_update: exact digit products, FP64 sums).
-opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag) {
+// the tensor cores (launch_oz_update: exact digit products, FP64 sums), or,
+// with emulate false, as four rank-32 FP64 updates (chol_syrk_kernel over the
+// whole trailing triangle, one per panel of the group).
+opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag, bool emulate) {
   cudaStream_t s1 = c->stream;
   for (int c0 = 0; c0 < n; c0 += GB) {
     const int c1 = std::min(n, c0 + GB);
@@ -774,11 +776,49 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag)
       }
     }
     if (c1 < n) {
-      launch_oz_update(s1, A, n, c0, c1 - c0, c1, w->oz_e, w->oz_d, flag);
-      c->launches += 2;
+      if (emulate) {
+        launch_oz_update(s1, A, n, c0, c1 - c0, c1, w->oz_e, w->oz_d, flag);
+        c->launches += 2;
+      } else {
+        const int tiles = (n - c1 + 31) / 32;
+        for (int k0 = c0; k0 < c1; k0 += NB) {
+          const int kb = std::min(NB, c1 - k0);
+          SCK(launch_pdl(chol_syrk_kernel<32>, dim3(tiles * (tiles + 1) / 2), dim3(256), 0, s1, A, n, k0, kb, flag,
+                         0, c1 - k0 - kb, n));
+          c->launches++;
+        }
+      }
     }
   }
   return OPF_OK;
+}
+
+// L = S + delta I factorised in place in w->L; ok: no pivot was non-positive.
+// Mode 1 (the default) emulates the trailing updates on the tensor cores.
+// Mode 0 also factorises S + delta I again with FP64 trailing updates when a
+// pivot fails, before the caller raises delta: the emulation errs by up to
+// ~5 K u max_k|P_rk| max_k|P_ck| per element (relative to the rows' largest
+// panel entries), where an FP64 update errs by ~K u sum_k |P_rk P_ck|, so on a
+// Schur complement whose rows span many decades a pivot the FP64 update keeps
+// positive could fail.  Mode 2: FP64 only.  fp64_runs counts the FP64
+// factorisations.
+opf_status factor_shifted(opf_ctx* c, StepWork* w, int nu, double delta, bool& ok, int& fp64_runs) {
+  cudaStream_t stream = c->stream;
+  auto run = [&](bool emulate) -> opf_status {
+    add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
+    SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
+    c->launches++;
+    const opf_status rc = launch_cholesky(c, w, w->L, nu, w->flag, emulate);
+    if (rc) return rc;
+    if (!emulate) fp64_runs++;
+    SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaStreamSynchronize(stream));
+    ok = !*w->h_flag;
+    return OPF_OK;
+  };
+  const opf_status rc = run(c->chol_mode != 2);
+  if (rc || ok || c->chol_mode != 0) return rc;
+  return run(false);
 }
 
 opf_status launch_chol_solve(opf_ctx* c, StepWork* w, double* A, int n, double* b) {
@@ -887,19 +927,15 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   // Cholesky with inertia correction
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double delta = delta0;
-  int tries = 0;
+  int tries = 0, fp64_runs = 0;
   for (;; tries++) {
-    add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
-    SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
-    c->launches++;
-    rc = launch_cholesky(c, w, w->L, nu, w->flag);
+    bool ok = false;
+    rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
     if (rc) {
       cudaStreamWaitEvent(stream, w->aux_done, 0);  // no work of this call outlives it
       return rc;
     }
-    SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    SCK(cudaStreamSynchronize(stream));
-    if (!*w->h_flag) break;
+    if (ok) break;
     if (tries >= max_inertia) {
       cudaStreamWaitEvent(stream, w->aux_done, 0);
       set_last_error("S_uu not positive definite after the inertia corrections");
@@ -1012,6 +1048,7 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
     info->delta = delta;
     info->halvings = halvings;
     info->inertia_tries = tries;
+    info->cholesky_fp64 = fp64_runs;
     info->pf_iterations = pfi.iterations;
     info->ms_hessian = ms_hessian;
     float ms = 0.f;
@@ -1125,10 +1162,11 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
   double mu = st->mu, delta = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0, kkt_first = 0.0, ap_min = 1.0;
   float ms_hess = 0.f, ms_chol = 0.f;
-  int it = 0, increases = 0;
+  int it = 0, increases = 0, fp64_runs = 0;
   // convexity: the smallest delta of {delta_start or 0, 1e-8, 1e-7, ...} with H_uu + delta I
   // positive definite (H_uu = H(0), no Gauss-Newton weights), so that the QP is convex
-  {
+  // (skipped with inertia_only: delta then grows only where an iteration's S needs it)
+  if (!(o && o->inertia_only)) {
     SCK(cudaMemsetAsync(w->omega, 0, m * sizeof(double), stream));
     SCK(cudaMemsetAsync(w->sig_u, 0, nu * sizeof(double), stream));
     opf_al_params p0 = pt;
@@ -1142,14 +1180,10 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     c->launches++;
     SCK(cudaEventRecord(ev[1], stream));
     for (int tries = 0;; tries++) {
-      add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
-      SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
-      c->launches++;
-      rc = launch_cholesky(c, w, w->L, nu, w->flag);
+      bool ok = false;
+      rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
       if (rc) return rc;
-      SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
-      SCK(cudaStreamSynchronize(stream));
-      if (!*w->h_flag) break;
+      if (ok) break;
       if (tries >= max_inertia) {
         set_last_error("tracking QP: H_uu not positive definite after the inertia corrections");
         return OPF_ENOTPD;
@@ -1194,14 +1228,10 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     SCK(cudaEventRecord(ev[1], stream));
     const double d_old = delta;
     for (int tries = 0;; tries++) {
-      add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
-      SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
-      c->launches++;
-      rc = launch_cholesky(c, w, w->L, nu, w->flag);
+      bool ok = false;
+      rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
       if (rc) return rc;
-      SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
-      SCK(cudaStreamSynchronize(stream));
-      if (!*w->h_flag) break;
+      if (ok) break;
       if (tries >= max_inertia) {
         set_last_error("tracking QP: S_uu not positive definite after the inertia corrections");
         return OPF_ENOTPD;
@@ -1297,6 +1327,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     info->halvings = halvings;
     info->pf_iterations = pfi.iterations;
     info->inertia_increases = increases;
+    info->cholesky_fp64 = fp64_runs;
     info->delta = delta;
     info->delta_convex = delta_convex;
     info->kkt = e_0;
@@ -1464,4 +1495,13 @@ extern "C" opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf
     binfo->failed = failed;
   }
   return first;
+}
+
+extern "C" opf_status opf_set_cholesky_mode(opf_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 2) {
+    set_last_error("ctx is required and mode must be 0, 1 or 2");
+    return OPF_EINVAL;
+  }
+  c->chol_mode = mode;
+  return OPF_OK;
 }

@@ -64,6 +64,30 @@ def test_al_step_parity(name, mu, delta_start):
     assert torch.isfinite(g["grad_u"]).all()
 
 
+@pytest.mark.parametrize("mode", [0, 2])
+def test_al_step_cholesky_modes(mode):
+    """The 9.2k-bus step with FP64 trailing updates (mode 2) and with the FP64 re-check of failed
+    pivots (mode 0): the same inertia corrections and step as the oracle's LAPACK-style FP64 step
+    (the test above runs the default, emulated updates)."""
+    net = synth.workload("large9200")
+    on, x, u, al, st = setup(net, mu=0.1)
+    ref = A.al_step(on, x, u, al["s"], st, al)
+    ctx = P.OPFContext(net)
+    ctx.set_cholesky_mode(mode)
+    xg, _ = ctx.powerflow(dev(u))
+    state = {k: dev(v) for k, v in st.items() if k != "mu"}
+    state.update(u=dev(u), s=dev(al["s"]), x=xg, mu=0.1)
+    al_dev = {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+    du, ds, inf = ctx.al_step(al_dev, state)
+    assert inf["delta"] == ref["delta"]
+    assert rel(du.cpu().numpy(), ref["du"]) < STEP_TOL
+    assert rel(ds.cpu().numpy(), ref["ds"]) < STEP_TOL
+    # mode 2 factorises in FP64 every time; mode 0 once per failed emulated try
+    assert inf["cholesky_fp64"] == (inf["inertia_tries"] + 1 if mode == 2 else inf["inertia_tries"])
+    with pytest.raises(P.OPFError):
+        ctx.set_cholesky_mode(3)
+
+
 def test_al_step_requires_state():
     net = synth.workload("tiny30")
     ctx = P.OPFContext(net)

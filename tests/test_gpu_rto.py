@@ -34,18 +34,21 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("name,seed_y", [("tiny30", None), ("tiny30", 3), ("medium1400", None)])
-def test_tracking_update_parity(name, seed_y):
+@pytest.mark.parametrize("name,seed_y,inertia_only", [("tiny30", None, False), ("tiny30", 3, False),
+                                                     ("medium1400", None, False), ("tiny30", 3, True),
+                                                     ("medium1400", None, True)])
+def test_tracking_update_parity(name, seed_y, inertia_only):
     net, on, x, u, s, al, st, pd, qd = tracking_instance(name)
     y = np.zeros(on.m) if seed_y is None else np.random.default_rng(seed_y).uniform(-0.05, 0.05, on.m)
-    ref = rto.tracking_update(on, x, u, s, y, st, al, pd=pd, qd=qd)
+    ref = rto.tracking_update(on, x, u, s, y, st, al, pd=pd, qd=qd, inertia_only=inertia_only)
     ctx = P.OPFContext(net)
     x0, _ = ctx.powerflow(dev(u))  # the state before the load change, as a warm start
     xg, _ = ctx.powerflow(dev(u), pd=dev(pd), qd=dev(qd), x0=x0)
     state = {k: dev(v) for k, v in st.items() if k != "mu"}
     state.update(u=dev(u), s=dev(s), x=xg, mu=st["mu"])
     yg = dev(y)
-    info = ctx.tracking_update(dict(sigma_f=al["sigma_f"], rho=al["rho"], sigma_c=dev(al["sigma_c"])), state, yg)
+    info = ctx.tracking_update(dict(sigma_f=al["sigma_f"], rho=al["rho"], sigma_c=dev(al["sigma_c"])), state, yg,
+                               inertia_only=inertia_only)
     assert info["qp_iterations"] == ref["iterations"]
     assert info["delta"] == ref["delta"] and info["halvings"] == ref["halvings"]
     assert info["delta_convex"] == ref["delta_convex"]

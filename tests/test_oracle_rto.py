@@ -26,7 +26,10 @@ def tracking_instance(name, step=1, mu=1e-2):
     return net, on, x1, u, s, al, st, pd, qd
 
 
-def test_qp_solution_matches_lbfgsb_on_the_convex_qp():
+@pytest.mark.parametrize("inertia_only", [False, True])
+def test_qp_solution_matches_lbfgsb_on_the_convex_qp(inertia_only):
+    """With and without the convexity search (inertia_only: delta grows only where an
+    iteration's S is not positive definite; here the QP is convex from delta_start on)."""
     net, on, x, u, s, al, st, pd, qd = tracking_instance("tiny30")
     y = np.zeros(on.m)
     alt = dict(al, y=y, s=s)
@@ -34,7 +37,8 @@ def test_qp_solution_matches_lbfgsb_on_the_convex_qp():
     H0 = on.reduced_hessian(x, u, alt, omega=np.zeros(on.m), pd=pd, qd=qd)
     H0 = 0.5 * (H0 + H0.T)
     delta = max(0.0, -np.linalg.eigvalsh(H0).min()) + 1e-3
-    out = rto.tracking_update(on, x, u, s, y, st, al, pd=pd, qd=qd, tol=1e-8, delta_start=delta)
+    out = rto.tracking_update(on, x, u, s, y, st, al, pd=pd, qd=qd, tol=1e-8, delta_start=delta,
+                              inertia_only=inertia_only)
     assert out["kkt"] <= 1e-8 and out["delta"] == delta and out["halvings"] == 0
     J = rto.explicit_jacobian(on, x, u, pd, qd)
     R = al["rho"] * al["sigma_c"] ** 2
