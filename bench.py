@@ -60,14 +60,19 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+# The sources that decide the HVP kernel's code, launch and data layout: the kernel
+# itself, the device structures it reads, the host set-up that builds its schedules
+# and tilings, and the symbolic analysis (ordering, fill, levels).
+HVP_SOURCES = ("opf_api.cu", "opf_internal.h", "opf_kernels.cu", "symbolic.cpp")
+
+
 def kernel_source_hash():
-    """SHA-256 over the library's sources in name order (csrc/*.cu, *.cpp, *.h)."""
+    """SHA-256 over the HVP kernel's sources (HVP_SOURCES, in that order)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cpp", ".h")):
-            with open(os.path.join(CSRC, f), "rb") as fh:
-                h.update(fh.read())
+    for f in HVP_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
@@ -88,7 +93,7 @@ def profiled_traffic():
     if "traffic_bytes_per_launch" not in vals or "kernel_source_sha256" not in vals:
         return None, "ncu summary without machine-readable traffic"
     if vals["kernel_source_sha256"] != kernel_source_hash():
-        return None, "library sources changed since the ncu capture"
+        return None, "HVP kernel sources changed since the ncu capture"
     return float(vals["traffic_bytes_per_launch"]), "ncu capture of " + vals.get("kernel_launch", "the kernel")
 
 
