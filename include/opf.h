@@ -555,10 +555,23 @@ opf_status opf_tracking_update(opf_ctx* ctx, const opf_al_params* p, double* y, 
 opf_status opf_set_cholesky_mode(opf_ctx* ctx, int mode);
 
 /*
+ * opf_set_update_engine: which tensor-core kernel runs the emulated trailing
+ * updates of the dense Cholesky (modes 0 and 1 of opf_set_cholesky_mode):
+ *   engine 0 (default): tcgen05.mma with the eight level sums of a 128 x 64
+ *     tile held in tensor memory, one persistent CTA per SM; its waits for the
+ *     tensor cores are bounded (opf_set_wait_limit) and a wait that gives up
+ *     makes the step or QP call return OPF_ETIMEOUT;
+ *   engine 1: warp-level mma.sync on 64 x 64 tiles.
+ * The two engines give bit-identical factors.  Errors: OPF_EINVAL.
+ */
+opf_status opf_set_update_engine(opf_ctx* ctx, int engine);
+
+/*
  * opf_set_wait_limit: iteration limit of every bounded device-side wait of
  * this context (the flag polls of the dense block's cluster LU and of the
- * dense triangular solves of opf_al_step); 0 restores each kernel's default
- * (2^22 and 2^24 polls).  A wait that reaches the limit stops waiting, records
+ * dense triangular solves of opf_al_step, the mbarrier polls of the tcgen05
+ * emulated Cholesky update); 0 restores each kernel's default (2^22, 2^24
+ * and 2^24 polls).  A wait that reaches the limit stops waiting, records
  * the timeout and lets its kernel finish; the call then returns OPF_ETIMEOUT
  * (a refactorisation also drops the context's state, as OPF_ESINGULAR does)
  * and the context stays usable.  Errors: OPF_EINVAL (spins < 0), OPF_ECUDA.
@@ -592,12 +605,16 @@ opf_status opf_set_wait_limit(opf_ctx* ctx, int spins);
  * digits against a per-row power of two; digit products accumulated exactly;
  * levels i + j >= 8 and the digit tails dropped).  Element (r, c) of the
  * update then errs by less than 5 K 2^-53 max_k |P_rk| max_k |P_ck| before the
- * final FP64 roundings.  Allocates and frees its workspace.  Errors:
- * OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA.
+ * final FP64 roundings.  engine 0: tcgen05 MMAs with the level sums in tensor
+ * memory (the default of the factorisation); 1: warp-level mma.sync.  Both
+ * sum the same exact integers and fold them the same way, so their results
+ * are bit-identical.  Allocates and frees its workspace.  Errors: OPF_EINVAL,
+ * OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT (a bounded wait of the tcgen05 kernel
+ * gave up; the result is void).
  */
 opf_status opf_fp64_peak(void* stream, double* tflops, float* ms_out);
 opf_status opf_pivot_reciprocal(void* stream, const double* u, double* r, int n);
-opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0);
+opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0, int engine);
 
 /*
  * opf_al_step_batched: one tracking update for each of n snapshots (contexts of

@@ -158,6 +158,7 @@ def lib():
         L.opf_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.opf_set_sweep_merge.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.opf_set_cholesky_mode.argtypes = [C.c_void_p, C.c_int]
+        L.opf_set_update_engine.argtypes = [C.c_void_p, C.c_int]
         L.opf_sweep_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
                                          C.POINTER(C.c_float)]
         L.opf_reduced_jacobian.argtypes = [C.c_void_p, C.POINTER(AlParams), C.POINTER(HessOpts), C.c_void_p,
@@ -176,7 +177,8 @@ def lib():
                                    C.POINTER(AlOpts), C.POINTER(AlInfo), C.POINTER(C.c_double)]
         L.opf_fp64_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)]
         L.opf_pivot_reciprocal.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
-        L.opf_dense_syrk_emulated.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.opf_dense_syrk_emulated.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                              C.c_int]
         L.opf_status_str.restype = C.c_char_p
         L.opf_status_str.argtypes = [C.c_int]
         L.opf_last_error.restype = C.c_char_p
@@ -289,14 +291,16 @@ def pivot_reciprocal(u):
     return r
 
 
-def dense_syrk_emulated(A, c0, K, r0):
+def dense_syrk_emulated(A, c0, K, r0, engine=0):
     """A[r0:, r0:] (lower) -= P P^T, P = A[r0:, c0:c0+K], in place on a column-major n x n
-    cuda float64 matrix given as its transpose view (A_t[j] = column j), emulated on tensor cores."""
+    cuda float64 matrix given as its transpose view (A_t[j] = column j), emulated on tensor cores
+    (engine 0: tcgen05, 1: warp-level mma.sync)."""
     import torch
     if A.dtype != torch.float64 or not A.is_cuda or not A.is_contiguous() or A.dim() != 2 or \
             A.shape[0] != A.shape[1]:
         raise ValueError("expected a square contiguous cuda float64 tensor")
-    st = lib().opf_dense_syrk_emulated(_stream(), C.c_void_p(A.data_ptr()), A.shape[0], int(c0), int(K), int(r0))
+    st = lib().opf_dense_syrk_emulated(_stream(), C.c_void_p(A.data_ptr()), A.shape[0], int(c0), int(K), int(r0),
+                                       int(engine))
     if st != 0:
         raise OPFError(st, "opf_dense_syrk_emulated")
     return A
@@ -566,6 +570,13 @@ class OPFContext:
         st = lib().opf_set_cholesky_mode(self.h, int(mode))
         if st != 0:
             raise OPFError(st, "opf_set_cholesky_mode")
+
+    def set_update_engine(self, engine):
+        """Tensor-core kernel of the emulated Cholesky updates (opf_set_update_engine): 0 tcgen05
+        (the default), 1 warp-level mma.sync."""
+        st = lib().opf_set_update_engine(self.h, int(engine))
+        if st != 0:
+            raise OPFError(st, "opf_set_update_engine")
 
     def set_sweep_merge(self, lookahead, narrow=4):
         """Level-merge schedule of the single-right-hand-side solves (opf_set_sweep_merge)."""

@@ -106,29 +106,43 @@ opf_status opf_pivot_reciprocal(void* stream, const double* u, double* r, int n)
   return OPF_OK;
 }
 
-opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0) {
-  if (!A || n < 1 || c0 < 0 || K < 32 || K > 128 || K % 32 != 0 || c0 + K > r0 || r0 >= n) {
-    set_last_error("need A, 0 <= c0, c0 + K <= r0 < n and K in {32, 64, 96, 128}");
+opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0, int engine) {
+  if (!A || n < 1 || c0 < 0 || K < 32 || K > 128 || K % 32 != 0 || c0 + K > r0 || r0 >= n || engine < 0 ||
+      engine > 1) {
+    set_last_error("need A, 0 <= c0, c0 + K <= r0 < n, K in {32, 64, 96, 128} and engine 0 or 1");
     return OPF_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const opf_status so = setup_oz();
   if (so != OPF_OK) return so;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("cannot query the device");
+    return OPF_ECUDA;
+  }
   const size_t M = (size_t)(n - r0);
   int* E = nullptr;
   int* flag = nullptr;
   void* D = nullptr;
-  if (cudaMalloc(&E, sizeof(int) * M) != cudaSuccess || cudaMalloc(&flag, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&D, (size_t)2 * 8 * (size_t)K * M) != cudaSuccess) {
+  if (cudaMalloc(&E, sizeof(int) * M) != cudaSuccess || cudaMalloc(&flag, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&D, (size_t)2 * 8 * (size_t)K * (size_t)oz_rows_tiled((int)M)) != cudaSuccess) {
     cudaGetLastError();
     if (E) cudaFree(E);
     if (flag) cudaFree(flag);
     set_last_error("cannot allocate the emulated-update workspace");
     return OPF_ENOMEM;
   }
-  cudaMemsetAsync(flag, 0, sizeof(int), st);
-  launch_oz_update(st, A, n, c0, K, r0, E, D, flag);
-  cudaError_t e = cudaStreamSynchronize(st);
+  cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
+  OzEngine eng;
+  eng.tcgen05 = engine == 0;
+  eng.err = flag + 1;
+  eng.sm_count = sms;
+  launch_oz_update(st, A, n, c0, K, r0, E, D, flag, eng);
+  int timeout = 0;
+  cudaError_t e = cudaMemcpyAsync(&timeout, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaFree(E);
   cudaFree(flag);
@@ -136,6 +150,10 @@ opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K
   if (e != cudaSuccess) {
     set_last_error(std::string("opf_dense_syrk_emulated: ") + cudaGetErrorString(e));
     return OPF_ECUDA;
+  }
+  if (timeout) {
+    set_last_error("opf_dense_syrk_emulated: a bounded wait for the tensor cores gave up");
+    return OPF_ETIMEOUT;
   }
   return OPF_OK;
 }

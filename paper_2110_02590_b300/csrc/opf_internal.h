@@ -401,13 +401,29 @@ void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, 
                              const LuTail& tail);
 
 opf_status setup_oz();
-void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag);
-// the two halves of launch_oz_update: digits, then the tiles of one part (0 all,
+// Which tensor-core engine runs the emulated update: the tcgen05 kernel (TMEM
+// accumulators; its bounded mbarrier waits record a timeout in *err, polling at
+// most lim times) or the warp-level mma.sync kernel.
+struct OzEngine {
+  bool tcgen05 = true;
+  int* err = nullptr;
+  long long lim = 1ll << 24;
+  int sm_count = 148;
+};
+void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag,
+                      const OzEngine& eng);
+// the halves of launch_oz_update: digits, then the tiles of one part (0 all,
 // 1 the first 128 columns, 2 the rest) on at most grid CTAs (0: one per tile)
+// with the warp-level MMAs, or the whole triangle with tcgen05
 void launch_oz_slice(cudaStream_t st, const double* A, int n, int c0, int K, int r0, int* E, void* D,
-                     const int* flag);
+                     const int* flag, bool tiled);
+// rows of the core-matrix digit layout of an M-row panel (M rounded up to 128);
+// the digit workspace holds 8 oz_rows_tiled(M) K bf16
+inline int oz_rows_tiled(int M) { return (M + 127) / 128 * 128; }
 void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D, const int* flag,
                     int part, int grid);
+void launch_oz_syrk_tc(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D,
+                       const int* flag, int* err, long long lim, int sm_count);
 
 opf_status setup_sweep_streams(opf_ctx* c, const std::vector<int>& bptr_f, const std::vector<int4>& bmeta_f,
                                const std::vector<int>& bptr_b, const std::vector<int4>& bmeta_b);
@@ -497,6 +513,7 @@ struct opf_ctx {
   opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
   int tuned_k = 0, tuned_threads = 0;  // opf_hessian_autotune's choice (0 = none)
   int chol_mode = 1;               // dense Cholesky trailing updates (opf_set_cholesky_mode)
+  int oz_engine = 0;               // emulated updates: 0 tcgen05, 1 warp-level mma.sync (opf_set_update_engine)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;
   cudaStream_t cap_stream = nullptr;

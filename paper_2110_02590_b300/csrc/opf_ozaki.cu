@@ -21,8 +21,12 @@
 //
 // The digits are computed with integer shifts of the FP64 bit patterns (no
 // rounding step), and the tensor-core work is 36 digit pairs per output: the
-// B300's bf16 rate (~1.1 PFLOP/s for mma.sync in registers) against its FP64
-// rate (~1 TFLOP/s) makes this ~10-30 times faster than FP64 FMAs.
+// B300's bf16 tensor rate (~1.8 PFLOP/s with tcgen05, ~1.1 with mma.sync in
+// registers) against its FP64 rate (~1.2 TFLOP/s) makes this ~10-30 times
+// faster than FP64 FMAs.  Two engines run the tile products: the tcgen05
+// kernel (default; level sums in tensor memory, digits staged by bulk copies)
+// and the warp-level mma.sync kernel; both sum the same exact integers and
+// round the same way, so their results are bit-identical.
 
 #include <cuda_bf16.h>
 
@@ -63,12 +67,19 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int E) {
 }  // namespace
 
 // Digits of P = A[r0 : r0 + M, c0 : c0 + K] (column-major A, leading dimension
-// n): E[r] and D[s][r][k] (bf16, row-major, K per row).  One CTA per 32 rows,
-// its 32 warps over the columns; the digits pass through shared memory so that both
-// the reads (along rows) and the writes (along columns) coalesce.
+// n): E[r] and the eight bf16 digit planes.  Row-major layout (tiled = false):
+// D[s][r][k], K per row, M rows.  Core-matrix layout (tiled = true), the one
+// the tcgen05 kernel stages with bulk copies: for each 16 columns of K (kc)
+// and digit s, a block of Mp rows (M rounded up to 128, the extra rows zero)
+// of 16 digits in 8-row x 8-column core matrices of 128 bytes, the two core
+// matrices of an 8-row group side by side (element (r, k) at ((kc 8 + s) Mp +
+// (r / 8) 8) 16 + ((k / 8) mod 2) 64 + (r mod 8) 8 + k mod 8), so 128 or 64
+// consecutive rows of one plane and kc are one contiguous run.  One CTA per 32
+// rows, its 32 warps over the columns; the digits pass through shared memory
+// so that the reads (along rows) coalesce and every thread writes 16 bytes.
 __global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict__ A, int n, int c0, int K, int r0,
-                                                      int M, int* __restrict__ E, __nv_bfloat16* __restrict__ D,
-                                                      const int* flag) {
+                                                      int M, int Mp, bool tiled, int* __restrict__ E,
+                                                      __nv_bfloat16* __restrict__ D, const int* flag) {
   pdl_wait();
   if (*flag) return;
   __shared__ int emax_s[32][32];
@@ -92,6 +103,7 @@ __global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict
   }
   __syncthreads();
   const int er = emax_s[0][lane];
+  const int rows_out = tiled ? Mp : M;
   for (int kt = 0; kt < K; kt += 32) {
     for (int kk = w; kk < 32; kk += nw) {
       const int k = kt + kk;
@@ -105,9 +117,18 @@ __global__ void __launch_bounds__(1024) oz_slice_kernel(const double* __restrict
       }
     }
     __syncthreads();
-    for (int q = w; q < OZ_S * 32; q += nw) {
-      const int s = q >> 5, rr = q & 31, row = blockIdx.x * 32 + rr;
-      if (row < M && kt + lane < K) D[((size_t)s * M + row) * K + kt + lane] = dig[s][lane][rr];
+    // one 16-byte piece (8 digits of one row and plane) per item: 8 planes x 32 rows x 4 groups
+    for (int it = threadIdx.x; it < OZ_S * 32 * 4; it += blockDim.x) {
+      const int g = it & 3, rr = (it >> 2) & 31, s = it >> 7;
+      const int row = blockIdx.x * 32 + rr, k0 = kt + g * 8;
+      if (row >= rows_out || k0 >= K) continue;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) v[e] = dig[s][g * 8 + e][rr];
+      const size_t idx = tiled ? (((size_t)(k0 >> 4) * OZ_S + s) * Mp + (row >> 3) * 8) * 16 + ((k0 >> 3) & 1) * 64 +
+                                     (row & 7) * 8
+                               : ((size_t)s * M + row) * K + k0;
+      *reinterpret_cast<uint4*>(D + idx) = *reinterpret_cast<const uint4*>(v);
     }
     __syncthreads();
   }
@@ -254,11 +275,384 @@ __global__ void __launch_bounds__(512, 1) oz_syrk_kernel(double* A, int n, int r
   pdl_trigger();
 }
 
+// ---------------------------------------------------------------------------
+// The same update on the fifth-generation tensor cores (tcgen05): 128 x 64
+// output tiles whose eight level sums live in tensor memory (TMEM) as eight
+// 128-lane x 64-column FP32 accumulators -- all 512 columns of the SM's TMEM,
+// so one CTA per SM, persistent over the tiles.  Warp-specialised:
+//   warp 0, the producer: per job (tile, 16 columns of K) 16 bulk copies
+//     (cp.async.bulk, the TMA engine) of the digit planes, in the core-matrix
+//     layout oz_slice writes, into one of four shared-memory stages, completed
+//     on the stage's `full` mbarrier by byte count;
+//   warp 1, the MMA issuer (it also allocates and frees the TMEM): per job the
+//     36 digit-pair MMAs (M = 128, N = 64, K = 16, bf16, FP32 accumulation:
+//     exact, as above), committed to the stage's `empty` mbarrier, and after a
+//     tile's last job to `accf`; before a tile's first MMA it waits on `acce`;
+//   warps 4-11, the epilogue: each reads TMEM lanes 32 (w mod 4) .. + 31 and
+//     half of the columns with tcgen05.ld, folds the levels exactly as the
+//     warp-level kernel does (so both engines give bit-identical results),
+//     updates A and arrives on `acce`.
+// The shared-memory operands use the no-swizzle K-major canonical layout: 8-row
+// x 16-byte core matrices, neighbours along K 128 bytes apart, 8-row groups 256
+// bytes apart.  Every wait is bounded: a wait that gives up sets `abort` (every
+// other wait loop watches it) and *err; after all roles stop, the copies and
+// MMAs already issued are drained with a limit of their own, far above their
+// duration, before the TMEM is freed.
+
+namespace {
+
+constexpr int TC_M = 128;                              // output rows per tile (TMEM lanes)
+constexpr int TC_N = 64;                               // output columns per tile
+constexpr int TC_KC = 16;                              // K per job: one MMA step
+constexpr int TC_NST = 4;                              // shared-memory stages
+constexpr int TC_PLANE_A = TC_M * TC_KC * 2;           // bytes of one digit plane of the row block
+constexpr int TC_PLANE_B = TC_N * TC_KC * 2;           // ... of the column block
+constexpr int TC_STAGE = OZ_S * (TC_PLANE_A + TC_PLANE_B);
+constexpr int TC_COLS = OZ_S * TC_N;                   // TMEM columns: the eight level accumulators
+constexpr int TC_EPI_WARPS = 8;                        // warps 4 .. 11
+constexpr int TC_THREADS = 32 * (4 + TC_EPI_WARPS);
+constexpr long long TC_DRAIN = 1ll << 26;             // polls of the drain after an abort
+// instruction descriptor (kind::f16): FP32 accumulator, bf16 A and B, both
+// K-major, N / 8 at bit 17, M / 16 at bit 24
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                              ((unsigned)(TC_M >> 4) << 24);
+
+// shared-memory matrix descriptor: no swizzle, K-major core matrices, leading
+// (K) byte offset 128, stride (row-group) byte offset 256, descriptor version 1
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr) {
+  return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)(128 >> 4) << 16) |
+         ((unsigned long long)(256 >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long ad, unsigned long long bd, bool acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(TC_IDESC), "r"((unsigned)acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool tc_try(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Poll for the mbarrier phase of this parity, at most lim times.
+__device__ __forceinline__ bool tc_poll(unsigned bar, unsigned parity, long long lim) {
+  for (long long it = 0; it < lim; it++)
+    if (tc_try(bar, parity)) return true;
+  return false;
+}
+
+// Wait for the mbarrier phase of this parity; false when `lim` polls pass or
+// another role has aborted.
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity, long long lim, volatile int* abort_) {
+  for (long long it = 0; it < lim; it++) {
+    if (tc_try(bar, parity)) return true;
+    if (*abort_) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned* r, unsigned taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// The update of one element in integer arithmetic: with X = hi 2^28 + lo (exact,
+// |X| < 2^76 as a 128-bit two's-complement pair), returns u = RN(X) 2^(e - 28)
+// (X rounded once to 53 bits, ties to even), which is what the warp-level
+// kernel's fma(lo, 2^-28, hi) times 2^e gives; ok is false when u would leave
+// the normal range (the caller then uses that FP64 formula).  Branch-free, so
+// the elements of a chunk interleave; one FP64 operation per element is left
+// (old - u) where the FP64 formula takes four.
+__device__ __forceinline__ double tc_fold(long long hi, long long lo, int e, bool& ok) {
+  unsigned long long xl = (unsigned long long)hi << 28;
+  long long xh = hi >> 36;
+  const unsigned long long l2 = xl + (unsigned long long)lo;
+  xh += (long long)(l2 < xl) - (long long)(lo < 0);
+  xl = l2;
+  const bool neg = xh < 0;
+  const unsigned long long nl = ~xl + 1ull;
+  const long long nh = ~xh + (long long)(nl == 0ull);
+  xl = neg ? nl : xl;
+  xh = neg ? nh : xh;
+  const bool zero = (xl | (unsigned long long)xh) == 0ull;
+  const int nb = xh ? 128 - __clzll(xh) : 64 - __clzll((long long)xl);  // bit length of |X|
+  int sh = nb - 53;
+  // sh <= 0: exact, m = |X| 2^-sh; 1 <= sh <= 23: the dropped bits round to nearest even
+  const int ls = max(-sh, 0), rs = min(max(sh, 1), 63);
+  const unsigned long long rem = xl & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
+  unsigned long long mr = (xl >> rs) | ((unsigned long long)xh << (64 - rs));
+  mr += (rem > half || (rem == half && (mr & 1ull))) ? 1ull : 0ull;
+  const bool carry = mr == (1ull << 53);
+  mr = carry ? (mr >> 1) : mr;
+  const unsigned long long m = sh > 0 ? mr : (xl << min(ls, 63));
+  sh = sh > 0 ? sh + (int)carry : sh;
+  const int biased = sh + e - 28 + 52 + 1023;
+  ok = zero || (biased >= 1 && biased <= 2046);
+  const double u = __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) |
+                                                    ((unsigned long long)(biased & 2047) << 52) |
+                                                    (m & ((1ull << 52) - 1ull))));
+  return zero ? 0.0 : u;
+}
+
+// (row tile, column tile) of tile t: row tile bi holds column tiles 0 ..
+// min(2 bi + 1, nct - 1) (the lower triangle in 128 x 64 tiles)
+__device__ __forceinline__ void tc_tile_of(int t, int nct, int& bi, int& bj) {
+  bi = 0;
+  for (;;) {
+    const int cnt = min(2 * bi + 2, nct);
+    if (t < cnt) break;
+    t -= cnt;
+    bi++;
+  }
+  bj = t;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1) oz_syrk_tc_kernel(double* A, int n, int r0, int M, int Mp, int K,
+                                                                   const __nv_bfloat16* __restrict__ D,
+                                                                   const int* __restrict__ E, const int* flag,
+                                                                   int* err, long long lim, int ntiles, int nct) {
+  pdl_wait();
+  if (*flag) return;
+  extern __shared__ __align__(1024) unsigned char tc_sm[];
+  __shared__ __align__(8) unsigned long long bars[2 * TC_NST + 2];  // full[4], empty[4], accf, acce
+  __shared__ unsigned tslot;
+  __shared__ volatile int abort_;
+  __shared__ int last_load, last_mma, last_taken;  // jobs: copied, committed, consumed by the MMAs
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned base = ((unsigned)__cvta_generic_to_shared(tc_sm) + 1023u) & ~1023u;
+  const unsigned b0 = (unsigned)__cvta_generic_to_shared(&bars[0]);
+  auto full = [&](int s) { return b0 + 8u * (unsigned)s; };
+  auto empty = [&](int s) { return b0 + 8u * (unsigned)(TC_NST + s); };
+  const unsigned accf = b0 + 8u * (2 * TC_NST), acce = accf + 8u;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(&tslot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * TC_NST + 1; s++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0 + 8u * (unsigned)s) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acce), "r"(TC_EPI_WARPS) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_ = 0;
+    last_load = last_mma = last_taken = -1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tslot;
+  const int nch = K / TC_KC;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int njobs = my_tiles * nch;
+  auto tile_rows = [&](int lt, int& rowA, int& rowB) {
+    int bi, bj;
+    tc_tile_of((int)blockIdx.x + lt * (int)gridDim.x, nct, bi, bj);
+    rowA = bi * TC_M;
+    rowB = bj * TC_N;
+  };
+  auto fail = [&]() {
+    abort_ = 1;
+    atomicExch(err, 1);
+  };
+
+  if (warp == 0) {  // producer
+    for (int j = 0; j < njobs; j++) {
+      const int s = j % TC_NST;
+      bool ok = true;
+      if (lane == 0) {
+        if (j >= TC_NST) ok = tc_wait(empty(s), (unsigned)(((j - TC_NST) / TC_NST) & 1), lim, &abort_);
+        if (ok) {
+          int ra, rb;
+          tile_rows(j / nch, ra, rb);
+          const int kc = j % nch;
+          const unsigned st = base + (unsigned)s * TC_STAGE;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(TC_STAGE)
+                       : "memory");
+#pragma unroll 1
+          for (int pl = 0; pl < OZ_S; pl++) {
+            const __nv_bfloat16* pa = D + (((size_t)kc * OZ_S + pl) * Mp + ra) * TC_KC;
+            const __nv_bfloat16* pb = D + (((size_t)kc * OZ_S + pl) * Mp + rb) * TC_KC;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    st + (unsigned)(pl * TC_PLANE_A)),
+                "l"(pa), "r"(TC_PLANE_A), "r"(full(s))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    st + (unsigned)(OZ_S * TC_PLANE_A + pl * TC_PLANE_B)),
+                "l"(pb), "r"(TC_PLANE_B), "r"(full(s))
+                : "memory");
+          }
+          last_load = j;
+        } else {
+          fail();
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+    }
+  } else if (warp == 1) {  // MMA issuer
+    for (int j = 0; j < njobs; j++) {
+      const int s = j % TC_NST, lt = j / nch, c = j % nch;
+      bool ok = true;
+      if (lane == 0) {
+        if (c == 0 && lt > 0) ok = tc_wait(acce, (unsigned)((lt - 1) & 1), lim, &abort_);  // accumulators read
+        if (ok) ok = tc_wait(full(s), (unsigned)((j / TC_NST) & 1), lim, &abort_);       // operands landed
+        if (ok) {
+          last_taken = j;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned sa = base + (unsigned)s * TC_STAGE, sb = sa + OZ_S * TC_PLANE_A;
+#pragma unroll
+          for (int i = 0; i < OZ_S; i++) {
+            const unsigned long long ad = tc_desc(sa + i * TC_PLANE_A);
+#pragma unroll
+            for (int jj = 0; jj + i < OZ_S; jj++)
+              tc_mma(tmem + (unsigned)((i + jj) * TC_N), ad, tc_desc(sb + jj * TC_PLANE_B), c > 0 || i > 0);
+          }
+          tc_commit(empty(s));
+          if (c == nch - 1) tc_commit(accf);
+          last_mma = j;
+        } else {
+          fail();
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+    }
+  } else if (warp >= 4) {  // epilogue
+    const int q = warp & 3, h = (warp - 4) >> 2;
+    const double s28 = __longlong_as_double((long long)(1023 - 28) << 52);  // 2^-28: levels 4-7 against 0-3
+    for (int lt = 0; lt < my_tiles; lt++) {
+      const bool ok = __all_sync(0xffffffffu, tc_wait(accf, (unsigned)(lt & 1), lim, &abort_));
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int ra, rb;
+      tile_rows(lt, ra, rb);
+      const int lr = ra + q * 32 + lane;
+      const int er = lr < M ? E[lr] : 0;
+      // the exponents of this warp's 32 columns, one load per lane (broadcast by shuffles)
+      const int ecol = rb + h * 32 + lane < M ? E[rb + h * 32 + lane] : 0;
+      // (1) both 16-column chunks out of TMEM: the levels folded into exact
+      // integers and rounded to the subtrahends u (the FP64 formula where they
+      // leave the normal range); then the accumulators are released, so the
+      // next tile's MMAs run while (2) updates A
+      double u[2][16];
+      unsigned fb[2] = {0u, 0u};
+#pragma unroll
+      for (int cc = 0; cc < 2; cc++) {
+        const int col0 = h * 32 + cc * 16;
+        // hi = (acc0 2^7 + acc1) 2^14 + (acc2 2^7 + acc3), lo likewise from levels
+        // 4-7: a pair folds exactly in 32-bit integers, since level t holds t + 1
+        // digit pairs over K <= 128 columns (|acc_t| <= (t + 1) 128 127^2), so
+        // |acc_t 2^7 + acc_t+1| < 1.87e9 < 2^31
+        long long hi[16], lo[16];
+#pragma unroll
+        for (int l = 0; l < OZ_S; l += 2) {
+          unsigned v0[16], v1[16];
+          tc_ld16(v0, tmem + ((unsigned)(q * 32) << 16) + (unsigned)(l * TC_N + col0));
+          tc_ld16(v1, tmem + ((unsigned)(q * 32) << 16) + (unsigned)((l + 1) * TC_N + col0));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            const int pr = __float2int_rz(__uint_as_float(v0[k])) * 128 + __float2int_rz(__uint_as_float(v1[k]));
+            if (l == 0) hi[k] = (long long)pr * (1ll << 14);
+            if (l == 2) hi[k] += pr;
+            if (l == 4) lo[k] = (long long)pr * (1ll << 14);
+            if (l == 6) lo[k] += pr;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int lc = rb + col0 + k;
+          const int ec = __shfl_sync(0xffffffffu, ecol, cc * 16 + k);
+          bool ok;
+          u[cc][k] = tc_fold(hi[k], lo[k], er + ec - 35, ok);
+          fb[cc] |= (lr < M && lc <= lr && !ok) ? (1u << k) : 0u;
+        }
+        if (fb[cc]) {  // rare: a subnormal or out-of-range subtrahend
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            if ((fb[cc] >> k) & 1u) u[cc][k] = fma((double)lo[k], s28, (double)hi[k]);  // x 2^21
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce) : "memory");
+      // (2) the old values of a chunk first (independent loads), then its updates
+#pragma unroll
+      for (int cc = 0; cc < 2; cc++) {
+        const int col0 = h * 32 + cc * 16;
+        double old[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int lc = rb + col0 + k;
+          old[k] = (lr < M && lc <= lr) ? A[(size_t)(r0 + lc) * n + r0 + lr] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int lc = rb + col0 + k;
+          if (lr < M && lc <= lr) {
+            double r = old[k] - u[cc][k];
+            if ((fb[cc] >> k) & 1u) {  // rare: a subnormal or out-of-range subtrahend
+              const int e = er + E[lc] - 35;
+              const double scl = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                                           : ldexp(1.0, e);
+              r = fma(-u[cc][k], scl, old[k]);
+            }
+            A[(size_t)(r0 + lc) * n + r0 + lr] = r;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (abort_ && threadIdx.x == 32) {
+    // drain: the MMAs already committed and the copies not yet consumed
+    // complete before the TMEM and the shared memory are released
+    if (last_mma >= 0) tc_poll(empty(last_mma % TC_NST), (unsigned)((last_mma / TC_NST) & 1), TC_DRAIN);
+    for (int j = last_taken + 1; j <= last_load; j++)
+      tc_poll(full(j % TC_NST), (unsigned)((j / TC_NST) & 1), TC_DRAIN);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
+  }
+  pdl_trigger();
+}
+
 size_t oz_syrk_smem() { return 2 * sizeof(unsigned short) * (size_t)OZ_STAGE; }
+size_t oz_syrk_tc_smem() { return (size_t)TC_NST * TC_STAGE + 1024; }
 
 opf_status setup_oz() {
   if (cudaFuncSetAttribute(oz_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_syrk_smem()) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaFuncSetAttribute(oz_syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)oz_syrk_tc_smem()) != cudaSuccess) {
     cudaGetLastError();
     set_last_error("cannot raise the shared-memory limit of the emulated FP64 update");
     return OPF_ECUDA;
@@ -269,16 +663,17 @@ opf_status setup_oz() {
 // Digits of P = A[r0 : n, c0 : c0 + K] (K <= 128, a multiple of 32) into E
 // (n - r0 ints) and D (8 (n - r0) K bf16).
 void launch_oz_slice(cudaStream_t st, const double* A, int n, int c0, int K, int r0, int* E, void* D,
-                     const int* flag) {
+                     const int* flag, bool tiled) {
   const int M = n - r0;
   if (M <= 0 || K <= 0) return;
-  launch_pdl(oz_slice_kernel, dim3((M + 31) / 32), dim3(1024), 0, st, A, n, c0, K, r0, M, E,
-             static_cast<__nv_bfloat16*>(D), flag);
+  const int Mp = oz_rows_tiled(M);
+  launch_pdl(oz_slice_kernel, dim3(((tiled ? Mp : M) + 31) / 32), dim3(1024), 0, st, A, n, c0, K, r0, M, Mp, tiled,
+             E, static_cast<__nv_bfloat16*>(D), flag);
 }
 
-// A[r0 :, r0 :] (lower) -= P P^T from the digits: part = 0 the whole triangle,
-// 1 the first 128 columns (all rows below), 2 the columns after them; grid 0
-// takes one CTA per tile, else at most grid CTAs.
+// A[r0 :, r0 :] (lower) -= P P^T from the digits, with the warp-level MMAs:
+// part = 0 the whole triangle, 1 the first 128 columns (all rows below), 2 the
+// columns after them; grid 0 takes one CTA per tile, else at most grid CTAs.
 void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D, const int* flag,
                     int part, int grid) {
   const int M = n - r0;
@@ -300,9 +695,27 @@ void launch_oz_syrk(cudaStream_t st, double* A, int n, int K, int r0, const int*
              static_cast<const __nv_bfloat16*>(D), E, flag, strip, toff, ntiles);
 }
 
-void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag) {
-  launch_oz_slice(st, A, n, c0, K, r0, E, D, flag);
-  launch_oz_syrk(st, A, n, K, r0, E, D, flag, 0, 0);
+// The same update on the tcgen05 tensor cores from the core-matrix digits: 128 x
+// 64 tiles of the lower triangle, one persistent CTA per SM (at most sm_count).
+void launch_oz_syrk_tc(cudaStream_t st, double* A, int n, int K, int r0, const int* E, const void* D,
+                       const int* flag, int* err, long long lim, int sm_count) {
+  const int M = n - r0;
+  if (M <= 0 || K <= 0) return;
+  const int nrt = (M + TC_M - 1) / TC_M, nct = (M + TC_N - 1) / TC_N;
+  int ntiles = 0;
+  for (int bi = 0; bi < nrt; bi++) ntiles += std::min(2 * bi + 2, nct);
+  const int g = std::max(1, std::min(ntiles, sm_count));
+  launch_pdl(oz_syrk_tc_kernel, dim3(g), dim3(TC_THREADS), oz_syrk_tc_smem(), st, A, n, r0, M, oz_rows_tiled(M), K,
+             static_cast<const __nv_bfloat16*>(D), E, flag, err, lim, ntiles, nct);
+}
+
+void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag,
+                      const OzEngine& eng) {
+  launch_oz_slice(st, A, n, c0, K, r0, E, D, flag, eng.tcgen05);
+  if (eng.tcgen05)
+    launch_oz_syrk_tc(st, A, n, K, r0, E, D, flag, eng.err, eng.lim, eng.sm_count);
+  else
+    launch_oz_syrk(st, A, n, K, r0, E, D, flag, 0, 0);
 }
 
 }  // namespace opf

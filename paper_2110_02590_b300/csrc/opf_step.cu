@@ -32,7 +32,7 @@ struct StepWork {
   double* red;                                  // [2]: alpha_p, alpha_d (as ordered bits)
   double* Dinv;                                 // [ceil(n_u / 32)][32][32]: inverses of the factor's diagonal blocks
   int* oz_e = nullptr;                          // [n_u] row exponents of the emulated trailing update
-  void* oz_d = nullptr;                         // [8][n_u][128] bf16 digits of the emulated trailing update
+  void* oz_d = nullptr;                         // 8 x 128 x (n_u rounded up to 128) bf16 digits of the emulated trailing update
   int* flag;
   double* h_red;
   double* h_ls = nullptr;  // pinned [8]: the line search's reductions
@@ -43,6 +43,7 @@ struct StepWork {
   cudaEvent_t aux_go = nullptr, aux_done = nullptr;
   unsigned* trsv_flags = nullptr;  // [ceil(n_u / 32)] block flags of the dense solves (epochs)
   int* trsv_err = nullptr;         // a dense-solve wait timed out
+  int* oz_err = nullptr;           // a wait of the tcgen05 emulated update timed out
   unsigned trsv_epoch = 0;
   // tracking QP (opf_tracking_update): grad q, the linearisation point w_t and its
   // state, the KKT reductions and the constraint values at the new point
@@ -704,6 +705,7 @@ opf_status alloc_step(opf_ctx* c) {
   }
   w->flag = reinterpret_cast<int*>(p);
   w->trsv_err = w->flag + 1;
+  w->oz_err = w->flag + 2;
   w->trsv_flags = reinterpret_cast<unsigned*>(w->flag + 8);
   if (cudaMemset(w->flag, 0, (8 + (size_t)nu / 32 + 1) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -714,7 +716,7 @@ opf_status alloc_step(opf_ctx* c) {
   }
   if (cudaMallocHost(&w->h_red, 2 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&w->h_ls, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&w->h_flag, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&w->h_flag, 4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     c->stepw = w;
     free_step_work(c);
@@ -722,7 +724,7 @@ opf_status alloc_step(opf_ctx* c) {
     return OPF_ENOMEM;
   }
   if (cudaMalloc(&w->oz_e, sizeof(int) * (size_t)nu) != cudaSuccess ||
-      cudaMalloc(&w->oz_d, (size_t)2 * 8 * GB * (size_t)nu) != cudaSuccess) {
+      cudaMalloc(&w->oz_d, (size_t)2 * 8 * GB * (size_t)oz_rows_tiled(nu)) != cudaSuccess) {
     cudaGetLastError();
     c->stepw = w;
     free_step_work(c);
@@ -777,7 +779,12 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag,
     }
     if (c1 < n) {
       if (emulate) {
-        launch_oz_update(s1, A, n, c0, c1 - c0, c1, w->oz_e, w->oz_d, flag);
+        OzEngine eng;
+        eng.tcgen05 = c->oz_engine == 0;
+        eng.err = w->oz_err;
+        eng.lim = c->wait_limit > 0 ? (long long)c->wait_limit : (1ll << 24);
+        eng.sm_count = c->sm_count;
+        launch_oz_update(s1, A, n, c0, c1 - c0, c1, w->oz_e, w->oz_d, flag, eng);
         c->launches += 2;
       } else {
         const int tiles = (n - c1 + 31) / 32;
@@ -811,9 +818,14 @@ opf_status factor_shifted(opf_ctx* c, StepWork* w, int nu, double delta, bool& o
     const opf_status rc = launch_cholesky(c, w, w->L, nu, w->flag, emulate);
     if (rc) return rc;
     if (!emulate) fp64_runs++;
-    SCK(cudaMemcpyAsync(w->h_flag, w->flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SCK(cudaMemcpyAsync(w->h_flag, w->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     SCK(cudaStreamSynchronize(stream));
-    ok = !*w->h_flag;
+    if (w->h_flag[2]) {  // a wait of the emulated update gave up: the factor is void
+      SCK(cudaMemsetAsync(w->oz_err, 0, sizeof(int), stream));
+      set_last_error("emulated Cholesky update: a bounded wait for the tensor cores gave up");
+      return OPF_ETIMEOUT;
+    }
+    ok = !w->h_flag[0];
     return OPF_OK;
   };
   const opf_status rc = run(c->chol_mode != 2);
@@ -1503,5 +1515,14 @@ extern "C" opf_status opf_set_cholesky_mode(opf_ctx* c, int mode) {
     return OPF_EINVAL;
   }
   c->chol_mode = mode;
+  return OPF_OK;
+}
+
+extern "C" opf_status opf_set_update_engine(opf_ctx* c, int engine) {
+  if (!c || engine < 0 || engine > 1) {
+    set_last_error("ctx is required and engine must be 0 (tcgen05) or 1 (mma.sync)");
+    return OPF_EINVAL;
+  }
+  c->oz_engine = engine;
   return OPF_OK;
 }

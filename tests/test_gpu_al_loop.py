@@ -55,9 +55,12 @@ def test_al_loop_parity(name, max_outer, gmax):
     far more closely.  (Over longer runs an Armijo test or a subproblem stop that falls within
     rounding of its threshold can go the other way; the converged run is compared at its end.)"""
     ref, info, hist, state, y = run_both(name, max_outer, scaling_gmax=gmax)
-    # the scales (the caller's, or the gradient rule's at the start) agree first
-    assert rel(info["sigma_c"].cpu().numpy(), ref["sigma_c"]) < 1e-12
-    assert abs(info["sigma_f"] - ref["sigma_f"]) <= 1e-12 * ref["sigma_f"]
+    # the scales (the caller's, or the gradient rule's at the start) agree first; the rule's
+    # scales are g_max over the largest |entry| of a row of the reduced Jacobian J (or of the
+    # cost gradient), and J's entries differ from the oracle's by summation order (the tile
+    # width is autotuned by timing), up to ~2e-12 relative here against 1e-9 in J's own parity
+    assert rel(info["sigma_c"].cpu().numpy(), ref["sigma_c"]) < 1e-10
+    assert abs(info["sigma_f"] - ref["sigma_f"]) <= 1e-10 * ref["sigma_f"]
     rh = np.array(ref["history"])
     assert info["outer"] == len(rh)
     assert info["converged"] == int(ref["converged"])

@@ -69,8 +69,9 @@ def test_pivot_reciprocal_zero_and_subnormal_give_nan():
     assert np.all(np.isnan(r)), r
 
 
+@pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("K,decades", [(128, 9), (64, 9), (128, 0)])
-def test_emulated_rank_k_update_error_bound(K, decades):
+def test_emulated_rank_k_update_error_bound(K, decades, engine):
     rng = np.random.default_rng(5 + K + decades)
     M, c0 = 512, 0
     r0 = c0 + K
@@ -83,7 +84,7 @@ def test_emulated_rank_k_update_error_bound(K, decades):
     Cm = A[r0:, r0:].copy()
     # column-major storage on the device: the tensor's row j is column j of A
     At = torch.as_tensor(np.ascontiguousarray(A.T), device=DEV)
-    P.dense_syrk_emulated(At, c0, K, r0)
+    P.dense_syrk_emulated(At, c0, K, r0, engine=engine)
     got = At.cpu().numpy().T[r0:, r0:]
     Pl = Pm.astype(np.longdouble)
     ref = Cm.astype(np.longdouble) - Pl @ Pl.T
@@ -98,6 +99,35 @@ def test_emulated_rank_k_update_error_bound(K, decades):
     assert np.array_equal(got[~lower], Cm[~lower])
     # and the update really happened: the result is the product's, not the input
     assert np.abs((got - Cm)[lower]).max() > 0.1
+
+
+@pytest.mark.parametrize("M,K,c0", [(2771, 128, 0), (300, 96, 8), (129, 32, 0), (64, 64, 40), (1, 128, 0)])
+def test_emulated_update_engines_bit_identical(M, K, c0):
+    """The tcgen05 kernel (level sums in tensor memory) and the warp-level mma.sync kernel add
+    the same exact integer digit products and fold them the same way: the updated triangles
+    are equal bit for bit, on ragged sizes (partial 128 x 64 and 64 x 64 tiles) and the
+    largest update of the 9.2k-bus grid's Schur complement (2,771 rows)."""
+    rng = np.random.default_rng(M + K)
+    r0 = c0 + K
+    n = r0 + M
+    A = rng.standard_normal((n, n)) * 10.0 ** rng.uniform(-6, 3, (n, 1))
+    outs = []
+    for engine in (0, 1):
+        At = torch.as_tensor(np.ascontiguousarray(A.T), device=DEV)
+        P.dense_syrk_emulated(At, c0, K, r0, engine=engine)
+        outs.append(At.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    # and it is the update: the lower triangle changed, everything else did not
+    low = np.tril(np.ones((M, M), dtype=bool))
+    got = outs[0].T
+    assert np.array_equal(got[:, :r0], A[:, :r0]) and np.array_equal(got[:r0, :], A[:r0, :])
+    blk, ref = got[r0:, r0:], A[r0:, r0:]
+    assert np.array_equal(blk[~low], ref[~low])
+    Pm = A[r0:, c0:c0 + K]
+    exact = ref - Pm @ Pm.T
+    scale = np.abs(Pm).max(axis=1)
+    err = np.abs(blk - exact)[low] / (np.outer(scale, scale)[low] + np.abs(ref)[low])
+    assert err.max() < 1e-12
 
 
 def test_fp64_peak_is_plausible():
