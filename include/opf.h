@@ -558,11 +558,16 @@ opf_status opf_set_cholesky_mode(opf_ctx* ctx, int mode);
  * opf_set_update_engine: which tensor-core kernel runs the emulated trailing
  * updates of the dense Cholesky (modes 0 and 1 of opf_set_cholesky_mode):
  *   engine 0 (default): tcgen05.mma with the eight level sums of a 128 x 64
- *     tile held in tensor memory, one persistent CTA per SM; its waits for the
- *     tensor cores are bounded (opf_set_wait_limit) and a wait that gives up
- *     makes the step or QP call return OPF_ETIMEOUT;
- *   engine 1: warp-level mma.sync on 64 x 64 tiles.
- * The two engines give bit-identical factors.  Errors: OPF_EINVAL.
+ *     tile held in tensor memory, one persistent CTA per SM, for the updates
+ *     of at least 80 such tiles (trailing blocks above ~1,000 rows); the
+ *     smaller updates, whose few 128-row tiles cannot hide their latency,
+ *     run on warp-level mma.sync;
+ *   engine 1: warp-level mma.sync on 64 x 64 tiles for every update;
+ *   engine 2: tcgen05 for every update.
+ * The tcgen05 kernel's waits for the tensor cores and its bulk copies are
+ * bounded (opf_set_wait_limit); a wait that gives up makes the step or QP call
+ * return OPF_ETIMEOUT.  All engines give bit-identical factors.  Errors:
+ * OPF_EINVAL.
  */
 opf_status opf_set_update_engine(opf_ctx* ctx, int engine);
 
@@ -605,10 +610,11 @@ opf_status opf_set_wait_limit(opf_ctx* ctx, int spins);
  * digits against a per-row power of two; digit products accumulated exactly;
  * levels i + j >= 8 and the digit tails dropped).  Element (r, c) of the
  * update then errs by less than 5 K 2^-53 max_k |P_rk| max_k |P_ck| before the
- * final FP64 roundings.  engine 0: tcgen05 MMAs with the level sums in tensor
- * memory (the default of the factorisation); 1: warp-level mma.sync.  Both
- * sum the same exact integers and fold them the same way, so their results
- * are bit-identical.  Allocates and frees its workspace.  Errors: OPF_EINVAL,
+ * final FP64 roundings.  engine as in opf_set_update_engine (0: tcgen05 MMAs
+ * with the level sums in tensor memory for updates of at least 80 tiles of
+ * 128 x 64, mma.sync below; 1: warp-level mma.sync; 2: tcgen05).  The engines
+ * sum the same exact integers and round the same way, so their results are
+ * bit-identical.  Allocates and frees its workspace.  Errors: OPF_EINVAL,
  * OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT (a bounded wait of the tcgen05 kernel
  * gave up; the result is void).
  */

@@ -294,7 +294,8 @@ def pivot_reciprocal(u):
 def dense_syrk_emulated(A, c0, K, r0, engine=0):
     """A[r0:, r0:] (lower) -= P P^T, P = A[r0:, c0:c0+K], in place on a column-major n x n
     cuda float64 matrix given as its transpose view (A_t[j] = column j), emulated on tensor cores
-    (engine 0: tcgen05, 1: warp-level mma.sync)."""
+    (engine 0: tcgen05 for large updates and mma.sync for small ones, 1: warp-level mma.sync,
+    2: tcgen05)."""
     import torch
     if A.dtype != torch.float64 or not A.is_cuda or not A.is_contiguous() or A.dim() != 2 or \
             A.shape[0] != A.shape[1]:
@@ -573,7 +574,8 @@ class OPFContext:
 
     def set_update_engine(self, engine):
         """Tensor-core kernel of the emulated Cholesky updates (opf_set_update_engine): 0 tcgen05
-        (the default), 1 warp-level mma.sync."""
+        for large updates and mma.sync for small ones (the default), 1 warp-level mma.sync,
+        2 tcgen05."""
         st = lib().opf_set_update_engine(self.h, int(engine))
         if st != 0:
             raise OPFError(st, "opf_set_update_engine")

@@ -108,8 +108,8 @@ opf_status opf_pivot_reciprocal(void* stream, const double* u, double* r, int n)
 
 opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K, int r0, int engine) {
   if (!A || n < 1 || c0 < 0 || K < 32 || K > 128 || K % 32 != 0 || c0 + K > r0 || r0 >= n || engine < 0 ||
-      engine > 1) {
-    set_last_error("need A, 0 <= c0, c0 + K <= r0 < n, K in {32, 64, 96, 128} and engine 0 or 1");
+      engine > 2) {
+    set_last_error("need A, 0 <= c0, c0 + K <= r0 < n, K in {32, 64, 96, 128} and engine 0, 1 or 2");
     return OPF_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -136,7 +136,7 @@ opf_status opf_dense_syrk_emulated(void* stream, double* A, int n, int c0, int K
   }
   cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
   OzEngine eng;
-  eng.tcgen05 = engine == 0;
+  eng.engine = engine;
   eng.err = flag + 1;
   eng.sm_count = sms;
   launch_oz_update(st, A, n, c0, K, r0, E, D, flag, eng);

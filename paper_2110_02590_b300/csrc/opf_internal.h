@@ -401,11 +401,14 @@ void launch_lu_dense_cluster(cudaStream_t st, int K, double* LU, const int* dp, 
                              const LuTail& tail);
 
 opf_status setup_oz();
-// Which tensor-core engine runs the emulated update: the tcgen05 kernel (TMEM
+// Which tensor-core engine runs the emulated update: 0 the tcgen05 kernel (TMEM
 // accumulators; its bounded mbarrier waits record a timeout in *err, polling at
-// most lim times) or the warp-level mma.sync kernel.
+// most lim times) for updates of at least OZ_TC_MIN_TILES 128 x 64 tiles and the
+// warp-level mma.sync kernel for smaller ones (whose latency the 128-row tiles
+// do not hide); 1 mma.sync only; 2 tcgen05 only.
+constexpr int OZ_TC_MIN_TILES = 80;
 struct OzEngine {
-  bool tcgen05 = true;
+  int engine = 0;
   int* err = nullptr;
   long long lim = 1ll << 24;
   int sm_count = 148;
@@ -513,7 +516,7 @@ struct opf_ctx {
   opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
   int tuned_k = 0, tuned_threads = 0;  // opf_hessian_autotune's choice (0 = none)
   int chol_mode = 1;               // dense Cholesky trailing updates (opf_set_cholesky_mode)
-  int oz_engine = 0;               // emulated updates: 0 tcgen05, 1 warp-level mma.sync (opf_set_update_engine)
+  int oz_engine = 0;               // emulated updates: 0 tcgen05 for large ones, 1 mma.sync, 2 tcgen05 (opf_set_update_engine)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;
   cudaStream_t cap_stream = nullptr;

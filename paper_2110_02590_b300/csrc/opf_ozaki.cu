@@ -711,8 +711,13 @@ void launch_oz_syrk_tc(cudaStream_t st, double* A, int n, int K, int r0, const i
 
 void launch_oz_update(cudaStream_t st, double* A, int n, int c0, int K, int r0, int* E, void* D, const int* flag,
                       const OzEngine& eng) {
-  launch_oz_slice(st, A, n, c0, K, r0, E, D, flag, eng.tcgen05);
-  if (eng.tcgen05)
+  const int M = n - r0;
+  const int nrt = (M + TC_M - 1) / TC_M, nct = (M + TC_N - 1) / TC_N;
+  int ntiles = 0;
+  for (int bi = 0; bi < nrt; bi++) ntiles += std::min(2 * bi + 2, nct);
+  const bool tc = eng.engine == 2 || (eng.engine == 0 && ntiles >= OZ_TC_MIN_TILES);
+  launch_oz_slice(st, A, n, c0, K, r0, E, D, flag, tc);
+  if (tc)
     launch_oz_syrk_tc(st, A, n, K, r0, E, D, flag, eng.err, eng.lim, eng.sm_count);
   else
     launch_oz_syrk(st, A, n, K, r0, E, D, flag, 0, 0);

@@ -780,7 +780,7 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag,
     if (c1 < n) {
       if (emulate) {
         OzEngine eng;
-        eng.tcgen05 = c->oz_engine == 0;
+        eng.engine = c->oz_engine;
         eng.err = w->oz_err;
         eng.lim = c->wait_limit > 0 ? (long long)c->wait_limit : (1ll << 24);
         eng.sm_count = c->sm_count;
@@ -1519,8 +1519,8 @@ extern "C" opf_status opf_set_cholesky_mode(opf_ctx* c, int mode) {
 }
 
 extern "C" opf_status opf_set_update_engine(opf_ctx* c, int engine) {
-  if (!c || engine < 0 || engine > 1) {
-    set_last_error("ctx is required and engine must be 0 (tcgen05) or 1 (mma.sync)");
+  if (!c || engine < 0 || engine > 2) {
+    set_last_error("ctx is required and engine must be 0 (tcgen05 for large updates), 1 (mma.sync) or 2 (tcgen05)");
     return OPF_EINVAL;
   }
   c->oz_engine = engine;

@@ -90,15 +90,15 @@ def test_al_step_cholesky_modes(mode):
 
 @pytest.mark.parametrize("name", ["medium1400", "large9200"])
 def test_al_step_update_engines_identical(name):
-    """The step with the emulated Cholesky updates on tcgen05 (the default) and on warp-level
-    mma.sync.  The two engines produce bit-identical updates (test_gpu_numerics); the rest of a
+    """The step with every emulated Cholesky update on tcgen05 and on warp-level mma.sync (the
+    default takes tcgen05 for the large updates only).  The two engines produce bit-identical updates (test_gpu_numerics); the rest of a
     step is not bit-reproducible from run to run (scalar reductions use atomics), so the steps
     agree to 1e-12 with the same inertia corrections."""
     net = synth.workload(name)
     on, x, u, al, st = setup(net, mu=0.1)
     al_dev = {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
     out = []
-    for engine in (0, 1):
+    for engine in (2, 1):
         ctx = P.OPFContext(net)
         ctx.set_update_engine(engine)
         xg, _ = ctx.powerflow(dev(u))
@@ -111,7 +111,7 @@ def test_al_step_update_engines_identical(name):
     assert d0 == d1 and t0 == t1
     assert rel(du0, du1) < 1e-12 and rel(ds0, ds1) < 1e-12 and rel(u0, u1) < 1e-12
     with pytest.raises(P.OPFError):
-        P.OPFContext(synth.workload("tiny30")).set_update_engine(2)
+        P.OPFContext(synth.workload("tiny30")).set_update_engine(3)
 
 
 def test_al_step_requires_state():

@@ -69,7 +69,7 @@ def test_pivot_reciprocal_zero_and_subnormal_give_nan():
     assert np.all(np.isnan(r)), r
 
 
-@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("engine", [0, 1, 2])
 @pytest.mark.parametrize("K,decades", [(128, 9), (64, 9), (128, 0)])
 def test_emulated_rank_k_update_error_bound(K, decades, engine):
     rng = np.random.default_rng(5 + K + decades)
@@ -104,19 +104,20 @@ def test_emulated_rank_k_update_error_bound(K, decades, engine):
 @pytest.mark.parametrize("M,K,c0", [(2771, 128, 0), (300, 96, 8), (129, 32, 0), (64, 64, 40), (1, 128, 0)])
 def test_emulated_update_engines_bit_identical(M, K, c0):
     """The tcgen05 kernel (level sums in tensor memory) and the warp-level mma.sync kernel add
-    the same exact integer digit products and fold them the same way: the updated triangles
-    are equal bit for bit, on ragged sizes (partial 128 x 64 and 64 x 64 tiles) and the
-    largest update of the 9.2k-bus grid's Schur complement (2,771 rows)."""
+    the same exact integer digit products and round them the same way (the tcgen05 epilogue
+    in integer arithmetic): the updated triangles are equal bit for bit, on ragged sizes
+    (partial 128 x 64 and 64 x 64 tiles) and the largest update of the 9.2k-bus grid's Schur
+    complement (2,771 rows)."""
     rng = np.random.default_rng(M + K)
     r0 = c0 + K
     n = r0 + M
     A = rng.standard_normal((n, n)) * 10.0 ** rng.uniform(-6, 3, (n, 1))
     outs = []
-    for engine in (0, 1):
+    for engine in (2, 1, 0):  # tcgen05, mma.sync, and the size-based choice between them
         At = torch.as_tensor(np.ascontiguousarray(A.T), device=DEV)
         P.dense_syrk_emulated(At, c0, K, r0, engine=engine)
         outs.append(At.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     # and it is the update: the lower triangle changed, everything else did not
     low = np.tril(np.ones((M, M), dtype=bool))
     got = outs[0].T
