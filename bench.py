@@ -303,6 +303,103 @@ def hvp_flops_per_column(sym, nx, nl):
     return 6 * nnz_strict + 2 * nx + 32 * nl
 
 
+def symmetric_lt_entries(net, sym, nu, k, sm_count):
+    """L^T-sweep work of a full Hessian built by its symmetry (opf_set_hessian_symmetry, the
+    library's default): the tile whose columns start at position p of the column order (v_ref,
+    then (v, p) of the PV buses in the elimination-tree postorder of their theta rows) sweeps the
+    bus blocks holding an elimination-tree ancestor of the right-hand-side rows of a control at
+    a position >= p.  Replicates the library's order and its split tiling (waves of k-wide tiles,
+    then k/2-wide ones; plain k-wide chunks when that tiling does not apply).  Returns (sum over
+    columns of the strictly triangular L^T entries swept, sum over tiles of the entries swept (the
+    factor entries each tile reads), sum over columns of the rows swept)."""
+    rp, ci, perm = sym["rowptr"], sym["colidx"], sym["perm"]
+    nx = len(perm)
+    pos = np.empty(nx, np.int64)
+    pos[perm] = np.arange(nx)
+    parent = np.full(nx, -1, np.int64)
+    colcnt = np.zeros(nx, np.int64)
+    for i in range(nx):
+        cols = ci[rp[i]:rp[i + 1]]
+        cols = cols[cols < i]
+        colcnt[cols] += 1
+        for j in cols:
+            if parent[j] < 0 or i < parent[j]:
+                parent[j] = i
+    nb, ref = net.n_bus, int(net.ref_bus)
+    typ = np.zeros(nb, int)
+    typ[np.asarray(net.gen_bus, int)] = 1
+    typ[ref] = 2
+    pv = [b for b in range(nb) if typ[b] == 1]
+    pq = [b for b in range(nb) if typ[b] == 0]
+    xs = pv + pq
+    pth = {b: int(pos[q]) for q, b in enumerate(xs)}
+    pvv = {b: int(pos[len(xs) + q]) for q, b in enumerate(pq)}
+    rowbus = np.empty(nx, np.int64)
+    for b, r in pth.items():
+        rowbus[r] = b
+    for b, r in pvv.items():
+        rowbus[r] = b
+    kids = [[] for _ in range(nx)]
+    for j in range(nx):
+        if parent[j] >= 0:
+            kids[parent[j]].append(j)
+    post, cnt = np.zeros(nx, np.int64), 0
+    for r in range(nx - 1, -1, -1):
+        if parent[r] >= 0:
+            continue
+        stack = [[r, 0]]
+        while stack:
+            v, c = stack[-1]
+            if c < len(kids[v]):
+                stack[-1][1] += 1
+                stack.append([kids[v][c], 0])
+            else:
+                post[v] = cnt
+                cnt += 1
+                stack.pop()
+    adj = [[] for _ in range(nb)]
+    for f, t in zip(net.br_from, net.br_to):
+        adj[int(f)].append(int(t))
+        adj[int(t)].append(int(f))
+    cols = [("v", ref)] + [c for b in sorted(pv, key=lambda b: post[pth[b]]) for c in (("v", b), ("p", b))]
+    assert len(cols) == nu
+    qrow = np.full(nx, -1, np.int64)
+    for q in range(nu - 1, -1, -1):
+        kind, b = cols[q]
+        rows = [pth[b]] if kind == "p" else \
+            [pth[o] for o in adj[b] if typ[o] != 2] + [pvv[o] for o in adj[b] if typ[o] == 0] + \
+            ([pth[b]] if typ[b] == 1 else [])
+        for r in rows:
+            x = r
+            while x >= 0 and qrow[x] < 0:
+                qrow[x] = q
+                x = parent[x]
+    # block marks: the largest mark of the block's rows (a block is swept whole)
+    bmark = np.full(nb, -1, np.int64)
+    np.maximum.at(bmark, rowbus, qrow)
+    rmark = bmark[rowbus]
+    order = np.argsort(-rmark, kind="stable")
+    csum_e = np.concatenate([[0], np.cumsum(colcnt[order])])
+    marks_desc = rmark[order]
+    # tiles: (first position, width)
+    waves = nu // (k * sm_count)
+    n1 = waves * sm_count
+    rem = nu - n1 * k
+    n2 = -(-rem // (k // 2)) if k >= 2 else 0
+    if k >= 2 and waves >= 1 and rem > 0 and n2 <= sm_count:
+        tiles = [(t * k, k) for t in range(n1)] + \
+            [(n1 * k + t * (k // 2), min(k // 2, nu - n1 * k - t * (k // 2))) for t in range(n2)]
+    else:
+        tiles = [(t * k, min(k, nu - t * k)) for t in range(-(-nu // k))]
+    ent = ent_tiles = rows_swept = 0
+    for p, w in tiles:
+        kept = int(np.searchsorted(-marks_desc, -p, side="right"))  # rows with mark >= p
+        ent += w * int(csum_e[kept])
+        ent_tiles += int(csum_e[kept])
+        rows_swept += w * kept
+    return ent, ent_tiles, rows_swept
+
+
 def hbm_bytes_per_hessian(sym, nx, nu, k):
     """Factor-plus-RHS bytes of a block of k directions, 24 nnz(L+U) + 64 n_x k, over all blocks."""
     nnz_lu = len(sym["colidx"]) - nx
@@ -310,18 +407,24 @@ def hbm_bytes_per_hessian(sym, nx, nu, k):
     return blocks * (24 * nnz_lu + 64 * nx * k)
 
 
-def solve_phase(sym, nx, nu, k, hvp_ms, share, hbm_peak, fp64_tf):
-    """Roofline of the triangular-solve phase of the HVP kernel: the three full sweeps (U for Z;
-    U^T, L^T for Psi) over the kernel time apportioned to them by the tiles' phase stamps.  Bytes:
+def solve_phase(sym, nx, nu, k, hvp_ms, share, hbm_peak, fp64_tf, lt=None):
+    """Roofline of the triangular-solve phase of the HVP kernel: the U sweep for Z and the U^T,
+    L^T sweeps for Psi over the kernel time apportioned to them by the tiles' phase stamps.  Bytes:
     12 B per factor entry each sweep reads (value + column index) and 16 n_x k (read + write of the
     right-hand side) per sweep and block of k directions; flops: 2 per strictly triangular entry
-    and direction, plus the diagonal scaling of U and U^T.  The pruned first L solve is left out
-    of time, bytes and flops alike."""
+    and direction, plus the diagonal scaling of U and U^T.  With lt (symmetric Hessian,
+    symmetric_lt_entries) the L^T sweep counts the entries and rows it sweeps.  The pruned first L
+    solve is left out of time, bytes and flops alike."""
     nnz_strict = (len(sym["colidx"]) - nx) // 2
     blocks = -(-nu // k)
     t_ms = hvp_ms * (share[1] + share[3])
-    byts = blocks * (12 * (3 * nnz_strict + 2 * nx) + 3 * 16 * nx * k)
-    flops = nu * (6 * nnz_strict + 2 * nx)
+    if lt is None:
+        byts = blocks * (12 * (3 * nnz_strict + 2 * nx) + 3 * 16 * nx * k)
+        flops = nu * (6 * nnz_strict + 2 * nx)
+    else:
+        ent, ent_t, rows_sw = lt
+        byts = blocks * (12 * (2 * nnz_strict + 2 * nx) + 2 * 16 * nx * k) + 12 * ent_t + 16 * rows_sw
+        flops = nu * (4 * nnz_strict + 2 * nx) + 2 * ent
     gbs = byts / (t_ms * 1e-3) / 1e9
     tfs = flops / (t_ms * 1e-3) / 1e12
     return {"ms": t_ms, "bytes": byts, "flops": flops, "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
@@ -680,9 +783,19 @@ def run_gpu(args):
     hvp_ms = statistics.median(h[1] for h in hs)
     # the HVP time by tile phase (one extra call with per-tile timer stamps), and the asymmetry
     flush.zero_()
-    _, prof = ctx.reduced_hessian(alh, phase_profile=True, asymmetry=True)
+    _, prof = ctx.reduced_hessian(alh, phase_profile=True)
     ph = prof["phase_ms"]
     share = [v / max(sum(ph), 1e-30) for v in ph]
+    # every column in full (no symmetry; the asymmetry report needs that form)
+    ctx.set_hessian_symmetry(False)
+    hf = []
+    for r in range(3):
+        flush.zero_()
+        _, finfo = ctx.reduced_hessian(alh)
+        hf.append((finfo["ms_total"], finfo["ms_hvp"]))
+    flush.zero_()
+    _, prof_full = ctx.reduced_hessian(alh, asymmetry=True)
+    ctx.set_hessian_symmetry(True)
     # plain form (k = 1, one direction per launch sequence: device-wide kernels around two
     # streamed single-RHS solves) on a column sample from the middle of the controls
     pc = max(1, min(args.plain_cols, nu))
@@ -693,11 +806,15 @@ def run_gpu(args):
 
     jac = None if args.no_extras else reduced_jacobian_leg(ctx, alh, flush, hess_ms)
 
-    flops = hvp_flops_per_column(sym, nx, net.n_branch) * nu
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    lt = symmetric_lt_entries(net, sym, nu, tune["block_k"], sm_count)
+    nnz_strict = (len(sym["colidx"]) - nx) // 2
+    flops_full = hvp_flops_per_column(sym, nx, net.n_branch) * nu
+    flops = flops_full - 2 * (nu * nnz_strict - lt[0])  # the L^T entries the symmetric tiles skip
     achieved_tf = flops / (hvp_ms * 1e-3) / 1e12
     hbm_peak, hbm_kind = peaks()
     hbm_b = hbm_bytes_per_hessian(sym, nx, nu, tune["block_k"])
-    solve = solve_phase(sym, nx, nu, tune["block_k"], hvp_ms, share, hbm_peak, fp64_tf)
+    solve = solve_phase(sym, nx, nu, tune["block_k"], hvp_ms, share, hbm_peak, fp64_tf, lt=lt)
     traffic, traffic_note = profiled_traffic()
     auto = None if args.no_autograd else autograd_batch(P, torch, dev, args.autograd_scenarios)
 
@@ -778,7 +895,14 @@ def run_gpu(args):
         "step_detail": {"pf_iterations": statistics.median(i[0]["iterations"] for i in infos),
                         "inertia_delta": statistics.median(i["delta"] for i in sinfos),
                         "halvings": sum(i["halvings"] for i in sinfos)},
-        "hessian_asymmetry": prof["asymmetry"],
+        "hessian_asymmetry": prof_full["asymmetry"],
+        "hessian_symmetry": {
+            "form": "default: each tile keeps the rows of the controls from its first column position on "
+                    "(its L^T sweep pruned to their Psi rows), a mirror kernel completes H",
+            "lt_entries_swept_frac": lt[0] / (nu * nnz_strict),
+            "ms_per_hessian_full_columns": statistics.median(h[0] for h in hf),
+            "ms_hvp_phase_full_columns": statistics.median(h[1] for h in hf),
+            "flops_per_launch_full_columns": flops_full},
         "plain": {"ms_per_hvp": plain_ms_per_col, "hvps_per_s": 1e3 / plain_ms_per_col,
                   "ms_per_hessian_extrapolated": plain_ms_per_col * nu, "columns_timed": pc,
                   "form": "one direction per launch sequence: 9 device-wide kernels per column around two "
@@ -795,6 +919,8 @@ def run_gpu(args):
                      "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": ("hvp_split_kernel" if (tune["block_k"], tune["threads"]) == (8, 256)
                                 else "hvp_tile_kernel"), "flops_per_launch": flops,
+                     "flops_note": "6 nnz(L strict) + 2 n_x + 32 n_l per column, less the L^T entries the "
+                                   "symmetric tiles skip (hessian_symmetry.lt_entries_swept_frac)",
                      "peak_note": "FP64 FMA rate of this GPU measured in this run (opf_fp64_peak: "
                                   f"{fp64_ms:.3f} ms probe); nominal 1.25 TFLOP/s",
                      "hbm": {"bytes_per_hessian": hbm_b, "achieved_gbs": hbm_b / (hvp_ms * 1e-3) / 1e9,

@@ -584,6 +584,22 @@ opf_status opf_set_update_engine(opf_ctx* ctx, int engine);
 opf_status opf_set_wait_limit(opf_ctx* ctx, int spins);
 
 /*
+ * opf_set_hessian_symmetry: whether a full reduced Hessian (opf_reduced_hessian
+ * over all columns, tiled, without the asymmetry report; also inside
+ * opf_al_step and opf_tracking_update) is built by its symmetry (on = 1, the
+ * default) or column by column in full (on = 0).  With symmetry, the tile of
+ * columns [p, p + k) in the tiling's column order (the elimination-tree order
+ * of the controls) keeps only the rows of the controls at positions >= p: its
+ * second adjoint Psi is needed on the elimination-tree ancestors of those
+ * controls' right-hand-side rows only, so its L^T sweep skips the other rows
+ * (on the 9.2k-bus grid 43% of that sweep's entries), and a mirror kernel
+ * fills the remaining entries from their transposes.  The result equals the
+ * full computation up to rounding (each entry is one of the two computed
+ * values of the symmetric pair).  Errors: OPF_EINVAL.
+ */
+opf_status opf_set_hessian_symmetry(opf_ctx* ctx, int on);
+
+/*
  * Measurement and verification entry points (no context; ordered on `stream`,
  * a cudaStream_t, NULL = legacy default stream; each call synchronises it).
  *

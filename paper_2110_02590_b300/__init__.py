@@ -166,6 +166,7 @@ def lib():
         L.opf_gradient_scaling.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.POINTER(C.c_double)]
         L.opf_set_wait_limit.argtypes = [C.c_void_p, C.c_int]
+        L.opf_set_hessian_symmetry.argtypes = [C.c_void_p, C.c_int]
         L.opf_tracking_update.argtypes = [C.c_void_p, C.POINTER(AlParams), C.c_void_p, C.POINTER(AlState),
                                           C.POINTER(QpOpts), C.POINTER(QpInfo)]
         L.opf_al_step_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(AlParams), C.POINTER(AlState),
@@ -506,6 +507,13 @@ class OPFContext:
         st = lib().opf_set_wait_limit(self.h, int(spins))
         if st != 0:
             raise OPFError(st, "opf_set_wait_limit")
+
+    def set_hessian_symmetry(self, on: bool) -> None:
+        """Full Hessians by their symmetry (opf_set_hessian_symmetry; on by default)."""
+        self._sync_stream()
+        st = lib().opf_set_hessian_symmetry(self.h, int(bool(on)))
+        if st != 0:
+            raise OPFError(st, "opf_set_hessian_symmetry")
 
     def launch_count(self) -> int:
         v = C.c_longlong()

@@ -503,6 +503,46 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
       }
       if (h.type[k] == opf::PV) out.push_back(pth[k]);
     };
+    // symmetric full Hessian: the position of each control in this order; per
+    // pivot row the last position whose right-hand side reaches it (controls
+    // taken from the last, so the first mark of a row is its largest; a walk
+    // stops at a marked row, whose ancestors carry larger marks already); the
+    // L^T sweep's backward levels with each level's blocks by descending mark
+    // (stable: equal marks keep the longest-first order)
+    {
+      std::vector<int> qpos(h.nu, 0), qrow(nx, -1), rr;
+      for (int q = 0; q < h.nu; q++) qpos[perm_cols[q]] = q;
+      for (int q = h.nu - 1; q >= 0; q--) {
+        rr.clear();
+        rhs_rows(perm_cols[q], rr);
+        for (int r : rr)
+          for (int x = r; x >= 0 && qrow[x] < 0; x = par[x]) qrow[x] = q;
+      }
+      std::vector<int4> meta_lt(bmeta_b.size());
+      std::vector<int> q_lt(bmeta_b.size());
+      std::vector<std::pair<int, int>> ord;
+      for (size_t l = 0; l + 1 < bsched_ptr_b.size(); l++) {
+        ord.clear();
+        for (int k = bsched_ptr_b[l]; k < bsched_ptr_b[l + 1]; k++) {
+          const int4 m = bmeta_b[k];
+          ord.push_back({m.w != 0 ? std::max(qrow[m.x], qrow[m.x - 1]) : qrow[m.x], k});
+        }
+        std::stable_sort(ord.begin(), ord.end(),
+                         [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first > b.first; });
+        for (size_t i = 0; i < ord.size(); i++) {
+          meta_lt[bsched_ptr_b[l] + i] = bmeta_b[ord[i].second];
+          q_lt[bsched_ptr_b[l] + i] = ord[i].first;
+        }
+      }
+      int4* q4p = nullptr;
+      TRY(dupload(c, &q4p, meta_lt));
+      n.bmeta_lt = q4p;
+      TRY(dupload(c, &ip, q_lt));
+      n.lt_q = ip;
+      TRY(dupload(c, &ip, qpos));
+      n.qpos = ip;
+      TRY(dalloc(c, &c->tstart, h.nu));
+    }
     // per block width: near-equal chunks of the order (as many tiles as a whole
     // number of waves over the SMs when that keeps tiles at least half full),
     // heaviest first by the reach of their first solve
@@ -1010,6 +1050,11 @@ static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hes
   int launches = 0;
   c->jac_out = J;
   c->jac_only = jac_only;
+  const bool asym = info && o && o->asymmetry && col0 == 0 && ncol == nu && !jac_only;
+  // the full Hessian by its symmetry: each tile keeps the rows at or after its
+  // first column position, the mirror kernel completes H
+  const bool sym = c->hess_sym && !plain && col0 == 0 && ncol == nu && !asym && !jac_only;
+  c->sym_now = sym;
   if (plain) {
     launches = launch_hvp_plain(c, H, col0, col0 + ncol, c->scratch);
   } else if (split) {
@@ -1019,6 +1064,11 @@ static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hes
     launch_hvp(c, C, H, grid, 0, 1, ntiles, col0, col0 + ncol);
     launches = 1;
   }
+  if (sym) {
+    launch_hess_mirror(c, H, nu);
+    launches++;
+  }
+  c->sym_now = false;
   CK(cudaEventRecord(c->ev[2], st));
   c->stamps_on = false;
   c->jac_out = nullptr;
@@ -1029,7 +1079,6 @@ static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hes
     CK(cudaMemcpyAsync(stamps.data(), c->stamps, sizeof(unsigned long long) * stamps.size(),
                        cudaMemcpyDeviceToHost, st));
   }
-  const bool asym = info && o && o->asymmetry && col0 == 0 && ncol == nu && !jac_only;
   if (asym) {  // after the timed region
     CK(cudaMemsetAsync(c->scal + 4, 0, 2 * sizeof(double), st));
     launch_hess_asymmetry(c, H, nu, c->scal + 4);
@@ -1266,6 +1315,12 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     cudaEventElapsedTime(&info->ms_total, c0->ev[0], c0->ev[2]);
     cudaEventElapsedTime(&info->ms_hvp, c0->ev[1], c0->ev[2]);
   }
+  return OPF_OK;
+}
+
+opf_status opf_set_hessian_symmetry(opf_ctx* c, int on) {
+  if (!c) FAIL(OPF_EINVAL, "ctx is required");
+  c->hess_sym = on != 0;
   return OPF_OK;
 }
 

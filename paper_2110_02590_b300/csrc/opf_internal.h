@@ -84,6 +84,15 @@ struct DevNet {
   const int *bptr_f, *bptr_b;
   const int4 *bmeta_f, *bmeta_b;
   int nblev_f, nblev_b;
+  // the backward levels again for the L^T sweep of a symmetric Hessian tile:
+  // each level's blocks by descending lt_q (then length), where lt_q of a block
+  // is the last position, in the full-Hessian column order, of a control whose
+  // right-hand-side rows have one of the block's rows as an elimination-tree
+  // ancestor; a tile whose first column position is p needs Psi exactly on the
+  // blocks with lt_q >= p, a prefix of every level (qpos: the position of each
+  // control in that order)
+  const int4* bmeta_lt;
+  const int *lt_q, *qpos;
   int r0, nroot;
   const int* slot_self;            // [4 * nb]: P-theta, P-v, Q-theta, Q-v
   const int* slot_adj;             // [4 * 2 nl]
@@ -117,6 +126,12 @@ struct HvpArgs {
   // dynamic shared memory of the tile (hvp_smem_bytes): reached-row values
   // [zs_cap][C], reach mask and its word prefix [rm_words] each, reach list [list_cap]
   int zs_cap, rm_words, list_cap;
+  // symmetric full Hessian: a tile computes only the rows of the controls at or
+  // after its first column position (pruning the L^T sweep to their Psi rows)
+  // and records that position per column in tstart; a mirror kernel fills the
+  // rest from the transposed entries
+  int sym;
+  int* tstart;
 };
 
 // Shared memory of the trailing dense block's LU (the whole block; larger blocks
@@ -150,6 +165,7 @@ void launch_hess_prep(opf_ctx* c, double sigma_f);
 size_t hvp_stride(const opf_ctx* c, int C);
 // sums[0] += ||H - H^T||_F^2, sums[1] += ||H||_F^2 (H: n x n column-major)
 void launch_hess_asymmetry(opf_ctx* c, const double* H, int n, double* sums);
+void launch_hess_mirror(opf_ctx* c, double* H, int n);  // completes a symmetric Hessian (HvpArgs::sym)
 bool launch_hvp(opf_ctx* c, int C, double* H, int grid, int first_tile, int tile_step, int ntiles,
                 int col0, int col_end);
 bool launch_hvp_scratch(opf_ctx* c, int C, double* H, double* scratch, int grid, int ntiles, int col0,
@@ -478,6 +494,7 @@ struct opf_ctx {
   int* colmap_split[6] = {};
   int split_n1[6] = {}, split_n2[6] = {};
   int* split_ctr = nullptr;  // the split launch's tile queues and per-SM CTA counts (2 + kSplitMaxSm)
+  int* tstart = nullptr;     // [n_u] first column position of each column's tile (symmetric Hessian)
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;
   double* scal = nullptr;         // [8] reductions: |g|^2, |g|_inf bits, F, ...
@@ -516,6 +533,8 @@ struct opf_ctx {
   opf::StepWork* stepw = nullptr;  // reduced-Newton step workspace (first opf_al_step)
   int tuned_k = 0, tuned_threads = 0;  // opf_hessian_autotune's choice (0 = none)
   int chol_mode = 1;               // dense Cholesky trailing updates (opf_set_cholesky_mode)
+  bool hess_sym = true;            // full Hessians by symmetry (opf_set_hessian_symmetry)
+  bool sym_now = false;            // set for the duration of one such launch
   int oz_engine = 0;               // emulated updates: 0 tcgen05 for large ones, 1 mma.sync, 2 tcgen05 (opf_set_update_engine)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;

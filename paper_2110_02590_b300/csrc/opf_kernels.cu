@@ -484,11 +484,14 @@ __device__ __forceinline__ void tri_regs(const DevNet& n, const double* __restri
 // known every thread updates its (row, column) items below (FWD) or above it.
 // DIAG: multiply each row by 1/U_ii once its sum is complete.  rmask (FWD
 // only): the rows below r0 are already final and the slab is zero outside the
-// rows set in the mask; only the trailing block remains.
+// rows set in the mask; only the trailing block remains.  lcnt (backward only):
+// run the levels of the L^T ordering (DevNet::bmeta_lt), only the first
+// lcnt[lv] blocks of level lv.
 template <int C, bool FWD, bool DIAG>
 __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
                                       const double* __restrict__ invdiag, double* X,
-                                      const unsigned* rmask = nullptr, double* tb = nullptr) {
+                                      const unsigned* rmask = nullptr, double* tb = nullptr,
+                                      const int* lcnt = nullptr) {
   constexpr int RPW = 32 / C;
   constexpr int TRI_MR = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -519,7 +522,7 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
   // levels of bus blocks (one or two pivot rows each, see DevNet::bmeta_f)
   const int nlev = (FWD && rmask) ? 0 : (FWD ? n.nblev_f : n.nblev_b);
   const int* lptr = FWD ? n.bptr_f : n.bptr_b;
-  const int4* lmeta = FWD ? n.bmeta_f : n.bmeta_b;
+  const int4* lmeta = FWD ? n.bmeta_f : (lcnt ? n.bmeta_lt : n.bmeta_b);
   const int nwarps = blockDim.x >> 5, grp = lane / C;
   // the block's other row and its coupling entry (the diagonal block's off-diagonal)
   auto other_of = [](const int4& m) { return FWD ? m.x + 1 : m.x - 1; };
@@ -528,13 +531,16 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
   // groups split the entries; else one lane group per block
   auto first_k = [&](int b, int e) { return (e - b <= nwarps && RPW > 1) ? b + warp : b + myslot; };
   const int4 none = make_int4(0, 0, 0, 0);
-  int b = nlev > 0 ? lptr[0] : 0, e = nlev > 0 ? lptr[1] : 0;
+  // level lv: blocks [b, e) of [b, ef) (e < ef: a prefix, with lcnt)
+  int b = nlev > 0 ? lptr[0] : 0, ef = nlev > 0 ? lptr[1] : 0;
+  int e = (lcnt && nlev > 0) ? b + lcnt[0] : ef;
   int k0 = first_k(b, e);
   int4 mt = k0 < e ? __ldg(lmeta + k0) : none;
   for (int lv = 0; lv < nlev; lv++) {
     // the next level's bounds and this thread's first record of it do not
     // depend on the slab: load them before this level's work
-    const int bn = e, en = (lv + 1 < nlev) ? lptr[lv + 2] : e;
+    const int bn = ef, efn = (lv + 1 < nlev) ? lptr[lv + 2] : ef;
+    const int en = (lcnt && lv + 1 < nlev) ? bn + lcnt[lv + 1] : efn;
     const int kn0 = first_k(bn, en);
     const int4 mtn = kn0 < en ? __ldg(lmeta + kn0) : none;
     if (e - b <= nwarps && RPW > 1) {
@@ -615,6 +621,7 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
     __syncthreads();
     b = bn;
     e = en;
+    ef = efn;
     k0 = kn0;
     mt = mtn;
   }
@@ -1260,6 +1267,7 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
   double* s_tb = a.zs_cap >= n.nroot ? s_zs : nullptr;
   __shared__ int s_col[32];
   __shared__ int s_nl;
+  __shared__ int s_qstart;
   __shared__ double s_part[2][16][32];  // per-warp partial row sums (<= 512 threads)
   const int r0 = n.r0, nwords = (r0 + 31) >> 5;
   const bool prune = nwords <= a.rm_words;
@@ -1577,14 +1585,49 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     }
     __syncthreads();
     hvp_stamp(a, tile, 3);
+    // symmetric Hessian: the tile's first column position qs; the tile keeps the
+    // rows of the controls at positions >= qs, so Psi is needed on the blocks
+    // whose lt_q >= qs only, a prefix of each level of the L^T ordering (its
+    // length by binary search, one level per thread, into the reach prefix
+    // words, free since phase (1))
+    const int* lcnt = nullptr;
+    int qs = 0;
+    if (a.sym) {
+      if (threadIdx.x == 0) {
+        int q = 1 << 30;
+        for (int c = 0; c < C; c++)
+          if (s_col[c] >= 0) q = min(q, n.qpos[s_col[c]]);
+        s_qstart = q;
+      }
+      __syncthreads();
+      qs = s_qstart;
+      if (n.nblev_b <= a.rm_words) {
+        for (int lv = threadIdx.x; lv < n.nblev_b; lv += blockDim.x) {
+          const int base = n.bptr_b[lv];
+          int lo = base, hi = n.bptr_b[lv + 1];
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(n.lt_q + mid) >= qs)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          s_pre[lv] = lo - base;
+        }
+        lcnt = s_pre;  // read after the U^T sweep's barriers
+      }
+      if ((int)threadIdx.x < C && s_col[threadIdx.x] >= 0) a.tstart[s_col[threadIdx.x]] = qs;
+    }
     // (5)-(6) second second-order adjoint: U^T then L^T sweeps
     sweep<C, true, true>(n, a.T, a.invdiag, R, nullptr, s_tb);
-    sweep<C, false, false>(n, a.T, a.invdiag, R, nullptr, s_tb);
+    sweep<C, false, false>(n, a.T, a.invdiag, R, nullptr, s_tb, lcnt);
     hvp_stamp(a, tile, 4);
     // (7) H[:, tile] += G_u^T Psi (buses by descending degree)
     for (int it = threadIdx.x; it < n.ngn * C; it += blockDim.x) {
       const int gi = n.gn_by_deg[it / C], c = it % C, k = n.gn_bus[gi], j = s_col[c];
       if (j < 0) continue;
+      const int4 bk = n.busrec[k];
+      if (a.sym && n.qpos[-2 - bk.x] < qs && (bk.w < 0 || n.qpos[bk.w] < qs)) continue;  // rows mirrored
       double gv = 0.0;
       const int q1 = n.adj_ptr[k + 1];
       int qb = n.adj_ptr[k];
@@ -1595,7 +1638,6 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       }
       if (qb < q1) gu_ends<C, 1>(n, R, E, qb, c, gv);
       double* Hc = a.H + (size_t)j * nu;
-      const int4 bk = n.busrec[k];
       if (bk.w >= 0) {  // PV bus
         const double psi = R[(size_t)bk.y * C + c];
         gv += psi * bw[6 * nb + k];
@@ -2124,6 +2166,8 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   a.tile_step = 1;
   a.col0 = col0;
   a.col_end = col_end;
+  a.sym = (full && c->sym_now) ? 1 : 0;
+  a.tstart = c->tstart;
   // shared-memory layout of the first solve's reach (no pruning when the mask
   // and list would take more than half of the budget)
   const int nwords = (c->dn.r0 + 31) / 32;
@@ -2305,6 +2349,35 @@ __global__ void __launch_bounds__(256) hess_asym_kernel(const double* __restrict
 void launch_hess_asymmetry(opf_ctx* c, const double* H, int n, double* sums) {
   const int nb = (n + 31) / 32;
   hess_asym_kernel<<<dim3(nb, nb), 256, 0, c->stream>>>(H, n, sums);
+  c->launches++;
+}
+
+// Completion of a symmetric Hessian (HvpArgs::sym): the tile of column j kept
+// the rows i with qpos[i] >= tstart[j]; the others take H(j, i), which the tile
+// of column i kept (qpos[i] < tstart[j] <= qpos[j] and tstart[i] <= qpos[i]).
+// One 32 x 32 tile per CTA, its mirror read through shared memory so both the
+// loads and the stores coalesce (column-major H, leading dimension n).
+__global__ void __launch_bounds__(256) hess_mirror_kernel(double* H, int n, const int* __restrict__ qpos,
+                                                          const int* __restrict__ tstart) {
+  __shared__ double B[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {  // B[r][tx] = H(bj*32 + tx, bi*32 + r)
+    const int i2 = bj * 32 + tx, j2 = bi * 32 + r;
+    B[r][tx] = (i2 < n && j2 < n) ? H[(size_t)j2 * n + i2] : 0.0;
+  }
+  __syncthreads();
+  const int i = bi * 32 + tx;
+  if (i >= n) return;
+  const int qi = qpos[i];
+  for (int r = ty; r < 32; r += 8) {
+    const int j = bj * 32 + r;
+    if (j < n && qi < tstart[j]) H[(size_t)j * n + i] = B[tx][r];  // H(i, j) = H(j, i)
+  }
+}
+
+void launch_hess_mirror(opf_ctx* c, double* H, int n) {
+  const int nb = (n + 31) / 32;
+  hess_mirror_kernel<<<dim3(nb, nb), 256, 0, c->stream>>>(H, n, c->dn.qpos, c->tstart);
   c->launches++;
 }
 

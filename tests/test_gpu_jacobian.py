@@ -86,7 +86,7 @@ def test_jacobian_large_sampled_columns():
     c = case("large9200")
     nu = c.on.nu
     J, H, info = c.ctx.reduced_jacobian(c.al_dev, hessian=True, block_k=8)
-    assert info["launches"] == 1
+    assert info["launches"] == 2  # the tiles (J beside H), then the Hessian's mirror
     cols = sorted({0, 1, 7, 8, 9, 100, 1449, 1450, 1451, 2000, nu - 3, nu - 2, nu - 1})
     Jo = scaling.explicit_jacobian(c.on, c.x_orc, c.u, cols=cols)
     Jn = J[:, cols].cpu().numpy()

@@ -182,6 +182,34 @@ def test_hessian_large_sampled_columns():
     assert np.linalg.norm(full - full.T) <= 1e-10 * np.linalg.norm(full)
 
 
+@pytest.mark.parametrize("name,block_k", [("tiny30", 4), ("medium1400", 8), ("batchB2000", 16), ("large9200", 8)])
+def test_hessian_by_symmetry_equals_full(name, block_k):
+    """The full Hessian by its symmetry (the default: a tile keeps the rows of the controls
+    from its first column position on, its L^T sweep pruned to their Psi rows, and a mirror
+    kernel completes H) against every column computed in full: each entry is one of the two
+    computed values of its symmetric pair, so the two agree to rounding; and both match the
+    oracle."""
+    c = case(name)
+    Hs, info_s = c.ctx.reduced_hessian(c.al_dev, block_k=block_k)
+    Hs = Hs.cpu().numpy().copy()
+    c.ctx.set_hessian_symmetry(False)
+    try:
+        Hf, info_f = c.ctx.reduced_hessian(c.al_dev, block_k=block_k)
+    finally:
+        c.ctx.set_hessian_symmetry(True)
+    Hf = Hf.cpu().numpy()
+    assert info_s["launches"] == info_f["launches"] + 1
+    # pairs inside a tile's own columns are both computed (equal to rounding); the rest mirrored
+    assert np.linalg.norm(Hs - Hs.T) <= 1e-13 * np.linalg.norm(Hs)
+    assert np.isfinite(Hs).all()
+    scale = np.abs(Hf).max()
+    assert np.minimum(np.abs(Hs - Hf), np.abs(Hs - Hf.T)).max() <= 1e-12 * scale
+    assert rel_fro(Hs, Hf) < 1e-12
+    if name != "large9200":
+        Ho = c.on.reduced_hessian(c.x_orc, c.u, c.al)
+        assert rel_fro(Hs, Ho) < HESS_TOL
+
+
 def test_hessian_custom_omega():
     """Second-order weights of the Schur complement (Prop. 3) go through the same kernels."""
     net = synth.workload("medium1400")
@@ -271,7 +299,7 @@ def test_hessian_large_launch_forms_agree():
     waves = nu // (8 * sm)
     rem = nu - waves * sm * 8
     if waves >= 1 and 0 < rem and -(-rem // 4) <= sm:
-        assert i0["tiles"] == waves * sm + -(-rem // 4) and i0["launches"] == 1
+        assert i0["tiles"] == waves * sm + -(-rem // 4) and i0["launches"] == 2  # tiles, then the mirror
     H0 = H0.cpu().numpy()
     ref = np.linalg.norm(H0)
     for kw in (dict(block_k=8, grid=sm), dict(block_k=8, threads=512), dict(block_k=4)):
