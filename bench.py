@@ -647,7 +647,7 @@ def batched_snapshots(P, torch, dev, block_k):
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
     bms = statistics.median(ms)
-    out = {"snapshots": len(snaps), "hvps": nhvp, "launches": 1, "tiles": info["tiles"], "grid": info["grid"],
+    out = {"snapshots": len(snaps), "hvps": nhvp, "launches": info["launches"], "tiles": info["tiles"], "grid": info["grid"],
            "ms_batched": bms, "hvps_per_s_batched": nhvp / (bms * 1e-3),
            "ms_per_snapshot_calls": seq_s * 1e3, "hvps_per_s_per_snapshot_calls": nhvp / seq_s}
     out["batched_steps"] = batched_steps(P, torch, dev, snaps)

@@ -1264,7 +1264,9 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     if (!(o && o->reuse_first_order)) launch_first_order(c, &params[k], nullptr);
     launch_hess_prep(c, params[k].sigma_f);
     c->stream = keep;
+    c->sym_now = c->hess_sym;  // each Hessian by its symmetry, mirrored after the launch
     args[k] = make_hvp_args(c, C, H[k], 0, c->h.nu, false);
+    c->sym_now = false;
   }
   // tile queue: contexts by decreasing factor size (longest processing time first)
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -1302,6 +1304,16 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
   for (int k = 0; k < n; k++) smem = std::max(smem, hvp_smem_bytes(args[k], C));
   launch_hvp_batch(st, C, d_args, d_tiles, ntot, d_counter, c0->scratch, stride, grid, smem);
   c0->launches++;
+  int launches = 1;
+  for (int k = 0; k < n; k++) {
+    if (!args[k].sym) continue;
+    opf_ctx* c = ctxs[k];
+    cudaStream_t keep = c->stream;
+    c->stream = st;
+    launch_hess_mirror(c, H[k], c->h.nu);
+    c->stream = keep;
+    launches++;
+  }
   CK(cudaEventRecord(c0->ev[2], st));
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
@@ -1309,7 +1321,7 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
     info->block_k = C;
     info->grid = grid;
     info->tiles = ntot;
-    info->launches = 1;
+    info->launches = launches;
     info->asymmetry = -1.0;
     for (int k = 0; k < 5; k++) info->phase_ms[k] = 0.f;
     cudaEventElapsedTime(&info->ms_total, c0->ev[0], c0->ev[2]);
