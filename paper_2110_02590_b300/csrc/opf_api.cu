@@ -2,6 +2,7 @@
 // gradient and reduced Hessian.  Host orchestration only; all arithmetic of
 // the path runs in the kernels of opf_kernels.cu.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -509,6 +510,8 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
     // stops at a marked row, whose ancestors carry larger marks already); the
     // L^T sweep's backward levels with each level's blocks by descending mark
     // (stable: equal marks keep the longest-first order)
+    std::vector<int> lt_mark;         // block marks, descending
+    std::vector<long long> lt_ent;    // L^T entries of the blocks with the first k marks
     {
       std::vector<int> qpos(h.nu, 0), qrow(nx, -1), rr;
       for (int q = 0; q < h.nu; q++) qpos[perm_cols[q]] = q;
@@ -533,6 +536,18 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
           meta_lt[bsched_ptr_b[l] + i] = bmeta_b[ord[i].second];
           q_lt[bsched_ptr_b[l] + i] = ord[i].first;
         }
+      }
+      std::vector<std::pair<int, long long>> me;
+      for (const int4& m : bmeta_b) {
+        const int q = m.w != 0 ? std::max(qrow[m.x], qrow[m.x - 1]) : qrow[m.x];
+        me.push_back({q, (long long)(m.z - m.y) * (m.w != 0 ? 2 : 1)});
+      }
+      std::sort(me.begin(), me.end(),
+                [](const std::pair<int, long long>& a, const std::pair<int, long long>& b) { return a.first > b.first; });
+      lt_ent.assign(1, 0);
+      for (auto& e : me) {
+        lt_mark.push_back(e.first);
+        lt_ent.push_back(lt_ent.back() + e.second);
       }
       int4* q4p = nullptr;
       TRY(dupload(c, &q4p, meta_lt));
@@ -594,8 +609,13 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
       const int waves = nu / (C * S);
       const int n1 = waves * S, rem = nu - n1 * C, n2 = (rem + C / 2 - 1) / (C / 2);
       if (waves < 1 || rem <= 0 || n2 > S) continue;
-      auto order = [&](int q0, int w, int T) {  // chunks of width w from q0, heaviest reach first
-        std::vector<std::pair<int, int>> cost(T);
+      // chunks of width w from q0, heaviest first by the work that varies between
+      // tiles: the first solve's reach (rows x the mean entries of a row of L)
+      // and the L^T entries a symmetric tile sweeps (the blocks marked at or
+      // after its first position)
+      const double row_ent = (double)(nnz - nx) / (2.0 * nx);
+      auto order = [&](int q0, int w, int T) {
+        std::vector<std::pair<double, int>> cost(T);
         for (int t = 0; t < T; t++) {
           int reach = 0;
           rows.clear();
@@ -606,7 +626,10 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
               stamp[x] = stamp_id;
               reach++;
             }
-          cost[t] = {-reach, t};
+          const int p = q0 + t * w;
+          const size_t kept = std::upper_bound(lt_mark.begin(), lt_mark.end(), p, std::greater<int>()) -
+                              lt_mark.begin();
+          cost[t] = {-(reach * row_ent + (double)lt_ent[kept]), t};
         }
         std::stable_sort(cost.begin(), cost.end());
         std::vector<int> m((size_t)T * w, -1);
@@ -626,7 +649,7 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   }
   TRY(dupload(c, &c->pd_nom, h.pd));
   TRY(dupload(c, &c->qd_nom, h.qd));
-  TRY(dupload(c, &c->split_ctr, std::vector<int>(2 + kSplitMaxSm, 0)));
+  TRY(dupload(c, &c->split_ctr, std::vector<int>(4 + kSplitMaxSm, 0)));
   // workspaces
   TRY(dalloc(c, &c->LU, nnz));
   TRY(dalloc(c, &c->T, nnz));

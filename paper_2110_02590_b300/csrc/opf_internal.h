@@ -493,7 +493,7 @@ struct opf_ctx {
   // C / 2 for the rest; colmap_split[k] holds n1 x C then n2 x C/2 columns
   int* colmap_split[6] = {};
   int split_n1[6] = {}, split_n2[6] = {};
-  int* split_ctr = nullptr;  // the split launch's tile queues and per-SM CTA counts (2 + kSplitMaxSm)
+  int* split_ctr = nullptr;  // the split launch's tile queues and per-SM CTA counts (4 + kSplitMaxSm)
   int* tstart = nullptr;     // [n_u] first column position of each column's tile (symmetric Hessian)
   double *vbus = nullptr, *thbus = nullptr;
   double *g = nullptr, *dvec = nullptr, *yvec = nullptr;

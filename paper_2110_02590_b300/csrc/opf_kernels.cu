@@ -1661,26 +1661,41 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
 // part with its own column map and workspace), one per CTA, all CTAs resident.
 // The hardware's CTA-to-SM placement is not round robin (some SMs were given
 // three of the first CTAs), so a CTA takes its tile by its rank on its SM: the
-// first per_sm CTAs of an SM take the next wide tile, the others the next
-// narrow one (each queue heaviest first; an empty queue sends the CTA to the
-// other).  ctr: [0] wide queue, [1] narrow queue, [2 + smid] CTAs seen per SM;
-// zero before the launch.
+// first per_sm CTAs of an SM take a wide tile, the others a narrow one (an
+// exhausted queue sends the CTA to the other).  The wide queue is ordered
+// heaviest first; a CTA of even rank takes the heaviest remaining tile and one
+// of odd rank the lightest, so the two wide tiles of an SM sum to about the
+// mean (an SM's CTAs start together, in no fixed order across SMs).
+// ctr: [0] wide claims, [1] narrow queue, [2] heavy end, [3] light end,
+// [4 + smid] CTAs seen per SM; zero before the launch.
 template <int C, int NT>
 __global__ void __launch_bounds__(NT, 3) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int per_sm, int* ctr) {
   __shared__ int s_pick;
   if (threadIdx.x == 0) {
     unsigned smid;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-    const int rank = smid < (unsigned)kSplitMaxSm ? atomicAdd(ctr + 2 + smid, 1) : 0;
-    int kind = rank < per_sm ? 0 : 1;
-    int t = atomicAdd(ctr + kind, 1);
-    if (t >= (kind == 0 ? a1.ntiles : a2.ntiles)) {
-      kind ^= 1;
-      t = atomicAdd(ctr + kind, 1);
+    const int rank = smid < (unsigned)kSplitMaxSm ? atomicAdd(ctr + 4 + smid, 1) : 0;
+    auto wide = [&]() -> int {  // a wide tile, or -1 when all are taken
+      if (atomicAdd(ctr, 1) >= a1.ntiles) return -1;
+      return (rank & 1) ? a1.ntiles - 1 - atomicAdd(ctr + 3, 1) : atomicAdd(ctr + 2, 1);
+    };
+    int kind = 1, t = -1;
+    if (rank < per_sm) {
+      t = wide();
+      kind = 0;
     }
-    s_pick = (t << 1) | kind;
+    if (t < 0) {
+      kind = 1;
+      t = atomicAdd(ctr + 1, 1);
+      if (t >= a2.ntiles) {
+        t = wide();
+        kind = 0;
+      }
+    }
+    s_pick = t < 0 ? -1 : ((t << 1) | kind);
   }
   __syncthreads();
+  if (s_pick < 0) return;
   const int t = s_pick >> 1;
   if ((s_pick & 1) == 0) {
     if (t < a1.ntiles) hvp_tile<C>(a1, a1.scratch + a1.stride * t, t);
@@ -2205,7 +2220,7 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   if (a2.stamps) a2.stamps += (size_t)n1 * 8;
   const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
   const int per_sm = std::max(1, n1 / c->sm_count);
-  cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (2 + kSplitMaxSm), c->stream);
+  cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (4 + kSplitMaxSm), c->stream);
   hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, per_sm, c->split_ctr);
   c->launches++;
 }
