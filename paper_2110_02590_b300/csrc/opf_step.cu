@@ -45,6 +45,13 @@ struct StepWork {
   int* trsv_err = nullptr;         // a dense-solve wait timed out
   int* oz_err = nullptr;           // a wait of the tcgen05 emulated update timed out
   unsigned trsv_epoch = 0;
+  // the factorisation's launch sequence as a CUDA graph, per trailing-update kind
+  // (FP64, emulated), captured on first use for the wait limit and update engine
+  // of that moment
+  cudaGraphExec_t chol_exec[2] = {nullptr, nullptr};
+  long long chol_lim[2] = {0, 0};
+  int chol_engine[2] = {-1, -1};
+  long long chol_kernels[2] = {0, 0};
   // tracking QP (opf_tracking_update): grad q, the linearisation point w_t and its
   // state, the KKT reductions and the constraint values at the new point
   void* qp_block = nullptr;
@@ -68,6 +75,8 @@ void free_step_work(opf_ctx* c) {
   if (w->h_flag) cudaFreeHost(w->h_flag);
   for (cudaEvent_t e : w->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaGraphExec_t g : w->chol_exec)
+    if (g) cudaGraphExecDestroy(g);
   delete w;
   c->stepw = nullptr;
 }
@@ -800,6 +809,47 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag,
   return OPF_OK;
 }
 
+// launch_cholesky on w->L as one graph launch (about three hundred kernels on
+// the 9.2k grid), captured on the context's capture stream at first use and
+// again when the wait limit or the update engine has changed since.
+opf_status launch_cholesky_graph(opf_ctx* c, StepWork* w, int n, bool emulate) {
+  const int e = emulate ? 1 : 0;
+  const long long lim = c->wait_limit > 0 ? (long long)c->wait_limit : (1ll << 24);
+  if (!w->chol_exec[e] || w->chol_lim[e] != lim || w->chol_engine[e] != c->oz_engine) {
+    if (w->chol_exec[e]) {
+      SCK(cudaStreamSynchronize(c->stream));
+      cudaGraphExecDestroy(w->chol_exec[e]);
+      w->chol_exec[e] = nullptr;
+    }
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    c->stream = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    opf_status rc = OPF_OK;
+    if (err == cudaSuccess) {
+      rc = launch_cholesky(c, w, w->L, n, w->flag, emulate);
+      err = cudaStreamEndCapture(c->cap_stream, &graph);
+    }
+    c->stream = user;
+    w->chol_kernels[e] = c->launches - l0;
+    c->launches = l0;
+    if (rc != OPF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    SCK(err);
+    err = cudaGraphInstantiate(&w->chol_exec[e], graph, 0);
+    cudaGraphDestroy(graph);
+    SCK(err);
+    w->chol_lim[e] = lim;
+    w->chol_engine[e] = c->oz_engine;
+  }
+  SCK(cudaGraphLaunch(w->chol_exec[e], c->stream));
+  c->launches += w->chol_kernels[e];
+  return OPF_OK;
+}
+
 // L = S + delta I factorised in place in w->L; ok: no pivot was non-positive.
 // Mode 1 (the default) emulates the trailing updates on the tensor cores.
 // Mode 0 also factorises S + delta I again with FP64 trailing updates when a
@@ -815,7 +865,7 @@ opf_status factor_shifted(opf_ctx* c, StepWork* w, int nu, double delta, bool& o
     add_diag_kernel<<<dim3(nblk(nu, 256), nu), 256, 0, stream>>>(w->L, w->S, nu, delta);
     SCK(cudaMemsetAsync(w->flag, 0, sizeof(int), stream));
     c->launches++;
-    const opf_status rc = launch_cholesky(c, w, w->L, nu, w->flag, emulate);
+    const opf_status rc = launch_cholesky_graph(c, w, nu, emulate);
     if (rc) return rc;
     if (!emulate) fp64_runs++;
     SCK(cudaMemcpyAsync(w->h_flag, w->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, stream));
