@@ -119,6 +119,36 @@ def test_dense_solve_wait_limit_is_etimeout_and_context_recovers():
     assert torch.allclose(state["s"], probe["s"], rtol=0, atol=1e-12)
 
 
+def test_tcgen05_update_wait_limit_is_etimeout_and_context_recovers():
+    """The tcgen05 emulated Cholesky update waits on mbarriers for its bulk copies and MMAs;
+    with a one-poll limit those waits give up, the kernel drains what it issued, frees its
+    tensor memory and the step returns OPF_ETIMEOUT with the state untouched.  The same
+    context then takes the normal step (the factorisation graph re-captured with the default
+    limit) and the later tcgen05 launches allocate their tensor memory again."""
+    net = synth.workload("medium1400")
+    u, al, state = step_state(net)
+    ctx = P.OPFContext(net)
+    ctx.set_update_engine(2)  # every emulated update on tcgen05 (the default keeps small ones on mma.sync)
+    probe = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in state.items()}
+    probe["x"], _ = ctx.powerflow(dev(u))
+    ctx.al_step(al_dev(al), probe)
+    state["x"], _ = ctx.powerflow(dev(u))
+    ctx.reduced_gradient(dict(al_dev(al), s=state["s"]))  # factors ready: the limit hits the step's waits
+    before = {k: v.clone() for k, v in state.items() if torch.is_tensor(v)}
+    ctx.set_wait_limit(1)
+    try:
+        with pytest.raises(P.OPFError) as ei:
+            ctx.al_step(al_dev(al), state)
+        assert ei.value.status == ETIMEOUT and "tensor cores" in str(ei.value)
+    finally:
+        ctx.set_wait_limit(0)
+    for k, v in before.items():
+        assert torch.equal(state[k], v), k
+    ctx.al_step(al_dev(al), state)
+    assert torch.allclose(state["u"], probe["u"], rtol=0, atol=1e-12)
+    assert torch.allclose(state["s"], probe["s"], rtol=0, atol=1e-12)
+
+
 def test_cluster_lu_wait_limit_is_etimeout_and_context_recovers():
     """The dense trailing block of the LU runs on a thread-block cluster whose CTAs poll
     per-step flags in shared memory; with a one-poll limit they give up (every CTA still
