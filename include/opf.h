@@ -329,7 +329,8 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
 
 /*
  * opf_reduced_hessian_noalloc: the same reduced Hessian as opf_reduced_hessian
- * (same tile kernel and output), for callers that must not allocate device
+ * (same tile kernel; every column computed in full, so the output equals
+ * opf_reduced_hessian's symmetric form to rounding), for callers that must not allocate device
  * memory during the call: a real-time tracking loop that cannot stall on the
  * allocator (cudaMalloc may synchronise the device and its latency is
  * unbounded), or a process whose device-memory budget is fixed at start-up.
