@@ -481,25 +481,35 @@ def autograd_batch(P, torch, dev, nscen):
     u = d(np.tile(synth.flat_control(net), (nscen, 1))).requires_grad_(True)
     pd, qd = d(pds).requires_grad_(True), d(qds).requires_grad_(True)
     s = d(np.tile(al["s"], (nscen, 1))).requires_grad_(True)
-    obj(u[:2], pd[:2], qd[:2], s[:2]).sum().backward()  # warm-up
+    for _ in range(2):  # warm-up: every context of the pool takes scenarios (first-use set-up)
+        obj(u, pd, qd, s).sum().backward()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    F = obj(u, pd, qd, s)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    F.sum().backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    runs = []
+    for _ in range(3):  # median of three passes (forward, then backward with the power flows recomputed)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        F = obj(u, pd, qd, s)
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        F.sum().backward()
+        torch.cuda.synchronize()
+        runs.append((tb - ta, time.perf_counter() - tb))
+    runs.sort(key=lambda r: r[0] + r[1])
+    fwd_s, bwd_s = runs[1]
+    t0, t1, t2 = 0.0, fwd_s, fwd_s + bwd_s
+    t_plain = time.perf_counter()
     for b in range(nscen):  # plain calls: one power flow and one adjoint gradient per scenario
         ctx.powerflow(u[b].detach(), pd=pd[b].detach(), qd=qd[b].detach(), x0=x0)
         ctx.reduced_gradient(dict(ald, s=s[b].detach()))
     torch.cuda.synchronize()
-    t3 = time.perf_counter()
-    return {"net": "2,000-bus synthetic grid", "scenarios": nscen, "ms_forward": 1e3 * (t1 - t0),
+    t3 = t2 + (time.perf_counter() - t_plain)
+    return {"net": "2,000-bus synthetic grid", "scenarios": nscen, "contexts": len(obj.pool),
+            "ms_forward": 1e3 * (t1 - t0),
             "ms_backward": 1e3 * (t2 - t1), "scenarios_per_s": nscen / (t2 - t0),
             "plain_ms": 1e3 * (t3 - t2), "plain_scenarios_per_s": nscen / (t3 - t2),
             "note": "forward: power flow + F per scenario; backward: power flow recomputed + adjoint gradient "
-                    "w.r.t. u, loads and s; plain: power flow + adjoint gradient per scenario"}
+                    "w.r.t. u, loads and s (median of three passes after two warm-up passes); plain: power "
+                    "flow + adjoint gradient per scenario"}
 
 
 def static_opf(P, torch, dev, name, max_outer=20, max_inner=60, scaling_gmax=100.0, keep_state=False):
