@@ -191,8 +191,8 @@ typedef struct {
   int block_k, grid, tiles, launches;
   float ms_total;  /* device time of the call (CUDA events on the context stream) */
   float ms_hvp;    /* device time of the HVP phase alone */
-  double asymmetry; /* ||H - H^T||_F / ||H||_F when requested for a full Hessian, else -1
-                       (H is assembled column block by column block and not symmetrised) */
+  double asymmetry; /* ||H - H^T||_F / ||H||_F when requested for a full Hessian (which is then
+                       assembled column by column, not by symmetry), else -1 */
   float phase_ms[5]; /* with phase_profile: ms_hvp times each phase's share of the tiles'
                         summed durations -- (1) pruned L solve of Z, (2) U sweep of Z,
                         (3)-(4) second-order terms, (5)-(6) U^T and L^T sweeps of Psi,
@@ -207,8 +207,13 @@ typedef struct {
  * terms of the injections, line flows and costs along every branch, then
  * G_x^T Psi = -(l_xu W + l_xx Z) (U^T then L^T sweeps) and
  * H[:, block] = l_uu W + l_ux Z + G_u^T Psi.  The factors of G_x are the ones
- * left by opf_powerflow (factorised once, Sec. III-C).  H is not
- * symmetrised.  opts/info may be NULL.  Errors: OPF_ESTATE, OPF_EINVAL.
+ * left by opf_powerflow (factorised once, Sec. III-C).  A full Hessian
+ * (every column, tiled, no asymmetry report) is built by its symmetry unless
+ * opf_set_hessian_symmetry turned that off: each tile keeps the rows of the
+ * controls from its first column position on and one more kernel fills the
+ * other entries from their transposes (info->launches counts it); otherwise H
+ * is assembled column by column and not symmetrised.  opts/info may be NULL.
+ * Errors: OPF_ESTATE, OPF_EINVAL.
  */
 opf_status opf_reduced_hessian(opf_ctx* ctx, const opf_al_params* p, const opf_hess_opts* opts,
                                double* H, opf_hess_info* info);
