@@ -182,7 +182,12 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
 }
 
 // Panel below the diagonal block: X21 = A21 L_kk^{-T} = A21 Dinv^T as a small
-// GEMM (16 rows x 32 columns per CTA, 2 outputs per thread), written in place.
+// GEMM (blockDim / 16 rows x 32 columns per CTA, at most 16 rows), written in place.  Dinv is lower
+// triangular, so column c takes the terms t <= c only; thread (row, c) also
+// owns column 31 - c, and the two runs of term pairs add up to 17 for every
+// thread, so a warp issues 34 FMAs per thread instead of 64 (the FP64 pipe
+// issues whole warp instructions).  Each column keeps the even and the odd
+// terms in separate sums, in increasing t, as the full product would.
 __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag,
                                                         const double* __restrict__ Dinv) {
   pdl_wait();
@@ -190,27 +195,35 @@ __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0
   __shared__ double M[NB][NB + 1];  // M[c][t] = (L_kk^{-1})_ct
   __shared__ double P[16][NB + 1];  // P[r][t] = A21[row r][t]
   const double* D = Dinv + (size_t)(k0 / NB) * NB * NB;
-  const int row0 = k0 + kb + blockIdx.x * 16;
+  const int rows = blockDim.x >> 4, row0 = k0 + kb + blockIdx.x * rows;
   for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) M[q >> 5][q & 31] = D[q];
-  for (int q = threadIdx.x; q < 16 * NB; q += blockDim.x) {
-    const int r = q & 15, tt = q >> 4, g = row0 + r;
+  for (int q = threadIdx.x; q < rows * NB; q += blockDim.x) {
+    const int r = q % rows, tt = q / rows, g = row0 + r;
     P[r][tt] = (tt < kb && g < n) ? A[(size_t)(k0 + tt) * n + g] : 0.0;
   }
   __syncthreads();
-  const int r = threadIdx.x >> 4, c0 = (threadIdx.x & 15) * 2;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const int r = threadIdx.x >> 4, c0 = threadIdx.x & 15, c1 = NB - 1 - c0;
+  const int n0 = (c0 + 2) >> 1;  // term pairs of column c0; column c1 takes the other 17 - n0
+  double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
 #pragma unroll
-  for (int tt = 0; tt < NB; tt += 2) {
-    const double p0 = P[r][tt], p1 = P[r][tt + 1];
-    s0 = fma(p0, M[c0][tt], s0);
-    s1 = fma(p0, M[c0 + 1][tt], s1);
-    s2 = fma(p1, M[c0][tt + 1], s2);
-    s3 = fma(p1, M[c0 + 1][tt + 1], s3);
+  for (int q = 0; q < 17; q++) {
+    const bool first = q < n0;
+    const int tt = first ? 2 * q : 2 * (q - n0), c = first ? c0 : c1;
+    double e = first ? e0 : e1, o = first ? o0 : o1;
+    e = fma(P[r][tt], M[c][tt], e);
+    o = fma(P[r][tt + 1], M[c][tt + 1], o);
+    if (first) {
+      e0 = e;
+      o0 = o;
+    } else {
+      e1 = e;
+      o1 = o;
+    }
   }
   const int g = row0 + r;
   if (g < n) {
-    if (c0 < kb) A[(size_t)(k0 + c0) * n + g] = s0 + s2;
-    if (c0 + 1 < kb) A[(size_t)(k0 + c0 + 1) * n + g] = s1 + s3;
+    if (c0 < kb) A[(size_t)(k0 + c0) * n + g] = e0 + o0;
+    if (c1 < kb) A[(size_t)(k0 + c1) * n + g] = e1 + o1;
   }
   pdl_trigger();
 }
@@ -778,11 +791,26 @@ opf_status launch_cholesky(opf_ctx* c, StepWork* w, double* A, int n, int* flag,
       c->launches++;
       const int rest = n - k0 - kb;
       if (rest <= 0) break;
-      SCK(launch_pdl(chol_trsm_kernel, dim3(nblk(rest, 16)), dim3(256), 0, s1, A, n, k0, kb, flag, w->Dinv));
+      {  // 8-row CTAs when they leave the busiest SM fewer rows than 16-row ones
+        const int sm = std::max(1, c->sm_count);
+        const int rows = ((nblk(rest, 8) + sm - 1) / sm) * 8 < ((nblk(rest, 16) + sm - 1) / sm) * 16 ? 8 : 16;
+        SCK(launch_pdl(chol_trsm_kernel, dim3(nblk(rest, rows)), dim3(16 * rows), 0, s1, A, n, k0, kb, flag,
+                       w->Dinv));
+      }
       c->launches++;
       if (k0 + kb < c1) {  // the group's remaining columns, all rows below
-        const dim3 grid(nblk(c1 - k0 - kb, 32), nblk(rest, 32));
-        SCK(launch_pdl(chol_syrk_kernel<32>, grid, dim3(256), 0, s1, A, n, k0, kb, flag, 2, 0, c1));
+        // a 32 x 32 tile is ~1,000 warp FP64 instructions (~10 us of one SM's
+        // FP64 pipe); 16 x 16 tiles when they leave the busiest SM less work
+        const long long t32 = (long long)nblk(c1 - k0 - kb, 32) * nblk(rest, 32);
+        const long long t16 = (long long)nblk(c1 - k0 - kb, 16) * nblk(rest, 16);
+        const int sm = std::max(1, c->sm_count);
+        if ((t16 + sm - 1) / sm < 4 * ((t32 + sm - 1) / sm)) {
+          const dim3 grid(nblk(c1 - k0 - kb, 16), nblk(rest, 16));
+          SCK(launch_pdl(chol_syrk_kernel<16>, grid, dim3(256), 0, s1, A, n, k0, kb, flag, 2, 0, c1));
+        } else {
+          const dim3 grid(nblk(c1 - k0 - kb, 32), nblk(rest, 32));
+          SCK(launch_pdl(chol_syrk_kernel<32>, grid, dim3(256), 0, s1, A, n, k0, kb, flag, 2, 0, c1));
+        }
         c->launches++;
       }
     }
