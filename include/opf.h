@@ -378,7 +378,10 @@ opf_status opf_reduced_hessian_noalloc(opf_ctx* ctx, const opf_al_params* p,
  * S_uu is factorised by a device FP64 Cholesky; delta (inertia correction) takes
  * 0, then 1e-8 * 10^k, k = 0 .. max_inertia - 1, until the factorisation succeeds
  * (with opts->delta_start > 0: delta_start, then 10x per try, as a loop that
- * carries the previous step's delta over).
+ * carries the previous step's delta over).  Success is monotone in delta (S_uu
+ * + delta I positive definite implies it for larger delta), so the first one,
+ * two or three candidates are tried in turn and the rest bisected: the same
+ * delta as trying each in turn, with fewer factorisations.
  * Step lengths: fraction to the boundary with tau = max(0.99, 1 - mu) for the
  * primal and the dual variables; the power flow is re-solved at u + alpha_p d_u
  * (warm start from x) and alpha_p halved until it converges, so the new iterate
@@ -418,6 +421,8 @@ typedef struct {
    * solves, J d_u and the fraction to the boundary; trial power flows and update */
   float ms_first_order, ms_rhs, ms_cholesky, ms_solve, ms_trial;
   int cholesky_fp64;  /* factorisations run with FP64 trailing updates (opf_set_cholesky_mode) */
+  int factorisations; /* factorisations of the inertia search (inertia_tries is the index of the
+                         chosen delta in the sequence, as trying each in turn would count it) */
 } opf_step_info;
 
 /* p supplies sigma_f, rho, sigma_c and y (its s and omega are ignored: s comes

@@ -83,7 +83,7 @@ class StepInfo(C.Structure):
                 ("inertia_tries", C.c_int), ("pf_iterations", C.c_int), ("ms_hessian", C.c_float),
                 ("ms_total", C.c_float), ("ms_first_order", C.c_float), ("ms_rhs", C.c_float),
                 ("ms_cholesky", C.c_float), ("ms_solve", C.c_float), ("ms_trial", C.c_float),
-                ("cholesky_fp64", C.c_int)]
+                ("cholesky_fp64", C.c_int), ("factorisations", C.c_int)]
 
 
 class AlOpts(C.Structure):

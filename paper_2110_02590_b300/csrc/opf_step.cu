@@ -1014,25 +1014,71 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   c->stream = stream;
   SCK(cudaEventRecord(w->aux_done, w->aux));
   SCK(cudaEventRecord(ev[3], stream));
-  // Cholesky with inertia correction
+  // Cholesky with inertia correction: the first delta of the sequence
+  // delta_0 = delta0, delta_t = delta0 10^t (delta0 > 0, carried over) or
+  // 1e-8 10^(t - 1) (delta0 = 0), t <= max_inertia, whose factorisation
+  // succeeds.  S + delta I positive definite implies it for every larger
+  // delta, so success is monotone in t and a bisection finds the same t as
+  // trying them in turn: the first few in turn (a carried-over delta usually
+  // succeeds at once or after one raise), then bisection over the rest (a
+  // fresh start on the 9.2k grid needs t = 17: 7 factorisations instead of 18).
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
-  double delta = delta0;
-  int tries = 0, fp64_runs = 0;
-  for (;; tries++) {
+  auto delta_at = [&](int t) {
+    if (t == 0) return delta0;
+    return delta0 > 0.0 ? delta0 * std::pow(10.0, (double)t) : 1e-8 * std::pow(10.0, (double)(t - 1));
+  };
+  int fp64_runs = 0, factorisations = 0, last = -1;
+  auto attempt = [&](int t, bool& ok) -> opf_status {
+    ok = false;
+    last = t;
+    factorisations++;
+    return factor_shifted(c, w, nu, delta_at(t), ok, fp64_runs);
+  };
+  auto fail = [&](opf_status r) {
+    cudaStreamWaitEvent(stream, w->aux_done, 0);  // no work of this call outlives it
+    if (r == OPF_ENOTPD) set_last_error("S_uu not positive definite after the inertia corrections");
+    return r;
+  };
+  int tries = -1, lo = -1;
+  const int nlinear = std::min(delta0 > 0.0 ? 3 : 1, max_inertia + 1);
+  for (int t = 0; t < nlinear; t++) {
     bool ok = false;
-    rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
-    if (rc) {
-      cudaStreamWaitEvent(stream, w->aux_done, 0);  // no work of this call outlives it
-      return rc;
+    rc = attempt(t, ok);
+    if (rc) return fail(rc);
+    if (ok) {
+      tries = t;
+      break;
     }
-    if (ok) break;
-    if (tries >= max_inertia) {
-      cudaStreamWaitEvent(stream, w->aux_done, 0);
-      set_last_error("S_uu not positive definite after the inertia corrections");
-      return OPF_ENOTPD;
-    }
-    delta = (delta0 > 0.0) ? delta0 * std::pow(10.0, (double)(tries + 1)) : 1e-8 * std::pow(10.0, (double)tries);
+    lo = t;
   }
+  if (tries < 0) {
+    int hi = max_inertia + 1;  // past the last delta: fails
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      bool ok = false;
+      rc = attempt(mid, ok);
+      if (rc) return fail(rc);
+      if (ok) {
+        hi = mid;
+      } else {
+        lo = mid;
+      }
+    }
+    if (hi > max_inertia) return fail(OPF_ENOTPD);
+    tries = hi;
+    // the factor in L is the last one computed: redo it if that was a failure;
+    // should the redo fail (success not monotone after all), go on in turn
+    while (last != tries) {
+      bool ok = false;
+      rc = attempt(tries, ok);
+      if (rc) return fail(rc);
+      if (!ok) {
+        if (++tries > max_inertia) return fail(OPF_ENOTPD);
+        last = -1;
+      }
+    }
+  }
+  const double delta = delta_at(tries);
   SCK(cudaStreamWaitEvent(stream, w->aux_done, 0));
   SCK(cudaEventRecord(ev[4], stream));
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
@@ -1139,6 +1185,7 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
     info->halvings = halvings;
     info->inertia_tries = tries;
     info->cholesky_fp64 = fp64_runs;
+    info->factorisations = factorisations;
     info->pf_iterations = pfi.iterations;
     info->ms_hessian = ms_hessian;
     float ms = 0.f;
