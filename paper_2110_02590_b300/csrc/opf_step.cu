@@ -911,6 +911,71 @@ opf_status factor_shifted(opf_ctx* c, StepWork* w, int nu, double delta, bool& o
   return run(false);
 }
 
+// Inertia correction: the first delta of the sequence delta_0 = d0, delta_t =
+// d0 10^t (d0 > 0) or 1e-8 10^(t - 1) (d0 = 0), t <= max_raises, for which
+// factor_shifted succeeds; L then holds that factorisation.  S + delta I
+// positive definite implies it for every larger delta, so success is monotone
+// in t and a bisection finds the same t as trying them in turn: the first
+// nlinear candidates in turn (a carried-over delta usually succeeds at once or
+// after one raise), then bisection over the rest (a fresh start on the 9.2k
+// grid needs t = 17: 6 factorisations instead of 18).  raises = t; OPF_ENOTPD
+// (with msg) when no candidate succeeds.
+opf_status inertia_search(opf_ctx* c, StepWork* w, int nu, double d0, int max_raises, int nlinear,
+                          const char* msg, double& delta, int& raises, int& factorisations, int& fp64_runs) {
+  auto delta_at = [&](int t) {
+    if (t == 0) return d0;
+    return d0 > 0.0 ? d0 * std::pow(10.0, (double)t) : 1e-8 * std::pow(10.0, (double)(t - 1));
+  };
+  int last = -1;
+  auto attempt = [&](int t, bool& ok) -> opf_status {
+    ok = false;
+    last = t;
+    factorisations++;
+    return factor_shifted(c, w, nu, delta_at(t), ok, fp64_runs);
+  };
+  int t_ok = -1, lo = -1;
+  for (int t = 0; t < std::min(nlinear, max_raises + 1); t++) {
+    bool ok = false;
+    const opf_status rc = attempt(t, ok);
+    if (rc) return rc;
+    if (ok) {
+      t_ok = t;
+      break;
+    }
+    lo = t;
+  }
+  if (t_ok < 0) {
+    int hi = max_raises + 1;  // past the last candidate: fails
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      bool ok = false;
+      const opf_status rc = attempt(mid, ok);
+      if (rc) return rc;
+      if (ok) {
+        hi = mid;
+      } else {
+        lo = mid;
+      }
+    }
+    t_ok = hi;
+    // L holds the last factorisation computed: redo the chosen one if that was
+    // a failure; should the redo fail (success not monotone after all), go on in turn
+    while (t_ok <= max_raises && last != t_ok) {
+      bool ok = false;
+      const opf_status rc = attempt(t_ok, ok);
+      if (rc) return rc;
+      if (!ok) t_ok++;
+    }
+    if (t_ok > max_raises) {
+      set_last_error(msg);
+      return OPF_ENOTPD;
+    }
+  }
+  delta = delta_at(t_ok);
+  raises = t_ok;
+  return OPF_OK;
+}
+
 opf_status launch_chol_solve(opf_ctx* c, StepWork* w, double* A, int n, double* b) {
   const int nb = (n + 31) / 32;  // Dinv holds the diagonal blocks' inverses from the factorisation
   chol_upper_copy_kernel<<<dim3(nb, nb), 256, 0, c->stream>>>(A, n);
@@ -1014,71 +1079,17 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   c->stream = stream;
   SCK(cudaEventRecord(w->aux_done, w->aux));
   SCK(cudaEventRecord(ev[3], stream));
-  // Cholesky with inertia correction: the first delta of the sequence
-  // delta_0 = delta0, delta_t = delta0 10^t (delta0 > 0, carried over) or
-  // 1e-8 10^(t - 1) (delta0 = 0), t <= max_inertia, whose factorisation
-  // succeeds.  S + delta I positive definite implies it for every larger
-  // delta, so success is monotone in t and a bisection finds the same t as
-  // trying them in turn: the first few in turn (a carried-over delta usually
-  // succeeds at once or after one raise), then bisection over the rest (a
-  // fresh start on the 9.2k grid needs t = 17: 7 factorisations instead of 18).
+  // Cholesky with inertia correction (inertia_search)
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
-  auto delta_at = [&](int t) {
-    if (t == 0) return delta0;
-    return delta0 > 0.0 ? delta0 * std::pow(10.0, (double)t) : 1e-8 * std::pow(10.0, (double)(t - 1));
-  };
-  int fp64_runs = 0, factorisations = 0, last = -1;
-  auto attempt = [&](int t, bool& ok) -> opf_status {
-    ok = false;
-    last = t;
-    factorisations++;
-    return factor_shifted(c, w, nu, delta_at(t), ok, fp64_runs);
-  };
-  auto fail = [&](opf_status r) {
+  double delta = 0.0;
+  int tries = 0, fp64_runs = 0, factorisations = 0;
+  rc = inertia_search(c, w, nu, delta0, max_inertia, delta0 > 0.0 ? 3 : 1,
+                      "S_uu not positive definite after the inertia corrections", delta, tries, factorisations,
+                      fp64_runs);
+  if (rc) {
     cudaStreamWaitEvent(stream, w->aux_done, 0);  // no work of this call outlives it
-    if (r == OPF_ENOTPD) set_last_error("S_uu not positive definite after the inertia corrections");
-    return r;
-  };
-  int tries = -1, lo = -1;
-  const int nlinear = std::min(delta0 > 0.0 ? 3 : 1, max_inertia + 1);
-  for (int t = 0; t < nlinear; t++) {
-    bool ok = false;
-    rc = attempt(t, ok);
-    if (rc) return fail(rc);
-    if (ok) {
-      tries = t;
-      break;
-    }
-    lo = t;
+    return rc;
   }
-  if (tries < 0) {
-    int hi = max_inertia + 1;  // past the last delta: fails
-    while (hi - lo > 1) {
-      const int mid = lo + (hi - lo) / 2;
-      bool ok = false;
-      rc = attempt(mid, ok);
-      if (rc) return fail(rc);
-      if (ok) {
-        hi = mid;
-      } else {
-        lo = mid;
-      }
-    }
-    if (hi > max_inertia) return fail(OPF_ENOTPD);
-    tries = hi;
-    // the factor in L is the last one computed: redo it if that was a failure;
-    // should the redo fail (success not monotone after all), go on in turn
-    while (last != tries) {
-      bool ok = false;
-      rc = attempt(tries, ok);
-      if (rc) return fail(rc);
-      if (!ok) {
-        if (++tries > max_inertia) return fail(OPF_ENOTPD);
-        last = -1;
-      }
-    }
-  }
-  const double delta = delta_at(tries);
   SCK(cudaStreamWaitEvent(stream, w->aux_done, 0));
   SCK(cudaEventRecord(ev[4], stream));
   SCK(cudaMemcpyAsync(w->du, w->r, nu * sizeof(double), cudaMemcpyDeviceToDevice, stream));
@@ -1316,18 +1327,12 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
     c->launches++;
     SCK(cudaEventRecord(ev[1], stream));
-    for (int tries = 0;; tries++) {
-      bool ok = false;
-      rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
-      if (rc) return rc;
-      if (ok) break;
-      if (tries >= max_inertia) {
-        set_last_error("tracking QP: H_uu not positive definite after the inertia corrections");
-        return OPF_ENOTPD;
-      }
-      delta = (delta > 0.0) ? 10.0 * delta : 1e-8;
-      increases++;
-    }
+    int raises = 0, nfac = 0;
+    rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? 3 : 1,
+                        "tracking QP: H_uu not positive definite after the inertia corrections", delta, raises, nfac,
+                        fp64_runs);
+    if (rc) return rc;
+    increases += raises;
     SCK(cudaEventRecord(ev[2], stream));
     float t = 0.f;
     cudaEventElapsedTime(&t, ev[1], ev[2]);
@@ -1364,17 +1369,13 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     // Cholesky; the QP's u-block regularisation delta only grows
     SCK(cudaEventRecord(ev[1], stream));
     const double d_old = delta;
-    for (int tries = 0;; tries++) {
-      bool ok = false;
-      rc = factor_shifted(c, w, nu, delta, ok, fp64_runs);
+    {
+      int raises = 0, nfac = 0;
+      rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? 3 : 1,
+                          "tracking QP: S_uu not positive definite after the inertia corrections", delta, raises,
+                          nfac, fp64_runs);
       if (rc) return rc;
-      if (ok) break;
-      if (tries >= max_inertia) {
-        set_last_error("tracking QP: S_uu not positive definite after the inertia corrections");
-        return OPF_ENOTPD;
-      }
-      delta = (delta > 0.0) ? 10.0 * delta : 1e-8;
-      increases++;
+      increases += raises;
     }
     SCK(cudaEventRecord(ev[2], stream));
     {
