@@ -505,7 +505,9 @@ opf_status opf_al_solve(opf_ctx* ctx, const opf_al_params* p, double* y, opf_al_
  * max(0.99, 1 - mu); delta starts at the smallest of 0 (or opts->delta_start),
  * 1e-8, 1e-7, ... that makes H_uu + delta I positive definite (H_uu = H(0), one
  * more Hessian and Cholesky before the iterations), so that the QP is convex,
- * and grows further only if an iteration's S is not positive definite; with
+ * and grows further only if an iteration's S is not positive definite (each
+ * search as in opf_al_step: the first candidates in turn, then a bisection,
+ * which success being monotone in delta makes equal to trying each in turn); with
  * opts->inertia_only the convexity search is skipped (H_uu is indefinite even
  * at an OPF optimum, along the directions that move active constraints, while
  * S, which holds the barrier terms of those bounds, is not).  grad q is carried from iteration to iteration through the Newton
