@@ -104,7 +104,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-cols", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
@@ -778,7 +778,8 @@ def run_gpu(args):
         if args.profile_step:
             torch.cuda.profiler.stop()
     launches = ctx.launch_count() - launches0
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step, value = job_value(nu, world, total_ms, args.steps)
 
     # the Hessian alone (exact weights) at the current state, and the HVP kernel phase
@@ -836,13 +837,14 @@ def run_gpu(args):
     dev_pd = torch.empty(net.n_bus, dtype=torch.float64, device=dev)
     dev_qd = torch.empty_like(dev_pd)
     ks = ke
+    e2e_infos = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(ks):
         sidx = args.warmup + args.steps + 1 + k  # the load sequence goes on from the timed steps
         dev_pd.copy_(host_pd[sidx], non_blocking=True)
         dev_qd.copy_(host_qd[sidx], non_blocking=True)
-        step(k, dev_pd, dev_qd)
+        e2e_infos.append(step(k, dev_pd, dev_qd))
         host_u.copy_(state["u"], non_blocking=True)
         host_s.copy_(state["s"], non_blocking=True)
         torch.cuda.synchronize()
@@ -904,7 +906,10 @@ def run_gpu(args):
         "ms_hessian_in_step": statistics.median(i["ms_hessian"] for i in sinfos),
         "step_detail": {"pf_iterations": statistics.median(i[0]["iterations"] for i in infos),
                         "inertia_delta": statistics.median(i["delta"] for i in sinfos),
-                        "halvings": sum(i["halvings"] for i in sinfos)},
+                        "halvings": sum(i["halvings"] for i in sinfos),
+                        "pf_iterations_total": sum(i[0]["iterations"] for i in infos),
+                        "factorisations": sum(i["factorisations"] for i in sinfos),
+                        "ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)]},
         "hessian_asymmetry": prof_full["asymmetry"],
         "hessian_symmetry": {
             "form": "default: each tile keeps the rows of the controls from its first column position on "
@@ -940,7 +945,9 @@ def run_gpu(args):
                                      "Ut_Lt_sweeps": share[3], "assembly": share[4]},
                      "solve_phase": solve},
         "e2e": {"value": world * nu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * net.n_bus,
-                "d2h_bytes_per_step": 8 * (nu + ctx.m), "ms_per_step": e2e_s * 1e3, "steps": ks},
+                "d2h_bytes_per_step": 8 * (nu + ctx.m), "ms_per_step": e2e_s * 1e3, "steps": ks,
+                "pf_iterations": sum(i[0]["iterations"] for i in e2e_infos),
+                "factorisations": sum(i[1]["factorisations"] for i in e2e_infos)},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
