@@ -486,18 +486,25 @@ __device__ __forceinline__ void tri_regs(const DevNet& n, const double* __restri
 // only): the rows below r0 are already final and the slab is zero outside the
 // rows set in the mask; only the trailing block remains.  lcnt (backward only):
 // run the levels of the L^T ordering (DevNet::bmeta_lt), only the first
-// lcnt[lv] blocks of level lv.
+// lcnt[lv] blocks of level lv.  zmask (backward only): a row below r0 whose
+// bit is clear starts from zero (its slab entries are not read: they were
+// never written).
 template <int C, bool FWD, bool DIAG>
 __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict__ V,
                                       const double* __restrict__ invdiag, double* X,
                                       const unsigned* rmask = nullptr, double* tb = nullptr,
-                                      const int* lcnt = nullptr) {
+                                      const int* lcnt = nullptr, const unsigned* zmask = nullptr) {
   constexpr int RPW = 32 / C;
   constexpr int TRI_MR = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = lane % C;
   const int nslots = (blockDim.x >> 5) * RPW, myslot = warp * RPW + lane / C;
   const int r0 = n.r0, s = n.nroot;
+  // a row's starting value
+  auto start = [&](int r) -> double {
+    if (!FWD && zmask && r < r0 && !((zmask[r >> 5] >> (r & 31)) & 1u)) return 0.0;
+    return X[(size_t)r * C + col];
+  };
   // the triangle in registers when the caller lends shared memory for it
   const bool treg = tb != nullptr && s * C <= TRI_MR * (int)blockDim.x;
   if (!FWD && treg) tri_regs<C, false, DIAG, TRI_MR>(n, V, invdiag, X, tb, false);
@@ -548,7 +555,7 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
         const int4 m = (k == k0) ? mt : __ldg(lmeta + k);
         const bool two = m.w != 0;
         const int lead = m.x, oth = other_of(m), q1 = m.z, off = m.w;
-        const double xl = X[(size_t)lead * C + col], xo = two ? X[(size_t)oth * C + col] : 0.0;
+        const double xl = start(lead), xo = two ? start(oth) : 0.0;
         double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
         int p = m.y + grp;
         for (; p + 3 * RPW < q1; p += 4 * RPW) {  // four slab reads in flight per lane
@@ -607,7 +614,7 @@ __device__ __forceinline__ void sweep(const DevNet& n, const double* __restrict_
         const bool two = m.w != 0;
         if (!DIAG && !two && m.y == m.z) continue;           // one row, no entries: final
         const int lead = m.x, oth = other_of(m);
-        double va = X[(size_t)lead * C + col], vb = two ? X[(size_t)oth * C + col] : 0.0;
+        double va = start(lead), vb = two ? start(oth) : 0.0;
         block_dot<C>(n, V, X, m.y, m.z, m.w, two, col, va, vb);
         if (DIAG) va *= invdiag[lead];
         X[(size_t)lead * C + col] = va;
@@ -1284,39 +1291,41 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
         s_col[threadIdx.x] = pos >= a.col_end ? NOCOL : pos;
       }
     }
-    // (0) right-hand side B = -G_u W, W = unit directions of the tile's columns
-    for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+    // (0) right-hand side B = -G_u W, W = unit directions of the tile's columns:
+    // first the rows it touches (marked), then, once the first solve's reach is
+    // known, the slab is cleared on the reached rows and the trailing block only
+    // (the U sweep starts the other rows from zero through the mask, so the slab
+    // is neither cleared nor read there), then the values
     if (prune)
       for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
     __syncthreads();
-    auto mark = [&](int r) {
-      if (prune && r < r0) atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+    auto rhs = [&](bool values) {
+      // Z[r][c] = v (set) or -= v; without values, mark row r
+      auto put = [&](int r, int c, double v, bool set) {
+        if (values) {
+          double& z = Z[(size_t)r * C + c];
+          z = set ? v : z - v;
+        } else if (prune && r < r0) {
+          atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+        }
+      };
+      for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const int j = s_col[c];
+        if (j < 0) continue;
+        const int k = a.ubus[j];
+        if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
+          put(n.pth[k], c, 1.0, true);
+          continue;
+        }
+        for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+          const int4 ar = n.adjrec[q];
+          if (ar.y >= 0) put(ar.y, c, values ? E[(size_t)q * ADJ_W + E_POV] : 0.0, false);
+          if (ar.x >= 0) put(ar.x, c, values ? E[(size_t)q * ADJ_W + E_QOV] : 0.0, false);
+        }
+        if (n.type[k] == PV) put(n.pth[k], c, values ? bw[6 * nb + k] : 0.0, false);
+      }
     };
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-      const int j = s_col[c];
-      if (j < 0) continue;
-      const int k = a.ubus[j];
-      if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
-        Z[(size_t)n.pth[k] * C + c] = 1.0;
-        mark(n.pth[k]);
-        continue;
-      }
-      for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-        const int4 ar = n.adjrec[q];
-        if (ar.y >= 0) {
-          Z[(size_t)ar.y * C + c] -= E[(size_t)q * ADJ_W + E_POV];
-          mark(ar.y);
-        }
-        if (ar.x >= 0) {
-          Z[(size_t)ar.x * C + c] -= E[(size_t)q * ADJ_W + E_QOV];
-          mark(ar.x);
-        }
-      }
-      if (n.type[k] == PV) {
-        Z[(size_t)n.pth[k] * C + c] -= bw[6 * nb + k];
-        mark(n.pth[k]);
-      }
-    }
+    rhs(false);
     __syncthreads();
     // (1) Z = L^{-1} B.  The solution is nonzero only on the elimination-tree
     // ancestors of the right-hand side's rows: mark them, list them in
@@ -1366,6 +1375,16 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
       __syncthreads();
       nl = s_nl;
     }
+    const bool reach = nl <= a.list_cap;  // the first solve and the U sweep see the reach only
+    if (reach) {
+      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x) Z[(size_t)s_list[idx / C] * C + idx % C] = 0.0;
+      for (size_t k = (size_t)r0 * C + threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+    } else {
+      for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+    }
+    __syncthreads();
+    rhs(true);
+    __syncthreads();
     const int ngrp = blockDim.x / C, g = threadIdx.x / C, nwarp = blockDim.x >> 5;
     const double* __restrict__ Vl = a.LU;
     if (nl <= a.zs_cap) {
@@ -1456,7 +1475,7 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
     }
     hvp_stamp(a, tile, 1);
     // (2) U sweep
-    sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
+    sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb, nullptr, reach ? s_mask : nullptr);
     hvp_stamp(a, tile, 2);
     // (2b) on request, the reduced constraint Jacobian of the tile's columns,
     // J W = d_x c Z + d_u c W (Sec. III-B), from the first adjoint Z just
