@@ -444,9 +444,11 @@ __global__ void sym_diag_kernel(double* S, int n, const double* sig_u) {
   }
 }
 
+// L = S + delta I on the lower triangle (the factorisation reads no other part;
+// the dense solves' transposed copy fills the strict upper triangle later).
 __global__ void add_diag_kernel(double* L, const double* S, int n, double delta) {
   const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || i < j) return;
   L[(size_t)j * n + i] = S[(size_t)j * n + i] + ((i == j) ? delta : 0.0);
 }
 
@@ -916,10 +918,12 @@ opf_status factor_shifted(opf_ctx* c, StepWork* w, int nu, double delta, bool& o
 // factor_shifted succeeds; L then holds that factorisation.  S + delta I
 // positive definite implies it for every larger delta, so success is monotone
 // in t and a bisection finds the same t as trying them in turn: the first
-// nlinear candidates in turn (a carried-over delta usually succeeds at once or
-// after one raise), then bisection over the rest (a fresh start on the 9.2k
-// grid needs t = 17: 6 factorisations instead of 18).  raises = t; OPF_ENOTPD
-// (with msg) when no candidate succeeds.
+// nlinear candidates in turn, then bisection over the rest.  Callers take all
+// of them in turn from a carried-over delta (which usually succeeds at once or
+// after a raise or two, where a bisection over 24 candidates would cost more)
+// and bisect after delta = 0 from a fresh start (the 9.2k grid then needs
+// t = 17: 6 factorisations instead of 18).  raises = t; OPF_ENOTPD (with msg)
+// when no candidate succeeds.
 opf_status inertia_search(opf_ctx* c, StepWork* w, int nu, double d0, int max_raises, int nlinear,
                           const char* msg, double& delta, int& raises, int& factorisations, int& fp64_runs) {
   auto delta_at = [&](int t) {
@@ -1083,7 +1087,7 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   const double delta0 = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double delta = 0.0;
   int tries = 0, fp64_runs = 0, factorisations = 0;
-  rc = inertia_search(c, w, nu, delta0, max_inertia, delta0 > 0.0 ? 3 : 1,
+  rc = inertia_search(c, w, nu, delta0, max_inertia, delta0 > 0.0 ? max_inertia + 1 : 1,
                       "S_uu not positive definite after the inertia corrections", delta, tries, factorisations,
                       fp64_runs);
   if (rc) {
@@ -1328,7 +1332,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     c->launches++;
     SCK(cudaEventRecord(ev[1], stream));
     int raises = 0, nfac = 0;
-    rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? 3 : 1,
+    rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? max_inertia + 1 : 1,
                         "tracking QP: H_uu not positive definite after the inertia corrections", delta, raises, nfac,
                         fp64_runs);
     if (rc) return rc;
@@ -1371,7 +1375,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     const double d_old = delta;
     {
       int raises = 0, nfac = 0;
-      rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? 3 : 1,
+      rc = inertia_search(c, w, nu, delta, max_inertia, delta > 0.0 ? max_inertia + 1 : 1,
                           "tracking QP: S_uu not positive definite after the inertia corrections", delta, raises,
                           nfac, fp64_runs);
       if (rc) return rc;

@@ -88,8 +88,8 @@ def test_al_step_cholesky_modes(mode):
         assert inf["cholesky_fp64"] == inf["factorisations"]
     else:
         assert (inf["inertia_tries"] > 0) <= inf["cholesky_fp64"] <= inf["factorisations"]
-    # one to three candidates in turn, then a bisection over the other (at most 24) and a redo
-    assert 1 <= inf["factorisations"] <= 3 + 5 + 1
+    # a fresh start: delta = 0, then a bisection over the other (at most 24) and a redo
+    assert 1 <= inf["factorisations"] <= 1 + 5 + 1
     with pytest.raises(P.OPFError):
         ctx.set_cholesky_mode(3)
 
