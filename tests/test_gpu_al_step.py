@@ -64,6 +64,23 @@ def test_al_step_parity(name, mu, delta_start):
     assert torch.isfinite(g["grad_u"]).all()
 
 
+def search_factorisations(t, max_raises=24, carried=False):
+    """Factorisations of the library's inertia search when the first succeeding candidate is t:
+    in turn from a carried-over delta; from a fresh start delta = 0, then a bisection over
+    1 .. max_raises, and the chosen candidate again when the bisection's last probe failed."""
+    if carried or t == 0:
+        return t + 1
+    n, lo, hi, last = 1, 0, max_raises + 1, 0
+    while hi - lo > 1:
+        mid = lo + (hi - lo) // 2
+        n, last = n + 1, mid
+        if mid >= t:
+            hi = mid
+        else:
+            lo = mid
+    return n + (last != hi)
+
+
 @pytest.mark.parametrize("mode", [0, 2])
 def test_al_step_cholesky_modes(mode):
     """The 9.2k-bus step with FP64 trailing updates (mode 2) and with the FP64 re-check of failed
@@ -88,10 +105,32 @@ def test_al_step_cholesky_modes(mode):
         assert inf["cholesky_fp64"] == inf["factorisations"]
     else:
         assert (inf["inertia_tries"] > 0) <= inf["cholesky_fp64"] <= inf["factorisations"]
-    # a fresh start: delta = 0, then a bisection over the other (at most 24) and a redo
-    assert 1 <= inf["factorisations"] <= 1 + 5 + 1
+    # a fresh start: delta = 0, then a bisection over the other 24 candidates
+    assert inf["factorisations"] == search_factorisations(inf["inertia_tries"])
     with pytest.raises(P.OPFError):
         ctx.set_cholesky_mode(3)
+
+
+def test_al_step_carried_delta():
+    """The inertia search from a carried-over delta tries the candidates in turn and reaches the
+    same delta as a fresh start: from delta / 100 on the 9.2k grid, two raises, three
+    factorisations (the fresh start's bisection took search_factorisations(t) for its t)."""
+    net = synth.workload("large9200")
+    on, x, u, al, st = setup(net, mu=0.1)
+    al_dev = {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in al.items()}
+    out = []
+    for start in (0.0, None):
+        ctx = P.OPFContext(net)
+        xg, _ = ctx.powerflow(dev(u))
+        state = {k: dev(v) for k, v in st.items() if k != "mu"}
+        state.update(u=dev(u), s=dev(al["s"]), x=xg, mu=0.1)
+        d0 = start if start is not None else out[0][0] / 100.0
+        du, ds, inf = ctx.al_step(al_dev, state, delta_start=d0)
+        out.append((inf["delta"], inf["inertia_tries"], inf["factorisations"], du.cpu().numpy()))
+    (d_f, t_f, n_f, du_f), (d_c, t_c, n_c, du_c) = out
+    assert d_f > 0.0 and n_f == search_factorisations(t_f) < t_f + 1
+    assert abs(d_c - d_f) <= 1e-12 * d_f and t_c == 2 and n_c == 3
+    assert rel(du_c, du_f) < 1e-9
 
 
 @pytest.mark.parametrize("name", ["medium1400", "large9200"])
