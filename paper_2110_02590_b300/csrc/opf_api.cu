@@ -982,6 +982,7 @@ opf_status opf_reduced_gradient(opf_ctx* c, const opf_al_params* p, double* F, d
 
 static opf_status ensure_scratch(opf_ctx* c, size_t doubles) {
   if (c->scratch_bytes >= doubles * sizeof(double)) return OPF_OK;
+  c->z_gen = -1;
   CK(cudaStreamSynchronize(c->stream));
   if (c->scratch) cudaFree(c->scratch);
   c->scratch = nullptr;
@@ -1079,6 +1080,7 @@ static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hes
   const bool sym = c->hess_sym && !plain && col0 == 0 && ncol == nu && !asym && !jac_only;
   c->sym_now = sym;
   if (plain) {
+    c->z_gen = -1;
     launches = launch_hvp_plain(c, H, col0, col0 + ncol, c->scratch);
   } else if (split) {
     launch_hvp_split(c, C, H);
@@ -1325,6 +1327,7 @@ opf_status opf_reduced_hessian_batched(opf_ctx* const* ctxs, int n, const opf_al
   CK(cudaEventRecord(c0->ev[1], st));
   size_t smem = 0;
   for (int k = 0; k < n; k++) smem = std::max(smem, hvp_smem_bytes(args[k], C));
+  c0->z_gen = -1;
   launch_hvp_batch(st, C, d_args, d_tiles, ntot, d_counter, c0->scratch, stride, grid, smem);
   c0->launches++;
   int launches = 1;

@@ -132,6 +132,12 @@ struct HvpArgs {
   // rest from the transposed entries
   int sym;
   int* tstart;
+  // 1: each tile's slab already holds its first adjoint Z from the previous
+  // launch with the same tiling and factors (one tile per CTA, each with its
+  // own slab): phases (0)-(2) are skipped.  Z = G_x^{-1} G_u W does not depend
+  // on the second-order weights, so a QP's Hessians at one linearisation
+  // point share it.
+  int zreuse;
 };
 
 // Shared memory of the trailing dense block's LU (the whole block; larger blocks
@@ -535,6 +541,13 @@ struct opf_ctx {
   int chol_mode = 1;               // dense Cholesky trailing updates (opf_set_cholesky_mode)
   bool hess_sym = true;            // full Hessians by symmetry (opf_set_hessian_symmetry)
   bool sym_now = false;            // set for the duration of one such launch
+  // first-adjoint reuse across split Hessian launches (HvpArgs::zreuse): allowed
+  // by the caller (z_reuse), valid while the factors (lu_gen) and the tile width
+  // are those of the last split launch (z_gen, z_C); other users of the
+  // scratch clear z_gen
+  bool z_reuse = false;
+  long long lu_gen = 0, z_gen = -1;
+  int z_C = 0;
   int oz_engine = 0;               // emulated updates: 0 tcgen05 for large ones, 1 mma.sync, 2 tcgen05 (opf_set_update_engine)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;

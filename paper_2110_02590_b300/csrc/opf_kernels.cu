@@ -1291,192 +1291,198 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
         s_col[threadIdx.x] = pos >= a.col_end ? NOCOL : pos;
       }
     }
-    // (0) right-hand side B = -G_u W, W = unit directions of the tile's columns:
-    // first the rows it touches (marked), then, once the first solve's reach is
-    // known, the slab is cleared on the reached rows and the trailing block only
-    // (the U sweep starts the other rows from zero through the mask, so the slab
-    // is neither cleared nor read there), then the values
-    if (prune)
-      for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
-    __syncthreads();
-    auto rhs = [&](bool values) {
-      // Z[r][c] = v (set) or -= v; without values, mark row r
-      auto put = [&](int r, int c, double v, bool set) {
-        if (values) {
-          double& z = Z[(size_t)r * C + c];
-          z = set ? v : z - v;
-        } else if (prune && r < r0) {
-          atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+    if (a.zreuse) {  // the slab holds this tile's first adjoint from the previous launch
+      __syncthreads();
+      hvp_stamp(a, tile, 1);
+      hvp_stamp(a, tile, 2);
+    } else {
+      // (0) right-hand side B = -G_u W, W = unit directions of the tile's columns:
+      // first the rows it touches (marked), then, once the first solve's reach is
+      // known, the slab is cleared on the reached rows and the trailing block only
+      // (the U sweep starts the other rows from zero through the mask, so the slab
+      // is neither cleared nor read there), then the values
+      if (prune)
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
+      __syncthreads();
+      auto rhs = [&](bool values) {
+        // Z[r][c] = v (set) or -= v; without values, mark row r
+        auto put = [&](int r, int c, double v, bool set) {
+          if (values) {
+            double& z = Z[(size_t)r * C + c];
+            z = set ? v : z - v;
+          } else if (prune && r < r0) {
+            atomicOr(&s_mask[r >> 5], 1u << (r & 31));
+          }
+        };
+        for (int c = threadIdx.x; c < C; c += blockDim.x) {
+          const int j = s_col[c];
+          if (j < 0) continue;
+          const int k = a.ubus[j];
+          if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
+            put(n.pth[k], c, 1.0, true);
+            continue;
+          }
+          for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
+            const int4 ar = n.adjrec[q];
+            if (ar.y >= 0) put(ar.y, c, values ? E[(size_t)q * ADJ_W + E_POV] : 0.0, false);
+            if (ar.x >= 0) put(ar.x, c, values ? E[(size_t)q * ADJ_W + E_QOV] : 0.0, false);
+          }
+          if (n.type[k] == PV) put(n.pth[k], c, values ? bw[6 * nb + k] : 0.0, false);
         }
       };
-      for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        const int j = s_col[c];
-        if (j < 0) continue;
-        const int k = a.ubus[j];
-        if (j >= 1 + n.npv) {  // p of a PV unit: dg/dp = -e_{P_k}
-          put(n.pth[k], c, 1.0, true);
-          continue;
-        }
-        for (int q = n.adj_ptr[k]; q < n.adj_ptr[k + 1]; q++) {
-          const int4 ar = n.adjrec[q];
-          if (ar.y >= 0) put(ar.y, c, values ? E[(size_t)q * ADJ_W + E_POV] : 0.0, false);
-          if (ar.x >= 0) put(ar.x, c, values ? E[(size_t)q * ADJ_W + E_QOV] : 0.0, false);
-        }
-        if (n.type[k] == PV) put(n.pth[k], c, values ? bw[6 * nb + k] : 0.0, false);
-      }
-    };
-    rhs(false);
-    __syncthreads();
-    // (1) Z = L^{-1} B.  The solution is nonzero only on the elimination-tree
-    // ancestors of the right-hand side's rows: mark them, list them in
-    // ascending order, and let one warp solve those rows one after another
-    // (no block-wide barrier); the trailing block follows as usual.
-    int nl = a.list_cap + 1;
-    if (prune) {
-      for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-        unsigned bits = s_mask[w];
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          bits &= bits - 1;
-          int x = n.eparent[w * 32 + b];
-          while (x >= 0 && x < r0) {  // parents increase: the walk ends
-            const unsigned m = 1u << (x & 31);
-            if (atomicOr(&s_mask[x >> 5], m) & m) break;  // the row's walk is someone else's
-            x = n.eparent[x];
-          }
-        }
-      }
+      rhs(false);
       __syncthreads();
-      if (warp == 0) {
-        int base = 0;
-        for (int w0 = 0; w0 < nwords; w0 += 32) {
-          const int w = w0 + lane;
-          const unsigned bits = w < nwords ? s_mask[w] : 0u;
-          const int cnt = __popc(bits);
-          int incl = cnt;
-#pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
-          }
-          int pos = base + incl - cnt;
-          if (w < nwords) s_pre[w] = pos;
-          unsigned bb = bits;
-          while (bb) {
-            const int b = __ffs(bb) - 1;
-            bb &= bb - 1;
-            if (pos < a.list_cap) s_list[pos] = w * 32 + b;
-            pos++;
-          }
-          base += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) s_nl = base;
-      }
-      __syncthreads();
-      nl = s_nl;
-    }
-    const bool reach = nl <= a.list_cap;  // the first solve and the U sweep see the reach only
-    if (reach) {
-      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x) Z[(size_t)s_list[idx / C] * C + idx % C] = 0.0;
-      for (size_t k = (size_t)r0 * C + threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
-    } else {
-      for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
-    }
-    __syncthreads();
-    rhs(true);
-    __syncthreads();
-    const int ngrp = blockDim.x / C, g = threadIdx.x / C, nwarp = blockDim.x >> 5;
-    const double* __restrict__ Vl = a.LU;
-    if (nl <= a.zs_cap) {
-      // right-looking over the reached rows with their values in shared
-      // memory: once row t is final, every lane group subtracts its column's
-      // multiples from the later reached rows (all reached: ancestors of t),
-      // one barrier per row; rows of the trailing block are left to it.
-      const int col = threadIdx.x % C;
-      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
-        s_zs[idx] = Z[(size_t)s_list[idx / C] * C + idx % C];
-      int e0 = 0, e1 = 0;
-      if (nl > 0) {
-        e0 = n.lcol_ptr[s_list[0]];
-        e1 = n.lcol_ptr[s_list[0] + 1];
-      }
-      __syncthreads();
-      for (int t = 0; t < nl; t++) {
-        int en0 = 0, en1 = 0;
-        if (t + 1 < nl) {  // the next column's extent, in flight during this one
-          const int in = s_list[t + 1];
-          en0 = n.lcol_ptr[in];
-          en1 = n.lcol_ptr[in + 1];
-        }
-        const double xt = s_zs[(size_t)t * C + col];
-        for (int e = e0 + g; e < e1; e += ngrp) {
-          const int2 rq = __ldg(n.lcol + e);
-          if (rq.x < r0) {
-            const int w = rq.x >> 5;
-            const unsigned m = s_mask[w];
-            const int pos = s_pre[w] + __popc(m & ((1u << (rq.x & 31)) - 1u));
-            s_zs[(size_t)pos * C + col] -= Vl[rq.y] * xt;
+      // (1) Z = L^{-1} B.  The solution is nonzero only on the elimination-tree
+      // ancestors of the right-hand side's rows: mark them, list them in
+      // ascending order, and let one warp solve those rows one after another
+      // (no block-wide barrier); the trailing block follows as usual.
+      int nl = a.list_cap + 1;
+      if (prune) {
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+          unsigned bits = s_mask[w];
+          while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            int x = n.eparent[w * 32 + b];
+            while (x >= 0 && x < r0) {  // parents increase: the walk ends
+              const unsigned m = 1u << (x & 31);
+              if (atomicOr(&s_mask[x >> 5], m) & m) break;  // the row's walk is someone else's
+              x = n.eparent[x];
+            }
           }
         }
-        e0 = en0;
-        e1 = en1;
         __syncthreads();
-      }
-      for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
-        Z[(size_t)s_list[idx / C] * C + idx % C] = s_zs[idx];
-    }
-    if (nl > a.zs_cap && nl <= a.list_cap) {
-      // the same with the reached values in the slab
-      const int col = threadIdx.x % C;
-      const double* __restrict__ V = Vl;
-      int pn0 = 0, pn1 = 0;
-      if (nl > 0) {
-        pn0 = n.rp[s_list[0]];
-        pn1 = n.dp[s_list[0]];
-      }
-      for (int t = 0; t < nl; t++) {
-        const int i = s_list[t], p0 = pn0, p1 = pn1;
-        if (t + 1 < nl) {  // the next row's extent, in flight during this row
-          pn0 = n.rp[s_list[t + 1]];
-          pn1 = n.dp[s_list[t + 1]];
+        if (warp == 0) {
+          int base = 0;
+          for (int w0 = 0; w0 < nwords; w0 += 32) {
+            const int w = w0 + lane;
+            const unsigned bits = w < nwords ? s_mask[w] : 0u;
+            const int cnt = __popc(bits);
+            int incl = cnt;
+  #pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, incl, off);
+              if (lane >= off) incl += y;
+            }
+            int pos = base + incl - cnt;
+            if (w < nwords) s_pre[w] = pos;
+            unsigned bb = bits;
+            while (bb) {
+              const int b = __ffs(bb) - 1;
+              bb &= bb - 1;
+              if (pos < a.list_cap) s_list[pos] = w * 32 + b;
+              pos++;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+          }
+          if (lane == 0) s_nl = base;
         }
-        double v0 = 0.0, v1 = 0.0;
-        int p = p0 + g;
-        for (; p + ngrp < p1; p += 2 * ngrp) {
-          const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + ngrp);
-          const bool b0 = (s_mask[c0 >> 5] >> (c0 & 31)) & 1u, b1 = (s_mask[c1 >> 5] >> (c1 & 31)) & 1u;
-          if (b0) v0 -= V[p] * Z[(size_t)c0 * C + col];
-          if (b1) v1 -= V[p + ngrp] * Z[(size_t)c1 * C + col];
-        }
-        if (p < p1) {
-          const int c0 = __ldg(n.ci + p);
-          if ((s_mask[c0 >> 5] >> (c0 & 31)) & 1u) v0 -= V[p] * Z[(size_t)c0 * C + col];
-        }
-        double v = v0 + v1;
-#pragma unroll
-        for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane < C) s_part[t & 1][warp][lane] = v;
-        // the row's right-hand side, read before any warp overwrites it
-        const double zi = lane < C ? Z[(size_t)i * C + lane] : 0.0;
         __syncthreads();
-        if (lane < C) {
-          double sum = zi;
-          for (int w = 0; w < nwarp; w++) sum += s_part[t & 1][w][lane];
-          Z[(size_t)i * C + lane] = sum;
-        }
-        __syncwarp();
+        nl = s_nl;
       }
-    }
-    if (nl <= a.list_cap) {
+      const bool reach = nl <= a.list_cap;  // the first solve and the U sweep see the reach only
+      if (reach) {
+        for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x) Z[(size_t)s_list[idx / C] * C + idx % C] = 0.0;
+        for (size_t k = (size_t)r0 * C + threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+      } else {
+        for (size_t k = threadIdx.x; k < (size_t)n.nx * C; k += blockDim.x) Z[k] = 0.0;
+      }
       __syncthreads();
-      sweep<C, true, false>(n, a.LU, a.invdiag, Z, s_mask, s_tb);
-    } else {
-      sweep<C, true, false>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
+      rhs(true);
+      __syncthreads();
+      const int ngrp = blockDim.x / C, g = threadIdx.x / C, nwarp = blockDim.x >> 5;
+      const double* __restrict__ Vl = a.LU;
+      if (nl <= a.zs_cap) {
+        // right-looking over the reached rows with their values in shared
+        // memory: once row t is final, every lane group subtracts its column's
+        // multiples from the later reached rows (all reached: ancestors of t),
+        // one barrier per row; rows of the trailing block are left to it.
+        const int col = threadIdx.x % C;
+        for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
+          s_zs[idx] = Z[(size_t)s_list[idx / C] * C + idx % C];
+        int e0 = 0, e1 = 0;
+        if (nl > 0) {
+          e0 = n.lcol_ptr[s_list[0]];
+          e1 = n.lcol_ptr[s_list[0] + 1];
+        }
+        __syncthreads();
+        for (int t = 0; t < nl; t++) {
+          int en0 = 0, en1 = 0;
+          if (t + 1 < nl) {  // the next column's extent, in flight during this one
+            const int in = s_list[t + 1];
+            en0 = n.lcol_ptr[in];
+            en1 = n.lcol_ptr[in + 1];
+          }
+          const double xt = s_zs[(size_t)t * C + col];
+          for (int e = e0 + g; e < e1; e += ngrp) {
+            const int2 rq = __ldg(n.lcol + e);
+            if (rq.x < r0) {
+              const int w = rq.x >> 5;
+              const unsigned m = s_mask[w];
+              const int pos = s_pre[w] + __popc(m & ((1u << (rq.x & 31)) - 1u));
+              s_zs[(size_t)pos * C + col] -= Vl[rq.y] * xt;
+            }
+          }
+          e0 = en0;
+          e1 = en1;
+          __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < nl * C; idx += blockDim.x)
+          Z[(size_t)s_list[idx / C] * C + idx % C] = s_zs[idx];
+      }
+      if (nl > a.zs_cap && nl <= a.list_cap) {
+        // the same with the reached values in the slab
+        const int col = threadIdx.x % C;
+        const double* __restrict__ V = Vl;
+        int pn0 = 0, pn1 = 0;
+        if (nl > 0) {
+          pn0 = n.rp[s_list[0]];
+          pn1 = n.dp[s_list[0]];
+        }
+        for (int t = 0; t < nl; t++) {
+          const int i = s_list[t], p0 = pn0, p1 = pn1;
+          if (t + 1 < nl) {  // the next row's extent, in flight during this row
+            pn0 = n.rp[s_list[t + 1]];
+            pn1 = n.dp[s_list[t + 1]];
+          }
+          double v0 = 0.0, v1 = 0.0;
+          int p = p0 + g;
+          for (; p + ngrp < p1; p += 2 * ngrp) {
+            const int c0 = __ldg(n.ci + p), c1 = __ldg(n.ci + p + ngrp);
+            const bool b0 = (s_mask[c0 >> 5] >> (c0 & 31)) & 1u, b1 = (s_mask[c1 >> 5] >> (c1 & 31)) & 1u;
+            if (b0) v0 -= V[p] * Z[(size_t)c0 * C + col];
+            if (b1) v1 -= V[p + ngrp] * Z[(size_t)c1 * C + col];
+          }
+          if (p < p1) {
+            const int c0 = __ldg(n.ci + p);
+            if ((s_mask[c0 >> 5] >> (c0 & 31)) & 1u) v0 -= V[p] * Z[(size_t)c0 * C + col];
+          }
+          double v = v0 + v1;
+  #pragma unroll
+          for (int off = C; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          if (lane < C) s_part[t & 1][warp][lane] = v;
+          // the row's right-hand side, read before any warp overwrites it
+          const double zi = lane < C ? Z[(size_t)i * C + lane] : 0.0;
+          __syncthreads();
+          if (lane < C) {
+            double sum = zi;
+            for (int w = 0; w < nwarp; w++) sum += s_part[t & 1][w][lane];
+            Z[(size_t)i * C + lane] = sum;
+          }
+          __syncwarp();
+        }
+      }
+      if (nl <= a.list_cap) {
+        __syncthreads();
+        sweep<C, true, false>(n, a.LU, a.invdiag, Z, s_mask, s_tb);
+      } else {
+        sweep<C, true, false>(n, a.LU, a.invdiag, Z, nullptr, s_tb);
+      }
+      hvp_stamp(a, tile, 1);
+      // (2) U sweep
+      sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb, nullptr, reach ? s_mask : nullptr);
+      hvp_stamp(a, tile, 2);
     }
-    hvp_stamp(a, tile, 1);
-    // (2) U sweep
-    sweep<C, false, true>(n, a.LU, a.invdiag, Z, nullptr, s_tb, nullptr, reach ? s_mask : nullptr);
-    hvp_stamp(a, tile, 2);
     // (2b) on request, the reduced constraint Jacobian of the tile's columns,
     // J W = d_x c Z + d_u c W (Sec. III-B), from the first adjoint Z just
     // computed: the |S|^2 rows of both branch ends and the PQ voltages here,
@@ -1949,6 +1955,7 @@ void launch_lu_kernels(opf_ctx* c) {
 void launch_lu(opf_ctx* c) {
   cudaGraphLaunch(c->lu_exec, c->stream);
   c->launches += c->lu_graph_kernels;
+  c->lu_gen++;  // new factors: first adjoints kept in the Hessian scratch are void
 }
 
 void launch_solve1(opf_ctx* c, const double* b, double* out, bool transposed, double scale) {
@@ -2127,6 +2134,7 @@ static void launch_hvp_t(opf_ctx* c, double* H, int grid, int first_tile, int ti
   a.ntiles = ntiles;
   a.first_tile = first_tile;
   a.tile_step = tile_step;
+  c->z_gen = -1;  // CTAs reuse their slabs across tiles
   const size_t sm = hvp_smem_bytes(a, C);
   if (c->hvp_threads == 512)
     hvp_tile_kernel<C, 512><<<grid, 512, sm, c->stream>>>(a);
@@ -2202,6 +2210,7 @@ HvpArgs make_hvp_args(opf_ctx* c, int C, double* H, int col0, int col_end, bool 
   a.col_end = col_end;
   a.sym = (full && c->sym_now) ? 1 : 0;
   a.tstart = c->tstart;
+  a.zreuse = 0;
   // shared-memory layout of the first solve's reach (no pruning when the mask
   // and list would take more than half of the budget)
   const int nwords = (c->dn.r0 + 31) / 32;
@@ -2237,6 +2246,9 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   a2.ntiles = n2;
   a2.scratch = c->scratch + a1.stride * (size_t)n1;
   if (a2.stamps) a2.stamps += (size_t)n1 * 8;
+  a1.zreuse = a2.zreuse = (c->z_reuse && c->z_gen == c->lu_gen && c->z_C == C) ? 1 : 0;
+  c->z_gen = c->lu_gen;
+  c->z_C = C;
   const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
   const int per_sm = std::max(1, n1 / c->sm_count);
   cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (4 + kSplitMaxSm), c->stream);

@@ -1311,6 +1311,13 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
   SCK(cudaMemcpyAsync(w->s0, st->s, m * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   SCK(cudaMemcpyAsync(w->x0, st->x, nx * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   pt.s = w->s0;  // the Hessian's first-order weights stay those of w_t
+  // every Hessian of this QP is taken at w_t: after the first, the tiles start
+  // from the first adjoints their slabs kept (the factors do not change until
+  // the trial power flows after the iterations)
+  struct ZReuseOff {
+    opf_ctx* c;
+    ~ZReuseOff() { c->z_reuse = false; }
+  } z_reuse_off{c};
   double mu = st->mu, delta = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0, kkt_first = 0.0, ap_min = 1.0;
   float ms_hess = 0.f, ms_chol = 0.f;
@@ -1327,6 +1334,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     opf_hess_info hi;
     rc = opf_reduced_hessian(c, &p0, &ho, w->S, &hi);
     if (rc) return rc;
+    c->z_reuse = true;
     ms_hess += hi.ms_total;
     sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
     c->launches++;
@@ -1364,6 +1372,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     opf_hess_info hi;
     rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
     if (rc) return rc;
+    c->z_reuse = true;
     ms_hess += hi.ms_total;
     sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
     // r = -grad_u psi - J^T v
