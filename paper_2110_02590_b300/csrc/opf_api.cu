@@ -675,6 +675,9 @@ static opf_status load_impl(opf_ctx* c, const opf_network_desc* d) {
   TRY(dalloc(c, &c->dFx, nx));
   TRY(dalloc(c, &c->dFu, h.nu));
   TRY(dalloc(c, &c->lam, nx));
+  TRY(dalloc(c, &c->dFx_w, nx));
+  TRY(dalloc(c, &c->dFu_w, h.nu));
+  TRY(dalloc(c, &c->lam_w, nx));
   TRY(dalloc(c, &c->btab, TAB_ROWS * (size_t)nl));
   TRY(dalloc(c, &c->busw, 8 * (size_t)nb));
   TRY(dalloc(c, &c->adjE, ADJ_W * 2 * (size_t)nl));
@@ -1068,7 +1071,12 @@ static opf_status hessian_impl(opf_ctx* c, const opf_al_params* p, const opf_hes
     c->stamps_on = true;
   }
   CK(cudaEventRecord(c->ev[0], st));
-  if (!(o && o->reuse_first_order)) launch_first_order(c, p, nullptr);
+  if (!(o && o->reuse_first_order)) {
+    if (c->fo_reuse)
+      launch_omega(c, p);
+    else
+      launch_first_order(c, p, nullptr);
+  }
   launch_hess_prep(c, p->sigma_f);
   CK(cudaEventRecord(c->ev[1], st));
   int launches = 0;

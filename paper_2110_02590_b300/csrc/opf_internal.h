@@ -199,6 +199,7 @@ bool launch_hvp_batch(cudaStream_t st, int C, const HvpArgs* args, const int2* t
 // J^T w for the reduced constraint Jacobian: the adjoint gradient with first-order
 // weights w and no cost (sigma_f = 0); needs the flows of the current state.
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out);
+void launch_omega(opf_ctx* c, const opf_al_params* p);  // omega (and phi') alone, from the last first order
 struct StepWork;
 void free_step_work(opf_ctx* c);
 // KKT errors of a barrier subproblem at st with gradient (gu, gs) (opf_al.cu):
@@ -517,6 +518,7 @@ struct opf_ctx {
   double *Pbus = nullptr, *Qbus = nullptr;
   double *cvec = nullptr, *phid = nullptr, *omega = nullptr;
   double *dFx = nullptr, *dFu = nullptr, *lam = nullptr;
+  double *dFx_w = nullptr, *dFu_w = nullptr, *lam_w = nullptr;  // launch_weighted_grad's own
   double *btab = nullptr;         // [TAB_ROWS nl] per-branch Hessian table
   double *busw = nullptr;         // [8 nb]: kQ, kP, diag v, diag p, dQi/dvi, dQi/dthi, dPi/dvi, dPi/dthi
   double* adjE = nullptr;         // [2 nl][ADJ_W] per-adjacency coefficients of the HVP gathers
@@ -548,6 +550,10 @@ struct opf_ctx {
   bool z_reuse = false;
   long long lu_gen = 0, z_gen = -1;
   int z_C = 0;
+  // set by a caller whose Hessians share the state and first-order weights and
+  // differ in omega only (the tracking QP): the Hessian entry refreshes omega
+  // and keeps c, phi', lambda of the previous call
+  bool fo_reuse = false;
   int oz_engine = 0;               // emulated updates: 0 tcgen05 for large ones, 1 mma.sync, 2 tcgen05 (opf_set_update_engine)
   void* batch_buf = nullptr;       // batched-Hessian argument and tile tables (grown on demand)
   size_t batch_bytes = 0;

@@ -2033,14 +2033,29 @@ void launch_eval_F(opf_ctx* c, const opf_al_params* p, double* F_out) {
   cudaMemcpyAsync(F_out, c->scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
 }
 
+// (in buffers of its own: the first-order adjoint lambda of the last Hessian or
+// gradient stays valid)
 void launch_weighted_grad(opf_ctx* c, const double* w, double* out) {
   const DevNet& n = c->dn;
   c->launches++;
-  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->u, w, c->Pbus, c->pd, 0.0, c->dFx, c->dFu,
+  dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->u, w, c->Pbus, c->pd, 0.0, c->dFx_w, c->dFu_w,
                                                         c->endflow);
-  launch_solve1(c, c->dFx, c->lam, true, -1.0);
+  launch_solve1(c, c->dFx_w, c->lam_w, true, -1.0);
   c->launches++;
-  grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->lam, c->dFu, out, c->endflow);
+  grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->lam_w, c->dFu_w, out, c->endflow);
+}
+
+// omega (and phi', unchanged when the first-order weights are) of p at the
+// state of the last launch_first_order: its flows, constraint values and lambda
+// stay.
+void launch_omega(opf_ctx* c, const opf_al_params* p) {
+  const DevNet& n = c->dn;
+  const int mm = std::max(n.m, n.ng);
+  cudaMemsetAsync(c->scal, 0, 8 * sizeof(double), c->stream);
+  al_weights_kernel<<<nblk(mm, 256), 256, 0, c->stream>>>(
+      n, c->cvec, p->sigma_c, p->y, p->s, p->omega, p->rho, p->sigma_f, c->Pbus, c->u, c->pd,
+      c->c0, c->phid, nullptr, c->omega, c->scal);
+  c->launches++;
 }
 
 void launch_grad_u(opf_ctx* c, double* gu) {

@@ -1314,9 +1314,11 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
   // every Hessian of this QP is taken at w_t: after the first, the tiles start
   // from the first adjoints their slabs kept (the factors do not change until
   // the trial power flows after the iterations)
+  // and the same state and first-order weights (pt: y, s_t): after the first,
+  // the Hessian entry refreshes omega only (launch_omega)
   struct ZReuseOff {
     opf_ctx* c;
-    ~ZReuseOff() { c->z_reuse = false; }
+    ~ZReuseOff() { c->z_reuse = c->fo_reuse = false; }
   } z_reuse_off{c};
   double mu = st->mu, delta = (o && o->delta_start > 0.0) ? o->delta_start : 0.0;
   double e_mu = 0.0, e_0 = 0.0, ap = 0.0, ad = 0.0, kkt_first = 0.0, ap_min = 1.0;
@@ -1334,7 +1336,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     opf_hess_info hi;
     rc = opf_reduced_hessian(c, &p0, &ho, w->S, &hi);
     if (rc) return rc;
-    c->z_reuse = true;
+    c->z_reuse = c->fo_reuse = true;
     ms_hess += hi.ms_total;
     sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
     c->launches++;
@@ -1372,7 +1374,7 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     opf_hess_info hi;
     rc = opf_reduced_hessian(c, &ps, &ho, w->S, &hi);
     if (rc) return rc;
-    c->z_reuse = true;
+    c->z_reuse = c->fo_reuse = true;
     ms_hess += hi.ms_total;
     sym_diag_kernel<<<dim3(nblk(nu, 32), nblk(nu, 32)), 256, 0, stream>>>(w->S, nu, w->sig_u);
     // r = -grad_u psi - J^T v
