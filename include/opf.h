@@ -692,7 +692,10 @@ opf_status opf_al_step_batched(opf_ctx* const* ctxs, int n, const opf_al_params*
  * grad_qd [n][n_bus] (total derivatives through g and the slack generation),
  * grad_s [n][m] = -phi'.  Row-major device arrays, scenario k at offset k times
  * the row length; pd/qd NULL = nominal loads; x_out [n][n_x] (may be NULL)
- * receives the states.  p: sigma_f, rho, sigma_c, y shared by the scenarios
+ * receives the states; with x0 == x_out each scenario starts from its own row
+ * of x_out instead (for example the states of a previous call at the same
+ * inputs, which converge at once: one factorisation, no Newton iteration, as
+ * an autograd backward pass needs).  p: sigma_f, rho, sigma_c, y shared by the scenarios
  * (its s and omega are ignored).  The scenarios are spread over a pool of nctx
  * contexts of that network, each on its own stream and host thread (give each
  * its own stream with opf_set_stream for the GPU to overlap them); the outputs

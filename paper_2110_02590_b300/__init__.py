@@ -342,10 +342,12 @@ def al_step_batched(ctxs, als, states, loads=None, block_k=0, delta_start=0.0):
     return out, list(stat), {k: getattr(binfo, k) for k, _ in BatchInfo._fields_}
 
 
-def objective_batched(ctxs, al, u, pd, qd, s, x0, grads=False):
+def objective_batched(ctxs, al, u, pd, qd, s, x0, grads=False, x_out=None):
     """F (and with grads=True the adjoint gradients w.r.t. u, pd, qd, s) for the scenarios
     u [n, n_u], pd/qd [n, n_bus], s [n, m] of one network, spread over the contexts `ctxs`
-    (each should own a stream: OPFContext.use_own_stream).  Returns a dict of cuda tensors."""
+    (each should own a stream: OPFContext.use_own_stream).  x_out [n, n_x] (optional)
+    receives the states; passing the same tensor as x0 starts each scenario from its own row.
+    Returns a dict of cuda tensors."""
     import torch
     c0 = ctxs[0]
     n = u.shape[0]
@@ -356,13 +358,17 @@ def objective_batched(ctxs, al, u, pd, qd, s, x0, grads=False):
     out = dict(F=z(n))
     if grads:
         out.update(grad_u=z(n, c0.nu), grad_pd=z(n, c0.net.n_bus), grad_qd=z(n, c0.net.n_bus), grad_s=z(n, c0.m))
-    for t in (u, pd, qd, s, x0):
+    for t in (u, pd, qd, s, x0, x_out):
         if t is not None:
             c0._dev(t)
+    if x_out is not None and tuple(x_out.shape) != (n, c0.nx):
+        raise ValueError(f"x_out must have shape ({n}, {c0.nx}), got {tuple(x_out.shape)}")
+    if x0 is not None and x0 is not x_out and x0.numel() != c0.nx:
+        raise ValueError(f"x0 must hold n_x = {c0.nx} values (or be x_out itself)")
     hs = (C.c_void_p * len(ctxs))(*[c.h.value for c in ctxs])
     stat = (C.c_int * max(1, n))()
     rc = lib().opf_objective_batched(hs, len(ctxs), n, C.byref(p), _ptr(u), _ptr(pd), _ptr(qd), _ptr(s), _ptr(x0),
-                                     None, _ptr(out["F"]), _ptr(out.get("grad_u")), _ptr(out.get("grad_pd")),
+                                     _ptr(x_out), _ptr(out["F"]), _ptr(out.get("grad_u")), _ptr(out.get("grad_pd")),
                                      _ptr(out.get("grad_qd")), _ptr(out.get("grad_s")), stat)
     if rc != 0:
         raise OPFError(rc, "opf_objective_batched")

@@ -1,10 +1,11 @@
 """Differentiable reduced AL objective: F(u, pd, qd, s) as a torch.autograd.Function.
 
 Forward: Newton-Raphson power flow at (u, pd, qd) and the value of the scaled
-AL functional F (Sec. IV-A).  Backward: the power flow is re-solved from the
-saved inputs (the state x is recomputed, not stored across the batch), then the
-adjoint gradient (Prop. 1) gives dF/du = d_u F + lambda^T G_u, dF/dpd and
-dF/dqd (total derivatives through g and the slack generation) and dF/ds = -phi'.
+AL functional F (Sec. IV-A); the states x [B, n_x] are kept for the backward
+pass.  Backward: each scenario's power flow restarts from its kept state (it
+converges at once: the factors at x, no Newton iteration), then the adjoint
+gradient (Prop. 1) gives dF/du = d_u F + lambda^T G_u, dF/dpd and dF/dqd
+(total derivatives through g and the slack generation) and dF/ds = -phi'.
 All arithmetic runs in libopf through the C ABI (opf_objective_batched: the
 power flows and adjoint solves of the scenarios spread over a pool of
 contexts of the network, each on its own stream); this module only moves
@@ -23,10 +24,12 @@ from paper_2110_02590_b300 import OPFContext, objective_batched
 class _ReducedObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u, pd, qd, s, obj):
+        x = torch.empty((u.shape[0], obj.x0.numel()), dtype=torch.float64, device=u.device)
         out = objective_batched(obj.pool, obj.al, u.detach().contiguous(), pd.detach().contiguous(),
-                                qd.detach().contiguous(), s.detach().contiguous(), obj.x0, grads=False)
+                                qd.detach().contiguous(), s.detach().contiguous(), obj.x0, grads=False, x_out=x)
         ctx.save_for_backward(u, pd, qd, s)
         ctx.obj = obj
+        ctx.x = x  # the converged states (restart points of the backward pass)
         return out["F"]
 
     @staticmethod
@@ -34,7 +37,7 @@ class _ReducedObjective(torch.autograd.Function):
         u, pd, qd, s = ctx.saved_tensors
         obj = ctx.obj
         g = objective_batched(obj.pool, obj.al, u.detach().contiguous(), pd.detach().contiguous(),
-                              qd.detach().contiguous(), s.detach().contiguous(), obj.x0, grads=True)
+                              qd.detach().contiguous(), s.detach().contiguous(), ctx.x, grads=True, x_out=ctx.x)
         w = gF.reshape(-1, 1)
         return w * g["grad_u"], w * g["grad_pd"], w * g["grad_qd"], w * g["grad_s"], None
 

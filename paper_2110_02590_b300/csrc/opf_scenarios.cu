@@ -4,7 +4,8 @@
 // own stream, driven by its own host thread, so the GPU overlaps the
 // scenarios' latency-bound power flows and solves (a 2,000-bus power flow
 // leaves most of the GPU idle).  Used by the autograd objective's forward and
-// backward passes (the states are recomputed, not stored).
+// backward passes (the backward pass restarts each scenario from the state the
+// forward pass returned, x0 == x_out).
 #include <algorithm>
 #include <atomic>
 #include <string>
@@ -39,6 +40,8 @@ extern "C" opf_status opf_objective_batched(opf_ctx* const* ctxs, int nctx, int 
       }
   }
   const size_t nu = c0->h.nu, nb = c0->h.nb, nx = c0->h.nx, m = c0->h.m;
+  // x0 == x_out: every scenario starts from its own row of x_out
+  const bool own_start = x_out && x0 == x_out;
   std::vector<opf_status> st(n, OPF_OK);
   std::vector<std::string> msg(n);
   std::atomic<int> next(0);
@@ -57,9 +60,11 @@ extern "C" opf_status opf_objective_batched(opf_ctx* const* ctxs, int nctx, int 
     }
     for (int k = next++; k < n; k = next++) {
       double* xk = x_out ? x_out + k * nx : x;
-      opf_status r = cudaMemcpyAsync(xk, x0, nx * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
-                         ? OPF_OK
-                         : OPF_ECUDA;
+      opf_status r = OPF_OK;
+      if (!own_start)
+        r = cudaMemcpyAsync(xk, x0, nx * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
+                ? OPF_OK
+                : OPF_ECUDA;
       if (r == OPF_OK)
         r = opf_powerflow(c, u + k * nu, pd ? pd + k * nb : nullptr, qd ? qd + k * nb : nullptr, xk, nullptr,
                           nullptr);
