@@ -1251,7 +1251,9 @@ __device__ __forceinline__ void hvp_stamp(const HvpArgs& a, int tile, int k) {
   }
 }
 
-template <int C>
+// ZR: the slab already holds the tile's first adjoint (HvpArgs::zreuse; a
+// separate instantiation, so the ordinary tile keeps its code unchanged)
+template <int C, bool ZR = false>
 __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) {
   hvp_stamp(a, tile, 0);
   const DevNet& n = a.n;
@@ -1291,7 +1293,7 @@ __device__ __forceinline__ void hvp_tile(const HvpArgs& a, double* Z, int tile) 
         s_col[threadIdx.x] = pos >= a.col_end ? NOCOL : pos;
       }
     }
-    if (a.zreuse) {  // the slab holds this tile's first adjoint from the previous launch
+    if (ZR) {  // the slab holds this tile's first adjoint from the previous launch
       __syncthreads();
       hvp_stamp(a, tile, 1);
       hvp_stamp(a, tile, 2);
@@ -1693,7 +1695,7 @@ __global__ void __launch_bounds__(NT) hvp_tile_kernel(HvpArgs a) {
 // mean (an SM's CTAs start together, in no fixed order across SMs).
 // ctr: [0] wide claims, [1] narrow queue, [2] heavy end, [3] light end,
 // [4 + smid] CTAs seen per SM; zero before the launch.
-template <int C, int NT>
+template <int C, int NT, bool ZR = false>
 __global__ void __launch_bounds__(NT, 3) hvp_split_kernel(HvpArgs a1, HvpArgs a2, int per_sm, int* ctr) {
   __shared__ int s_pick;
   if (threadIdx.x == 0) {
@@ -1723,9 +1725,9 @@ __global__ void __launch_bounds__(NT, 3) hvp_split_kernel(HvpArgs a1, HvpArgs a2
   if (s_pick < 0) return;
   const int t = s_pick >> 1;
   if ((s_pick & 1) == 0) {
-    if (t < a1.ntiles) hvp_tile<C>(a1, a1.scratch + a1.stride * t, t);
+    if (t < a1.ntiles) hvp_tile<C, ZR>(a1, a1.scratch + a1.stride * t, t);
   } else {
-    if (t < a2.ntiles) hvp_tile<C / 2>(a2, a2.scratch + a2.stride * t, t);
+    if (t < a2.ntiles) hvp_tile<C / 2, ZR>(a2, a2.scratch + a2.stride * t, t);
   }
 }
 
@@ -2267,7 +2269,10 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   const size_t sm = std::max(hvp_smem_bytes(a1, C), hvp_smem_bytes(a2, C / 2));
   const int per_sm = std::max(1, n1 / c->sm_count);
   cudaMemsetAsync(c->split_ctr, 0, sizeof(int) * (4 + kSplitMaxSm), c->stream);
-  hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, per_sm, c->split_ctr);
+  if (a1.zreuse)
+    hvp_split_kernel<C, 256, true><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, per_sm, c->split_ctr);
+  else
+    hvp_split_kernel<C, 256><<<n1 + n2, 256, sm, c->stream>>>(a1, a2, per_sm, c->split_ctr);
   c->launches++;
 }
 
@@ -2297,9 +2302,12 @@ static void setup_hvp_smem_t() {
   cudaFuncSetAttribute(hvp_tile_kernel<C, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
   cudaFuncSetAttribute(hvp_tile_kernel<C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
   cudaFuncSetAttribute(hvp_batch_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, HVP_DYN_SMEM);
-  if (C >= 2)
+  if (C >= 2) {
     cudaFuncSetAttribute(hvp_split_kernel<(C >= 2 ? C : 2), 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          HVP_DYN_SMEM);
+    cudaFuncSetAttribute(hvp_split_kernel<(C >= 2 ? C : 2), 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         HVP_DYN_SMEM);
+  }
 }
 
 void setup_hvp_smem() {
