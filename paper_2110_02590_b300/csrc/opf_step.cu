@@ -182,12 +182,12 @@ __global__ void __launch_bounds__(512) chol_diag_kernel(double* A, int n, int k0
 }
 
 // Panel below the diagonal block: X21 = A21 L_kk^{-T} = A21 Dinv^T as a small
-// GEMM (blockDim / 16 rows x 32 columns per CTA, at most 16 rows), written in place.  Dinv is lower
-// triangular, so column c takes the terms t <= c only; thread (row, c) also
-// owns column 31 - c, and the two runs of term pairs add up to 17 for every
-// thread, so a warp issues 34 FMAs per thread instead of 64 (the FP64 pipe
-// issues whole warp instructions).  Each column keeps the even and the odd
-// terms in separate sums, in increasing t, as the full product would.
+// GEMM (blockDim / 16 rows x 32 columns per CTA, at most 16 rows), written in
+// place.  Dinv is lower triangular, so column c takes the terms t <= c only;
+// thread (row, c) also owns column 31 - c, and the two runs of term pairs add
+// up to 17 for every thread, so a warp issues 34 FMAs per thread instead of 64
+// (the FP64 pipe issues whole warp instructions).  Each column keeps the even
+// and the odd terms in separate sums, in increasing t, as the full product would.
 __global__ void __launch_bounds__(256) chol_trsm_kernel(double* A, int n, int k0, int kb, const int* flag,
                                                         const double* __restrict__ Dinv) {
   pdl_wait();
