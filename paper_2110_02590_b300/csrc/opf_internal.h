@@ -187,6 +187,10 @@ int hvp_tiles(const opf_ctx* c, int C, int col0, int col_end, bool balanced);  /
 // one launch (false when the context has no split tiling at this width).
 bool launch_hvp_split(opf_ctx* c, int C, double* H);
 size_t hvp_split_scratch(const opf_ctx* c, int C);  // doubles of workspace it needs
+// z [n_x] = (dx/du) d from the first adjoints the last split Hessian launch left
+// in its slabs (valid while the factors and the slabs are those of that launch);
+// false (nothing launched) when they are not
+bool launch_state_direction(opf_ctx* c, const double* d, double* z);
 // The plain form: Hessian columns col0 .. col_end - 1 one at a time, each a
 // sequence of device-wide launches around two streamed single-RHS solves;
 // work holds hvp_plain_scratch doubles.  Returns the kernels launched.

@@ -2276,6 +2276,49 @@ static void launch_hvp_split_t(opf_ctx* c, double* H, int lk) {
   c->launches++;
 }
 
+// z = (dx/du) d = sum over the tiles' columns j of Z_j d_j, from the first
+// adjoints Z = G_x^{-1}(-G_u W) the last split Hessian launch left in its slabs
+// (rows in the factor's pivot order, written to their state positions):
+// the state direction of a control step without a triangular solve.
+// blockIdx.y takes a range of tiles; the ranges meet in atomic sums (z zeroed
+// by the caller).
+__global__ void zd_slab_kernel(const double* __restrict__ S1, size_t st1, int n1, int C1,
+                               const double* __restrict__ S2, size_t st2, int n2, int C2,
+                               const int* __restrict__ colmap, const double* __restrict__ d,
+                               const int* __restrict__ perm, int nx, int tiles_per_y, double* z) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx) return;
+  const int t0 = blockIdx.y * tiles_per_y, t1 = min(n1 + n2, t0 + tiles_per_y);
+  double s = 0.0;
+  for (int t = t0; t < t1; t++) {
+    const bool wide = t < n1;
+    const int C = wide ? C1 : C2;
+    const double* Zt = wide ? S1 + st1 * t : S2 + st2 * (t - n1);
+    const int* cm = wide ? colmap + (size_t)t * C1 : colmap + (size_t)n1 * C1 + (size_t)(t - n1) * C2;
+    for (int c = 0; c < C; c++) {
+      const int j = __ldg(cm + c);
+      if (j >= 0) s = fma(Zt[(size_t)k * C + c], __ldg(d + j), s);
+    }
+  }
+  atomicAdd(z + perm[k], s);
+}
+
+bool launch_state_direction(opf_ctx* c, const double* d, double* z) {
+  if (c->z_gen != c->lu_gen || c->z_C < 2) return false;
+  int lk = 0;
+  while ((1 << lk) < c->z_C) lk++;
+  const int n1 = c->split_n1[lk], n2 = c->split_n2[lk], C = c->z_C;
+  if (n1 <= 0 || !c->colmap_split[lk]) return false;
+  const size_t st1 = hvp_stride(c, C), st2 = hvp_stride(c, C / 2);
+  const int nx = c->dn.nx, per_y = 16;
+  cudaMemsetAsync(z, 0, sizeof(double) * (size_t)nx, c->stream);
+  const dim3 grid(nblk(nx, 256), nblk(n1 + n2, per_y));
+  zd_slab_kernel<<<grid, 256, 0, c->stream>>>(c->scratch, st1, n1, C, c->scratch + st1 * (size_t)n1, st2, n2, C / 2,
+                                             c->colmap_split[lk], d, c->dn.perm, nx, per_y, z);
+  c->launches++;
+  return true;
+}
+
 bool launch_hvp_split(opf_ctx* c, int C, double* H) {
   int lk = 0;
   while ((1 << lk) < C) lk++;

@@ -1100,9 +1100,12 @@ opf_status step_end(opf_ctx* c, const opf_al_params* p, opf_al_state* st, const 
   rc = launch_chol_solve(c, w, w->L, nu, w->du);
   if (rc) return rc;
   // J d_u: z = -G_x^{-1} G_u d_u, then the directional derivatives of c
-  gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
-  c->launches++;
-  launch_solve1(c, w->b, w->z, false, -1.0);
+  // (from the Hessian's first adjoints when its slabs still hold them)
+  if (!launch_state_direction(c, w->du, w->z)) {
+    gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
+    c->launches++;
+    launch_solve1(c, w->b, w->z, false, -1.0);
+  }
   jvp_branch_kernel<<<nblk(c->dn.nl, 256), 256, 0, stream>>>(c->dn, c->btab, c->flows, w->z, w->du, w->Jdu);
   jvp_bus_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->z, w->du, w->Jdu);
   c->launches += 2;
@@ -1410,9 +1413,11 @@ extern "C" opf_status opf_tracking_update(opf_ctx* c, const opf_al_params* p, do
     rc = launch_chol_solve(c, w, w->L, nu, w->du);
     if (rc) return rc;
     // J d_u
-    gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
-    c->launches++;
-    launch_solve1(c, w->b, w->z, false, -1.0);
+    if (!launch_state_direction(c, w->du, w->z)) {
+      gu_times_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->du, w->b);
+      c->launches++;
+      launch_solve1(c, w->b, w->z, false, -1.0);
+    }
     jvp_branch_kernel<<<nblk(c->dn.nl, 256), 256, 0, stream>>>(c->dn, c->btab, c->flows, w->z, w->du, w->Jdu);
     jvp_bus_kernel<<<nblk(nb, 256), 256, 0, stream>>>(c->dn, c->btab, w->z, w->du, w->Jdu);
     c->launches += 2;
