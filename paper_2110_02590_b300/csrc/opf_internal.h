@@ -191,6 +191,9 @@ size_t hvp_split_scratch(const opf_ctx* c, int C);  // doubles of workspace it n
 // in its slabs (valid while the factors and the slabs are those of that launch);
 // false (nothing launched) when they are not
 bool launch_state_direction(opf_ctx* c, const double* d, double* z);
+// out [n_u] = base + G_u^T lambda with lambda = -G_x^{-T} w [n_x], from the same
+// slabs (false, nothing launched, when they do not hold the first adjoints)
+bool launch_adjoint_from_slabs(opf_ctx* c, const double* w, const double* base, double* out);
 // The plain form: Hessian columns col0 .. col_end - 1 one at a time, each a
 // sequence of device-wide launches around two streamed single-RHS solves;
 // work holds hvp_plain_scratch doubles.  Returns the kernels launched.

@@ -2042,6 +2042,8 @@ void launch_weighted_grad(opf_ctx* c, const double* w, double* out) {
   c->launches++;
   dF_bus_kernel<<<nblk(n.nb, 256), 256, 0, c->stream>>>(n, c->u, w, c->Pbus, c->pd, 0.0, c->dFx_w, c->dFu_w,
                                                         c->endflow);
+  // d_u + G_u^T lambda = d_u + Z^T d_x from the Hessian's slabs when they hold its first adjoints
+  if (launch_adjoint_from_slabs(c, c->dFx_w, c->dFu_w, out)) return;
   launch_solve1(c, c->dFx_w, c->lam_w, true, -1.0);
   c->launches++;
   grad_u_kernel<<<nblk(n.ngn, 128), 128, 0, c->stream>>>(n, c->lam_w, c->dFu_w, out, c->endflow);
@@ -2301,6 +2303,64 @@ __global__ void zd_slab_kernel(const double* __restrict__ S1, size_t st1, int n1
     }
   }
   atomicAdd(z + perm[k], s);
+}
+
+// out_j = base_j + sum_k Z_j[k] w[perm[k]] for every column j of the tiles whose
+// first adjoints the last split Hessian launch left in its slabs: G_u^T lambda
+// for lambda = -G_x^{-T} w without the transposed solve (Z = -G_x^{-1} G_u).
+// One CTA per tile; each thread sums its rows for the tile's columns, then a
+// block reduction.
+template <int CMAX>
+__global__ void __launch_bounds__(256) zt_slab_kernel(const double* __restrict__ S1, size_t st1, int n1, int C1,
+                                                      const double* __restrict__ S2, size_t st2, int C2,
+                                                      const int* __restrict__ colmap, const double* __restrict__ w,
+                                                      const int* __restrict__ perm, int nx,
+                                                      const double* __restrict__ base, double* out) {
+  __shared__ double red[8][CMAX];
+  const int t = blockIdx.x, wide = t < n1, C = wide ? C1 : C2;
+  const double* Zt = wide ? S1 + st1 * t : S2 + st2 * (t - n1);
+  const int* cm = wide ? colmap + (size_t)t * C1 : colmap + (size_t)n1 * C1 + (size_t)(t - n1) * C2;
+  double acc[CMAX];
+#pragma unroll
+  for (int c = 0; c < CMAX; c++) acc[c] = 0.0;
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+    const double wk = __ldg(w + __ldg(perm + k));
+#pragma unroll
+    for (int c = 0; c < CMAX; c++)
+      if (c < C) acc[c] = fma(Zt[(size_t)k * C + c], wk, acc[c]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < CMAX; c++) {
+    double v = acc[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < C) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); q++) v += red[q][threadIdx.x];
+    const int j = __ldg(cm + threadIdx.x);
+    if (j >= 0) out[j] = base[j] + v;
+  }
+}
+
+bool launch_adjoint_from_slabs(opf_ctx* c, const double* w, const double* base, double* out) {
+  if (c->z_gen != c->lu_gen || c->z_C < 2 || c->z_C > 16) return false;
+  int lk = 0;
+  while ((1 << lk) < c->z_C) lk++;
+  const int n1 = c->split_n1[lk], n2 = c->split_n2[lk], C = c->z_C;
+  if (n1 <= 0 || !c->colmap_split[lk]) return false;
+  const size_t st1 = hvp_stride(c, C), st2 = hvp_stride(c, C / 2);
+  const double* S2 = c->scratch + st1 * (size_t)n1;
+  if (C <= 8)
+    zt_slab_kernel<8><<<n1 + n2, 256, 0, c->stream>>>(c->scratch, st1, n1, C, S2, st2, C / 2, c->colmap_split[lk],
+                                                      w, c->dn.perm, c->dn.nx, base, out);
+  else
+    zt_slab_kernel<16><<<n1 + n2, 256, 0, c->stream>>>(c->scratch, st1, n1, C, S2, st2, C / 2, c->colmap_split[lk],
+                                                       w, c->dn.perm, c->dn.nx, base, out);
+  c->launches++;
+  return true;
 }
 
 bool launch_state_direction(opf_ctx* c, const double* d, double* z) {
